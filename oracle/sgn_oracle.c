@@ -1,0 +1,564 @@
+/*
+ * Oracle for the split-form SBP semi-discretization of the 2D hyperbolized
+ * Serre-Green-Naghdi equations (arXiv 2601.02540).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * CPU restatement of what the GPU library computes.  Only the test-suite, the
+ * smoke check and the CPU-baseline leg of the benchmark may load it.  It shares
+ * no code, header or constant with the CUDA library.
+ *
+ * The same source is compiled twice:
+ *   - with `real` = double           -> liboracle.so       (the reference values)
+ *   - with `real` = double _Complex  -> liboracle_cplx.so  (complex-step
+ *     directional derivatives, i.e. the tangent-linear model: every function
+ *     below is a rational function of the state and the bathymetry, so
+ *     Im f(x + i*eps*d) / eps = f'(x) d to rounding for tiny eps).
+ * Build flags: -O2 -ffp-contract=off (no fused multiply-add), so every
+ * expression is evaluated exactly as written, left to right.
+ *
+ * Layout: a state q holds five planes h, u, v, w, eta (in that order), each
+ * plane nx*ny values with x fastest: q[f*nx*ny + j*nx + i].  The bathymetry b
+ * is one plane.  Node i sits at x_i = xmin + i*dx, j at y_j = ymin + j*dy.
+ *
+ * Citations are to the paper's sections and equations:
+ *   Sec. 4.1, eq. (sd_periodic_2D_SGN)      periodic semi-discretization
+ *   Sec. 4.2, eq. (semi_2D)                 reflecting semi-discretization (SATs)
+ *   Remark "Concrete SBP operators and SATs" (rem:concrete_sbp) operators, M, SATs
+ *   Thm. 4.1 proof, eq. (splitcondition)    energy E and its derivatives
+ *   Sec. 6, eq. (initialization)            eta = h and the initial w
+ */
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#ifdef ORC_COMPLEX
+#include <complex.h>
+typedef double _Complex real;
+#define ORC(name) orcc_##name
+#else
+typedef double real;
+#define ORC(name) orc_##name
+#endif
+
+enum { BC_PERIODIC = 0, BC_REFLECTING = 1 };
+
+/* Planted-mistake hooks for the mutation test.  They exist only in the build
+ * made with -DORC_MUTABLE (never the reference build), where the test selects
+ * one mistake at a time to show that the pins detect it:
+ *   orc_mut_f/orc_mut_k/orc_mut_kind: term k of field f dropped (kind 0),
+ *       sign-flipped (1) or halved (2);
+ *   orc_mut_op: 1 one-sided boundary row with 1/(2dx), 2 periodic wrap
+ *       missing at the last node, 3 SAT weight 1/dx, 4 SAT sign flipped in y,
+ *       5 trapezoid end weights missing in M. */
+#ifdef ORC_MUTABLE
+int orc_mut_f = -1, orc_mut_k = -1, orc_mut_kind = 0, orc_mut_op = 0;
+#define MUT_OP(n) (orc_mut_op == (n))
+#else
+#define MUT_OP(n) 0
+#endif
+enum { F_H = 0, F_U = 1, F_V = 2, F_W = 3, F_ETA = 4, NFIELD = 5 };
+
+typedef struct {
+    int nx, ny;
+    double xmin, xmax, ymin, ymax;
+    int bc;
+    double g, lambda;
+} orc_grid;
+
+/* Grid spacing.  Periodic: nx nodes cover [xmin, xmax) and x_max is the image
+ * of x_min; reflecting: both end points are nodes (Remark rem:concrete_sbp,
+ * and the nodal grid of Sec. 2.2). */
+void ORC(spacing)(const orc_grid* G, double* dx, double* dy)
+{
+    if (G->bc == BC_PERIODIC) {
+        *dx = (G->xmax - G->xmin) / G->nx;
+        *dy = (G->ymax - G->ymin) / G->ny;
+    } else {
+        *dx = (G->xmax - G->xmin) / (G->nx - 1);
+        *dy = (G->ymax - G->ymin) / (G->ny - 1);
+    }
+}
+
+/* Diagonal of the 1D mass matrix M (Remark rem:concrete_sbp):
+ * periodic dx*diag(1,...,1); reflecting dx*diag(1/2,1,...,1,1/2). */
+static double mass_1d(int bc, int i, int n, double d)
+{
+    if (MUT_OP(5)) return d;
+    if (bc == BC_REFLECTING && (i == 0 || i == n - 1)) return 0.5 * d;
+    return d;
+}
+
+/* 2D mass matrix M = M_x (x) M_y, entry for node (i, j). */
+double ORC(mass_weight)(const orc_grid* G, int i, int j)
+{
+    double dx, dy;
+    ORC(spacing)(G, &dx, &dy);
+    return mass_1d(G->bc, i, G->nx, dx) * mass_1d(G->bc, j, G->ny, dy);
+}
+
+/* First-derivative SBP operator along one direction of a 1D line of n values
+ * spaced s apart in memory (Remark rem:concrete_sbp).
+ * Periodic: (f[k+1] - f[k-1]) / (2 d), indices modulo n.
+ * Reflecting: the same central stencil in the interior, and the one-sided
+ * rows (f[1] - f[0]) / d at k = 0 and (f[n-1] - f[n-2]) / d at k = n-1. */
+static void sbp_line(int bc, int n, double d, const real* f, long s, real* out)
+{
+    for (int k = 0; k < n; k++) {
+        real val;
+        if (bc == BC_PERIODIC) {
+            int kp = (k + 1) % n;
+            int km = (k - 1 + n) % n;
+            if (MUT_OP(2) && k == n - 1) kp = k;
+            val = (f[kp * s] - f[km * s]) / (2.0 * d);
+        } else if (k == 0) {
+            val = (f[1 * s] - f[0]) / d;
+            if (MUT_OP(1)) val = (f[1 * s] - f[0]) / (2.0 * d);
+        } else if (k == n - 1) {
+            val = (f[(n - 1) * s] - f[(n - 2) * s]) / d;
+        } else {
+            val = (f[(k + 1) * s] - f[(k - 1) * s]) / (2.0 * d);
+        }
+        out[k * s] = val;
+    }
+}
+
+/* D_x = D (x) I: the 1D operator applied along every row (fixed j). */
+void ORC(dx_apply)(const orc_grid* G, const real* f, real* out)
+{
+    double dx, dy;
+    ORC(spacing)(G, &dx, &dy);
+    for (int j = 0; j < G->ny; j++)
+        sbp_line(G->bc, G->nx, dx, f + (long)j * G->nx, 1, out + (long)j * G->nx);
+}
+
+/* D_y = I (x) D: the 1D operator applied along every column (fixed i). */
+void ORC(dy_apply)(const orc_grid* G, const real* f, real* out)
+{
+    double dx, dy;
+    ORC(spacing)(G, &dx, &dy);
+    for (int i = 0; i < G->nx; i++)
+        sbp_line(G->bc, G->ny, dy, f + i, G->nx, out + i);
+}
+
+/* Derivatives needed by the right-hand side: the twelve D_x and twelve D_y
+ * operands of eqs. (sd_periodic_2D_SGN) / (semi_2D), each as a full plane. */
+enum {
+    P_H, P_U, P_V, P_W, P_ETA, P_B,
+    P_HS,      /* h (h + b)     */
+    P_UU,      /* u^2           */
+    P_VV,      /* v^2           */
+    P_HU,      /* h u           */
+    P_HV,      /* h v           */
+    P_HUV,     /* h u v         */
+    P_HUW,     /* h u w         */
+    P_HVW,     /* h v w         */
+    P_E2H,     /* eta^2 / h     */
+    NPROD
+};
+
+typedef struct {
+    long n;
+    real* dx[NPROD];
+    real* dy[NPROD];
+    real* buf;
+} derivs;
+
+static int derivs_compute(const orc_grid* G, const real* b, const real* q, derivs* D)
+{
+    long n = (long)G->nx * G->ny;
+    D->n = n;
+    D->buf = (real*)malloc(sizeof(real) * n * (2 * NPROD + 1));
+    if (!D->buf) return -1;
+    real* prod = D->buf + 2 * NPROD * n;
+    const real* h = q + F_H * n;
+    const real* u = q + F_U * n;
+    const real* v = q + F_V * n;
+    const real* w = q + F_W * n;
+    const real* eta = q + F_ETA * n;
+    for (int p = 0; p < NPROD; p++) {
+        D->dx[p] = D->buf + (2 * p) * n;
+        D->dy[p] = D->buf + (2 * p + 1) * n;
+        for (long c = 0; c < n; c++) {
+            real val;
+            switch (p) {
+            case P_H:   val = h[c]; break;
+            case P_U:   val = u[c]; break;
+            case P_V:   val = v[c]; break;
+            case P_W:   val = w[c]; break;
+            case P_ETA: val = eta[c]; break;
+            case P_B:   val = b[c]; break;
+            case P_HS:  val = h[c] * (h[c] + b[c]); break;
+            case P_UU:  val = u[c] * u[c]; break;
+            case P_VV:  val = v[c] * v[c]; break;
+            case P_HU:  val = h[c] * u[c]; break;
+            case P_HV:  val = h[c] * v[c]; break;
+            case P_HUV: val = h[c] * u[c] * v[c]; break;
+            case P_HUW: val = h[c] * u[c] * w[c]; break;
+            case P_HVW: val = h[c] * v[c] * w[c]; break;
+            default:    val = eta[c] * eta[c] / h[c]; break; /* P_E2H */
+            }
+            prod[c] = val;
+        }
+        ORC(dx_apply)(G, prod, D->dx[p]);
+        ORC(dy_apply)(G, prod, D->dy[p]);
+    }
+    return 0;
+}
+
+/* The individual terms of each equation at one node, in the order printed in
+ * eqs. (sd_periodic_2D_SGN) / (semi_2D).  For h, u, v, w the terms are those
+ * of the left-hand side (the time derivative moved aside); the caller combines
+ * them.  Returned counts: nt[f] terms for field f. */
+#define MAXTERMS 16
+typedef struct {
+    int nt[NFIELD];
+    real t[NFIELD][MAXTERMS];
+} node_terms;
+
+static void terms_at(const orc_grid* G, const real* b, const real* q, const derivs* D,
+                     long c, int i, int j, node_terms* T)
+{
+    const long n = D->n;
+    const double g = G->g, lam = G->lambda;
+    const real h = q[F_H * n + c], u = q[F_U * n + c], v = q[F_V * n + c];
+    const real w = q[F_W * n + c], eta = q[F_ETA * n + c], bb = b[c];
+    (void)bb;
+#define DX(p) (D->dx[p][c])
+#define DY(p) (D->dy[p][c])
+    int k;
+
+    /* h equation: h_t + u D_x h + h D_x u + v D_y h + h D_y v - SAT = 0 */
+    k = 0;
+    T->t[F_H][k++] = u * DX(P_H);
+    T->t[F_H][k++] = h * DX(P_U);
+    T->t[F_H][k++] = v * DY(P_H);
+    T->t[F_H][k++] = h * DY(P_V);
+    if (G->bc == BC_REFLECTING) {
+        /* -M^{-1} R^T B N_x R (h u) - M^{-1} R^T B N_y R (h v), evaluated as in
+         * Remark rem:concrete_sbp; corners receive both contributions. */
+        double dx, dy;
+        ORC(spacing)(G, &dx, &dy);
+        real satx = 0.0, saty = 0.0;
+        if (MUT_OP(3)) dx = 2.0 * dx;
+        if (MUT_OP(4)) dy = -dy;
+        if (i == 0) satx = -(2.0 / dx) * (h * u);
+        if (i == G->nx - 1) satx = (2.0 / dx) * (h * u);
+        if (j == 0) saty = -(2.0 / dy) * (h * v);
+        if (j == G->ny - 1) saty = (2.0 / dy) * (h * v);
+        T->t[F_H][k++] = -satx;
+        T->t[F_H][k++] = -saty;
+    }
+    T->nt[F_H] = k;
+
+    /* h u_t + [these terms] = 0 */
+    k = 0;
+    T->t[F_U][k++] = g * DX(P_HS);
+    T->t[F_U][k++] = -g * (h + bb) * DX(P_H);
+    T->t[F_U][k++] = 0.5 * h * DX(P_UU);
+    T->t[F_U][k++] = -0.5 * (u * u) * DX(P_H);
+    T->t[F_U][k++] = 0.5 * u * DX(P_HU);
+    T->t[F_U][k++] = -0.5 * (h * u) * DX(P_U);
+    T->t[F_U][k++] = 0.5 * DY(P_HUV);
+    T->t[F_U][k++] = -0.5 * (u * v) * DY(P_H);
+    T->t[F_U][k++] = 0.5 * (h * v) * DY(P_U);
+    T->t[F_U][k++] = -0.5 * (h * u) * DY(P_V);
+    T->t[F_U][k++] = (lam / 6.0) * (eta * eta / (h * h)) * DX(P_H);
+    T->t[F_U][k++] = (lam / 3.0) * DX(P_ETA);
+    T->t[F_U][k++] = -(lam / 3.0) * (eta / h) * DX(P_ETA);
+    T->t[F_U][k++] = -(lam / 6.0) * DX(P_E2H);
+    T->t[F_U][k++] = (lam / 2.0) * (1.0 - eta / h) * DX(P_B);
+    T->nt[F_U] = k;
+
+    /* h v_t + [these terms] = 0 */
+    k = 0;
+    T->t[F_V][k++] = g * DY(P_HS);
+    T->t[F_V][k++] = -g * (h + bb) * DY(P_H);
+    T->t[F_V][k++] = 0.5 * h * DY(P_VV);
+    T->t[F_V][k++] = -0.5 * (v * v) * DY(P_H);
+    T->t[F_V][k++] = 0.5 * v * DY(P_HV);
+    T->t[F_V][k++] = -0.5 * (h * v) * DY(P_V);
+    T->t[F_V][k++] = 0.5 * DX(P_HUV);
+    T->t[F_V][k++] = -0.5 * (u * v) * DX(P_H);
+    T->t[F_V][k++] = 0.5 * (h * u) * DX(P_V);
+    T->t[F_V][k++] = -0.5 * (h * v) * DX(P_U);
+    T->t[F_V][k++] = (lam / 6.0) * (eta * eta / (h * h)) * DY(P_H);
+    T->t[F_V][k++] = (lam / 3.0) * DY(P_ETA);
+    T->t[F_V][k++] = -(lam / 3.0) * (eta / h) * DY(P_ETA);
+    T->t[F_V][k++] = -(lam / 6.0) * DY(P_E2H);
+    T->t[F_V][k++] = (lam / 2.0) * (1.0 - eta / h) * DY(P_B);
+    T->nt[F_V] = k;
+
+    /* h w_t + [these terms] = lambda (1 - eta/h); the source is stored as the
+     * last term with its sign flipped so that all terms share one convention. */
+    k = 0;
+    T->t[F_W][k++] = 0.5 * DX(P_HUW);
+    T->t[F_W][k++] = 0.5 * (h * u) * DX(P_W);
+    T->t[F_W][k++] = -0.5 * (u * w) * DX(P_H);
+    T->t[F_W][k++] = -0.5 * (h * w) * DX(P_U);
+    T->t[F_W][k++] = 0.5 * DY(P_HVW);
+    T->t[F_W][k++] = 0.5 * (h * v) * DY(P_W);
+    T->t[F_W][k++] = -0.5 * (v * w) * DY(P_H);
+    T->t[F_W][k++] = -0.5 * (h * w) * DY(P_V);
+    T->t[F_W][k++] = -lam * (1.0 - eta / h);
+    T->nt[F_W] = k;
+
+    /* eta_t + [these terms] = 0, with the source w stored as -w */
+    k = 0;
+    T->t[F_ETA][k++] = u * DX(P_ETA);
+    T->t[F_ETA][k++] = v * DY(P_ETA);
+    T->t[F_ETA][k++] = 1.5 * u * DX(P_B);
+    T->t[F_ETA][k++] = 1.5 * v * DY(P_B);
+    T->t[F_ETA][k++] = -w;
+    T->nt[F_ETA] = k;
+#undef DX
+#undef DY
+#ifdef ORC_MUTABLE
+    if (orc_mut_f >= 0 && orc_mut_k < T->nt[orc_mut_f]) {
+        real* tm = &T->t[orc_mut_f][orc_mut_k];
+        *tm = orc_mut_kind == 0 ? 0.0 : (orc_mut_kind == 1 ? -*tm : 0.5 * *tm);
+    }
+#endif
+}
+
+/* Right-hand side dq/dt of eq. (sd_periodic_2D_SGN) (periodic) or eq.
+ * (semi_2D) (reflecting).  The h and eta equations give the time derivative
+ * directly; the u, v, w equations give h times it, so their sums are divided
+ * by h.  Returns 0, or -1 when out of memory. */
+int ORC(rhs)(const orc_grid* G, const real* b, const real* q, real* dq)
+{
+    derivs D;
+    if (derivs_compute(G, b, q, &D)) return -1;
+    const long n = D.n;
+    for (int j = 0; j < G->ny; j++)
+        for (int i = 0; i < G->nx; i++) {
+            long c = (long)j * G->nx + i;
+            node_terms T;
+            terms_at(G, b, q, &D, c, i, j, &T);
+            const real h = q[F_H * n + c];
+            for (int f = 0; f < NFIELD; f++) {
+                real s = 0.0;
+                for (int k = 0; k < T.nt[f]; k++) s = s + T.t[f][k];
+                real val = -s;
+                if (f == F_U || f == F_V || f == F_W) val = val / h;
+                dq[f * n + c] = val;
+            }
+        }
+    free(D.buf);
+    return 0;
+}
+
+#ifndef ORC_COMPLEX
+/* Magnitude scale of each RHS value: the sum of the absolute values of the
+ * terms that are added to form it (divided by |h| where the RHS is).  The
+ * rounding error of any evaluation order of the sum is bounded by a small
+ * multiple of unit round-off times this scale, so parity tolerances are
+ * stated relative to it. */
+int orc_rhs_scale(const orc_grid* G, const real* b, const real* q, real* scale)
+{
+    derivs D;
+    if (derivs_compute(G, b, q, &D)) return -1;
+    const long n = D.n;
+    for (int j = 0; j < G->ny; j++)
+        for (int i = 0; i < G->nx; i++) {
+            long c = (long)j * G->nx + i;
+            node_terms T;
+            terms_at(G, b, q, &D, c, i, j, &T);
+            const real h = q[F_H * n + c];
+            for (int f = 0; f < NFIELD; f++) {
+                real s = 0.0;
+                for (int k = 0; k < T.nt[f]; k++) s += fabs(T.t[f][k]);
+                if (f == F_U || f == F_V || f == F_W) s = s / fabs(h);
+                scale[f * n + c] = s;
+            }
+        }
+    free(D.buf);
+    return 0;
+}
+#endif
+
+/* Initialization of the auxiliary variables, eq. (initialization):
+ * eta = h, w = -h (D_x u + D_y v) + 3/2 (u D_x b + v D_y b). */
+int ORC(init_aux)(const orc_grid* G, const real* b, real* q)
+{
+    const long n = (long)G->nx * G->ny;
+    real* tmp = (real*)malloc(sizeof(real) * n * 4);
+    if (!tmp) return -1;
+    real *dxu = tmp, *dyv = tmp + n, *dxb = tmp + 2 * n, *dyb = tmp + 3 * n;
+    ORC(dx_apply)(G, q + F_U * n, dxu);
+    ORC(dy_apply)(G, q + F_V * n, dyv);
+    ORC(dx_apply)(G, b, dxb);
+    ORC(dy_apply)(G, b, dyb);
+    for (long c = 0; c < n; c++) {
+        const real h = q[F_H * n + c], u = q[F_U * n + c], v = q[F_V * n + c];
+        q[F_ETA * n + c] = h;
+        q[F_W * n + c] = -h * (dxu[c] + dyv[c]) + 1.5 * (u * dxb[c] + v * dyb[c]);
+    }
+    free(tmp);
+    return 0;
+}
+
+/* Classical fourth-order Runge-Kutta, fixed step dt, nsteps steps, in place:
+ * k1 = f(q), k2 = f(q + dt/2 k1), k3 = f(q + dt/2 k2), k4 = f(q + dt k3),
+ * q <- q + dt/6 (k1 + 2 k2 + 2 k3 + k4). */
+int ORC(rk4)(const orc_grid* G, const real* b, real* q, double dt, int nsteps)
+{
+    const long m = (long)NFIELD * G->nx * G->ny;
+    real* buf = (real*)malloc(sizeof(real) * m * 5);
+    if (!buf) return -1;
+    real *k1 = buf, *k2 = buf + m, *k3 = buf + 2 * m, *k4 = buf + 3 * m, *y = buf + 4 * m;
+    int rc = 0;
+    for (int s = 0; s < nsteps && rc == 0; s++) {
+        rc |= ORC(rhs)(G, b, q, k1);
+        for (long c = 0; c < m; c++) y[c] = q[c] + (dt / 2.0) * k1[c];
+        rc |= ORC(rhs)(G, b, y, k2);
+        for (long c = 0; c < m; c++) y[c] = q[c] + (dt / 2.0) * k2[c];
+        rc |= ORC(rhs)(G, b, y, k3);
+        for (long c = 0; c < m; c++) y[c] = q[c] + dt * k3[c];
+        rc |= ORC(rhs)(G, b, y, k4);
+        for (long c = 0; c < m; c++)
+            q[c] = q[c] + (dt / 6.0) * (k1[c] + 2.0 * k2[c] + 2.0 * k3[c] + k4[c]);
+    }
+    free(buf);
+    return rc;
+}
+
+/* Pointwise energy of Thm. 4.1:
+ * E = h ((u^2 + v^2)/2 + w^2/6 + g/2 (h + 2 b) + lambda/6 (eta/h - 1)^2). */
+static real energy_density(double g, double lam, real h, real u, real v, real w, real eta, real b)
+{
+    real r = eta / h - 1.0;
+    return h * ((u * u + v * v) / 2.0 + w * w / 6.0 + (g / 2.0) * (h + 2.0 * b) + (lam / 6.0) * r * r);
+}
+
+/* Total energy 1^T M E (plain left-to-right sum; the complex build gives its
+ * directional derivative by complex step).  Result written to *out. */
+void ORC(energy_total)(const orc_grid* G, const real* b, const real* q, real* out)
+{
+    const long n = (long)G->nx * G->ny;
+    real s = 0.0;
+    for (int j = 0; j < G->ny; j++)
+        for (int i = 0; i < G->nx; i++) {
+            long c = (long)j * G->nx + i;
+            real e = energy_density(G->g, G->lambda, q[F_H * n + c], q[F_U * n + c], q[F_V * n + c],
+                                    q[F_W * n + c], q[F_ETA * n + c], b[c]);
+            s += ORC(mass_weight)(G, i, j) * e;
+        }
+    *out = s;
+}
+
+/* Gauge recording and gauge-misfit loss for the inversion problem: run nsteps
+ * RK4 steps from q0 (copied), and every `every` steps read h at `ng` gauge
+ * nodes (flat node indices).  record: writes them to out[(k-1)*ng + g];
+ * loss: returns sum over k, g of (h - obs)^2. */
+int ORC(gauge_run)(const orc_grid* G, const real* b, const real* q0, double dt, int nsteps,
+                   int every, int ng, const long* gauge, const double* obs, real* out, real* loss)
+{
+    const long m = (long)NFIELD * G->nx * G->ny;
+    real* q = (real*)malloc(sizeof(real) * m);
+    if (!q) return -1;
+    memcpy(q, q0, sizeof(real) * m);
+    real acc = 0.0;
+    int rc = 0;
+    for (int k = 1; every * k <= nsteps && rc == 0; k++) {
+        rc |= ORC(rk4)(G, b, q, dt, every);
+        for (int gi = 0; gi < ng; gi++) {
+            real hv = q[F_H * (long)G->nx * G->ny + gauge[gi]];
+            if (out) out[(long)(k - 1) * ng + gi] = hv;
+            if (obs) {
+                real d = hv - obs[(long)(k - 1) * ng + gi];
+                acc += d * d;
+            }
+        }
+    }
+    if (loss) *loss = acc;
+    free(q);
+    return rc;
+}
+
+/* Energy rate along a direction d: sum over nodes of M * (d_q E . d), with the
+ * derivatives of E listed after eq. (splitcondition):
+ *   dE/dh = u^2/2 + v^2/2 + w^2/6 + g h + g b + lambda/6 (1 - eta^2/h^2),
+ *   dE/du = h u,  dE/dv = h v,  dE/dw = h w / 3,  dE/deta = -lambda/3 (1 - eta/h).
+ * Plain left-to-right sum; result written to *out. */
+void ORC(energy_rate)(const orc_grid* G, const real* b, const real* q, const real* d, real* out)
+{
+    const long n = (long)G->nx * G->ny;
+    const double g = G->g, lam = G->lambda;
+    real s = 0.0;
+    for (int j = 0; j < G->ny; j++)
+        for (int i = 0; i < G->nx; i++) {
+            long c = (long)j * G->nx + i;
+            real h = q[F_H * n + c], u = q[F_U * n + c], v = q[F_V * n + c];
+            real w = q[F_W * n + c], eta = q[F_ETA * n + c], bb = b[c];
+            real dEh = 0.5 * u * u + 0.5 * v * v + w * w / 6.0 + g * h + g * bb
+                     + (lam / 6.0) * (1.0 - eta * eta / (h * h));
+            real r = dEh * d[F_H * n + c] + (h * u) * d[F_U * n + c] + (h * v) * d[F_V * n + c]
+                   + (h * w / 3.0) * d[F_W * n + c] - (lam / 3.0) * (1.0 - eta / h) * d[F_ETA * n + c];
+            s += ORC(mass_weight)(G, i, j) * r;
+        }
+    *out = s;
+}
+
+#ifndef ORC_COMPLEX
+/* Neumaier-compensated running sum. */
+typedef struct { double s, c; } csum;
+static void csum_add(csum* a, double x)
+{
+    double t = a->s + x;
+    if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+    else a->c += (x - t) + a->s;
+    a->s = t;
+}
+
+/* Diagnostics (Thm. 4.1 / 4.2 and eq. (splitcondition)), compensated sums:
+ *   out[0] = 1^T M h                            total mass
+ *   out[1] = 1^T M E                            total energy
+ *   out[2] = 1^T M E',  E' = E + g b^2 / 2      the same energy shifted by a
+ *            time-independent constant: h(u^2+v^2)/2 + h w^2/6 + g/2 (h+b)^2
+ *            + lambda h/6 (eta/h - 1)^2
+ *   out[3] = <d_q E, dq/dt>_M                   semi-discrete energy rate
+ *   out[4] = sum M sum_k |d_{q_k} E| * scale_k  magnitude scale of out[3]
+ *            (scale_k = orc_rhs_scale), bounding its rounding error. */
+int orc_diagnostics(const orc_grid* G, const double* b, const double* q, double* out)
+{
+    const long n = (long)G->nx * G->ny;
+    double* dq = (double*)malloc(sizeof(double) * n * NFIELD * 2);
+    if (!dq) return -1;
+    double* sc = dq + n * NFIELD;
+    if (orc_rhs(G, b, q, dq) || orc_rhs_scale(G, b, q, sc)) { free(dq); return -1; }
+    const double g = G->g, lam = G->lambda;
+    csum mass = {0, 0}, en = {0, 0}, en2 = {0, 0}, rate = {0, 0}, rsc = {0, 0};
+    for (int j = 0; j < G->ny; j++)
+        for (int i = 0; i < G->nx; i++) {
+            long c = (long)j * G->nx + i;
+            double M = orc_mass_weight(G, i, j);
+            double h = q[F_H * n + c], u = q[F_U * n + c], v = q[F_V * n + c];
+            double w = q[F_W * n + c], eta = q[F_ETA * n + c], bb = b[c];
+            double rho = eta / h;
+            csum_add(&mass, M * h);
+            csum_add(&en, M * energy_density(g, lam, h, u, v, w, eta, bb));
+            double e2 = h * (u * u + v * v) / 2.0 + h * w * w / 6.0 + (g / 2.0) * (h + bb) * (h + bb)
+                      + (lam / 6.0) * h * (rho - 1.0) * (rho - 1.0);
+            csum_add(&en2, M * e2);
+            /* derivatives of E, as listed after eq. (splitcondition) */
+            double dEh = 0.5 * u * u + 0.5 * v * v + w * w / 6.0 + g * h + g * bb
+                       + (lam / 6.0) * (1.0 - eta * eta / (h * h));
+            double dEu = h * u, dEv = h * v, dEw = h * w / 3.0;
+            double dEeta = -(lam / 3.0) * (1.0 - eta / h);
+            double r = dEh * dq[F_H * n + c] + dEu * dq[F_U * n + c] + dEv * dq[F_V * n + c]
+                     + dEw * dq[F_W * n + c] + dEeta * dq[F_ETA * n + c];
+            csum_add(&rate, M * r);
+            double s = fabs(dEh) * sc[F_H * n + c] + fabs(dEu) * sc[F_U * n + c]
+                     + fabs(dEv) * sc[F_V * n + c] + fabs(dEw) * sc[F_W * n + c]
+                     + fabs(dEeta) * sc[F_ETA * n + c];
+            csum_add(&rsc, M * s);
+        }
+    out[0] = mass.s + mass.c;
+    out[1] = en.s + en.c;
+    out[2] = en2.s + en2.c;
+    out[3] = rate.s + rate.c;
+    out[4] = rsc.s + rsc.c;
+    free(dq);
+    return 0;
+}
+#endif

@@ -1,0 +1,315 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module is shared by the CUDA path, the oracle tests and the benchmark.
+It holds none of the method's arithmetic: it only draws bathymetries, initial
+water heights and velocities, the fixed time step, gauge positions and random
+directions.  The auxiliary variables (eta, w) are NOT set here; each side runs
+its own initialization (eq. (initialization) of Sec. 6).
+
+All draws use numpy's PCG64 with seed 1000 + workload number, in the order
+written in each function, so that every consumer sees identical bits.
+
+Workloads (stand-ins for the paper's Gaussian-obstacle / dam-break style
+problems; none of the paper's measured data is used):
+  1  periodic [-50,50]^2, flat b = 0, h = 1 + 0.1 exp(-(x^2+y^2)/25)
+  2  reflecting [0,200]x[0,100], b = -1 + 8 Gaussian bumps, one Gaussian hump
+  3  periodic square, dx = dy = 0.1, b = -1 + smooth random Fourier field
+     (64 modes, rms 0.1), 16 Gaussian humps
+  4  reflecting [0,100]^2, b as workload 2, plus a perturbed "truth" bathymetry,
+     16 gauges for the inversion loss, 20 random directions
+  5  ragged ensemble: 256 square instances of sizes {128,...,512}
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+PERIODIC = 0
+REFLECTING = 1
+G_DEFAULT = 9.81
+LAMBDA_DEFAULT = 500.0
+
+
+@dataclass
+class Problem:
+    """One synthetic instance: grid, bathymetry and the raw initial state.
+
+    q0 has the five planes (h, u, v, w, eta) with w = 0 and eta = 0 left for
+    the consumer's own initialization of the auxiliary variables.
+    """
+    nx: int
+    ny: int
+    xmin: float
+    xmax: float
+    ymin: float
+    ymax: float
+    bc: int
+    b: np.ndarray
+    q0: np.ndarray
+    g: float = G_DEFAULT
+    lam: float = LAMBDA_DEFAULT
+    dt: float = 0.0
+    nsteps: int = 0
+    name: str = ""
+    extra: dict = field(default_factory=dict)
+
+    def spacing(self) -> tuple[float, float]:
+        if self.bc == PERIODIC:
+            return (self.xmax - self.xmin) / self.nx, (self.ymax - self.ymin) / self.ny
+        return (self.xmax - self.xmin) / (self.nx - 1), (self.ymax - self.ymin) / (self.ny - 1)
+
+    def nodes(self) -> tuple[np.ndarray, np.ndarray]:
+        dx, dy = self.spacing()
+        return self.xmin + dx * np.arange(self.nx), self.ymin + dy * np.arange(self.ny)
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny
+
+
+def _mesh(nx, ny, xmin, xmax, ymin, ymax, bc):
+    if bc == PERIODIC:
+        dx, dy = (xmax - xmin) / nx, (ymax - ymin) / ny
+    else:
+        dx, dy = (xmax - xmin) / (nx - 1), (ymax - ymin) / (ny - 1)
+    x = xmin + dx * np.arange(nx)
+    y = ymin + dy * np.arange(ny)
+    return np.meshgrid(x, y)  # X[j, i], Y[j, i]
+
+
+def _dist2(X, Y, x0, y0, bc, lx, ly):
+    """Squared distance; minimum image on periodic domains."""
+    ddx = X - x0
+    ddy = Y - y0
+    if bc == PERIODIC:
+        ddx = ddx - lx * np.round(ddx / lx)
+        ddy = ddy - ly * np.round(ddy / ly)
+    return ddx * ddx + ddy * ddy
+
+
+def cfl_dt(b: np.ndarray, h: np.ndarray, u: np.ndarray, v: np.ndarray, dx: float, dy: float,
+           g: float, lam: float, cfl: float = 0.2) -> float:
+    """Fixed time step: cfl * min(dx, dy) / (max(|u|,|v|) + sqrt(g max h + lambda/3)).
+
+    The lambda/3 term is the squared frozen-coefficient speed of the relaxation
+    pressure at eta = h (linearizing p(h, eta) of Sec. 3.2), computed once from
+    the initial state and held fixed.
+    """
+    umax = float(max(np.abs(u).max(), np.abs(v).max()))
+    c = umax + np.sqrt(g * float(h.max()) + lam / 3.0)
+    return cfl * min(dx, dy) / c
+
+
+def _raw_state(h, u=None, v=None):
+    ny, nx = h.shape
+    q = np.zeros((5, ny, nx))
+    q[0] = h
+    if u is not None:
+        q[1] = u
+    if v is not None:
+        q[2] = v
+    return q
+
+
+def _bumps(rng, n, X, Y, bc, xmin, xmax, ymin, ymax, amp, width):
+    """Sum of n Gaussian bumps a exp(-r^2/w^2); centres, amplitudes, widths drawn
+    in that order per bump."""
+    lx, ly = xmax - xmin, ymax - ymin
+    s = np.zeros_like(X)
+    params = []
+    for _ in range(n):
+        x0 = rng.uniform(xmin, xmax)
+        y0 = rng.uniform(ymin, ymax)
+        a = rng.uniform(*amp)
+        w = rng.uniform(*width)
+        params.append((x0, y0, a, w))
+    for x0, y0, a, w in params:
+        s += a * np.exp(-_dist2(X, Y, x0, y0, bc, lx, ly) / (w * w))
+    return s, params
+
+
+def _cap(bumps: np.ndarray, limit: float = 0.8) -> tuple[np.ndarray, bool]:
+    """Keep a rest depth of at least 1 - limit: scale the bumps if their sum
+    exceeds `limit` (the paper excludes dry states)."""
+    m = float(bumps.max())
+    if m > limit:
+        return bumps * (limit / m), True
+    return bumps, False
+
+
+# ----------------------------------------------------------------------------- workloads
+def workload1(nx: int = 64, ny: int = 64, nsteps: int = 200) -> Problem:
+    """Periodic [-50,50]^2, flat bottom, h = 1 + 0.1 exp(-(x^2+y^2)/25)."""
+    xmin, xmax, ymin, ymax = -50.0, 50.0, -50.0, 50.0
+    X, Y = _mesh(nx, ny, xmin, xmax, ymin, ymax, PERIODIC)
+    b = np.zeros((ny, nx))
+    h = 1.0 + 0.1 * np.exp(-(X * X + Y * Y) / 25.0)
+    q = _raw_state(h)
+    p = Problem(nx, ny, xmin, xmax, ymin, ymax, PERIODIC, b, q, nsteps=nsteps, name="workload1")
+    dx, dy = p.spacing()
+    p.dt = cfl_dt(b, h, q[1], q[2], dx, dy, p.g, p.lam)
+    return p
+
+
+def workload2(nx: int = 1024, ny: int = 512, nsteps: int = 2000, seed: int = 1002) -> Problem:
+    """Reflecting [0,200]x[0,100], b = -1 + 8 bumps (a~U(0.1,0.5), w~U(5,20)),
+    one hump 0.05 exp(-r^2/25) centred in [20,180]x[20,80]."""
+    xmin, xmax, ymin, ymax = 0.0, 200.0, 0.0, 100.0
+    return _reflecting_bumpy(nx, ny, nsteps, seed, xmin, xmax, ymin, ymax, "workload2",
+                             hump_amp=(0.05, 0.05), hump_box=(20.0, 180.0, 20.0, 80.0))
+
+
+def _reflecting_bumpy(nx, ny, nsteps, seed, xmin, xmax, ymin, ymax, name, hump_amp, hump_box,
+                      bc=REFLECTING, rng=None):
+    rng = rng if rng is not None else np.random.Generator(np.random.PCG64(seed))
+    X, Y = _mesh(nx, ny, xmin, xmax, ymin, ymax, bc)
+    bumps, params = _bumps(rng, 8, X, Y, bc, xmin, xmax, ymin, ymax, (0.1, 0.5), (5.0, 20.0))
+    bumps, capped = _cap(bumps)
+    b = -1.0 + bumps
+    hx = rng.uniform(hump_box[0], hump_box[1])
+    hy = rng.uniform(hump_box[2], hump_box[3])
+    ha = rng.uniform(*hump_amp) if hump_amp[0] != hump_amp[1] else hump_amp[0]
+    hump = ha * np.exp(-_dist2(X, Y, hx, hy, bc, xmax - xmin, ymax - ymin) / 25.0)
+    h = -b + hump
+    q = _raw_state(h)
+    p = Problem(nx, ny, xmin, xmax, ymin, ymax, bc, b, q, nsteps=nsteps, name=name,
+                extra=dict(capped=capped, bumps=params, hump=(hx, hy, ha)))
+    dx, dy = p.spacing()
+    p.dt = cfl_dt(b, h, q[1], q[2], dx, dy, p.g, p.lam)
+    return p
+
+
+def workload3(nx: int = 8192, ny: int = 8192, nsteps: int = 500, seed: int = 1003,
+              spacing: float = 0.1) -> Problem:
+    """Periodic, dx = dy = 0.1, b = -1 + 0.1 F / rms(F) with F a sum of 64
+    random-phase Fourier modes (integer wavenumbers in [-8,8]^2 without 0),
+    h = -b + 16 Gaussian humps (a~U(0.01,0.1), w~U(5,20))."""
+    lx, ly = nx * spacing, ny * spacing
+    xmin, xmax, ymin, ymax = 0.0, lx, 0.0, ly
+    rng = np.random.Generator(np.random.PCG64(seed))
+    modes = []
+    while len(modes) < 64:
+        kx, ky = rng.integers(-8, 9, size=2)
+        if kx == 0 and ky == 0:
+            continue
+        modes.append((int(kx), int(ky), rng.uniform(0.0, 2.0 * np.pi)))
+    x = xmin + spacing * np.arange(nx)
+    y = ymin + spacing * np.arange(ny)
+    # cos(a + b) = cos a cos b - sin a sin b keeps memory at a few planes
+    F = np.zeros((ny, nx))
+    for kx, ky, ph in modes:
+        ax = 2.0 * np.pi * kx * x / lx + ph
+        ay = 2.0 * np.pi * ky * y / ly
+        F += np.outer(np.cos(ay), np.cos(ax)) - np.outer(np.sin(ay), np.sin(ax))
+    rms = float(np.sqrt(np.mean(F * F)))
+    b = -1.0 + 0.1 * F / rms
+    del F
+    humps = np.zeros((ny, nx))
+    params = []
+    for _ in range(16):
+        x0 = rng.uniform(xmin, xmax)
+        y0 = rng.uniform(ymin, ymax)
+        a = rng.uniform(0.01, 0.1)
+        w = rng.uniform(5.0, 20.0)
+        params.append((x0, y0, a, w))
+    for x0, y0, a, w in params:
+        ddx = x - x0
+        ddx = ddx - lx * np.round(ddx / lx)
+        ddy = y - y0
+        ddy = ddy - ly * np.round(ddy / ly)
+        humps += a * np.outer(np.exp(-ddy * ddy / (w * w)), np.exp(-ddx * ddx / (w * w)))
+    h = -b + humps
+    del humps
+    q = _raw_state(h)
+    p = Problem(nx, ny, xmin, xmax, ymin, ymax, PERIODIC, b, q, nsteps=nsteps, name="workload3",
+                extra=dict(modes=modes, humps=params))
+    p.dt = cfl_dt(b, h, q[1], q[2], spacing, spacing, p.g, p.lam)
+    return p
+
+
+def workload4(n: int = 512, nsteps: int = 2000, seed: int = 1004, every: int = 10,
+              ngauges: int = 16, ndirs: int = 20) -> Problem:
+    """Inversion: reflecting [0,100]^2, b as workload 2; truth bathymetry
+    b_true = b + 4 bumps (a~U(0.02,0.05), w~U(5,15)); both runs start from the
+    same free surface (h0 = zeta0 - b); 16 gauge nodes drawn in [n/8, 7n/8)^2;
+    20 unit-norm Gaussian directions over (b, h0)."""
+    xmin, xmax, ymin, ymax = 0.0, 100.0, 0.0, 100.0
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p = _reflecting_bumpy(n, n, nsteps, seed, xmin, xmax, ymin, ymax, "workload4",
+                          hump_amp=(0.05, 0.05), hump_box=(20.0, 80.0, 20.0, 80.0), rng=rng)
+    X, Y = _mesh(n, n, xmin, xmax, ymin, ymax, REFLECTING)
+    pert, pparams = _bumps(rng, 4, X, Y, REFLECTING, xmin, xmax, ymin, ymax, (0.02, 0.05), (5.0, 15.0))
+    zeta0 = p.q0[0] + p.b            # free surface of the model run
+    b_true = p.b + pert
+    h_true0 = zeta0 - b_true
+    lo, hi = n // 8, (7 * n) // 8
+    gi = rng.integers(lo, hi, size=ngauges)
+    gj = rng.integers(lo, hi, size=ngauges)
+    gauges = (gj * n + gi).astype(np.int64)
+    dirs = rng.standard_normal((ndirs, 2, n, n))
+    dirs /= np.sqrt(np.sum(dirs * dirs, axis=(1, 2, 3)))[:, None, None, None]
+    p.extra.update(b_true=b_true, h_true0=h_true0, gauges=gauges, every=every, dirs=dirs,
+                   pert=pparams)
+    # one dt for both runs (the larger of the two max depths)
+    dx, dy = p.spacing()
+    p.dt = min(p.dt, cfl_dt(b_true, h_true0, p.q0[1], p.q0[2], dx, dy, p.g, p.lam))
+    return p
+
+
+ENSEMBLE_SIZES = (128, 192, 256, 384, 512)
+
+
+def workload5(ninst: int = 256, nsteps: int = 1000, seed: int = 1005,
+              sizes: tuple[int, ...] = ENSEMBLE_SIZES) -> list[Problem]:
+    """Ragged ensemble: sizes N~U(sizes) (square), half periodic and half
+    reflecting (shuffled), domain [0,100]^2, b as workload 2, hump amplitude
+    U(0.01, 0.2), each with its own fixed dt."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ns = rng.choice(np.array(sizes), size=ninst)
+    bcs = np.array([PERIODIC] * (ninst // 2) + [REFLECTING] * (ninst - ninst // 2))
+    rng.shuffle(bcs)
+    out = []
+    for k in range(ninst):
+        n = int(ns[k])
+        p = _reflecting_bumpy(n, n, nsteps, seed, 0.0, 100.0, 0.0, 100.0, f"workload5[{k}]",
+                              hump_amp=(0.01, 0.2), hump_box=(20.0, 80.0, 20.0, 80.0),
+                              bc=int(bcs[k]), rng=rng)
+        out.append(p)
+    return out
+
+
+# ----------------------------------------------------------------------------- test states
+def smooth_state(nx: int, ny: int, bc: int, seed: int = 0, xmin=0.0, xmax=1.0, ymin=0.0,
+                 ymax=1.0, lam: float = LAMBDA_DEFAULT, amp: float = 0.2) -> Problem:
+    """A generic smooth state with every variable active (u, v, w != 0 and
+    eta != h), built from a few random low Fourier modes, h in about
+    [0.8, 1.2] over a bathymetry near -1.  Used by parity and invariant tests."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    X, Y = _mesh(nx, ny, xmin, xmax, ymin, ymax, bc)
+    lx, ly = xmax - xmin, ymax - ymin
+
+    # integer wavenumbers make periodic fields; on reflecting grids they are
+    # shifted so that the two walls see different values
+    shift = 0.0 if bc == PERIODIC else 0.37
+
+    def field_(scale):
+        f = np.zeros_like(X)
+        for _ in range(4):
+            kx, ky = rng.integers(0, 3, size=2) + shift
+            ph = rng.uniform(0, 2 * np.pi)
+            a = rng.uniform(-1, 1)
+            f += a * np.cos(2 * np.pi * (kx * (X - xmin) / lx + ky * (Y - ymin) / ly) + ph)
+        return scale * f / 4.0
+
+    b = -1.0 + field_(0.3)
+    h = 1.0 + field_(amp)
+    u = field_(0.5)
+    v = field_(0.5)
+    w = field_(0.3)
+    eta = h * (1.0 + field_(0.05))
+    q = np.stack([h, u, v, w, eta])
+    p = Problem(nx, ny, xmin, xmax, ymin, ymax, bc, b, q, lam=lam, name=f"smooth[{seed}]")
+    dx, dy = p.spacing()
+    p.dt = cfl_dt(b, h, u, v, dx, dy, p.g, lam)
+    return p
