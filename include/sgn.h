@@ -1,0 +1,141 @@
+/*
+ * sgn.h - C ABI of libsgn.so: the split-form summation-by-parts (SBP)
+ * semi-discretization of the 2D hyperbolized Serre-Green-Naghdi (SGN)
+ * equations with variable bathymetry (arXiv 2601.02540), fused with classical
+ * fourth-order Runge-Kutta stages, on one NVIDIA B300 GPU (sm_103a).
+ *
+ * The operations and the passages of the paper that define them:
+ *   sgn_rhs          the right-hand side of eq. (sd_periodic_2D_SGN) (periodic,
+ *                    Sec. 4.1) or eq. (semi_2D) (reflecting walls with SATs,
+ *                    Sec. 4.2), with the second-order SBP operators and SATs of
+ *                    the remark "Concrete SBP operators and SATs" (Sec. 4).
+ *   sgn_init_aux     eq. (initialization) of Sec. 6: eta = h and
+ *                    w = -h (D_x u + D_y v) + 3/2 (u D_x b + v D_y b).
+ *   sgn_step         classical RK4 with a fixed time step applied to that RHS.
+ *   sgn_mass_energy  total mass 1^T M h and energy 1^T M E of Thm. 4.1/4.2 and
+ *                    the semi-discrete energy rate <d_q E, q_t>_M of eq.
+ *                    (splitcondition).
+ *
+ * Data layout.  A state is five planes (h, u, v, w, eta), each plane nx*ny
+ * values, x fastest: element (f, j, i) at index f*nx*ny + j*nx + i.  Node
+ * (i, j) sits at x_i = xmin + i*dx, y_j = ymin + j*dy, where
+ *   periodic:   dx = (xmax - xmin) / nx       (x_max is the image of x_min)
+ *   reflecting: dx = (xmax - xmin) / (nx - 1) (both walls are nodes)
+ * and likewise in y.  The bathymetry b is one plane.
+ *
+ * Precision (sgn_params.prec):
+ *   SGN_F64         state, RHS and stage states in double.
+ *   SGN_F32         state, RHS and stage states in float.
+ *   SGN_F32_F64ACC  the caller's state q (= q_n) and the RK accumulator are
+ *                   double; the RHS and the intermediate stage states are
+ *                   float.
+ *   "state type" below means double for SGN_F64 and SGN_F32_F64ACC, float for
+ *   SGN_F32.  Bathymetry arguments are always double.  Diagnostics are always
+ *   accumulated in double.
+ *
+ * Memory and streams.  Every pointer named *_dev is device memory of the
+ * current CUDA device, owned by the caller, contiguous in the layout above,
+ * aligned to at least 16 bytes and not overlapping any other argument unless
+ * stated.  The context owns its own scratch (RK registers, reduction
+ * partials), allocated in sgn_create.  `stream` is a cudaStream_t (NULL = the
+ * legacy default stream).  Calls are asynchronous on `stream` except
+ * sgn_create, sgn_destroy, sgn_mass_energy and sgn_check, which synchronize.
+ * A context may be used by one stream at a time.
+ *
+ * Errors.  Every call returns a status; nothing is thrown and nothing exits.
+ * Invalid arguments return SGN_E_INVAL without launching any kernel.  Kernels
+ * latch a device flag when a stage input has h <= 0 (SGN_E_NONPOSITIVE_H) or a
+ * non-finite h (SGN_E_NONFINITE); the flag is reported (and cleared) by the
+ * next synchronizing call.  sgn_last_error() returns a message for the last
+ * failure of the calling thread.
+ */
+#ifndef SGN_H
+#define SGN_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define SGN_API __attribute__((visibility("default")))
+#else
+#define SGN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SGN_OK = 0,
+    SGN_E_INVAL = 1,          /* bad argument: null pointer, size, parameter */
+    SGN_E_NOMEM = 2,          /* device or pinned-host allocation failed */
+    SGN_E_CUDA = 3,           /* a CUDA runtime call failed */
+    SGN_E_NONPOSITIVE_H = 4,  /* a stage input had h <= 0 (dry state; excluded by the paper) */
+    SGN_E_NONFINITE = 5,      /* a stage input had a non-finite h */
+    SGN_E_TIMEOUT = 6,        /* a bounded device wait gave up */
+    SGN_E_UNSUPPORTED = 7     /* valid request this build does not implement */
+} sgn_status;
+
+typedef enum { SGN_BC_PERIODIC = 0, SGN_BC_REFLECTING = 1 } sgn_bc;
+typedef enum { SGN_F64 = 0, SGN_F32 = 1, SGN_F32_F64ACC = 2 } sgn_prec;
+
+typedef struct {
+    int nx, ny;                    /* nodes per direction, each >= 3 */
+    double xmin, xmax, ymin, ymax; /* domain, xmax > xmin, ymax > ymin */
+    int bc;                        /* sgn_bc, both directions */
+    double g;                      /* gravitational acceleration, > 0 */
+    double lambda;                 /* relaxation parameter, >= 0 */
+    int prec;                      /* sgn_prec */
+} sgn_params;
+
+typedef struct sgn_ctx sgn_ctx;
+
+/* Create a context for one grid.  Validates `p`, allocates the scratch and
+ * copies the bathymetry b_dev (double, nx*ny, device) into the context.
+ * Synchronizes.  On failure *out is NULL. */
+SGN_API sgn_status sgn_create(const sgn_params* p, const void* b_dev, sgn_ctx** out);
+
+/* Free the context and its scratch.  Synchronizes.  NULL is a no-op. */
+SGN_API sgn_status sgn_destroy(sgn_ctx* ctx);
+
+/* Replace the bathymetry (double, nx*ny, device).  Asynchronous on stream. */
+SGN_API sgn_status sgn_set_bathymetry(sgn_ctx* ctx, const void* b_dev, void* stream);
+
+/* Initialize the auxiliary variables in place (eq. (initialization)): reads
+ * h, u, v of q_dev (state type) and writes w and eta, evaluated in double. */
+SGN_API sgn_status sgn_init_aux(sgn_ctx* ctx, void* q_dev, void* stream);
+
+/* dq_dev = RHS(q_dev): both state type, five planes, no overlap.  In
+ * SGN_F32_F64ACC the inputs are rounded to float and the RHS is evaluated in
+ * float, then widened. */
+SGN_API sgn_status sgn_rhs(sgn_ctx* ctx, const void* q_dev, void* dq_dev, void* stream);
+
+/* Advance q_dev (state type, in place) by nsteps >= 0 classical RK4 steps of
+ * size dt (finite, > 0): 4 fused RHS+stage launches per step. */
+SGN_API sgn_status sgn_step(sgn_ctx* ctx, void* q_dev, double dt, int nsteps, void* stream);
+
+/* Diagnostics of q_dev (state type), accumulated in double in a fixed order
+ * (bitwise reproducible for a given grid):
+ *   out[0] = 1^T M h       out[1] = 1^T M E      out[2] = 1^T M E'
+ *   out[3] = <d_q E, RHS(q)>_M
+ * with E = h((u^2+v^2)/2 + w^2/6 + g/2 (h + 2b) + lambda/6 (eta/h - 1)^2)
+ * and E' = E + g b^2/2 (the same energy shifted by a constant in time).
+ * out is host memory of 4 doubles.  Synchronizes `stream`, then reports any
+ * latched device flag. */
+SGN_API sgn_status sgn_mass_energy(sgn_ctx* ctx, const void* q_dev, double* out, void* stream);
+
+/* Synchronize `stream` and report (and clear) the latched device flag. */
+SGN_API sgn_status sgn_check(sgn_ctx* ctx, void* stream);
+
+/* Human-readable name of a status, and the last error message of the calling
+ * thread (never NULL). */
+SGN_API const char* sgn_status_str(sgn_status s);
+SGN_API const char* sgn_last_error(void);
+
+/* Kernel launches issued by this library since load (all contexts). */
+SGN_API unsigned long long sgn_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGN_H */

@@ -1,0 +1,413 @@
+// sgn_api.cu - host side of libsgn.so: argument validation, context scratch,
+// kernel dispatch and the C ABI declared in include/sgn.h.
+#include "sgn.h"
+#include "sgn_kernels.cuh"
+
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+using sgn::Geom;
+using sgn::StageArgs;
+
+namespace {
+
+thread_local char g_err[512] = "";
+std::atomic<unsigned long long> g_launches{0};
+
+sgn_status fail(sgn_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+sgn_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(SGN_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(call, what)                               \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+}  // namespace
+
+struct sgn_ctx {
+    sgn_params p;
+    Geom G;
+    size_t tc_size, ta_size;     // compute/stage-state and state element sizes
+    double* b64 = nullptr;       // bathymetry in double
+    void* bT = nullptr;          // bathymetry in the compute type (aliases b64 for F64)
+    void* acc = nullptr;         // RK accumulator, state type
+    void* Qa = nullptr;          // stage states, compute type
+    void* Qb = nullptr;
+    double* partials = nullptr;  // NDIAG per block
+    double* dout = nullptr;      // NDIAG device
+    double* hout = nullptr;      // NDIAG pinned host
+    int* flag = nullptr;         // device error bits
+    int* hflag = nullptr;        // pinned host copy
+    long long nblk = 0;
+    dim3 grid;
+};
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+sgn_status check_state_ptr(const void* p, const char* name) {
+    if (!p) return fail(SGN_E_INVAL, "%s is NULL", name);
+    if (reinterpret_cast<uintptr_t>(p) % 16 != 0) return fail(SGN_E_INVAL, "%s is not 16-byte aligned", name);
+    if (!is_device_ptr(p)) return fail(SGN_E_INVAL, "%s is not device memory", name);
+    return SGN_OK;
+}
+
+template <typename TC, typename TIN, typename TA, int BC, int MODE>
+cudaError_t launch_stage(const sgn_ctx* c, const StageArgs<TC, TIN, TA>& a, cudaStream_t s) {
+    auto kern = sgn::k_stage<TC, TIN, TA, BC, MODE>;
+    const size_t smem = (size_t)sgn::N_OPS * sgn::HALO_N * sizeof(TC);
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    kern<<<c->grid, dim3(sgn::TILE_X, sgn::THREADS_Y), smem, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename TC, typename TIN, typename TA>
+StageArgs<TC, TIN, TA> base_args(const sgn_ctx* c) {
+    StageArgs<TC, TIN, TA> a;
+    std::memset(&a, 0, sizeof(a));
+    a.b = static_cast<const TC*>(c->bT);
+    a.flag = c->flag;
+    a.G = c->G;
+    return a;
+}
+
+template <typename TC, typename TA, int BC>
+cudaError_t run_steps(sgn_ctx* c, TA* q, double dt, int nsteps, cudaStream_t s) {
+    TA* acc = static_cast<TA*>(c->acc);
+    TC* Qa = static_cast<TC*>(c->Qa);
+    TC* Qb = static_cast<TC*>(c->Qb);
+    const TA dt6 = (TA)(dt / 6.0), dt3 = (TA)(dt / 3.0), dt2 = (TA)(dt / 2.0), dt1 = (TA)dt;
+    StageArgs<TC, TA, TA> a1 = base_args<TC, TA, TA>(c);
+    a1.X = q; a1.qn = q; a1.acc = acc; a1.Qout = Qa; a1.c_acc = dt6; a1.c_q = dt2;
+    StageArgs<TC, TC, TA> a2 = base_args<TC, TC, TA>(c);
+    a2.X = Qa; a2.qn = q; a2.acc = acc; a2.Qout = Qb; a2.c_acc = dt3; a2.c_q = dt2;
+    StageArgs<TC, TC, TA> a3 = a2;
+    a3.X = Qb; a3.Qout = Qa; a3.c_acc = dt3; a3.c_q = dt1;
+    StageArgs<TC, TC, TA> a4 = base_args<TC, TC, TA>(c);
+    a4.X = Qa; a4.acc = acc; a4.out = q; a4.c_acc = dt6;
+    for (int n = 0; n < nsteps; n++) {
+        cudaError_t e;
+        // k1 = f(q_n)
+        if ((e = launch_stage<TC, TA, TA, BC, sgn::MODE_S1>(c, a1, s)) != cudaSuccess) return e;
+        // k2 = f(q_n + dt/2 k1)
+        if ((e = launch_stage<TC, TC, TA, BC, sgn::MODE_S2>(c, a2, s)) != cudaSuccess) return e;
+        // k3 = f(q_n + dt/2 k2)
+        if ((e = launch_stage<TC, TC, TA, BC, sgn::MODE_S3>(c, a3, s)) != cudaSuccess) return e;
+        // k4 = f(q_n + dt k3); q_{n+1} = acc + dt/6 k4
+        if ((e = launch_stage<TC, TC, TA, BC, sgn::MODE_S4>(c, a4, s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename TC, typename TA, int BC>
+cudaError_t run_rhs(sgn_ctx* c, const TA* q, TA* dq, cudaStream_t s) {
+    StageArgs<TC, TA, TA> a = base_args<TC, TA, TA>(c);
+    a.X = q; a.out = dq;
+    return launch_stage<TC, TA, TA, BC, sgn::MODE_RHS>(c, a, s);
+}
+
+template <typename TC, typename TA, int BC>
+cudaError_t run_diag(sgn_ctx* c, const TA* q, cudaStream_t s) {
+    StageArgs<TC, TA, TA> a = base_args<TC, TA, TA>(c);
+    a.X = q; a.partials = c->partials;
+    cudaError_t e = launch_stage<TC, TA, TA, BC, sgn::MODE_DIAG>(c, a, s);
+    if (e != cudaSuccess) return e;
+    sgn::k_reduce_partials<<<1, 256, 0, s>>>(c->partials, c->nblk, c->dout);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename TA, int BC>
+cudaError_t run_init(sgn_ctx* c, TA* q, cudaStream_t s) {
+    dim3 blk(32, 8), grd((c->p.nx + 31) / 32, (c->p.ny + 7) / 8);
+    sgn::k_init_aux<TA, BC><<<grd, blk, 0, s>>>(q, c->b64, c->G);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// dispatch on (precision, boundary) to a functor templated on <TC, TA, BC>
+template <typename F>
+cudaError_t dispatch(const sgn_ctx* c, F& f) {
+    const bool refl = c->p.bc == SGN_BC_REFLECTING;
+    switch (c->p.prec) {
+    case SGN_F64:
+        return refl ? f.template operator()<double, double, sgn::BC_REFLECTING>()
+                    : f.template operator()<double, double, sgn::BC_PERIODIC>();
+    case SGN_F32:
+        return refl ? f.template operator()<float, float, sgn::BC_REFLECTING>()
+                    : f.template operator()<float, float, sgn::BC_PERIODIC>();
+    default:
+        return refl ? f.template operator()<float, double, sgn::BC_REFLECTING>()
+                    : f.template operator()<float, double, sgn::BC_PERIODIC>();
+    }
+}
+
+struct RhsOp {
+    sgn_ctx* c; const void* q; void* dq; cudaStream_t s;
+    template <typename TC, typename TA, int BC>
+    cudaError_t operator()() { return run_rhs<TC, TA, BC>(c, static_cast<const TA*>(q), static_cast<TA*>(dq), s); }
+};
+
+struct StepOp {
+    sgn_ctx* c; void* q; double dt; int n; cudaStream_t s;
+    template <typename TC, typename TA, int BC>
+    cudaError_t operator()() { return run_steps<TC, TA, BC>(c, static_cast<TA*>(q), dt, n, s); }
+};
+
+struct DiagOp {
+    sgn_ctx* c; const void* q; cudaStream_t s;
+    template <typename TC, typename TA, int BC>
+    cudaError_t operator()() { return run_diag<TC, TA, BC>(c, static_cast<const TA*>(q), s); }
+};
+
+sgn_status read_flag(sgn_ctx* c, cudaStream_t s) {
+    CUDA_TRY(cudaMemcpyAsync(c->hflag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, s), "read flag");
+    CUDA_TRY(cudaStreamSynchronize(s), "synchronize");
+    const int f = *c->hflag;
+    if (f) {
+        CUDA_TRY(cudaMemsetAsync(c->flag, 0, sizeof(int), s), "clear flag");
+        CUDA_TRY(cudaStreamSynchronize(s), "synchronize");
+        if (f & sgn::FLAG_NONFINITE) return fail(SGN_E_NONFINITE, "a stage input had a non-finite water height");
+        return fail(SGN_E_NONPOSITIVE_H, "a stage input had a non-positive water height");
+    }
+    return SGN_OK;
+}
+
+void free_ctx(sgn_ctx* c) {
+    if (!c) return;
+    if (c->bT && c->bT != c->b64) cudaFree(c->bT);
+    cudaFree(c->b64);
+    cudaFree(c->acc);
+    cudaFree(c->Qa);
+    cudaFree(c->Qb);
+    cudaFree(c->partials);
+    cudaFree(c->dout);
+    cudaFree(c->flag);
+    cudaFreeHost(c->hout);
+    cudaFreeHost(c->hflag);
+    delete c;
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+}  // namespace
+
+extern "C" {
+
+const char* sgn_status_str(sgn_status s) {
+    switch (s) {
+    case SGN_OK: return "SGN_OK";
+    case SGN_E_INVAL: return "SGN_E_INVAL";
+    case SGN_E_NOMEM: return "SGN_E_NOMEM";
+    case SGN_E_CUDA: return "SGN_E_CUDA";
+    case SGN_E_NONPOSITIVE_H: return "SGN_E_NONPOSITIVE_H";
+    case SGN_E_NONFINITE: return "SGN_E_NONFINITE";
+    case SGN_E_TIMEOUT: return "SGN_E_TIMEOUT";
+    case SGN_E_UNSUPPORTED: return "SGN_E_UNSUPPORTED";
+    }
+    return "SGN_E_UNKNOWN";
+}
+
+const char* sgn_last_error(void) { return g_err; }
+
+unsigned long long sgn_launch_count(void) { return g_launches.load(); }
+
+sgn_status sgn_create(const sgn_params* p, const void* b_dev, sgn_ctx** out) {
+    if (!out) return fail(SGN_E_INVAL, "out is NULL");
+    *out = nullptr;
+    if (!p) return fail(SGN_E_INVAL, "params is NULL");
+    if (p->nx < 3 || p->ny < 3) return fail(SGN_E_INVAL, "grid %dx%d: need nx, ny >= 3", p->nx, p->ny);
+    if ((p->ny + sgn::TILE_Y - 1) / sgn::TILE_Y > 65535)
+        return fail(SGN_E_INVAL, "ny = %d exceeds the launch-grid limit", p->ny);
+    if (!(std::isfinite(p->xmin) && std::isfinite(p->xmax) && p->xmax > p->xmin &&
+          std::isfinite(p->ymin) && std::isfinite(p->ymax) && p->ymax > p->ymin))
+        return fail(SGN_E_INVAL, "domain must be finite with xmax > xmin and ymax > ymin");
+    if (p->bc != SGN_BC_PERIODIC && p->bc != SGN_BC_REFLECTING) return fail(SGN_E_INVAL, "bc = %d", p->bc);
+    if (p->prec != SGN_F64 && p->prec != SGN_F32 && p->prec != SGN_F32_F64ACC)
+        return fail(SGN_E_INVAL, "prec = %d", p->prec);
+    if (!finite_pos(p->g)) return fail(SGN_E_INVAL, "g must be finite and > 0");
+    if (!(std::isfinite(p->lambda) && p->lambda >= 0.0)) return fail(SGN_E_INVAL, "lambda must be finite and >= 0");
+    if (!b_dev) return fail(SGN_E_INVAL, "b_dev is NULL");
+    if (!is_device_ptr(b_dev)) return fail(SGN_E_INVAL, "b_dev is not device memory");
+
+    sgn_ctx* c = new (std::nothrow) sgn_ctx();
+    if (!c) return fail(SGN_E_NOMEM, "host allocation");
+    c->p = *p;
+    const bool per = p->bc == SGN_BC_PERIODIC;
+    const double dx = per ? (p->xmax - p->xmin) / p->nx : (p->xmax - p->xmin) / (p->nx - 1);
+    const double dy = per ? (p->ymax - p->ymin) / p->ny : (p->ymax - p->ymin) / (p->ny - 1);
+    Geom& G = c->G;
+    G.nx = p->nx;
+    G.ny = p->ny;
+    G.plane = (long long)p->nx * p->ny;
+    G.cx2 = 1.0 / (2.0 * dx);
+    G.cy2 = 1.0 / (2.0 * dy);
+    G.cx1 = 1.0 / dx;
+    G.cy1 = 1.0 / dy;
+    G.satx = 2.0 / dx;
+    G.saty = 2.0 / dy;
+    G.dx = dx;
+    G.dy = dy;
+    G.g = p->g;
+    G.lam = p->lambda;
+    G.lam2 = p->lambda / 2.0;
+    G.lam3 = p->lambda / 3.0;
+    G.lam6 = p->lambda / 6.0;
+    c->tc_size = p->prec == SGN_F64 ? sizeof(double) : sizeof(float);
+    c->ta_size = p->prec == SGN_F32 ? sizeof(float) : sizeof(double);
+    c->grid = dim3((p->nx + sgn::TILE_X - 1) / sgn::TILE_X, (p->ny + sgn::TILE_Y - 1) / sgn::TILE_Y);
+    c->nblk = (long long)c->grid.x * c->grid.y;
+
+    const size_t plane = (size_t)G.plane;
+    bool ok = cudaMalloc(&c->b64, plane * sizeof(double)) == cudaSuccess;
+    if (ok && p->prec != SGN_F64) ok = cudaMalloc(&c->bT, plane * sizeof(float)) == cudaSuccess;
+    if (ok && p->prec == SGN_F64) c->bT = c->b64;
+    ok = ok && cudaMalloc(&c->acc, 5 * plane * c->ta_size) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->Qa, 5 * plane * c->tc_size) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->Qb, 5 * plane * c->tc_size) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->partials, (size_t)c->nblk * sgn::NDIAG * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->dout, sgn::NDIAG * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->flag, sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMallocHost(&c->hout, sgn::NDIAG * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMallocHost(&c->hflag, sizeof(int)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        const size_t need = 5 * plane * (c->ta_size + 2 * c->tc_size);
+        free_ctx(c);
+        return fail(SGN_E_NOMEM, "allocating about %zu bytes of scratch", need);
+    }
+    cudaError_t e = cudaMemset(c->flag, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(c->b64, b_dev, plane * sizeof(double), cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess && p->prec != SGN_F64) {
+        sgn::k_convert<float><<<592, 256>>>(c->b64, static_cast<float*>(c->bT), (long long)plane);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        sgn_status st = cuda_fail(e, "sgn_create");
+        free_ctx(c);
+        return st;
+    }
+    *out = c;
+    return SGN_OK;
+}
+
+sgn_status sgn_destroy(sgn_ctx* c) {
+    if (!c) return SGN_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    free_ctx(c);
+    if (e != cudaSuccess) return cuda_fail(e, "sgn_destroy");
+    return SGN_OK;
+}
+
+sgn_status sgn_set_bathymetry(sgn_ctx* c, const void* b_dev, void* stream) {
+    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
+    if (!b_dev || !is_device_ptr(b_dev)) return fail(SGN_E_INVAL, "b_dev is not device memory");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t plane = (size_t)c->G.plane;
+    CUDA_TRY(cudaMemcpyAsync(c->b64, b_dev, plane * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy b");
+    if (c->p.prec != SGN_F64) {
+        sgn::k_convert<float><<<592, 256, 0, s>>>(c->b64, static_cast<float*>(c->bT), (long long)plane);
+        count_launch();
+        CUDA_TRY(cudaGetLastError(), "convert b");
+    }
+    return SGN_OK;
+}
+
+sgn_status sgn_init_aux(sgn_ctx* c, void* q_dev, void* stream) {
+    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
+    sgn_status st = check_state_ptr(q_dev, "q_dev");
+    if (st != SGN_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    const bool refl = c->p.bc == SGN_BC_REFLECTING;
+    if (c->p.prec == SGN_F32)
+        e = refl ? run_init<float, sgn::BC_REFLECTING>(c, static_cast<float*>(q_dev), s)
+                 : run_init<float, sgn::BC_PERIODIC>(c, static_cast<float*>(q_dev), s);
+    else
+        e = refl ? run_init<double, sgn::BC_REFLECTING>(c, static_cast<double*>(q_dev), s)
+                 : run_init<double, sgn::BC_PERIODIC>(c, static_cast<double*>(q_dev), s);
+    if (e != cudaSuccess) return cuda_fail(e, "sgn_init_aux");
+    return SGN_OK;
+}
+
+sgn_status sgn_rhs(sgn_ctx* c, const void* q_dev, void* dq_dev, void* stream) {
+    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
+    sgn_status st = check_state_ptr(q_dev, "q_dev");
+    if (st == SGN_OK) st = check_state_ptr(dq_dev, "dq_dev");
+    if (st != SGN_OK) return st;
+    if (q_dev == dq_dev) return fail(SGN_E_INVAL, "q_dev and dq_dev must not overlap");
+    RhsOp f{c, q_dev, dq_dev, static_cast<cudaStream_t>(stream)};
+    cudaError_t e = dispatch(c, f);
+    if (e != cudaSuccess) return cuda_fail(e, "sgn_rhs");
+    return SGN_OK;
+}
+
+sgn_status sgn_step(sgn_ctx* c, void* q_dev, double dt, int nsteps, void* stream) {
+    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
+    sgn_status st = check_state_ptr(q_dev, "q_dev");
+    if (st != SGN_OK) return st;
+    if (!finite_pos(dt)) return fail(SGN_E_INVAL, "dt must be finite and > 0");
+    if (nsteps < 0) return fail(SGN_E_INVAL, "nsteps must be >= 0");
+    StepOp f{c, q_dev, dt, nsteps, static_cast<cudaStream_t>(stream)};
+    cudaError_t e = dispatch(c, f);
+    if (e != cudaSuccess) return cuda_fail(e, "sgn_step");
+    return SGN_OK;
+}
+
+sgn_status sgn_mass_energy(sgn_ctx* c, const void* q_dev, double* out, void* stream) {
+    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
+    if (!out) return fail(SGN_E_INVAL, "out is NULL");
+    sgn_status st = check_state_ptr(q_dev, "q_dev");
+    if (st != SGN_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DiagOp f{c, q_dev, s};
+    cudaError_t e = dispatch(c, f);
+    if (e != cudaSuccess) return cuda_fail(e, "sgn_mass_energy");
+    CUDA_TRY(cudaMemcpyAsync(c->hout, c->dout, sgn::NDIAG * sizeof(double), cudaMemcpyDeviceToHost, s),
+             "copy diagnostics");
+    st = read_flag(c, s);
+    for (int k = 0; k < sgn::NDIAG; k++) out[k] = c->hout[k];
+    return st;
+}
+
+sgn_status sgn_check(sgn_ctx* c, void* stream) {
+    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
+    return read_flag(c, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,351 @@
+// sgn_kernels.cuh - sm_103a kernels for the split-form SBP semi-discretization of
+// the 2D hyperbolized Serre-Green-Naghdi equations (arXiv 2601.02540, Sec. 4),
+// fused with the stages of classical RK4.
+//
+// One thread block owns a TILE_X x TILE_Y tile of output nodes.  It stages the
+// six input planes (h, u, v, w, eta, b) of the tile plus a one-node halo in
+// shared memory, forms every product that is differentiated (h(h+b), u^2, v^2,
+// hu, hv, huv, huw, hvw, eta^2/h) and the reciprocal 1/h once per node, then
+// each thread evaluates the right-hand side of eq. (sd_periodic_2D_SGN) /
+// eq. (semi_2D) at its nodes and applies the RK4 stage algebra.  The halo is
+// wrapped (periodic) or clamped (reflecting: the one-sided boundary rows of
+// the SBP operator never read beyond the wall).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sgn {
+
+enum { BC_PERIODIC = 0, BC_REFLECTING = 1 };
+
+// RK4 stage modes.  RHS writes dq; S1..S4 are the four stages of classical RK4
+// on three registers (q_n, acc, Q):
+//   S1: k = f(q_n); acc = q_n + dt/6 k; Q = q_n + dt/2 k
+//   S2: k = f(Q);   acc += dt/3 k;      Q' = q_n + dt/2 k
+//   S3: k = f(Q');  acc += dt/3 k;      Q  = q_n + dt k
+//   S4: k = f(Q);   q_n = acc + dt/6 k
+// DIAG computes k = f(q) and reduces mass, energy and the energy rate.
+enum { MODE_RHS = 0, MODE_S1 = 1, MODE_S2 = 2, MODE_S3 = 3, MODE_S4 = 4, MODE_DIAG = 5 };
+
+constexpr int TILE_X = 32;
+constexpr int THREADS_Y = 8;
+constexpr int ROWS_PER_THREAD = 2;
+constexpr int TILE_Y = THREADS_Y * ROWS_PER_THREAD;
+constexpr int HALO_X = TILE_X + 2;
+constexpr int HALO_Y = TILE_Y + 2;
+constexpr int HALO_N = HALO_X * HALO_Y;
+constexpr int BLOCK_THREADS = TILE_X * THREADS_Y;
+
+// shared-memory planes: the differentiated operands, then 1/h
+enum {
+    OP_H, OP_U, OP_V, OP_W, OP_ETA, OP_B,
+    OP_HS, OP_UU, OP_VV, OP_HU, OP_HV, OP_HUV, OP_HUW, OP_HVW, OP_E2H,
+    OP_R, N_OPS
+};
+
+constexpr int NDIAG = 4;
+constexpr int FLAG_NONPOSITIVE = 1;
+constexpr int FLAG_NONFINITE = 2;
+
+struct Geom {
+    int nx, ny;
+    long long plane;       // nx * ny
+    double cx2, cy2;       // 1 / (2 dx), 1 / (2 dy): central rows
+    double cx1, cy1;       // 1 / dx, 1 / dy: one-sided boundary rows
+    double satx, saty;     // 2 / dx, 2 / dy: SAT weights
+    double dx, dy;         // mass-matrix spacing
+    double g, lam;
+    double lam2, lam3, lam6;  // lambda/2, lambda/3, lambda/6
+};
+
+template <typename TC, typename TIN, typename TA>
+struct StageArgs {
+    const TIN* X;        // stage input state (5 planes)
+    const TC* b;         // bathymetry (1 plane)
+    const TA* qn;        // q_n (stages 1-3)
+    TA* acc;             // RK accumulator
+    TC* Qout;            // next stage state
+    TA* out;             // dq (RHS) or q_{n+1} (stage 4)
+    double* partials;    // DIAG: NDIAG doubles per block
+    int* flag;           // latched error bits
+    Geom G;
+    TA c_acc, c_q;       // stage coefficients (see the modes)
+};
+
+template <typename T>
+__device__ __forceinline__ T pos_inf();
+template <>
+__device__ __forceinline__ double pos_inf<double>() { return __longlong_as_double(0x7ff0000000000000LL); }
+template <>
+__device__ __forceinline__ float pos_inf<float>() { return __int_as_float(0x7f800000); }
+
+// Index of the halo node at global coordinate k (k may be -1 or >= n).
+template <int BC>
+__device__ __forceinline__ int halo_index(int k, int n) {
+    if (k < 0) return BC == BC_PERIODIC ? n - 1 : 0;
+    if (k >= n) return (BC == BC_PERIODIC && k == n) ? 0 : n - 1;
+    return k;
+}
+
+// Right-hand side at the node held in shared-memory slot t, global (gi, gj).
+// Terms are grouped by the difference they multiply; every term of eq.
+// (sd_periodic_2D_SGN) / (semi_2D) appears exactly once.
+template <typename TC, int BC>
+__device__ __forceinline__ void node_rhs(const TC* __restrict__ sm, int t, int gi, int gj,
+                                         const Geom& G, TC k[5]) {
+    int tl = t - 1, tr = t + 1, tb = t - HALO_X, tt = t + HALO_X;
+    TC sx = (TC)G.cx2, sy = (TC)G.cy2;
+    if (BC == BC_REFLECTING) {
+        // one-sided first/last rows of the reflecting operator: (f1 - f0)/dx
+        if (gi == 0) { tl = t; sx = (TC)G.cx1; }
+        if (gi == G.nx - 1) { tr = t; sx = (TC)G.cx1; }
+        if (gj == 0) { tb = t; sy = (TC)G.cy1; }
+        if (gj == G.ny - 1) { tt = t; sy = (TC)G.cy1; }
+    }
+#define SM_(op, idx) sm[(op) * HALO_N + (idx)]
+#define DXU(op) (SM_(op, tr) - SM_(op, tl))
+#define DYU(op) (SM_(op, tt) - SM_(op, tb))
+    const TC h = SM_(OP_H, t), u = SM_(OP_U, t), v = SM_(OP_V, t);
+    const TC w = SM_(OP_W, t), eta = SM_(OP_ETA, t), b = SM_(OP_B, t);
+    const TC r = SM_(OP_R, t);
+    const TC hu = SM_(OP_HU, t), hv = SM_(OP_HV, t);
+    const TC g = (TC)G.g;
+    const TC rho = eta * r;          // eta / h
+    const TC om = TC(1) - rho;       // 1 - eta / h
+    const TC s = h + b;
+    const TC lam6r2 = (TC)G.lam6 * rho * rho;
+    const TC uv = u * v, hw = h * w, uw = u * w, vw = v * w;
+    const TC half = TC(0.5);
+
+    const TC dxh = DXU(OP_H), dxu = DXU(OP_U), dxv = DXU(OP_V), dxw = DXU(OP_W);
+    const TC dxe = DXU(OP_ETA), dxb = DXU(OP_B);
+    const TC dyh = DYU(OP_H), dyu = DYU(OP_U), dyv = DYU(OP_V), dyw = DYU(OP_W);
+    const TC dye = DYU(OP_ETA), dyb = DYU(OP_B);
+
+    // h_t = -(u D_x h + h D_x u + v D_y h + h D_y v) + SAT
+    TC kh = -(sx * (u * dxh + h * dxu) + sy * (v * dyh + h * dyv));
+    if (BC == BC_REFLECTING) {
+        // M^{-1} R^T B N_x R (hu) + M^{-1} R^T B N_y R (hv); corners get both
+        if (gi == 0) kh -= (TC)G.satx * hu;
+        if (gi == G.nx - 1) kh += (TC)G.satx * hu;
+        if (gj == 0) kh -= (TC)G.saty * hv;
+        if (gj == G.ny - 1) kh += (TC)G.saty * hv;
+    }
+
+    // h u_t = -[ g D_x(h(h+b)) - g(h+b) D_x h + 1/2 h D_x(u^2) - 1/2 u^2 D_x h
+    //           + 1/2 u D_x(hu) - 1/2 hu D_x u + 1/2 D_y(huv) - 1/2 uv D_y h
+    //           + 1/2 hv D_y u - 1/2 hu D_y v + lam/6 (eta/h)^2 D_x h + lam/3 D_x eta
+    //           - lam/3 (eta/h) D_x eta - lam/6 D_x(eta^2/h) + lam/2 (1 - eta/h) D_x b ]
+    const TC Xu = dxh * (lam6r2 - g * s - half * (u * u)) + dxe * ((TC)G.lam3 * om)
+                + dxb * ((TC)G.lam2 * om) + g * DXU(OP_HS) + half * h * DXU(OP_UU)
+                + half * u * DXU(OP_HU) - half * hu * dxu - (TC)G.lam6 * DXU(OP_E2H);
+    const TC Yu = half * (DYU(OP_HUV) - uv * dyh + hv * dyu - hu * dyv);
+    const TC ku = -r * (sx * Xu + sy * Yu);
+
+    // h v_t: the same with x and y (and u and v) exchanged
+    const TC Yv = dyh * (lam6r2 - g * s - half * (v * v)) + dye * ((TC)G.lam3 * om)
+                + dyb * ((TC)G.lam2 * om) + g * DYU(OP_HS) + half * h * DYU(OP_VV)
+                + half * v * DYU(OP_HV) - half * hv * dyv - (TC)G.lam6 * DYU(OP_E2H);
+    const TC Xv = half * (DXU(OP_HUV) - uv * dxh + hu * dxv - hv * dxu);
+    const TC kv = -r * (sy * Yv + sx * Xv);
+
+    // h w_t = lam (1 - eta/h) - 1/2 [ D_x(huw) + hu D_x w - uw D_x h - hw D_x u
+    //                                + D_y(hvw) + hv D_y w - vw D_y h - hw D_y v ]
+    const TC Xw = DXU(OP_HUW) + hu * dxw - uw * dxh - hw * dxu;
+    const TC Yw = DYU(OP_HVW) + hv * dyw - vw * dyh - hw * dyv;
+    const TC kw = r * ((TC)G.lam * om - half * (sx * Xw + sy * Yw));
+
+    // eta_t = w - u D_x eta - v D_y eta - 3/2 u D_x b - 3/2 v D_y b
+    const TC ke = w - u * (sx * (dxe + TC(1.5) * dxb)) - v * (sy * (dye + TC(1.5) * dyb));
+#undef DXU
+#undef DYU
+#undef SM_
+    k[0] = kh; k[1] = ku; k[2] = kv; k[3] = kw; k[4] = ke;
+}
+
+template <typename TC, typename TIN, typename TA, int BC, int MODE>
+__global__ void __launch_bounds__(BLOCK_THREADS)
+k_stage(StageArgs<TC, TIN, TA> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TC* sm = reinterpret_cast<TC*>(smem_raw);
+    const Geom& G = a.G;
+    const int i0 = blockIdx.x * TILE_X;
+    const int j0 = blockIdx.y * TILE_Y;
+    const long long P = G.plane;
+    const int tid = threadIdx.y * TILE_X + threadIdx.x;
+
+    // ---- phase 1: halo tile of the inputs and of every differentiated product
+    int bad = 0;
+    for (int t = tid; t < HALO_N; t += BLOCK_THREADS) {
+        const int li = t % HALO_X, lj = t / HALO_X;
+        const int gi = halo_index<BC>(i0 - 1 + li, G.nx);
+        const int gj = halo_index<BC>(j0 - 1 + lj, G.ny);
+        const long long c = (long long)gj * G.nx + gi;
+        const TC h = (TC)a.X[c];
+        const TC u = (TC)a.X[P + c];
+        const TC v = (TC)a.X[2 * P + c];
+        const TC w = (TC)a.X[3 * P + c];
+        const TC eta = (TC)a.X[4 * P + c];
+        const TC bb = a.b[c];
+        if (!(h > TC(0))) bad |= (h <= TC(0)) ? FLAG_NONPOSITIVE : FLAG_NONFINITE;  // NaN -> non-finite
+        else if (!(h < pos_inf<TC>())) bad |= FLAG_NONFINITE;
+        const TC r = TC(1) / h;
+        const TC hu = h * u, hv = h * v;
+        sm[OP_H * HALO_N + t] = h;
+        sm[OP_U * HALO_N + t] = u;
+        sm[OP_V * HALO_N + t] = v;
+        sm[OP_W * HALO_N + t] = w;
+        sm[OP_ETA * HALO_N + t] = eta;
+        sm[OP_B * HALO_N + t] = bb;
+        sm[OP_HS * HALO_N + t] = h * (h + bb);
+        sm[OP_UU * HALO_N + t] = u * u;
+        sm[OP_VV * HALO_N + t] = v * v;
+        sm[OP_HU * HALO_N + t] = hu;
+        sm[OP_HV * HALO_N + t] = hv;
+        sm[OP_HUV * HALO_N + t] = hu * v;
+        sm[OP_HUW * HALO_N + t] = hu * w;
+        sm[OP_HVW * HALO_N + t] = hv * w;
+        sm[OP_E2H * HALO_N + t] = eta * eta * r;
+        sm[OP_R * HALO_N + t] = r;
+    }
+    if (bad) atomicOr(a.flag, bad);
+    __syncthreads();
+
+    // ---- phase 2: right-hand side and stage algebra at this thread's nodes
+    double dsum[NDIAG] = {0.0, 0.0, 0.0, 0.0};
+    const int gi = i0 + threadIdx.x;
+#pragma unroll
+    for (int ry = 0; ry < ROWS_PER_THREAD; ry++) {
+        const int ly = threadIdx.y + ry * THREADS_Y;
+        const int gj = j0 + ly;
+        if (gi >= G.nx || gj >= G.ny) continue;
+        const int t = (ly + 1) * HALO_X + (threadIdx.x + 1);
+        TC k[5];
+        node_rhs<TC, BC>(sm, t, gi, gj, G, k);
+        const long long c = (long long)gj * G.nx + gi;
+        if (MODE == MODE_RHS) {
+#pragma unroll
+            for (int f = 0; f < 5; f++) a.out[f * P + c] = (TA)k[f];
+        } else if (MODE == MODE_S1 || MODE == MODE_S2 || MODE == MODE_S3) {
+#pragma unroll
+            for (int f = 0; f < 5; f++) {
+                const TA qv = a.qn[f * P + c];
+                const TA kv = (TA)k[f];
+                const TA av = (MODE == MODE_S1) ? qv : a.acc[f * P + c];
+                a.acc[f * P + c] = av + a.c_acc * kv;
+                a.Qout[f * P + c] = (TC)(qv + a.c_q * kv);
+            }
+        } else if (MODE == MODE_S4) {
+#pragma unroll
+            for (int f = 0; f < 5; f++) a.out[f * P + c] = a.acc[f * P + c] + a.c_acc * (TA)k[f];
+        } else if (MODE == MODE_DIAG) {
+            // mass, energy E, shifted energy E' = E + g b^2/2, and the rate
+            // <d_q E, q_t>_M with the derivatives listed after eq. (splitcondition)
+            const double h = (double)sm[OP_H * HALO_N + t], u = (double)sm[OP_U * HALO_N + t];
+            const double v = (double)sm[OP_V * HALO_N + t], w = (double)sm[OP_W * HALO_N + t];
+            const double eta = (double)sm[OP_ETA * HALO_N + t], bb = (double)sm[OP_B * HALO_N + t];
+            double wx = G.dx, wy = G.dy;
+            if (BC == BC_REFLECTING) {
+                if (gi == 0 || gi == G.nx - 1) wx *= 0.5;
+                if (gj == 0 || gj == G.ny - 1) wy *= 0.5;
+            }
+            const double M = wx * wy;
+            const double rho = eta / h;
+            const double kin = 0.5 * (u * u + v * v);
+            const double E = h * (kin + w * w / 6.0 + 0.5 * G.g * (h + 2.0 * bb)
+                                  + G.lam6 * (rho - 1.0) * (rho - 1.0));
+            const double Es = h * kin + h * w * w / 6.0 + 0.5 * G.g * (h + bb) * (h + bb)
+                            + G.lam6 * h * (rho - 1.0) * (rho - 1.0);
+            const double dEh = kin + w * w / 6.0 + G.g * (h + bb) + G.lam6 * (1.0 - rho * rho);
+            const double rate = dEh * (double)k[0] + h * u * (double)k[1] + h * v * (double)k[2]
+                              + (h * w / 3.0) * (double)k[3] - G.lam3 * (1.0 - rho) * (double)k[4];
+            dsum[0] += M * h;
+            dsum[1] += M * E;
+            dsum[2] += M * Es;
+            dsum[3] += M * rate;
+        }
+    }
+
+    if (MODE == MODE_DIAG) {
+        // fixed-order block reduction: warp shuffle, then thread q over the warps
+        __shared__ double red[BLOCK_THREADS / 32][NDIAG];
+        const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+        for (int q = 0; q < NDIAG; q++) {
+            double x = dsum[q];
+            for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+            if (lane == 0) red[warp][q] = x;
+        }
+        __syncthreads();
+        if (tid < NDIAG) {
+            double x = 0.0;
+            for (int wgi = 0; wgi < BLOCK_THREADS / 32; wgi++) x += red[wgi][tid];
+            const long long blk = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+            a.partials[blk * NDIAG + tid] = x;
+        }
+    }
+}
+
+// Second pass of the diagnostics: one block sums the per-block partials in a
+// fixed order (each thread a strided slice, then a fixed tree).
+__global__ void __launch_bounds__(256) k_reduce_partials(const double* __restrict__ partials,
+                                                          long long nblk, double* __restrict__ out) {
+    __shared__ double red[256][NDIAG];
+    double s[NDIAG] = {0.0, 0.0, 0.0, 0.0};
+    for (long long k = threadIdx.x; k < nblk; k += 256)
+#pragma unroll
+        for (int q = 0; q < NDIAG; q++) s[q] += partials[k * NDIAG + q];
+#pragma unroll
+    for (int q = 0; q < NDIAG; q++) red[threadIdx.x][q] = s[q];
+    __syncthreads();
+    for (int stride = 128; stride > 0; stride >>= 1) {
+        if ((int)threadIdx.x < stride)
+#pragma unroll
+            for (int q = 0; q < NDIAG; q++) red[threadIdx.x][q] += red[threadIdx.x + stride][q];
+        __syncthreads();
+    }
+    if (threadIdx.x < NDIAG) out[threadIdx.x] = red[0][threadIdx.x];
+}
+
+// Initialization of the auxiliary variables, eq. (initialization):
+// eta = h, w = -h (D_x u + D_y v) + 3/2 (u D_x b + v D_y b), evaluated in double.
+template <typename TS, int BC>
+__global__ void __launch_bounds__(256) k_init_aux(TS* __restrict__ q, const double* __restrict__ b, Geom G) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= G.nx || j >= G.ny) return;
+    const long long P = G.plane;
+    int il = i - 1, ir = i + 1, jb = j - 1, jt = j + 1;
+    double sx = G.cx2, sy = G.cy2;
+    if (BC == BC_PERIODIC) {
+        if (il < 0) il = G.nx - 1;
+        if (ir >= G.nx) ir = 0;
+        if (jb < 0) jb = G.ny - 1;
+        if (jt >= G.ny) jt = 0;
+    } else {
+        if (i == 0) { il = 0; sx = G.cx1; }
+        if (i == G.nx - 1) { ir = G.nx - 1; sx = G.cx1; }
+        if (j == 0) { jb = 0; sy = G.cy1; }
+        if (j == G.ny - 1) { jt = G.ny - 1; sy = G.cy1; }
+    }
+    const long long c = (long long)j * G.nx + i;
+    const long long cl = (long long)j * G.nx + il, cr = (long long)j * G.nx + ir;
+    const long long cb = (long long)jb * G.nx + i, ct = (long long)jt * G.nx + i;
+    const double h = (double)q[c], u = (double)q[P + c], v = (double)q[2 * P + c];
+    const double dxu = sx * ((double)q[P + cr] - (double)q[P + cl]);
+    const double dyv = sy * ((double)q[2 * P + ct] - (double)q[2 * P + cb]);
+    const double dxb = sx * (b[cr] - b[cl]);
+    const double dyb = sy * (b[ct] - b[cb]);
+    q[3 * P + c] = (TS)(-h * (dxu + dyv) + 1.5 * (u * dxb + v * dyb));
+    q[4 * P + c] = (TS)h;
+}
+
+template <typename TD>
+__global__ void k_convert(const double* __restrict__ src, TD* __restrict__ dst, long long n) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        dst[k] = (TD)src[k];
+}
+
+}  // namespace sgn

@@ -1,0 +1,195 @@
+"""Thin ctypes binding of libsgn.so (include/sgn.h).
+
+The functions below carry the C names and only marshal arguments: torch CUDA
+tensors become device pointers, the current torch stream becomes the
+``cudaStream_t``, and a non-OK status raises :class:`SgnError`.  Every step of
+the computation runs in the library's CUDA kernels; there is no CPU path.
+``Solver`` is a small convenience wrapper that owns a context.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsgn.so")
+
+SGN_OK = 0
+STATUS = {0: "SGN_OK", 1: "SGN_E_INVAL", 2: "SGN_E_NOMEM", 3: "SGN_E_CUDA",
+          4: "SGN_E_NONPOSITIVE_H", 5: "SGN_E_NONFINITE", 6: "SGN_E_TIMEOUT",
+          7: "SGN_E_UNSUPPORTED"}
+PERIODIC, REFLECTING = 0, 1
+F64, F32, F32_F64ACC = 0, 1, 2
+PREC = {"f64": F64, "f32": F32, "f32_f64acc": F32_F64ACC}
+
+# every entry point the header declares: name -> (restype, argtypes)
+_V = ctypes.c_void_p
+_SIGNATURES = {
+    "sgn_create": (ctypes.c_int, [_V, _V, _V]),
+    "sgn_destroy": (ctypes.c_int, [_V]),
+    "sgn_set_bathymetry": (ctypes.c_int, [_V, _V, _V]),
+    "sgn_init_aux": (ctypes.c_int, [_V, _V, _V]),
+    "sgn_rhs": (ctypes.c_int, [_V, _V, _V, _V]),
+    "sgn_step": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_int, _V]),
+    "sgn_mass_energy": (ctypes.c_int, [_V, _V, _V, _V]),
+    "sgn_check": (ctypes.c_int, [_V, _V]),
+    "sgn_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "sgn_last_error": (ctypes.c_char_p, []),
+    "sgn_launch_count": (ctypes.c_ulonglong, []),
+}
+
+
+class SgnError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("xmin", ctypes.c_double), ("xmax", ctypes.c_double),
+                ("ymin", ctypes.c_double), ("ymax", ctypes.c_double),
+                ("bc", ctypes.c_int), ("g", ctypes.c_double), ("lam", ctypes.c_double),
+                ("prec", ctypes.c_int)]
+
+
+_lib_handle = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsgn.so (built in-tree).  Raises if it is missing: no fallback."""
+    global _lib_handle
+    if _lib_handle is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run `python -m paper_2601_02540_b300.build`")
+        h = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(h, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib_handle = h
+    return _lib_handle
+
+
+def _ok(status: int, where: str) -> None:
+    if status != SGN_OK:
+        raise SgnError(status, where, lib().sgn_last_error().decode())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t: torch.Tensor, dtype: torch.dtype, name: str) -> ctypes.c_void_p:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ----------------------------------------------------------------------------- C names
+def sgn_create(params: Params, b: torch.Tensor) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _ok(lib().sgn_create(ctypes.byref(params), _dptr(b, torch.float64, "b"), ctypes.byref(ctx)),
+        "sgn_create")
+    return ctx
+
+
+def sgn_destroy(ctx) -> None:
+    _ok(lib().sgn_destroy(ctx), "sgn_destroy")
+
+
+def sgn_set_bathymetry(ctx, b: torch.Tensor, stream=None) -> None:
+    _ok(lib().sgn_set_bathymetry(ctx, _dptr(b, torch.float64, "b"), _stream(stream)),
+        "sgn_set_bathymetry")
+
+
+def sgn_init_aux(ctx, q: torch.Tensor, dtype: torch.dtype, stream=None) -> None:
+    _ok(lib().sgn_init_aux(ctx, _dptr(q, dtype, "q"), _stream(stream)), "sgn_init_aux")
+
+
+def sgn_rhs(ctx, q: torch.Tensor, dq: torch.Tensor, dtype: torch.dtype, stream=None) -> None:
+    _ok(lib().sgn_rhs(ctx, _dptr(q, dtype, "q"), _dptr(dq, dtype, "dq"), _stream(stream)), "sgn_rhs")
+
+
+def sgn_step(ctx, q: torch.Tensor, dt: float, nsteps: int, dtype: torch.dtype, stream=None) -> None:
+    _ok(lib().sgn_step(ctx, _dptr(q, dtype, "q"), float(dt), int(nsteps), _stream(stream)), "sgn_step")
+
+
+def sgn_mass_energy(ctx, q: torch.Tensor, dtype: torch.dtype, stream=None) -> list[float]:
+    out = (ctypes.c_double * 4)()
+    _ok(lib().sgn_mass_energy(ctx, _dptr(q, dtype, "q"), out, _stream(stream)), "sgn_mass_energy")
+    return list(out)
+
+
+def sgn_check(ctx, stream=None) -> None:
+    _ok(lib().sgn_check(ctx, _stream(stream)), "sgn_check")
+
+
+def sgn_launch_count() -> int:
+    return int(lib().sgn_launch_count())
+
+
+# ----------------------------------------------------------------------------- wrapper
+class Solver:
+    """One grid: owns a library context.  ``state_dtype`` is float64 except in
+    pure f32 mode.  States are torch tensors of shape (5, ny, nx)."""
+
+    def __init__(self, nx: int, ny: int, xmin: float, xmax: float, ymin: float, ymax: float,
+                 bc: int, b: torch.Tensor, g: float = 9.81, lam: float = 500.0, prec: str = "f64"):
+        self.prec = prec
+        self.state_dtype = torch.float32 if prec == "f32" else torch.float64
+        self.shape = (5, ny, nx)
+        self.params = Params(nx, ny, xmin, xmax, ymin, ymax, bc, g, lam, PREC[prec])
+        self.ctx = None
+        self.ctx = sgn_create(self.params, b.to(torch.float64).contiguous())
+
+    @classmethod
+    def from_problem(cls, p, device="cuda", prec: str = "f64") -> "Solver":
+        b = torch.as_tensor(p.b, dtype=torch.float64, device=device)
+        return cls(p.nx, p.ny, p.xmin, p.xmax, p.ymin, p.ymax, p.bc, b, p.g, p.lam, prec)
+
+    def state(self, q, device="cuda") -> torch.Tensor:
+        return torch.as_tensor(q, device=device).to(self.state_dtype).contiguous()
+
+    def set_bathymetry(self, b: torch.Tensor) -> None:
+        sgn_set_bathymetry(self.ctx, b.to(torch.float64).contiguous())
+
+    def init_aux(self, q: torch.Tensor) -> torch.Tensor:
+        sgn_init_aux(self.ctx, q, self.state_dtype)
+        return q
+
+    def rhs(self, q: torch.Tensor, dq: torch.Tensor | None = None) -> torch.Tensor:
+        if dq is None:
+            dq = torch.empty_like(q)
+        sgn_rhs(self.ctx, q, dq, self.state_dtype)
+        return dq
+
+    def step(self, q: torch.Tensor, dt: float, nsteps: int) -> torch.Tensor:
+        sgn_step(self.ctx, q, dt, nsteps, self.state_dtype)
+        return q
+
+    def mass_energy(self, q: torch.Tensor) -> dict:
+        m, e, es, r = sgn_mass_energy(self.ctx, q, self.state_dtype)
+        return dict(mass=m, energy=e, energy_shifted=es, dEdt=r)
+
+    def check(self) -> None:
+        sgn_check(self.ctx)
+
+    def close(self) -> None:
+        if self.ctx is not None and self.ctx.value:
+            sgn_destroy(self.ctx)
+        self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
