@@ -1,0 +1,381 @@
+"""Benchmark of the fused split-form SBP RHS + RK4 stage path on one B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--no-drift] [--size N]
+
+One bench step = one classical RK4 time step (4 fused RHS+stage launches) of
+the large periodic workload: 8192 x 8192 nodes, dx = dy = 0.1, bathymetry
+-1 + a 64-mode random Fourier field (rms 0.1), 16 Gaussian humps, lambda = 500,
+g = 9.81; the job is 500 such steps.  The metric is cell-stage updates per
+second (one node through one RK stage); the headline precision is FP64, with
+FP32 and FP32-state/FP64-accumulator variants, their HBM/ALU roofline
+fractions, and the energy drift and FP32-vs-FP64 errors of the full 500-step
+job reported beside it.
+
+The state (2.7 GB in FP64) is far larger than the 126 MB L2, so no flush is
+needed between timed steps.  Timing uses CUDA events on the stream the kernels
+run on, with a synchronize on both sides, after W warm-up steps; SM clocks and
+throttle reasons are sampled with nvidia-smi during the timed region.
+
+Under torchrun (N > 1) every rank runs its own replica of the workload (the
+path has no exchange in this configuration: replicas only), the timed region is
+bracketed by barriers and the slowest rank's time is used.
+
+--impl reference times the CPU oracle (tests' reference implementation, plain
+FP64 C, one thread) on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2601_02540_b300 import inputs  # noqa: E402
+
+METRIC = "cell-stage updates/s"
+UNIT = "cell-stages/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6400.0
+FP64_NOMINAL_TFLOPS = 1.25     # B300 dense FP64 (nominal; no measured entry)
+# Algorithmic bytes per cell-stage of the three-register RK4 stage kernels
+# (each plane read or written once per stage, halos from cache):
+#   stage 1: read q, b; write acc, Q             16 planes
+#   stages 2, 3: read Q, b, q, acc; write acc, Q  26 planes
+#   stage 4: read Q, b, acc; write q              16 planes
+BYTES_PER_CELL_STAGE = {"f64": 84 * 8 / 4, "f32": 84 * 4 / 4, "f32_f64acc": 536 / 4}
+# Algorithmic floating-point operations per cell-stage (an FMA counts 2):
+# differentiated products 12, pointwise coefficients 9, 24 differences, h 9,
+# u 37, v 37, w 19, eta 10, stage algebra 17.5 (average of 20, 20, 20, 10).
+FLOPS_PER_CELL_STAGE = 174.5
+DTYPE_NAME = {"f64": "f64", "f32": "f32", "f32_f64acc": "f32+f64acc"}
+
+
+def _peaks() -> tuple[float, str]:
+    try:
+        with open(PEAKS_FILE) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("sgn_kernels.cuh", "sgn_api.cu"):
+        with open(os.path.join(ROOT, "paper_2601_02540_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(prec: str) -> float | None:
+    """DRAM bytes per launch of the stage kernel from the committed ncu summary,
+    or None when the kernels changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "k_stage_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    vals, khash = {}, None
+    with open(path) as fh:
+        for line in fh:
+            line = line.strip()
+            if line.startswith("kernel_hash"):
+                khash = line.split()[-1]
+            elif line.startswith("traffic_bytes_per_launch"):
+                parts = line.split()
+                vals[parts[1]] = float(parts[2])
+    if khash != _kernel_hash():
+        return None
+    return vals.get(prec)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        if self.proc is None or self.file is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def _time_steps(torch, solver, q, dt, steps, warmup, dist=None):
+    from paper_2601_02540_b300 import sgn
+    for _ in range(warmup):
+        solver.step(q, dt, 1)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    n0 = sgn.sgn_launch_count()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    solver.step(q, dt, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = sgn.sgn_launch_count() - n0
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    return ms, launches
+
+
+def _roofline(prec: str, cells: int, ms_total: float, launches_per_step: int, steps: int,
+              hbm_peak: float, hbm_kind: str) -> dict:
+    launch_ms = ms_total / (launches_per_step * steps)
+    traffic = _ncu_traffic(prec)
+    if prec == "f64":
+        achieved = FLOPS_PER_CELL_STAGE * cells / (launch_ms * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": traffic,
+                "peak_kind": "nominal FP64 (no measured FP64 entry)",
+                "kernel": "k_stage (RK4 stage, 4 launches/step)",
+                "launch_ms": launch_ms,
+                "hbm": {"achieved": BYTES_PER_CELL_STAGE[prec] * cells / (launch_ms * 1e-3) / 1e9,
+                        "peak": hbm_peak, "unit": "GB/s",
+                        "frac": BYTES_PER_CELL_STAGE[prec] * cells / (launch_ms * 1e-3) / 1e9 / hbm_peak}}
+    achieved = BYTES_PER_CELL_STAGE[prec] * cells / (launch_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": hbm_kind,
+            "kernel": "k_stage (RK4 stage, 4 launches/step)", "launch_ms": launch_ms}
+
+
+def _cpu_baseline(p_full: inputs.Problem) -> dict:
+    import oracle as orc
+    n = 1024
+    nst = 4
+    p = inputs.workload3(n, n)
+    g = orc.Grid(p.nx, p.ny, p.xmin, p.xmax, p.ymin, p.ymax, p.bc, p.g, p.lam)
+    q0 = orc.init_aux(g, p.b, p.q0)
+    t0 = time.perf_counter()
+    orc.rk4(g, p.b, q0, p_full.dt, nst)
+    sec = time.perf_counter() - t0
+    return {"value": 4 * n * n * nst / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"same recipe at {n}x{n} (dx = 0.1), {nst} RK4 steps, single-threaded C, "
+                      f"{sec:.1f} s"}
+
+
+def run_ours(args) -> None:
+    import torch
+    from paper_2601_02540_b300 import sgn
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    else:
+        torch.cuda.set_device(0)
+
+    p = inputs.workload3(args.size, args.size)
+    cells = p.nx * p.ny
+    hbm_peak, hbm_kind = _peaks()
+    results = {}
+    finals = {}
+    drift = {}
+    for prec in ("f64", "f32", "f32_f64acc"):
+        s = sgn.Solver.from_problem(p, prec=prec)
+        q = s.state(p.q0)
+        s.init_aux(q)
+        q_init = q.clone()
+        if prec == "f64":
+            with ClockSampler(local) as clk:
+                ms, launches = _time_steps(torch, s, q, p.dt, args.steps, args.warmup, dist)
+            clocks = clk.summary()
+        else:
+            ms, launches = _time_steps(torch, s, q, p.dt, args.steps, args.warmup, dist)
+        rate = 4.0 * cells * args.steps / (ms * 1e-3)
+        results[prec] = {"value": rate * world, "ms_per_step": ms / args.steps,
+                         "gpu_launches": launches,
+                         "roofline": _roofline(prec, cells, ms, 4, args.steps, hbm_peak, hbm_kind)}
+        if not args.no_drift:
+            # the full job, outside the timed region: energy drift and final state
+            q.copy_(q_init)
+            d0 = s.mass_energy(q)
+            s.step(q, p.dt, p.nsteps)
+            d1 = s.mass_energy(q)
+            drift[prec] = {"energy": abs(d1["energy"] - d0["energy"]) / abs(d0["energy"]),
+                           "energy_shifted": abs(d1["energy_shifted"] - d0["energy_shifted"])
+                           / abs(d0["energy_shifted"]),
+                           "mass": abs(d1["mass"] - d0["mass"]) / abs(d0["mass"]),
+                           "steps": p.nsteps}
+            finals[prec] = q.double()
+        if prec == "f64":
+            e2e = _e2e(torch, s, p, q_init, args.steps)
+        del q, q_init
+        s.close()
+        torch.cuda.empty_cache()
+
+    errors = {}
+    if "f64" in finals:
+        ref = finals["f64"]
+        for prec in ("f32", "f32_f64acc"):
+            if prec in finals:
+                d = (finals[prec] - ref).abs().amax(dim=(1, 2))
+                den = ref.abs().amax(dim=(1, 2)).clamp_min(1e-3 * float(ref[0].abs().max()))
+                errors[prec] = {f: float(v) for f, v in zip(("h", "u", "v", "w", "eta"),
+                                                             (d / den).tolist())}
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cpu = _cpu_baseline(p) if world == 1 and not args.no_cpu else None
+    head = results["f64"]
+    line = {
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"periodic {p.nx}x{p.ny} SGN split-form SBP, RK4 (4 fused stages/step)",
+                   "nx": p.nx, "ny": p.ny, "bc": "periodic", "dx": 0.1, "lambda": p.lam,
+                   "g": p.g, "dt": p.dt, "job_steps": p.nsteps, "cells": cells,
+                   "l2": f"inputs larger than L2 ({5 * cells * 8 / 1e9:.2f} GB FP64 state), no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": head["roofline"],
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": head["gpu_launches"],
+        "clocks": clocks,
+        "variants": {DTYPE_NAME[k]: {"value": v["value"], "ms_per_step": v["ms_per_step"],
+                                     "roofline": v["roofline"]} for k, v in results.items()
+                     if k != "f64"},
+        "energy_drift": drift,
+        "errors_vs_f64_after_job": errors,
+        "kernel_hash": _kernel_hash(),
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _e2e(torch, s, p, q_init_dev, steps: int) -> dict:
+    """Same metric through the public API with host buffers: the initial state
+    is copied from pinned host memory, every step is followed by a read-back of
+    its diagnostics (mass, energy, energy rate), and the final state is copied
+    back, all inside the timed region."""
+    host_in = q_init_dev.cpu().pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    q = torch.empty_like(q_init_dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    q.copy_(host_in, non_blocking=True)
+    for _ in range(steps):
+        s.step(q, p.dt, 1)
+        s.mass_energy(q)
+    host_out.copy_(q, non_blocking=True)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    nbytes = host_in.numel() * host_in.element_size()
+    return {"value": 4.0 * p.nx * p.ny * steps / sec, "unit": UNIT,
+            "h2d_bytes_per_step": nbytes / steps, "d2h_bytes_per_step": (nbytes + 32 * steps) / steps}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as orc
+    p = inputs.workload3(256, 256)
+    g = orc.Grid(p.nx, p.ny, p.xmin, p.xmax, p.ymin, p.ymax, p.bc, p.g, p.lam)
+    q = orc.init_aux(g, p.b, p.q0)
+    for _ in range(args.warmup):
+        q = orc.rk4(g, p.b, q, p.dt, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        q = orc.rk4(g, p.b, q, p.dt, 1)
+    sec = time.perf_counter() - t0
+    value = 4.0 * p.nx * p.ny * args.steps / sec
+    sample = "periodic workload recipe at 256x256 (dx = 0.1), one RK4 step per bench step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "periodic 8192x8192 SGN split-form SBP, RK4 (4 fused stages/step)",
+                   "sampled_as": "256x256"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-drift", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--size", type=int, default=8192,
+                    help="grid side (8192 = the workload; smaller sizes only for profiling)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -196,16 +196,13 @@ def workload3(nx: int = 8192, ny: int = 8192, nsteps: int = 500, seed: int = 100
         modes.append((int(kx), int(ky), rng.uniform(0.0, 2.0 * np.pi)))
     x = xmin + spacing * np.arange(nx)
     y = ymin + spacing * np.arange(ny)
-    # cos(a + b) = cos a cos b - sin a sin b keeps memory at a few planes
-    F = np.zeros((ny, nx))
-    for kx, ky, ph in modes:
-        ax = 2.0 * np.pi * kx * x / lx + ph
-        ay = 2.0 * np.pi * ky * y / ly
-        F += np.outer(np.cos(ay), np.cos(ax)) - np.outer(np.sin(ay), np.sin(ax))
+    # F = sum_m cos(ax_m + ay_m) = Cy @ Cx - Sy @ Sx (two rank-64 products)
+    ax = np.array([2.0 * np.pi * kx * x / lx + ph for kx, _, ph in modes])   # (64, nx)
+    ay = np.array([2.0 * np.pi * ky * y / ly for _, ky, _ in modes]).T       # (ny, 64)
+    F = np.cos(ay) @ np.cos(ax) - np.sin(ay) @ np.sin(ax)
     rms = float(np.sqrt(np.mean(F * F)))
     b = -1.0 + 0.1 * F / rms
     del F
-    humps = np.zeros((ny, nx))
     params = []
     for _ in range(16):
         x0 = rng.uniform(xmin, xmax)
@@ -213,14 +210,13 @@ def workload3(nx: int = 8192, ny: int = 8192, nsteps: int = 500, seed: int = 100
         a = rng.uniform(0.01, 0.1)
         w = rng.uniform(5.0, 20.0)
         params.append((x0, y0, a, w))
-    for x0, y0, a, w in params:
-        ddx = x - x0
-        ddx = ddx - lx * np.round(ddx / lx)
-        ddy = y - y0
-        ddy = ddy - ly * np.round(ddy / ly)
-        humps += a * np.outer(np.exp(-ddy * ddy / (w * w)), np.exp(-ddx * ddx / (w * w)))
-    h = -b + humps
-    del humps
+
+    def _img(d, L):
+        return d - L * np.round(d / L)
+
+    ex = np.array([np.exp(-_img(x - x0, lx) ** 2 / (w * w)) for x0, _, _, w in params])      # (16, nx)
+    ey = np.array([a * np.exp(-_img(y - y0, ly) ** 2 / (w * w)) for _, y0, a, w in params]).T  # (ny, 16)
+    h = -b + ey @ ex
     q = _raw_state(h)
     p = Problem(nx, ny, xmin, xmax, ymin, ymax, PERIODIC, b, q, nsteps=nsteps, name="workload3",
                 extra=dict(modes=modes, humps=params))

@@ -1,0 +1,243 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle.
+
+Sizes span several 32x16 tiles with ragged tails, tiny odd grids, both
+boundary treatments, the workloads' own initial states and generic states
+with every variable active; the full-size workloads are checked on the whole
+grid where the oracle is fast enough (1024x512) and on sampled patches where it
+is not (8192^2).  Tolerances are stated in gpu_util.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from oracle import PERIODIC, REFLECTING
+from paper_2601_02540_b300 import inputs, sgn
+import gpu_util as gu
+import pins
+
+pytestmark = pytest.mark.gpu
+
+GRIDS = [(3, 3), (5, 3), (7, 9), (33, 17), (65, 40), (100, 37), (130, 70)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    sgn.lib()
+
+
+# ------------------------------------------------------------------ right-hand side
+@pytest.mark.parametrize("bc", [PERIODIC, REFLECTING])
+@pytest.mark.parametrize("nx,ny", GRIDS)
+def test_rhs_parity_generic_states(bc, nx, ny):
+    for seed in (1, 2):
+        p = inputs.smooth_state(nx, ny, bc, seed=seed, xmax=1.3, ymax=0.9)
+        s = gu.solver(p)
+        dq = gu.to_np(s.rhs(s.state(p.q0)))
+        ref, sc = gu.oracle_rhs_and_scale(p, p.q0)
+        e = gu.rhs_errors(dq, ref, sc)
+        assert np.all(e <= gu.RHS_TOL), e
+        s.close()
+
+
+@pytest.mark.parametrize("make", [lambda: inputs.workload1(),
+                                  lambda: inputs.workload2(200, 100),
+                                  lambda: inputs.workload2()],
+                         ids=["workload1", "workload2_small", "workload2_full"])
+def test_rhs_parity_workloads(make):
+    """Workload initial states (after initialization) and the state after a few
+    oracle steps, so that u, v, w are active; whole grid."""
+    p = make()
+    g = pins.grid_of(p)
+    q0 = orc.init_aux(g, p.b, p.q0)
+    q5 = orc.rk4(g, p.b, q0, p.dt, 5)
+    s = gu.solver(p)
+    for q in (q0, q5):
+        dq = gu.to_np(s.rhs(s.state(q)))
+        ref, sc = gu.oracle_rhs_and_scale(p, q)
+        e = gu.rhs_errors(dq, ref, sc)
+        assert np.all(e <= gu.RHS_TOL), e
+    s.close()
+
+
+@pytest.mark.parametrize("bc", [PERIODIC, REFLECTING])
+def test_init_aux_parity(bc):
+    p = inputs.smooth_state(70, 45, bc, seed=3)
+    s = gu.solver(p)
+    q = gu.to_np(gu.gpu_init(s, p.q0))
+    ref = orc.init_aux(pins.grid_of(p), p.b, p.q0)
+    assert np.array_equal(q[4], ref[4])
+    assert np.array_equal(q[:3], ref[:3])
+    assert np.max(np.abs(q[3] - ref[3])) <= 1e-13 * np.max(np.abs(ref[3]))
+    s.close()
+
+
+# ------------------------------------------------------------------ time stepping
+def _step_compare(p: inputs.Problem, nsteps: int):
+    g = pins.grid_of(p)
+    q0 = orc.init_aux(g, p.b, p.q0)
+    ref = orc.rk4(g, p.b, q0, p.dt, nsteps)
+    s = gu.solver(p)
+    q = s.state(q0)
+    s.step(q, p.dt, nsteps)
+    out = gu.to_np(q)
+    s.close()
+    return gu.state_errors(out, ref), out, ref
+
+
+def test_step_parity_workload1_full():
+    """Periodic 64^2, 200 RK4 steps, FP64: within 1e-10 of the oracle."""
+    p = inputs.workload1()
+    e, out, ref = _step_compare(p, p.nsteps)
+    assert np.all(e <= gu.STEP_TOL), e
+
+
+@pytest.mark.parametrize("bc", [PERIODIC, REFLECTING])
+@pytest.mark.parametrize("nx,ny", [(5, 3), (33, 17), (100, 37)])
+def test_step_parity_generic(bc, nx, ny):
+    p = inputs.smooth_state(nx, ny, bc, seed=4, xmax=1.3, ymax=0.9)
+    e, _, _ = _step_compare(p, 20)
+    assert np.all(e <= gu.STEP_TOL), e
+
+
+def test_step_parity_workload2_reduced():
+    p = inputs.workload2(160, 80)
+    e, _, _ = _step_compare(p, 300)
+    assert np.all(e <= gu.STEP_TOL), e
+
+
+def test_step_parity_workload2_full_size():
+    """1024x512 reflecting, the launch configuration of the full workload,
+    10 steps on the whole grid."""
+    p = inputs.workload2()
+    e, _, _ = _step_compare(p, 10)
+    assert np.all(e <= gu.STEP_TOL), e
+
+
+def _patch(a: np.ndarray, j0: int, i0: int, m: int) -> np.ndarray:
+    ny, nx = a.shape[-2:]
+    jj = (np.arange(j0, j0 + m) % ny)[:, None]
+    ii = (np.arange(i0, i0 + m) % nx)[None, :]
+    return a[..., jj, ii]
+
+
+def test_workload3_full_size_sampled_patches():
+    """8192^2 periodic: RHS and one RK4 step on the whole grid; eight sampled
+    patches recomputed by the oracle (with a halo of 1 for the RHS and 4 for a
+    step, the domain of dependence), interiors compared."""
+    p = inputs.workload3()
+    dx, dy = p.spacing()
+    q_host = orc.init_aux(pins.grid_of(p), p.b, p.q0)
+    s = gu.solver(p)
+    q = s.state(q_host)
+    dq = gu.to_np(s.rhs(q))
+    s.step(q, p.dt, 1)
+    q1 = gu.to_np(q)
+    s.close()
+    rng = np.random.default_rng(7)
+    m = 24
+    for _ in range(8):
+        j0, i0 = (int(v) for v in rng.integers(0, 8192, size=2))
+        for halo, what in ((1, "rhs"), (4, "step")):
+            n = m + 2 * halo
+            g = orc.Grid(n, n, 0.0, n * dx, 0.0, n * dy, PERIODIC, p.g, p.lam)
+            bp = _patch(p.b, j0 - halo, i0 - halo, n)
+            qp = _patch(q_host, j0 - halo, i0 - halo, n)
+            sl = (slice(None), slice(halo, halo + m), slice(halo, halo + m))
+            if what == "rhs":
+                ref = orc.rhs(g, bp, qp)[sl]
+                sc = orc.rhs_scale(g, bp, qp)[sl]
+                got = _patch(dq, j0, i0, m)
+                e = gu.rhs_errors(got, ref, sc)
+                assert np.all(e <= gu.RHS_TOL), (what, e)
+            else:
+                ref = orc.rk4(g, bp, qp, p.dt, 1)[sl]
+                got = _patch(q1, j0, i0, m)
+                e = gu.state_errors(got, ref)
+                assert np.all(e <= gu.STEP_TOL), (what, e)
+
+
+# ------------------------------------------------------------------ diagnostics
+@pytest.mark.parametrize("bc", [PERIODIC, REFLECTING])
+def test_mass_energy_parity(bc):
+    p = inputs.smooth_state(130, 70, bc, seed=5)
+    g = pins.grid_of(p)
+    s = gu.solver(p)
+    d = s.mass_energy(s.state(p.q0))
+    ref = orc.diagnostics(g, p.b, p.q0)
+    for k in ("mass", "energy", "energy_shifted"):
+        assert abs(d[k] - ref[k]) <= 1e-13 * abs(ref[k]), (k, d[k], ref[k])
+    # Thm. 4.1/4.2: the semi-discrete energy rate vanishes up to rounding
+    assert abs(d["dEdt"]) <= 1e-13 * ref["dEdt_scale"], (d["dEdt"], ref["dEdt_scale"])
+    s.close()
+
+
+def test_mass_conserved_by_gpu_steps():
+    p = inputs.workload2(256, 128)
+    s = gu.solver(p)
+    q = gu.gpu_init(s, p.q0)
+    m0 = s.mass_energy(q)["mass"]
+    s.step(q, p.dt, 200)
+    m1 = s.mass_energy(q)["mass"]
+    assert abs(m1 - m0) <= 1e-13 * abs(m0)
+    s.close()
+
+
+def test_diagnostics_and_steps_are_deterministic():
+    p = inputs.smooth_state(100, 37, REFLECTING, seed=6)
+    s = gu.solver(p)
+    outs = []
+    for _ in range(2):
+        q = s.state(p.q0)
+        s.step(q, p.dt, 7)
+        outs.append((gu.to_np(q), s.mass_energy(q)))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
+    s.close()
+
+
+# ------------------------------------------------------------------ errors (benign)
+def test_nonfinite_and_nonpositive_h_are_reported():
+    p = inputs.smooth_state(40, 20, PERIODIC, seed=1)
+    s = gu.solver(p)
+    q = s.state(p.q0)
+    q[0, 3, 5] = float("nan")
+    with pytest.raises(sgn.SgnError) as ei:
+        s.mass_energy(q)
+    assert ei.value.status == 5
+    q = s.state(p.q0)
+    q[0, 7, 9] = -0.5
+    s.step(q, p.dt, 1)
+    with pytest.raises(sgn.SgnError) as ei:
+        s.check()
+    assert ei.value.status == 4
+    # the flag was cleared: a valid state passes again
+    s.mass_energy(s.state(p.q0))
+    s.close()
+
+
+def test_invalid_pointers_rejected():
+    p = inputs.smooth_state(16, 16, PERIODIC, seed=1)
+    s = gu.solver(p)
+    host = np.zeros((5, 16, 16))
+    dev = s.state(p.q0)
+    lib = sgn.lib()
+    assert lib.sgn_rhs(s.ctx, ctypes.c_void_p(host.ctypes.data), ctypes.c_void_p(dev.data_ptr()), None) == 1
+    assert lib.sgn_rhs(s.ctx, ctypes.c_void_p(dev.data_ptr()), ctypes.c_void_p(dev.data_ptr()), None) == 1
+    assert lib.sgn_step(s.ctx, ctypes.c_void_p(dev.data_ptr()), float("nan"), 1, None) == 1
+    assert lib.sgn_step(s.ctx, ctypes.c_void_p(dev.data_ptr() + 8), 0.1, 1, None) == 1
+    s.close()
+
+
+def test_zero_steps_is_identity():
+    p = inputs.smooth_state(20, 12, REFLECTING, seed=2)
+    s = gu.solver(p)
+    q = s.state(p.q0)
+    s.step(q, p.dt, 0)
+    assert np.array_equal(gu.to_np(q), p.q0)
+    s.close()
