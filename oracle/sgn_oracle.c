@@ -140,6 +140,30 @@ void ORC(dy_apply)(const orc_grid* G, const real* f, real* out)
         sbp_line(G->bc, G->ny, dy, f + i, G->nx, out + i);
 }
 
+#ifndef ORC_COMPLEX
+/* |D| |f| along one line: the SBP operator with each entry replaced by its
+ * absolute value, applied to |f|, i.e. the magnitude of the two operands each
+ * difference subtracts.  Used only for the rounding-error scale. */
+static void sbp_line_abs(int bc, int n, double d, const real* f, long s, real* out)
+{
+    for (int k = 0; k < n; k++) {
+        real val;
+        if (bc == BC_PERIODIC) {
+            int kp = (k + 1) % n;
+            int km = (k - 1 + n) % n;
+            val = (fabs(f[kp * s]) + fabs(f[km * s])) / (2.0 * d);
+        } else if (k == 0) {
+            val = (fabs(f[1 * s]) + fabs(f[0])) / d;
+        } else if (k == n - 1) {
+            val = (fabs(f[(n - 1) * s]) + fabs(f[(n - 2) * s])) / d;
+        } else {
+            val = (fabs(f[(k + 1) * s]) + fabs(f[(k - 1) * s])) / (2.0 * d);
+        }
+        out[k * s] = val;
+    }
+}
+#endif
+
 /* Derivatives needed by the right-hand side: the twelve D_x and twelve D_y
  * operands of eqs. (sd_periodic_2D_SGN) / (semi_2D), each as a full plane. */
 enum {
@@ -163,7 +187,8 @@ typedef struct {
     real* buf;
 } derivs;
 
-static int derivs_compute(const orc_grid* G, const real* b, const real* q, derivs* D)
+/* absval = 1 (real build only): |D| |product| instead of D product. */
+static int derivs_compute(const orc_grid* G, const real* b, const real* q, derivs* D, int absval)
 {
     long n = (long)G->nx * G->ny;
     D->n = n;
@@ -199,6 +224,18 @@ static int derivs_compute(const orc_grid* G, const real* b, const real* q, deriv
             }
             prod[c] = val;
         }
+#ifndef ORC_COMPLEX
+        if (absval) {
+            double dx, dy;
+            ORC(spacing)(G, &dx, &dy);
+            for (int j = 0; j < G->ny; j++)
+                sbp_line_abs(G->bc, G->nx, dx, prod + (long)j * G->nx, 1, D->dx[p] + (long)j * G->nx);
+            for (int i = 0; i < G->nx; i++)
+                sbp_line_abs(G->bc, G->ny, dy, prod + i, G->nx, D->dy[p] + i);
+            continue;
+        }
+#endif
+        (void)absval;
         ORC(dx_apply)(G, prod, D->dx[p]);
         ORC(dy_apply)(G, prod, D->dy[p]);
     }
@@ -327,7 +364,7 @@ static void terms_at(const orc_grid* G, const real* b, const real* q, const deri
 int ORC(rhs)(const orc_grid* G, const real* b, const real* q, real* dq)
 {
     derivs D;
-    if (derivs_compute(G, b, q, &D)) return -1;
+    if (derivs_compute(G, b, q, &D, 0)) return -1;
     const long n = D.n;
     for (int j = 0; j < G->ny; j++)
         for (int i = 0; i < G->nx; i++) {
@@ -348,15 +385,18 @@ int ORC(rhs)(const orc_grid* G, const real* b, const real* q, real* dq)
 }
 
 #ifndef ORC_COMPLEX
-/* Magnitude scale of each RHS value: the sum of the absolute values of the
- * terms that are added to form it (divided by |h| where the RHS is).  The
- * rounding error of any evaluation order of the sum is bounded by a small
- * multiple of unit round-off times this scale, so parity tolerances are
- * stated relative to it. */
+/* Rounding-error scale of each RHS value (forward error bound): every term
+ * coef * D f is replaced by |coef| * |D| |f| (the size of the operands the
+ * difference subtracts, not the size of the difference), pointwise terms by
+ * their absolute value, and the factor (1 - eta/h) by 1 + |eta/h| (it is itself
+ * a difference of two O(1) numbers); the terms are then summed (and divided by
+ * |h| where the RHS is).  Any evaluation of the RHS in a precision with unit
+ * round-off u carries an error of a small multiple of u times this scale, so
+ * the parity tolerances are stated with it. */
 int orc_rhs_scale(const orc_grid* G, const real* b, const real* q, real* scale)
 {
     derivs D;
-    if (derivs_compute(G, b, q, &D)) return -1;
+    if (derivs_compute(G, b, q, &D, 1)) return -1;
     const long n = D.n;
     for (int j = 0; j < G->ny; j++)
         for (int i = 0; i < G->nx; i++) {
@@ -364,6 +404,14 @@ int orc_rhs_scale(const orc_grid* G, const real* b, const real* q, real* scale)
             node_terms T;
             terms_at(G, b, q, &D, c, i, j, &T);
             const real h = q[F_H * n + c];
+            /* The factor (1 - eta/h) in the last term of the u and v
+             * equations and in the source of the w equation is itself a
+             * difference of two O(1) numbers: its rounding error scales with
+             * 1 + |eta/h|, not with its (possibly tiny) value. */
+            const real rho = fabs(q[F_ETA * n + c] / h);
+            T.t[F_U][14] = (G->lambda / 2.0) * (1.0 + rho) * D.dx[P_B][c];
+            T.t[F_V][14] = (G->lambda / 2.0) * (1.0 + rho) * D.dy[P_B][c];
+            T.t[F_W][8] = G->lambda * (1.0 + rho);
             for (int f = 0; f < NFIELD; f++) {
                 real s = 0.0;
                 for (int k = 0; k < T.nt[f]; k++) s += fabs(T.t[f][k]);

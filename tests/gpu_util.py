@@ -2,12 +2,15 @@
 library (C ABI via the ctypes binding) and through the oracle, and compare.
 
 Tolerances (FP64 path):
-  RHS    ||gpu_f - orc_f||_inf <= 1e-12 * max(||orc_f||_inf, 1e-2 * ||S_f||_inf)
-         per field f, where S_f is the oracle's sum of |terms| of that RHS value.
-         This is the norm-wise relative bound of 1e-12 per RHS; the floor only
-         matters for fields whose RHS vanishes identically (e.g. w_t of a state
-         at rest), where a relative error has no meaning and the rounding level
-         of the summed terms is the natural scale.
+  RHS    ||gpu_f - orc_f||_inf <= 1e-12 * ||orc_f||_inf + 16 u ||S_f||_inf
+         per field f, u = 2^-53, where S_f is the oracle's forward rounding-error
+         scale of that RHS value (each term coef * D f counted as
+         |coef| |D| |f|, see oracle.rhs_scale).  The first part is the norm-wise
+         relative bound of 1e-12 per RHS; the second is the rounding error any
+         FP64 evaluation of the printed formula carries, which dominates only
+         where the result is a near-cancellation of much larger terms (a state
+         near rest, where the split-form differences of O(1) fields nearly
+         cancel; a field whose RHS vanishes identically).
   steps  ||gpu_f - orc_f||_inf <= 1e-10 * max(||orc_f||_inf, 1e-3 * ||orc_h||_inf)
          per field after the run (same reading for fields that stay near 0).
 """
@@ -22,6 +25,8 @@ import pins
 
 RHS_TOL = 1e-12
 STEP_TOL = 1e-10
+U64 = 2.0 ** -53
+ROUNDING_MULT = 16.0
 
 
 def solver(p: inputs.Problem, prec: str = "f64") -> sgn.Solver:
@@ -39,11 +44,18 @@ def to_np(t: torch.Tensor) -> np.ndarray:
 
 
 def rhs_errors(gpu: np.ndarray, ref: np.ndarray, scale: np.ndarray) -> np.ndarray:
-    """Per-field error normalized by the RHS tolerance denominator."""
+    """Per-field error divided by its allowance; <= 1 passes."""
     err = np.max(np.abs(gpu - ref), axis=(1, 2))
-    den = np.maximum(np.max(np.abs(ref), axis=(1, 2)), 1e-2 * np.max(scale, axis=(1, 2)))
-    den = np.where(den > 0, den, 1.0)
-    return err / den
+    allow = RHS_TOL * np.max(np.abs(ref), axis=(1, 2)) + ROUNDING_MULT * U64 * np.max(scale, axis=(1, 2))
+    allow = np.where(allow > 0, allow, np.finfo(float).tiny)
+    return err / allow
+
+
+def rhs_rel(gpu: np.ndarray, ref: np.ndarray) -> np.ndarray:
+    """Plain norm-wise relative error per field (reported, not asserted)."""
+    err = np.max(np.abs(gpu - ref), axis=(1, 2))
+    den = np.max(np.abs(ref), axis=(1, 2))
+    return np.where(den > 0, err / np.where(den > 0, den, 1.0), err)
 
 
 def state_errors(gpu: np.ndarray, ref: np.ndarray) -> np.ndarray:
