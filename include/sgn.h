@@ -123,6 +123,28 @@ SGN_API sgn_status sgn_step(sgn_ctx* ctx, void* q_dev, double dt, int nsteps, vo
  * latched device flag. */
 SGN_API sgn_status sgn_mass_energy(sgn_ctx* ctx, const void* q_dev, double* out, void* stream);
 
+/* The diagnostics of sgn_mass_energy for callers that may not allocate device
+ * memory: code embedded in a framework whose allocator owns every byte of the
+ * device, latency-critical loops where cudaMalloc/cudaFree would implicitly
+ * synchronize the device, plugins that are not allowed to allocate.  There is
+ * no counterpart in the paper; it is a second way to run the same reduction.
+ *
+ * Needs no context: p describes the grid (prec must be SGN_F64, else
+ * SGN_E_UNSUPPORTED), b_dev is the bathymetry (double, nx*ny, device), q_dev
+ * the state (double, five planes, device, 16-byte aligned), out 4 doubles of
+ * host memory, filled as by sgn_mass_energy.  Calls no allocating routine:
+ * the per-block partial sums live in a 1 MiB array of static device memory
+ * that every GPU which loads the library keeps until the process exits.  That
+ * limits the grid to 32768 blocks of 32x16 nodes (16,777,216 nodes, e.g.
+ * 4096x4096); larger grids return SGN_E_INVAL.  The first call on a device
+ * looks up the array's device address and sets the kernel's shared-memory
+ * limit (make that first call before any stream capture).  All calls share
+ * the one array: calls that overlap on the GPU (other streams, other threads)
+ * race and must be serialized by the caller.  Synchronizes `stream`; reports a
+ * non-positive or non-finite h like sgn_mass_energy. */
+SGN_API sgn_status sgn_mass_energy_noalloc(const sgn_params* p, const void* b_dev, const void* q_dev,
+                                           double* out, void* stream);
+
 /* Synchronize `stream` and report (and clear) the latched device flag. */
 SGN_API sgn_status sgn_check(sgn_ctx* ctx, void* stream);
 

@@ -42,6 +42,9 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 }  // namespace
 
+// Message for sgn_last_error() from other translation units of the library.
+void sgn_record_error(const char* msg) { fail(SGN_E_INVAL, "%s", msg); }
+
 struct sgn_ctx {
     sgn_params p;
     Geom G;

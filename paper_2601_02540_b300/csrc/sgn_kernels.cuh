@@ -289,7 +289,7 @@ k_stage(StageArgs<TC, TIN, TA> a) {
 
 // Second pass of the diagnostics: one block sums the per-block partials in a
 // fixed order (each thread a strided slice, then a fixed tree).
-__global__ void __launch_bounds__(256) k_reduce_partials(const double* __restrict__ partials,
+static __global__ void __launch_bounds__(256) k_reduce_partials(const double* __restrict__ partials,
                                                           long long nblk, double* __restrict__ out) {
     __shared__ double red[256][NDIAG];
     double s[NDIAG] = {0.0, 0.0, 0.0, 0.0};

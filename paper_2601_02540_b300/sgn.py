@@ -35,6 +35,7 @@ _SIGNATURES = {
     "sgn_step": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_int, _V]),
     "sgn_mass_energy": (ctypes.c_int, [_V, _V, _V, _V]),
     "sgn_check": (ctypes.c_int, [_V, _V]),
+    "sgn_mass_energy_noalloc": (ctypes.c_int, [_V, _V, _V, _V, _V]),
     "sgn_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "sgn_last_error": (ctypes.c_char_p, []),
     "sgn_launch_count": (ctypes.c_ulonglong, []),
@@ -126,6 +127,16 @@ def sgn_step(ctx, q: torch.Tensor, dt: float, nsteps: int, dtype: torch.dtype, s
 def sgn_mass_energy(ctx, q: torch.Tensor, dtype: torch.dtype, stream=None) -> list[float]:
     out = (ctypes.c_double * 4)()
     _ok(lib().sgn_mass_energy(ctx, _dptr(q, dtype, "q"), out, _stream(stream)), "sgn_mass_energy")
+    return list(out)
+
+
+def sgn_mass_energy_noalloc(params: Params, b: torch.Tensor, q: torch.Tensor, stream=None) -> list[float]:
+    """Diagnostics without a context and without any device allocation (FP64
+    only; grids up to 4096x4096); see include/sgn.h."""
+    out = (ctypes.c_double * 4)()
+    _ok(lib().sgn_mass_energy_noalloc(ctypes.byref(params), _dptr(b, torch.float64, "b"),
+                                      _dptr(q, torch.float64, "q"), out, _stream(stream)),
+        "sgn_mass_energy_noalloc")
     return list(out)
 
 
