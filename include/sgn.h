@@ -15,6 +15,8 @@
  *   sgn_mass_energy  total mass 1^T M h and energy 1^T M E of Thm. 4.1/4.2 and
  *                    the semi-discrete energy rate <d_q E, q_t>_M of eq.
  *                    (splitcondition).
+ *   sgn_rhs_vjp, sgn_step_record, sgn_step_vjp   the discrete adjoint of the
+ *                    RHS and of one RK4 step (no counterpart in the paper).
  *
  * Data layout.  A state is five planes (h, u, v, w, eta), each plane nx*ny
  * values, x fastest: element (f, j, i) at index f*nx*ny + j*nx + i.  Node
@@ -144,6 +146,36 @@ SGN_API sgn_status sgn_mass_energy(sgn_ctx* ctx, const void* q_dev, double* out,
  * non-positive or non-finite h like sgn_mass_energy. */
 SGN_API sgn_status sgn_mass_energy_noalloc(const sgn_params* p, const void* b_dev, const void* q_dev,
                                            double* out, void* stream);
+
+/* Adjoint of the RHS (the paper has no adjoint; this is the exact transpose of
+ * the Jacobian of the discrete RHS of eqs. (sd_periodic_2D_SGN) / (semi_2D) as
+ * sgn_rhs evaluates it):
+ *   qbar_dev  = J(q)^T abar            (overwritten, five planes)
+ *   bbar_dev += (d RHS / d b)^T abar   (accumulated, one plane)
+ * All double, device; qbar_dev must not overlap q_dev or abar_dev.  SGN_F64
+ * contexts only (else SGN_E_UNSUPPORTED).  Asynchronous. */
+SGN_API sgn_status sgn_rhs_vjp(sgn_ctx* ctx, const void* q_dev, const void* abar_dev, void* qbar_dev,
+                               void* bbar_dev, void* stream);
+
+/* Like sgn_step, and records every step's stage states for the adjoint:
+ * before step n the stash slot n (20 planes at stash_dev + 20*n*nx*ny doubles)
+ * receives [q_n | Q2 | Q3 | Q4] with Q2 = q_n + dt/2 k1, Q3 = q_n + dt/2 k2,
+ * Q4 = q_n + dt k3.  stash_dev holds nsteps slots (caller-owned, device,
+ * double).  SGN_F64 only.  Asynchronous. */
+SGN_API sgn_status sgn_step_record(sgn_ctx* ctx, void* q_dev, double dt, int nsteps, void* stash_dev,
+                                   void* stream);
+
+/* Adjoint of one classical RK4 step of size dt, using one stash slot written
+ * by sgn_step_record: on entry qbar_dev holds the cotangent of q_{n+1}, on
+ * return that of q_n:  k4bar = dt/6 qbar', Q4bar = J(Q4)^T k4bar,
+ * k3bar = dt/3 qbar' + dt Q4bar, Q3bar = J(Q3)^T k3bar, k2bar = dt/3 qbar' +
+ * dt/2 Q3bar, Q2bar = J(Q2)^T k2bar, k1bar = dt/6 qbar' + dt/2 Q2bar,
+ * Q1bar = J(q_n)^T k1bar, qbar = qbar' + Q1bar + Q2bar + Q3bar + Q4bar, and
+ * bbar_dev += sum_s (d RHS / d b)(Q_s)^T ks_bar.  Four fused adjoint launches.
+ * The first call allocates 15 planes of context scratch (SGN_E_NOMEM if that
+ * fails).  SGN_F64 only.  Asynchronous. */
+SGN_API sgn_status sgn_step_vjp(sgn_ctx* ctx, const void* stash_dev, void* qbar_dev, void* bbar_dev,
+                                double dt, void* stream);
 
 /* Synchronize `stream` and report (and clear) the latched device flag. */
 SGN_API sgn_status sgn_check(sgn_ctx* ctx, void* stream);

@@ -2,6 +2,7 @@
 // kernel dispatch and the C ABI declared in include/sgn.h.
 #include "sgn.h"
 #include "sgn_kernels.cuh"
+#include "sgn_adjoint.cuh"
 
 #include <atomic>
 #include <cmath>
@@ -61,6 +62,7 @@ struct sgn_ctx {
     int* hflag = nullptr;        // pinned host copy
     long long nblk = 0;
     dim3 grid;
+    double* adj = nullptr;       // adjoint scratch (FP64): accumulator + two cotangents
 };
 
 namespace {
@@ -219,12 +221,61 @@ void free_ctx(sgn_ctx* c) {
     cudaFree(c->partials);
     cudaFree(c->dout);
     cudaFree(c->flag);
+    cudaFree(c->adj);
     cudaFreeHost(c->hout);
     cudaFreeHost(c->hflag);
     delete c;
 }
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+template <int BC, int MODE>
+cudaError_t launch_adjoint(const sgn_ctx* c, const sgn::AdjArgs& a, cudaStream_t s) {
+    auto kern = sgn::k_adjoint<BC, MODE>;
+    const size_t smem = (size_t)sgn::ADJ_PLANES * sgn::ADJ_HN * sizeof(double);
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    const dim3 grid((c->p.nx + sgn::ADJ_TX - 1) / sgn::ADJ_TX, (c->p.ny + sgn::ADJ_TY - 1) / sgn::ADJ_TY);
+    kern<<<grid, dim3(sgn::ADJ_TX, sgn::ADJ_TY), smem, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t adjoint(const sgn_ctx* c, const sgn::AdjArgs& a, cudaStream_t s) {
+    return c->p.bc == SGN_BC_REFLECTING ? launch_adjoint<sgn::BC_REFLECTING, MODE>(c, a, s)
+                                        : launch_adjoint<sgn::BC_PERIODIC, MODE>(c, a, s);
+}
+
+// One RK4 step that also records its stage states: stash = [q_n | Q2 | Q3 | Q4].
+template <int BC>
+cudaError_t record_step(sgn_ctx* c, double* q, double dt, double* stash, cudaStream_t s) {
+    const long long P5 = 5 * c->G.plane;
+    double* acc = static_cast<double*>(c->acc);
+    cudaError_t e = cudaMemcpyAsync(stash, q, P5 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    StageArgs<double, double, double> a1 = base_args<double, double, double>(c);
+    a1.X = q; a1.qn = q; a1.acc = acc; a1.Qout = stash + P5; a1.c_acc = dt / 6.0; a1.c_q = dt / 2.0;
+    if ((e = launch_stage<double, double, double, BC, sgn::MODE_S1>(c, a1, s)) != cudaSuccess) return e;
+    StageArgs<double, double, double> a2 = a1;
+    a2.X = stash + P5; a2.Qout = stash + 2 * P5; a2.c_acc = dt / 3.0; a2.c_q = dt / 2.0;
+    if ((e = launch_stage<double, double, double, BC, sgn::MODE_S2>(c, a2, s)) != cudaSuccess) return e;
+    StageArgs<double, double, double> a3 = a1;
+    a3.X = stash + 2 * P5; a3.Qout = stash + 3 * P5; a3.c_acc = dt / 3.0; a3.c_q = dt;
+    if ((e = launch_stage<double, double, double, BC, sgn::MODE_S3>(c, a3, s)) != cudaSuccess) return e;
+    StageArgs<double, double, double> a4 = base_args<double, double, double>(c);
+    a4.X = stash + 3 * P5; a4.acc = acc; a4.out = q; a4.c_acc = dt / 6.0;
+    return launch_stage<double, double, double, BC, sgn::MODE_S4>(c, a4, s);
+}
+
+sgn_status need_f64(const sgn_ctx* c, const char* what) {
+    if (c->p.prec != SGN_F64) return fail(SGN_E_UNSUPPORTED, "%s: the adjoint is implemented for SGN_F64 only", what);
+    return SGN_OK;
+}
 
 }  // namespace
 
@@ -411,6 +462,98 @@ sgn_status sgn_mass_energy(sgn_ctx* c, const void* q_dev, double* out, void* str
 sgn_status sgn_check(sgn_ctx* c, void* stream) {
     if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
     return read_flag(c, static_cast<cudaStream_t>(stream));
+}
+
+sgn_status sgn_rhs_vjp(sgn_ctx* c, const void* q_dev, const void* abar_dev, void* qbar_dev,
+                       void* bbar_dev, void* stream) {
+    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
+    sgn_status st = need_f64(c, "sgn_rhs_vjp");
+    if (st == SGN_OK) st = check_state_ptr(q_dev, "q_dev");
+    if (st == SGN_OK) st = check_state_ptr(abar_dev, "abar_dev");
+    if (st == SGN_OK) st = check_state_ptr(qbar_dev, "qbar_dev");
+    if (st == SGN_OK) st = check_state_ptr(bbar_dev, "bbar_dev");
+    if (st != SGN_OK) return st;
+    if (qbar_dev == q_dev || qbar_dev == abar_dev) return fail(SGN_E_INVAL, "qbar_dev must not overlap the inputs");
+    sgn::AdjArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.X = static_cast<const double*>(q_dev);
+    a.b = c->b64;
+    a.A = static_cast<const double*>(abar_dev);
+    a.a_scale = 1.0;
+    a.qbar = static_cast<double*>(qbar_dev);
+    a.bbar = static_cast<double*>(bbar_dev);
+    a.G = c->G;
+    cudaError_t e = adjoint<sgn::ADJ_MODE_RHS>(c, a, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "sgn_rhs_vjp");
+    return SGN_OK;
+}
+
+sgn_status sgn_step_record(sgn_ctx* c, void* q_dev, double dt, int nsteps, void* stash_dev, void* stream) {
+    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
+    sgn_status st = need_f64(c, "sgn_step_record");
+    if (st == SGN_OK) st = check_state_ptr(q_dev, "q_dev");
+    if (st == SGN_OK && nsteps > 0) st = check_state_ptr(stash_dev, "stash_dev");
+    if (st != SGN_OK) return st;
+    if (!finite_pos(dt)) return fail(SGN_E_INVAL, "dt must be finite and > 0");
+    if (nsteps < 0) return fail(SGN_E_INVAL, "nsteps must be >= 0");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double* q = static_cast<double*>(q_dev);
+    double* stash = static_cast<double*>(stash_dev);
+    const long long P20 = 20 * c->G.plane;
+    for (int n = 0; n < nsteps; n++) {
+        cudaError_t e = c->p.bc == SGN_BC_REFLECTING
+                            ? record_step<sgn::BC_REFLECTING>(c, q, dt, stash + n * P20, s)
+                            : record_step<sgn::BC_PERIODIC>(c, q, dt, stash + n * P20, s);
+        if (e != cudaSuccess) return cuda_fail(e, "sgn_step_record");
+    }
+    return SGN_OK;
+}
+
+sgn_status sgn_step_vjp(sgn_ctx* c, const void* stash_dev, void* qbar_dev, void* bbar_dev, double dt,
+                        void* stream) {
+    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
+    sgn_status st = need_f64(c, "sgn_step_vjp");
+    if (st == SGN_OK) st = check_state_ptr(stash_dev, "stash_dev");
+    if (st == SGN_OK) st = check_state_ptr(qbar_dev, "qbar_dev");
+    if (st == SGN_OK) st = check_state_ptr(bbar_dev, "bbar_dev");
+    if (st != SGN_OK) return st;
+    if (!finite_pos(dt)) return fail(SGN_E_INVAL, "dt must be finite and > 0");
+    const long long P5 = 5 * c->G.plane;
+    if (!c->adj) {
+        if (cudaMalloc(&c->adj, 3 * P5 * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            c->adj = nullptr;
+            return fail(SGN_E_NOMEM, "adjoint scratch (%lld bytes)", (long long)(3 * P5 * sizeof(double)));
+        }
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const double* stash = static_cast<const double*>(stash_dev);
+    double* qbar = static_cast<double*>(qbar_dev);
+    double* qacc = c->adj;
+    double* A0 = c->adj + P5;
+    double* A1 = c->adj + 2 * P5;
+    sgn::AdjArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.b = c->b64;
+    a.bbar = static_cast<double*>(bbar_dev);
+    a.qprime = qbar;
+    a.G = c->G;
+    cudaError_t e;
+    // stage 4: k4bar = dt/6 qbar'; Q4bar = J(Q4)^T k4bar; k3bar = dt/3 qbar' + dt Q4bar
+    a.X = stash + 3 * P5; a.A = qbar; a.a_scale = dt / 6.0;
+    a.first = 1; a.qacc_out = qacc; a.Anext = A0; a.c_prime = dt / 3.0; a.c_bar = dt;
+    if ((e = adjoint<sgn::ADJ_MODE_STAGE>(c, a, s)) != cudaSuccess) return cuda_fail(e, "sgn_step_vjp");
+    // stage 3: Q3bar = J(Q3)^T k3bar; k2bar = dt/3 qbar' + dt/2 Q3bar
+    a.X = stash + 2 * P5; a.A = A0; a.a_scale = 1.0;
+    a.first = 0; a.qacc_in = qacc; a.qacc_out = qacc; a.Anext = A1; a.c_prime = dt / 3.0; a.c_bar = dt / 2.0;
+    if ((e = adjoint<sgn::ADJ_MODE_STAGE>(c, a, s)) != cudaSuccess) return cuda_fail(e, "sgn_step_vjp");
+    // stage 2: Q2bar = J(Q2)^T k2bar; k1bar = dt/6 qbar' + dt/2 Q2bar
+    a.X = stash + P5; a.A = A1; a.Anext = A0; a.c_prime = dt / 6.0; a.c_bar = dt / 2.0;
+    if ((e = adjoint<sgn::ADJ_MODE_STAGE>(c, a, s)) != cudaSuccess) return cuda_fail(e, "sgn_step_vjp");
+    // stage 1: Q1bar = J(q_n)^T k1bar; qbar = qbar' + Q1bar + Q2bar + Q3bar + Q4bar
+    a.X = stash; a.A = A0; a.Anext = nullptr; a.qacc_out = qbar;
+    if ((e = adjoint<sgn::ADJ_MODE_STAGE>(c, a, s)) != cudaSuccess) return cuda_fail(e, "sgn_step_vjp");
+    return SGN_OK;
 }
 
 }  // extern "C"

@@ -36,6 +36,9 @@ _SIGNATURES = {
     "sgn_mass_energy": (ctypes.c_int, [_V, _V, _V, _V]),
     "sgn_check": (ctypes.c_int, [_V, _V]),
     "sgn_mass_energy_noalloc": (ctypes.c_int, [_V, _V, _V, _V, _V]),
+    "sgn_rhs_vjp": (ctypes.c_int, [_V, _V, _V, _V, _V, _V]),
+    "sgn_step_record": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_int, _V, _V]),
+    "sgn_step_vjp": (ctypes.c_int, [_V, _V, _V, _V, ctypes.c_double, _V]),
     "sgn_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "sgn_last_error": (ctypes.c_char_p, []),
     "sgn_launch_count": (ctypes.c_ulonglong, []),
@@ -140,6 +143,26 @@ def sgn_mass_energy_noalloc(params: Params, b: torch.Tensor, q: torch.Tensor, st
     return list(out)
 
 
+def sgn_rhs_vjp(ctx, q: torch.Tensor, abar: torch.Tensor, qbar: torch.Tensor, bbar: torch.Tensor,
+                stream=None) -> None:
+    f = torch.float64
+    _ok(lib().sgn_rhs_vjp(ctx, _dptr(q, f, "q"), _dptr(abar, f, "abar"), _dptr(qbar, f, "qbar"),
+                          _dptr(bbar, f, "bbar"), _stream(stream)), "sgn_rhs_vjp")
+
+
+def sgn_step_record(ctx, q: torch.Tensor, dt: float, nsteps: int, stash: torch.Tensor, stream=None) -> None:
+    f = torch.float64
+    _ok(lib().sgn_step_record(ctx, _dptr(q, f, "q"), float(dt), int(nsteps), _dptr(stash, f, "stash"),
+                              _stream(stream)), "sgn_step_record")
+
+
+def sgn_step_vjp(ctx, stash_slot: torch.Tensor, qbar: torch.Tensor, bbar: torch.Tensor, dt: float,
+                 stream=None) -> None:
+    f = torch.float64
+    _ok(lib().sgn_step_vjp(ctx, _dptr(stash_slot, f, "stash"), _dptr(qbar, f, "qbar"),
+                           _dptr(bbar, f, "bbar"), float(dt), _stream(stream)), "sgn_step_vjp")
+
+
 def sgn_check(ctx, stream=None) -> None:
     _ok(lib().sgn_check(ctx, _stream(stream)), "sgn_check")
 
@@ -190,6 +213,22 @@ class Solver:
     def mass_energy(self, q: torch.Tensor) -> dict:
         m, e, es, r = sgn_mass_energy(self.ctx, q, self.state_dtype)
         return dict(mass=m, energy=e, energy_shifted=es, dEdt=r)
+
+    def rhs_vjp(self, q: torch.Tensor, abar: torch.Tensor, bbar: torch.Tensor | None = None):
+        """(J(q)^T abar, bbar + (dRHS/db)^T abar); FP64 contexts only."""
+        qbar = torch.empty_like(q)
+        if bbar is None:
+            bbar = torch.zeros(q.shape[1:], dtype=torch.float64, device=q.device)
+        sgn_rhs_vjp(self.ctx, q, abar, qbar, bbar)
+        return qbar, bbar
+
+    def step_record(self, q: torch.Tensor, dt: float, nsteps: int, stash: torch.Tensor) -> torch.Tensor:
+        sgn_step_record(self.ctx, q, dt, nsteps, stash)
+        return q
+
+    def step_vjp(self, stash_slot: torch.Tensor, qbar: torch.Tensor, bbar: torch.Tensor, dt: float):
+        sgn_step_vjp(self.ctx, stash_slot, qbar, bbar, dt)
+        return qbar, bbar
 
     def check(self) -> None:
         sgn_check(self.ctx)

@@ -1,0 +1,189 @@
+"""The hand-written adjoint against the oracle's tangent-linear model (complex
+step) and against finite differences.
+
+- RHS: the full transposed Jacobian on tiny grids, element by element
+  (GPU VJP of unit cotangents vs oracle JVP of unit directions), and dot-product
+  tests <J d, a> = <d, J^T a> on multi-tile ragged grids, both boundaries.
+- One RK4 step: dot-product test through sgn_step_record + sgn_step_vjp.
+- The gauge-misfit rollout gradient (checkpointing + recomputation) against the
+  oracle's complex-step derivative of the whole rollout, and against central
+  finite differences of the GPU loss (eps = 1e-6) on the inversion workload.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from oracle import PERIODIC, REFLECTING
+from paper_2601_02540_b300 import adjoint, inputs, sgn
+import pins
+
+pytestmark = pytest.mark.gpu
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+@pytest.mark.parametrize("bc", [PERIODIC, REFLECTING])
+@pytest.mark.parametrize("nx,ny", [(3, 3), (5, 4)])
+def test_rhs_vjp_full_transpose_tiny(bc, nx, ny):
+    p = inputs.smooth_state(nx, ny, bc, seed=3, xmax=1.3, ymax=0.9)
+    g = pins.grid_of(p)
+    n = 5 * nx * ny
+    m = nx * ny
+    # oracle Jacobian columns (state and bathymetry directions) by complex step
+    Jq = np.zeros((n, n))
+    Jb = np.zeros((n, m))
+    zq = np.zeros_like(p.q0)
+    zb = np.zeros_like(p.b)
+    for k in range(n):
+        d = np.zeros(n)
+        d[k] = 1.0
+        Jq[:, k] = orc.rhs_jvp(g, p.b, p.q0, zb, d.reshape(p.q0.shape)).ravel()
+    for k in range(m):
+        d = np.zeros(m)
+        d[k] = 1.0
+        Jb[:, k] = orc.rhs_jvp(g, p.b, p.q0, d.reshape(p.b.shape), zq).ravel()
+    s = sgn.Solver.from_problem(p)
+    q = _t(p.q0)
+    JqT = np.zeros((n, n))
+    JbT = np.zeros((m, n))
+    for k in range(n):
+        a = np.zeros(n)
+        a[k] = 1.0
+        qbar, bbar = s.rhs_vjp(q, _t(a.reshape(p.q0.shape)))
+        JqT[:, k] = qbar.cpu().numpy().ravel()
+        JbT[:, k] = bbar.cpu().numpy().ravel()
+    s.close()
+    scale = np.max(np.abs(Jq))
+    assert np.max(np.abs(JqT - Jq.T)) <= 1e-13 * scale, np.max(np.abs(JqT - Jq.T)) / scale
+    assert np.max(np.abs(JbT - Jb.T)) <= 1e-13 * np.max(np.abs(Jb)), np.max(np.abs(JbT - Jb.T))
+
+
+@pytest.mark.parametrize("bc", [PERIODIC, REFLECTING])
+@pytest.mark.parametrize("nx,ny", [(33, 17), (100, 37)])
+def test_rhs_vjp_dot_product(bc, nx, ny):
+    p = inputs.smooth_state(nx, ny, bc, seed=8, xmax=1.3, ymax=0.9)
+    g = pins.grid_of(p)
+    rng = np.random.default_rng(4)
+    s = sgn.Solver.from_problem(p)
+    for _ in range(3):
+        dq = rng.standard_normal(p.q0.shape)
+        db = rng.standard_normal(p.b.shape)
+        a = rng.standard_normal(p.q0.shape)
+        jd = orc.rhs_jvp(g, p.b, p.q0, db, dq)
+        qbar, bbar = s.rhs_vjp(_t(p.q0), _t(a))
+        lhs = float(np.sum(jd * a))
+        rhs = float(np.sum(dq * qbar.cpu().numpy()) + np.sum(db * bbar.cpu().numpy()))
+        mag = float(np.sum(np.abs(jd * a)))
+        assert abs(lhs - rhs) <= 1e-13 * mag, (lhs, rhs, mag)
+    s.close()
+
+
+@pytest.mark.parametrize("bc", [PERIODIC, REFLECTING])
+def test_step_vjp_dot_product(bc):
+    p = inputs.smooth_state(40, 23, bc, seed=9, xmax=1.3, ymax=0.9)
+    g = pins.grid_of(p)
+    rng = np.random.default_rng(5)
+    s = sgn.Solver.from_problem(p)
+    stash = torch.empty((1, 20, p.ny, p.nx), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        dq = rng.standard_normal(p.q0.shape)
+        db = rng.standard_normal(p.b.shape)
+        a = rng.standard_normal(p.q0.shape)
+        _, jd = orc.rk4_jvp(g, p.b, p.q0, db, dq, p.dt, 1)
+        q = _t(p.q0)
+        s.step_record(q, p.dt, 1, stash)
+        qbar = _t(a)
+        bbar = torch.zeros((p.ny, p.nx), dtype=torch.float64, device="cuda")
+        s.step_vjp(stash[0], qbar, bbar, p.dt)
+        lhs = float(np.sum(jd * a))
+        rhs = float(np.sum(dq * qbar.cpu().numpy()) + np.sum(db * bbar.cpu().numpy()))
+        mag = float(np.sum(np.abs(jd * a)))
+        assert abs(lhs - rhs) <= 1e-13 * mag, (lhs, rhs, mag)
+    s.close()
+
+
+def test_step_record_matches_step():
+    p = inputs.smooth_state(40, 23, REFLECTING, seed=2)
+    s = sgn.Solver.from_problem(p)
+    q1 = _t(p.q0)
+    s.step(q1, p.dt, 3)
+    q2 = _t(p.q0)
+    stash = torch.empty((3, 20, p.ny, p.nx), dtype=torch.float64, device="cuda")
+    s.step_record(q2, p.dt, 3, stash)
+    assert torch.equal(q1, q2)
+    assert torch.equal(stash[0, :5], _t(p.q0))
+    s.close()
+
+
+def _inversion_problem(n, nsteps, every, ngauges=16, seed=1004):
+    p = inputs.workload4(n=n, nsteps=nsteps, every=every, ngauges=ngauges, ndirs=5, seed=seed)
+    return p
+
+
+def _gpu_loss_and_grad(p, obs, K, need_grad=True):
+    s = sgn.Solver.from_problem(p)
+    gauges = torch.as_tensor(p.extra["gauges"], device="cuda")
+    b = _t(p.b).requires_grad_(need_grad)
+    h0 = _t(p.q0[0]).requires_grad_(need_grad)
+    out = adjoint.gauge_rollout(b, h0, s, p.dt, p.nsteps, p.extra["every"], gauges, K)
+    loss = torch.sum((out - _t(obs)) ** 2)
+    if need_grad:
+        loss.backward()
+        gb, gh = b.grad.cpu().numpy(), h0.grad.cpu().numpy()
+    else:
+        gb = gh = None
+    s.close()
+    return float(loss.item()), gb, gh
+
+
+def test_rollout_gradient_matches_oracle_tlm():
+    """Small reflecting inversion problem: the checkpointed adjoint gradient
+    along random directions equals the oracle's complex-step derivative of the
+    whole rollout (checkpoint K = 7 does not divide the 40 steps)."""
+    p = _inversion_problem(48, 40, 4, ngauges=6)
+    g = pins.grid_of(p)
+    gauges = p.extra["gauges"]
+    # observations: the truth run (perturbed bathymetry), computed by the oracle
+    qt = orc.init_aux(g, p.extra["b_true"], np.stack([p.extra["h_true0"]] + [np.zeros_like(p.b)] * 4))
+    obs = orc.gauge_record(g, p.extra["b_true"], qt, p.dt, p.nsteps, p.extra["every"], gauges)
+    loss, gb, gh = _gpu_loss_and_grad(p, obs, K=7)
+    q0 = orc.init_aux(g, p.b, p.q0)
+    loss_o = orc.gauge_loss(g, p.b, q0, p.dt, p.nsteps, p.extra["every"], gauges, obs)
+    assert abs(loss - loss_o) <= 1e-10 * abs(loss_o)
+    for d in p.extra["dirs"][:3]:
+        db, dh = d[0], d[1]
+        dq = np.zeros_like(p.q0)
+        dq[0] = dh
+        dq[4] = dh          # eta0 = h0
+        tlm = orc.gauge_loss_jvp(g, p.b, q0, db, dq, p.dt, p.nsteps, p.extra["every"], gauges, obs)
+        adj = float(np.sum(gb * db) + np.sum(gh * dh))
+        assert abs(adj - tlm) <= 1e-10 * abs(tlm), (adj, tlm)
+
+
+def test_rollout_gradient_matches_finite_differences():
+    """Inversion workload recipe at 128^2, 300 steps, gauges every 10 steps:
+    gradient vs central differences of the GPU loss, eps = 1e-6, 5 unit
+    directions over (b, h0)."""
+    p = _inversion_problem(128, 300, 10)
+    g = pins.grid_of(p)
+    qt = orc.init_aux(g, p.extra["b_true"], np.stack([p.extra["h_true0"]] + [np.zeros_like(p.b)] * 4))
+    obs = orc.gauge_record(g, p.extra["b_true"], qt, p.dt, p.nsteps, p.extra["every"], p.extra["gauges"])
+    loss, gb, gh = _gpu_loss_and_grad(p, obs, K=100)
+    eps = 1e-6
+    b0, h00 = p.b.copy(), p.q0[0].copy()
+    for d in p.extra["dirs"]:
+        p.b = b0 + eps * d[0]
+        p.q0[0] = h00 + eps * d[1]
+        lp, _, _ = _gpu_loss_and_grad(p, obs, K=100, need_grad=False)
+        p.b = b0 - eps * d[0]
+        p.q0[0] = h00 - eps * d[1]
+        lm, _, _ = _gpu_loss_and_grad(p, obs, K=100, need_grad=False)
+        fd = (lp - lm) / (2 * eps)
+        adj = float(np.sum(gb * d[0]) + np.sum(gh * d[1]))
+        assert abs(adj - fd) <= 1e-5 * abs(adj), (adj, fd)
+    p.b, p.q0[0] = b0, h00
