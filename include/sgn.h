@@ -177,6 +177,47 @@ SGN_API sgn_status sgn_step_record(sgn_ctx* ctx, void* q_dev, double dt, int nst
 SGN_API sgn_status sgn_step_vjp(sgn_ctx* ctx, const void* stash_dev, void* qbar_dev, void* bbar_dev,
                                 double dt, void* stream);
 
+/* ---- Ragged ensembles ----------------------------------------------------
+ * Many independent grids (each its own size, boundary treatment, parameters
+ * and fixed time step) advanced together: one launch per RK4 stage covers a
+ * tile list spanning every instance, and sgn_batch_step replays CUDA graphs of
+ * 25 steps.  The arithmetic per node is the single-grid kernel's, in the same
+ * order, so each instance evolves exactly as with sgn_step.
+ *
+ * Packed layout: instance i owns nx_i*ny_i nodes starting at node offset
+ * off_i = sum_{k<i} nx_k*ny_k.  Bathymetry: one plane per instance at off_i
+ * (double).  State: five planes per instance at 5*off_i (state type of prec),
+ * each plane nx_i*ny_i values, x fastest. */
+typedef struct {
+    int nx, ny;                    /* >= 3 */
+    double xmin, xmax, ymin, ymax;
+    int bc;                        /* sgn_bc */
+    double g, lambda;
+    double dt;                     /* this instance's fixed RK4 step, > 0 */
+} sgn_instance;
+
+typedef struct sgn_batch sgn_batch;
+
+/* Copy the instance table and the packed bathymetry, build the tile lists and
+ * allocate the RK registers.  Synchronizes. */
+SGN_API sgn_status sgn_batch_create(const sgn_instance* inst, int ninst, int prec, const void* b_dev,
+                                    sgn_batch** out);
+SGN_API sgn_status sgn_batch_destroy(sgn_batch* batch);
+/* total nodes of all instances (the packed plane length), or -1 */
+SGN_API long long sgn_batch_cells(const sgn_batch* batch);
+/* eq. (initialization) for every instance, in place on the packed state */
+SGN_API sgn_status sgn_batch_init_aux(sgn_batch* batch, void* q_dev, void* stream);
+/* nsteps RK4 steps of every instance (each with its own dt), in place */
+SGN_API sgn_status sgn_batch_step(sgn_batch* batch, void* q_dev, int nsteps, void* stream);
+/* per-instance diagnostics as sgn_mass_energy: out[4*i + k], host, 4*ninst
+ * doubles.  Synchronizes; reports a latched h <= 0 / non-finite flag. */
+SGN_API sgn_status sgn_batch_mass_energy(sgn_batch* batch, const void* q_dev, double* out, void* stream);
+/* Tile height 8*rows, rows in {1, 2, 4} (default 2). */
+SGN_API sgn_status sgn_batch_set_rows(sgn_batch* batch, int rows);
+/* Time 5 steps of each tile height on a copy of q_dev (allocated and freed
+ * here), keep the fastest and return it in *rows_out.  Synchronizes. */
+SGN_API sgn_status sgn_batch_autotune(sgn_batch* batch, const void* q_dev, int* rows_out, void* stream);
+
 /* Synchronize `stream` and report (and clear) the latched device flag. */
 SGN_API sgn_status sgn_check(sgn_ctx* ctx, void* stream);
 

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsgn.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["sgn_api.cu", "sgn_noalloc.cu"]
+SOURCES = ["sgn_api.cu", "sgn_noalloc.cu", "sgn_batch.cu"]
 
 
 def _sources() -> list[str]:

@@ -43,8 +43,10 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 }  // namespace
 
-// Message for sgn_last_error() from other translation units of the library.
+// Message for sgn_last_error() and the launch counter, for the other translation
+// units of the library.
 void sgn_record_error(const char* msg) { fail(SGN_E_INVAL, "%s", msg); }
+void sgn_count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 struct sgn_ctx {
     sgn_params p;

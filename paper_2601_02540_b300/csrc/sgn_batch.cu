@@ -1,0 +1,494 @@
+// sgn_batch.cu - ragged ensembles: many independent grids advanced by one
+// launch per RK4 stage (sgn_batch_* in include/sgn.h), replayed from CUDA
+// graphs, with the tile height chosen by timing (sgn_batch_autotune).
+#include "sgn.h"
+#include "sgn_batch.cuh"
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+void sgn_record_error(const char* msg);
+void sgn_count_launches(unsigned long long n);
+
+namespace {
+
+sgn_status bfail(sgn_status s, const char* msg) {
+    sgn_record_error(msg);
+    return s;
+}
+
+sgn_status bcuda(cudaError_t e, const char* what) {
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+    sgn_record_error(buf);
+    return SGN_E_CUDA;
+}
+
+constexpr int kGraphSteps = 25;   // RK4 steps captured per graph replay
+
+}  // namespace
+
+struct sgn_batch {
+    int ninst = 0;
+    int prec = SGN_F64;
+    int rows = 2;                      // rows per thread (tile height 8*rows)
+    long long cells = 0;
+    size_t tc = 8, ta = 8;
+    std::vector<sgn::InstDesc> hdesc;
+    sgn::InstDesc* desc = nullptr;     // device
+    int4* tiles[3] = {nullptr, nullptr, nullptr};   // tile lists for rows = 1, 2, 4
+    long long ntiles[3] = {0, 0, 0};
+    double* b64 = nullptr;
+    void* bT = nullptr;
+    void* acc = nullptr;
+    void* Qa = nullptr;
+    void* Qb = nullptr;
+    double* partials = nullptr;        // NDIAG per tile (largest tile list)
+    double* dout = nullptr;
+    int* flag = nullptr;
+    cudaStream_t cap = nullptr;        // private stream used only for graph capture
+    cudaGraphExec_t exec = nullptr;
+    const void* exec_q = nullptr;
+    int exec_rows = 0;
+    bool capturing = false;            // launches recorded into a graph are counted on replay
+};
+
+namespace {
+
+int rows_index(int rows) { return rows == 1 ? 0 : (rows == 2 ? 1 : 2); }
+
+template <typename TC, typename TIN, typename TA, int MODE, int ROWS>
+cudaError_t blaunch(const sgn_batch* B, const sgn::BatchArgs<TC, TIN, TA>& a, cudaStream_t s) {
+    const int ri = rows_index(ROWS);
+    const size_t smem = (size_t)sgn::N_OPS * (sgn::TILE_X + 2) * (sgn::THREADS_Y * ROWS + 2) * sizeof(TC);
+    sgn::BatchArgs<TC, TIN, TA> b = a;
+    b.tiles = B->tiles[ri];
+    sgn::k_batch_stage<TC, TIN, TA, MODE, ROWS>
+        <<<(unsigned)B->ntiles[ri], dim3(sgn::TILE_X, sgn::THREADS_Y), smem, s>>>(b);
+    if (!B->capturing) sgn_count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename TC, typename TIN, typename TA, int MODE, int ROWS>
+cudaError_t set_attr() {
+    const size_t smem = (size_t)sgn::N_OPS * (sgn::TILE_X + 2) * (sgn::THREADS_Y * ROWS + 2) * sizeof(TC);
+    return cudaFuncSetAttribute(sgn::k_batch_stage<TC, TIN, TA, MODE, ROWS>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <typename TC, typename TA, int ROWS>
+cudaError_t set_attrs_rows() {
+    cudaError_t e = set_attr<TC, TA, TA, sgn::MODE_S1, ROWS>();
+    if (e == cudaSuccess) e = set_attr<TC, TC, TA, sgn::MODE_S2, ROWS>();
+    if (e == cudaSuccess) e = set_attr<TC, TC, TA, sgn::MODE_S3, ROWS>();
+    if (e == cudaSuccess) e = set_attr<TC, TC, TA, sgn::MODE_S4, ROWS>();
+    if (e == cudaSuccess) e = set_attr<TC, TA, TA, sgn::MODE_DIAG, ROWS>();
+    return e;
+}
+
+template <typename TC, typename TA>
+cudaError_t set_attrs() {
+    cudaError_t e = set_attrs_rows<TC, TA, 1>();
+    if (e == cudaSuccess) e = set_attrs_rows<TC, TA, 2>();
+    if (e == cudaSuccess) e = set_attrs_rows<TC, TA, 4>();
+    return e;
+}
+
+// nsteps RK4 steps, four launches each (ping-pong stage states as sgn_step)
+template <typename TC, typename TA, int ROWS>
+cudaError_t bsteps(sgn_batch* B, TA* q, int nsteps, cudaStream_t s) {
+    sgn::BatchArgs<TC, TA, TA> a1;
+    std::memset(&a1, 0, sizeof(a1));
+    a1.desc = B->desc;
+    a1.b = static_cast<const TC*>(B->bT);
+    a1.flag = B->flag;
+    a1.X = q; a1.qn = q; a1.acc = static_cast<TA*>(B->acc); a1.Qout = static_cast<TC*>(B->Qa); a1.stage = 0;
+    sgn::BatchArgs<TC, TC, TA> a2;
+    std::memset(&a2, 0, sizeof(a2));
+    a2.desc = B->desc;
+    a2.b = a1.b;
+    a2.flag = B->flag;
+    a2.qn = q; a2.acc = a1.acc; a2.X = static_cast<TC*>(B->Qa); a2.Qout = static_cast<TC*>(B->Qb); a2.stage = 1;
+    sgn::BatchArgs<TC, TC, TA> a3 = a2;
+    a3.X = static_cast<TC*>(B->Qb); a3.Qout = static_cast<TC*>(B->Qa); a3.stage = 2;
+    sgn::BatchArgs<TC, TC, TA> a4 = a2;
+    a4.X = static_cast<TC*>(B->Qa); a4.Qout = nullptr; a4.qn = nullptr; a4.out = q; a4.stage = 3;
+    for (int n = 0; n < nsteps; n++) {
+        cudaError_t e;
+        if ((e = blaunch<TC, TA, TA, sgn::MODE_S1, ROWS>(B, a1, s)) != cudaSuccess) return e;
+        if ((e = blaunch<TC, TC, TA, sgn::MODE_S2, ROWS>(B, a2, s)) != cudaSuccess) return e;
+        if ((e = blaunch<TC, TC, TA, sgn::MODE_S3, ROWS>(B, a3, s)) != cudaSuccess) return e;
+        if ((e = blaunch<TC, TC, TA, sgn::MODE_S4, ROWS>(B, a4, s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename TC, typename TA>
+cudaError_t bsteps_rows(sgn_batch* B, void* q, int nsteps, int rows, cudaStream_t s) {
+    TA* qq = static_cast<TA*>(q);
+    if (rows == 1) return bsteps<TC, TA, 1>(B, qq, nsteps, s);
+    if (rows == 4) return bsteps<TC, TA, 4>(B, qq, nsteps, s);
+    return bsteps<TC, TA, 2>(B, qq, nsteps, s);
+}
+
+cudaError_t bsteps_any(sgn_batch* B, void* q, int nsteps, int rows, cudaStream_t s) {
+    switch (B->prec) {
+    case SGN_F64: return bsteps_rows<double, double>(B, q, nsteps, rows, s);
+    case SGN_F32: return bsteps_rows<float, float>(B, q, nsteps, rows, s);
+    default: return bsteps_rows<float, double>(B, q, nsteps, rows, s);
+    }
+}
+
+template <typename TC, typename TA, int ROWS>
+cudaError_t bdiag(sgn_batch* B, const TA* q, cudaStream_t s) {
+    sgn::BatchArgs<TC, TA, TA> a;
+    std::memset(&a, 0, sizeof(a));
+    a.desc = B->desc;
+    a.b = static_cast<const TC*>(B->bT);
+    a.flag = B->flag;
+    a.X = q;
+    a.partials = B->partials;
+    cudaError_t e = blaunch<TC, TA, TA, sgn::MODE_DIAG, ROWS>(B, a, s);
+    if (e != cudaSuccess) return e;
+    sgn::k_batch_reduce<<<B->ninst, 256, 0, s>>>(B->desc, B->partials, B->dout);
+    sgn_count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename TC, typename TA>
+cudaError_t bdiag_rows(sgn_batch* B, const void* q, cudaStream_t s) {
+    const TA* qq = static_cast<const TA*>(q);
+    if (B->rows == 1) return bdiag<TC, TA, 1>(B, qq, s);
+    if (B->rows == 4) return bdiag<TC, TA, 4>(B, qq, s);
+    return bdiag<TC, TA, 2>(B, qq, s);
+}
+
+void free_batch(sgn_batch* B) {
+    if (!B) return;
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->cap) cudaStreamDestroy(B->cap);
+    cudaFree(B->desc);
+    for (auto* t : B->tiles) cudaFree(t);
+    if (B->bT && B->bT != B->b64) cudaFree(B->bT);
+    cudaFree(B->b64);
+    cudaFree(B->acc);
+    cudaFree(B->Qa);
+    cudaFree(B->Qb);
+    cudaFree(B->partials);
+    cudaFree(B->dout);
+    cudaFree(B->flag);
+    delete B;
+}
+
+bool devptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// (re)build the graph of kGraphSteps RK4 steps for this state pointer and tiling
+sgn_status ensure_graph(sgn_batch* B, void* q) {
+    if (B->exec && B->exec_q == q && B->exec_rows == B->rows) return SGN_OK;
+    if (B->exec) {
+        cudaGraphExecDestroy(B->exec);
+        B->exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bcuda(e, "begin capture");
+    B->capturing = true;
+    cudaError_t el = bsteps_any(B, q, kGraphSteps, B->rows, B->cap);
+    B->capturing = false;
+    e = cudaStreamEndCapture(B->cap, &graph);
+    if (el != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return bcuda(el != cudaSuccess ? el : e, "capture");
+    }
+    e = cudaGraphInstantiate(&B->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        B->exec = nullptr;
+        return bcuda(e, "instantiate graph");
+    }
+    B->exec_q = q;
+    B->exec_rows = B->rows;
+    return SGN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sgn_status sgn_batch_create(const sgn_instance* inst, int ninst, int prec, const void* b_dev, sgn_batch** out) {
+    if (!out) return bfail(SGN_E_INVAL, "out is NULL");
+    *out = nullptr;
+    if (!inst || ninst <= 0) return bfail(SGN_E_INVAL, "need at least one instance");
+    if (prec != SGN_F64 && prec != SGN_F32 && prec != SGN_F32_F64ACC) return bfail(SGN_E_INVAL, "bad prec");
+    if (!devptr(b_dev)) return bfail(SGN_E_INVAL, "b_dev is not device memory");
+    sgn_batch* B = new (std::nothrow) sgn_batch();
+    if (!B) return bfail(SGN_E_NOMEM, "host allocation");
+    B->ninst = ninst;
+    B->prec = prec;
+    B->tc = prec == SGN_F64 ? 8 : 4;
+    B->ta = prec == SGN_F32 ? 4 : 8;
+    B->hdesc.resize(ninst);
+    std::vector<int4> tl[3];
+    long long off = 0;
+    for (int k = 0; k < ninst; k++) {
+        const sgn_instance& p = inst[k];
+        if (p.nx < 3 || p.ny < 3 || (p.bc != SGN_BC_PERIODIC && p.bc != SGN_BC_REFLECTING) ||
+            !(std::isfinite(p.xmin) && std::isfinite(p.xmax) && p.xmax > p.xmin && std::isfinite(p.ymin) &&
+              std::isfinite(p.ymax) && p.ymax > p.ymin) ||
+            !(std::isfinite(p.g) && p.g > 0) || !(std::isfinite(p.lambda) && p.lambda >= 0) ||
+            !(std::isfinite(p.dt) && p.dt > 0)) {
+            free_batch(B);
+            return bfail(SGN_E_INVAL, "invalid instance parameters");
+        }
+        sgn::InstDesc& d = B->hdesc[k];
+        std::memset(&d, 0, sizeof(d));
+        const bool per = p.bc == SGN_BC_PERIODIC;
+        const double dx = per ? (p.xmax - p.xmin) / p.nx : (p.xmax - p.xmin) / (p.nx - 1);
+        const double dy = per ? (p.ymax - p.ymin) / p.ny : (p.ymax - p.ymin) / (p.ny - 1);
+        sgn::Geom& G = d.G;
+        G.nx = p.nx;
+        G.ny = p.ny;
+        G.plane = (long long)p.nx * p.ny;
+        G.cx2 = 1.0 / (2.0 * dx);
+        G.cy2 = 1.0 / (2.0 * dy);
+        G.cx1 = 1.0 / dx;
+        G.cy1 = 1.0 / dy;
+        G.satx = 2.0 / dx;
+        G.saty = 2.0 / dy;
+        G.dx = dx;
+        G.dy = dy;
+        G.g = p.g;
+        G.lam = p.lambda;
+        G.lam2 = p.lambda / 2.0;
+        G.lam3 = p.lambda / 3.0;
+        G.lam6 = p.lambda / 6.0;
+        d.bc = p.bc;
+        d.off = off;
+        // same coefficients, computed the same way, as sgn_step
+        d.c_acc[0] = p.dt / 6.0; d.c_q[0] = p.dt / 2.0;
+        d.c_acc[1] = p.dt / 3.0; d.c_q[1] = p.dt / 2.0;
+        d.c_acc[2] = p.dt / 3.0; d.c_q[2] = p.dt;
+        d.c_acc[3] = p.dt / 6.0; d.c_q[3] = 0.0;
+        off += G.plane;
+    }
+    B->cells = off;
+    // tile lists for the three tile heights; the descriptor keeps the rows = 2
+    // list's range, the others are stored per list below
+    for (int ri = 0; ri < 3; ri++) {
+        const int th = sgn::THREADS_Y * (ri == 0 ? 1 : (ri == 1 ? 2 : 4));
+        for (int k = 0; k < ninst; k++) {
+            const sgn::Geom& G = B->hdesc[k].G;
+            for (int j0 = 0; j0 < G.ny; j0 += th)
+                for (int i0 = 0; i0 < G.nx; i0 += sgn::TILE_X) tl[ri].push_back(make_int4(k, i0, j0, 0));
+        }
+        B->ntiles[ri] = (long long)tl[ri].size();
+    }
+    if (B->ntiles[0] > 2147483647LL) {
+        free_batch(B);
+        return bfail(SGN_E_INVAL, "too many tiles");
+    }
+    const size_t n = (size_t)B->cells;
+    bool ok = cudaMalloc(&B->desc, sizeof(sgn::InstDesc) * ninst) == cudaSuccess;
+    for (int ri = 0; ri < 3 && ok; ri++) ok = cudaMalloc(&B->tiles[ri], sizeof(int4) * tl[ri].size()) == cudaSuccess;
+    ok = ok && cudaMalloc(&B->b64, n * sizeof(double)) == cudaSuccess;
+    if (ok && prec != SGN_F64) ok = cudaMalloc(&B->bT, n * sizeof(float)) == cudaSuccess;
+    if (ok && prec == SGN_F64) B->bT = B->b64;
+    ok = ok && cudaMalloc(&B->acc, 5 * n * B->ta) == cudaSuccess;
+    ok = ok && cudaMalloc(&B->Qa, 5 * n * B->tc) == cudaSuccess;
+    ok = ok && cudaMalloc(&B->Qb, 5 * n * B->tc) == cudaSuccess;
+    ok = ok && cudaMalloc(&B->partials, (size_t)B->ntiles[0] * sgn::NDIAG * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc(&B->dout, (size_t)ninst * sgn::NDIAG * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc(&B->flag, sizeof(int)) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_batch(B);
+        return bfail(SGN_E_NOMEM, "batch scratch");
+    }
+    // per-list tile ranges are recomputed on the device side only for diagnostics,
+    // which use the rows-specific list: store the ranges of list `rows` on use
+    cudaError_t e = cudaSuccess;
+    for (int ri = 0; ri < 3 && e == cudaSuccess; ri++)
+        e = cudaMemcpy(B->tiles[ri], tl[ri].data(), sizeof(int4) * tl[ri].size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(B->flag, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(B->b64, b_dev, n * sizeof(double), cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess && prec != SGN_F64) {
+        sgn::k_convert<float><<<592, 256>>>(B->b64, static_cast<float*>(B->bT), (long long)n);
+        sgn_count_launches(1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        switch (prec) {
+        case SGN_F64: e = set_attrs<double, double>(); break;
+        case SGN_F32: e = set_attrs<float, float>(); break;
+        default: e = set_attrs<float, double>(); break;
+        }
+    }
+    if (e == cudaSuccess) {
+        // descriptors with the tile ranges of the default list (rows = 2)
+        std::vector<long long> first(ninst, -1), count(ninst, 0);
+        for (size_t k = 0; k < tl[1].size(); k++) {
+            const int i = tl[1][k].x;
+            if (first[i] < 0) first[i] = (long long)k;
+            count[i]++;
+        }
+        for (int i = 0; i < ninst; i++) {
+            B->hdesc[i].tile0 = first[i];
+            B->hdesc[i].ntiles = (int)count[i];
+        }
+        e = cudaMemcpy(B->desc, B->hdesc.data(), sizeof(sgn::InstDesc) * ninst, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        sgn_status st = bcuda(e, "sgn_batch_create");
+        free_batch(B);
+        return st;
+    }
+    *out = B;
+    return SGN_OK;
+}
+
+sgn_status sgn_batch_destroy(sgn_batch* B) {
+    if (!B) return SGN_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    free_batch(B);
+    return e == cudaSuccess ? SGN_OK : bcuda(e, "sgn_batch_destroy");
+}
+
+long long sgn_batch_cells(const sgn_batch* B) { return B ? B->cells : -1; }
+
+sgn_status sgn_batch_set_rows(sgn_batch* B, int rows) {
+    if (!B) return bfail(SGN_E_INVAL, "batch is NULL");
+    if (rows != 1 && rows != 2 && rows != 4) return bfail(SGN_E_INVAL, "rows must be 1, 2 or 4");
+    B->rows = rows;
+    return SGN_OK;
+}
+
+sgn_status sgn_batch_step(sgn_batch* B, void* q_dev, int nsteps, void* stream) {
+    if (!B) return bfail(SGN_E_INVAL, "batch is NULL");
+    if (!devptr(q_dev) || reinterpret_cast<uintptr_t>(q_dev) % 16 != 0)
+        return bfail(SGN_E_INVAL, "q_dev must be 16-byte aligned device memory");
+    if (nsteps < 0) return bfail(SGN_E_INVAL, "nsteps must be >= 0");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int left = nsteps;
+    if (left >= kGraphSteps) {
+        sgn_status st = ensure_graph(B, q_dev);
+        if (st != SGN_OK) return st;
+        while (left >= kGraphSteps) {
+            cudaError_t e = cudaGraphLaunch(B->exec, s);
+            if (e != cudaSuccess) return bcuda(e, "graph launch");
+            sgn_count_launches(4ull * kGraphSteps);
+            left -= kGraphSteps;
+        }
+    }
+    if (left > 0) {
+        cudaError_t e = bsteps_any(B, q_dev, left, B->rows, s);
+        if (e != cudaSuccess) return bcuda(e, "sgn_batch_step");
+    }
+    return SGN_OK;
+}
+
+sgn_status sgn_batch_mass_energy(sgn_batch* B, const void* q_dev, double* out, void* stream) {
+    if (!B || !out) return bfail(SGN_E_INVAL, "batch and out must not be NULL");
+    if (!devptr(q_dev)) return bfail(SGN_E_INVAL, "q_dev is not device memory");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the per-instance tile ranges in the descriptors refer to the rows = 2 list
+    const int saved = B->rows;
+    B->rows = 2;
+    cudaError_t e;
+    switch (B->prec) {
+    case SGN_F64: e = bdiag_rows<double, double>(B, q_dev, s); break;
+    case SGN_F32: e = bdiag_rows<float, float>(B, q_dev, s); break;
+    default: e = bdiag_rows<float, double>(B, q_dev, s); break;
+    }
+    B->rows = saved;
+    if (e != cudaSuccess) return bcuda(e, "sgn_batch_mass_energy");
+    int flag = 0;
+    e = cudaMemcpyAsync(out, B->dout, (size_t)B->ninst * sgn::NDIAG * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, B->flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return bcuda(e, "sgn_batch_mass_energy");
+    if (flag) {
+        cudaMemset(B->flag, 0, sizeof(int));
+        if (flag & sgn::FLAG_NONFINITE) return bfail(SGN_E_NONFINITE, "a stage input had a non-finite water height");
+        return bfail(SGN_E_NONPOSITIVE_H, "a stage input had a non-positive water height");
+    }
+    return SGN_OK;
+}
+
+sgn_status sgn_batch_autotune(sgn_batch* B, const void* q_dev, int* rows_out, void* stream) {
+    if (!B) return bfail(SGN_E_INVAL, "batch is NULL");
+    if (!devptr(q_dev)) return bfail(SGN_E_INVAL, "q_dev is not device memory");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = 5 * (size_t)B->cells * B->ta;
+    void* work = nullptr;
+    if (cudaMalloc(&work, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(SGN_E_NOMEM, "autotune work copy");
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int cand[3] = {1, 2, 4};
+    float best = 1e30f;
+    int best_rows = B->rows;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 3 && e == cudaSuccess; k++) {
+        e = cudaMemcpyAsync(work, q_dev, bytes, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = bsteps_any(B, work, 2, cand[k], s);   // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = bsteps_any(B, work, 5, cand[k], s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best) {
+            best = ms;
+            best_rows = cand[k];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(work);
+    if (e != cudaSuccess) return bcuda(e, "sgn_batch_autotune");
+    B->rows = best_rows;
+    if (rows_out) *rows_out = best_rows;
+    return SGN_OK;
+}
+
+sgn_status sgn_batch_init_aux(sgn_batch* B, void* q_dev, void* stream) {
+    if (!B) return bfail(SGN_E_INVAL, "batch is NULL");
+    if (!devptr(q_dev)) return bfail(SGN_E_INVAL, "q_dev is not device memory");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int k = 0; k < B->ninst; k++) {
+        const sgn::InstDesc& d = B->hdesc[k];
+        const dim3 blk(32, 8), grd((d.G.nx + 31) / 32, (d.G.ny + 7) / 8);
+        if (B->prec == SGN_F32) {
+            float* q = static_cast<float*>(q_dev) + 5 * d.off;
+            if (d.bc == SGN_BC_REFLECTING) sgn::k_init_aux<float, sgn::BC_REFLECTING><<<grd, blk, 0, s>>>(q, B->b64 + d.off, d.G);
+            else sgn::k_init_aux<float, sgn::BC_PERIODIC><<<grd, blk, 0, s>>>(q, B->b64 + d.off, d.G);
+        } else {
+            double* q = static_cast<double*>(q_dev) + 5 * d.off;
+            if (d.bc == SGN_BC_REFLECTING) sgn::k_init_aux<double, sgn::BC_REFLECTING><<<grd, blk, 0, s>>>(q, B->b64 + d.off, d.G);
+            else sgn::k_init_aux<double, sgn::BC_PERIODIC><<<grd, blk, 0, s>>>(q, B->b64 + d.off, d.G);
+        }
+        sgn_count_launches(1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return bcuda(e, "sgn_batch_init_aux");
+    }
+    return SGN_OK;
+}
+
+}  // extern "C"

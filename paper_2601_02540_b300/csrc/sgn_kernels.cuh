@@ -91,10 +91,11 @@ __device__ __forceinline__ int halo_index(int k, int n) {
 // Right-hand side at the node held in shared-memory slot t, global (gi, gj).
 // Terms are grouped by the difference they multiply; every term of eq.
 // (sd_periodic_2D_SGN) / (semi_2D) appears exactly once.
-template <typename TC, int BC>
+// HX/HN: row stride and plane size of the shared-memory halo tile.
+template <typename TC, int BC, int HX = HALO_X, int HN = HALO_N>
 __device__ __forceinline__ void node_rhs(const TC* __restrict__ sm, int t, int gi, int gj,
                                          const Geom& G, TC k[5]) {
-    int tl = t - 1, tr = t + 1, tb = t - HALO_X, tt = t + HALO_X;
+    int tl = t - 1, tr = t + 1, tb = t - HX, tt = t + HX;
     TC sx = (TC)G.cx2, sy = (TC)G.cy2;
     if (BC == BC_REFLECTING) {
         // one-sided first/last rows of the reflecting operator: (f1 - f0)/dx
@@ -103,7 +104,7 @@ __device__ __forceinline__ void node_rhs(const TC* __restrict__ sm, int t, int g
         if (gj == 0) { tb = t; sy = (TC)G.cy1; }
         if (gj == G.ny - 1) { tt = t; sy = (TC)G.cy1; }
     }
-#define SM_(op, idx) sm[(op) * HALO_N + (idx)]
+#define SM_(op, idx) sm[(op) * HN + (idx)]
 #define DXU(op) (SM_(op, tr) - SM_(op, tl))
 #define DYU(op) (SM_(op, tt) - SM_(op, tb))
     const TC h = SM_(OP_H, t), u = SM_(OP_U, t), v = SM_(OP_V, t);

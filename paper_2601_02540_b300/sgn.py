@@ -39,6 +39,14 @@ _SIGNATURES = {
     "sgn_rhs_vjp": (ctypes.c_int, [_V, _V, _V, _V, _V, _V]),
     "sgn_step_record": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_int, _V, _V]),
     "sgn_step_vjp": (ctypes.c_int, [_V, _V, _V, _V, ctypes.c_double, _V]),
+    "sgn_batch_create": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int, _V, _V]),
+    "sgn_batch_destroy": (ctypes.c_int, [_V]),
+    "sgn_batch_cells": (ctypes.c_longlong, [_V]),
+    "sgn_batch_init_aux": (ctypes.c_int, [_V, _V, _V]),
+    "sgn_batch_step": (ctypes.c_int, [_V, _V, ctypes.c_int, _V]),
+    "sgn_batch_mass_energy": (ctypes.c_int, [_V, _V, _V, _V]),
+    "sgn_batch_set_rows": (ctypes.c_int, [_V, ctypes.c_int]),
+    "sgn_batch_autotune": (ctypes.c_int, [_V, _V, _V, _V]),
     "sgn_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "sgn_last_error": (ctypes.c_char_p, []),
     "sgn_launch_count": (ctypes.c_ulonglong, []),
@@ -57,6 +65,14 @@ class Params(ctypes.Structure):
                 ("ymin", ctypes.c_double), ("ymax", ctypes.c_double),
                 ("bc", ctypes.c_int), ("g", ctypes.c_double), ("lam", ctypes.c_double),
                 ("prec", ctypes.c_int)]
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("xmin", ctypes.c_double), ("xmax", ctypes.c_double),
+                ("ymin", ctypes.c_double), ("ymax", ctypes.c_double),
+                ("bc", ctypes.c_int), ("g", ctypes.c_double), ("lam", ctypes.c_double),
+                ("dt", ctypes.c_double)]
 
 
 _lib_handle = None
@@ -237,6 +253,82 @@ class Solver:
         if self.ctx is not None and self.ctx.value:
             sgn_destroy(self.ctx)
         self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------------- ensembles
+def sgn_batch_create(insts, prec: int, b_packed: torch.Tensor) -> ctypes.c_void_p:
+    arr = (Instance * len(insts))(*insts)
+    h = ctypes.c_void_p()
+    _ok(lib().sgn_batch_create(arr, len(insts), prec, _dptr(b_packed, torch.float64, "b"), ctypes.byref(h)),
+        "sgn_batch_create")
+    return h
+
+
+class BatchSolver:
+    """A ragged ensemble packed into one state buffer (see include/sgn.h)."""
+
+    def __init__(self, problems, prec: str = "f32", device: str = "cuda"):
+        self.prec = prec
+        self.state_dtype = torch.float32 if prec == "f32" else torch.float64
+        self.problems = problems
+        self.sizes = [p.nx * p.ny for p in problems]
+        self.offsets = [0]
+        for n in self.sizes:
+            self.offsets.append(self.offsets[-1] + n)
+        insts = [Instance(p.nx, p.ny, p.xmin, p.xmax, p.ymin, p.ymax, p.bc, p.g, p.lam, p.dt) for p in problems]
+        b = torch.cat([torch.as_tensor(p.b, dtype=torch.float64).reshape(-1) for p in problems]).to(device)
+        self.handle = None
+        self.handle = sgn_batch_create(insts, PREC[prec], b.contiguous())
+        self.cells = int(lib().sgn_batch_cells(self.handle))
+        self.device = device
+
+    def pack(self, states) -> torch.Tensor:
+        parts = [torch.as_tensor(q, dtype=self.state_dtype).reshape(-1) for q in states]
+        return torch.cat(parts).to(self.device).contiguous()
+
+    def unpack(self, q: torch.Tensor):
+        out = []
+        for k, p in enumerate(self.problems):
+            o = 5 * self.offsets[k]
+            out.append(q[o:o + 5 * self.sizes[k]].view(5, p.ny, p.nx))
+        return out
+
+    def init_aux(self, q):
+        _ok(lib().sgn_batch_init_aux(self.handle, _dptr(q, self.state_dtype, "q"), _stream(None)),
+            "sgn_batch_init_aux")
+        return q
+
+    def step(self, q, nsteps: int):
+        _ok(lib().sgn_batch_step(self.handle, _dptr(q, self.state_dtype, "q"), int(nsteps), _stream(None)),
+            "sgn_batch_step")
+        return q
+
+    def mass_energy(self, q):
+        out = (ctypes.c_double * (4 * len(self.problems)))()
+        _ok(lib().sgn_batch_mass_energy(self.handle, _dptr(q, self.state_dtype, "q"), out, _stream(None)),
+            "sgn_batch_mass_energy")
+        import numpy as np
+        return np.array(out[:]).reshape(len(self.problems), 4)
+
+    def set_rows(self, rows: int):
+        _ok(lib().sgn_batch_set_rows(self.handle, int(rows)), "sgn_batch_set_rows")
+
+    def autotune(self, q) -> int:
+        r = ctypes.c_int()
+        _ok(lib().sgn_batch_autotune(self.handle, _dptr(q, self.state_dtype, "q"), ctypes.byref(r),
+                                     _stream(None)), "sgn_batch_autotune")
+        return r.value
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            lib().sgn_batch_destroy(self.handle)
+        self.handle = None
 
     def __del__(self):
         try:

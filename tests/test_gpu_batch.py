@@ -1,0 +1,105 @@
+"""Ragged ensembles: one launch per RK4 stage over every instance must evolve
+each instance exactly as the single-grid path does (same per-node arithmetic),
+and match the oracle."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from oracle import PERIODIC, REFLECTING
+from paper_2601_02540_b300 import inputs, sgn
+import gpu_util as gu
+import pins
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(33, 17, PERIODIC), (40, 23, REFLECTING), (64, 48, PERIODIC), (5, 3, REFLECTING),
+          (100, 37, REFLECTING), (128, 128, PERIODIC), (3, 3, PERIODIC)]
+
+
+def _ensemble():
+    probs = []
+    for k, (nx, ny, bc) in enumerate(SHAPES):
+        p = inputs.smooth_state(nx, ny, bc, seed=20 + k, xmax=1.0 + 0.1 * k, ymax=0.8 + 0.05 * k,
+                                lam=300.0 + 50 * k)
+        probs.append(p)
+    return probs
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32_f64acc"])
+def test_batch_equals_single_grid_bitwise(prec):
+    probs = _ensemble()
+    bs = sgn.BatchSolver(probs, prec=prec)
+    q = bs.pack([p.q0 for p in probs])
+    bs.step(q, 30)          # one 25-step graph replay + 5 direct steps
+    got = bs.unpack(q)
+    for p, g in zip(probs, got):
+        s = sgn.Solver.from_problem(p, prec=prec)
+        qs = s.state(p.q0)
+        s.step(qs, p.dt, 30)
+        assert torch.equal(qs, g), p.name
+        s.close()
+    bs.close()
+
+
+def test_batch_tile_heights_agree_and_autotune():
+    probs = _ensemble()
+    bs = sgn.BatchSolver(probs, prec="f64")
+    ref = None
+    for rows in (1, 2, 4):
+        bs.set_rows(rows)
+        q = bs.pack([p.q0 for p in probs])
+        bs.step(q, 27)
+        if ref is None:
+            ref = q.clone()
+        assert torch.equal(q, ref), rows
+    q = bs.pack([p.q0 for p in probs])
+    assert bs.autotune(q) in (1, 2, 4)
+    assert torch.equal(q, bs.pack([p.q0 for p in probs]))   # autotune works on a copy
+    bs.close()
+
+
+def test_batch_matches_oracle_and_diagnostics():
+    probs = _ensemble()
+    bs = sgn.BatchSolver(probs, prec="f64")
+    q = bs.pack([p.q0 for p in probs])
+    bs.init_aux(q)
+    diag = bs.mass_energy(q)
+    for k, (p, g) in enumerate(zip(probs, bs.unpack(q))):
+        grid = pins.grid_of(p)
+        q0 = orc.init_aux(grid, p.b, p.q0)
+        assert np.array_equal(g.cpu().numpy()[4], q0[4])
+        d = orc.diagnostics(grid, p.b, q0)
+        assert abs(diag[k, 0] - d["mass"]) <= 1e-13 * abs(d["mass"])
+        assert abs(diag[k, 1] - d["energy"]) <= 1e-13 * abs(d["energy"])
+        assert abs(diag[k, 3]) <= 1e-13 * d["dEdt_scale"]
+    bs.step(q, 20)
+    for p, g in zip(probs, bs.unpack(q)):
+        grid = pins.grid_of(p)
+        ref = orc.rk4(grid, p.b, orc.init_aux(grid, p.b, p.q0), p.dt, 20)
+        e = gu.state_errors(g.cpu().numpy(), ref)
+        assert np.all(e <= gu.STEP_TOL), (p.name, e)
+    bs.close()
+
+
+def test_batch_workload_recipe_small():
+    """The ensemble recipe (sizes, half periodic / half reflecting) at 8
+    instances: per-instance diagnostics equal the single-grid diagnostics."""
+    probs = inputs.workload5(ninst=8, nsteps=10, sizes=(128, 192))
+    bs = sgn.BatchSolver(probs, prec="f32")
+    q = bs.pack([p.q0 for p in probs])
+    bs.init_aux(q)
+    bs.step(q, 10)
+    diag = bs.mass_energy(q)
+    for k, p in enumerate(probs):
+        s = sgn.Solver.from_problem(p, prec="f32")
+        qs = s.state(p.q0)
+        s.init_aux(qs)
+        s.step(qs, p.dt, 10)
+        assert torch.equal(qs, bs.unpack(q)[k])
+        d = s.mass_energy(qs)
+        assert diag[k, 0] == d["mass"] and diag[k, 1] == d["energy"]
+        s.close()
+    bs.close()
