@@ -278,6 +278,8 @@ def run_ours(args) -> None:
             dist.destroy_process_group()
         return
     cpu = _cpu_baseline(p) if world == 1 and not args.no_cpu else None
+    ens = None if args.no_extra else _ensemble(torch, 50, 5)
+    adj = None if args.no_extra else _adjoint(torch)
     head = results["f64"]
     line = {
         "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
@@ -297,6 +299,8 @@ def run_ours(args) -> None:
         "variants": {DTYPE_NAME[k]: {"value": v["value"], "ms_per_step": v["ms_per_step"],
                                      "roofline": v["roofline"]} for k, v in results.items()
                      if k != "f64"},
+        "ensemble": ens,
+        "adjoint": adj,
         "energy_drift": drift,
         "errors_vs_f64_after_job": errors,
         "kernel_hash": _kernel_hash(),
@@ -304,6 +308,84 @@ def run_ours(args) -> None:
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _ensemble(torch, steps: int, warmup: int) -> dict:
+    """Ragged ensemble (256 instances, N in {128,...,512}, half periodic, half
+    reflecting, FP32 state, each with its own dt): the batched path (one
+    launch per stage over all instances, graph replays, autotuned tile height)
+    against a per-instance launch loop, both timed with CUDA events."""
+    from paper_2601_02540_b300 import sgn
+    probs = inputs.workload5()
+    cells = sum(p.nx * p.ny for p in probs)
+    bs = sgn.BatchSolver(probs, prec="f32")
+    q = bs.pack([p.q0 for p in probs])
+    bs.init_aux(q)
+    rows = bs.autotune(q)
+    bs.step(q, warmup)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    bs.step(q, steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1)
+    d = bs.mass_energy(q)
+    bs.close()
+    solvers = [sgn.Solver.from_problem(p, prec="f32") for p in probs]
+    states = [s.init_aux(s.state(p.q0)) for s, p in zip(solvers, probs)]
+    for s, st, p in zip(solvers, states, probs):
+        s.step(st, p.dt, warmup)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        for s, st, p in zip(solvers, states, probs):
+            s.step(st, p.dt, 1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_loop = e0.elapsed_time(e1)
+    for s in solvers:
+        s.close()
+    rate_b = 4.0 * cells * steps / (ms_batch * 1e-3)
+    rate_l = 4.0 * cells * steps / (ms_loop * 1e-3)
+    return {"workload": "256 instances N~U{128,192,256,384,512}, half periodic/half reflecting, FP32",
+            "cells": cells, "steps": steps, "value": rate_b, "unit": UNIT,
+            "per_instance_loop": rate_l, "speedup_vs_loop": rate_b / rate_l, "rows": rows,
+            "hbm_gbs": BYTES_PER_CELL_STAGE["f32"] * rate_b / 1e9,
+            "mass_finite": bool(np.all(np.isfinite(d)))}
+
+
+def _adjoint(torch) -> dict:
+    """Inversion workload: 512^2 reflecting, 2000 RK4 steps, 16 gauges read
+    every 10 steps, checkpoints every 100 steps; time of the forward rollout
+    (with checkpoints) and of the backward pass (segment recomputation with
+    stage stashes + adjoint steps)."""
+    from paper_2601_02540_b300 import adjoint, sgn
+    p = inputs.workload4()
+    s = sgn.Solver.from_problem(p, prec="f64")
+    gauges = torch.as_tensor(p.extra["gauges"], device="cuda")
+    b = torch.as_tensor(p.b, device="cuda").requires_grad_(True)
+    h0 = torch.as_tensor(p.q0[0], device="cuda").requires_grad_(True)
+    obs = torch.zeros((p.nsteps // p.extra["every"], gauges.numel()), dtype=torch.float64, device="cuda")
+    # warm-up with the same operations (loads every kernel module once)
+    out = adjoint.gauge_rollout(b, h0, s, p.dt, 20, p.extra["every"], gauges, 10)
+    torch.sum((out - obs[: out.shape[0]]) ** 2).backward()
+    b.grad = None
+    h0.grad = None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = adjoint.gauge_rollout(b, h0, s, p.dt, p.nsteps, p.extra["every"], gauges, 100)
+    loss = torch.sum((out - obs) ** 2)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    loss.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    s.close()
+    fwd, bwd = t1 - t0, t2 - t1
+    return {"workload": "reflecting 512x512, 2000 RK4 steps, 16 gauges every 10 steps, K = 100, FP64",
+            "forward_s": fwd, "backward_s": bwd, "backward_over_forward": bwd / fwd,
+            "total_over_forward": (fwd + bwd) / fwd}
 
 
 def _e2e(torch, s, p, q_init_dev, steps: int) -> dict:
@@ -366,6 +448,7 @@ def main() -> None:
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-drift", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-extra", action="store_true", help="skip the ensemble and adjoint legs")
     ap.add_argument("--size", type=int, default=8192,
                     help="grid side (8192 = the workload; smaller sizes only for profiling)")
     args = ap.parse_args()
