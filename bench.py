@@ -372,20 +372,26 @@ def _adjoint(torch) -> dict:
     torch.sum((out - obs[: out.shape[0]]) ** 2).backward()
     b.grad = None
     h0.grad = None
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    out = adjoint.gauge_rollout(b, h0, s, p.dt, p.nsteps, p.extra["every"], gauges, 100)
-    loss = torch.sum((out - obs) ** 2)
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    loss.backward()
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
+    res = {"workload": "reflecting 512x512, 2000 RK4 steps, 16 gauges every 10 steps, FP64"}
+    for name, K in (("checkpoint_K100", 100), ("all_stages_kept", 0)):
+        b.grad = None
+        h0.grad = None
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = adjoint.gauge_rollout(b, h0, s, p.dt, p.nsteps, p.extra["every"], gauges, K)
+        loss = torch.sum((out - obs) ** 2)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        loss.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        fwd, bwd = t1 - t0, t2 - t1
+        res[name] = {"forward_s": fwd, "backward_s": bwd, "backward_over_forward": bwd / fwd,
+                     "stash_gb": (min(K, p.nsteps) if K > 0 else p.nsteps) * 20 * p.nx * p.ny * 8 / 1e9}
+        del out, loss
+        torch.cuda.empty_cache()
     s.close()
-    fwd, bwd = t1 - t0, t2 - t1
-    return {"workload": "reflecting 512x512, 2000 RK4 steps, 16 gauges every 10 steps, K = 100, FP64",
-            "forward_s": fwd, "backward_s": bwd, "backward_over_forward": bwd / fwd,
-            "total_over_forward": (fwd + bwd) / fwd}
+    return res
 
 
 def _e2e(torch, s, p, q_init_dev, steps: int) -> dict:

@@ -153,7 +153,8 @@ SGN_API sgn_status sgn_mass_energy_noalloc(const sgn_params* p, const void* b_de
  *   qbar_dev  = J(q)^T abar            (overwritten, five planes)
  *   bbar_dev += (d RHS / d b)^T abar   (accumulated, one plane)
  * All double, device; qbar_dev must not overlap q_dev or abar_dev.  SGN_F64
- * contexts only (else SGN_E_UNSUPPORTED).  Asynchronous. */
+ * contexts only (else SGN_E_UNSUPPORTED).  The first adjoint call of a context
+ * allocates 55 planes of scratch (SGN_E_NOMEM if that fails).  Asynchronous. */
 SGN_API sgn_status sgn_rhs_vjp(sgn_ctx* ctx, const void* q_dev, const void* abar_dev, void* qbar_dev,
                                void* bbar_dev, void* stream);
 
@@ -171,9 +172,9 @@ SGN_API sgn_status sgn_step_record(sgn_ctx* ctx, void* q_dev, double dt, int nst
  * k3bar = dt/3 qbar' + dt Q4bar, Q3bar = J(Q3)^T k3bar, k2bar = dt/3 qbar' +
  * dt/2 Q3bar, Q2bar = J(Q2)^T k2bar, k1bar = dt/6 qbar' + dt/2 Q2bar,
  * Q1bar = J(q_n)^T k1bar, qbar = qbar' + Q1bar + Q2bar + Q3bar + Q4bar, and
- * bbar_dev += sum_s (d RHS / d b)(Q_s)^T ks_bar.  Four fused adjoint launches.
- * The first call allocates 15 planes of context scratch (SGN_E_NOMEM if that
- * fails).  SGN_F64 only.  Asynchronous. */
+ * bbar_dev += sum_s (d RHS / d b)(Q_s)^T ks_bar.  Eight launches (two per
+ * stage).  The first adjoint call of a context allocates 55 planes of scratch
+ * (SGN_E_NOMEM if that fails).  SGN_F64 only.  Asynchronous. */
 SGN_API sgn_status sgn_step_vjp(sgn_ctx* ctx, const void* stash_dev, void* qbar_dev, void* bbar_dev,
                                 double dt, void* stream);
 

@@ -7,12 +7,15 @@ state is at rest (u = v = 0), so the initialization of the auxiliary variables
 gives eta0 = h0 and w0 = 0 (eq. (initialization)); the gradient with respect
 to h0 is therefore qbar_h + qbar_eta of the initial state.
 
-Forward: ``sgn_step`` with a copy of the state kept every K steps (checkpoint).
-Backward: for each segment, last to first, recompute it from its checkpoint
-with ``sgn_step_record`` (which keeps the four stage states of every step of
-the segment), then walk its steps backwards with ``sgn_step_vjp``, adding the
-gauge cotangents to qbar_h at the observation steps.  Memory: the K-step
-stash, 20 planes per step (4.2 GB at 512^2 for K = 100).
+Forward (K > 0): ``sgn_step`` with a copy of the state kept every K steps
+(checkpoint).  Backward: for each segment, last to first, recompute it from its
+checkpoint with ``sgn_step_record`` (which keeps the four stage states of
+every step of the segment), then walk its steps backwards with
+``sgn_step_vjp``, adding the gauge cotangents to qbar_h at the observation
+steps.  Memory: the K-step stash, 20 planes per step (4.2 GB at 512^2 for
+K = 100).  K <= 0 keeps the stage states of every step during the forward pass
+instead (no recomputation; 84 GB at 512^2 for 2000 steps, which fits in a
+B300's HBM).
 
 The gauge sampling, the seed injection and the checkpoint copies are small
 torch tensor operations; every RHS, stage and adjoint evaluation runs in the
@@ -39,18 +42,28 @@ class GaugeRollout(torch.autograd.Function):
         nobs = nsteps // every
         obs = torch.empty((nobs, gauges.numel()), dtype=torch.float64, device=h0.device)
         checkpoints = {}
+        stash = None
+        if K <= 0:
+            # keep every step's stage states (no recomputation in the backward pass)
+            stash = torch.empty((nsteps, 20, ny, nx), dtype=torch.float64, device=h0.device)
         step = 0
         while step < nsteps:
-            if step % K == 0:
+            if K > 0 and step % K == 0:
                 checkpoints[step] = q.clone()
-            nxt = min(nsteps, (step // every + 1) * every, (step // K + 1) * K)
-            solver.step(q, dt, nxt - step)
+            nxt = min(nsteps, (step // every + 1) * every)
+            if K > 0:
+                nxt = min(nxt, (step // K + 1) * K)
+                solver.step(q, dt, nxt - step)
+            else:
+                solver.step_record(q, dt, nxt - step, stash[step:nxt])
             step = nxt
             if step % every == 0:
                 obs[step // every - 1] = q[0].reshape(-1)[gauges]
         ctx.solver, ctx.dt, ctx.nsteps, ctx.every, ctx.K = solver, dt, nsteps, every, K
         ctx.gauges = gauges
         ctx.checkpoints = checkpoints
+        ctx.stash = stash
+        ctx.shape = (ny, nx)
         ctx.b = b
         return obs
 
@@ -59,24 +72,32 @@ class GaugeRollout(torch.autograd.Function):
         solver, dt, nsteps, every, K = ctx.solver, ctx.dt, ctx.nsteps, ctx.every, ctx.K
         gauges = ctx.gauges
         solver.set_bathymetry(ctx.b)
-        q0 = ctx.checkpoints[0]
-        _, ny, nx = q0.shape
-        qbar = torch.zeros_like(q0)
-        bbar = torch.zeros((ny, nx), dtype=torch.float64, device=q0.device)
+        ny, nx = ctx.shape
+        dev = grad_obs.device
+        qbar = torch.zeros((5, ny, nx), dtype=torch.float64, device=dev)
+        bbar = torch.zeros((ny, nx), dtype=torch.float64, device=dev)
         grad_obs = grad_obs.to(torch.float64).contiguous()
-        starts = sorted(ctx.checkpoints)
-        stash = None
-        for s0 in reversed(starts):
-            L = min(K, nsteps - s0)
-            if stash is None or stash.shape[0] < L:
-                stash = torch.empty((L, 20, ny, nx), dtype=torch.float64, device=q0.device)
-            q = ctx.checkpoints[s0].clone()
-            solver.step_record(q, dt, L, stash)
+        if K > 0:
+            segments = [(s0, min(K, nsteps - s0)) for s0 in sorted(ctx.checkpoints)]
+        else:
+            segments = [(0, nsteps)]
+        stash = ctx.stash
+        for s0, L in reversed(segments):
+            if K > 0:
+                # recompute the segment from its checkpoint, keeping its stage states
+                if stash is None or stash.shape[0] < L:
+                    stash = torch.empty((L, 20, ny, nx), dtype=torch.float64, device=dev)
+                q = ctx.checkpoints[s0].clone()
+                solver.step_record(q, dt, L, stash)
+                base = 0
+            else:
+                base = s0
             for n in reversed(range(L)):
                 g = s0 + n + 1                      # this step produces q_g
                 if g % every == 0:
                     qbar[0].reshape(-1).index_add_(0, gauges, grad_obs[g // every - 1])
-                solver.step_vjp(stash[n], qbar, bbar, dt)
+                solver.step_vjp(stash[base + n], qbar, bbar, dt)
+        ctx.stash = None
         h0bar = qbar[0] + qbar[4]
         return bbar, h0bar, None, None, None, None, None, None
 

@@ -9,33 +9,31 @@
 //   - "pointwise" part: d k_f / d q_c with every D P_t held fixed (needs the
 //     differences at c);
 //   - "product" part: P̄_t(n) = sum_c D_{c,n} V_t(c) with
-//     V_t(c) = sum_f a_f(c) coef_{f,t}(c), a gather over the rows c of the SBP
-//     operator that touch column n (periodic: V(n-1) - V(n+1); reflecting: the
-//     one-sided end rows add their own node), followed by the chain rule
-//     through P_t(q_n, b_n).
-// The gather form writes each output node once: no atomics.
-//
-// One 32x8 tile per 256-thread block (one node per thread), halo 1.  Shared
-// memory: products and 1/h (16 planes), the cotangent (5) and one set of 12
-// direction weights V (x first, then reused for y): 33 planes of 34x10 doubles.
+//     V_t(c) = sum_f a_f(c) coef_{f,t}(c) (the row factor of D included), a
+//     gather over the rows c of the SBP operator that touch column n
+//     (periodic: V(n-1) - V(n+1); reflecting: V(n-1) for n >= 1, -V(n+1) for
+//     n <= N-2, and the one-sided end rows add +V(N-1) at n = N-1 and -V(0) at
+//     n = 0), then the chain rule through P_t(q_n, b_n).
+// Two passes, both one node per thread and free of halos and atomics:
+//   k_adj_weights  products P_t, 1/h and the 24 direction weights of each node
+//                  into scratch planes;
+//   k_adj_gather   differences, pointwise part, gathers of the weights of the
+//                  neighbours, chain rule, and (stage mode) the reverse RK4
+//                  stage algebra.
 #pragma once
 
 #include "sgn_kernels.cuh"
 
 namespace sgn {
 
-constexpr int ADJ_TX = 32;
-constexpr int ADJ_TY = 8;
-constexpr int ADJ_HX = ADJ_TX + 2;
-constexpr int ADJ_HY = ADJ_TY + 2;
-constexpr int ADJ_HN = ADJ_HX * ADJ_HY;
-constexpr int ADJ_THREADS = ADJ_TX * ADJ_TY;
-constexpr int ADJ_A = N_OPS;            // first cotangent plane
-constexpr int ADJ_V = N_OPS + 5;        // first direction-weight plane
-constexpr int ADJ_PLANES = N_OPS + 5 + 12;
+// scratch layout (planes): products and 1/h (N_OPS), x weights (12), y weights (12)
+constexpr int ADJ_WX = N_OPS;
+constexpr int ADJ_WY = N_OPS + 12;
+constexpr int ADJ_SCRATCH_PLANES = N_OPS + 24;
+constexpr int ADJ_BLOCK = 256;
 
-// direction-weight slots: x uses {H,U,V,W,ETA,B,HS,UU,HU,HUV,HUW,E2H},
-// y uses {H,U,V,W,ETA,B,HS,VV,HV,HUV,HVW,E2H}; slot 7..10 differ
+// weight slots: x uses {H,U,V,W,ETA,B,HS,UU,HU,HUV,HUW,E2H},
+// y uses {H,U,V,W,ETA,B,HS,VV,HV,HUV,HVW,E2H}
 enum { VW_H, VW_U, VW_V, VW_W, VW_ETA, VW_B, VW_HS, VW_SQ, VW_HM, VW_HUV, VW_HMW, VW_E2H };
 
 enum { ADJ_MODE_RHS = 0, ADJ_MODE_STAGE = 1 };
@@ -45,6 +43,7 @@ struct AdjArgs {
     const double* b;       // bathymetry
     const double* A;       // cotangent (5 planes), used as a_scale * A
     double a_scale;
+    double* scratch;       // ADJ_SCRATCH_PLANES planes
     double* qbar;          // RHS mode: output J^T a (5 planes)
     double* bbar;          // accumulated (1 plane)
     // stage mode: Qbar = J^T a;  qacc_out = (first ? qprime : qacc_in) + Qbar;
@@ -58,176 +57,162 @@ struct AdjArgs {
     Geom G;
 };
 
-// Direction weights V_t(c) (see the header comment) at the node in slot t of the
-// halo tile, for the x (DIR = 0) or y (DIR = 1) differences, scaled by the row
-// factor s (1/(2 dx) inside, 1/dx on a reflecting end row).
-template <int DIR>
-__device__ __forceinline__ void dir_weights(const double* __restrict__ sm, int t, double s,
-                                            const Geom& G, double* __restrict__ out) {
-    const double h = sm[OP_H * ADJ_HN + t], u = sm[OP_U * ADJ_HN + t], v = sm[OP_V * ADJ_HN + t];
-    const double w = sm[OP_W * ADJ_HN + t], eta = sm[OP_ETA * ADJ_HN + t], bb = sm[OP_B * ADJ_HN + t];
-    const double r = sm[OP_R * ADJ_HN + t];
-    const double ah = sm[(ADJ_A + 0) * ADJ_HN + t], au = sm[(ADJ_A + 1) * ADJ_HN + t];
-    const double av = sm[(ADJ_A + 2) * ADJ_HN + t], aw = sm[(ADJ_A + 3) * ADJ_HN + t];
-    const double ae = sm[(ADJ_A + 4) * ADJ_HN + t];
-    const double rho = eta * r, om = 1.0 - rho, sfs = h + bb;
-    const double ru = -r * au, rv = -r * av, rw = -0.5 * r * aw;   // d k / d B for u, v, w
-    const double hu = h * u, hv = h * v, hw = h * w;
-    if (DIR == 0) {
-        const double C1 = G.lam6 * rho * rho - G.g * sfs - 0.5 * u * u;
-        out[VW_H] = s * (-u * ah + ru * C1 - 0.5 * rv * u * v - rw * u * w);
-        out[VW_U] = s * (-h * ah - 0.5 * ru * hu - 0.5 * rv * hv - rw * hw);
-        out[VW_V] = s * (0.5 * rv * hu);
-        out[VW_W] = s * (rw * hu);
-        out[VW_ETA] = s * (ru * G.lam3 * om - u * ae);
-        out[VW_B] = s * (ru * G.lam2 * om - 1.5 * u * ae);
-        out[VW_HS] = s * (ru * G.g);
-        out[VW_SQ] = s * (0.5 * ru * h);    // u^2
-        out[VW_HM] = s * (0.5 * ru * u);    // hu
-        out[VW_HUV] = s * (0.5 * rv);
-        out[VW_HMW] = s * rw;               // huw
-        out[VW_E2H] = s * (-G.lam6 * ru);
-    } else {
-        const double C2 = G.lam6 * rho * rho - G.g * sfs - 0.5 * v * v;
-        out[VW_H] = s * (-v * ah + rv * C2 - 0.5 * ru * u * v - rw * v * w);
-        out[VW_V] = s * (-h * ah - 0.5 * rv * hv - 0.5 * ru * hu - rw * hw);
-        out[VW_U] = s * (0.5 * ru * hv);
-        out[VW_W] = s * (rw * hv);
-        out[VW_ETA] = s * (rv * G.lam3 * om - v * ae);
-        out[VW_B] = s * (rv * G.lam2 * om - 1.5 * v * ae);
-        out[VW_HS] = s * (rv * G.g);
-        out[VW_SQ] = s * (0.5 * rv * h);    // v^2
-        out[VW_HM] = s * (0.5 * rv * v);    // hv
-        out[VW_HUV] = s * (0.5 * ru);
-        out[VW_HMW] = s * rw;               // hvw
-        out[VW_E2H] = s * (-G.lam6 * rv);
-    }
-}
-
 template <int BC>
 __device__ __forceinline__ double row_scale(int k, int n, double c2, double c1) {
     if (BC == BC_REFLECTING && (k == 0 || k == n - 1)) return c1;
     return c2;
 }
 
-template <int BC, int MODE>
-__global__ void __launch_bounds__(ADJ_THREADS)
-k_adjoint(AdjArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* sm = reinterpret_cast<double*>(smem_raw);
+// Pass 1: products, 1/h and the direction weights V^x, V^y of one node.
+template <int BC>
+__global__ void __launch_bounds__(ADJ_BLOCK) k_adj_weights(AdjArgs a) {
     const Geom& G = a.G;
-    const int i0 = blockIdx.x * ADJ_TX, j0 = blockIdx.y * ADJ_TY;
     const long long P = G.plane;
-    const int tid = threadIdx.y * ADJ_TX + threadIdx.x;
+    const long long c = (long long)blockIdx.x * ADJ_BLOCK + threadIdx.x;
+    if (c >= P) return;
+    const int j = (int)(c / G.nx), i = (int)(c - (long long)j * G.nx);
+    const double h = a.X[c], u = a.X[P + c], v = a.X[2 * P + c], w = a.X[3 * P + c];
+    const double eta = a.X[4 * P + c], bb = a.b[c];
+    const double r = recip<double>(h);
+    const double hu = h * u, hv = h * v, hw = h * w;
+    double* S = a.scratch;
+    S[OP_H * P + c] = h;
+    S[OP_U * P + c] = u;
+    S[OP_V * P + c] = v;
+    S[OP_W * P + c] = w;
+    S[OP_ETA * P + c] = eta;
+    S[OP_B * P + c] = bb;
+    S[OP_HS * P + c] = h * (h + bb);
+    S[OP_UU * P + c] = u * u;
+    S[OP_VV * P + c] = v * v;
+    S[OP_HU * P + c] = hu;
+    S[OP_HV * P + c] = hv;
+    S[OP_HUV * P + c] = hu * v;
+    S[OP_HUW * P + c] = hu * w;
+    S[OP_HVW * P + c] = hv * w;
+    S[OP_E2H * P + c] = eta * eta * r;
+    S[OP_R * P + c] = r;
 
-    // ---- phase 1: state, products, 1/h and the cotangent on the halo tile
-    for (int t = tid; t < ADJ_HN; t += ADJ_THREADS) {
-        const int li = t % ADJ_HX, lj = t / ADJ_HX;
-        const int gi = halo_index<BC>(i0 - 1 + li, G.nx);
-        const int gj = halo_index<BC>(j0 - 1 + lj, G.ny);
-        const long long c = (long long)gj * G.nx + gi;
-        const double h = a.X[c], u = a.X[P + c], v = a.X[2 * P + c], w = a.X[3 * P + c];
-        const double eta = a.X[4 * P + c], bb = a.b[c];
-        const double r = 1.0 / h, hu = h * u, hv = h * v;
-        sm[OP_H * ADJ_HN + t] = h;
-        sm[OP_U * ADJ_HN + t] = u;
-        sm[OP_V * ADJ_HN + t] = v;
-        sm[OP_W * ADJ_HN + t] = w;
-        sm[OP_ETA * ADJ_HN + t] = eta;
-        sm[OP_B * ADJ_HN + t] = bb;
-        sm[OP_HS * ADJ_HN + t] = h * (h + bb);
-        sm[OP_UU * ADJ_HN + t] = u * u;
-        sm[OP_VV * ADJ_HN + t] = v * v;
-        sm[OP_HU * ADJ_HN + t] = hu;
-        sm[OP_HV * ADJ_HN + t] = hv;
-        sm[OP_HUV * ADJ_HN + t] = hu * v;
-        sm[OP_HUW * ADJ_HN + t] = hu * w;
-        sm[OP_HVW * ADJ_HN + t] = hv * w;
-        sm[OP_E2H * ADJ_HN + t] = eta * eta * r;
-        sm[OP_R * ADJ_HN + t] = r;
-#pragma unroll
-        for (int f = 0; f < 5; f++) sm[(ADJ_A + f) * ADJ_HN + t] = a.a_scale * a.A[f * P + c];
+    const double s = a.a_scale;
+    const double ah = s * a.A[c], au = s * a.A[P + c], av = s * a.A[2 * P + c];
+    const double aw = s * a.A[3 * P + c], ae = s * a.A[4 * P + c];
+    const double rho = eta * r, om = 1.0 - rho;
+    const double cc = G.lam6 * rho * rho - G.g * (h + bb);   // common part of C1, C2
+    const double ra = -r * au, rb = -r * av, rc = -0.5 * r * aw;  // d k / d B for u, v, w
+    // x weights (row factor of column i)
+    {
+        const double sx = row_scale<BC>(i, G.nx, G.cx2, G.cx1);
+        const double ru = sx * ra, rv = sx * rb, rw = sx * rc, sah = sx * ah, sae = sx * ae;
+        double* W = S + ADJ_WX * P + c;
+        W[VW_H * P] = -u * sah + ru * (cc - 0.5 * u * u) - 0.5 * rv * (u * v) - rw * (u * w);
+        W[VW_U * P] = -h * sah - 0.5 * ru * hu - 0.5 * rv * hv - rw * hw;
+        W[VW_V * P] = 0.5 * rv * hu;
+        W[VW_W * P] = rw * hu;
+        W[VW_ETA * P] = ru * G.lam3 * om - u * sae;
+        W[VW_B * P] = ru * G.lam2 * om - 1.5 * u * sae;
+        W[VW_HS * P] = ru * G.g;
+        W[VW_SQ * P] = 0.5 * ru * h;      // u^2
+        W[VW_HM * P] = 0.5 * ru * u;      // hu
+        W[VW_HUV * P] = 0.5 * rv;
+        W[VW_HMW * P] = rw;               // huw
+        W[VW_E2H * P] = -G.lam6 * ru;
     }
-    __syncthreads();
+    // y weights (row factor of row j)
+    {
+        const double sy = row_scale<BC>(j, G.ny, G.cy2, G.cy1);
+        const double ru = sy * ra, rv = sy * rb, rw = sy * rc, sah = sy * ah, sae = sy * ae;
+        double* W = S + ADJ_WY * P + c;
+        W[VW_H * P] = -v * sah + rv * (cc - 0.5 * v * v) - 0.5 * ru * (u * v) - rw * (v * w);
+        W[VW_V * P] = -h * sah - 0.5 * rv * hv - 0.5 * ru * hu - rw * hw;
+        W[VW_U * P] = 0.5 * ru * hv;
+        W[VW_W * P] = rw * hv;
+        W[VW_ETA * P] = rv * G.lam3 * om - v * sae;
+        W[VW_B * P] = rv * G.lam2 * om - 1.5 * v * sae;
+        W[VW_HS * P] = rv * G.g;
+        W[VW_SQ * P] = 0.5 * rv * h;      // v^2
+        W[VW_HM * P] = 0.5 * rv * v;      // hv
+        W[VW_HUV * P] = 0.5 * ru;
+        W[VW_HMW * P] = rw;               // hvw
+        W[VW_E2H * P] = -G.lam6 * rv;
+    }
+}
 
-    const int li = threadIdx.x + 1, lj = threadIdx.y + 1;
-    const int gi = i0 + threadIdx.x, gj = j0 + threadIdx.y;
-    const int t = lj * ADJ_HX + li;
-    const bool active = gi < G.nx && gj < G.ny;
-    // P̄ over the 15 product slots: h u v w eta b hs uu vv hu hv huv huw hvw e2h
+// Pass 2: everything else at one node.
+template <int BC, int MODE>
+__global__ void __launch_bounds__(ADJ_BLOCK, 2) k_adj_gather(AdjArgs a) {
+    const Geom& G = a.G;
+    const long long P = G.plane;
+    const long long c = (long long)blockIdx.x * ADJ_BLOCK + threadIdx.x;
+    if (c >= P) return;
+    const int j = (int)(c / G.nx), i = (int)(c - (long long)j * G.nx);
+    const double* __restrict__ S = a.scratch;
+
+    // neighbours: left/right/below/above (periodic wrap; clamped at walls)
+    const long long row = (long long)j * G.nx;
+    long long cl, cr, cb, ct;
+    if (BC == BC_PERIODIC) {
+        cl = row + (i == 0 ? G.nx - 1 : i - 1);
+        cr = row + (i == G.nx - 1 ? 0 : i + 1);
+        cb = (long long)(j == 0 ? G.ny - 1 : j - 1) * G.nx + i;
+        ct = (long long)(j == G.ny - 1 ? 0 : j + 1) * G.nx + i;
+    } else {
+        cl = i > 0 ? c - 1 : c;
+        cr = i < G.nx - 1 ? c + 1 : c;
+        cb = j > 0 ? c - G.nx : c;
+        ct = j < G.ny - 1 ? c + G.nx : c;
+    }
+
+    // ---- product part: gathers of the neighbours' weights
     double pb[N_OPS - 1];
 #pragma unroll
     for (int k = 0; k < N_OPS - 1; k++) pb[k] = 0.0;
-
-    // ---- phases 2-3: x weights on the halo tile, then the x gather
-    for (int tt = tid; tt < ADJ_HN; tt += ADJ_THREADS) {
-        const int gx = halo_index<BC>(i0 - 1 + tt % ADJ_HX, G.nx);
-        double vw[12];
-        dir_weights<0>(sm, tt, row_scale<BC>(gx, G.nx, G.cx2, G.cx1), G, vw);
-#pragma unroll
-        for (int k = 0; k < 12; k++) sm[(ADJ_V + k) * ADJ_HN + tt] = vw[k];
-    }
-    __syncthreads();
-    if (active) {
-        // P̄(n) = V(n-1) - V(n+1) (periodic); reflecting: V(n-1) if n >= 1,
-        // -V(n+1) if n <= N-2, +V(n) on the last row, -V(n) on the first row.
-        const bool has_l = BC == BC_PERIODIC || gi >= 1;
-        const bool has_r = BC == BC_PERIODIC || gi <= G.nx - 2;
-        const double self = (BC == BC_REFLECTING) ? ((gi == G.nx - 1 ? 1.0 : 0.0) - (gi == 0 ? 1.0 : 0.0)) : 0.0;
+    {
+        const bool has_l = BC == BC_PERIODIC || i >= 1;
+        const bool has_r = BC == BC_PERIODIC || i <= G.nx - 2;
+        const double self = (BC == BC_REFLECTING) ? ((i == G.nx - 1 ? 1.0 : 0.0) - (i == 0 ? 1.0 : 0.0)) : 0.0;
         const int slot_of[12] = {OP_H, OP_U, OP_V, OP_W, OP_ETA, OP_B, OP_HS, OP_UU, OP_HU, OP_HUV, OP_HUW, OP_E2H};
 #pragma unroll
         for (int k = 0; k < 12; k++) {
-            const double* V = sm + (ADJ_V + k) * ADJ_HN;
-            double g = self * V[t];
-            if (has_l) g += V[t - 1];
-            if (has_r) g -= V[t + 1];
+            const double* V = S + (ADJ_WX + k) * P;
+            double g = 0.0;
+            if (BC == BC_REFLECTING && self != 0.0) g = self * V[c];
+            if (has_l) g += V[cl];
+            if (has_r) g -= V[cr];
             pb[slot_of[k]] += g;
         }
     }
-    __syncthreads();
-
-    // ---- phases 4-5: y weights, then the y gather
-    for (int tt = tid; tt < ADJ_HN; tt += ADJ_THREADS) {
-        const int gy = halo_index<BC>(j0 - 1 + tt / ADJ_HX, G.ny);
-        double vw[12];
-        dir_weights<1>(sm, tt, row_scale<BC>(gy, G.ny, G.cy2, G.cy1), G, vw);
-#pragma unroll
-        for (int k = 0; k < 12; k++) sm[(ADJ_V + k) * ADJ_HN + tt] = vw[k];
-    }
-    __syncthreads();
-    if (!active) return;
     {
-        const bool has_b = BC == BC_PERIODIC || gj >= 1;
-        const bool has_t = BC == BC_PERIODIC || gj <= G.ny - 2;
-        const double self = (BC == BC_REFLECTING) ? ((gj == G.ny - 1 ? 1.0 : 0.0) - (gj == 0 ? 1.0 : 0.0)) : 0.0;
+        const bool has_b = BC == BC_PERIODIC || j >= 1;
+        const bool has_t = BC == BC_PERIODIC || j <= G.ny - 2;
+        const double self = (BC == BC_REFLECTING) ? ((j == G.ny - 1 ? 1.0 : 0.0) - (j == 0 ? 1.0 : 0.0)) : 0.0;
         const int slot_of[12] = {OP_H, OP_U, OP_V, OP_W, OP_ETA, OP_B, OP_HS, OP_VV, OP_HV, OP_HUV, OP_HVW, OP_E2H};
 #pragma unroll
         for (int k = 0; k < 12; k++) {
-            const double* V = sm + (ADJ_V + k) * ADJ_HN;
-            double g = self * V[t];
-            if (has_b) g += V[t - ADJ_HX];
-            if (has_t) g -= V[t + ADJ_HX];
+            const double* V = S + (ADJ_WY + k) * P;
+            double g = 0.0;
+            if (BC == BC_REFLECTING && self != 0.0) g = self * V[c];
+            if (has_b) g += V[cb];
+            if (has_t) g -= V[ct];
             pb[slot_of[k]] += g;
         }
     }
 
     // ---- pointwise part: d k / d q at this node with every difference fixed
-    int tl = t - 1, tr = t + 1, tb = t - ADJ_HX, tu = t + ADJ_HX;
     double sx = G.cx2, sy = G.cy2, sgx = 0.0, sgy = 0.0;
     if (BC == BC_REFLECTING) {
-        if (gi == 0) { tl = t; sx = G.cx1; sgx = -G.satx; }
-        if (gi == G.nx - 1) { tr = t; sx = G.cx1; sgx = G.satx; }
-        if (gj == 0) { tb = t; sy = G.cy1; sgy = -G.saty; }
-        if (gj == G.ny - 1) { tu = t; sy = G.cy1; sgy = G.saty; }
+        if (i == 0) { sx = G.cx1; sgx = -G.satx; }
+        if (i == G.nx - 1) { sx = G.cx1; sgx = G.satx; }
+        if (j == 0) { sy = G.cy1; sgy = -G.saty; }
+        if (j == G.ny - 1) { sy = G.cy1; sgy = G.saty; }
     }
-#define DX_(op) (sx * (sm[(op) * ADJ_HN + tr] - sm[(op) * ADJ_HN + tl]))
-#define DY_(op) (sy * (sm[(op) * ADJ_HN + tu] - sm[(op) * ADJ_HN + tb]))
-    const double h = sm[OP_H * ADJ_HN + t], u = sm[OP_U * ADJ_HN + t], v = sm[OP_V * ADJ_HN + t];
-    const double w = sm[OP_W * ADJ_HN + t], eta = sm[OP_ETA * ADJ_HN + t], bb = sm[OP_B * ADJ_HN + t];
-    const double r = sm[OP_R * ADJ_HN + t];
-    const double ah = sm[(ADJ_A + 0) * ADJ_HN + t], au = sm[(ADJ_A + 1) * ADJ_HN + t];
-    const double av = sm[(ADJ_A + 2) * ADJ_HN + t], aw = sm[(ADJ_A + 3) * ADJ_HN + t];
-    const double ae = sm[(ADJ_A + 4) * ADJ_HN + t];
+#define DX_(op) (sx * (S[(op) * P + cr] - S[(op) * P + cl]))
+#define DY_(op) (sy * (S[(op) * P + ct] - S[(op) * P + cb]))
+    const double h = S[OP_H * P + c], u = S[OP_U * P + c], v = S[OP_V * P + c];
+    const double w = S[OP_W * P + c], eta = S[OP_ETA * P + c], bb = S[OP_B * P + c];
+    const double r = S[OP_R * P + c];
+    const double sc = a.a_scale;
+    const double ah = sc * a.A[c], au = sc * a.A[P + c], av = sc * a.A[2 * P + c];
+    const double aw = sc * a.A[3 * P + c], ae = sc * a.A[4 * P + c];
     const double rho = eta * r, om = 1.0 - rho, sfs = h + bb;
     const double hu = h * u, hv = h * v, hw = h * w, uv = u * v, uw = u * w, vw_ = v * w;
     const double xh = DX_(OP_H), xu = DX_(OP_U), xv = DX_(OP_V), xw = DX_(OP_W), xe = DX_(OP_ETA), xb = DX_(OP_B);
@@ -249,7 +234,7 @@ k_adjoint(AdjArgs a) {
     const double Bw = G.lam * om - 0.5 * (xhuw + hu * xw - uw * xh - hw * xu
                                           + yhvw + hv * yw - vw_ * yh - hw * yv);
     const double ku = -r * Bu, kv = -r * Bv, kw = r * Bw;
-    const double lr = G.lam3 * rho * r;   // d/dh and d/deta helpers
+    const double lr = G.lam3 * rho * r;
     const double dBu_dh = xh * (-G.lam3 * rho * rho * r - G.g) + xe * lr + xb * G.lam2 * rho * r
                         + 0.5 * xuu - 0.5 * u * xu + 0.5 * (v * yu - u * yv);
     const double dBv_dh = yh * (-G.lam3 * rho * rho * r - G.g) + ye * lr + yb * G.lam2 * rho * r
@@ -277,7 +262,6 @@ k_adjoint(AdjArgs a) {
     eb += pb[OP_ETA] + 2.0 * rho * pb[OP_E2H];
     bbar += pb[OP_B] + h * pb[OP_HS];
 
-    const long long c = (long long)gj * G.nx + gi;
     const double qb[5] = {hb, ub, vb, wb, eb};
     a.bbar[c] += bbar;
     if (MODE == ADJ_MODE_RHS) {

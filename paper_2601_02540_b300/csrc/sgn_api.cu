@@ -233,16 +233,12 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 template <int BC, int MODE>
 cudaError_t launch_adjoint(const sgn_ctx* c, const sgn::AdjArgs& a, cudaStream_t s) {
-    auto kern = sgn::k_adjoint<BC, MODE>;
-    const size_t smem = (size_t)sgn::ADJ_PLANES * sgn::ADJ_HN * sizeof(double);
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [&] {
-        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    });
-    if (attr_err != cudaSuccess) return attr_err;
-    const dim3 grid((c->p.nx + sgn::ADJ_TX - 1) / sgn::ADJ_TX, (c->p.ny + sgn::ADJ_TY - 1) / sgn::ADJ_TY);
-    kern<<<grid, dim3(sgn::ADJ_TX, sgn::ADJ_TY), smem, s>>>(a);
+    const unsigned blocks = (unsigned)((c->G.plane + sgn::ADJ_BLOCK - 1) / sgn::ADJ_BLOCK);
+    sgn::k_adj_weights<BC><<<blocks, sgn::ADJ_BLOCK, 0, s>>>(a);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sgn::k_adj_gather<BC, MODE><<<blocks, sgn::ADJ_BLOCK, 0, s>>>(a);
     count_launch();
     return cudaGetLastError();
 }
@@ -251,6 +247,19 @@ template <int MODE>
 cudaError_t adjoint(const sgn_ctx* c, const sgn::AdjArgs& a, cudaStream_t s) {
     return c->p.bc == SGN_BC_REFLECTING ? launch_adjoint<sgn::BC_REFLECTING, MODE>(c, a, s)
                                         : launch_adjoint<sgn::BC_PERIODIC, MODE>(c, a, s);
+}
+
+// Adjoint scratch, allocated on first use: RK accumulator and two cotangents
+// (15 planes), then the products and direction weights (ADJ_SCRATCH_PLANES).
+sgn_status adjoint_scratch(sgn_ctx* c) {
+    if (c->adj) return SGN_OK;
+    const size_t bytes = (size_t)(15 + sgn::ADJ_SCRATCH_PLANES) * (size_t)c->G.plane * sizeof(double);
+    if (cudaMalloc(&c->adj, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        c->adj = nullptr;
+        return fail(SGN_E_NOMEM, "adjoint scratch (%zu bytes)", bytes);
+    }
+    return SGN_OK;
 }
 
 // One RK4 step that also records its stage states: stash = [q_n | Q2 | Q3 | Q4].
@@ -476,8 +485,11 @@ sgn_status sgn_rhs_vjp(sgn_ctx* c, const void* q_dev, const void* abar_dev, void
     if (st == SGN_OK) st = check_state_ptr(bbar_dev, "bbar_dev");
     if (st != SGN_OK) return st;
     if (qbar_dev == q_dev || qbar_dev == abar_dev) return fail(SGN_E_INVAL, "qbar_dev must not overlap the inputs");
+    st = adjoint_scratch(c);
+    if (st != SGN_OK) return st;
     sgn::AdjArgs a;
     std::memset(&a, 0, sizeof(a));
+    a.scratch = c->adj + 15 * c->G.plane;
     a.X = static_cast<const double*>(q_dev);
     a.b = c->b64;
     a.A = static_cast<const double*>(abar_dev);
@@ -521,13 +533,8 @@ sgn_status sgn_step_vjp(sgn_ctx* c, const void* stash_dev, void* qbar_dev, void*
     if (st != SGN_OK) return st;
     if (!finite_pos(dt)) return fail(SGN_E_INVAL, "dt must be finite and > 0");
     const long long P5 = 5 * c->G.plane;
-    if (!c->adj) {
-        if (cudaMalloc(&c->adj, 3 * P5 * sizeof(double)) != cudaSuccess) {
-            cudaGetLastError();
-            c->adj = nullptr;
-            return fail(SGN_E_NOMEM, "adjoint scratch (%lld bytes)", (long long)(3 * P5 * sizeof(double)));
-        }
-    }
+    st = adjoint_scratch(c);
+    if (st != SGN_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const double* stash = static_cast<const double*>(stash_dev);
     double* qbar = static_cast<double*>(qbar_dev);
@@ -537,6 +544,7 @@ sgn_status sgn_step_vjp(sgn_ctx* c, const void* stash_dev, void* qbar_dev, void*
     sgn::AdjArgs a;
     std::memset(&a, 0, sizeof(a));
     a.b = c->b64;
+    a.scratch = c->adj + 15 * c->G.plane;
     a.bbar = static_cast<double*>(bbar_dev);
     a.qprime = qbar;
     a.G = c->G;

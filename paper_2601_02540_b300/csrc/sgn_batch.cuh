@@ -65,7 +65,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs<TC, TIN, TA>& a, cons
         const TC bb = bp[c];
         if (!(h > TC(0))) bad |= (h <= TC(0)) ? FLAG_NONPOSITIVE : FLAG_NONFINITE;
         else if (!(h < pos_inf<TC>())) bad |= FLAG_NONFINITE;
-        const TC r = TC(1) / h;
+        const TC r = recip<TC>(h);
         const TC hu = h * u, hv = h * v;
         sm[OP_H * HN + t] = h;
         sm[OP_U * HN + t] = u;

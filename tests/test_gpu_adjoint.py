@@ -152,6 +152,8 @@ def test_rollout_gradient_matches_oracle_tlm():
     qt = orc.init_aux(g, p.extra["b_true"], np.stack([p.extra["h_true0"]] + [np.zeros_like(p.b)] * 4))
     obs = orc.gauge_record(g, p.extra["b_true"], qt, p.dt, p.nsteps, p.extra["every"], gauges)
     loss, gb, gh = _gpu_loss_and_grad(p, obs, K=7)
+    _, gb_all, gh_all = _gpu_loss_and_grad(p, obs, K=0)   # every stage kept, no recomputation
+    assert np.array_equal(gb, gb_all) and np.array_equal(gh, gh_all)
     q0 = orc.init_aux(g, p.b, p.q0)
     loss_o = orc.gauge_loss(g, p.b, q0, p.dt, p.nsteps, p.extra["every"], gauges, obs)
     assert abs(loss - loss_o) <= 1e-10 * abs(loss_o)
