@@ -195,19 +195,69 @@ k_stage(StageArgs<TC, TIN, TA> a) {
     const long long P = G.plane;
     const int tid = threadIdx.y * TILE_X + threadIdx.x;
 
+    // Memory-bound (float) variants issue every global load of the block early
+    // so that more bytes are in flight: the stage operands of this thread's
+    // output nodes first, then all halo-tile inputs of its share of the tile.
+    // (the stage operands only when they are float: 20 doubles of early loads
+    // cost the mixed-precision variant more occupancy than they gain)
+    constexpr bool kEarly = sizeof(TC) == 4;
+    constexpr bool kEarlyStage = kEarly && sizeof(TA) == 4;
+    constexpr int NPER = (HALO_N + BLOCK_THREADS - 1) / BLOCK_THREADS;
+    const int gi = i0 + threadIdx.x;
+    TA pq[ROWS_PER_THREAD][5], pa[ROWS_PER_THREAD][5];
+    if (kEarlyStage && (MODE == MODE_S1 || MODE == MODE_S2 || MODE == MODE_S3 || MODE == MODE_S4)) {
+#pragma unroll
+        for (int ry = 0; ry < ROWS_PER_THREAD; ry++) {
+            const int gj = j0 + threadIdx.y + ry * THREADS_Y;
+            if (gi >= G.nx || gj >= G.ny) continue;
+            const long long c = (long long)gj * G.nx + gi;
+#pragma unroll
+            for (int f = 0; f < 5; f++) {
+                if (MODE != MODE_S4) pq[ry][f] = a.qn[f * P + c];
+                if (MODE != MODE_S1) pa[ry][f] = a.acc[f * P + c];
+            }
+        }
+    }
+
     // ---- phase 1: halo tile of the inputs and of every differentiated product
     int bad = 0;
-    for (int t = tid; t < HALO_N; t += BLOCK_THREADS) {
-        const int li = t % HALO_X, lj = t / HALO_X;
-        const int gi = halo_index<BC>(i0 - 1 + li, G.nx);
-        const int gj = halo_index<BC>(j0 - 1 + lj, G.ny);
-        const long long c = (long long)gj * G.nx + gi;
-        const TC h = (TC)a.X[c];
-        const TC u = (TC)a.X[P + c];
-        const TC v = (TC)a.X[2 * P + c];
-        const TC w = (TC)a.X[3 * P + c];
-        const TC eta = (TC)a.X[4 * P + c];
-        const TC bb = a.b[c];
+    TC lh[NPER], lu[NPER], lv[NPER], lw[NPER], le[NPER], lb[NPER];
+    if (kEarly) {
+#pragma unroll
+        for (int k = 0; k < NPER; k++) {
+            const int t = tid + k * BLOCK_THREADS;
+            if (t >= HALO_N) continue;
+            const int li = t % HALO_X, lj = t / HALO_X;
+            const int gx = halo_index<BC>(i0 - 1 + li, G.nx);
+            const int gy = halo_index<BC>(j0 - 1 + lj, G.ny);
+            const long long c = (long long)gy * G.nx + gx;
+            lh[k] = (TC)a.X[c];
+            lu[k] = (TC)a.X[P + c];
+            lv[k] = (TC)a.X[2 * P + c];
+            lw[k] = (TC)a.X[3 * P + c];
+            le[k] = (TC)a.X[4 * P + c];
+            lb[k] = a.b[c];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NPER; k++) {
+        const int t = tid + k * BLOCK_THREADS;
+        if (t >= HALO_N) continue;
+        TC h, u, v, w, eta, bb;
+        if (kEarly) {
+            h = lh[k]; u = lu[k]; v = lv[k]; w = lw[k]; eta = le[k]; bb = lb[k];
+        } else {
+            const int li = t % HALO_X, lj = t / HALO_X;
+            const int gx = halo_index<BC>(i0 - 1 + li, G.nx);
+            const int gy = halo_index<BC>(j0 - 1 + lj, G.ny);
+            const long long c = (long long)gy * G.nx + gx;
+            h = (TC)a.X[c];
+            u = (TC)a.X[P + c];
+            v = (TC)a.X[2 * P + c];
+            w = (TC)a.X[3 * P + c];
+            eta = (TC)a.X[4 * P + c];
+            bb = a.b[c];
+        }
         if (!(h > TC(0))) bad |= (h <= TC(0)) ? FLAG_NONPOSITIVE : FLAG_NONFINITE;  // NaN -> non-finite
         else if (!(h < pos_inf<TC>())) bad |= FLAG_NONFINITE;
         const TC r = recip<TC>(h);
@@ -234,7 +284,6 @@ k_stage(StageArgs<TC, TIN, TA> a) {
 
     // ---- phase 2: right-hand side and stage algebra at this thread's nodes
     double dsum[NDIAG] = {0.0, 0.0, 0.0, 0.0};
-    const int gi = i0 + threadIdx.x;
 #pragma unroll
     for (int ry = 0; ry < ROWS_PER_THREAD; ry++) {
         const int ly = threadIdx.y + ry * THREADS_Y;
@@ -250,15 +299,16 @@ k_stage(StageArgs<TC, TIN, TA> a) {
         } else if (MODE == MODE_S1 || MODE == MODE_S2 || MODE == MODE_S3) {
 #pragma unroll
             for (int f = 0; f < 5; f++) {
-                const TA qv = a.qn[f * P + c];
+                const TA qv = kEarlyStage ? pq[ry][f] : a.qn[f * P + c];
                 const TA kv = (TA)k[f];
-                const TA av = (MODE == MODE_S1) ? qv : a.acc[f * P + c];
+                const TA av = (MODE == MODE_S1) ? qv : (kEarlyStage ? pa[ry][f] : a.acc[f * P + c]);
                 a.acc[f * P + c] = av + a.c_acc * kv;
                 a.Qout[f * P + c] = (TC)(qv + a.c_q * kv);
             }
         } else if (MODE == MODE_S4) {
 #pragma unroll
-            for (int f = 0; f < 5; f++) a.out[f * P + c] = a.acc[f * P + c] + a.c_acc * (TA)k[f];
+            for (int f = 0; f < 5; f++)
+                a.out[f * P + c] = (kEarlyStage ? pa[ry][f] : a.acc[f * P + c]) + a.c_acc * (TA)k[f];
         } else if (MODE == MODE_DIAG) {
             // mass, energy E, shifted energy E' = E + g b^2/2, and the rate
             // <d_q E, q_t>_M with the derivatives listed after eq. (splitcondition)
