@@ -53,10 +53,11 @@ FP64_NOMINAL_TFLOPS = 1.25     # B300 dense FP64 (nominal; no measured entry)
 #   stages 2, 3: read Q, b, q, acc; write acc, Q  26 planes
 #   stage 4: read Q, b, acc; write q              16 planes
 BYTES_PER_CELL_STAGE = {"f64": 84 * 8 / 4, "f32": 84 * 4 / 4, "f32_f64acc": 536 / 4}
-# Algorithmic floating-point operations per cell-stage (an FMA counts 2):
-# differentiated products 12, pointwise coefficients 9, 24 differences, h 9,
-# u 37, v 37, w 19, eta 10, stage algebra 17.5 (average of 20, 20, 20, 10).
-FLOPS_PER_CELL_STAGE = 174.5
+# Algorithmic floating-point operations per cell-stage of the implemented
+# formulation (an FMA counts 2; 1/h counts 1): products and eta + 3/2 b 14,
+# pointwise coefficients 16, 22 differences, h 9, u 25, v 25, w 18, eta 6,
+# stage algebra 17.5 (average of 20, 20, 20, 10).
+FLOPS_PER_CELL_STAGE = 152.5
 DTYPE_NAME = {"f64": "f64", "f32": "f32", "f32_f64acc": "f32+f64acc"}
 
 

@@ -65,24 +65,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs<TC, TIN, TA>& a, cons
         const TC bb = bp[c];
         if (!(h > TC(0))) bad |= (h <= TC(0)) ? FLAG_NONPOSITIVE : FLAG_NONFINITE;
         else if (!(h < pos_inf<TC>())) bad |= FLAG_NONFINITE;
-        const TC r = recip<TC>(h);
-        const TC hu = h * u, hv = h * v;
-        sm[OP_H * HN + t] = h;
-        sm[OP_U * HN + t] = u;
-        sm[OP_V * HN + t] = v;
-        sm[OP_W * HN + t] = w;
-        sm[OP_ETA * HN + t] = eta;
-        sm[OP_B * HN + t] = bb;
-        sm[OP_HS * HN + t] = h * (h + bb);
-        sm[OP_UU * HN + t] = u * u;
-        sm[OP_VV * HN + t] = v * v;
-        sm[OP_HU * HN + t] = hu;
-        sm[OP_HV * HN + t] = hv;
-        sm[OP_HUV * HN + t] = hu * v;
-        sm[OP_HUW * HN + t] = hu * w;
-        sm[OP_HVW * HN + t] = hv * w;
-        sm[OP_E2H * HN + t] = eta * eta * r;
-        sm[OP_R * HN + t] = r;
+        store_operands<TC, HN>(sm, t, h, u, v, w, eta, bb);
     }
     if (bad) atomicOr(a.flag, bad);
     __syncthreads();
@@ -106,35 +89,14 @@ __device__ __forceinline__ void batch_tile(const BatchArgs<TC, TIN, TA>& a, cons
                 const TA qv = a.qn[f * P + c];
                 const TA kv = (TA)k[f];
                 const TA av = (MODE == MODE_S1) ? qv : a.acc[f * P + c];
-                a.acc[f * P + c] = av + c_acc * kv;
-                a.Qout[f * P + c] = (TC)(qv + c_q * kv);
+                a.acc[f * P + c] = fma_(c_acc, kv, av);
+                a.Qout[f * P + c] = (TC)fma_(c_q, kv, qv);
             }
         } else if (MODE == MODE_S4) {
 #pragma unroll
-            for (int f = 0; f < 5; f++) a.out[f * P + c] = a.acc[f * P + c] + c_acc * (TA)k[f];
+            for (int f = 0; f < 5; f++) a.out[f * P + c] = fma_(c_acc, (TA)k[f], a.acc[f * P + c]);
         } else if (MODE == MODE_DIAG) {
-            const double h = (double)sm[OP_H * HN + t], u = (double)sm[OP_U * HN + t];
-            const double v = (double)sm[OP_V * HN + t], w = (double)sm[OP_W * HN + t];
-            const double eta = (double)sm[OP_ETA * HN + t], bb = (double)sm[OP_B * HN + t];
-            double wx = G.dx, wy = G.dy;
-            if (BC == BC_REFLECTING) {
-                if (gi == 0 || gi == G.nx - 1) wx *= 0.5;
-                if (gj == 0 || gj == G.ny - 1) wy *= 0.5;
-            }
-            const double M = wx * wy;
-            const double rho = eta / h;
-            const double kin = 0.5 * (u * u + v * v);
-            const double E = h * (kin + w * w / 6.0 + 0.5 * G.g * (h + 2.0 * bb)
-                                  + G.lam6 * (rho - 1.0) * (rho - 1.0));
-            const double Es = h * kin + h * w * w / 6.0 + 0.5 * G.g * (h + bb) * (h + bb)
-                            + G.lam6 * h * (rho - 1.0) * (rho - 1.0);
-            const double dEh = kin + w * w / 6.0 + G.g * (h + bb) + G.lam6 * (1.0 - rho * rho);
-            const double rate = dEh * (double)k[0] + h * u * (double)k[1] + h * v * (double)k[2]
-                              + (h * w / 3.0) * (double)k[3] - G.lam3 * (1.0 - rho) * (double)k[4];
-            dsum[0] += M * h;
-            dsum[1] += M * E;
-            dsum[2] += M * Es;
-            dsum[3] += M * rate;
+            node_diag<TC, BC, HN>(sm, t, gi, gj, G, k, dsum);
         }
     }
     if (MODE == MODE_DIAG) {

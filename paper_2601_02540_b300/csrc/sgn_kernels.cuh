@@ -37,11 +37,12 @@ constexpr int HALO_Y = TILE_Y + 2;
 constexpr int HALO_N = HALO_X * HALO_Y;
 constexpr int BLOCK_THREADS = TILE_X * THREADS_Y;
 
-// shared-memory planes: the differentiated operands, then 1/h
+// shared-memory planes: the differentiated operands, eta + 3/2 b (eta and b are
+// differentiated only in that combination, see node_rhs), then 1/h
 enum {
     OP_H, OP_U, OP_V, OP_W, OP_ETA, OP_B,
     OP_HS, OP_UU, OP_VV, OP_HU, OP_HV, OP_HUV, OP_HUW, OP_HVW, OP_E2H,
-    OP_R, N_OPS
+    OP_E15, OP_R, N_OPS
 };
 
 constexpr int NDIAG = 4;
@@ -99,6 +100,19 @@ __device__ __forceinline__ double recip<double>(double h) {
 template <>
 __device__ __forceinline__ float recip<float>(float h) { return 1.0f / h; }
 
+// Explicitly rounded arithmetic for the per-node RHS and stage algebra:
+// products and sums that the compiler may not fuse, and fused multiply-adds
+// where fusion is intended.  Every kernel that inlines the same code then
+// rounds identically (the batched and single-grid paths agree bit for bit).
+__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
 // Index of the halo node at global coordinate k (k may be -1 or >= n).
 template <int BC>
 __device__ __forceinline__ int halo_index(int k, int n) {
@@ -107,10 +121,39 @@ __device__ __forceinline__ int halo_index(int k, int n) {
     return k;
 }
 
+// The shared-memory operands of one node: the raw fields, every product that
+// is differentiated, eta + 3/2 b and 1/h (HN: plane size of the tile).
+template <typename TC, int HN>
+__device__ __forceinline__ void store_operands(TC* __restrict__ sm, int t, TC h, TC u, TC v, TC w,
+                                               TC eta, TC bb) {
+    const TC r = recip<TC>(h);
+    const TC hu = mul_(h, u), hv = mul_(h, v);
+    sm[OP_H * HN + t] = h;
+    sm[OP_U * HN + t] = u;
+    sm[OP_V * HN + t] = v;
+    sm[OP_W * HN + t] = w;
+    sm[OP_ETA * HN + t] = eta;
+    sm[OP_B * HN + t] = bb;
+    sm[OP_HS * HN + t] = mul_(h, add_(h, bb));
+    sm[OP_UU * HN + t] = mul_(u, u);
+    sm[OP_VV * HN + t] = mul_(v, v);
+    sm[OP_HU * HN + t] = hu;
+    sm[OP_HV * HN + t] = hv;
+    sm[OP_HUV * HN + t] = mul_(hu, v);
+    sm[OP_HUW * HN + t] = mul_(hu, w);
+    sm[OP_HVW * HN + t] = mul_(hv, w);
+    sm[OP_E2H * HN + t] = mul_(mul_(eta, eta), r);
+    sm[OP_E15 * HN + t] = fma_(TC(1.5), bb, eta);
+    sm[OP_R * HN + t] = r;
+}
+
 // Right-hand side at the node held in shared-memory slot t, global (gi, gj).
-// Terms are grouped by the difference they multiply; every term of eq.
-// (sd_periodic_2D_SGN) / (semi_2D) appears exactly once.
-// HX/HN: row stride and plane size of the shared-memory halo tile.
+// Every term of eq. (sd_periodic_2D_SGN) / (semi_2D) appears once; terms are
+// grouped by the difference they multiply, and two exact regroupings save
+// arithmetic: lam/3 (1 - eta/h) D eta + lam/2 (1 - eta/h) D b =
+// lam/3 (1 - eta/h) D(eta + 3/2 b), and in the eta equation
+// u D eta + 3/2 u D b = u D(eta + 3/2 b) (D is linear), so eta and b are
+// differentiated only through eta + 3/2 b.
 template <typename TC, int BC, int HX = HALO_X, int HN = HALO_N>
 __device__ __forceinline__ void node_rhs(const TC* __restrict__ sm, int t, int gi, int gj,
                                          const Geom& G, TC k[5]) {
@@ -124,64 +167,103 @@ __device__ __forceinline__ void node_rhs(const TC* __restrict__ sm, int t, int g
         if (gj == G.ny - 1) { tt = t; sy = (TC)G.cy1; }
     }
 #define SM_(op, idx) sm[(op) * HN + (idx)]
-#define DXU(op) (SM_(op, tr) - SM_(op, tl))
-#define DYU(op) (SM_(op, tt) - SM_(op, tb))
+#define DXU(op) sub_(SM_(op, tr), SM_(op, tl))
+#define DYU(op) sub_(SM_(op, tt), SM_(op, tb))
     const TC h = SM_(OP_H, t), u = SM_(OP_U, t), v = SM_(OP_V, t);
     const TC w = SM_(OP_W, t), eta = SM_(OP_ETA, t), b = SM_(OP_B, t);
     const TC r = SM_(OP_R, t);
-    const TC hu = SM_(OP_HU, t), hv = SM_(OP_HV, t);
-    const TC g = (TC)G.g;
-    const TC rho = eta * r;          // eta / h
-    const TC om = TC(1) - rho;       // 1 - eta / h
-    const TC s = h + b;
-    const TC lam6r2 = (TC)G.lam6 * rho * rho;
-    const TC uv = u * v, hw = h * w, uw = u * w, vw = v * w;
+    const TC hu = SM_(OP_HU, t), hv = SM_(OP_HV, t), uu = SM_(OP_UU, t), vv = SM_(OP_VV, t);
+    const TC g = (TC)G.g, lam = (TC)G.lam, lam3 = (TC)G.lam3, lam6 = (TC)G.lam6;
     const TC half = TC(0.5);
+    const TC rho = mul_(eta, r);                          // eta / h
+    const TC om = sub_(TC(1), rho);                       // 1 - eta / h
+    const TC base = fma_(lam6, mul_(rho, rho), -mul_(g, add_(h, b)));   // lam/6 (eta/h)^2 - g (h + b)
+    const TC lom = mul_(lam3, om);
+    const TC uv = mul_(u, v), hw = mul_(h, w), uw = mul_(u, w), vw = mul_(v, w);
+    const TC rsx = mul_(r, sx), rsy = mul_(r, sy);
+    const TC hrsx = mul_(half, rsx), hrsy = mul_(half, rsy);
 
-    const TC dxh = DXU(OP_H), dxu = DXU(OP_U), dxv = DXU(OP_V), dxw = DXU(OP_W);
-    const TC dxe = DXU(OP_ETA), dxb = DXU(OP_B);
-    const TC dyh = DYU(OP_H), dyu = DYU(OP_U), dyv = DYU(OP_V), dyw = DYU(OP_W);
-    const TC dye = DYU(OP_ETA), dyb = DYU(OP_B);
+    const TC dxh = DXU(OP_H), dxu = DXU(OP_U), dxv = DXU(OP_V), dxw = DXU(OP_W), dxf = DXU(OP_E15);
+    const TC dyh = DYU(OP_H), dyu = DYU(OP_U), dyv = DYU(OP_V), dyw = DYU(OP_W), dyf = DYU(OP_E15);
 
     // h_t = -(u D_x h + h D_x u + v D_y h + h D_y v) + SAT
-    TC kh = -(sx * (u * dxh + h * dxu) + sy * (v * dyh + h * dyv));
+    TC kh = -fma_(sx, fma_(u, dxh, mul_(h, dxu)), mul_(sy, fma_(v, dyh, mul_(h, dyv))));
     if (BC == BC_REFLECTING) {
         // M^{-1} R^T B N_x R (hu) + M^{-1} R^T B N_y R (hv); corners get both
-        if (gi == 0) kh -= (TC)G.satx * hu;
-        if (gi == G.nx - 1) kh += (TC)G.satx * hu;
-        if (gj == 0) kh -= (TC)G.saty * hv;
-        if (gj == G.ny - 1) kh += (TC)G.saty * hv;
+        if (gi == 0) kh = fma_(-(TC)G.satx, hu, kh);
+        if (gi == G.nx - 1) kh = fma_((TC)G.satx, hu, kh);
+        if (gj == 0) kh = fma_(-(TC)G.saty, hv, kh);
+        if (gj == G.ny - 1) kh = fma_((TC)G.saty, hv, kh);
     }
 
     // h u_t = -[ g D_x(h(h+b)) - g(h+b) D_x h + 1/2 h D_x(u^2) - 1/2 u^2 D_x h
     //           + 1/2 u D_x(hu) - 1/2 hu D_x u + 1/2 D_y(huv) - 1/2 uv D_y h
     //           + 1/2 hv D_y u - 1/2 hu D_y v + lam/6 (eta/h)^2 D_x h + lam/3 D_x eta
     //           - lam/3 (eta/h) D_x eta - lam/6 D_x(eta^2/h) + lam/2 (1 - eta/h) D_x b ]
-    const TC Xu = dxh * (lam6r2 - g * s - half * (u * u)) + dxe * ((TC)G.lam3 * om)
-                + dxb * ((TC)G.lam2 * om) + g * DXU(OP_HS) + half * h * DXU(OP_UU)
-                + half * u * DXU(OP_HU) - half * hu * dxu - (TC)G.lam6 * DXU(OP_E2H);
-    const TC Yu = half * (DYU(OP_HUV) - uv * dyh + hv * dyu - hu * dyv);
-    const TC ku = -r * (sx * Xu + sy * Yu);
+    TC Xu = mul_(fma_(-half, uu, base), dxh);
+    Xu = fma_(lom, dxf, Xu);
+    Xu = fma_(g, DXU(OP_HS), Xu);
+    Xu = fma_(half, fma_(-hu, dxu, fma_(u, DXU(OP_HU), mul_(h, DXU(OP_UU)))), Xu);
+    Xu = fma_(-lam6, DXU(OP_E2H), Xu);
+    const TC Yu2 = fma_(-hu, dyv, fma_(hv, dyu, fma_(-uv, dyh, DYU(OP_HUV))));   // 2 x the y part
+    const TC ku = -fma_(rsx, Xu, mul_(hrsy, Yu2));
 
     // h v_t: the same with x and y (and u and v) exchanged
-    const TC Yv = dyh * (lam6r2 - g * s - half * (v * v)) + dye * ((TC)G.lam3 * om)
-                + dyb * ((TC)G.lam2 * om) + g * DYU(OP_HS) + half * h * DYU(OP_VV)
-                + half * v * DYU(OP_HV) - half * hv * dyv - (TC)G.lam6 * DYU(OP_E2H);
-    const TC Xv = half * (DXU(OP_HUV) - uv * dxh + hu * dxv - hv * dxu);
-    const TC kv = -r * (sy * Yv + sx * Xv);
+    TC Yv = mul_(fma_(-half, vv, base), dyh);
+    Yv = fma_(lom, dyf, Yv);
+    Yv = fma_(g, DYU(OP_HS), Yv);
+    Yv = fma_(half, fma_(-hv, dyv, fma_(v, DYU(OP_HV), mul_(h, DYU(OP_VV)))), Yv);
+    Yv = fma_(-lam6, DYU(OP_E2H), Yv);
+    const TC Xv2 = fma_(-hv, dxu, fma_(hu, dxv, fma_(-uv, dxh, DXU(OP_HUV))));
+    const TC kv = -fma_(rsy, Yv, mul_(hrsx, Xv2));
 
     // h w_t = lam (1 - eta/h) - 1/2 [ D_x(huw) + hu D_x w - uw D_x h - hw D_x u
     //                                + D_y(hvw) + hv D_y w - vw D_y h - hw D_y v ]
-    const TC Xw = DXU(OP_HUW) + hu * dxw - uw * dxh - hw * dxu;
-    const TC Yw = DYU(OP_HVW) + hv * dyw - vw * dyh - hw * dyv;
-    const TC kw = r * ((TC)G.lam * om - half * (sx * Xw + sy * Yw));
+    const TC Xw = fma_(-hw, dxu, fma_(-uw, dxh, fma_(hu, dxw, DXU(OP_HUW))));
+    const TC Yw = fma_(-hw, dyv, fma_(-vw, dyh, fma_(hv, dyw, DYU(OP_HVW))));
+    const TC kw = fma_(r, mul_(lam, om), -fma_(hrsx, Xw, mul_(hrsy, Yw)));
 
     // eta_t = w - u D_x eta - v D_y eta - 3/2 u D_x b - 3/2 v D_y b
-    const TC ke = w - u * (sx * (dxe + TC(1.5) * dxb)) - v * (sy * (dye + TC(1.5) * dyb));
+    const TC ke = fma_(-v, mul_(sy, dyf), fma_(-u, mul_(sx, dxf), w));
 #undef DXU
 #undef DYU
 #undef SM_
     k[0] = kh; k[1] = ku; k[2] = kv; k[3] = kw; k[4] = ke;
+}
+
+// Diagnostics of one node, accumulated into dsum: mass M h, energy M E,
+// shifted energy M E' (E' = E + g b^2/2) and the rate M <d_q E, k> with the
+// derivatives listed after eq. (splitcondition); explicitly rounded.
+template <typename TC, int BC, int HN>
+__device__ __forceinline__ void node_diag(const TC* __restrict__ sm, int t, int gi, int gj, const Geom& G,
+                                          const TC k[5], double dsum[4]) {
+    const double h = (double)sm[OP_H * HN + t], u = (double)sm[OP_U * HN + t];
+    const double v = (double)sm[OP_V * HN + t], w = (double)sm[OP_W * HN + t];
+    const double eta = (double)sm[OP_ETA * HN + t], bb = (double)sm[OP_B * HN + t];
+    double wx = G.dx, wy = G.dy;
+    if (BC == BC_REFLECTING) {
+        if (gi == 0 || gi == G.nx - 1) wx = mul_(0.5, wx);
+        if (gj == 0 || gj == G.ny - 1) wy = mul_(0.5, wy);
+    }
+    const double M = mul_(wx, wy);
+    const double rho = __ddiv_rn(eta, h);
+    const double rm1 = sub_(rho, 1.0);
+    const double kin = mul_(0.5, fma_(u, u, mul_(v, v)));
+    const double w26 = __ddiv_rn(mul_(w, w), 6.0);
+    const double relax = mul_(G.lam6, mul_(rm1, rm1));
+    const double E = mul_(h, add_(add_(kin, w26), fma_(0.5 * G.g, fma_(2.0, bb, h), relax)));
+    const double s = add_(h, bb);
+    const double Es = fma_(h, add_(add_(kin, w26), relax), mul_(0.5 * G.g, mul_(s, s)));
+    const double dEh = add_(add_(kin, w26), fma_(G.g, s, mul_(G.lam6, fma_(-rho, rho, 1.0))));
+    double rate = mul_(dEh, (double)k[0]);
+    rate = fma_(mul_(h, u), (double)k[1], rate);
+    rate = fma_(mul_(h, v), (double)k[2], rate);
+    rate = fma_(__ddiv_rn(mul_(h, w), 3.0), (double)k[3], rate);
+    rate = fma_(-mul_(G.lam3, sub_(1.0, rho)), (double)k[4], rate);
+    dsum[0] = fma_(M, h, dsum[0]);
+    dsum[1] = fma_(M, E, dsum[1]);
+    dsum[2] = fma_(M, Es, dsum[2]);
+    dsum[3] = fma_(M, rate, dsum[3]);
 }
 
 template <typename TC, typename TIN, typename TA, int BC, int MODE>
@@ -260,24 +342,7 @@ k_stage(StageArgs<TC, TIN, TA> a) {
         }
         if (!(h > TC(0))) bad |= (h <= TC(0)) ? FLAG_NONPOSITIVE : FLAG_NONFINITE;  // NaN -> non-finite
         else if (!(h < pos_inf<TC>())) bad |= FLAG_NONFINITE;
-        const TC r = recip<TC>(h);
-        const TC hu = h * u, hv = h * v;
-        sm[OP_H * HALO_N + t] = h;
-        sm[OP_U * HALO_N + t] = u;
-        sm[OP_V * HALO_N + t] = v;
-        sm[OP_W * HALO_N + t] = w;
-        sm[OP_ETA * HALO_N + t] = eta;
-        sm[OP_B * HALO_N + t] = bb;
-        sm[OP_HS * HALO_N + t] = h * (h + bb);
-        sm[OP_UU * HALO_N + t] = u * u;
-        sm[OP_VV * HALO_N + t] = v * v;
-        sm[OP_HU * HALO_N + t] = hu;
-        sm[OP_HV * HALO_N + t] = hv;
-        sm[OP_HUV * HALO_N + t] = hu * v;
-        sm[OP_HUW * HALO_N + t] = hu * w;
-        sm[OP_HVW * HALO_N + t] = hv * w;
-        sm[OP_E2H * HALO_N + t] = eta * eta * r;
-        sm[OP_R * HALO_N + t] = r;
+        store_operands<TC, HALO_N>(sm, t, h, u, v, w, eta, bb);
     }
     if (bad) atomicOr(a.flag, bad);
     __syncthreads();
@@ -302,38 +367,15 @@ k_stage(StageArgs<TC, TIN, TA> a) {
                 const TA qv = kEarlyStage ? pq[ry][f] : a.qn[f * P + c];
                 const TA kv = (TA)k[f];
                 const TA av = (MODE == MODE_S1) ? qv : (kEarlyStage ? pa[ry][f] : a.acc[f * P + c]);
-                a.acc[f * P + c] = av + a.c_acc * kv;
-                a.Qout[f * P + c] = (TC)(qv + a.c_q * kv);
+                a.acc[f * P + c] = fma_(a.c_acc, kv, av);
+                a.Qout[f * P + c] = (TC)fma_(a.c_q, kv, qv);
             }
         } else if (MODE == MODE_S4) {
 #pragma unroll
             for (int f = 0; f < 5; f++)
-                a.out[f * P + c] = (kEarlyStage ? pa[ry][f] : a.acc[f * P + c]) + a.c_acc * (TA)k[f];
+                a.out[f * P + c] = fma_(a.c_acc, (TA)k[f], kEarlyStage ? pa[ry][f] : a.acc[f * P + c]);
         } else if (MODE == MODE_DIAG) {
-            // mass, energy E, shifted energy E' = E + g b^2/2, and the rate
-            // <d_q E, q_t>_M with the derivatives listed after eq. (splitcondition)
-            const double h = (double)sm[OP_H * HALO_N + t], u = (double)sm[OP_U * HALO_N + t];
-            const double v = (double)sm[OP_V * HALO_N + t], w = (double)sm[OP_W * HALO_N + t];
-            const double eta = (double)sm[OP_ETA * HALO_N + t], bb = (double)sm[OP_B * HALO_N + t];
-            double wx = G.dx, wy = G.dy;
-            if (BC == BC_REFLECTING) {
-                if (gi == 0 || gi == G.nx - 1) wx *= 0.5;
-                if (gj == 0 || gj == G.ny - 1) wy *= 0.5;
-            }
-            const double M = wx * wy;
-            const double rho = eta / h;
-            const double kin = 0.5 * (u * u + v * v);
-            const double E = h * (kin + w * w / 6.0 + 0.5 * G.g * (h + 2.0 * bb)
-                                  + G.lam6 * (rho - 1.0) * (rho - 1.0));
-            const double Es = h * kin + h * w * w / 6.0 + 0.5 * G.g * (h + bb) * (h + bb)
-                            + G.lam6 * h * (rho - 1.0) * (rho - 1.0);
-            const double dEh = kin + w * w / 6.0 + G.g * (h + bb) + G.lam6 * (1.0 - rho * rho);
-            const double rate = dEh * (double)k[0] + h * u * (double)k[1] + h * v * (double)k[2]
-                              + (h * w / 3.0) * (double)k[3] - G.lam3 * (1.0 - rho) * (double)k[4];
-            dsum[0] += M * h;
-            dsum[1] += M * E;
-            dsum[2] += M * Es;
-            dsum[3] += M * rate;
+            node_diag<TC, BC, HALO_N>(sm, t, gi, gj, G, k, dsum);
         }
     }
 
