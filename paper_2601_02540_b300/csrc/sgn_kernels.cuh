@@ -81,6 +81,23 @@ __device__ __forceinline__ double pos_inf<double>() { return __longlong_as_doubl
 template <>
 __device__ __forceinline__ float pos_inf<float>() { return __int_as_float(0x7f800000); }
 
+// Error bits for a water height: 0 if h is positive and finite.  Tested on the
+// bit pattern (integer pipe): positive finite values are exactly the patterns
+// strictly between +0 and +inf; NaN (either sign) is non-finite, everything
+// else at or below zero (including -inf) is non-positive.
+__device__ __forceinline__ int h_flags(double h) {
+    const long long bits = __double_as_longlong(h);
+    if (bits > 0 && bits < 0x7ff0000000000000LL) return 0;
+    const long long mag = bits & 0x7fffffffffffffffLL;
+    return (mag > 0x7ff0000000000000LL || bits == 0x7ff0000000000000LL) ? FLAG_NONFINITE : FLAG_NONPOSITIVE;
+}
+__device__ __forceinline__ int h_flags(float h) {
+    const int bits = __float_as_int(h);
+    if (bits > 0 && bits < 0x7f800000) return 0;
+    const int mag = bits & 0x7fffffff;
+    return (mag > 0x7f800000 || bits == 0x7f800000) ? FLAG_NONFINITE : FLAG_NONPOSITIVE;
+}
+
 // 1/h.  Double: Newton-Raphson iteration for the reciprocal,
 // x <- x + x (1 - h x) (each step doubles the correct bits), twice, from the
 // hardware's approximate reciprocal (PTX rcp.approx.ftz.f64); the result is
@@ -266,14 +283,16 @@ __device__ __forceinline__ void node_diag(const TC* __restrict__ sm, int t, int 
     dsum[3] = fma_(M, rate, dsum[3]);
 }
 
-template <typename TC, typename TIN, typename TA, int BC, int MODE>
-__global__ void __launch_bounds__(BLOCK_THREADS)
-k_stage(StageArgs<TC, TIN, TA> a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TC* sm = reinterpret_cast<TC*>(smem_raw);
-    const Geom& G = a.G;
-    const int i0 = blockIdx.x * TILE_X;
-    const int j0 = blockIdx.y * TILE_Y;
+// One output tile (TILE_X x 8*ROWS nodes at (i0, j0)) of a stage launch: the
+// body shared by the single-grid and the batched kernels.  The pointers of `a`
+// address this grid's planes; `G` is its geometry; DIAG writes the tile's
+// partial sums to partial_slot[0..NDIAG).
+template <typename TC, typename TIN, typename TA, int BC, int MODE, int ROWS>
+__device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, const Geom& G, int i0, int j0,
+                                           TC* __restrict__ sm, double* partial_slot) {
+    constexpr int ROWS_PER_THREAD = ROWS;
+    constexpr int HALO_X = TILE_X + 2;
+    constexpr int HALO_N = HALO_X * (THREADS_Y * ROWS + 2);
     const long long P = G.plane;
     const int tid = threadIdx.y * TILE_X + threadIdx.x;
 
@@ -340,8 +359,7 @@ k_stage(StageArgs<TC, TIN, TA> a) {
             eta = (TC)a.X[4 * P + c];
             bb = a.b[c];
         }
-        if (!(h > TC(0))) bad |= (h <= TC(0)) ? FLAG_NONPOSITIVE : FLAG_NONFINITE;  // NaN -> non-finite
-        else if (!(h < pos_inf<TC>())) bad |= FLAG_NONFINITE;
+        bad |= h_flags(h);
         store_operands<TC, HALO_N>(sm, t, h, u, v, w, eta, bb);
     }
     if (bad) atomicOr(a.flag, bad);
@@ -356,7 +374,7 @@ k_stage(StageArgs<TC, TIN, TA> a) {
         if (gi >= G.nx || gj >= G.ny) continue;
         const int t = (ly + 1) * HALO_X + (threadIdx.x + 1);
         TC k[5];
-        node_rhs<TC, BC>(sm, t, gi, gj, G, k);
+        node_rhs<TC, BC, HALO_X, HALO_N>(sm, t, gi, gj, G, k);
         const long long c = (long long)gj * G.nx + gi;
         if (MODE == MODE_RHS) {
 #pragma unroll
@@ -393,10 +411,19 @@ k_stage(StageArgs<TC, TIN, TA> a) {
         if (tid < NDIAG) {
             double x = 0.0;
             for (int wgi = 0; wgi < BLOCK_THREADS / 32; wgi++) x += red[wgi][tid];
-            const long long blk = (long long)blockIdx.y * gridDim.x + blockIdx.x;
-            a.partials[blk * NDIAG + tid] = x;
+            partial_slot[tid] = x;
         }
     }
+}
+
+template <typename TC, typename TIN, typename TA, int BC, int MODE>
+__global__ void __launch_bounds__(BLOCK_THREADS)
+k_stage(StageArgs<TC, TIN, TA> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TC* sm = reinterpret_cast<TC*>(smem_raw);
+    const long long blk = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+    stage_tile<TC, TIN, TA, BC, MODE, ROWS_PER_THREAD>(a, a.G, blockIdx.x * TILE_X, blockIdx.y * TILE_Y, sm,
+                                                       a.partials ? a.partials + blk * NDIAG : nullptr);
 }
 
 // Second pass of the diagnostics: one block sums the per-block partials in a
