@@ -89,7 +89,7 @@ sgn_status check_state_ptr(const void* p, const char* name) {
 template <typename TC, typename TIN, typename TA, int BC, int MODE>
 cudaError_t launch_stage(const sgn_ctx* c, const StageArgs<TC, TIN, TA>& a, cudaStream_t s) {
     auto kern = sgn::k_stage<TC, TIN, TA, BC, MODE>;
-    const size_t smem = (size_t)sgn::N_OPS * sgn::HALO_N * sizeof(TC);
+    const size_t smem = sgn::stage_smem_bytes<TC, MODE>(sgn::ROWS_PER_THREAD);
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
@@ -335,22 +335,7 @@ sgn_status sgn_create(const sgn_params* p, const void* b_dev, sgn_ctx** out) {
     const double dx = per ? (p->xmax - p->xmin) / p->nx : (p->xmax - p->xmin) / (p->nx - 1);
     const double dy = per ? (p->ymax - p->ymin) / p->ny : (p->ymax - p->ymin) / (p->ny - 1);
     Geom& G = c->G;
-    G.nx = p->nx;
-    G.ny = p->ny;
-    G.plane = (long long)p->nx * p->ny;
-    G.cx2 = 1.0 / (2.0 * dx);
-    G.cy2 = 1.0 / (2.0 * dy);
-    G.cx1 = 1.0 / dx;
-    G.cy1 = 1.0 / dy;
-    G.satx = 2.0 / dx;
-    G.saty = 2.0 / dy;
-    G.dx = dx;
-    G.dy = dy;
-    G.g = p->g;
-    G.lam = p->lambda;
-    G.lam2 = p->lambda / 2.0;
-    G.lam3 = p->lambda / 3.0;
-    G.lam6 = p->lambda / 6.0;
+    sgn::fill_geom(G, p->nx, p->ny, dx, dy, p->g, p->lambda);
     c->tc_size = p->prec == SGN_F64 ? sizeof(double) : sizeof(float);
     c->ta_size = p->prec == SGN_F32 ? sizeof(float) : sizeof(double);
     c->grid = dim3((p->nx + sgn::TILE_X - 1) / sgn::TILE_X, (p->ny + sgn::TILE_Y - 1) / sgn::TILE_Y);

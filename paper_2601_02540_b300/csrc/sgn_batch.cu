@@ -64,7 +64,7 @@ int rows_index(int rows) { return rows == 1 ? 0 : (rows == 2 ? 1 : 2); }
 template <typename TC, typename TIN, typename TA, int MODE, int ROWS>
 cudaError_t blaunch(const sgn_batch* B, const sgn::BatchArgs<TC, TIN, TA>& a, cudaStream_t s) {
     const int ri = rows_index(ROWS);
-    const size_t smem = (size_t)sgn::N_OPS * (sgn::TILE_X + 2) * (sgn::THREADS_Y * ROWS + 2) * sizeof(TC);
+    const size_t smem = sgn::stage_smem_bytes<TC, MODE>(ROWS);
     sgn::BatchArgs<TC, TIN, TA> b = a;
     b.tiles = B->tiles[ri];
     sgn::k_batch_stage<TC, TIN, TA, MODE, ROWS>
@@ -75,7 +75,7 @@ cudaError_t blaunch(const sgn_batch* B, const sgn::BatchArgs<TC, TIN, TA>& a, cu
 
 template <typename TC, typename TIN, typename TA, int MODE, int ROWS>
 cudaError_t set_attr() {
-    const size_t smem = (size_t)sgn::N_OPS * (sgn::TILE_X + 2) * (sgn::THREADS_Y * ROWS + 2) * sizeof(TC);
+    const size_t smem = sgn::stage_smem_bytes<TC, MODE>(ROWS);
     return cudaFuncSetAttribute(sgn::k_batch_stage<TC, TIN, TA, MODE, ROWS>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
@@ -257,23 +257,7 @@ sgn_status sgn_batch_create(const sgn_instance* inst, int ninst, int prec, const
         const bool per = p.bc == SGN_BC_PERIODIC;
         const double dx = per ? (p.xmax - p.xmin) / p.nx : (p.xmax - p.xmin) / (p.nx - 1);
         const double dy = per ? (p.ymax - p.ymin) / p.ny : (p.ymax - p.ymin) / (p.ny - 1);
-        sgn::Geom& G = d.G;
-        G.nx = p.nx;
-        G.ny = p.ny;
-        G.plane = (long long)p.nx * p.ny;
-        G.cx2 = 1.0 / (2.0 * dx);
-        G.cy2 = 1.0 / (2.0 * dy);
-        G.cx1 = 1.0 / dx;
-        G.cy1 = 1.0 / dy;
-        G.satx = 2.0 / dx;
-        G.saty = 2.0 / dy;
-        G.dx = dx;
-        G.dy = dy;
-        G.g = p.g;
-        G.lam = p.lambda;
-        G.lam2 = p.lambda / 2.0;
-        G.lam3 = p.lambda / 3.0;
-        G.lam6 = p.lambda / 6.0;
+        sgn::fill_geom(d.G, p.nx, p.ny, dx, dy, p.g, p.lambda);
         d.bc = p.bc;
         d.off = off;
         // same coefficients, computed the same way, as sgn_step
@@ -281,7 +265,7 @@ sgn_status sgn_batch_create(const sgn_instance* inst, int ninst, int prec, const
         d.c_acc[1] = p.dt / 3.0; d.c_q[1] = p.dt / 2.0;
         d.c_acc[2] = p.dt / 3.0; d.c_q[2] = p.dt;
         d.c_acc[3] = p.dt / 6.0; d.c_q[3] = 0.0;
-        off += G.plane;
+        off += d.G.plane;
     }
     B->cells = off;
     // tile lists for the three tile heights; the descriptor keeps the rows = 2

@@ -58,7 +58,49 @@ struct Geom {
     double dx, dy;         // mass-matrix spacing
     double g, lam;
     double lam2, lam3, lam6;  // lambda/2, lambda/3, lambda/6
+    // the same constants rounded to float, so that float kernels never convert
+    // (a double-to-float conversion occupies the FP64 pipe)
+    float f_cx2, f_cy2, f_cx1, f_cy1, f_satx, f_saty, f_g, f_lam, f_lam3, f_lam6;
 };
+
+// Host: fill a Geom for an nx x ny grid with spacing (dx, dy).
+inline void fill_geom(Geom& G, int nx, int ny, double dx, double dy, double g, double lam) {
+    G.nx = nx;
+    G.ny = ny;
+    G.plane = (long long)nx * ny;
+    G.cx2 = 1.0 / (2.0 * dx);
+    G.cy2 = 1.0 / (2.0 * dy);
+    G.cx1 = 1.0 / dx;
+    G.cy1 = 1.0 / dy;
+    G.satx = 2.0 / dx;
+    G.saty = 2.0 / dy;
+    G.dx = dx;
+    G.dy = dy;
+    G.g = g;
+    G.lam = lam;
+    G.lam2 = lam / 2.0;
+    G.lam3 = lam / 3.0;
+    G.lam6 = lam / 6.0;
+    G.f_cx2 = (float)G.cx2;
+    G.f_cy2 = (float)G.cy2;
+    G.f_cx1 = (float)G.cx1;
+    G.f_cy1 = (float)G.cy1;
+    G.f_satx = (float)G.satx;
+    G.f_saty = (float)G.saty;
+    G.f_g = (float)G.g;
+    G.f_lam = (float)G.lam;
+    G.f_lam3 = (float)G.lam3;
+    G.f_lam6 = (float)G.lam6;
+}
+
+// A grid constant in the compute type TC (the double or the float copy).
+template <typename TC>
+__device__ __forceinline__ TC gsel(double d, float f);
+template <>
+__device__ __forceinline__ double gsel<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float gsel<float>(double, float f) { return f; }
+#define GC(TC, name) gsel<TC>(G.name, G.f_##name)
 
 template <typename TC, typename TIN, typename TA>
 struct StageArgs {
@@ -140,57 +182,73 @@ __device__ __forceinline__ int halo_index(int k, int n) {
 
 // The shared-memory operands of one node: the raw fields, every product that
 // is differentiated, eta + 3/2 b and 1/h (HN: plane size of the tile).
+template <typename TC>
+__device__ __forceinline__ void make_ops(TC h, TC u, TC v, TC w, TC eta, TC bb, TC o[N_OPS]) {
+    const TC r = recip<TC>(h);
+    const TC hu = mul_(h, u), hv = mul_(h, v);
+    o[OP_H] = h;
+    o[OP_U] = u;
+    o[OP_V] = v;
+    o[OP_W] = w;
+    o[OP_ETA] = eta;
+    o[OP_B] = bb;
+    o[OP_HS] = mul_(h, add_(h, bb));
+    o[OP_UU] = mul_(u, u);
+    o[OP_VV] = mul_(v, v);
+    o[OP_HU] = hu;
+    o[OP_HV] = hv;
+    o[OP_HUV] = mul_(hu, v);
+    o[OP_HUW] = mul_(hu, w);
+    o[OP_HVW] = mul_(hv, w);
+    o[OP_E2H] = mul_(mul_(eta, eta), r);
+    o[OP_E15] = fma_(TC(1.5), bb, eta);
+    o[OP_R] = r;
+}
+
 template <typename TC, int HN>
 __device__ __forceinline__ void store_operands(TC* __restrict__ sm, int t, TC h, TC u, TC v, TC w,
                                                TC eta, TC bb) {
-    const TC r = recip<TC>(h);
-    const TC hu = mul_(h, u), hv = mul_(h, v);
-    sm[OP_H * HN + t] = h;
-    sm[OP_U * HN + t] = u;
-    sm[OP_V * HN + t] = v;
-    sm[OP_W * HN + t] = w;
-    sm[OP_ETA * HN + t] = eta;
-    sm[OP_B * HN + t] = bb;
-    sm[OP_HS * HN + t] = mul_(h, add_(h, bb));
-    sm[OP_UU * HN + t] = mul_(u, u);
-    sm[OP_VV * HN + t] = mul_(v, v);
-    sm[OP_HU * HN + t] = hu;
-    sm[OP_HV * HN + t] = hv;
-    sm[OP_HUV * HN + t] = mul_(hu, v);
-    sm[OP_HUW * HN + t] = mul_(hu, w);
-    sm[OP_HVW * HN + t] = mul_(hv, w);
-    sm[OP_E2H * HN + t] = mul_(mul_(eta, eta), r);
-    sm[OP_E15 * HN + t] = fma_(TC(1.5), bb, eta);
-    sm[OP_R * HN + t] = r;
+    TC o[N_OPS];
+    make_ops<TC>(h, u, v, w, eta, bb, o);
+#pragma unroll
+    for (int op = 0; op < N_OPS; op++) sm[op * HN + t] = o[op];
 }
 
-// Right-hand side at the node held in shared-memory slot t, global (gi, gj).
+// Where node_rhs reads its operands: position 0 is the node itself, 1-4 its
+// left, right, lower and upper neighbours (already resolved to the node itself
+// on a reflecting wall, where the one-sided row uses it).
+enum { POS_C = 0, POS_L = 1, POS_R = 2, POS_B = 3, POS_T = 4 };
+
+template <typename TC, int HN>
+struct SmemOps {            // operands staged in a shared-memory halo tile
+    const TC* sm;
+    int idx[5];
+    __device__ __forceinline__ TC get(int op, int pos) const { return sm[op * HN + idx[pos]]; }
+};
+
+// Right-hand side at node (gi, gj), its operands read from S (S.get(op, pos)).
 // Every term of eq. (sd_periodic_2D_SGN) / (semi_2D) appears once; terms are
 // grouped by the difference they multiply, and two exact regroupings save
 // arithmetic: lam/3 (1 - eta/h) D eta + lam/2 (1 - eta/h) D b =
 // lam/3 (1 - eta/h) D(eta + 3/2 b), and in the eta equation
 // u D eta + 3/2 u D b = u D(eta + 3/2 b) (D is linear), so eta and b are
 // differentiated only through eta + 3/2 b.
-template <typename TC, int BC, int HX = HALO_X, int HN = HALO_N>
-__device__ __forceinline__ void node_rhs(const TC* __restrict__ sm, int t, int gi, int gj,
-                                         const Geom& G, TC k[5]) {
-    int tl = t - 1, tr = t + 1, tb = t - HX, tt = t + HX;
-    TC sx = (TC)G.cx2, sy = (TC)G.cy2;
+template <typename TC, int BC, typename Src>
+__device__ __forceinline__ void node_rhs_src(const Src& S, int gi, int gj, const Geom& G, TC k[5]) {
+    TC sx = GC(TC, cx2), sy = GC(TC, cy2);
     if (BC == BC_REFLECTING) {
         // one-sided first/last rows of the reflecting operator: (f1 - f0)/dx
-        if (gi == 0) { tl = t; sx = (TC)G.cx1; }
-        if (gi == G.nx - 1) { tr = t; sx = (TC)G.cx1; }
-        if (gj == 0) { tb = t; sy = (TC)G.cy1; }
-        if (gj == G.ny - 1) { tt = t; sy = (TC)G.cy1; }
+        if (gi == 0 || gi == G.nx - 1) sx = GC(TC, cx1);
+        if (gj == 0 || gj == G.ny - 1) sy = GC(TC, cy1);
     }
-#define SM_(op, idx) sm[(op) * HN + (idx)]
-#define DXU(op) sub_(SM_(op, tr), SM_(op, tl))
-#define DYU(op) sub_(SM_(op, tt), SM_(op, tb))
-    const TC h = SM_(OP_H, t), u = SM_(OP_U, t), v = SM_(OP_V, t);
-    const TC w = SM_(OP_W, t), eta = SM_(OP_ETA, t), b = SM_(OP_B, t);
-    const TC r = SM_(OP_R, t);
-    const TC hu = SM_(OP_HU, t), hv = SM_(OP_HV, t), uu = SM_(OP_UU, t), vv = SM_(OP_VV, t);
-    const TC g = (TC)G.g, lam = (TC)G.lam, lam3 = (TC)G.lam3, lam6 = (TC)G.lam6;
+#define SM_(op, pos) S.get(op, pos)
+#define DXU(op) sub_(SM_(op, POS_R), SM_(op, POS_L))
+#define DYU(op) sub_(SM_(op, POS_T), SM_(op, POS_B))
+    const TC h = SM_(OP_H, POS_C), u = SM_(OP_U, POS_C), v = SM_(OP_V, POS_C);
+    const TC w = SM_(OP_W, POS_C), eta = SM_(OP_ETA, POS_C), b = SM_(OP_B, POS_C);
+    const TC r = SM_(OP_R, POS_C);
+    const TC hu = SM_(OP_HU, POS_C), hv = SM_(OP_HV, POS_C), uu = SM_(OP_UU, POS_C), vv = SM_(OP_VV, POS_C);
+    const TC g = GC(TC, g), lam = GC(TC, lam), lam3 = GC(TC, lam3), lam6 = GC(TC, lam6);
     const TC half = TC(0.5);
     const TC rho = mul_(eta, r);                          // eta / h
     const TC om = sub_(TC(1), rho);                       // 1 - eta / h
@@ -207,10 +265,10 @@ __device__ __forceinline__ void node_rhs(const TC* __restrict__ sm, int t, int g
     TC kh = -fma_(sx, fma_(u, dxh, mul_(h, dxu)), mul_(sy, fma_(v, dyh, mul_(h, dyv))));
     if (BC == BC_REFLECTING) {
         // M^{-1} R^T B N_x R (hu) + M^{-1} R^T B N_y R (hv); corners get both
-        if (gi == 0) kh = fma_(-(TC)G.satx, hu, kh);
-        if (gi == G.nx - 1) kh = fma_((TC)G.satx, hu, kh);
-        if (gj == 0) kh = fma_(-(TC)G.saty, hv, kh);
-        if (gj == G.ny - 1) kh = fma_((TC)G.saty, hv, kh);
+        if (gi == 0) kh = fma_(-GC(TC, satx), hu, kh);
+        if (gi == G.nx - 1) kh = fma_(GC(TC, satx), hu, kh);
+        if (gj == 0) kh = fma_(-GC(TC, saty), hv, kh);
+        if (gj == G.ny - 1) kh = fma_(GC(TC, saty), hv, kh);
     }
 
     // h u_t = -[ g D_x(h(h+b)) - g(h+b) D_x h + 1/2 h D_x(u^2) - 1/2 u^2 D_x h
@@ -248,6 +306,27 @@ __device__ __forceinline__ void node_rhs(const TC* __restrict__ sm, int t, int g
     k[0] = kh; k[1] = ku; k[2] = kv; k[3] = kw; k[4] = ke;
 }
 
+// Right-hand side at the node held in shared-memory slot t of a halo tile with
+// row stride HX and plane size HN, global (gi, gj).
+template <typename TC, int BC, int HX = HALO_X, int HN = HALO_N>
+__device__ __forceinline__ void node_rhs(const TC* __restrict__ sm, int t, int gi, int gj,
+                                         const Geom& G, TC k[5]) {
+    SmemOps<TC, HN> S;
+    S.sm = sm;
+    S.idx[POS_C] = t;
+    S.idx[POS_L] = t - 1;
+    S.idx[POS_R] = t + 1;
+    S.idx[POS_B] = t - HX;
+    S.idx[POS_T] = t + HX;
+    if (BC == BC_REFLECTING) {
+        if (gi == 0) S.idx[POS_L] = t;
+        if (gi == G.nx - 1) S.idx[POS_R] = t;
+        if (gj == 0) S.idx[POS_B] = t;
+        if (gj == G.ny - 1) S.idx[POS_T] = t;
+    }
+    node_rhs_src<TC, BC>(S, gi, gj, G, k);
+}
+
 // Diagnostics of one node, accumulated into dsum: mass M h, energy M E,
 // shifted energy M E' (E' = E + g b^2/2) and the rate M <d_q E, k> with the
 // derivatives listed after eq. (splitcondition); explicitly rounded.
@@ -281,6 +360,12 @@ __device__ __forceinline__ void node_diag(const TC* __restrict__ sm, int t, int 
     dsum[1] = fma_(M, E, dsum[1]);
     dsum[2] = fma_(M, Es, dsum[2]);
     dsum[3] = fma_(M, rate, dsum[3]);
+}
+
+// Dynamic shared memory of a stage launch: the halo tile of the operands.
+template <typename TC, int MODE>
+constexpr size_t stage_smem_bytes(int rows) {
+    return (size_t)N_OPS * (TILE_X + 2) * (THREADS_Y * rows + 2) * sizeof(TC);
 }
 
 // One output tile (TILE_X x 8*ROWS nodes at (i0, j0)) of a stage launch: the

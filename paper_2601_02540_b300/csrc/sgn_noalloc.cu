@@ -113,23 +113,7 @@ extern "C" SGN_API sgn_status sgn_mass_energy_noalloc(const sgn_params* p, const
     a.b = static_cast<const double*>(b_dev);
     a.partials = scratch;
     a.flag = reinterpret_cast<int*>(scratch + kFlagOffset);
-    sgn::Geom& G = a.G;
-    G.nx = p->nx;
-    G.ny = p->ny;
-    G.plane = (long long)p->nx * p->ny;
-    G.cx2 = 1.0 / (2.0 * dx);
-    G.cy2 = 1.0 / (2.0 * dy);
-    G.cx1 = 1.0 / dx;
-    G.cy1 = 1.0 / dy;
-    G.satx = 2.0 / dx;
-    G.saty = 2.0 / dy;
-    G.dx = dx;
-    G.dy = dy;
-    G.g = p->g;
-    G.lam = p->lambda;
-    G.lam2 = p->lambda / 2.0;
-    G.lam3 = p->lambda / 3.0;
-    G.lam6 = p->lambda / 6.0;
+    sgn::fill_geom(a.G, p->nx, p->ny, dx, dy, p->g, p->lambda);
 
     // the flag must start at zero; the partials and out are fully overwritten
     e = cudaMemsetAsync(a.flag, 0, sizeof(int), s);
