@@ -80,7 +80,7 @@ def _kernel_hash() -> str:
 def _ncu_traffic(prec: str) -> float | None:
     """DRAM bytes per launch of the stage kernel from the committed ncu summary,
     or None when the kernels changed since it was captured."""
-    path = os.path.join(ROOT, "profiles", "k_stage_traffic.txt")
+    path = os.path.join(ROOT, "profiles", "k_stage_traffic_4096.md")
     if not os.path.exists(path):
         return None
     vals, khash = {}, None
