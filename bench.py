@@ -70,10 +70,10 @@ def _peaks() -> tuple[float, str]:
 
 
 def _kernel_hash() -> str:
+    """Hash of the source that defines the stage kernels and their tile shape."""
     h = hashlib.sha256()
-    for f in ("sgn_kernels.cuh", "sgn_api.cu"):
-        with open(os.path.join(ROOT, "paper_2601_02540_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(ROOT, "paper_2601_02540_b300", "csrc", "sgn_kernels.cuh"), "rb") as fh:
+        h.update(fh.read())
     return h.hexdigest()[:16]
 
 
