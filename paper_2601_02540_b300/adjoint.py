@@ -7,10 +7,12 @@ state is at rest (u = v = 0), so the initialization of the auxiliary variables
 gives eta0 = h0 and w0 = 0 (eq. (initialization)); the gradient with respect
 to h0 is therefore qbar_h + qbar_eta of the initial state.
 
-Forward (K > 0): ``sgn_step`` with a copy of the state kept every K steps
-(checkpoint).  Backward: for each segment, last to first, recompute it from its
-checkpoint with ``sgn_step_record`` (which keeps the four stage states of
-every step of the segment), then walk its steps backwards with
+Forward (K > 0): ``sgn_step`` with a copy of the state kept at the start of
+every K-step segment (checkpoint); the last segment runs through
+``sgn_step_record`` instead, which keeps the four stage states of each of its
+steps, so the backward pass need not recompute it.  Backward: for each
+segment, last to first, recompute it from its checkpoint with
+``sgn_step_record`` (except the last), then walk its steps backwards with
 ``sgn_step_vjp``, adding the gauge cotangents to qbar_h at the observation
 steps.  Memory: the K-step stash, 20 planes per step (4.2 GB at 512^2 for
 K = 100).  K <= 0 keeps the stage states of every step during the forward pass
@@ -43,19 +45,25 @@ class GaugeRollout(torch.autograd.Function):
         obs = torch.empty((nobs, gauges.numel()), dtype=torch.float64, device=h0.device)
         checkpoints = {}
         stash = None
+        last = 0
         if K <= 0:
             # keep every step's stage states (no recomputation in the backward pass)
             stash = torch.empty((nsteps, 20, ny, nx), dtype=torch.float64, device=h0.device)
+        elif nsteps > 0:
+            # the last segment keeps its stage states (stash indexed from its start)
+            last = ((nsteps - 1) // K) * K
+            stash = torch.empty((nsteps - last, 20, ny, nx), dtype=torch.float64, device=h0.device)
         step = 0
         while step < nsteps:
-            if K > 0 and step % K == 0:
+            if K > 0 and step % K == 0 and step < last:
                 checkpoints[step] = q.clone()
             nxt = min(nsteps, (step // every + 1) * every)
             if K > 0:
                 nxt = min(nxt, (step // K + 1) * K)
+            if K > 0 and step < last:
                 solver.step(q, dt, nxt - step)
             else:
-                solver.step_record(q, dt, nxt - step, stash[step:nxt])
+                solver.step_record(q, dt, nxt - step, stash[step - last:nxt - last])
             step = nxt
             if step % every == 0:
                 obs[step // every - 1] = q[0].reshape(-1)[gauges]
@@ -63,6 +71,7 @@ class GaugeRollout(torch.autograd.Function):
         ctx.gauges = gauges
         ctx.checkpoints = checkpoints
         ctx.stash = stash
+        ctx.last = last
         ctx.shape = (ny, nx)
         ctx.b = b
         return obs
@@ -79,11 +88,15 @@ class GaugeRollout(torch.autograd.Function):
         grad_obs = grad_obs.to(torch.float64).contiguous()
         if K > 0:
             segments = [(s0, min(K, nsteps - s0)) for s0 in sorted(ctx.checkpoints)]
+            if nsteps > 0:
+                segments.append((ctx.last, nsteps - ctx.last))
         else:
             segments = [(0, nsteps)]
         stash = ctx.stash
         for s0, L in reversed(segments):
-            if K > 0:
+            if K > 0 and s0 == ctx.last:
+                base = 0                            # kept by the forward pass
+            elif K > 0:
                 # recompute the segment from its checkpoint, keeping its stage states
                 if stash is None or stash.shape[0] < L:
                     stash = torch.empty((L, 20, ny, nx), dtype=torch.float64, device=dev)

@@ -15,55 +15,88 @@
 //     n <= N-2, and the one-sided end rows add +V(N-1) at n = N-1 and -V(0) at
 //     n = 0), then the chain rule through P_t(q_n, b_n).
 // Two passes, both one node per thread and free of halos and atomics:
-//   k_adj_weights  products P_t, 1/h and the 24 direction weights of each node
+//   k_adj_weights  products P_t, 1/h and the 22 direction weights of each node
 //                  into scratch planes;
 //   k_adj_gather   differences, pointwise part, gathers of the weights of the
 //                  neighbours, chain rule, and (stage mode) the reverse RK4
 //                  stage algebra.
+// The kernels are FP64-pipe bound, so the formulas are arranged for the fewest
+// FP64 instructions: h r = 1 (r = 1/h) is used to cancel factors exactly up to
+// rounding, constant factors of the differences are folded on the host, and
+// the cotangent of a stage is carried as sigma * A with the scale sigma applied
+// only where a result is accumulated (see AdjArgs).
 #pragma once
 
 #include "sgn_kernels.cuh"
 
 namespace sgn {
 
-// scratch layout (planes): products and 1/h (N_OPS), x weights (12), y weights (12)
+// scratch layout (planes): products and 1/h at their OP_ slots (the state planes
+// themselves are read from the state), x weights (11), y weights (11)
+constexpr int ADJ_NW = 11;
 constexpr int ADJ_WX = N_OPS;
-constexpr int ADJ_WY = N_OPS + 12;
-constexpr int ADJ_SCRATCH_PLANES = N_OPS + 24;
+constexpr int ADJ_WY = N_OPS + ADJ_NW;
+constexpr int ADJ_SCRATCH_PLANES = N_OPS + 2 * ADJ_NW;
 constexpr int ADJ_BLOCK = 256;
 
-// weight slots: x uses {H,U,V,W,ETA,B,HS,UU,HU,HUV,HUW,E2H},
-// y uses {H,U,V,W,ETA,B,HS,VV,HV,HUV,HVW,E2H}
-enum { VW_H, VW_U, VW_V, VW_W, VW_ETA, VW_B, VW_HS, VW_SQ, VW_HM, VW_HUV, VW_HMW, VW_E2H };
+// weight slots: x uses {H,U,V,W,E15,HS,UU,HU,HUV,HUW,E2H},
+// y uses {H,U,V,W,E15,HS,VV,HV,HUV,HVW,E2H}.  eta and b enter the forward RHS
+// only through eta + 3/2 b, so one E15 slot carries both (d/d eta = 1, d/d b = 3/2).
+enum { VW_H, VW_U, VW_V, VW_W, VW_E15, VW_HS, VW_SQ, VW_HM, VW_HUV, VW_HMW, VW_E2H };
 
 enum { ADJ_MODE_RHS = 0, ADJ_MODE_STAGE = 1 };
+
+// Per-direction constants of the pointwise part, for interior rows ([0]) and
+// the one-sided boundary rows ([1]): s = row factor of D, hs = s/2, gs = g s,
+// l6s = (lambda/6) s.
+struct AdjDir {
+    double s, hs, gs, l6s;
+};
 
 struct AdjArgs {
     const double* X;       // state at which the Jacobian is taken (5 planes)
     const double* b;       // bathymetry
-    const double* A;       // cotangent (5 planes), used as a_scale * A
-    double a_scale;
+    const double* A;       // cotangent direction (5 planes); the cotangent is sigma * A
+    double sigma;          // scale of the cotangent, applied to every result
     double* scratch;       // ADJ_SCRATCH_PLANES planes
-    double* qbar;          // RHS mode: output J^T a (5 planes)
+    double* qbar;          // RHS mode: output J^T (sigma A) (5 planes)
     double* bbar;          // accumulated (1 plane)
-    // stage mode: Qbar = J^T a;  qacc_out = (first ? qprime : qacc_in) + Qbar;
-    //             Anext = c_prime * qprime + c_bar * Qbar (when Anext != nullptr)
+    // stage mode, with Qbar = J^T (sigma A):
+    //   qacc_out = (first ? qprime : qacc_in) + Qbar
+    //   Anext    = kappa * qprime + J^T A   (when Anext != nullptr)
+    // so that the next stage's cotangent c' qprime + cbar Qbar equals
+    // sigma' * Anext with sigma' = cbar sigma and kappa = c' / sigma'.
     const double* qprime;
     const double* qacc_in;
     double* qacc_out;
     double* Anext;
-    double c_prime, c_bar;
+    double kappa;
     int first;
     Geom G;
+    AdjDir kx[2], ky[2];
+    double m2lam3;         // -2 lambda / 3
+    double lam2x;          // 2 lambda
 };
 
-template <int BC>
-__device__ __forceinline__ double row_scale(int k, int n, double c2, double c1) {
-    if (BC == BC_REFLECTING && (k == 0 || k == n - 1)) return c1;
-    return c2;
+// Host: the derived constants of AdjArgs.
+inline void fill_adj_constants(AdjArgs& a) {
+    const Geom& G = a.G;
+    const double sx[2] = {G.cx2, G.cx1}, sy[2] = {G.cy2, G.cy1};
+    for (int k = 0; k < 2; k++) {
+        a.kx[k] = {sx[k], 0.5 * sx[k], G.g * sx[k], G.lam6 * sx[k]};
+        a.ky[k] = {sy[k], 0.5 * sy[k], G.g * sy[k], G.lam6 * sy[k]};
+    }
+    a.m2lam3 = -2.0 * G.lam3;
+    a.lam2x = 2.0 * G.lam;
 }
 
-// Pass 1: products, 1/h and the direction weights V^x, V^y of one node.
+// x with its sign bit flipped where m has it set (an exact negation).
+__device__ __forceinline__ double flip_sign(double x, unsigned long long m) {
+    return __longlong_as_double((long long)((unsigned long long)__double_as_longlong(x) ^ m));
+}
+
+// Pass 1: products, 1/h and the direction weights V^x, V^y of one node
+// (for the cotangent direction A; sigma is applied by the gather pass).
 template <int BC>
 __global__ void __launch_bounds__(ADJ_BLOCK) k_adj_weights(AdjArgs a) {
     const Geom& G = a.G;
@@ -75,64 +108,60 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adj_weights(AdjArgs a) {
     const double eta = a.X[4 * P + c], bb = a.b[c];
     const double r = recip<double>(h);
     const double hu = h * u, hv = h * v, hw = h * w;
+    const double hsum = h + bb, rho = eta * r;
     double* S = a.scratch;
-    S[OP_H * P + c] = h;
-    S[OP_U * P + c] = u;
-    S[OP_V * P + c] = v;
-    S[OP_W * P + c] = w;
-    S[OP_ETA * P + c] = eta;
-    S[OP_B * P + c] = bb;
-    S[OP_HS * P + c] = h * (h + bb);
-    S[OP_UU * P + c] = u * u;
-    S[OP_VV * P + c] = v * v;
+    S[OP_HS * P + c] = h * hsum;
     S[OP_HU * P + c] = hu;
     S[OP_HV * P + c] = hv;
     S[OP_HUV * P + c] = hu * v;
     S[OP_HUW * P + c] = hu * w;
     S[OP_HVW * P + c] = hv * w;
-    S[OP_E2H * P + c] = eta * eta * r;
+    S[OP_E2H * P + c] = rho * eta;
+    S[OP_E15 * P + c] = fma(1.5, bb, eta);
     S[OP_R * P + c] = r;
 
-    const double s = a.a_scale;
-    const double ah = s * a.A[c], au = s * a.A[P + c], av = s * a.A[2 * P + c];
-    const double aw = s * a.A[3 * P + c], ae = s * a.A[4 * P + c];
-    const double rho = eta * r, om = 1.0 - rho;
-    const double cc = G.lam6 * rho * rho - G.g * (h + bb);   // common part of C1, C2
-    const double ra = -r * au, rb = -r * av, rc = -0.5 * r * aw;  // d k / d B for u, v, w
-    // x weights (row factor of column i)
+    const double ah = a.A[c], au = a.A[P + c], av = a.A[2 * P + c];
+    const double aw = a.A[3 * P + c], ae = a.A[4 * P + c];
+    const double lom = G.lam3 * (1.0 - rho);                       // lam/3 (1 - rho)
+    const double cc = fma(G.lam6 * rho, rho, -G.g * hsum);         // lam/6 rho^2 - g (h + b)
+    const double ra = -r * au, rb = -r * av, rc = (-0.5 * r) * aw; // d k / d B for u, v, w
+    const double uv = u * v;
+    // x weights (row factor s of column i)
     {
-        const double sx = row_scale<BC>(i, G.nx, G.cx2, G.cx1);
-        const double ru = sx * ra, rv = sx * rb, rw = sx * rc, sah = sx * ah, sae = sx * ae;
+        const bool wall = BC == BC_REFLECTING && (i == 0 || i == G.nx - 1);
+        const double sx = wall ? a.kx[1].s : a.kx[0].s, hsx = wall ? a.kx[1].hs : a.kx[0].hs;
+        const double ru = sx * ra, rw = sx * rc, sah = sx * ah, sae = sx * ae;
+        const double hru = 0.5 * ru, hrv = hsx * rb;
         double* W = S + ADJ_WX * P + c;
-        W[VW_H * P] = -u * sah + ru * (cc - 0.5 * u * u) - 0.5 * rv * (u * v) - rw * (u * w);
-        W[VW_U * P] = -h * sah - 0.5 * ru * hu - 0.5 * rv * hv - rw * hw;
-        W[VW_V * P] = 0.5 * rv * hu;
+        W[VW_H * P] = fma(-rw, u * w, fma(-hrv, uv, fma(-u, sah, ru * fma(-0.5 * u, u, cc))));
+        W[VW_U * P] = fma(-rw, hw, fma(-hrv, hv, fma(-hru, hu, -h * sah)));
+        W[VW_V * P] = hrv * hu;
         W[VW_W * P] = rw * hu;
-        W[VW_ETA * P] = ru * G.lam3 * om - u * sae;
-        W[VW_B * P] = ru * G.lam2 * om - 1.5 * u * sae;
+        W[VW_E15 * P] = fma(ru, lom, -u * sae);
         W[VW_HS * P] = ru * G.g;
-        W[VW_SQ * P] = 0.5 * ru * h;      // u^2
-        W[VW_HM * P] = 0.5 * ru * u;      // hu
-        W[VW_HUV * P] = 0.5 * rv;
-        W[VW_HMW * P] = rw;               // huw
+        W[VW_SQ * P] = hru * h;          // u^2
+        W[VW_HM * P] = hru * u;          // hu
+        W[VW_HUV * P] = hrv;
+        W[VW_HMW * P] = rw;              // huw
         W[VW_E2H * P] = -G.lam6 * ru;
     }
-    // y weights (row factor of row j)
+    // y weights (row factor s of row j)
     {
-        const double sy = row_scale<BC>(j, G.ny, G.cy2, G.cy1);
-        const double ru = sy * ra, rv = sy * rb, rw = sy * rc, sah = sy * ah, sae = sy * ae;
+        const bool wall = BC == BC_REFLECTING && (j == 0 || j == G.ny - 1);
+        const double sy = wall ? a.ky[1].s : a.ky[0].s, hsy = wall ? a.ky[1].hs : a.ky[0].hs;
+        const double rv = sy * rb, rw = sy * rc, sah = sy * ah, sae = sy * ae;
+        const double hrv = 0.5 * rv, hru = hsy * ra;
         double* W = S + ADJ_WY * P + c;
-        W[VW_H * P] = -v * sah + rv * (cc - 0.5 * v * v) - 0.5 * ru * (u * v) - rw * (v * w);
-        W[VW_V * P] = -h * sah - 0.5 * rv * hv - 0.5 * ru * hu - rw * hw;
-        W[VW_U * P] = 0.5 * ru * hv;
+        W[VW_H * P] = fma(-rw, v * w, fma(-hru, uv, fma(-v, sah, rv * fma(-0.5 * v, v, cc))));
+        W[VW_V * P] = fma(-rw, hw, fma(-hru, hu, fma(-hrv, hv, -h * sah)));
+        W[VW_U * P] = hru * hv;
         W[VW_W * P] = rw * hv;
-        W[VW_ETA * P] = rv * G.lam3 * om - v * sae;
-        W[VW_B * P] = rv * G.lam2 * om - 1.5 * v * sae;
+        W[VW_E15 * P] = fma(rv, lom, -v * sae);
         W[VW_HS * P] = rv * G.g;
-        W[VW_SQ * P] = 0.5 * rv * h;      // v^2
-        W[VW_HM * P] = 0.5 * rv * v;      // hv
-        W[VW_HUV * P] = 0.5 * ru;
-        W[VW_HMW * P] = rw;               // hvw
+        W[VW_SQ * P] = hrv * h;          // v^2
+        W[VW_HM * P] = hrv * v;          // hv
+        W[VW_HUV * P] = hru;
+        W[VW_HMW * P] = rw;              // hvw
         W[VW_E2H * P] = -G.lam6 * rv;
     }
 }
@@ -162,117 +191,136 @@ __global__ void __launch_bounds__(ADJ_BLOCK, 2) k_adj_gather(AdjArgs a) {
         ct = j < G.ny - 1 ? c + G.nx : c;
     }
 
-    // ---- product part: gathers of the neighbours' weights
-    double pb[N_OPS - 1];
-#pragma unroll
-    for (int k = 0; k < N_OPS - 1; k++) pb[k] = 0.0;
-    {
-        const bool has_l = BC == BC_PERIODIC || i >= 1;
-        const bool has_r = BC == BC_PERIODIC || i <= G.nx - 2;
-        const double self = (BC == BC_REFLECTING) ? ((i == G.nx - 1 ? 1.0 : 0.0) - (i == 0 ? 1.0 : 0.0)) : 0.0;
-        const int slot_of[12] = {OP_H, OP_U, OP_V, OP_W, OP_ETA, OP_B, OP_HS, OP_UU, OP_HU, OP_HUV, OP_HUW, OP_E2H};
-#pragma unroll
-        for (int k = 0; k < 12; k++) {
-            const double* V = S + (ADJ_WX + k) * P;
-            double g = 0.0;
-            if (BC == BC_REFLECTING && self != 0.0) g = self * V[c];
-            if (has_l) g += V[cl];
-            if (has_r) g -= V[cr];
-            pb[slot_of[k]] += g;
-        }
-    }
-    {
-        const bool has_b = BC == BC_PERIODIC || j >= 1;
-        const bool has_t = BC == BC_PERIODIC || j <= G.ny - 2;
-        const double self = (BC == BC_REFLECTING) ? ((j == G.ny - 1 ? 1.0 : 0.0) - (j == 0 ? 1.0 : 0.0)) : 0.0;
-        const int slot_of[12] = {OP_H, OP_U, OP_V, OP_W, OP_ETA, OP_B, OP_HS, OP_VV, OP_HV, OP_HUV, OP_HVW, OP_E2H};
-#pragma unroll
-        for (int k = 0; k < 12; k++) {
-            const double* V = S + (ADJ_WY + k) * P;
-            double g = 0.0;
-            if (BC == BC_REFLECTING && self != 0.0) g = self * V[c];
-            if (has_b) g += V[cb];
-            if (has_t) g -= V[ct];
-            pb[slot_of[k]] += g;
-        }
-    }
-
-    // ---- pointwise part: d k / d q at this node with every difference fixed
-    double sx = G.cx2, sy = G.cy2, sgx = 0.0, sgy = 0.0;
+    // ---- product part: gathers of the neighbours' weights.  At a reflecting
+    // wall the clamped neighbour index is the node itself and its weight enters
+    // with a flipped sign (the one-sided end rows of the SBP operator).
+    unsigned long long fl = 0ull, fr = 0ull, fb = 0ull, ft = 0ull;
     if (BC == BC_REFLECTING) {
-        if (i == 0) { sx = G.cx1; sgx = -G.satx; }
-        if (i == G.nx - 1) { sx = G.cx1; sgx = G.satx; }
-        if (j == 0) { sy = G.cy1; sgy = -G.saty; }
-        if (j == G.ny - 1) { sy = G.cy1; sgy = G.saty; }
+        const unsigned long long sgn_bit = 0x8000000000000000ull;
+        fl = i == 0 ? sgn_bit : 0ull;
+        fr = i == G.nx - 1 ? sgn_bit : 0ull;
+        fb = j == 0 ? sgn_bit : 0ull;
+        ft = j == G.ny - 1 ? sgn_bit : 0ull;
     }
-#define DX_(op) (sx * (S[(op) * P + cr] - S[(op) * P + cl]))
-#define DY_(op) (sy * (S[(op) * P + ct] - S[(op) * P + cb]))
-    const double h = S[OP_H * P + c], u = S[OP_U * P + c], v = S[OP_V * P + c];
-    const double w = S[OP_W * P + c], eta = S[OP_ETA * P + c], bb = S[OP_B * P + c];
-    const double r = S[OP_R * P + c];
-    const double sc = a.a_scale;
-    const double ah = sc * a.A[c], au = sc * a.A[P + c], av = sc * a.A[2 * P + c];
-    const double aw = sc * a.A[3 * P + c], ae = sc * a.A[4 * P + c];
-    const double rho = eta * r, om = 1.0 - rho, sfs = h + bb;
-    const double hu = h * u, hv = h * v, hw = h * w, uv = u * v, uw = u * w, vw_ = v * w;
-    const double xh = DX_(OP_H), xu = DX_(OP_U), xv = DX_(OP_V), xw = DX_(OP_W), xe = DX_(OP_ETA), xb = DX_(OP_B);
-    const double yh = DY_(OP_H), yu = DY_(OP_U), yv = DY_(OP_V), yw = DY_(OP_W), ye = DY_(OP_ETA), yb = DY_(OP_B);
-    const double xhs = DX_(OP_HS), xuu = DX_(OP_UU), xhu = DX_(OP_HU), xhuv = DX_(OP_HUV), xhuw = DX_(OP_HUW);
-    const double xe2h = DX_(OP_E2H);
-    const double yhs = DY_(OP_HS), yvv = DY_(OP_VV), yhv = DY_(OP_HV), yhuv = DY_(OP_HUV), yhvw = DY_(OP_HVW);
-    const double ye2h = DY_(OP_E2H);
-#undef DX_
-#undef DY_
-    const double C1 = G.lam6 * rho * rho - G.g * sfs - 0.5 * u * u;
-    const double C2 = G.lam6 * rho * rho - G.g * sfs - 0.5 * v * v;
-    const double Bu = xh * C1 + xe * G.lam3 * om + xb * G.lam2 * om + G.g * xhs + 0.5 * h * xuu
-                    + 0.5 * u * xhu - 0.5 * hu * xu - G.lam6 * xe2h
-                    + 0.5 * (yhuv - uv * yh + hv * yu - hu * yv);
-    const double Bv = yh * C2 + ye * G.lam3 * om + yb * G.lam2 * om + G.g * yhs + 0.5 * h * yvv
-                    + 0.5 * v * yhv - 0.5 * hv * yv - G.lam6 * ye2h
-                    + 0.5 * (xhuv - uv * xh + hu * xv - hv * xu);
-    const double Bw = G.lam * om - 0.5 * (xhuw + hu * xw - uw * xh - hw * xu
-                                          + yhvw + hv * yw - vw_ * yh - hw * yv);
-    const double ku = -r * Bu, kv = -r * Bv, kw = r * Bw;
-    const double lr = G.lam3 * rho * r;
-    const double dBu_dh = xh * (-G.lam3 * rho * rho * r - G.g) + xe * lr + xb * G.lam2 * rho * r
-                        + 0.5 * xuu - 0.5 * u * xu + 0.5 * (v * yu - u * yv);
-    const double dBv_dh = yh * (-G.lam3 * rho * rho * r - G.g) + ye * lr + yb * G.lam2 * rho * r
-                        + 0.5 * yvv - 0.5 * v * yv + 0.5 * (u * xv - v * xu);
-    const double dBw_dh = G.lam * rho * r - 0.5 * (u * xw - w * xu + v * yw - w * yv);
+    const double* __restrict__ WX = S + ADJ_WX * P;
+    const double* __restrict__ WY = S + ADJ_WY * P;
+#define GX_(k) (flip_sign(WX[(k) * P + cl], fl) - flip_sign(WX[(k) * P + cr], fr))
+#define GY_(k) (flip_sign(WY[(k) * P + cb], fb) - flip_sign(WY[(k) * P + ct], ft))
+    const double pH = GX_(VW_H) + GY_(VW_H), pU = GX_(VW_U) + GY_(VW_U);
+    const double pV = GX_(VW_V) + GY_(VW_V), pW = GX_(VW_W) + GY_(VW_W);
+    const double pF = GX_(VW_E15) + GY_(VW_E15), pHS = GX_(VW_HS) + GY_(VW_HS);
+    const double pHUV = GX_(VW_HUV) + GY_(VW_HUV), pE2H = GX_(VW_E2H) + GY_(VW_E2H);
+    const double pUU = GX_(VW_SQ), pHU = GX_(VW_HM), pHUW = GX_(VW_HMW);
+    const double pVV = GY_(VW_SQ), pHV = GY_(VW_HM), pHVW = GY_(VW_HMW);
+#undef GX_
+#undef GY_
 
-    double hb = ah * (-(xu + yv) + sgx * u + sgy * v)
-              + au * (-r * ku - r * dBu_dh) + av * (-r * kv - r * dBv_dh) + aw * (-r * kw + r * dBw_dh);
-    double ub = ah * (-xh + sgx * h) - au * r * (-u * xh + 0.5 * xhu - 0.5 * h * xu - 0.5 * (v * yh + h * yv))
-              - av * r * 0.5 * (-v * xh + h * xv) - aw * 0.5 * r * (h * xw - w * xh) - ae * (xe + 1.5 * xb);
-    double vb = ah * (-yh + sgy * h) - au * r * 0.5 * (-u * yh + h * yu)
-              - av * r * (-v * yh + 0.5 * yhv - 0.5 * h * yv - 0.5 * (u * xh + h * xu))
-              - aw * 0.5 * r * (h * yw - w * yh) - ae * (ye + 1.5 * yb);
-    double wb = aw * 0.5 * r * (u * xh + h * xu + v * yh + h * yv) + ae;
-    double eb = -au * r * (xh * lr - xe * G.lam3 * r - xb * G.lam2 * r)
-              - av * r * (yh * lr - ye * G.lam3 * r - yb * G.lam2 * r) - aw * G.lam * r * r;
-    double bbar = r * G.g * (au * xh + av * yh);
+    // ---- pointwise part: d k / d q at this node with every difference fixed.
+    // With k_u = -r B_u, k_w = r B_w (B the brackets of the forward kernel) the
+    // h-derivatives combine as d(k_u)/dh = r^2 G_u, d(k_v)/dh = r^2 G_v,
+    // d(k_w)/dh = r^2 G_w, where (using r h = 1; the dropped terms are rounding)
+    //   G_u = D_x h (lam/2 rho^2 - u^2/2 - g b) + lam/3 (1 - 2 rho) D_x(eta + 3/2 b)
+    //         + g D_x(h(h+b)) + u/2 D_x(hu) - lam/6 D_x(eta^2/h) + (D_y(huv) - uv D_y h)/2,
+    //   G_w = lam (2 rho - 1) + (D_x(huw) - uw D_x h + D_y(hvw) - vw D_y h)/2,
+    // eta and b enter only through D(eta + 3/2 b), and r h = 1 also reduces the
+    // u-, v- and w-derivatives to the forms below.
+    const bool wx = BC == BC_REFLECTING && (i == 0 || i == G.nx - 1);
+    const bool wy = BC == BC_REFLECTING && (j == 0 || j == G.ny - 1);
+    const AdjDir kx = wx ? a.kx[1] : a.kx[0];
+    const AdjDir ky = wy ? a.ky[1] : a.ky[0];
+    double sgx = 0.0, sgy = 0.0;
+    if (BC == BC_REFLECTING) {
+        if (i == 0) sgx = -G.satx;
+        if (i == G.nx - 1) sgx = G.satx;
+        if (j == 0) sgy = -G.saty;
+        if (j == G.ny - 1) sgy = G.saty;
+    }
+    const double* __restrict__ X = a.X;
+#define RX_(base) ((base)[cr] - (base)[cl])
+#define RY_(base) ((base)[ct] - (base)[cb])
+    const double h = X[c], u = X[P + c], v = X[2 * P + c], w = X[3 * P + c], eta = X[4 * P + c];
+    const double bb = a.b[c];
+    const double r = S[OP_R * P + c];
+    const double ah = a.A[c], au = a.A[P + c], av = a.A[2 * P + c];
+    const double aw = a.A[3 * P + c], ae = a.A[4 * P + c];
+    // differences used more than once, scaled
+    const double xh = kx.s * RX_(X), xu = kx.s * RX_(X + P), xv = kx.s * RX_(X + 2 * P);
+    const double xw = kx.s * RX_(X + 3 * P), xf = kx.s * RX_(S + OP_E15 * P);
+    const double yh = ky.s * RY_(X), yu = ky.s * RY_(X + P), yv = ky.s * RY_(X + 2 * P);
+    const double yw = ky.s * RY_(X + 3 * P), yf = ky.s * RY_(S + OP_E15 * P);
+    const double hxhu = kx.hs * RX_(S + OP_HU * P), hyhv = ky.hs * RY_(S + OP_HV * P);  // D(hu)/2, D(hv)/2
+
+    const double ar = r * au, br = r * av, cr_ = r * aw;
+    const double rho = eta * r, rho2 = rho * rho;
+    const double hu = h * u, hv = h * v, hw = h * w, uv = u * v, uw = u * w, vw_ = v * w;
+    const double q2 = fma(G.lam2, rho2, -G.g * bb);       // lam/2 rho^2 - g b
+    const double l12 = fma(a.m2lam3, rho, G.lam3);        // lam/3 (1 - 2 rho)
+    const double huv = 0.5 * uv;
+    double Gu = xh * fma(-0.5 * u, u, q2);
+    Gu = fma(l12, xf, Gu);
+    Gu = fma(kx.gs, RX_(S + OP_HS * P), Gu);
+    Gu = fma(u, hxhu, Gu);
+    Gu = fma(-kx.l6s, RX_(S + OP_E2H * P), Gu);
+    Gu = fma(ky.hs, RY_(S + OP_HUV * P), Gu);
+    Gu = fma(-huv, yh, Gu);
+    double Gv = yh * fma(-0.5 * v, v, q2);
+    Gv = fma(l12, yf, Gv);
+    Gv = fma(ky.gs, RY_(S + OP_HS * P), Gv);
+    Gv = fma(v, hyhv, Gv);
+    Gv = fma(-ky.l6s, RY_(S + OP_E2H * P), Gv);
+    Gv = fma(kx.hs, RX_(S + OP_HUV * P), Gv);
+    Gv = fma(-huv, xh, Gv);
+    double Gw = fma(a.lam2x, rho, -G.lam);
+    Gw = fma(kx.hs, RX_(S + OP_HUW * P), Gw);
+    Gw = fma(ky.hs, RY_(S + OP_HVW * P), Gw);
+    Gw = fma(-0.5, fma(uw, xh, vw_ * yh), Gw);
+#undef RX_
+#undef RY_
+
+    const double divu = xu + yv;
+    double hb = fma(-ah, divu, r * fma(ar, Gu, fma(br, Gv, cr_ * Gw)));
+    const double aru = ar * u, brv = br * v, crw = cr_ * w;
+    const double hau = 0.5 * au, hav = 0.5 * av, haw = 0.5 * aw;
+    double ub = xh * (fma(0.5, brv + crw, aru) - ah);
+    ub = fma(ar, fma(0.5 * v, yh, -hxhu), ub);
+    ub = fma(-ae, xf, fma(-haw, xw, fma(-hav, xv, fma(hau, divu, ub))));
+    double vb = yh * (fma(0.5, aru + crw, brv) - ah);
+    vb = fma(br, fma(0.5 * u, xh, -hyhv), vb);
+    vb = fma(-ae, yf, fma(-haw, yw, fma(-hau, yu, fma(hav, divu, vb))));
+    double wb = fma(0.5 * cr_, fma(u, xh, v * yh), fma(haw, divu, ae));
+    // d/d eta: only rho and 1 - rho depend on eta (d rho / d eta = r)
+    double eb = fma(ar, fma(rho, xh, -xf), br * fma(rho, yh, -yf));
+    eb = -r * fma(G.lam3, eb, G.lam * cr_);
+    double bbar = G.g * fma(ar, xh, br * yh);
+    if (BC == BC_REFLECTING) {
+        // SAT of the h equation: d/dh and d/du, d/dv of (sgx hu + sgy hv)
+        hb = fma(ah, fma(sgx, u, sgy * v), hb);
+        ub = fma(ah * sgx, h, ub);
+        vb = fma(ah * sgy, h, vb);
+    }
 
     // ---- chain rule through the products
-    hb += pb[OP_H] + (2.0 * h + bb) * pb[OP_HS] + u * pb[OP_HU] + v * pb[OP_HV] + uv * pb[OP_HUV]
-        + uw * pb[OP_HUW] + vw_ * pb[OP_HVW] - rho * rho * pb[OP_E2H];
-    ub += pb[OP_U] + 2.0 * u * pb[OP_UU] + h * pb[OP_HU] + hv * pb[OP_HUV] + hw * pb[OP_HUW];
-    vb += pb[OP_V] + 2.0 * v * pb[OP_VV] + h * pb[OP_HV] + hu * pb[OP_HUV] + hw * pb[OP_HVW];
-    wb += pb[OP_W] + hu * pb[OP_HUW] + hv * pb[OP_HVW];
-    eb += pb[OP_ETA] + 2.0 * rho * pb[OP_E2H];
-    bbar += pb[OP_B] + h * pb[OP_HS];
+    hb = fma(-rho2, pE2H, fma(vw_, pHVW, fma(uw, pHUW, fma(uv, pHUV, fma(v, pHV, fma(u, pHU,
+         fma(fma(2.0, h, bb), pHS, hb + pH)))))));
+    ub = fma(hw, pHUW, fma(hv, pHUV, fma(h, pHU, fma(2.0 * u, pUU, ub + pU))));
+    vb = fma(hw, pHVW, fma(hu, pHUV, fma(h, pHV, fma(2.0 * v, pVV, vb + pV))));
+    wb = fma(hv, pHVW, fma(hu, pHUW, wb + pW));
+    eb = fma(2.0 * rho, pE2H, eb + pF);
+    bbar = fma(h, pHS, fma(1.5, pF, bbar));
 
     const double qb[5] = {hb, ub, vb, wb, eb};
-    a.bbar[c] += bbar;
+    const double sg = a.sigma;
+    a.bbar[c] = fma(sg, bbar, a.bbar[c]);
     if (MODE == ADJ_MODE_RHS) {
 #pragma unroll
-        for (int f = 0; f < 5; f++) a.qbar[f * P + c] = qb[f];
+        for (int f = 0; f < 5; f++) a.qbar[f * P + c] = sg * qb[f];
     } else {
 #pragma unroll
         for (int f = 0; f < 5; f++) {
-            const double base = a.first ? a.qprime[f * P + c] : a.qacc_in[f * P + c];
-            a.qacc_out[f * P + c] = base + qb[f];
-            if (a.Anext) a.Anext[f * P + c] = a.c_prime * a.qprime[f * P + c] + a.c_bar * qb[f];
+            const double qp = a.qprime[f * P + c];
+            const double base = a.first ? qp : a.qacc_in[f * P + c];
+            a.qacc_out[f * P + c] = fma(sg, qb[f], base);
+            if (a.Anext) a.Anext[f * P + c] = fma(a.kappa, qp, qb[f]);
         }
     }
 }

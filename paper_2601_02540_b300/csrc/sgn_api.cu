@@ -478,10 +478,11 @@ sgn_status sgn_rhs_vjp(sgn_ctx* c, const void* q_dev, const void* abar_dev, void
     a.X = static_cast<const double*>(q_dev);
     a.b = c->b64;
     a.A = static_cast<const double*>(abar_dev);
-    a.a_scale = 1.0;
+    a.sigma = 1.0;
     a.qbar = static_cast<double*>(qbar_dev);
     a.bbar = static_cast<double*>(bbar_dev);
     a.G = c->G;
+    sgn::fill_adj_constants(a);
     cudaError_t e = adjoint<sgn::ADJ_MODE_RHS>(c, a, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "sgn_rhs_vjp");
     return SGN_OK;
@@ -526,6 +527,13 @@ sgn_status sgn_step_vjp(sgn_ctx* c, const void* stash_dev, void* qbar_dev, void*
     double* qacc = c->adj;
     double* A0 = c->adj + P5;
     double* A1 = c->adj + 2 * P5;
+    // The cotangent of stage s is sigma_s * A_s: sigma_4 = dt/6, A_4 = qbar', and
+    // k_{s-1} = c' qbar' + cbar Qbar_s gives sigma_{s-1} = cbar sigma_s and
+    // A_{s-1} = (c' / sigma_{s-1}) qbar' + J^T A_s (one FMA per value).
+    const double sig4 = dt / 6.0, sig3 = dt * sig4, sig2 = 0.5 * dt * sig3, sig1 = 0.5 * dt * sig2;
+    const double kap3 = (dt / 3.0) / sig3, kap2 = (dt / 3.0) / sig2, kap1 = (dt / 6.0) / sig1;
+    if (!(std::isnormal(sig1) && std::isfinite(kap1)))
+        return fail(SGN_E_INVAL, "dt = %g is outside the range of the scaled adjoint recurrence", dt);
     sgn::AdjArgs a;
     std::memset(&a, 0, sizeof(a));
     a.b = c->b64;
@@ -533,20 +541,21 @@ sgn_status sgn_step_vjp(sgn_ctx* c, const void* stash_dev, void* qbar_dev, void*
     a.bbar = static_cast<double*>(bbar_dev);
     a.qprime = qbar;
     a.G = c->G;
+    sgn::fill_adj_constants(a);
     cudaError_t e;
     // stage 4: k4bar = dt/6 qbar'; Q4bar = J(Q4)^T k4bar; k3bar = dt/3 qbar' + dt Q4bar
-    a.X = stash + 3 * P5; a.A = qbar; a.a_scale = dt / 6.0;
-    a.first = 1; a.qacc_out = qacc; a.Anext = A0; a.c_prime = dt / 3.0; a.c_bar = dt;
+    a.X = stash + 3 * P5; a.A = qbar; a.sigma = sig4;
+    a.first = 1; a.qacc_out = qacc; a.Anext = A0; a.kappa = kap3;
     if ((e = adjoint<sgn::ADJ_MODE_STAGE>(c, a, s)) != cudaSuccess) return cuda_fail(e, "sgn_step_vjp");
     // stage 3: Q3bar = J(Q3)^T k3bar; k2bar = dt/3 qbar' + dt/2 Q3bar
-    a.X = stash + 2 * P5; a.A = A0; a.a_scale = 1.0;
-    a.first = 0; a.qacc_in = qacc; a.qacc_out = qacc; a.Anext = A1; a.c_prime = dt / 3.0; a.c_bar = dt / 2.0;
+    a.X = stash + 2 * P5; a.A = A0; a.sigma = sig3;
+    a.first = 0; a.qacc_in = qacc; a.qacc_out = qacc; a.Anext = A1; a.kappa = kap2;
     if ((e = adjoint<sgn::ADJ_MODE_STAGE>(c, a, s)) != cudaSuccess) return cuda_fail(e, "sgn_step_vjp");
     // stage 2: Q2bar = J(Q2)^T k2bar; k1bar = dt/6 qbar' + dt/2 Q2bar
-    a.X = stash + P5; a.A = A1; a.Anext = A0; a.c_prime = dt / 6.0; a.c_bar = dt / 2.0;
+    a.X = stash + P5; a.A = A1; a.sigma = sig2; a.Anext = A0; a.kappa = kap1;
     if ((e = adjoint<sgn::ADJ_MODE_STAGE>(c, a, s)) != cudaSuccess) return cuda_fail(e, "sgn_step_vjp");
     // stage 1: Q1bar = J(q_n)^T k1bar; qbar = qbar' + Q1bar + Q2bar + Q3bar + Q4bar
-    a.X = stash; a.A = A0; a.Anext = nullptr; a.qacc_out = qbar;
+    a.X = stash; a.A = A0; a.sigma = sig1; a.Anext = nullptr; a.qacc_out = qbar;
     if ((e = adjoint<sgn::ADJ_MODE_STAGE>(c, a, s)) != cudaSuccess) return cuda_fail(e, "sgn_step_vjp");
     return SGN_OK;
 }

@@ -189,3 +189,19 @@ def test_rollout_gradient_matches_finite_differences():
         adj = float(np.sum(gb * d[0]) + np.sum(gh * d[1]))
         assert abs(adj - fd) <= 1e-5 * abs(adj), (adj, fd)
     p.b, p.q0[0] = b0, h00
+
+
+def test_step_vjp_rejects_dt_outside_scaled_range():
+    """The stage cotangents carry the factor dt^4/24; a dt that underflows it is
+    refused before any launch, and qbar is left untouched."""
+    p = inputs.smooth_state(16, 9, PERIODIC, seed=2)
+    s = sgn.Solver.from_problem(p)
+    stash = torch.empty((1, 20, p.ny, p.nx), dtype=torch.float64, device="cuda")
+    s.step_record(_t(p.q0), p.dt, 1, stash)
+    qbar = _t(np.ones_like(p.q0))
+    bbar = torch.zeros((p.ny, p.nx), dtype=torch.float64, device="cuda")
+    with pytest.raises(sgn.SgnError) as ei:
+        s.step_vjp(stash[0], qbar, bbar, 1e-90)
+    assert ei.value.status == 1          # SGN_E_INVAL
+    assert torch.equal(qbar, _t(np.ones_like(p.q0)))
+    s.close()
