@@ -356,13 +356,17 @@ def _ensemble(torch, steps: int, warmup: int) -> dict:
             "mass_finite": bool(np.all(np.isfinite(d)))}
 
 
-def _adjoint(torch) -> dict:
+def _adjoint(torch, nsteps: int = 0) -> dict:
     """Inversion workload: 512^2 reflecting, 2000 RK4 steps, 16 gauges read
     every 10 steps, checkpoints every 100 steps; time of the forward rollout
-    (with checkpoints) and of the backward pass (segment recomputation with
-    stage stashes + adjoint steps)."""
+    (with checkpoints; the last segment keeps its stage states) and of the
+    backward pass (recomputation of the other segments with stage stashes +
+    adjoint steps), and the same with every stage state kept (no
+    recomputation)."""
     from paper_2601_02540_b300 import adjoint, sgn
     p = inputs.workload4()
+    if nsteps > 0:
+        p.nsteps = nsteps
     s = sgn.Solver.from_problem(p, prec="f64")
     gauges = torch.as_tensor(p.extra["gauges"], device="cuda")
     b = torch.as_tensor(p.b, device="cuda").requires_grad_(True)
@@ -373,7 +377,7 @@ def _adjoint(torch) -> dict:
     torch.sum((out - obs[: out.shape[0]]) ** 2).backward()
     b.grad = None
     h0.grad = None
-    res = {"workload": "reflecting 512x512, 2000 RK4 steps, 16 gauges every 10 steps, FP64"}
+    res = {"workload": f"reflecting 512x512, {p.nsteps} RK4 steps, 16 gauges every 10 steps, FP64"}
     for name, K in (("checkpoint_K100", 100), ("all_stages_kept", 0)):
         b.grad = None
         h0.grad = None
@@ -388,6 +392,7 @@ def _adjoint(torch) -> dict:
         t2 = time.perf_counter()
         fwd, bwd = t1 - t0, t2 - t1
         res[name] = {"forward_s": fwd, "backward_s": bwd, "backward_over_forward": bwd / fwd,
+                     "total_over_forward": (fwd + bwd) / fwd,
                      "stash_gb": (min(K, p.nsteps) if K > 0 else p.nsteps) * 20 * p.nx * p.ny * 8 / 1e9}
         del out, loss
         torch.cuda.empty_cache()
@@ -458,9 +463,15 @@ def main() -> None:
     ap.add_argument("--no-extra", action="store_true", help="skip the ensemble and adjoint legs")
     ap.add_argument("--size", type=int, default=8192,
                     help="grid side (8192 = the workload; smaller sizes only for profiling)")
+    ap.add_argument("--adjoint-only", type=int, default=0, metavar="NSTEPS",
+                    help="run only the adjoint leg with NSTEPS RK4 steps and print its JSON (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.adjoint_only > 0:
+        import torch
+        print(json.dumps({"adjoint": _adjoint(torch, args.adjoint_only)}))
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

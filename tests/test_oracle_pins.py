@@ -349,3 +349,17 @@ def test_gauge_loss_special_cases():
     fd = (O.gauge_loss(g, p.b + e * db, q0 + e * dq, p.dt, 12, 3, gauges, obs)
           - O.gauge_loss(g, p.b - e * db, q0 - e * dq, p.dt, 12, 3, gauges, obs)) / (2 * e)
     assert abs(jv - fd) <= 1e-6 * abs(jv), (jv, fd)
+
+
+@pytest.mark.parametrize("bc", [PERIODIC, REFLECTING])
+@pytest.mark.parametrize("nx,ny", [(5, 3), (33, 17)])
+def test_rhs_scale_bounds_the_rhs(bc, nx, ny):
+    """The rounding scale S_f sums |coef| |D| |f| over the terms of the RHS
+    value (and |pointwise terms|), so by the triangle inequality it bounds
+    |k_f| at every node; it is what the parity tolerances multiply by u."""
+    p = inputs.smooth_state(nx, ny, bc, seed=4, xmax=1.3, ymax=0.9)
+    g = pins.grid_of(p)
+    k = O.rhs(g, p.b, p.q0)
+    S = O.rhs_scale(g, p.b, p.q0)
+    assert np.all(S >= np.abs(k) * (1 - 1e-14))
+    assert np.all(S > 0)
