@@ -128,7 +128,11 @@ def _bind(lib: ctypes.CDLL, pre: str, real: bool) -> None:
     ]
     if real:
         sig += [("rhs_scale", ctypes.c_int, [_P, _P, _P, _P]),
-                ("diagnostics", ctypes.c_int, [_P, _P, _P, _P])]
+                ("diagnostics", ctypes.c_int, [_P, _P, _P, _P]),
+                ("bs3_fixed", ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, _P]),
+                ("rk_adaptive", ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_int, _P, _P])]
     for name, res, args in sig:
         fn = getattr(lib, pre + name)
         fn.restype = res
@@ -194,6 +198,36 @@ class Oracle:
         g = grid.c()
         self._ok(self._r.orc_init_aux(ctypes.byref(g), _ptr(b), _ptr(q)), "init_aux")
         return q
+
+    def bs3_fixed(self, grid: Grid, b, q, dt: float, nsteps: int):
+        """The third-order FSAL pair of the adaptive integrator with a fixed
+        step (every step accepted): (q after nsteps, error vector e of the
+        last step)."""
+        b = _arr(b)
+        q = _arr(q).copy()
+        _check(grid, b, q)
+        e = np.zeros_like(q)
+        g = grid.c()
+        self._ok(self._r.orc_bs3_fixed(ctypes.byref(g), _ptr(b), _ptr(q), dt, nsteps, _ptr(e)),
+                 "bs3_fixed")
+        return q, e
+
+    def rk_adaptive(self, grid: Grid, b, q, t0: float, t_end: float, dt0: float,
+                    rtol: float = 1e-6, atol: float = 1e-6, max_attempts: int = 100000):
+        """Adaptive integration from t0 to t_end (Sec. 6): (q, history, stats)
+        with history[k] = (dt, err, accepted) of attempt k and stats =
+        {accepted, rejected, t, dt_next}."""
+        b = _arr(b)
+        q = _arr(q).copy()
+        _check(grid, b, q)
+        hist = np.zeros((max_attempts, 3))
+        st = np.zeros(4)
+        g = grid.c()
+        n = self._r.orc_rk_adaptive(ctypes.byref(g), _ptr(b), _ptr(q), t0, t_end, dt0, rtol, atol,
+                                    max_attempts, _ptr(hist), _ptr(st))
+        self._ok(0 if n >= 0 else n, "rk_adaptive")
+        return q, hist[:n].copy(), dict(accepted=int(st[0]), rejected=int(st[1]), t=float(st[2]),
+                                        dt_next=float(st[3]))
 
     def rk4(self, grid: Grid, b, q, dt: float, nsteps: int) -> np.ndarray:
         b = _arr(b)

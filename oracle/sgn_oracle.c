@@ -26,6 +26,7 @@
  *   Remark "Concrete SBP operators and SATs" (rem:concrete_sbp) operators, M, SATs
  *   Thm. 4.1 proof, eq. (splitcondition)    energy E and its derivatives
  *   Sec. 6, eq. (initialization)            eta = h and the initial w
+ *   Sec. 6 (time integration)               adaptive third-order FSAL pair
  */
 #include <stdlib.h>
 #include <string.h>
@@ -608,5 +609,125 @@ int orc_diagnostics(const orc_grid* G, const double* b, const double* q, double*
     out[4] = rsc.s + rsc.c;
     free(dq);
     return 0;
+}
+#endif
+
+/* ---- Adaptive time stepping (Sec. 6) -------------------------------------
+ * The paper integrates the semi-discretization with an explicit third-order
+ * Runge-Kutta pair that has the first-same-as-last (FSAL) property, an
+ * embedded error estimator and automatic step-size control, with relative and
+ * absolute tolerances 1e-6; it does not print the pair's coefficients.  The
+ * pair restated here is the third-order FSAL pair of Bogacki and Shampine
+ * (1989) with its embedded second-order solution:
+ *   k1 = f(q_n)                      (the k4 of the previous accepted step)
+ *   k2 = f(q_n + dt (1/2) k1)
+ *   k3 = f(q_n + dt (3/4) k2)
+ *   q_{n+1} = q_n + dt (2/9 k1 + 1/3 k2 + 4/9 k3)
+ *   k4 = f(q_{n+1})
+ *   qhat_{n+1} = q_n + dt (7/24 k1 + 1/4 k2 + 1/3 k3 + 1/8 k4)
+ *   e = q_{n+1} - qhat_{n+1} = dt sum_i (b_i - bhat_i) k_i
+ * Error of an attempt (root-mean-square over all 5 nx ny values):
+ *   err = sqrt( mean( (e / (atol + rtol max(|q_n|, |q_{n+1}|)))^2 ) ).
+ * Control: accept when err <= 1; the next step size is
+ *   dt * min(QMAX, max(QMIN, SAFETY err^(-1/3)))     (QMAX when err = 0)
+ * with SAFETY = 0.9, QMIN = 0.2, QMAX = 10; a rejected attempt is retried
+ * from q_n (k1 is kept).  A step that would pass t_end is cut to land on it. */
+#ifndef ORC_COMPLEX
+static const double BS_B[4] = {2.0 / 9.0, 1.0 / 3.0, 4.0 / 9.0, 0.0};
+static const double BS_BHAT[4] = {7.0 / 24.0, 1.0 / 4.0, 1.0 / 3.0, 1.0 / 8.0};
+#define BS_SAFETY 0.9
+#define BS_QMIN 0.2
+#define BS_QMAX 10.0
+
+/* One attempt of size dt from q (with k1 = f(q)): writes q1 = q_{n+1},
+ * k4 = f(q1) and the error vector e; returns err (or -1 on failure).
+ * work holds 3 * m values. */
+static double bs3_attempt(const orc_grid* G, const double* b, const double* q, const double* k1,
+                          double dt, double rtol, double atol, double* q1, double* k4, double* e,
+                          double* work)
+{
+    const long m = (long)NFIELD * G->nx * G->ny;
+    double *k2 = work, *k3 = work + m, *y = work + 2 * m;
+    for (long c = 0; c < m; c++) y[c] = q[c] + dt * (0.5 * k1[c]);
+    if (orc_rhs(G, b, y, k2)) return -1.0;
+    for (long c = 0; c < m; c++) y[c] = q[c] + dt * (0.75 * k2[c]);
+    if (orc_rhs(G, b, y, k3)) return -1.0;
+    for (long c = 0; c < m; c++)
+        q1[c] = q[c] + dt * (BS_B[0] * k1[c] + BS_B[1] * k2[c] + BS_B[2] * k3[c]);
+    if (orc_rhs(G, b, q1, k4)) return -1.0;
+    double s = 0.0;
+    for (long c = 0; c < m; c++) {
+        e[c] = dt * ((BS_B[0] - BS_BHAT[0]) * k1[c] + (BS_B[1] - BS_BHAT[1]) * k2[c]
+                     + (BS_B[2] - BS_BHAT[2]) * k3[c] + (BS_B[3] - BS_BHAT[3]) * k4[c]);
+        double sc = atol + rtol * fmax(fabs(q[c]), fabs(q1[c]));
+        double r = e[c] / sc;
+        s += r * r;
+    }
+    return sqrt(s / (double)m);
+}
+
+/* Fixed step size dt for nsteps steps (every step accepted), in place.  If
+ * e_last is not NULL it receives the error vector e of the last step. */
+int orc_bs3_fixed(const orc_grid* G, const double* b, double* q, double dt, int nsteps, double* e_last)
+{
+    const long m = (long)NFIELD * G->nx * G->ny;
+    double* buf = (double*)malloc(sizeof(double) * m * 7);
+    if (!buf) return -1;
+    double *k1 = buf, *k4 = buf + m, *q1 = buf + 2 * m, *e = buf + 3 * m, *work = buf + 4 * m;
+    int rc = orc_rhs(G, b, q, k1);
+    for (int n = 0; n < nsteps && rc == 0; n++) {
+        if (bs3_attempt(G, b, q, k1, dt, 1.0, 1.0, q1, k4, e, work) < 0.0) { rc = -1; break; }
+        memcpy(q, q1, sizeof(double) * m);
+        memcpy(k1, k4, sizeof(double) * m);
+        if (e_last) memcpy(e_last, e, sizeof(double) * m);
+    }
+    free(buf);
+    return rc;
+}
+
+/* Adaptive integration of q (in place) from t0 to t_end, first attempt dt0,
+ * at most max_attempts attempts.  hist (if not NULL) receives per attempt
+ * {dt, err, accepted}.  stats: {accepted, rejected, t reached, next dt}.
+ * Returns the number of attempts, or -1 on failure. */
+int orc_rk_adaptive(const orc_grid* G, const double* b, double* q, double t0, double t_end,
+                    double dt0, double rtol, double atol, int max_attempts, double* hist, double* stats)
+{
+    const long m = (long)NFIELD * G->nx * G->ny;
+    double* buf = (double*)malloc(sizeof(double) * m * 7);
+    if (!buf) return -1;
+    double *k1 = buf, *k4 = buf + m, *q1 = buf + 2 * m, *e = buf + 3 * m, *work = buf + 4 * m;
+    if (orc_rhs(G, b, q, k1)) { free(buf); return -1; }
+    double t = t0, dt = dt0;
+    int acc = 0, rej = 0, n = 0;
+    while (t < t_end && n < max_attempts) {
+        const int last = dt >= t_end - t;
+        const double h = last ? t_end - t : dt;
+        const double err = bs3_attempt(G, b, q, k1, h, rtol, atol, q1, k4, e, work);
+        if (err < 0.0) { free(buf); return -1; }
+        const int ok = err <= 1.0;
+        const double fac = err == 0.0 ? BS_QMAX
+                                      : fmin(BS_QMAX, fmax(BS_QMIN, BS_SAFETY * pow(err, -1.0 / 3.0)));
+        if (hist) {
+            hist[3 * n] = h;
+            hist[3 * n + 1] = err;
+            hist[3 * n + 2] = ok;
+        }
+        if (ok) {
+            memcpy(q, q1, sizeof(double) * m);
+            memcpy(k1, k4, sizeof(double) * m);
+            t = last ? t_end : t + h;
+            acc++;
+        } else {
+            rej++;
+        }
+        dt = h * fac;
+        n++;
+    }
+    stats[0] = acc;
+    stats[1] = rej;
+    stats[2] = t;
+    stats[3] = dt;
+    free(buf);
+    return n;
 }
 #endif
