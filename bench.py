@@ -281,6 +281,7 @@ def run_ours(args) -> None:
     cpu = _cpu_baseline(p) if world == 1 and not args.no_cpu else None
     ens = None if args.no_extra else _ensemble(torch, 50, 5)
     adj = None if args.no_extra else _adjoint(torch)
+    adapt = None if args.no_extra else _adaptive(torch, args.size, results["f64"]["ms_per_step"])
     head = results["f64"]
     line = {
         "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
@@ -302,6 +303,7 @@ def run_ours(args) -> None:
                      if k != "f64"},
         "ensemble": ens,
         "adjoint": adj,
+        "adaptive": adapt,
         "energy_drift": drift,
         "errors_vs_f64_after_job": errors,
         "kernel_hash": _kernel_hash(),
@@ -398,6 +400,38 @@ def _adjoint(torch, nsteps: int = 0) -> dict:
         torch.cuda.empty_cache()
     s.close()
     return res
+
+
+def _adaptive(torch, size: int, rk4_ms_per_step: float) -> dict:
+    """The paper's time path (Sec. 6): adaptive third-order FSAL pair, rtol =
+    atol = 1e-6, on the benchmark workload (FP64), over the job's time span
+    (500 fixed CFL steps), first step the CFL step.  Wall-clock time of the
+    whole call (the host reads the error norm after every attempt); one RHS
+    evaluation per node and stage counts as one cell-stage.  The fixed-step
+    RK4 job time over the same span is given for comparison."""
+    from paper_2601_02540_b300 import sgn
+    p = inputs.workload3(size, size)
+    s = sgn.Solver.from_problem(p, prec="f64")
+    q0 = s.state(p.q0)
+    s.init_aux(q0)
+    q = q0.clone()
+    s.step_adaptive(q, 0.0, 2 * p.dt, p.dt, want_history=False)       # warm-up (loads the kernels)
+    q.copy_(q0)
+    T = p.nsteps * p.dt
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, hist = s.step_adaptive(q, 0.0, T, p.dt)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    s.close()
+    rhs_evals = 3 * st["attempts"] + 1
+    cells = p.nx * p.ny
+    return {"workload": f"periodic {p.nx}x{p.ny}, t in [0, {p.nsteps} dt_cfl], rtol = atol = 1e-6, FP64",
+            "rk4_fixed_step_job_s": rk4_ms_per_step * p.nsteps / 1e3,
+            "accepted": st["accepted"], "rejected": st["rejected"], "rhs_evaluations": rhs_evals,
+            "mean_accepted_dt_over_cfl": float(np.mean([h[0] for h in hist if h[2] == 1.0]) / p.dt),
+            "wall_s": wall, "value": rhs_evals * cells / wall, "unit": "cell-stages/s",
+            "ms_per_rhs": wall / rhs_evals * 1e3}
 
 
 def _e2e(torch, s, p, q_init_dev, steps: int) -> dict:

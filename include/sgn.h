@@ -15,6 +15,8 @@
  *   sgn_mass_energy  total mass 1^T M h and energy 1^T M E of Thm. 4.1/4.2 and
  *                    the semi-discrete energy rate <d_q E, q_t>_M of eq.
  *                    (splitcondition).
+ *   sgn_step_adaptive  adaptive time integration with an embedded
+ *                    third-order FSAL pair and step-size control (Sec. 6).
  *   sgn_rhs_vjp, sgn_step_record, sgn_step_vjp   the discrete adjoint of the
  *                    RHS and of one RK4 step (no counterpart in the paper).
  *
@@ -180,6 +182,33 @@ SGN_API sgn_status sgn_step_record(sgn_ctx* ctx, void* q_dev, double dt, int nst
  * Asynchronous. */
 SGN_API sgn_status sgn_step_vjp(sgn_ctx* ctx, const void* stash_dev, void* qbar_dev, void* bbar_dev,
                                 double dt, void* stream);
+
+/* Adaptive time integration of q_dev (double, in place) from t0 to t_end
+ * (Sec. 6: the paper uses an explicit third-order Runge-Kutta pair with the
+ * first-same-as-last property, an embedded error estimate and automatic
+ * step-size control, rtol = atol = 1e-6; it does not print the pair).  The
+ * pair is Bogacki-Shampine 3(2): k1 = f(q_n) (reused from the previous
+ * accepted step), k2 = f(q_n + dt/2 k1), k3 = f(q_n + 3dt/4 k2),
+ * q_{n+1} = q_n + dt (2/9 k1 + 1/3 k2 + 4/9 k3), k4 = f(q_{n+1}), error
+ * e = dt (-5/72 k1 + 1/12 k2 + 1/9 k3 - 1/8 k4).  An attempt is accepted when
+ *   err = sqrt(mean over all 5 nx ny values of (e / (atol + rtol max(|q_n|, |q_{n+1}|)))^2) <= 1;
+ * the next step size is dt min(10, max(0.2, 0.9 err^(-1/3))) (10 when err = 0);
+ * a rejected attempt is retried from q_n; a step that would pass t_end is cut
+ * to land on it.  An attempt whose stage inputs have h <= 0 or a non-finite h
+ * counts as rejected with err = +inf.  The first attempt has size dt0 > 0;
+ * rtol, atol >= 0, not both 0; at most max_attempts attempts.
+ * Three fused RHS launches and one reduction per attempt; the host reads err
+ * after each attempt (synchronizes `stream` every attempt).
+ * hist (host, 3*max_attempts doubles, or NULL) receives {dt, err, accepted}
+ * per attempt; stats (host, 5 doubles) receives {accepted, rejected, t
+ * reached, next dt, attempts}.  SGN_F64 contexts only (else
+ * SGN_E_UNSUPPORTED).  The first call of a context allocates 35 planes of
+ * scratch (SGN_E_NOMEM if that fails).  An initial state with h <= 0 or a
+ * non-finite h returns SGN_E_NONPOSITIVE_H / SGN_E_NONFINITE without an
+ * attempt. */
+SGN_API sgn_status sgn_step_adaptive(sgn_ctx* ctx, void* q_dev, double t0, double t_end, double dt0,
+                                     double rtol, double atol, int max_attempts, double* hist,
+                                     double* stats, void* stream);
 
 /* ---- Ragged ensembles ----------------------------------------------------
  * Many independent grids (each its own size, boundary treatment, parameters

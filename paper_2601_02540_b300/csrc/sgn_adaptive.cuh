@@ -1,0 +1,125 @@
+// sgn_adaptive.cuh - stage kernels of the adaptive time integrator.
+//
+// The paper advances the semi-discretization (eq. (sd_periodic_2D_SGN) /
+// eq. (semi_2D)) with an explicit third-order Runge-Kutta pair that has the
+// first-same-as-last (FSAL) property, an embedded error estimate and automatic
+// step-size control (Sec. 6); it does not print the pair.  The pair here is
+// the Bogacki-Shampine 3(2) pair:
+//   k1 = f(q_n)                      (the k4 of the previous accepted step)
+//   k2 = f(Y2),  Y2 = q_n + dt/2 k1
+//   k3 = f(Y3),  Y3 = q_n + 3dt/4 k2
+//   q1 = q_n + dt (2/9 k1 + 1/3 k2 + 4/9 k3),  k4 = f(q1)
+//   e  = dt (-5/72 k1 + 1/12 k2 + 1/9 k3 - 1/8 k4)   (third minus second order)
+// Three launches per attempt, each the halo-tile RHS evaluation of k_stage
+// (same operands, same node_rhs) with its own load and epilogue:
+//   BS_K2  forms Y2 = q_n + c_in k1 while staging the halo tile, writes k2 and
+//          Y3 = q_n + c_y k2 at its nodes;
+//   BS_K3  stages Y3, writes k3 and q1 = q_n + cb1 k1 + cb2 k2 + cb3 k3;
+//   BS_K4  stages q1, writes k4 and the per-block sum of
+//          (e / (atol + rtol max(|q_n|, |q1|)))^2 over its nodes and fields
+//          (fixed-order reduction; the host takes the root mean square).
+// FP64 only.
+#pragma once
+
+#include "sgn_kernels.cuh"
+
+namespace sgn {
+
+enum { BS_K2 = 0, BS_K3 = 1, BS_K4 = 2 };
+
+struct BsArgs {
+    const double* q;       // q_n (5 planes)
+    const double* k1;      // f(q_n)
+    const double* k2;      // BS_K3, BS_K4
+    const double* k3;      // BS_K4
+    const double* X;       // stage input: Y3 (BS_K3) or q1 (BS_K4)
+    const double* b;
+    double* kout;          // this stage's k
+    double* Yout;          // BS_K2: Y3; BS_K3: q1
+    double* partials;      // BS_K4: NDIAG doubles per block, the sum in slot 0
+    int* flag;
+    Geom G;
+    double c_in, c_y;              // dt/2, 3dt/4
+    double cb1, cb2, cb3;          // dt b1, dt b2, dt b3
+    double ce1, ce2, ce3, ce4;     // dt (b_i - bhat_i)
+    double rtol, atol;
+};
+
+template <int BC, int MODE>
+__global__ void __launch_bounds__(BLOCK_THREADS) k_bs3_stage(BsArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* sm = reinterpret_cast<double*>(smem_raw);
+    const Geom& G = a.G;
+    const long long P = G.plane;
+    const int i0 = blockIdx.x * TILE_X, j0 = blockIdx.y * TILE_Y;
+    const int tid = threadIdx.y * TILE_X + threadIdx.x;
+
+    // ---- phase 1: halo tile of the stage input and of its products
+    int bad = 0;
+    for (int t = tid; t < HALO_N; t += BLOCK_THREADS) {
+        const int li = t % HALO_X, lj = t / HALO_X;
+        const int gx = halo_index<BC>(i0 - 1 + li, G.nx);
+        const int gy = halo_index<BC>(j0 - 1 + lj, G.ny);
+        const long long c = (long long)gy * G.nx + gx;
+        double y[5];
+#pragma unroll
+        for (int f = 0; f < 5; f++)
+            y[f] = (MODE == BS_K2) ? fma_(a.c_in, a.k1[f * P + c], a.q[f * P + c]) : a.X[f * P + c];
+        bad |= h_flags(y[0]);
+        store_operands<double, HALO_N>(sm, t, y[0], y[1], y[2], y[3], y[4], a.b[c]);
+    }
+    if (bad) atomicOr(a.flag, bad);
+    __syncthreads();
+
+    // ---- phase 2: k at this thread's nodes and the stage epilogue
+    double esum = 0.0;
+    const int gi = i0 + threadIdx.x;
+#pragma unroll
+    for (int ry = 0; ry < ROWS_PER_THREAD; ry++) {
+        const int ly = threadIdx.y + ry * THREADS_Y;
+        const int gj = j0 + ly;
+        if (gi >= G.nx || gj >= G.ny) continue;
+        const int t = (ly + 1) * HALO_X + (threadIdx.x + 1);
+        double k[5];
+        node_rhs<double, BC, HALO_X, HALO_N>(sm, t, gi, gj, G, k);
+        const long long c = (long long)gj * G.nx + gi;
+#pragma unroll
+        for (int f = 0; f < 5; f++) {
+            const long long o = f * P + c;
+            a.kout[o] = k[f];
+            if (MODE == BS_K2) {
+                a.Yout[o] = fma_(a.c_y, k[f], a.q[o]);
+            } else if (MODE == BS_K3) {
+                a.Yout[o] = fma_(a.cb3, k[f], fma_(a.cb2, a.k2[o], fma_(a.cb1, a.k1[o], a.q[o])));
+            } else {
+                const double e = fma_(a.ce4, k[f], fma_(a.ce3, a.k3[o], fma_(a.ce2, a.k2[o],
+                                                                            mul_(a.ce1, a.k1[o]))));
+                const double q1 = sm[f * HALO_N + t];     // this node's stage input (OP_H..OP_ETA)
+                const double sc = fma_(a.rtol, fmax(fabs(a.q[o]), fabs(q1)), a.atol);
+                const double r = mul_(e, recip<double>(sc));
+                esum = fma_(r, r, esum);
+            }
+        }
+    }
+
+    if (MODE == BS_K4) {
+        // fixed-order block sum: warp shuffle, then thread 0 over the warps
+        __shared__ double red[BLOCK_THREADS / 32];
+        const int lane = tid & 31, warp = tid >> 5;
+        double x = esum;
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+        if (lane == 0) red[warp] = x;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+            for (int wg = 0; wg < BLOCK_THREADS / 32; wg++) s += red[wg];
+            double* slot = a.partials + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * NDIAG;
+            slot[0] = s;
+            slot[1] = 0.0;
+            slot[2] = 0.0;
+            slot[3] = 0.0;
+        }
+    }
+}
+
+}  // namespace sgn

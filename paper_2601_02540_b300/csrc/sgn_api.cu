@@ -3,7 +3,9 @@
 #include "sgn.h"
 #include "sgn_kernels.cuh"
 #include "sgn_adjoint.cuh"
+#include "sgn_adaptive.cuh"
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -65,6 +67,7 @@ struct sgn_ctx {
     long long nblk = 0;
     dim3 grid;
     double* adj = nullptr;       // adjoint scratch (FP64): accumulator + two cotangents
+    double* bs = nullptr;        // adaptive integrator scratch (FP64): k1..k4, Y3, q1, q (35 planes)
 };
 
 namespace {
@@ -224,6 +227,7 @@ void free_ctx(sgn_ctx* c) {
     cudaFree(c->dout);
     cudaFree(c->flag);
     cudaFree(c->adj);
+    cudaFree(c->bs);
     cudaFreeHost(c->hout);
     cudaFreeHost(c->hflag);
     delete c;
@@ -285,6 +289,129 @@ cudaError_t record_step(sgn_ctx* c, double* q, double dt, double* stash, cudaStr
 
 sgn_status need_f64(const sgn_ctx* c, const char* what) {
     if (c->p.prec != SGN_F64) return fail(SGN_E_UNSUPPORTED, "%s: the adjoint is implemented for SGN_F64 only", what);
+    return SGN_OK;
+}
+
+// ---- adaptive integrator (Sec. 6): third-order FSAL pair, host-side control
+template <int BC, int MODE>
+cudaError_t launch_bs3(const sgn_ctx* c, const sgn::BsArgs& a, cudaStream_t s) {
+    auto kern = sgn::k_bs3_stage<BC, MODE>;
+    const size_t smem = sgn::stage_smem_bytes<double, sgn::MODE_RHS>(sgn::ROWS_PER_THREAD);
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    kern<<<c->grid, dim3(sgn::TILE_X, sgn::THREADS_Y), smem, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// Bogacki-Shampine 3(2): weights of the third-order solution and of the
+// embedded second-order one (its stage 4 is f(q_{n+1}), the FSAL stage).
+constexpr double BS_B1 = 2.0 / 9.0, BS_B2 = 1.0 / 3.0, BS_B3 = 4.0 / 9.0;
+constexpr double BS_E1 = 2.0 / 9.0 - 7.0 / 24.0, BS_E2 = 1.0 / 3.0 - 1.0 / 4.0;
+constexpr double BS_E3 = 4.0 / 9.0 - 1.0 / 3.0, BS_E4 = -1.0 / 8.0;
+// step-size control: dt_next = dt min(QMAX, max(QMIN, SAFETY err^(-1/3)))
+constexpr double BS_SAFETY = 0.9, BS_QMIN = 0.2, BS_QMAX = 10.0;
+
+template <int BC>
+sgn_status run_adaptive(sgn_ctx* c, double* q_user, double t0, double t_end, double dt0, double rtol,
+                        double atol, int max_attempts, double* hist, double* stats, cudaStream_t s) {
+    const long long P5 = 5 * c->G.plane;
+    const size_t bytes5 = (size_t)P5 * sizeof(double);
+    double* k1 = c->bs;
+    double* k2 = c->bs + P5;
+    double* k3 = c->bs + 2 * P5;
+    double* k4 = c->bs + 3 * P5;
+    double* Y3 = c->bs + 4 * P5;
+    double* q1 = c->bs + 5 * P5;
+    double* qc = c->bs + 6 * P5;
+    CUDA_TRY(cudaMemcpyAsync(qc, q_user, bytes5, cudaMemcpyDeviceToDevice, s), "copy q");
+    CUDA_TRY((run_rhs<double, double, BC>(c, qc, k1, s)), "k1");
+    sgn_status st = read_flag(c, s);
+    if (st != SGN_OK) return st;
+
+    sgn::BsArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.b = c->b64;
+    a.flag = c->flag;
+    a.G = c->G;
+    a.rtol = rtol;
+    a.atol = atol;
+    a.partials = c->partials;
+    double t = t0, dt = dt0;
+    int acc = 0, rej = 0, n = 0;
+    while (t < t_end && n < max_attempts) {
+        const bool last = dt >= t_end - t;
+        const double h = last ? t_end - t : dt;
+        a.q = qc;
+        a.k1 = k1;
+        a.k2 = k2;
+        a.k3 = k3;
+        // k2 = f(q + h/2 k1); Y3 = q + 3h/4 k2
+        a.c_in = 0.5 * h;
+        a.c_y = 0.75 * h;
+        a.kout = k2;
+        a.Yout = Y3;
+        CUDA_TRY((launch_bs3<BC, sgn::BS_K2>(c, a, s)), "adaptive stage 2");
+        // k3 = f(Y3); q1 = q + h (b1 k1 + b2 k2 + b3 k3)
+        a.X = Y3;
+        a.kout = k3;
+        a.Yout = q1;
+        a.cb1 = h * BS_B1;
+        a.cb2 = h * BS_B2;
+        a.cb3 = h * BS_B3;
+        CUDA_TRY((launch_bs3<BC, sgn::BS_K3>(c, a, s)), "adaptive stage 3");
+        // k4 = f(q1); error partial sums
+        a.X = q1;
+        a.kout = k4;
+        a.ce1 = h * BS_E1;
+        a.ce2 = h * BS_E2;
+        a.ce3 = h * BS_E3;
+        a.ce4 = h * BS_E4;
+        CUDA_TRY((launch_bs3<BC, sgn::BS_K4>(c, a, s)), "adaptive stage 4");
+        sgn::k_reduce_partials<<<1, 256, 0, s>>>(c->partials, c->nblk, c->dout);
+        count_launch();
+        CUDA_TRY(cudaGetLastError(), "error reduction");
+        CUDA_TRY(cudaMemcpyAsync(c->hout, c->dout, sizeof(double), cudaMemcpyDeviceToHost, s), "copy error");
+        CUDA_TRY(cudaMemcpyAsync(c->hflag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, s), "copy flag");
+        CUDA_TRY(cudaStreamSynchronize(s), "synchronize");
+        double err;
+        if (*c->hflag) {
+            // a trial stage left the admissible states: reject as an infinite error
+            CUDA_TRY(cudaMemsetAsync(c->flag, 0, sizeof(int), s), "clear flag");
+            err = INFINITY;
+        } else {
+            err = std::sqrt(c->hout[0] / (double)P5);
+        }
+        const bool ok = err <= 1.0;
+        const double fac = err == 0.0 ? BS_QMAX
+                                      : std::fmin(BS_QMAX, std::fmax(BS_QMIN, BS_SAFETY * std::pow(err, -1.0 / 3.0)));
+        if (hist) {
+            hist[3 * n] = h;
+            hist[3 * n + 1] = err;
+            hist[3 * n + 2] = ok ? 1.0 : 0.0;
+        }
+        if (ok) {
+            std::swap(qc, q1);
+            std::swap(k1, k4);
+            t = last ? t_end : t + h;
+            acc++;
+        } else {
+            rej++;
+        }
+        dt = h * fac;
+        n++;
+    }
+    CUDA_TRY(cudaMemcpyAsync(q_user, qc, bytes5, cudaMemcpyDeviceToDevice, s), "copy q back");
+    CUDA_TRY(cudaStreamSynchronize(s), "synchronize");
+    stats[0] = acc;
+    stats[1] = rej;
+    stats[2] = t;
+    stats[3] = dt;
+    stats[4] = n;
     return SGN_OK;
 }
 
@@ -558,6 +685,34 @@ sgn_status sgn_step_vjp(sgn_ctx* c, const void* stash_dev, void* qbar_dev, void*
     a.X = stash; a.A = A0; a.sigma = sig1; a.Anext = nullptr; a.qacc_out = qbar;
     if ((e = adjoint<sgn::ADJ_MODE_STAGE>(c, a, s)) != cudaSuccess) return cuda_fail(e, "sgn_step_vjp");
     return SGN_OK;
+}
+
+sgn_status sgn_step_adaptive(sgn_ctx* c, void* q_dev, double t0, double t_end, double dt0, double rtol,
+                             double atol, int max_attempts, double* hist, double* stats, void* stream) {
+    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
+    if (c->p.prec != SGN_F64) return fail(SGN_E_UNSUPPORTED, "sgn_step_adaptive needs an SGN_F64 context");
+    sgn_status st = check_state_ptr(q_dev, "q_dev");
+    if (st != SGN_OK) return st;
+    if (!stats) return fail(SGN_E_INVAL, "stats is NULL");
+    if (!(std::isfinite(t0) && std::isfinite(t_end) && t_end >= t0))
+        return fail(SGN_E_INVAL, "need finite t0 <= t_end");
+    if (!finite_pos(dt0)) return fail(SGN_E_INVAL, "dt0 must be finite and > 0");
+    if (!(finite_pos(rtol) || rtol == 0.0) || !(finite_pos(atol) || atol == 0.0) || rtol + atol <= 0.0)
+        return fail(SGN_E_INVAL, "rtol, atol must be finite, >= 0 and not both 0");
+    if (max_attempts < 0) return fail(SGN_E_INVAL, "max_attempts must be >= 0");
+    if (!c->bs) {
+        const size_t bytes = (size_t)35 * (size_t)c->G.plane * sizeof(double);
+        if (cudaMalloc(&c->bs, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            c->bs = nullptr;
+            return fail(SGN_E_NOMEM, "adaptive integrator scratch (%zu bytes)", bytes);
+        }
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double* q = static_cast<double*>(q_dev);
+    return c->p.bc == SGN_BC_REFLECTING
+               ? run_adaptive<sgn::BC_REFLECTING>(c, q, t0, t_end, dt0, rtol, atol, max_attempts, hist, stats, s)
+               : run_adaptive<sgn::BC_PERIODIC>(c, q, t0, t_end, dt0, rtol, atol, max_attempts, hist, stats, s);
 }
 
 }  // extern "C"

@@ -33,6 +33,8 @@ _SIGNATURES = {
     "sgn_init_aux": (ctypes.c_int, [_V, _V, _V]),
     "sgn_rhs": (ctypes.c_int, [_V, _V, _V, _V]),
     "sgn_step": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_int, _V]),
+    "sgn_step_adaptive": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, _V, _V, _V]),
     "sgn_mass_energy": (ctypes.c_int, [_V, _V, _V, _V]),
     "sgn_check": (ctypes.c_int, [_V, _V]),
     "sgn_mass_energy_noalloc": (ctypes.c_int, [_V, _V, _V, _V, _V]),
@@ -143,6 +145,22 @@ def sgn_step(ctx, q: torch.Tensor, dt: float, nsteps: int, dtype: torch.dtype, s
     _ok(lib().sgn_step(ctx, _dptr(q, dtype, "q"), float(dt), int(nsteps), _stream(stream)), "sgn_step")
 
 
+def sgn_step_adaptive(ctx, q: torch.Tensor, t0: float, t_end: float, dt0: float, rtol: float,
+                      atol: float, max_attempts: int, want_history: bool = True, stream=None):
+    """Adaptive integration (FP64 contexts); returns (stats, history) with
+    stats = {accepted, rejected, t, dt_next, attempts} and history an
+    (attempts, 3) list of (dt, err, accepted) or None."""
+    st = (ctypes.c_double * 5)()
+    hist = (ctypes.c_double * (3 * max(int(max_attempts), 1)))() if want_history else None
+    _ok(lib().sgn_step_adaptive(ctx, _dptr(q, torch.float64, "q"), float(t0), float(t_end), float(dt0),
+                                float(rtol), float(atol), int(max_attempts), hist, st, _stream(stream)),
+        "sgn_step_adaptive")
+    n = int(st[4])
+    stats = dict(accepted=int(st[0]), rejected=int(st[1]), t=float(st[2]), dt_next=float(st[3]), attempts=n)
+    history = [tuple(hist[3 * k:3 * k + 3]) for k in range(n)] if want_history else None
+    return stats, history
+
+
 def sgn_mass_energy(ctx, q: torch.Tensor, dtype: torch.dtype, stream=None) -> list[float]:
     out = (ctypes.c_double * 4)()
     _ok(lib().sgn_mass_energy(ctx, _dptr(q, dtype, "q"), out, _stream(stream)), "sgn_mass_energy")
@@ -225,6 +243,12 @@ class Solver:
     def step(self, q: torch.Tensor, dt: float, nsteps: int) -> torch.Tensor:
         sgn_step(self.ctx, q, dt, nsteps, self.state_dtype)
         return q
+
+    def step_adaptive(self, q: torch.Tensor, t0: float, t_end: float, dt0: float, rtol: float = 1e-6,
+                      atol: float = 1e-6, max_attempts: int = 100000, want_history: bool = True):
+        """Adaptive third-order FSAL integration from t0 to t_end in place
+        (FP64 contexts); see sgn_step_adaptive."""
+        return sgn_step_adaptive(self.ctx, q, t0, t_end, dt0, rtol, atol, max_attempts, want_history)
 
     def mass_energy(self, q: torch.Tensor) -> dict:
         m, e, es, r = sgn_mass_energy(self.ctx, q, self.state_dtype)

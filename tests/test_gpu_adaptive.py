@@ -1,0 +1,105 @@
+"""The adaptive integrator (sgn_step_adaptive) against the oracle's
+(Sec. 6: third-order FSAL pair with embedded error estimate and step-size
+control).
+
+Both sides take their accept/reject decisions and step sizes from their own
+error norms, which differ only by rounding (the GPU sums the error in a
+different order and evaluates the RHS with FMA); so the attempt histories must
+agree: the same decisions, step sizes within 1e-9 relative, error norms within
+1e-7 relative, and the final state within the step tolerance 1e-10.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from oracle import PERIODIC, REFLECTING
+from paper_2601_02540_b300 import inputs, sgn
+import gpu_util as gu
+import pins
+
+pytestmark = pytest.mark.gpu
+
+
+def _compare(p, q0, T, dt0, rtol=1e-6, atol=1e-6):
+    g = pins.grid_of(p)
+    qo, ho, so = orc.rk_adaptive(g, p.b, q0, 0.0, T, dt0, rtol, atol)
+    s = gu.solver(p)
+    q = s.state(q0)
+    st, hist = s.step_adaptive(q, 0.0, T, dt0, rtol, atol)
+    s.close()
+    hg = np.array(hist)
+    assert st["attempts"] == len(ho) and st["accepted"] == so["accepted"] and st["rejected"] == so["rejected"]
+    assert st["t"] == so["t"] == T
+    assert np.array_equal(hg[:, 2], ho[:, 2])
+    assert np.all(np.abs(hg[:, 0] - ho[:, 0]) <= 1e-9 * ho[:, 0])
+    assert np.all(np.abs(hg[:, 1] - ho[:, 1]) <= 1e-7 * ho[:, 1])
+    e = gu.state_errors(gu.to_np(q), qo)
+    assert np.all(e <= gu.STEP_TOL), e
+    return st, hg
+
+
+@pytest.mark.parametrize("bc", [PERIODIC, REFLECTING])
+@pytest.mark.parametrize("nx,ny", [(33, 17), (100, 37)])
+def test_adaptive_matches_oracle_generic(bc, nx, ny):
+    p = inputs.smooth_state(nx, ny, bc, seed=11, xmax=4.0, ymax=3.0, lam=50.0)
+    _compare(p, p.q0, 30 * p.dt, p.dt)
+
+
+def test_adaptive_matches_oracle_workload1():
+    """Periodic 64^2 hump (workload 1) over its whole run time, 200 RK4 steps
+    of the fixed-step workload, paper tolerances rtol = atol = 1e-6."""
+    p = inputs.workload1()
+    g = pins.grid_of(p)
+    q0 = orc.init_aux(g, p.b, p.q0)
+    st, _ = _compare(p, q0, p.nsteps * p.dt, p.dt)
+    assert st["accepted"] > 10
+
+
+def test_adaptive_rejection_path_matches_oracle():
+    """A first step far above the stable size is rejected on both sides."""
+    p = inputs.smooth_state(40, 23, REFLECTING, seed=12, xmax=4.0, ymax=3.0, lam=50.0)
+    st, hg = _compare(p, p.q0, 20 * p.dt, 2.5 * p.dt, 1e-7, 1e-7)
+    assert hg[0, 2] == 0 and st["rejected"] >= 1
+
+
+def test_adaptive_workload2_reduced_matches_oracle():
+    p = inputs.workload2(200, 100)
+    g = pins.grid_of(p)
+    q0 = orc.init_aux(g, p.b, p.q0)
+    _compare(p, q0, 40 * p.dt, p.dt)
+
+
+def test_adaptive_only_f64_and_bad_arguments():
+    p = inputs.smooth_state(16, 9, PERIODIC, seed=2)
+    s = gu.solver(p, "f32")
+    q = torch.as_tensor(p.q0, dtype=torch.float64, device="cuda")   # the library checks the context
+    with pytest.raises(sgn.SgnError) as ei:
+        s.step_adaptive(q, 0.0, 1.0, 0.1)
+    assert ei.value.status == 7      # SGN_E_UNSUPPORTED
+    s.close()
+    s = gu.solver(p)
+    q = s.state(p.q0)
+    for args in ((1.0, 0.0, 0.1), (0.0, 1.0, 0.0), (0.0, 1.0, 0.1, 0.0, 0.0)):
+        with pytest.raises(sgn.SgnError) as ei:
+            s.step_adaptive(q, *args)
+        assert ei.value.status == 1  # SGN_E_INVAL
+    st, hist = s.step_adaptive(q, 0.5, 0.5, 0.1)   # empty interval: no attempt
+    assert st["attempts"] == 0 and torch.equal(q, s.state(p.q0))
+    s.close()
+
+
+def test_adaptive_nonpositive_initial_state_is_reported():
+    p = inputs.smooth_state(16, 9, REFLECTING, seed=2)
+    q0 = p.q0.copy()
+    q0[0, 3, 4] = -0.5
+    s = gu.solver(p)
+    q = s.state(q0)
+    with pytest.raises(sgn.SgnError) as ei:
+        s.step_adaptive(q, 0.0, 1.0, 0.1)
+    assert ei.value.status == 4      # SGN_E_NONPOSITIVE_H
+    st, _ = s.step_adaptive(s.state(p.q0), 0.0, 2 * p.dt, p.dt)   # the context stays usable
+    assert st["t"] == 2 * p.dt
+    s.close()
