@@ -130,6 +130,7 @@ def _bind(lib: ctypes.CDLL, pre: str, real: bool) -> None:
         sig += [("rhs_scale", ctypes.c_int, [_P, _P, _P, _P]),
                 ("diagnostics", ctypes.c_int, [_P, _P, _P, _P]),
                 ("bs3_fixed", ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, _P]),
+                ("rrk4", ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, _P, _P]),
                 ("rk_adaptive", ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_double,
                                                ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                ctypes.c_int, _P, _P])]
@@ -228,6 +229,20 @@ class Oracle:
         self._ok(0 if n >= 0 else n, "rk_adaptive")
         return q, hist[:n].copy(), dict(accepted=int(st[0]), rejected=int(st[1]), t=float(st[2]),
                                         dt_next=float(st[3]))
+
+    def rrk4(self, grid: Grid, b, q, dt: float, nsteps: int):
+        """Relaxation RK4 (energy-conserving): (q, gammas per step, time reached)."""
+        b = _arr(b)
+        q = _arr(q).copy()
+        _check(grid, b, q)
+        gam = np.zeros(max(nsteps, 1))
+        t = ctypes.c_double(0.0)
+        g = grid.c()
+        rc = self._r.orc_rrk4(ctypes.byref(g), _ptr(b), _ptr(q), dt, nsteps, _ptr(gam), ctypes.byref(t))
+        if rc == -2:
+            raise ArithmeticError("relaxation: no sign change of the energy change on [1/2, 3/2]")
+        self._ok(rc, "rrk4")
+        return q, gam[:nsteps].copy(), t.value
 
     def rk4(self, grid: Grid, b, q, dt: float, nsteps: int) -> np.ndarray:
         b = _arr(b)

@@ -731,3 +731,73 @@ int orc_rk_adaptive(const orc_grid* G, const double* b, double* q, double t0, do
     return n;
 }
 #endif
+
+/* ---- Relaxation Runge-Kutta (Sec. 7, named there as future work) ----------
+ * Standard explicit Runge-Kutta methods do not conserve the energy of Thm.
+ * 4.1 / 4.2 in the fully discrete scheme (Sec. 6, energy conservation).  The
+ * relaxation approach (Ketcheson 2019; Ranocha et al. 2020) scales the RK
+ * update d = q_{n+1}^{RK} - q_n by a factor gamma_n chosen so that
+ *     E(q_n + gamma_n d) = E(q_n)          (1^T M E, Thm. 4.1)
+ * and advances time by gamma_n dt: q_{n+1} = q_n + gamma_n d,
+ * t_{n+1} = t_n + gamma_n dt (the relaxed step keeps the order of the RK
+ * method).  gamma_n is the root near 1 (gamma = 0 is the trivial root).
+ * Here: classical RK4 for d; the root by bisection on [1/2, 3/2] of
+ *     r(gamma) = sum over nodes of M (E_node(q_n + gamma d) - E_node(q_n))
+ * (compensated sum), to a bracket of 4 ulp or 200 halvings. */
+#ifndef ORC_COMPLEX
+static double energy_change(const orc_grid* G, const double* b, const double* q, const double* d,
+                            double gam)
+{
+    const long n = (long)G->nx * G->ny;
+    csum acc = {0.0, 0.0};
+    for (int j = 0; j < G->ny; j++)
+        for (int i = 0; i < G->nx; i++) {
+            long c = (long)j * G->nx + i;
+            double e0 = energy_density(G->g, G->lambda, q[F_H * n + c], q[F_U * n + c], q[F_V * n + c],
+                                       q[F_W * n + c], q[F_ETA * n + c], b[c]);
+            double e1 = energy_density(G->g, G->lambda, q[F_H * n + c] + gam * d[F_H * n + c],
+                                       q[F_U * n + c] + gam * d[F_U * n + c],
+                                       q[F_V * n + c] + gam * d[F_V * n + c],
+                                       q[F_W * n + c] + gam * d[F_W * n + c],
+                                       q[F_ETA * n + c] + gam * d[F_ETA * n + c], b[c]);
+            csum_add(&acc, orc_mass_weight(G, i, j) * (e1 - e0));
+        }
+    return acc.s + acc.c;
+}
+
+/* nsteps relaxed RK4 steps of nominal size dt, in place.  gammas (may be
+ * NULL) receives gamma_n per step; *t_out the time reached from 0.  Returns
+ * 0, -1 on allocation failure, -2 if r does not change sign on [1/2, 3/2]. */
+int orc_rrk4(const orc_grid* G, const double* b, double* q, double dt, int nsteps, double* gammas,
+             double* t_out)
+{
+    const long m = (long)NFIELD * G->nx * G->ny;
+    double* q1 = (double*)malloc(sizeof(double) * m * 2);
+    if (!q1) return -1;
+    double* d = q1 + m;
+    double t = 0.0;
+    int rc = 0;
+    for (int s = 0; s < nsteps && rc == 0; s++) {
+        memcpy(q1, q, sizeof(double) * m);
+        if (orc_rk4(G, b, q1, dt, 1)) { rc = -1; break; }
+        for (long c = 0; c < m; c++) d[c] = q1[c] - q[c];
+        double lo = 0.5, hi = 1.5;
+        double rlo = energy_change(G, b, q, d, lo), rhi = energy_change(G, b, q, d, hi);
+        if (!(rlo * rhi < 0.0)) { rc = -2; break; }
+        for (int it = 0; it < 200 && hi - lo > 4.0 * 2.220446049250313e-16 * hi; it++) {
+            double mid = 0.5 * (lo + hi);
+            double rm = energy_change(G, b, q, d, mid);
+            if (rm == 0.0) { lo = hi = mid; break; }
+            if ((rm < 0.0) == (rlo < 0.0)) { lo = mid; rlo = rm; }
+            else hi = mid;
+        }
+        double gam = 0.5 * (lo + hi);
+        for (long c = 0; c < m; c++) q[c] = q[c] + gam * d[c];
+        t += gam * dt;
+        if (gammas) gammas[s] = gam;
+    }
+    if (t_out) *t_out = t;
+    free(q1);
+    return rc;
+}
+#endif
