@@ -15,6 +15,8 @@
  *   sgn_mass_energy  total mass 1^T M h and energy 1^T M E of Thm. 4.1/4.2 and
  *                    the semi-discrete energy rate <d_q E, q_t>_M of eq.
  *                    (splitcondition).
+ *   sgn_step_relaxed energy-conserving relaxation RK4 (named as future work
+ *                    in the paper's conclusions; energy of Thm. 4.1).
  *   sgn_step_adaptive  adaptive time integration with an embedded
  *                    third-order FSAL pair and step-size control (Sec. 6).
  *   sgn_rhs_vjp, sgn_step_record, sgn_step_vjp   the discrete adjoint of the
@@ -182,6 +184,24 @@ SGN_API sgn_status sgn_step_record(sgn_ctx* ctx, void* q_dev, double dt, int nst
  * Asynchronous. */
 SGN_API sgn_status sgn_step_vjp(sgn_ctx* ctx, const void* stash_dev, void* qbar_dev, void* bbar_dev,
                                 double dt, void* stream);
+
+/* Relaxation RK4: nsteps energy-conserving steps of nominal size dt > 0 on
+ * q_dev (double, in place).  The paper names relaxation Runge-Kutta methods as
+ * future work and shows that plain RK does not conserve the energy 1^T M E of
+ * Thm. 4.1 / 4.2 in the fully discrete scheme.  Each step computes the plain
+ * RK4 update q1 (the four fused stage launches of sgn_step), then the root
+ * gamma near 1 of E(q + gamma (q1 - q)) = E(q), and sets q <- q + gamma (q1 - q);
+ * the step advances time by gamma dt.  The energy change is summed per node in
+ * a form without cancellation, reduced in a fixed order, and gamma is found by
+ * Newton's method on the host (one reduction per step, a second only when
+ * |gamma - 1| > 1e-3).  gammas (host, nsteps doubles, or NULL) receives gamma
+ * per step, *t_out (or NULL) the time advanced.  Synchronizes `stream` every
+ * step.  SGN_F64 contexts only (else SGN_E_UNSUPPORTED).  The first call of a
+ * context allocates 5 planes of scratch.  A stage input with h <= 0 returns
+ * SGN_E_NONPOSITIVE_H (non-finite: SGN_E_NONFINITE); no root near 1 returns
+ * SGN_E_NONFINITE. */
+SGN_API sgn_status sgn_step_relaxed(sgn_ctx* ctx, void* q_dev, double dt, int nsteps, double* gammas,
+                                    double* t_out, void* stream);
 
 /* Adaptive time integration of q_dev (double, in place) from t0 to t_end
  * (Sec. 6: the paper uses an explicit third-order Runge-Kutta pair with the

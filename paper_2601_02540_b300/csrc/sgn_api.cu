@@ -4,6 +4,7 @@
 #include "sgn_kernels.cuh"
 #include "sgn_adjoint.cuh"
 #include "sgn_adaptive.cuh"
+#include "sgn_rrk.cuh"
 
 #include <algorithm>
 #include <atomic>
@@ -50,6 +51,8 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void sgn_record_error(const char* msg) { fail(SGN_E_INVAL, "%s", msg); }
 void sgn_count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+constexpr int kHostOut = sgn::NDIAG > sgn::NRRK ? sgn::NDIAG : sgn::NRRK;
+
 struct sgn_ctx {
     sgn_params p;
     Geom G;
@@ -61,13 +64,15 @@ struct sgn_ctx {
     void* Qb = nullptr;
     double* partials = nullptr;  // NDIAG per block
     double* dout = nullptr;      // NDIAG device
-    double* hout = nullptr;      // NDIAG pinned host
+    double* hout = nullptr;      // pinned host results (kHostOut doubles: diagnostics, relaxation sums)
     int* flag = nullptr;         // device error bits
     int* hflag = nullptr;        // pinned host copy
     long long nblk = 0;
     dim3 grid;
     double* adj = nullptr;       // adjoint scratch (FP64): accumulator + two cotangents
     double* bs = nullptr;        // adaptive integrator scratch (FP64): k1..k4, Y3, q1, q (35 planes)
+    double* rrk = nullptr;       // relaxation scratch (FP64): plain RK4 update (5 planes), partials, sums
+    long long rrk_nblk = 0;
 };
 
 namespace {
@@ -228,6 +233,7 @@ void free_ctx(sgn_ctx* c) {
     cudaFree(c->flag);
     cudaFree(c->adj);
     cudaFree(c->bs);
+    cudaFree(c->rrk);
     cudaFreeHost(c->hout);
     cudaFreeHost(c->hflag);
     delete c;
@@ -415,6 +421,81 @@ sgn_status run_adaptive(sgn_ctx* c, double* q_user, double t0, double t_end, dou
     return SGN_OK;
 }
 
+// ---- relaxation RK4: gamma from E(q + gamma d) = E(q), host-side Newton
+// Newton on F(gamma) = (E(q + gamma d) - E(q)) / gamma from the six sums of
+// k_rrk_sums about gamma_c; returns false if it does not converge.
+bool rrk_newton(const double* S, double gamma_c, double* gamma) {
+    double g = gamma_c;
+    for (int it = 0; it < 50; it++) {
+        const double tau = g - gamma_c;
+        const double F = S[0] + g * (S[1] + g * S[2]) + S[3] + tau * (S[4] + tau * S[5]);
+        const double dF = S[1] + 2.0 * g * S[2] + S[4] + 2.0 * tau * S[5];
+        if (!(std::isfinite(F) && std::isfinite(dF)) || dF == 0.0) return false;
+        const double step = F / dF;
+        g -= step;
+        if (std::fabs(step) <= 1e-16 * std::fabs(g)) {
+            *gamma = g;
+            return std::isfinite(g) && g > 0.0;
+        }
+    }
+    *gamma = g;
+    return std::isfinite(g) && g > 0.0;
+}
+
+template <int BC>
+sgn_status run_relaxed(sgn_ctx* c, double* q, double dt, int nsteps, double* gammas, double* t_out,
+                       cudaStream_t s) {
+    const long long P5 = 5 * c->G.plane;
+    double* q1 = c->rrk;
+    double* part = c->rrk + P5;
+    double* dsum = part + c->rrk_nblk * sgn::NRRK;
+    const unsigned nblk = (unsigned)c->rrk_nblk;
+    double* acc = static_cast<double*>(c->acc);
+    double* Qa = static_cast<double*>(c->Qa);
+    double* Qb = static_cast<double*>(c->Qb);
+    StageArgs<double, double, double> a1 = base_args<double, double, double>(c);
+    a1.X = q; a1.qn = q; a1.acc = acc; a1.Qout = Qa; a1.c_acc = dt / 6.0; a1.c_q = dt / 2.0;
+    StageArgs<double, double, double> a2 = base_args<double, double, double>(c);
+    a2.X = Qa; a2.qn = q; a2.acc = acc; a2.Qout = Qb; a2.c_acc = dt / 3.0; a2.c_q = dt / 2.0;
+    StageArgs<double, double, double> a3 = a2;
+    a3.X = Qb; a3.Qout = Qa; a3.c_acc = dt / 3.0; a3.c_q = dt;
+    StageArgs<double, double, double> a4 = base_args<double, double, double>(c);
+    a4.X = Qa; a4.acc = acc; a4.out = q1; a4.c_acc = dt / 6.0;    // plain RK4 update, kept apart
+    double t = 0.0;
+    for (int n = 0; n < nsteps; n++) {
+        CUDA_TRY((launch_stage<double, double, double, BC, sgn::MODE_S1>(c, a1, s)), "relaxed stage 1");
+        CUDA_TRY((launch_stage<double, double, double, BC, sgn::MODE_S2>(c, a2, s)), "relaxed stage 2");
+        CUDA_TRY((launch_stage<double, double, double, BC, sgn::MODE_S3>(c, a3, s)), "relaxed stage 3");
+        CUDA_TRY((launch_stage<double, double, double, BC, sgn::MODE_S4>(c, a4, s)), "relaxed stage 4");
+        double gamma_c = 1.0, gamma = 1.0;
+        bool done = false;
+        for (int pass = 0; pass < 8 && !done; pass++) {
+            sgn::k_rrk_sums<BC><<<nblk, sgn::RRK_BLOCK, 0, s>>>(q, q1, c->b64, c->G, gamma_c, part);
+            count_launch();
+            sgn::k_rrk_reduce<<<1, 256, 0, s>>>(part, c->rrk_nblk, dsum);
+            count_launch();
+            CUDA_TRY(cudaGetLastError(), "relaxation sums");
+            CUDA_TRY(cudaMemcpyAsync(c->hout, dsum, sgn::NRRK * sizeof(double), cudaMemcpyDeviceToHost, s),
+                     "copy relaxation sums");
+            sgn_status st = read_flag(c, s);     // synchronizes
+            if (st != SGN_OK) return st;
+            if (!rrk_newton(c->hout, gamma_c, &gamma))
+                return fail(SGN_E_NONFINITE, "relaxation: no energy-conserving gamma near 1 (step %d)", n);
+            done = std::fabs(gamma - gamma_c) <= 1e-3;
+            gamma_c = gamma;
+        }
+        if (!done) return fail(SGN_E_NONFINITE, "relaxation: gamma did not settle (step %d)", n);
+        sgn::k_rrk_update<<<592, 256, 0, s>>>(q, q1, gamma, P5);
+        count_launch();
+        CUDA_TRY(cudaGetLastError(), "relaxed update");
+        if (gammas) gammas[n] = gamma;
+        t += gamma * dt;
+    }
+    CUDA_TRY(cudaStreamSynchronize(s), "synchronize");
+    if (t_out) *t_out = t;
+    return SGN_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -478,7 +559,7 @@ sgn_status sgn_create(const sgn_params* p, const void* b_dev, sgn_ctx** out) {
     ok = ok && cudaMalloc(&c->partials, (size_t)c->nblk * sgn::NDIAG * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc(&c->dout, sgn::NDIAG * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc(&c->flag, sizeof(int)) == cudaSuccess;
-    ok = ok && cudaMallocHost(&c->hout, sgn::NDIAG * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMallocHost(&c->hout, kHostOut * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMallocHost(&c->hflag, sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -685,6 +766,30 @@ sgn_status sgn_step_vjp(sgn_ctx* c, const void* stash_dev, void* qbar_dev, void*
     a.X = stash; a.A = A0; a.sigma = sig1; a.Anext = nullptr; a.qacc_out = qbar;
     if ((e = adjoint<sgn::ADJ_MODE_STAGE>(c, a, s)) != cudaSuccess) return cuda_fail(e, "sgn_step_vjp");
     return SGN_OK;
+}
+
+sgn_status sgn_step_relaxed(sgn_ctx* c, void* q_dev, double dt, int nsteps, double* gammas, double* t_out,
+                            void* stream) {
+    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
+    if (c->p.prec != SGN_F64) return fail(SGN_E_UNSUPPORTED, "sgn_step_relaxed needs an SGN_F64 context");
+    sgn_status st = check_state_ptr(q_dev, "q_dev");
+    if (st != SGN_OK) return st;
+    if (!finite_pos(dt)) return fail(SGN_E_INVAL, "dt must be finite and > 0");
+    if (nsteps < 0) return fail(SGN_E_INVAL, "nsteps must be >= 0");
+    if (!c->rrk) {
+        const long long nblk = (c->G.plane + sgn::RRK_BLOCK - 1) / sgn::RRK_BLOCK;
+        const size_t bytes = ((size_t)5 * (size_t)c->G.plane + (size_t)(nblk + 1) * sgn::NRRK) * sizeof(double);
+        if (cudaMalloc(&c->rrk, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            c->rrk = nullptr;
+            return fail(SGN_E_NOMEM, "relaxation scratch (%zu bytes)", bytes);
+        }
+        c->rrk_nblk = nblk;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double* q = static_cast<double*>(q_dev);
+    return c->p.bc == SGN_BC_REFLECTING ? run_relaxed<sgn::BC_REFLECTING>(c, q, dt, nsteps, gammas, t_out, s)
+                                        : run_relaxed<sgn::BC_PERIODIC>(c, q, dt, nsteps, gammas, t_out, s);
 }
 
 sgn_status sgn_step_adaptive(sgn_ctx* c, void* q_dev, double t0, double t_end, double dt0, double rtol,

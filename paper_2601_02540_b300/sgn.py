@@ -33,6 +33,7 @@ _SIGNATURES = {
     "sgn_init_aux": (ctypes.c_int, [_V, _V, _V]),
     "sgn_rhs": (ctypes.c_int, [_V, _V, _V, _V]),
     "sgn_step": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_int, _V]),
+    "sgn_step_relaxed": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_int, _V, _V, _V]),
     "sgn_step_adaptive": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, ctypes.c_int, _V, _V, _V]),
     "sgn_mass_energy": (ctypes.c_int, [_V, _V, _V, _V]),
@@ -145,6 +146,15 @@ def sgn_step(ctx, q: torch.Tensor, dt: float, nsteps: int, dtype: torch.dtype, s
     _ok(lib().sgn_step(ctx, _dptr(q, dtype, "q"), float(dt), int(nsteps), _stream(stream)), "sgn_step")
 
 
+def sgn_step_relaxed(ctx, q: torch.Tensor, dt: float, nsteps: int, stream=None):
+    """Relaxation RK4 (FP64 contexts); returns (gammas, time advanced)."""
+    gam = (ctypes.c_double * max(int(nsteps), 1))()
+    t = ctypes.c_double(0.0)
+    _ok(lib().sgn_step_relaxed(ctx, _dptr(q, torch.float64, "q"), float(dt), int(nsteps), gam,
+                               ctypes.byref(t), _stream(stream)), "sgn_step_relaxed")
+    return list(gam[:int(nsteps)]), t.value
+
+
 def sgn_step_adaptive(ctx, q: torch.Tensor, t0: float, t_end: float, dt0: float, rtol: float,
                       atol: float, max_attempts: int, want_history: bool = True, stream=None):
     """Adaptive integration (FP64 contexts); returns (stats, history) with
@@ -243,6 +253,10 @@ class Solver:
     def step(self, q: torch.Tensor, dt: float, nsteps: int) -> torch.Tensor:
         sgn_step(self.ctx, q, dt, nsteps, self.state_dtype)
         return q
+
+    def step_relaxed(self, q: torch.Tensor, dt: float, nsteps: int):
+        """Energy-conserving relaxation RK4 in place (FP64 contexts): (gammas, time advanced)."""
+        return sgn_step_relaxed(self.ctx, q, dt, nsteps)
 
     def step_adaptive(self, q: torch.Tensor, t0: float, t_end: float, dt0: float, rtol: float = 1e-6,
                       atol: float = 1e-6, max_attempts: int = 100000, want_history: bool = True):
