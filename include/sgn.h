@@ -15,6 +15,8 @@
  *   sgn_mass_energy  total mass 1^T M h and energy 1^T M E of Thm. 4.1/4.2 and
  *                    the semi-discrete energy rate <d_q E, q_t>_M of eq.
  *                    (splitcondition).
+ *   sgn_mms_exact, sgn_mms_source, sgn_step_mms   the manufactured solution
+ *                    of Sec. 6.1.2 and RK4 with its source terms.
  *   sgn_step_relaxed energy-conserving relaxation RK4 (named as future work
  *                    in the paper's conclusions; energy of Thm. 4.1).
  *   sgn_step_adaptive  adaptive time integration with an embedded
@@ -184,6 +186,31 @@ SGN_API sgn_status sgn_step_record(sgn_ctx* ctx, void* q_dev, double dt, int nst
  * Asynchronous. */
 SGN_API sgn_status sgn_step_vjp(sgn_ctx* ctx, const void* stash_dev, void* qbar_dev, void* bbar_dev,
                                 double dt, void* stream);
+
+/* ---- Manufactured solution (Sec. 6.1.2) ----------------------------------
+ * The paper verifies the full 2D scheme, both boundary treatments, with the
+ * manufactured solution
+ *   b   = 0.08 (cos 2pi x cos 2pi y + 1/2 cos 4pi x cos 4pi y)
+ *   h   = 2 + 1/2 sin 2pi x sin 2pi y cos 2pi t - b
+ *   u   = 0.3 sin 2pi x sin 2pi t,  v = 0.3 sin 2pi y sin 2pi t
+ *   eta = h,  w = -h (u_x + v_y) + 3/2 (u b_x + v b_y)
+ * (on [-1,1]^2 with lambda = 500 to t = 1), made exact by source terms
+ * S = q_t - F(q), F the continuum right-hand side of eq. (2D_hyperbolic_SGN)
+ * in primitive variables.  Node (i, j) of the context's grid sits at
+ * (xmin + i dx, ymin + j dy).  All double, device, five planes.
+ *
+ * sgn_mms_exact: q_dev <- the manufactured state at time t; b_dev (one
+ *   plane, or NULL) <- b.  Asynchronous.
+ * sgn_mms_source: s_dev <- S at every node at time t.  Asynchronous.
+ * sgn_step_mms: nsteps classical RK4 steps of size dt from time t0 of
+ *   q' = RHS(q) + S(t), the source evaluated at the stage times t_n,
+ *   t_n + dt/2, t_n + dt/2, t_n + dt inside the four fused stage launches.
+ *   SGN_F64 contexts only (else SGN_E_UNSUPPORTED).  Asynchronous; the
+ *   context's bathymetry should be the manufactured b (sgn_mms_exact then
+ *   sgn_set_bathymetry). */
+SGN_API sgn_status sgn_mms_exact(sgn_ctx* ctx, double t, void* q_dev, void* b_dev, void* stream);
+SGN_API sgn_status sgn_mms_source(sgn_ctx* ctx, double t, void* s_dev, void* stream);
+SGN_API sgn_status sgn_step_mms(sgn_ctx* ctx, void* q_dev, double t0, double dt, int nsteps, void* stream);
 
 /* Relaxation RK4: nsteps energy-conserving steps of nominal size dt > 0 on
  * q_dev (double, in place).  The paper names relaxation Runge-Kutta methods as

@@ -5,6 +5,7 @@
 #include "sgn_adjoint.cuh"
 #include "sgn_adaptive.cuh"
 #include "sgn_rrk.cuh"
+#include "sgn_mms.cuh"
 
 #include <algorithm>
 #include <atomic>
@@ -421,6 +422,59 @@ sgn_status run_adaptive(sgn_ctx* c, double* q_user, double t0, double t_end, dou
     return SGN_OK;
 }
 
+// ---- manufactured solution (Sec. 6.1.2): forced RK4 stages
+sgn::MmsTime mms_time(double t) {
+    const double pi = 3.14159265358979323846;
+    return {std::sin(2.0 * pi * t), std::cos(2.0 * pi * t)};
+}
+
+template <int BC, int MODE>
+cudaError_t launch_mms(const sgn_ctx* c, const sgn::MmsArgs& m, cudaStream_t s) {
+    auto kern = sgn::k_mms_stage<BC, MODE>;
+    const size_t smem = sgn::stage_smem_bytes<double, sgn::MODE_RHS>(sgn::ROWS_PER_THREAD);
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    kern<<<c->grid, dim3(sgn::TILE_X, sgn::THREADS_Y), smem, s>>>(m);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <int BC>
+cudaError_t run_mms_steps(sgn_ctx* c, double* q, double t0, double dt, int nsteps, cudaStream_t s) {
+    double* acc = static_cast<double*>(c->acc);
+    double* Qa = static_cast<double*>(c->Qa);
+    double* Qb = static_cast<double*>(c->Qb);
+    sgn::MmsArgs m1, m2, m3, m4;
+    m1.st = base_args<double, double, double>(c);
+    m1.st.X = q; m1.st.qn = q; m1.st.acc = acc; m1.st.Qout = Qa; m1.st.c_acc = dt / 6.0; m1.st.c_q = dt / 2.0;
+    m2.st = base_args<double, double, double>(c);
+    m2.st.X = Qa; m2.st.qn = q; m2.st.acc = acc; m2.st.Qout = Qb; m2.st.c_acc = dt / 3.0; m2.st.c_q = dt / 2.0;
+    m3.st = m2.st;
+    m3.st.X = Qb; m3.st.Qout = Qa; m3.st.c_acc = dt / 3.0; m3.st.c_q = dt;
+    m4.st = base_args<double, double, double>(c);
+    m4.st.X = Qa; m4.st.acc = acc; m4.st.out = q; m4.st.c_acc = dt / 6.0;
+    for (sgn::MmsArgs* m : {&m1, &m2, &m3, &m4}) {
+        m->xmin = c->p.xmin;
+        m->ymin = c->p.ymin;
+    }
+    cudaError_t e;
+    for (int n = 0; n < nsteps; n++) {
+        const double t = t0 + n * dt;
+        m1.T = mms_time(t);
+        m2.T = m3.T = mms_time(t + 0.5 * dt);
+        m4.T = mms_time(t + dt);
+        if ((e = launch_mms<BC, sgn::MODE_S1>(c, m1, s)) != cudaSuccess) return e;
+        if ((e = launch_mms<BC, sgn::MODE_S2>(c, m2, s)) != cudaSuccess) return e;
+        if ((e = launch_mms<BC, sgn::MODE_S3>(c, m3, s)) != cudaSuccess) return e;
+        if ((e = launch_mms<BC, sgn::MODE_S4>(c, m4, s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // ---- relaxation RK4: gamma from E(q + gamma d) = E(q), host-side Newton
 // Newton on F(gamma) = (E(q + gamma d) - E(q)) / gamma from the six sums of
 // k_rrk_sums about gamma_c; returns false if it does not converge.
@@ -449,7 +503,6 @@ sgn_status run_relaxed(sgn_ctx* c, double* q, double dt, int nsteps, double* gam
     double* q1 = c->rrk;
     double* part = c->rrk + P5;
     double* dsum = part + c->rrk_nblk * sgn::NRRK;
-    const unsigned nblk = (unsigned)c->rrk_nblk;
     double* acc = static_cast<double*>(c->acc);
     double* Qa = static_cast<double*>(c->Qa);
     double* Qb = static_cast<double*>(c->Qb);
@@ -470,7 +523,7 @@ sgn_status run_relaxed(sgn_ctx* c, double* q, double dt, int nsteps, double* gam
         double gamma_c = 1.0, gamma = 1.0;
         bool done = false;
         for (int pass = 0; pass < 8 && !done; pass++) {
-            sgn::k_rrk_sums<BC><<<nblk, sgn::RRK_BLOCK, 0, s>>>(q, q1, c->b64, c->G, gamma_c, part);
+            sgn::k_rrk_sums<BC><<<sgn::RRK_GRID, sgn::RRK_BLOCK, 0, s>>>(q, q1, c->b64, c->G, gamma_c, part);
             count_launch();
             sgn::k_rrk_reduce<<<1, 256, 0, s>>>(part, c->rrk_nblk, dsum);
             count_launch();
@@ -768,6 +821,50 @@ sgn_status sgn_step_vjp(sgn_ctx* c, const void* stash_dev, void* qbar_dev, void*
     return SGN_OK;
 }
 
+sgn_status sgn_mms_exact(sgn_ctx* c, double t, void* q_dev, void* b_dev, void* stream) {
+    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
+    sgn_status st = check_state_ptr(q_dev, "q_dev");
+    if (st == SGN_OK && b_dev) st = check_state_ptr(b_dev, "b_dev");
+    if (st != SGN_OK) return st;
+    if (!std::isfinite(t)) return fail(SGN_E_INVAL, "t must be finite");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    dim3 blk(32, 8), grd((c->p.nx + 31) / 32, (c->p.ny + 7) / 8);
+    sgn::k_mms_exact<<<grd, blk, 0, s>>>(static_cast<double*>(q_dev), static_cast<double*>(b_dev), c->G, c->p.xmin,
+                                         c->p.ymin, mms_time(t));
+    count_launch();
+    CUDA_TRY(cudaGetLastError(), "sgn_mms_exact");
+    return SGN_OK;
+}
+
+sgn_status sgn_mms_source(sgn_ctx* c, double t, void* s_dev, void* stream) {
+    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
+    sgn_status st = check_state_ptr(s_dev, "s_dev");
+    if (st != SGN_OK) return st;
+    if (!std::isfinite(t)) return fail(SGN_E_INVAL, "t must be finite");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    dim3 blk(32, 8), grd((c->p.nx + 31) / 32, (c->p.ny + 7) / 8);
+    sgn::k_mms_source<<<grd, blk, 0, s>>>(static_cast<double*>(s_dev), c->G, c->p.xmin, c->p.ymin, mms_time(t));
+    count_launch();
+    CUDA_TRY(cudaGetLastError(), "sgn_mms_source");
+    return SGN_OK;
+}
+
+sgn_status sgn_step_mms(sgn_ctx* c, void* q_dev, double t0, double dt, int nsteps, void* stream) {
+    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
+    if (c->p.prec != SGN_F64) return fail(SGN_E_UNSUPPORTED, "sgn_step_mms needs an SGN_F64 context");
+    sgn_status st = check_state_ptr(q_dev, "q_dev");
+    if (st != SGN_OK) return st;
+    if (!std::isfinite(t0)) return fail(SGN_E_INVAL, "t0 must be finite");
+    if (!finite_pos(dt)) return fail(SGN_E_INVAL, "dt must be finite and > 0");
+    if (nsteps < 0) return fail(SGN_E_INVAL, "nsteps must be >= 0");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double* q = static_cast<double*>(q_dev);
+    cudaError_t e = c->p.bc == SGN_BC_REFLECTING ? run_mms_steps<sgn::BC_REFLECTING>(c, q, t0, dt, nsteps, s)
+                                                 : run_mms_steps<sgn::BC_PERIODIC>(c, q, t0, dt, nsteps, s);
+    if (e != cudaSuccess) return cuda_fail(e, "sgn_step_mms");
+    return SGN_OK;
+}
+
 sgn_status sgn_step_relaxed(sgn_ctx* c, void* q_dev, double dt, int nsteps, double* gammas, double* t_out,
                             void* stream) {
     if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
@@ -777,7 +874,7 @@ sgn_status sgn_step_relaxed(sgn_ctx* c, void* q_dev, double dt, int nsteps, doub
     if (!finite_pos(dt)) return fail(SGN_E_INVAL, "dt must be finite and > 0");
     if (nsteps < 0) return fail(SGN_E_INVAL, "nsteps must be >= 0");
     if (!c->rrk) {
-        const long long nblk = (c->G.plane + sgn::RRK_BLOCK - 1) / sgn::RRK_BLOCK;
+        const long long nblk = sgn::RRK_GRID;
         const size_t bytes = ((size_t)5 * (size_t)c->G.plane + (size_t)(nblk + 1) * sgn::NRRK) * sizeof(double);
         if (cudaMalloc(&c->rrk, bytes) != cudaSuccess) {
             cudaGetLastError();

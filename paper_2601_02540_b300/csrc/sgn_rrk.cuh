@@ -18,7 +18,9 @@
 //   rho = dh / D, F0 = n0 + gamma_c n1,
 //   lam/6 F0/(h D),  lam/6 (n1 - F0 rho)/(h D),  lam/6 (F0 rho^2 - n1 rho)/(h D)
 // (the expansion in tau = gamma - gamma_c drops O(tau^3 rho^2) terms; the host
-// re-centres when |gamma - gamma_c| > 1e-3).  k_rrk_update writes q + gamma d.
+// re-centres when |gamma - gamma_c| > 1e-3).  A fixed grid of RRK_GRID blocks:
+// each thread accumulates its strided nodes, then the block sums its threads
+// in a fixed order (one partial per block).  k_rrk_update writes q + gamma d.
 #pragma once
 
 #include "sgn_kernels.cuh"
@@ -27,15 +29,16 @@ namespace sgn {
 
 constexpr int NRRK = 6;
 constexpr int RRK_BLOCK = 256;
+constexpr int RRK_GRID = 148 * 4;     // a fixed grid: every thread sums a strided set of nodes
 
 template <int BC>
 __global__ void __launch_bounds__(RRK_BLOCK) k_rrk_sums(const double* __restrict__ q, const double* __restrict__ q1,
                                                         const double* __restrict__ b, Geom G, double gamma_c,
                                                         double* __restrict__ partials) {
     const long long P = G.plane;
-    const long long c = (long long)blockIdx.x * RRK_BLOCK + threadIdx.x;
     double s[NRRK] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    if (c < P) {
+    for (long long c = (long long)blockIdx.x * RRK_BLOCK + threadIdx.x; c < P;
+         c += (long long)RRK_GRID * RRK_BLOCK) {
         const int j = (int)(c / G.nx), i = (int)(c - (long long)j * G.nx);
         double wx = G.dx, wy = G.dy;
         if (BC == BC_REFLECTING) {
@@ -56,16 +59,16 @@ __global__ void __launch_bounds__(RRK_BLOCK) k_rrk_sums(const double* __restrict
         const double A = eta - h, al = de - dh;
         const double n0 = A * fma(2.0 * al, h, -A * dh), n1 = al * al * h;
         const double D = fma(gamma_c, dh, h);
-        const double rD = recip<double>(h * D);
-        const double rho = dh * recip<double>(D);
+        const double rD = recip<double>(h * D);        // 1 / (h D)
+        const double rho = dh * h * rD;                  // dh / D
         const double F0 = fma(gamma_c, n1, n0);
-        s[0] = M * a1;
-        s[1] = M * a2;
-        s[2] = M * a3;
+        s[0] = fma(M, a1, s[0]);
+        s[1] = fma(M, a2, s[1]);
+        s[2] = fma(M, a3, s[2]);
         const double ml = M * G.lam6 * rD;
-        s[3] = ml * F0;
-        s[4] = ml * fma(-F0, rho, n1);
-        s[5] = ml * rho * fma(F0, rho, -n1);
+        s[3] = fma(ml, F0, s[3]);
+        s[4] = fma(ml, fma(-F0, rho, n1), s[4]);
+        s[5] = fma(ml * rho, fma(F0, rho, -n1), s[5]);
     }
     // fixed-order block sum: warp shuffle, then thread q over the warps
     __shared__ double red[RRK_BLOCK / 32][NRRK];

@@ -33,6 +33,9 @@ _SIGNATURES = {
     "sgn_init_aux": (ctypes.c_int, [_V, _V, _V]),
     "sgn_rhs": (ctypes.c_int, [_V, _V, _V, _V]),
     "sgn_step": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_int, _V]),
+    "sgn_mms_exact": (ctypes.c_int, [_V, ctypes.c_double, _V, _V, _V]),
+    "sgn_mms_source": (ctypes.c_int, [_V, ctypes.c_double, _V, _V]),
+    "sgn_step_mms": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_double, ctypes.c_int, _V]),
     "sgn_step_relaxed": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_int, _V, _V, _V]),
     "sgn_step_adaptive": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, ctypes.c_int, _V, _V, _V]),
@@ -146,6 +149,21 @@ def sgn_step(ctx, q: torch.Tensor, dt: float, nsteps: int, dtype: torch.dtype, s
     _ok(lib().sgn_step(ctx, _dptr(q, dtype, "q"), float(dt), int(nsteps), _stream(stream)), "sgn_step")
 
 
+def sgn_mms_exact(ctx, t: float, q: torch.Tensor, b: torch.Tensor | None = None, stream=None) -> None:
+    f = torch.float64
+    _ok(lib().sgn_mms_exact(ctx, float(t), _dptr(q, f, "q"), None if b is None else _dptr(b, f, "b"),
+                            _stream(stream)), "sgn_mms_exact")
+
+
+def sgn_mms_source(ctx, t: float, s: torch.Tensor, stream=None) -> None:
+    _ok(lib().sgn_mms_source(ctx, float(t), _dptr(s, torch.float64, "s"), _stream(stream)), "sgn_mms_source")
+
+
+def sgn_step_mms(ctx, q: torch.Tensor, t0: float, dt: float, nsteps: int, stream=None) -> None:
+    _ok(lib().sgn_step_mms(ctx, _dptr(q, torch.float64, "q"), float(t0), float(dt), int(nsteps),
+                           _stream(stream)), "sgn_step_mms")
+
+
 def sgn_step_relaxed(ctx, q: torch.Tensor, dt: float, nsteps: int, stream=None):
     """Relaxation RK4 (FP64 contexts); returns (gammas, time advanced)."""
     gam = (ctypes.c_double * max(int(nsteps), 1))()
@@ -252,6 +270,23 @@ class Solver:
 
     def step(self, q: torch.Tensor, dt: float, nsteps: int) -> torch.Tensor:
         sgn_step(self.ctx, q, dt, nsteps, self.state_dtype)
+        return q
+
+    def mms_exact(self, t: float, with_b: bool = False):
+        """The manufactured state of Sec. 6.1.2 at time t on this grid (and b)."""
+        q = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        b = torch.empty(self.shape[1:], dtype=torch.float64, device="cuda") if with_b else None
+        sgn_mms_exact(self.ctx, t, q, b)
+        return (q, b) if with_b else q
+
+    def mms_source(self, t: float) -> torch.Tensor:
+        s = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        sgn_mms_source(self.ctx, t, s)
+        return s
+
+    def step_mms(self, q: torch.Tensor, t0: float, dt: float, nsteps: int) -> torch.Tensor:
+        """RK4 with the manufactured source (FP64 contexts), in place."""
+        sgn_step_mms(self.ctx, q, t0, dt, nsteps)
         return q
 
     def step_relaxed(self, q: torch.Tensor, dt: float, nsteps: int):
