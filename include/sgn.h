@@ -17,6 +17,8 @@
  *                    (splitcondition).
  *   sgn_mms_exact, sgn_mms_source, sgn_step_mms   the manufactured solution
  *                    of Sec. 6.1.2 and RK4 with its source terms.
+ *   sgn_step_sponge  RK4 with the relaxation zones of the wave-tank
+ *                    experiments (Sec. 6).
  *   sgn_step_relaxed energy-conserving relaxation RK4 (named as future work
  *                    in the paper's conclusions; energy of Thm. 4.1).
  *   sgn_step_adaptive  adaptive time integration with an embedded
@@ -211,6 +213,20 @@ SGN_API sgn_status sgn_step_vjp(sgn_ctx* ctx, const void* stash_dev, void* qbar_
 SGN_API sgn_status sgn_mms_exact(sgn_ctx* ctx, double t, void* q_dev, void* b_dev, void* stream);
 SGN_API sgn_status sgn_mms_source(sgn_ctx* ctx, double t, void* s_dev, void* stream);
 SGN_API sgn_status sgn_step_mms(sgn_ctx* ctx, void* q_dev, double t0, double dt, int nsteps, void* stream);
+
+/* Relaxation zones (Sec. 6, the wave-tank experiments: zones at the ends of
+ * the domain absorb outgoing waves): nsteps classical RK4 steps of size dt of
+ *   q' = RHS(q) - sigma(x, y) (q - q0)
+ * on q_dev (double, in place), q0_dev the rest state (double, five planes, not
+ * overlapping q_dev).  sigma rises quadratically from 0 at the inner edge of a
+ * zone to sigma_max at the domain boundary: with d = min(x - xmin, xmax - x),
+ * sigma_x = sigma_max ((width_x - d) / width_x)^2 for d < width_x, else 0;
+ * likewise in y; corners take sigma_x + sigma_y; a width of 0 disables that
+ * direction.  The source is evaluated at the stage inputs inside the four
+ * fused stage launches.  SGN_F64 contexts only (else SGN_E_UNSUPPORTED).
+ * Asynchronous. */
+SGN_API sgn_status sgn_step_sponge(sgn_ctx* ctx, void* q_dev, double dt, int nsteps, const void* q0_dev,
+                                   double width_x, double width_y, double sigma_max, void* stream);
 
 /* Relaxation RK4: nsteps energy-conserving steps of nominal size dt > 0 on
  * q_dev (double, in place).  The paper names relaxation Runge-Kutta methods as

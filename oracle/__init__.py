@@ -131,6 +131,10 @@ def _bind(lib: ctypes.CDLL, pre: str, real: bool) -> None:
                 ("diagnostics", ctypes.c_int, [_P, _P, _P, _P]),
                 ("bs3_fixed", ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, _P]),
                 ("rrk4", ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, _P, _P]),
+                ("sponge_sigma", ctypes.c_double, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                   ctypes.c_double, ctypes.c_double]),
+                ("rk4_sponge", ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, _P,
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_double]),
                 ("rk_adaptive", ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_double,
                                                ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                ctypes.c_int, _P, _P])]
@@ -229,6 +233,24 @@ class Oracle:
         self._ok(0 if n >= 0 else n, "rk_adaptive")
         return q, hist[:n].copy(), dict(accepted=int(st[0]), rejected=int(st[1]), t=float(st[2]),
                                         dt_next=float(st[3]))
+
+    def sponge_sigma(self, grid: Grid, wx: float, wy: float, smax: float) -> np.ndarray:
+        """Relaxation-zone damping coefficient sigma at every node."""
+        g = grid.c()
+        return np.array([[self._r.orc_sponge_sigma(ctypes.byref(g), i, j, wx, wy, smax)
+                          for i in range(grid.nx)] for j in range(grid.ny)])
+
+    def rk4_sponge(self, grid: Grid, b, q, dt: float, nsteps: int, q0, wx: float, wy: float,
+                   smax: float) -> np.ndarray:
+        """RK4 of q' = RHS(q) - sigma (q - q0) (relaxation zones)."""
+        b, q0 = _arr(b), _arr(q0)
+        q = _arr(q).copy()
+        _check(grid, b, q)
+        _check(grid, b, q0)
+        g = grid.c()
+        self._ok(self._r.orc_rk4_sponge(ctypes.byref(g), _ptr(b), _ptr(q), dt, nsteps, _ptr(q0), wx, wy, smax),
+                 "rk4_sponge")
+        return q
 
     def rrk4(self, grid: Grid, b, q, dt: float, nsteps: int):
         """Relaxation RK4 (energy-conserving): (q, gammas per step, time reached)."""

@@ -801,3 +801,67 @@ int orc_rrk4(const orc_grid* G, const double* b, double* q, double dt, int nstep
     return rc;
 }
 #endif
+
+/* ---- Relaxation zones (Sec. 6, the wave-tank experiments) ----------------
+ * Zones of width wx at both x-ends (and wy at both y-ends) absorb outgoing
+ * waves: every equation gets the source -sigma (q - q0), q0 the rest state,
+ * with sigma rising quadratically from 0 at the inner edge of a zone to smax
+ * at the domain boundary:  sigma_x = smax ((wx - d_x) / wx)^2 for d_x < wx,
+ * d_x = min(x - xmin, xmax - x) (0 outside), likewise in y; corners take
+ * sigma_x + sigma_y.  Width 0 disables a direction. */
+#ifndef ORC_COMPLEX
+double orc_sponge_sigma(const orc_grid* G, int i, int j, double wx, double wy, double smax)
+{
+    double dx, dy;
+    orc_spacing(G, &dx, &dy);
+    const double x = G->xmin + i * dx, y = G->ymin + j * dy;
+    double s = 0.0;
+    if (wx > 0.0) {
+        double d = fmin(x - G->xmin, G->xmax - x);
+        if (d < wx) s += smax * ((wx - d) / wx) * ((wx - d) / wx);
+    }
+    if (wy > 0.0) {
+        double d = fmin(y - G->ymin, G->ymax - y);
+        if (d < wy) s += smax * ((wy - d) / wy) * ((wy - d) / wy);
+    }
+    return s;
+}
+
+static int rhs_sponge(const orc_grid* G, const double* b, const double* y, const double* q0, double wx,
+                      double wy, double smax, double* k)
+{
+    if (orc_rhs(G, b, y, k)) return -1;
+    const long n = (long)G->nx * G->ny;
+    for (int j = 0; j < G->ny; j++)
+        for (int i = 0; i < G->nx; i++) {
+            const double sg = orc_sponge_sigma(G, i, j, wx, wy, smax);
+            const long c = (long)j * G->nx + i;
+            for (int f = 0; f < NFIELD; f++) k[f * n + c] -= sg * (y[f * n + c] - q0[f * n + c]);
+        }
+    return 0;
+}
+
+/* Classical RK4 (as orc_rk4) of q' = RHS(q) - sigma (q - q0), in place. */
+int orc_rk4_sponge(const orc_grid* G, const double* b, double* q, double dt, int nsteps, const double* q0,
+                   double wx, double wy, double smax)
+{
+    const long m = (long)NFIELD * G->nx * G->ny;
+    double* buf = (double*)malloc(sizeof(double) * m * 5);
+    if (!buf) return -1;
+    double *k1 = buf, *k2 = buf + m, *k3 = buf + 2 * m, *k4 = buf + 3 * m, *y = buf + 4 * m;
+    int rc = 0;
+    for (int s = 0; s < nsteps && rc == 0; s++) {
+        rc |= rhs_sponge(G, b, q, q0, wx, wy, smax, k1);
+        for (long c = 0; c < m; c++) y[c] = q[c] + (dt / 2.0) * k1[c];
+        rc |= rhs_sponge(G, b, y, q0, wx, wy, smax, k2);
+        for (long c = 0; c < m; c++) y[c] = q[c] + (dt / 2.0) * k2[c];
+        rc |= rhs_sponge(G, b, y, q0, wx, wy, smax, k3);
+        for (long c = 0; c < m; c++) y[c] = q[c] + dt * k3[c];
+        rc |= rhs_sponge(G, b, y, q0, wx, wy, smax, k4);
+        for (long c = 0; c < m; c++)
+            q[c] = q[c] + (dt / 6.0) * (k1[c] + 2.0 * k2[c] + 2.0 * k3[c] + k4[c]);
+    }
+    free(buf);
+    return rc;
+}
+#endif

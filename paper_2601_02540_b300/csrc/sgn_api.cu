@@ -428,9 +428,9 @@ sgn::MmsTime mms_time(double t) {
     return {std::sin(2.0 * pi * t), std::cos(2.0 * pi * t)};
 }
 
-template <int BC, int MODE>
-cudaError_t launch_mms(const sgn_ctx* c, const sgn::MmsArgs& m, cudaStream_t s) {
-    auto kern = sgn::k_mms_stage<BC, MODE>;
+template <int BC, int MODE, int FORCING>
+cudaError_t launch_forced(const sgn_ctx* c, const sgn::MmsArgs& m, cudaStream_t s) {
+    auto kern = sgn::k_forced_stage<BC, MODE, FORCING>;
     const size_t smem = sgn::stage_smem_bytes<double, sgn::MODE_RHS>(sgn::ROWS_PER_THREAD);
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
@@ -443,12 +443,13 @@ cudaError_t launch_mms(const sgn_ctx* c, const sgn::MmsArgs& m, cudaStream_t s) 
     return cudaGetLastError();
 }
 
-template <int BC>
-cudaError_t run_mms_steps(sgn_ctx* c, double* q, double t0, double dt, int nsteps, cudaStream_t s) {
+template <int BC, int FORCING>
+cudaError_t run_forced_steps(sgn_ctx* c, double* q, double t0, double dt, int nsteps, const sgn::MmsArgs& proto,
+                             cudaStream_t s) {
     double* acc = static_cast<double*>(c->acc);
     double* Qa = static_cast<double*>(c->Qa);
     double* Qb = static_cast<double*>(c->Qb);
-    sgn::MmsArgs m1, m2, m3, m4;
+    sgn::MmsArgs m1 = proto, m2 = proto, m3 = proto, m4 = proto;
     m1.st = base_args<double, double, double>(c);
     m1.st.X = q; m1.st.qn = q; m1.st.acc = acc; m1.st.Qout = Qa; m1.st.c_acc = dt / 6.0; m1.st.c_q = dt / 2.0;
     m2.st = base_args<double, double, double>(c);
@@ -457,22 +458,28 @@ cudaError_t run_mms_steps(sgn_ctx* c, double* q, double t0, double dt, int nstep
     m3.st.X = Qb; m3.st.Qout = Qa; m3.st.c_acc = dt / 3.0; m3.st.c_q = dt;
     m4.st = base_args<double, double, double>(c);
     m4.st.X = Qa; m4.st.acc = acc; m4.st.out = q; m4.st.c_acc = dt / 6.0;
-    for (sgn::MmsArgs* m : {&m1, &m2, &m3, &m4}) {
-        m->xmin = c->p.xmin;
-        m->ymin = c->p.ymin;
-    }
     cudaError_t e;
     for (int n = 0; n < nsteps; n++) {
         const double t = t0 + n * dt;
         m1.T = mms_time(t);
         m2.T = m3.T = mms_time(t + 0.5 * dt);
         m4.T = mms_time(t + dt);
-        if ((e = launch_mms<BC, sgn::MODE_S1>(c, m1, s)) != cudaSuccess) return e;
-        if ((e = launch_mms<BC, sgn::MODE_S2>(c, m2, s)) != cudaSuccess) return e;
-        if ((e = launch_mms<BC, sgn::MODE_S3>(c, m3, s)) != cudaSuccess) return e;
-        if ((e = launch_mms<BC, sgn::MODE_S4>(c, m4, s)) != cudaSuccess) return e;
+        if ((e = launch_forced<BC, sgn::MODE_S1, FORCING>(c, m1, s)) != cudaSuccess) return e;
+        if ((e = launch_forced<BC, sgn::MODE_S2, FORCING>(c, m2, s)) != cudaSuccess) return e;
+        if ((e = launch_forced<BC, sgn::MODE_S3, FORCING>(c, m3, s)) != cudaSuccess) return e;
+        if ((e = launch_forced<BC, sgn::MODE_S4, FORCING>(c, m4, s)) != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+sgn::MmsArgs forced_proto(const sgn_ctx* c) {
+    sgn::MmsArgs m;
+    std::memset(&m, 0, sizeof(m));
+    m.xmin = c->p.xmin;
+    m.ymin = c->p.ymin;
+    m.xmax = c->p.xmax;
+    m.ymax = c->p.ymax;
+    return m;
 }
 
 // ---- relaxation RK4: gamma from E(q + gamma d) = E(q), host-side Newton
@@ -859,9 +866,40 @@ sgn_status sgn_step_mms(sgn_ctx* c, void* q_dev, double t0, double dt, int nstep
     if (nsteps < 0) return fail(SGN_E_INVAL, "nsteps must be >= 0");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     double* q = static_cast<double*>(q_dev);
-    cudaError_t e = c->p.bc == SGN_BC_REFLECTING ? run_mms_steps<sgn::BC_REFLECTING>(c, q, t0, dt, nsteps, s)
-                                                 : run_mms_steps<sgn::BC_PERIODIC>(c, q, t0, dt, nsteps, s);
+    const sgn::MmsArgs proto = forced_proto(c);
+    cudaError_t e =
+        c->p.bc == SGN_BC_REFLECTING
+            ? run_forced_steps<sgn::BC_REFLECTING, sgn::FORCING_MMS>(c, q, t0, dt, nsteps, proto, s)
+            : run_forced_steps<sgn::BC_PERIODIC, sgn::FORCING_MMS>(c, q, t0, dt, nsteps, proto, s);
     if (e != cudaSuccess) return cuda_fail(e, "sgn_step_mms");
+    return SGN_OK;
+}
+
+sgn_status sgn_step_sponge(sgn_ctx* c, void* q_dev, double dt, int nsteps, const void* q0_dev, double width_x,
+                           double width_y, double sigma_max, void* stream) {
+    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
+    if (c->p.prec != SGN_F64) return fail(SGN_E_UNSUPPORTED, "sgn_step_sponge needs an SGN_F64 context");
+    sgn_status st = check_state_ptr(q_dev, "q_dev");
+    if (st == SGN_OK) st = check_state_ptr(q0_dev, "q0_dev");
+    if (st != SGN_OK) return st;
+    if (q0_dev == q_dev) return fail(SGN_E_INVAL, "q0_dev must not overlap q_dev");
+    if (!finite_pos(dt)) return fail(SGN_E_INVAL, "dt must be finite and > 0");
+    if (nsteps < 0) return fail(SGN_E_INVAL, "nsteps must be >= 0");
+    if (!(std::isfinite(width_x) && width_x >= 0.0 && std::isfinite(width_y) && width_y >= 0.0))
+        return fail(SGN_E_INVAL, "zone widths must be finite and >= 0");
+    if (!(std::isfinite(sigma_max) && sigma_max >= 0.0)) return fail(SGN_E_INVAL, "sigma_max must be finite and >= 0");
+    sgn::MmsArgs proto = forced_proto(c);
+    proto.q0 = static_cast<const double*>(q0_dev);
+    proto.wx = width_x;
+    proto.wy = width_y;
+    proto.smax = sigma_max;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double* q = static_cast<double*>(q_dev);
+    cudaError_t e =
+        c->p.bc == SGN_BC_REFLECTING
+            ? run_forced_steps<sgn::BC_REFLECTING, sgn::FORCING_SPONGE>(c, q, 0.0, dt, nsteps, proto, s)
+            : run_forced_steps<sgn::BC_PERIODIC, sgn::FORCING_SPONGE>(c, q, 0.0, dt, nsteps, proto, s);
+    if (e != cudaSuccess) return cuda_fail(e, "sgn_step_sponge");
     return SGN_OK;
 }
 

@@ -1,7 +1,8 @@
-// sgn_mms.cuh - the manufactured solution of Sec. 6.1.2 on the GPU: its exact
-// fields and the source terms S = q_t - F(q) that make it an exact solution of
-// the continuum system eq. (2D_hyperbolic_SGN), added pointwise to the
-// split-form RHS inside fused RK4 stage kernels.
+// sgn_mms.cuh - pointwise forcings inside fused RK4 stage kernels: the
+// manufactured solution of Sec. 6.1.2 (its exact fields and the source terms
+// S = q_t - F(q) that make it an exact solution of the continuum system eq.
+// (2D_hyperbolic_SGN)) and the relaxation zones of the wave-tank experiments
+// (Sec. 6).
 //
 // Manufactured solution (Sec. 6.1.2, any domain; the paper uses [-1,1]^2):
 //   b   = 0.08 (cos 2pi x cos 2pi y + 1/2 cos 4pi x cos 4pi y)
@@ -114,16 +115,46 @@ __device__ __forceinline__ void mms_source(double x, double y, MmsTime T, double
     S[4] = eta.t - etat;
 }
 
+// Pointwise forcings added to the split-form RHS inside the RK4 stages:
+//   FORCING_MMS     the manufactured-solution source S(x, y, t_stage);
+//   FORCING_SPONGE  relaxation zones (Sec. 6, wave-tank experiments):
+//                   -sigma(x, y) (q - q0), q0 the rest state, sigma rising
+//                   quadratically from 0 at the inner edge of a zone of width
+//                   wx (wy) to smax at the domain boundary; corners take the sum.
+enum { FORCING_MMS = 0, FORCING_SPONGE = 1 };
+
 struct MmsArgs {
     StageArgs<double, double, double> st;   // the RK4 stage operands (as k_stage)
     double xmin, ymin;                      // node (i, j) at (xmin + i dx, ymin + j dy)
-    MmsTime T;                              // time factors of this stage
+    double xmax, ymax;                      // domain ends (relaxation-zone distances)
+    MmsTime T;                              // time factors of this stage (MMS)
+    const double* q0;                       // rest state (sponge), 5 planes
+    double wx, wy, smax;                    // zone widths (0: none) and the boundary value of sigma
 };
 
-// RK4 stage (modes S1..S4 of k_stage) with the manufactured source added to
-// the split-form RHS at every node: k = RHS(X) + S(x, y, t_stage).
-template <int BC, int MODE>
-__global__ void __launch_bounds__(BLOCK_THREADS) k_mms_stage(MmsArgs m) {
+__device__ __forceinline__ double sponge_sigma(double x, double y, const MmsArgs& m) {
+    double s = 0.0;
+    if (m.wx > 0.0) {
+        const double d = fmin(x - m.xmin, m.xmax - x);
+        if (d < m.wx) {
+            const double r = (m.wx - d) / m.wx;
+            s += m.smax * r * r;
+        }
+    }
+    if (m.wy > 0.0) {
+        const double d = fmin(y - m.ymin, m.ymax - y);
+        if (d < m.wy) {
+            const double r = (m.wy - d) / m.wy;
+            s += m.smax * r * r;
+        }
+    }
+    return s;
+}
+
+// RK4 stage (modes S1..S4 of k_stage) with a pointwise forcing added to the
+// split-form RHS at every node.
+template <int BC, int MODE, int FORCING>
+__global__ void __launch_bounds__(BLOCK_THREADS) k_forced_stage(MmsArgs m) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* sm = reinterpret_cast<double*>(smem_raw);
     const StageArgs<double, double, double>& a = m.st;
@@ -153,8 +184,15 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_mms_stage(MmsArgs m) {
         const int t = (ly + 1) * HALO_X + (threadIdx.x + 1);
         double k[5], S[5];
         node_rhs<double, BC, HALO_X, HALO_N>(sm, t, gi, gj, G, k);
-        mms_source(m.xmin + gi * G.dx, m.ymin + gj * G.dy, m.T, G.g, G.lam, S);
         const long long c = (long long)gj * G.nx + gi;
+        const double x = m.xmin + gi * G.dx, y = m.ymin + gj * G.dy;
+        if (FORCING == FORCING_MMS) {
+            mms_source(x, y, m.T, G.g, G.lam, S);
+        } else {
+            const double sg = sponge_sigma(x, y, m);
+#pragma unroll
+            for (int f = 0; f < 5; f++) S[f] = -sg * (sm[f * HALO_N + t] - m.q0[f * P + c]);
+        }
 #pragma unroll
         for (int f = 0; f < 5; f++) {
             const double kv = k[f] + S[f];

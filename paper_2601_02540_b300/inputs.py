@@ -275,6 +275,57 @@ def workload5(ninst: int = 256, nsteps: int = 1000, seed: int = 1005,
     return out
 
 
+# ----------------------------------------------------------------------------- solitary wave
+SOLITON_L = 30.0
+
+
+def soliton_fields(p: Problem, t: float) -> tuple[np.ndarray, np.ndarray]:
+    """(h, velocity along the propagation direction) of the SGN solitary wave
+    (Sec. 5, eq. (solitary_wave_analytical)) on p's grid at time t:
+    h = h_inf (1 + eps sech^2(kappa (s - C t))), vel = C (1 - h_inf / h),
+    with kappa^2 = 3 eps / (4 h_inf^2 (1 + eps)), C^2 = g h_inf (1 + eps),
+    eps = A / h_inf, s the coordinate along the propagation direction wrapped
+    to the periodic interval [-30, 30)."""
+    e = p.extra
+    X, Y = _mesh(p.nx, p.ny, p.xmin, p.xmax, p.ymin, p.ymax, p.bc)
+    s = X if e["direction"] == "x" else Y
+    L = 2.0 * SOLITON_L
+    xi = np.mod(s - e["C"] * t + SOLITON_L, L) - SOLITON_L
+    h = e["h_inf"] * (1.0 + e["eps"] / np.cosh(e["kappa"] * xi) ** 2)
+    return h, e["C"] * (1.0 - e["h_inf"] / h)
+
+
+def soliton(n: int, direction: str = "x", amp: float = 0.2, h_inf: float = 1.0, lam: float = 30000.0,
+            ncross: int = 4, g: float = G_DEFAULT, cfl: float = 0.2) -> Problem:
+    """The solitary-wave convergence case (Sec. 6.1.1): the SGN solitary wave on
+    [-30, 30] (periodic, n nodes) along `direction`, repeated over `ncross`
+    nodes of the same spacing in the other direction (periodic), flat
+    bathymetry b = 0, lambda = 30000 (the hyperbolic system then stays close
+    to SGN, whose solution this is); eta and w are left to the initialization.
+    Time: one traversal of the domain, t = 60 / C, in nsteps fixed steps no
+    larger than the CFL step."""
+    eps = amp / h_inf
+    kappa = np.sqrt(3.0 * eps / (4.0 * h_inf ** 2 * (1.0 + eps)))
+    C = np.sqrt(g * h_inf * (1.0 + eps))
+    dx = 2.0 * SOLITON_L / n
+    if direction == "x":
+        nx, ny, xmin, xmax, ymin, ymax = n, ncross, -SOLITON_L, SOLITON_L, 0.0, ncross * dx
+    else:
+        nx, ny, xmin, xmax, ymin, ymax = ncross, n, 0.0, ncross * dx, -SOLITON_L, SOLITON_L
+    p = Problem(nx, ny, xmin, xmax, ymin, ymax, PERIODIC, np.zeros((ny, nx)), np.zeros((5, ny, nx)),
+                g=g, lam=lam, name=f"soliton_{direction}_{n}")
+    p.extra.update(direction=direction, eps=eps, kappa=kappa, C=C, h_inf=h_inf, amp=amp)
+    h, vel = soliton_fields(p, 0.0)
+    p.q0[0] = h
+    p.q0[1 if direction == "x" else 2] = vel
+    T = 2.0 * SOLITON_L / C
+    dt = cfl_dt(p.b, h, p.q0[1], p.q0[2], dx, dx, g, lam, cfl)
+    p.nsteps = int(np.ceil(T / dt))
+    p.dt = T / p.nsteps
+    p.extra["t_end"] = T
+    return p
+
+
 # ----------------------------------------------------------------------------- test states
 def smooth_state(nx: int, ny: int, bc: int, seed: int = 0, xmin=0.0, xmax=1.0, ymin=0.0,
                  ymax=1.0, lam: float = LAMBDA_DEFAULT, amp: float = 0.2) -> Problem:

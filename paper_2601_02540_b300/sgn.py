@@ -36,6 +36,8 @@ _SIGNATURES = {
     "sgn_mms_exact": (ctypes.c_int, [_V, ctypes.c_double, _V, _V, _V]),
     "sgn_mms_source": (ctypes.c_int, [_V, ctypes.c_double, _V, _V]),
     "sgn_step_mms": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_double, ctypes.c_int, _V]),
+    "sgn_step_sponge": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_int, _V, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, _V]),
     "sgn_step_relaxed": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_int, _V, _V, _V]),
     "sgn_step_adaptive": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, ctypes.c_int, _V, _V, _V]),
@@ -164,6 +166,13 @@ def sgn_step_mms(ctx, q: torch.Tensor, t0: float, dt: float, nsteps: int, stream
                            _stream(stream)), "sgn_step_mms")
 
 
+def sgn_step_sponge(ctx, q: torch.Tensor, dt: float, nsteps: int, q0: torch.Tensor, width_x: float,
+                    width_y: float, sigma_max: float, stream=None) -> None:
+    f = torch.float64
+    _ok(lib().sgn_step_sponge(ctx, _dptr(q, f, "q"), float(dt), int(nsteps), _dptr(q0, f, "q0"), float(width_x),
+                              float(width_y), float(sigma_max), _stream(stream)), "sgn_step_sponge")
+
+
 def sgn_step_relaxed(ctx, q: torch.Tensor, dt: float, nsteps: int, stream=None):
     """Relaxation RK4 (FP64 contexts); returns (gammas, time advanced)."""
     gam = (ctypes.c_double * max(int(nsteps), 1))()
@@ -287,6 +296,12 @@ class Solver:
     def step_mms(self, q: torch.Tensor, t0: float, dt: float, nsteps: int) -> torch.Tensor:
         """RK4 with the manufactured source (FP64 contexts), in place."""
         sgn_step_mms(self.ctx, q, t0, dt, nsteps)
+        return q
+
+    def step_sponge(self, q: torch.Tensor, dt: float, nsteps: int, q0: torch.Tensor, width_x: float,
+                    width_y: float = 0.0, sigma_max: float = 5.0) -> torch.Tensor:
+        """RK4 with relaxation zones toward the rest state q0 (FP64 contexts), in place."""
+        sgn_step_sponge(self.ctx, q, dt, nsteps, q0, width_x, width_y, sigma_max)
         return q
 
     def step_relaxed(self, q: torch.Tensor, dt: float, nsteps: int):

@@ -363,3 +363,56 @@ def test_rhs_scale_bounds_the_rhs(bc, nx, ny):
     S = O.rhs_scale(g, p.b, p.q0)
     assert np.all(S >= np.abs(k) * (1 - 1e-14))
     assert np.all(S > 0)
+
+
+# ------------------------------------------------------------------ solitary wave
+@pytest.mark.slow
+def test_soliton_second_order_against_sgn_solution():
+    """Sec. 6.1.1 with lambda = 30000: the split-form scheme (RK4) converges at
+    second order to the closed-form SGN solitary wave (eq.
+    (solitary_wave_analytical)) of which the hyperbolic system is a close
+    approximation; here over an eighth of a domain traversal."""
+    errs = []
+    for n in (64, 128, 256):
+        p = inputs.soliton(n, ncross=3)
+        g = pins.grid_of(p)
+        q0 = O.init_aux(g, p.b, p.q0)
+        k = p.nsteps // 8
+        q = O.rk4(g, p.b, q0, p.dt, k)
+        h, u = inputs.soliton_fields(p, k * p.dt)
+        errs.append((np.max(np.abs(q[0] - h)), np.max(np.abs(q[1] - u))))
+        assert np.max(np.abs(q[2])) <= 1e-12          # nothing moves across
+    errs = np.array(errs)
+    orders = np.log2(errs[-2] / errs[-1])
+    assert np.all((orders > 1.85) & (orders < 2.2)), (orders, errs)
+
+
+# ------------------------------------------------------------------ relaxation zones
+@pytest.mark.parametrize("bc", [PERIODIC, REFLECTING])
+def test_sponge_profile_and_rest_state(bc):
+    """Relaxation zones (Sec. 6, wave-tank experiments): sigma is 0 away from
+    the zones, reaches sigma_max where a reflecting wall node sits on the
+    boundary, grows as the square of the depth into the zone, corners add
+    both directions; a lake at rest equal to q0 is left unchanged."""
+    g = Grid(41, 31, 0.0, 40.0, 0.0, 30.0, bc, 9.81, 500.0)
+    wx, wy, smax = 5.0, 4.0, 5.0
+    sg = O.sponge_sigma(g, wx, wy, smax)
+    xs, ys = g.nodes()
+    dxw = np.minimum(xs - g.xmin, g.xmax - xs)
+    dyw = np.minimum(ys - g.ymin, g.ymax - ys)
+    inner = np.outer(dyw >= wy, dxw >= wx)
+    assert np.all(sg[inner] == 0.0) and np.all(sg >= 0.0)
+    j = 15                                   # a row outside the y zones
+    zx = dxw < wx
+    prof = sg[j, zx] / smax
+    depth = (wx - dxw[zx]) / wx
+    assert np.allclose(prof, depth ** 2, rtol=1e-14, atol=0)
+    if bc == REFLECTING:
+        assert sg[j, 0] == smax and sg[j, -1] == smax and sg[0, 0] == 2 * smax
+    # rest state
+    b = -1.0 + 0.1 * np.outer(np.cos(ys / 5.0), np.sin(xs / 7.0))
+    q0 = np.zeros((5, g.ny, g.nx))
+    q0[0] = 0.3 - b
+    q0[4] = q0[0]
+    q = O.rk4_sponge(g, b, q0, 0.01, 20, q0, wx, wy, smax)
+    assert np.max(np.abs(q - q0)) <= 1e-13
