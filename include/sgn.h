@@ -123,6 +123,18 @@ SGN_API sgn_status sgn_rhs(sgn_ctx* ctx, const void* q_dev, void* dq_dev, void* 
  * size dt (finite, > 0): 4 fused RHS+stage launches per step. */
 SGN_API sgn_status sgn_step(sgn_ctx* ctx, void* q_dev, double dt, int nsteps, void* stream);
 
+/* sgn_step that also monitors every new state: the fourth stage launch of
+ * each step (which produces q_{n+1}) reduces its mass 1^T M h, energy 1^T M E
+ * and shifted energy 1^T M E' (Thm. 4.1; as out[0..2] of sgn_mass_energy, and
+ * equal to them bit for bit: the same per-node arithmetic on the stored
+ * double state and the same fixed-order reduction).  out (host, 3*nsteps
+ * doubles) receives {mass, energy, shifted energy} after each step.  The
+ * energy rate (which needs one more RHS evaluation) is not monitored.
+ * Synchronizes `stream` at the end and reports a latched h <= 0 / non-finite
+ * flag.  The first call with more steps than before allocates 4 doubles per
+ * step of device scratch. */
+SGN_API sgn_status sgn_step_diag(sgn_ctx* ctx, void* q_dev, double dt, int nsteps, double* out, void* stream);
+
 /* Diagnostics of q_dev (state type), accumulated in double in a fixed order
  * (bitwise reproducible for a given grid):
  *   out[0] = 1^T M h       out[1] = 1^T M E      out[2] = 1^T M E'

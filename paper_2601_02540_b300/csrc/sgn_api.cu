@@ -16,6 +16,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 using sgn::Geom;
 using sgn::StageArgs;
@@ -73,6 +74,8 @@ struct sgn_ctx {
     double* adj = nullptr;       // adjoint scratch (FP64): accumulator + two cotangents
     double* bs = nullptr;        // adaptive integrator scratch (FP64): k1..k4, Y3, q1, q (35 planes)
     double* rrk = nullptr;       // relaxation scratch (FP64): plain RK4 update (5 planes), partials, sums
+    double* mon = nullptr;       // per-step monitor sums of sgn_step_diag (NDIAG per step)
+    int mon_cap = 0;
     long long rrk_nblk = 0;
 };
 
@@ -115,13 +118,16 @@ StageArgs<TC, TIN, TA> base_args(const sgn_ctx* c) {
     StageArgs<TC, TIN, TA> a;
     std::memset(&a, 0, sizeof(a));
     a.b = static_cast<const TC*>(c->bT);
+    a.b64 = c->b64;
     a.flag = c->flag;
     a.G = c->G;
     return a;
 }
 
+// nsteps RK4 steps; with `mon` the fourth stage also reduces the mass and
+// energies of each new state into mon[NDIAG n ..] (mode S4D).
 template <typename TC, typename TA, int BC>
-cudaError_t run_steps(sgn_ctx* c, TA* q, double dt, int nsteps, cudaStream_t s) {
+cudaError_t run_steps(sgn_ctx* c, TA* q, double dt, int nsteps, cudaStream_t s, double* mon = nullptr) {
     TA* acc = static_cast<TA*>(c->acc);
     TC* Qa = static_cast<TC*>(c->Qa);
     TC* Qb = static_cast<TC*>(c->Qb);
@@ -143,7 +149,16 @@ cudaError_t run_steps(sgn_ctx* c, TA* q, double dt, int nsteps, cudaStream_t s) 
         // k3 = f(q_n + dt/2 k2)
         if ((e = launch_stage<TC, TC, TA, BC, sgn::MODE_S3>(c, a3, s)) != cudaSuccess) return e;
         // k4 = f(q_n + dt k3); q_{n+1} = acc + dt/6 k4
-        if ((e = launch_stage<TC, TC, TA, BC, sgn::MODE_S4>(c, a4, s)) != cudaSuccess) return e;
+        if (!mon) {
+            if ((e = launch_stage<TC, TC, TA, BC, sgn::MODE_S4>(c, a4, s)) != cudaSuccess) return e;
+        } else {
+            StageArgs<TC, TC, TA> a4d = a4;
+            a4d.partials = c->partials;
+            if ((e = launch_stage<TC, TC, TA, BC, sgn::MODE_S4D>(c, a4d, s)) != cudaSuccess) return e;
+            sgn::k_reduce_partials<<<1, 256, 0, s>>>(c->partials, c->nblk, mon + (long long)n * sgn::NDIAG);
+            count_launch();
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
     }
     return cudaSuccess;
 }
@@ -203,6 +218,12 @@ struct StepOp {
     cudaError_t operator()() { return run_steps<TC, TA, BC>(c, static_cast<TA*>(q), dt, n, s); }
 };
 
+struct StepDiagOp {
+    sgn_ctx* c; void* q; double dt; int n; double* mon; cudaStream_t s;
+    template <typename TC, typename TA, int BC>
+    cudaError_t operator()() { return run_steps<TC, TA, BC>(c, static_cast<TA*>(q), dt, n, s, mon); }
+};
+
 struct DiagOp {
     sgn_ctx* c; const void* q; cudaStream_t s;
     template <typename TC, typename TA, int BC>
@@ -235,6 +256,7 @@ void free_ctx(sgn_ctx* c) {
     cudaFree(c->adj);
     cudaFree(c->bs);
     cudaFree(c->rrk);
+    cudaFree(c->mon);
     cudaFreeHost(c->hout);
     cudaFreeHost(c->hflag);
     delete c;
@@ -705,6 +727,39 @@ sgn_status sgn_step(sgn_ctx* c, void* q_dev, double dt, int nsteps, void* stream
     cudaError_t e = dispatch(c, f);
     if (e != cudaSuccess) return cuda_fail(e, "sgn_step");
     return SGN_OK;
+}
+
+sgn_status sgn_step_diag(sgn_ctx* c, void* q_dev, double dt, int nsteps, double* out, void* stream) {
+    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
+    if (!out && nsteps > 0) return fail(SGN_E_INVAL, "out is NULL");
+    sgn_status st = check_state_ptr(q_dev, "q_dev");
+    if (st != SGN_OK) return st;
+    if (!finite_pos(dt)) return fail(SGN_E_INVAL, "dt must be finite and > 0");
+    if (nsteps < 0) return fail(SGN_E_INVAL, "nsteps must be >= 0");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (nsteps > c->mon_cap) {
+        CUDA_TRY(cudaStreamSynchronize(s), "synchronize");
+        cudaFree(c->mon);
+        c->mon = nullptr;
+        c->mon_cap = 0;
+        if (cudaMalloc(&c->mon, (size_t)nsteps * sgn::NDIAG * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            c->mon = nullptr;
+            return fail(SGN_E_NOMEM, "monitor buffer for %d steps", nsteps);
+        }
+        c->mon_cap = nsteps;
+    }
+    StepDiagOp f{c, q_dev, dt, nsteps, c->mon, s};
+    cudaError_t e = dispatch(c, f);
+    if (e != cudaSuccess) return cuda_fail(e, "sgn_step_diag");
+    if (nsteps == 0) return read_flag(c, s);
+    std::vector<double> tmp((size_t)nsteps * sgn::NDIAG);
+    CUDA_TRY(cudaMemcpyAsync(tmp.data(), c->mon, tmp.size() * sizeof(double), cudaMemcpyDeviceToHost, s),
+             "copy monitor");
+    st = read_flag(c, s);
+    for (int n = 0; n < nsteps; n++)
+        for (int k = 0; k < 3; k++) out[3 * n + k] = tmp[(size_t)n * sgn::NDIAG + k];
+    return st;
 }
 
 sgn_status sgn_mass_energy(sgn_ctx* c, const void* q_dev, double* out, void* stream) {

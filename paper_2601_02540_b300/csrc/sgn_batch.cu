@@ -149,6 +149,7 @@ cudaError_t bdiag(sgn_batch* B, const TA* q, cudaStream_t s) {
     std::memset(&a, 0, sizeof(a));
     a.desc = B->desc;
     a.b = static_cast<const TC*>(B->bT);
+    a.b64 = B->b64;
     a.flag = B->flag;
     a.X = q;
     a.partials = B->partials;

@@ -31,6 +31,7 @@ struct BatchArgs {
     const int4* tiles;     // {instance, i0, j0, 0}
     const TIN* X;          // packed stage input
     const TC* b;           // packed bathymetry (compute type)
+    const double* b64;     // packed bathymetry (double; diagnostics)
     const TA* qn;
     TA* acc;
     TC* Qout;
@@ -57,6 +58,7 @@ k_batch_stage(BatchArgs<TC, TIN, TA> a) {
     s.Qout = a.Qout ? a.Qout + so : nullptr;
     s.out = a.out ? a.out + so : nullptr;
     s.partials = nullptr;
+    s.b64 = a.b64 ? a.b64 + d.off : nullptr;
     s.flag = a.flag;
     s.G = d.G;
     s.c_acc = (TA)d.c_acc[a.stage];

@@ -26,7 +26,9 @@ enum { BC_PERIODIC = 0, BC_REFLECTING = 1 };
 //   S3: k = f(Q');  acc += dt/3 k;      Q  = q_n + dt k
 //   S4: k = f(Q);   q_n = acc + dt/6 k
 // DIAG computes k = f(q) and reduces mass, energy and the energy rate.
-enum { MODE_RHS = 0, MODE_S1 = 1, MODE_S2 = 2, MODE_S3 = 3, MODE_S4 = 4, MODE_DIAG = 5 };
+// S4D is S4 that also reduces the mass and energies of the new state q_{n+1}
+// (the per-step monitor, fused into the stage that produces the state).
+enum { MODE_RHS = 0, MODE_S1 = 1, MODE_S2 = 2, MODE_S3 = 3, MODE_S4 = 4, MODE_DIAG = 5, MODE_S4D = 6 };
 
 constexpr int TILE_X = 32;
 constexpr int THREADS_Y = 8;
@@ -110,7 +112,8 @@ struct StageArgs {
     TA* acc;             // RK accumulator
     TC* Qout;            // next stage state
     TA* out;             // dq (RHS) or q_{n+1} (stage 4)
-    double* partials;    // DIAG: NDIAG doubles per block
+    double* partials;    // DIAG, S4D: NDIAG doubles per block
+    const double* b64;   // DIAG, S4D: bathymetry in double
     int* flag;           // latched error bits
     Geom G;
     TA c_acc, c_q;       // stage coefficients (see the modes)
@@ -327,39 +330,71 @@ __device__ __forceinline__ void node_rhs(const TC* __restrict__ sm, int t, int g
     node_rhs_src<TC, BC>(S, gi, gj, G, k);
 }
 
-// Diagnostics of one node, accumulated into dsum: mass M h, energy M E,
-// shifted energy M E' (E' = E + g b^2/2) and the rate M <d_q E, k> with the
-// derivatives listed after eq. (splitcondition); explicitly rounded.
-template <typename TC, int BC, int HN>
-__device__ __forceinline__ void node_diag(const TC* __restrict__ sm, int t, int gi, int gj, const Geom& G,
-                                          const TC k[5], double dsum[4]) {
-    const double h = (double)sm[OP_H * HN + t], u = (double)sm[OP_U * HN + t];
-    const double v = (double)sm[OP_V * HN + t], w = (double)sm[OP_W * HN + t];
-    const double eta = (double)sm[OP_ETA * HN + t], bb = (double)sm[OP_B * HN + t];
+// Mass weight of node (gi, gj): dx dy, halved on each reflecting wall.
+template <int BC>
+__device__ __forceinline__ double mass_weight(int gi, int gj, const Geom& G) {
     double wx = G.dx, wy = G.dy;
     if (BC == BC_REFLECTING) {
         if (gi == 0 || gi == G.nx - 1) wx = mul_(0.5, wx);
         if (gj == 0 || gj == G.ny - 1) wy = mul_(0.5, wy);
     }
-    const double M = mul_(wx, wy);
-    const double rho = __ddiv_rn(eta, h);
-    const double rm1 = sub_(rho, 1.0);
-    const double kin = mul_(0.5, fma_(u, u, mul_(v, v)));
-    const double w26 = __ddiv_rn(mul_(w, w), 6.0);
+    return mul_(wx, wy);
+}
+
+// Pointwise energy of Thm. 4.1 and its parts, explicitly rounded:
+// E = h ((u^2+v^2)/2 + w^2/6 + g/2 (h + 2b) + lambda/6 (eta/h - 1)^2) and the
+// shifted E' = E + g b^2/2 = h (kin + w^2/6 + relax) + g/2 (h + b)^2.
+struct NodeEnergy {
+    double rho, kin, w26, s, E, Es;
+};
+__device__ __forceinline__ NodeEnergy node_energy(double h, double u, double v, double w, double eta, double bb,
+                                                  const Geom& G) {
+    NodeEnergy e;
+    e.rho = mul_(eta, recip<double>(h));
+    const double rm1 = sub_(e.rho, 1.0);
+    e.kin = mul_(0.5, fma_(u, u, mul_(v, v)));
+    e.w26 = mul_(mul_(w, w), 1.0 / 6.0);
     const double relax = mul_(G.lam6, mul_(rm1, rm1));
-    const double E = mul_(h, add_(add_(kin, w26), fma_(0.5 * G.g, fma_(2.0, bb, h), relax)));
-    const double s = add_(h, bb);
-    const double Es = fma_(h, add_(add_(kin, w26), relax), mul_(0.5 * G.g, mul_(s, s)));
-    const double dEh = add_(add_(kin, w26), fma_(G.g, s, mul_(G.lam6, fma_(-rho, rho, 1.0))));
+    e.E = mul_(h, add_(add_(e.kin, e.w26), fma_(0.5 * G.g, fma_(2.0, bb, h), relax)));
+    e.s = add_(h, bb);
+    e.Es = fma_(h, add_(add_(e.kin, e.w26), relax), mul_(0.5 * G.g, mul_(e.s, e.s)));
+    return e;
+}
+
+// Diagnostics of one node, accumulated into dsum: mass M h, energy M E,
+// shifted energy M E' (E' = E + g b^2/2) and the rate M <d_q E, k> with the
+// derivatives listed after eq. (splitcondition); explicitly rounded.
+// The state and the bathymetry are taken as stored (in double), not as the
+// compute-type copies of the tile, so that the diagnostics of a float-stage
+// context are those of its double state.
+template <typename TC, int BC>
+__device__ __forceinline__ void node_diag(const double q[5], double bb, int gi, int gj, const Geom& G,
+                                          const TC k[5], double dsum[4]) {
+    const double h = q[0], u = q[1], v = q[2], w = q[3], eta = q[4];
+    const double M = mass_weight<BC>(gi, gj, G);
+    const NodeEnergy e = node_energy(h, u, v, w, eta, bb, G);
+    const double dEh = add_(add_(e.kin, e.w26), fma_(G.g, e.s, mul_(G.lam6, fma_(-e.rho, e.rho, 1.0))));
     double rate = mul_(dEh, (double)k[0]);
     rate = fma_(mul_(h, u), (double)k[1], rate);
     rate = fma_(mul_(h, v), (double)k[2], rate);
-    rate = fma_(__ddiv_rn(mul_(h, w), 3.0), (double)k[3], rate);
-    rate = fma_(-mul_(G.lam3, sub_(1.0, rho)), (double)k[4], rate);
+    rate = fma_(mul_(mul_(h, w), 1.0 / 3.0), (double)k[3], rate);
+    rate = fma_(-mul_(G.lam3, sub_(1.0, e.rho)), (double)k[4], rate);
     dsum[0] = fma_(M, h, dsum[0]);
-    dsum[1] = fma_(M, E, dsum[1]);
-    dsum[2] = fma_(M, Es, dsum[2]);
+    dsum[1] = fma_(M, e.E, dsum[1]);
+    dsum[2] = fma_(M, e.Es, dsum[2]);
     dsum[3] = fma_(M, rate, dsum[3]);
+}
+
+// Mass and energies of a node's new state (mode S4D): the first three
+// diagnostics of node_diag, the same arithmetic.
+template <int BC>
+__device__ __forceinline__ void node_mass_energy(const double q[5], double bb, int gi, int gj, const Geom& G,
+                                                 double dsum[4]) {
+    const double M = mass_weight<BC>(gi, gj, G);
+    const NodeEnergy e = node_energy(q[0], q[1], q[2], q[3], q[4], bb, G);
+    dsum[0] = fma_(M, q[0], dsum[0]);
+    dsum[1] = fma_(M, e.E, dsum[1]);
+    dsum[2] = fma_(M, e.Es, dsum[2]);
 }
 
 // Dynamic shared memory of a stage launch: the halo tile of the operands.
@@ -391,7 +426,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
     constexpr int NPER = (HALO_N + BLOCK_THREADS - 1) / BLOCK_THREADS;
     const int gi = i0 + threadIdx.x;
     TA pq[ROWS_PER_THREAD][5], pa[ROWS_PER_THREAD][5];
-    if (kEarlyStage && (MODE == MODE_S1 || MODE == MODE_S2 || MODE == MODE_S3 || MODE == MODE_S4)) {
+    if (kEarlyStage && (MODE == MODE_S1 || MODE == MODE_S2 || MODE == MODE_S3 || MODE == MODE_S4 ||
+                        MODE == MODE_S4D)) {
 #pragma unroll
         for (int ry = 0; ry < ROWS_PER_THREAD; ry++) {
             const int gj = j0 + threadIdx.y + ry * THREADS_Y;
@@ -399,7 +435,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
             const long long c = (long long)gj * G.nx + gi;
 #pragma unroll
             for (int f = 0; f < 5; f++) {
-                if (MODE != MODE_S4) pq[ry][f] = a.qn[f * P + c];
+                if (MODE != MODE_S4 && MODE != MODE_S4D) pq[ry][f] = a.qn[f * P + c];
                 if (MODE != MODE_S1) pa[ry][f] = a.acc[f * P + c];
             }
         }
@@ -473,16 +509,24 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
                 a.acc[f * P + c] = fma_(a.c_acc, kv, av);
                 a.Qout[f * P + c] = (TC)fma_(a.c_q, kv, qv);
             }
-        } else if (MODE == MODE_S4) {
+        } else if (MODE == MODE_S4 || MODE == MODE_S4D) {
+            double qn1[5];
 #pragma unroll
-            for (int f = 0; f < 5; f++)
-                a.out[f * P + c] = fma_(a.c_acc, (TA)k[f], kEarlyStage ? pa[ry][f] : a.acc[f * P + c]);
+            for (int f = 0; f < 5; f++) {
+                const TA o = fma_(a.c_acc, (TA)k[f], kEarlyStage ? pa[ry][f] : a.acc[f * P + c]);
+                a.out[f * P + c] = o;
+                qn1[f] = (double)o;
+            }
+            if (MODE == MODE_S4D) node_mass_energy<BC>(qn1, a.b64[c], gi, gj, G, dsum);
         } else if (MODE == MODE_DIAG) {
-            node_diag<TC, BC, HALO_N>(sm, t, gi, gj, G, k, dsum);
+            double qd[5];
+#pragma unroll
+            for (int f = 0; f < 5; f++) qd[f] = (double)a.X[f * P + c];
+            node_diag<TC, BC>(qd, a.b64[c], gi, gj, G, k, dsum);
         }
     }
 
-    if (MODE == MODE_DIAG) {
+    if (MODE == MODE_DIAG || MODE == MODE_S4D) {
         // fixed-order block reduction: warp shuffle, then thread q over the warps
         __shared__ double red[BLOCK_THREADS / 32][NDIAG];
         const int lane = tid & 31, warp = tid >> 5;

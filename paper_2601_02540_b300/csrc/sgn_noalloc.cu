@@ -111,6 +111,7 @@ extern "C" SGN_API sgn_status sgn_mass_energy_noalloc(const sgn_params* p, const
     sgn::StageArgs<double, double, double> a{};
     a.X = static_cast<const double*>(q_dev);
     a.b = static_cast<const double*>(b_dev);
+    a.b64 = a.b;
     a.partials = scratch;
     a.flag = reinterpret_cast<int*>(scratch + kFlagOffset);
     sgn::fill_geom(a.G, p->nx, p->ny, dx, dy, p->g, p->lambda);

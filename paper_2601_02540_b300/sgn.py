@@ -42,6 +42,7 @@ _SIGNATURES = {
     "sgn_step_adaptive": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, ctypes.c_int, _V, _V, _V]),
     "sgn_mass_energy": (ctypes.c_int, [_V, _V, _V, _V]),
+    "sgn_step_diag": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_int, _V, _V]),
     "sgn_check": (ctypes.c_int, [_V, _V]),
     "sgn_mass_energy_noalloc": (ctypes.c_int, [_V, _V, _V, _V, _V]),
     "sgn_rhs_vjp": (ctypes.c_int, [_V, _V, _V, _V, _V, _V]),
@@ -198,6 +199,15 @@ def sgn_step_adaptive(ctx, q: torch.Tensor, t0: float, t_end: float, dt0: float,
     return stats, history
 
 
+def sgn_step_diag(ctx, q: torch.Tensor, dt: float, nsteps: int, dtype: torch.dtype, stream=None) -> list:
+    """RK4 steps with the mass, energy and shifted energy of every new state
+    (fused into the fourth stage): a list of (mass, energy, energy_shifted)."""
+    out = (ctypes.c_double * (3 * max(int(nsteps), 1)))()
+    _ok(lib().sgn_step_diag(ctx, _dptr(q, dtype, "q"), float(dt), int(nsteps), out, _stream(stream)),
+        "sgn_step_diag")
+    return [tuple(out[3 * k:3 * k + 3]) for k in range(int(nsteps))]
+
+
 def sgn_mass_energy(ctx, q: torch.Tensor, dtype: torch.dtype, stream=None) -> list[float]:
     out = (ctypes.c_double * 4)()
     _ok(lib().sgn_mass_energy(ctx, _dptr(q, dtype, "q"), out, _stream(stream)), "sgn_mass_energy")
@@ -313,6 +323,10 @@ class Solver:
         """Adaptive third-order FSAL integration from t0 to t_end in place
         (FP64 contexts); see sgn_step_adaptive."""
         return sgn_step_adaptive(self.ctx, q, t0, t_end, dt0, rtol, atol, max_attempts, want_history)
+
+    def step_diag(self, q: torch.Tensor, dt: float, nsteps: int) -> list:
+        """nsteps RK4 steps; (mass, energy, energy_shifted) after each."""
+        return sgn_step_diag(self.ctx, q, dt, nsteps, self.state_dtype)
 
     def mass_energy(self, q: torch.Tensor) -> dict:
         m, e, es, r = sgn_mass_energy(self.ctx, q, self.state_dtype)
