@@ -39,8 +39,15 @@
  *   SGN_F32_F64ACC  the caller's state q (= q_n) and the RK accumulator are
  *                   double; the RHS and the intermediate stage states are
  *                   float.
- *   "state type" below means double for SGN_F64 and SGN_F32_F64ACC, float for
- *   SGN_F32.  Bathymetry arguments are always double.  Diagnostics are always
+ *   SGN_DF64        the state and the RK accumulator are double; the RHS is
+ *                   evaluated, and the intermediate stage states are stored,
+ *                   in double-word arithmetic (a float pair hi + lo, about 48
+ *                   significant bits, relative rounding ~2^-48) on the FP32
+ *                   units, which on this GPU outnumber the FP64 units 64 to
+ *                   one.  The adjoint, adaptive, relaxed, manufactured and
+ *                   relaxation-zone entry points need SGN_F64.
+ *   "state type" below means double for SGN_F64, SGN_F32_F64ACC and SGN_DF64,
+ *   float for SGN_F32.  Bathymetry arguments are always double.  Diagnostics are always
  *   accumulated in double.
  *
  * Memory and streams.  Every pointer named *_dev is device memory of the
@@ -86,7 +93,7 @@ typedef enum {
 } sgn_status;
 
 typedef enum { SGN_BC_PERIODIC = 0, SGN_BC_REFLECTING = 1 } sgn_bc;
-typedef enum { SGN_F64 = 0, SGN_F32 = 1, SGN_F32_F64ACC = 2 } sgn_prec;
+typedef enum { SGN_F64 = 0, SGN_F32 = 1, SGN_F32_F64ACC = 2, SGN_DF64 = 3 } sgn_prec;
 
 typedef struct {
     int nx, ny;                    /* nodes per direction, each >= 3 */

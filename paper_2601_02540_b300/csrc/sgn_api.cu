@@ -200,6 +200,9 @@ cudaError_t dispatch(const sgn_ctx* c, F& f) {
     case SGN_F32:
         return refl ? f.template operator()<float, float, sgn::BC_REFLECTING>()
                     : f.template operator()<float, float, sgn::BC_PERIODIC>();
+    case SGN_DF64:
+        return refl ? f.template operator()<sgn::df64, double, sgn::BC_REFLECTING>()
+                    : f.template operator()<sgn::df64, double, sgn::BC_PERIODIC>();
     default:
         return refl ? f.template operator()<float, double, sgn::BC_REFLECTING>()
                     : f.template operator()<float, double, sgn::BC_PERIODIC>();
@@ -263,6 +266,17 @@ void free_ctx(sgn_ctx* c) {
 }
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+// The compute-type copy of the bathymetry (float or df64) from the double one.
+cudaError_t convert_bathymetry(sgn_ctx* c, cudaStream_t s) {
+    const long long n = c->G.plane;
+    if (c->p.prec == SGN_DF64)
+        sgn::k_convert<sgn::df64><<<592, 256, 0, s>>>(c->b64, static_cast<sgn::df64*>(c->bT), n);
+    else
+        sgn::k_convert<float><<<592, 256, 0, s>>>(c->b64, static_cast<float*>(c->bT), n);
+    count_launch();
+    return cudaGetLastError();
+}
 
 template <int BC, int MODE>
 cudaError_t launch_adjoint(const sgn_ctx* c, const sgn::AdjArgs& a, cudaStream_t s) {
@@ -611,7 +625,7 @@ sgn_status sgn_create(const sgn_params* p, const void* b_dev, sgn_ctx** out) {
           std::isfinite(p->ymin) && std::isfinite(p->ymax) && p->ymax > p->ymin))
         return fail(SGN_E_INVAL, "domain must be finite with xmax > xmin and ymax > ymin");
     if (p->bc != SGN_BC_PERIODIC && p->bc != SGN_BC_REFLECTING) return fail(SGN_E_INVAL, "bc = %d", p->bc);
-    if (p->prec != SGN_F64 && p->prec != SGN_F32 && p->prec != SGN_F32_F64ACC)
+    if (p->prec != SGN_F64 && p->prec != SGN_F32 && p->prec != SGN_F32_F64ACC && p->prec != SGN_DF64)
         return fail(SGN_E_INVAL, "prec = %d", p->prec);
     if (!finite_pos(p->g)) return fail(SGN_E_INVAL, "g must be finite and > 0");
     if (!(std::isfinite(p->lambda) && p->lambda >= 0.0)) return fail(SGN_E_INVAL, "lambda must be finite and >= 0");
@@ -626,14 +640,14 @@ sgn_status sgn_create(const sgn_params* p, const void* b_dev, sgn_ctx** out) {
     const double dy = per ? (p->ymax - p->ymin) / p->ny : (p->ymax - p->ymin) / (p->ny - 1);
     Geom& G = c->G;
     sgn::fill_geom(G, p->nx, p->ny, dx, dy, p->g, p->lambda);
-    c->tc_size = p->prec == SGN_F64 ? sizeof(double) : sizeof(float);
+    c->tc_size = (p->prec == SGN_F64 || p->prec == SGN_DF64) ? 8 : sizeof(float);
     c->ta_size = p->prec == SGN_F32 ? sizeof(float) : sizeof(double);
     c->grid = dim3((p->nx + sgn::TILE_X - 1) / sgn::TILE_X, (p->ny + sgn::TILE_Y - 1) / sgn::TILE_Y);
     c->nblk = (long long)c->grid.x * c->grid.y;
 
     const size_t plane = (size_t)G.plane;
     bool ok = cudaMalloc(&c->b64, plane * sizeof(double)) == cudaSuccess;
-    if (ok && p->prec != SGN_F64) ok = cudaMalloc(&c->bT, plane * sizeof(float)) == cudaSuccess;
+    if (ok && p->prec != SGN_F64) ok = cudaMalloc(&c->bT, plane * c->tc_size) == cudaSuccess;
     if (ok && p->prec == SGN_F64) c->bT = c->b64;
     ok = ok && cudaMalloc(&c->acc, 5 * plane * c->ta_size) == cudaSuccess;
     ok = ok && cudaMalloc(&c->Qa, 5 * plane * c->tc_size) == cudaSuccess;
@@ -651,11 +665,7 @@ sgn_status sgn_create(const sgn_params* p, const void* b_dev, sgn_ctx** out) {
     }
     cudaError_t e = cudaMemset(c->flag, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(c->b64, b_dev, plane * sizeof(double), cudaMemcpyDeviceToDevice);
-    if (e == cudaSuccess && p->prec != SGN_F64) {
-        sgn::k_convert<float><<<592, 256>>>(c->b64, static_cast<float*>(c->bT), (long long)plane);
-        count_launch();
-        e = cudaGetLastError();
-    }
+    if (e == cudaSuccess && p->prec != SGN_F64) e = convert_bathymetry(c, nullptr);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         sgn_status st = cuda_fail(e, "sgn_create");
@@ -680,11 +690,7 @@ sgn_status sgn_set_bathymetry(sgn_ctx* c, const void* b_dev, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t plane = (size_t)c->G.plane;
     CUDA_TRY(cudaMemcpyAsync(c->b64, b_dev, plane * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy b");
-    if (c->p.prec != SGN_F64) {
-        sgn::k_convert<float><<<592, 256, 0, s>>>(c->b64, static_cast<float*>(c->bT), (long long)plane);
-        count_launch();
-        CUDA_TRY(cudaGetLastError(), "convert b");
-    }
+    if (c->p.prec != SGN_F64) CUDA_TRY(convert_bathymetry(c, s), "convert b");
     return SGN_OK;
 }
 

@@ -15,6 +15,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "sgn_df64.cuh"
+
 namespace sgn {
 
 enum { BC_PERIODIC = 0, BC_REFLECTING = 1 };
@@ -61,9 +63,17 @@ struct Geom {
     double g, lam;
     double lam2, lam3, lam6;  // lambda/2, lambda/3, lambda/6
     // the same constants rounded to float, so that float kernels never convert
-    // (a double-to-float conversion occupies the FP64 pipe)
+    // (a double-to-float conversion occupies the FP64 pipe), and as df64 pairs
     float f_cx2, f_cy2, f_cx1, f_cy1, f_satx, f_saty, f_g, f_lam, f_lam3, f_lam6;
+    df64 w_cx2, w_cy2, w_cx1, w_cy1, w_satx, w_saty, w_g, w_lam, w_lam3, w_lam6;
 };
+
+// Host: a double as a df64 pair (hi the nearest float, lo the nearest float
+// to the remainder).
+inline df64 host_df64(double x) {
+    const float hi = (float)x;
+    return {hi, (float)(x - (double)hi)};
+}
 
 // Host: fill a Geom for an nx x ny grid with spacing (dx, dy).
 inline void fill_geom(Geom& G, int nx, int ny, double dx, double dy, double g, double lam) {
@@ -93,16 +103,45 @@ inline void fill_geom(Geom& G, int nx, int ny, double dx, double dy, double g, d
     G.f_lam = (float)G.lam;
     G.f_lam3 = (float)G.lam3;
     G.f_lam6 = (float)G.lam6;
+    G.w_cx2 = host_df64(G.cx2);
+    G.w_cy2 = host_df64(G.cy2);
+    G.w_cx1 = host_df64(G.cx1);
+    G.w_cy1 = host_df64(G.cy1);
+    G.w_satx = host_df64(G.satx);
+    G.w_saty = host_df64(G.saty);
+    G.w_g = host_df64(G.g);
+    G.w_lam = host_df64(G.lam);
+    G.w_lam3 = host_df64(G.lam3);
+    G.w_lam6 = host_df64(G.lam6);
 }
 
 // A grid constant in the compute type TC (the double or the float copy).
 template <typename TC>
-__device__ __forceinline__ TC gsel(double d, float f);
+__device__ __forceinline__ TC gsel(double d, float f, df64 w);
 template <>
-__device__ __forceinline__ double gsel<double>(double d, float) { return d; }
+__device__ __forceinline__ double gsel<double>(double d, float, df64) { return d; }
 template <>
-__device__ __forceinline__ float gsel<float>(double, float f) { return f; }
-#define GC(TC, name) gsel<TC>(G.name, G.f_##name)
+__device__ __forceinline__ float gsel<float>(double, float f, df64) { return f; }
+template <>
+__device__ __forceinline__ df64 gsel<df64>(double, float, df64 w) { return w; }
+#define GC(TC, name) gsel<TC>(G.name, G.f_##name, G.w_##name)
+
+// A small literal (0.5, 1, 1.5: exact in float) in the compute type.
+template <typename TC>
+__device__ __forceinline__ TC tc_const(double d) { return (TC)d; }
+template <>
+__device__ __forceinline__ df64 tc_const<df64>(double d) { return df64_of_float((float)d); }
+
+// Conversions between the storage and compute types (df64 by integer
+// operations on the bit patterns, see sgn_df64.cuh).
+template <typename TO, typename TI>
+__device__ __forceinline__ TO cvt(TI x) { return (TO)x; }
+template <>
+__device__ __forceinline__ df64 cvt<df64, double>(double x) { return df64_from_double(x); }
+template <>
+__device__ __forceinline__ df64 cvt<df64, df64>(df64 x) { return x; }
+template <>
+__device__ __forceinline__ double cvt<double, df64>(df64 x) { return double_of_df64(x); }
 
 template <typename TC, typename TIN, typename TA>
 struct StageArgs {
@@ -136,6 +175,8 @@ __device__ __forceinline__ int h_flags(double h) {
     const long long mag = bits & 0x7fffffffffffffffLL;
     return (mag > 0x7ff0000000000000LL || bits == 0x7ff0000000000000LL) ? FLAG_NONFINITE : FLAG_NONPOSITIVE;
 }
+__device__ __forceinline__ int h_flags(float h);
+__device__ __forceinline__ int h_flags(df64 h) { return h_flags(h.hi); }
 __device__ __forceinline__ int h_flags(float h) {
     const int bits = __float_as_int(h);
     if (bits > 0 && bits < 0x7f800000) return 0;
@@ -161,6 +202,8 @@ __device__ __forceinline__ double recip<double>(double h) {
 }
 template <>
 __device__ __forceinline__ float recip<float>(float h) { return 1.0f / h; }
+template <>
+__device__ __forceinline__ df64 recip<df64>(df64 h) { return recip_df64(h); }
 
 // Explicitly rounded arithmetic for the per-node RHS and stage algebra:
 // products and sums that the compiler may not fuse, and fused multiply-adds
@@ -204,7 +247,7 @@ __device__ __forceinline__ void make_ops(TC h, TC u, TC v, TC w, TC eta, TC bb, 
     o[OP_HUW] = mul_(hu, w);
     o[OP_HVW] = mul_(hv, w);
     o[OP_E2H] = mul_(mul_(eta, eta), r);
-    o[OP_E15] = fma_(TC(1.5), bb, eta);
+    o[OP_E15] = fma_(tc_const<TC>(1.5), bb, eta);
     o[OP_R] = r;
 }
 
@@ -252,9 +295,9 @@ __device__ __forceinline__ void node_rhs_src(const Src& S, int gi, int gj, const
     const TC r = SM_(OP_R, POS_C);
     const TC hu = SM_(OP_HU, POS_C), hv = SM_(OP_HV, POS_C), uu = SM_(OP_UU, POS_C), vv = SM_(OP_VV, POS_C);
     const TC g = GC(TC, g), lam = GC(TC, lam), lam3 = GC(TC, lam3), lam6 = GC(TC, lam6);
-    const TC half = TC(0.5);
+    const TC half = tc_const<TC>(0.5);
     const TC rho = mul_(eta, r);                          // eta / h
-    const TC om = sub_(TC(1), rho);                       // 1 - eta / h
+    const TC om = sub_(tc_const<TC>(1.0), rho);                       // 1 - eta / h
     const TC base = fma_(lam6, mul_(rho, rho), -mul_(g, add_(h, b)));   // lam/6 (eta/h)^2 - g (h + b)
     const TC lom = mul_(lam3, om);
     const TC uv = mul_(u, v), hw = mul_(h, w), uw = mul_(u, w), vw = mul_(v, w);
@@ -374,11 +417,11 @@ __device__ __forceinline__ void node_diag(const double q[5], double bb, int gi, 
     const double M = mass_weight<BC>(gi, gj, G);
     const NodeEnergy e = node_energy(h, u, v, w, eta, bb, G);
     const double dEh = add_(add_(e.kin, e.w26), fma_(G.g, e.s, mul_(G.lam6, fma_(-e.rho, e.rho, 1.0))));
-    double rate = mul_(dEh, (double)k[0]);
-    rate = fma_(mul_(h, u), (double)k[1], rate);
-    rate = fma_(mul_(h, v), (double)k[2], rate);
-    rate = fma_(mul_(mul_(h, w), 1.0 / 3.0), (double)k[3], rate);
-    rate = fma_(-mul_(G.lam3, sub_(1.0, e.rho)), (double)k[4], rate);
+    double rate = mul_(dEh, cvt<double>(k[0]));
+    rate = fma_(mul_(h, u), cvt<double>(k[1]), rate);
+    rate = fma_(mul_(h, v), cvt<double>(k[2]), rate);
+    rate = fma_(mul_(mul_(h, w), 1.0 / 3.0), cvt<double>(k[3]), rate);
+    rate = fma_(-mul_(G.lam3, sub_(1.0, e.rho)), cvt<double>(k[4]), rate);
     dsum[0] = fma_(M, h, dsum[0]);
     dsum[1] = fma_(M, e.E, dsum[1]);
     dsum[2] = fma_(M, e.Es, dsum[2]);
@@ -453,11 +496,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
             const int gx = halo_index<BC>(i0 - 1 + li, G.nx);
             const int gy = halo_index<BC>(j0 - 1 + lj, G.ny);
             const long long c = (long long)gy * G.nx + gx;
-            lh[k] = (TC)a.X[c];
-            lu[k] = (TC)a.X[P + c];
-            lv[k] = (TC)a.X[2 * P + c];
-            lw[k] = (TC)a.X[3 * P + c];
-            le[k] = (TC)a.X[4 * P + c];
+            lh[k] = cvt<TC>(a.X[c]);
+            lu[k] = cvt<TC>(a.X[P + c]);
+            lv[k] = cvt<TC>(a.X[2 * P + c]);
+            lw[k] = cvt<TC>(a.X[3 * P + c]);
+            le[k] = cvt<TC>(a.X[4 * P + c]);
             lb[k] = a.b[c];
         }
     }
@@ -473,11 +516,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
             const int gx = halo_index<BC>(i0 - 1 + li, G.nx);
             const int gy = halo_index<BC>(j0 - 1 + lj, G.ny);
             const long long c = (long long)gy * G.nx + gx;
-            h = (TC)a.X[c];
-            u = (TC)a.X[P + c];
-            v = (TC)a.X[2 * P + c];
-            w = (TC)a.X[3 * P + c];
-            eta = (TC)a.X[4 * P + c];
+            h = cvt<TC>(a.X[c]);
+            u = cvt<TC>(a.X[P + c]);
+            v = cvt<TC>(a.X[2 * P + c]);
+            w = cvt<TC>(a.X[3 * P + c]);
+            eta = cvt<TC>(a.X[4 * P + c]);
             bb = a.b[c];
         }
         bad |= h_flags(h);
@@ -499,29 +542,29 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
         const long long c = (long long)gj * G.nx + gi;
         if (MODE == MODE_RHS) {
 #pragma unroll
-            for (int f = 0; f < 5; f++) a.out[f * P + c] = (TA)k[f];
+            for (int f = 0; f < 5; f++) a.out[f * P + c] = cvt<TA>(k[f]);
         } else if (MODE == MODE_S1 || MODE == MODE_S2 || MODE == MODE_S3) {
 #pragma unroll
             for (int f = 0; f < 5; f++) {
                 const TA qv = kEarlyStage ? pq[ry][f] : a.qn[f * P + c];
-                const TA kv = (TA)k[f];
+                const TA kv = cvt<TA>(k[f]);
                 const TA av = (MODE == MODE_S1) ? qv : (kEarlyStage ? pa[ry][f] : a.acc[f * P + c]);
                 a.acc[f * P + c] = fma_(a.c_acc, kv, av);
-                a.Qout[f * P + c] = (TC)fma_(a.c_q, kv, qv);
+                a.Qout[f * P + c] = cvt<TC>(fma_(a.c_q, kv, qv));
             }
         } else if (MODE == MODE_S4 || MODE == MODE_S4D) {
             double qn1[5];
 #pragma unroll
             for (int f = 0; f < 5; f++) {
-                const TA o = fma_(a.c_acc, (TA)k[f], kEarlyStage ? pa[ry][f] : a.acc[f * P + c]);
+                const TA o = fma_(a.c_acc, cvt<TA>(k[f]), kEarlyStage ? pa[ry][f] : a.acc[f * P + c]);
                 a.out[f * P + c] = o;
-                qn1[f] = (double)o;
+                qn1[f] = cvt<double>(o);
             }
             if (MODE == MODE_S4D) node_mass_energy<BC>(qn1, a.b64[c], gi, gj, G, dsum);
         } else if (MODE == MODE_DIAG) {
             double qd[5];
 #pragma unroll
-            for (int f = 0; f < 5; f++) qd[f] = (double)a.X[f * P + c];
+            for (int f = 0; f < 5; f++) qd[f] = cvt<double>(a.X[f * P + c]);
             node_diag<TC, BC>(qd, a.b64[c], gi, gj, G, k, dsum);
         }
     }
@@ -613,7 +656,7 @@ template <typename TD>
 __global__ void k_convert(const double* __restrict__ src, TD* __restrict__ dst, long long n) {
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x)
-        dst[k] = (TD)src[k];
+        dst[k] = cvt<TD>(src[k]);
 }
 
 }  // namespace sgn

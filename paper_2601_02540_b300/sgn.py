@@ -21,8 +21,8 @@ STATUS = {0: "SGN_OK", 1: "SGN_E_INVAL", 2: "SGN_E_NOMEM", 3: "SGN_E_CUDA",
           4: "SGN_E_NONPOSITIVE_H", 5: "SGN_E_NONFINITE", 6: "SGN_E_TIMEOUT",
           7: "SGN_E_UNSUPPORTED"}
 PERIODIC, REFLECTING = 0, 1
-F64, F32, F32_F64ACC = 0, 1, 2
-PREC = {"f64": F64, "f32": F32, "f32_f64acc": F32_F64ACC}
+F64, F32, F32_F64ACC, DF64 = 0, 1, 2, 3
+PREC = {"f64": F64, "f32": F32, "f32_f64acc": F32_F64ACC, "df64": DF64}
 
 # every entry point the header declares: name -> (restype, argtypes)
 _V = ctypes.c_void_p

@@ -22,7 +22,7 @@ import gpu_util as gu
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f32_f64acc"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32_f64acc", "df64"])
 @pytest.mark.parametrize("bc", [PERIODIC, REFLECTING])
 def test_step_diag_equals_step_then_mass_energy(prec, bc):
     p = inputs.smooth_state(70, 45, bc, seed=31, xmax=1.3, ymax=0.9)
