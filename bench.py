@@ -52,13 +52,14 @@ FP64_NOMINAL_TFLOPS = 1.25     # B300 dense FP64 (nominal; no measured entry)
 #   stage 1: read q, b; write acc, Q             16 planes
 #   stages 2, 3: read Q, b, q, acc; write acc, Q  26 planes
 #   stage 4: read Q, b, acc; write q              16 planes
-BYTES_PER_CELL_STAGE = {"f64": 84 * 8 / 4, "f32": 84 * 4 / 4, "f32_f64acc": 536 / 4}
+BYTES_PER_CELL_STAGE = {"f64": 84 * 8 / 4, "f32": 84 * 4 / 4, "f32_f64acc": 536 / 4,
+                        "df64": 84 * 8 / 4}     # df64: stage states as float pairs, 8 bytes
 # Algorithmic floating-point operations per cell-stage of the implemented
 # formulation (an FMA counts 2; 1/h counts 1): products and eta + 3/2 b 14,
 # pointwise coefficients 16, 22 differences, h 9, u 25, v 25, w 18, eta 6,
 # stage algebra 17.5 (average of 20, 20, 20, 10).
 FLOPS_PER_CELL_STAGE = 152.5
-DTYPE_NAME = {"f64": "f64", "f32": "f32", "f32_f64acc": "f32+f64acc"}
+DTYPE_NAME = {"f64": "f64", "f32": "f32", "f32_f64acc": "f32+f64acc", "df64": "df64 (float pairs)"}
 
 
 def _peaks() -> tuple[float, str]:
@@ -232,7 +233,7 @@ def run_ours(args) -> None:
     results = {}
     finals = {}
     drift = {}
-    for prec in ("f64", "f32", "f32_f64acc"):
+    for prec in ("f64", "f32", "f32_f64acc", "df64"):
         s = sgn.Solver.from_problem(p, prec=prec)
         q = s.state(p.q0)
         s.init_aux(q)
@@ -268,7 +269,7 @@ def run_ours(args) -> None:
     errors = {}
     if "f64" in finals:
         ref = finals["f64"]
-        for prec in ("f32", "f32_f64acc"):
+        for prec in ("f32", "f32_f64acc", "df64"):
             if prec in finals:
                 d = (finals[prec] - ref).abs().amax(dim=(1, 2))
                 den = ref.abs().amax(dim=(1, 2)).clamp_min(1e-3 * float(ref[0].abs().max()))

@@ -101,7 +101,7 @@ sgn_status check_state_ptr(const void* p, const char* name) {
 template <typename TC, typename TIN, typename TA, int BC, int MODE>
 cudaError_t launch_stage(const sgn_ctx* c, const StageArgs<TC, TIN, TA>& a, cudaStream_t s) {
     auto kern = sgn::k_stage<TC, TIN, TA, BC, MODE>;
-    const size_t smem = sgn::stage_smem_bytes<TC, MODE>(sgn::ROWS_PER_THREAD);
+    const size_t smem = sgn::stage_smem_bytes<TC, MODE>(sgn::StageShape<TC>::rows);
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
@@ -619,7 +619,9 @@ sgn_status sgn_create(const sgn_params* p, const void* b_dev, sgn_ctx** out) {
     *out = nullptr;
     if (!p) return fail(SGN_E_INVAL, "params is NULL");
     if (p->nx < 3 || p->ny < 3) return fail(SGN_E_INVAL, "grid %dx%d: need nx, ny >= 3", p->nx, p->ny);
-    if ((p->ny + sgn::TILE_Y - 1) / sgn::TILE_Y > 65535)
+    // tile height of the stage kernels for this compute type (StageShape)
+    const int tile_y = p->prec == SGN_DF64 ? sgn::THREADS_Y * sgn::StageShape<sgn::df64>::rows : sgn::TILE_Y;
+    if ((p->ny + tile_y - 1) / tile_y > 65535)
         return fail(SGN_E_INVAL, "ny = %d exceeds the launch-grid limit", p->ny);
     if (!(std::isfinite(p->xmin) && std::isfinite(p->xmax) && p->xmax > p->xmin &&
           std::isfinite(p->ymin) && std::isfinite(p->ymax) && p->ymax > p->ymin))
@@ -642,7 +644,7 @@ sgn_status sgn_create(const sgn_params* p, const void* b_dev, sgn_ctx** out) {
     sgn::fill_geom(G, p->nx, p->ny, dx, dy, p->g, p->lambda);
     c->tc_size = (p->prec == SGN_F64 || p->prec == SGN_DF64) ? 8 : sizeof(float);
     c->ta_size = p->prec == SGN_F32 ? sizeof(float) : sizeof(double);
-    c->grid = dim3((p->nx + sgn::TILE_X - 1) / sgn::TILE_X, (p->ny + sgn::TILE_Y - 1) / sgn::TILE_Y);
+    c->grid = dim3((p->nx + sgn::TILE_X - 1) / sgn::TILE_X, (p->ny + tile_y - 1) / tile_y);
     c->nblk = (long long)c->grid.x * c->grid.y;
 
     const size_t plane = (size_t)G.plane;

@@ -103,19 +103,19 @@ __device__ __forceinline__ df64 recip_df64(df64 h) {
     return r;
 }
 
-// double -> df64 by integer operations: hi = the double truncated to 24
+// double -> df64 by integer operations only: hi = the double truncated to 24
 // significant bits, lo = the next 24 of the remaining 29 (truncated), so
-// hi + lo equals x to within 2^-48 |x|.  Zero and values outside the normal
-// float range take the exact conversion path.
+// hi + lo equals x to within 2^-48 |x|.  Magnitudes below the normal float
+// range become +-0; above it (and infinities) +-inf; NaN stays NaN.
 __device__ __forceinline__ df64 df64_from_double(double x) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
     const unsigned sign = (unsigned)(bits >> 63) << 31;
-    if ((bits << 1) == 0ull) return {__uint_as_float(sign), 0.0f};      // +-0
     const int E = (int)((bits >> 52) & 0x7ff);
     const int ef = E - 1023 + 127;
-    if (ef < 1 || ef > 254) {
-        const float h = __double2float_rz(x);
-        return {h, __double2float_rn(x - (double)h)};
+    if (ef < 1) return {__uint_as_float(sign), 0.0f};                    // +-0 and tiny
+    if (ef > 254) {
+        const bool nan = E == 0x7ff && (bits & 0xfffffffffffffull) != 0ull;
+        return {__uint_as_float(sign | 0x7f800000u | (nan ? 0x400000u : 0u)), 0.0f};
     }
     const unsigned long long m = bits & 0xfffffffffffffull;
     df64 r;
@@ -136,16 +136,18 @@ __device__ __forceinline__ df64 df64_from_double(double x) {
     return r;
 }
 
-// float -> double by integer operations (exact; zero and subnormal floats
-// take the exact conversion instruction).
+// float -> double by integer operations only (exact for normal floats;
+// subnormal floats, below 2^-126, become +-0; infinities and NaN keep their
+// class).
 __device__ __forceinline__ double double_of_float_bits(float f) {
     const unsigned b = __float_as_uint(f);
-    if ((b << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)(b >> 31) << 63));  // +-0
+    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
     const unsigned e = (b >> 23) & 0xff;
-    if (e == 0 || e == 0xff) return (double)f;
-    const unsigned long long d = ((unsigned long long)(b >> 31) << 63) |
-                                 ((unsigned long long)(e - 127 + 1023) << 52) |
-                                 ((unsigned long long)(b & 0x7fffffu) << 29);
+    const unsigned long long m = (unsigned long long)(b & 0x7fffffu) << 29;
+    unsigned long long d;
+    if (e == 0) d = sign;                                          // +-0 and subnormal
+    else if (e == 0xff) d = sign | 0x7ff0000000000000ull | m;      // inf, NaN
+    else d = sign | ((unsigned long long)(e - 127 + 1023) << 52) | m;
     return __longlong_as_double((long long)d);
 }
 

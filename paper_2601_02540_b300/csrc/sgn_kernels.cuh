@@ -440,6 +440,18 @@ __device__ __forceinline__ void node_mass_energy(const double q[5], double bb, i
     dsum[2] = fma_(M, e.Es, dsum[2]);
 }
 
+// Next stage state Q = q_n + c k in the compute type: in the state type and
+// rounded (float, double), or, for df64, entirely in float-pair arithmetic
+// (no FP64-pipe instruction).
+template <typename TC, typename TA>
+__device__ __forceinline__ TC stage_state(TA c, TC k, TA kv, TA qv) {
+    return cvt<TC>(fma_(c, kv, qv));
+}
+template <>
+__device__ __forceinline__ df64 stage_state<df64, double>(double c, df64 k, double, double qv) {
+    return fma_(df64_from_double(c), k, df64_from_double(qv));
+}
+
 // Dynamic shared memory of a stage launch: the halo tile of the operands.
 template <typename TC, int MODE>
 constexpr size_t stage_smem_bytes(int rows) {
@@ -550,7 +562,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
                 const TA kv = cvt<TA>(k[f]);
                 const TA av = (MODE == MODE_S1) ? qv : (kEarlyStage ? pa[ry][f] : a.acc[f * P + c]);
                 a.acc[f * P + c] = fma_(a.c_acc, kv, av);
-                a.Qout[f * P + c] = cvt<TC>(fma_(a.c_q, kv, qv));
+                a.Qout[f * P + c] = stage_state<TC, TA>(a.c_q, k[f], kv, qv);
             }
         } else if (MODE == MODE_S4 || MODE == MODE_S4D) {
             double qn1[5];
@@ -588,14 +600,30 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
     }
 }
 
+// Tile shape of the single-grid stage kernel per compute type: rows per
+// thread (tile height 8 rows) and the blocks per SM the registers must allow.
+// df64 is bound by the latency of its dependent float operations, so it takes
+// 32x8 tiles (half the shared memory) and four resident blocks.
+template <typename TC>
+struct StageShape {
+    static constexpr int rows = ROWS_PER_THREAD;
+    static constexpr int min_blocks = 1;
+};
+template <>
+struct StageShape<df64> {
+    static constexpr int rows = 1;
+    static constexpr int min_blocks = 4;
+};
+
 template <typename TC, typename TIN, typename TA, int BC, int MODE>
-__global__ void __launch_bounds__(BLOCK_THREADS)
+__global__ void __launch_bounds__(BLOCK_THREADS, StageShape<TC>::min_blocks)
 k_stage(StageArgs<TC, TIN, TA> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TC* sm = reinterpret_cast<TC*>(smem_raw);
     const long long blk = (long long)blockIdx.y * gridDim.x + blockIdx.x;
-    stage_tile<TC, TIN, TA, BC, MODE, ROWS_PER_THREAD>(a, a.G, blockIdx.x * TILE_X, blockIdx.y * TILE_Y, sm,
-                                                       a.partials ? a.partials + blk * NDIAG : nullptr);
+    constexpr int R = StageShape<TC>::rows;
+    stage_tile<TC, TIN, TA, BC, MODE, R>(a, a.G, blockIdx.x * TILE_X, blockIdx.y * (THREADS_Y * R), sm,
+                                         a.partials ? a.partials + blk * NDIAG : nullptr);
 }
 
 // Second pass of the diagnostics: one block sums the per-block partials in a
