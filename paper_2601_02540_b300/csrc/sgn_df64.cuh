@@ -151,6 +151,27 @@ __device__ __forceinline__ double double_of_float_bits(float f) {
     return __longlong_as_double((long long)d);
 }
 
+// double -> float rounded to nearest (ties to even) by integer operations only:
+// the same value as the conversion instruction for results in the normal
+// float range; magnitudes below it become +-0, above it +-inf (NaN stays NaN).
+__device__ __forceinline__ float float_of_double_rn(double x) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const unsigned sign = (unsigned)(bits >> 63) << 31;
+    const int E = (int)((bits >> 52) & 0x7ff);
+    const int ef = E - 1023 + 127;
+    if (ef < 1) return __uint_as_float(sign);
+    if (ef > 254) {
+        const bool nan = E == 0x7ff && (bits & 0xfffffffffffffull) != 0ull;
+        return __uint_as_float(sign | 0x7f800000u | (nan ? 0x400000u : 0u));
+    }
+    const unsigned long long m = bits & 0xfffffffffffffull;
+    unsigned body = ((unsigned)ef << 23) | (unsigned)(m >> 29);     // exponent and 23 fraction bits
+    const unsigned rest = (unsigned)(m & 0x1fffffffull);              // the 29 dropped bits
+    const unsigned half = 0x10000000u;
+    body += (rest > half || (rest == half && (body & 1u))) ? 1u : 0u; // a carry may reach the exponent
+    return __uint_as_float(sign | body);
+}
+
 // df64 -> double: the two parts exactly, then one rounded double addition.
 __device__ __forceinline__ double double_of_df64(df64 a) {
     return __dadd_rn(double_of_float_bits(a.hi), double_of_float_bits(a.lo));

@@ -142,6 +142,13 @@ template <>
 __device__ __forceinline__ df64 cvt<df64, df64>(df64 x) { return x; }
 template <>
 __device__ __forceinline__ double cvt<double, df64>(df64 x) { return double_of_df64(x); }
+// float <-> double (the mixed-precision mode) without the FP64-pipe conversion
+// instructions: round to nearest even by integer operations, and the exact
+// widening of a normal float (below 2^-126 flushes to zero)
+template <>
+__device__ __forceinline__ float cvt<float, double>(double x) { return float_of_double_rn(x); }
+template <>
+__device__ __forceinline__ double cvt<double, float>(float x) { return double_of_float_bits(x); }
 
 template <typename TC, typename TIN, typename TA>
 struct StageArgs {
