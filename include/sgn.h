@@ -44,8 +44,9 @@
  *                   in double-word arithmetic (a float pair hi + lo, about 48
  *                   significant bits, relative rounding ~2^-48) on the FP32
  *                   units, which on this GPU outnumber the FP64 units 64 to
- *                   one.  The adjoint, adaptive, relaxed, manufactured and
- *                   relaxation-zone entry points need SGN_F64.
+ *                   one.  The adjoint, relaxed, manufactured and
+ *                   relaxation-zone entry points need SGN_F64; the adaptive
+ *                   integrator takes SGN_F64 or SGN_DF64.
  *   "state type" below means double for SGN_F64, SGN_F32_F64ACC and SGN_DF64,
  *   float for SGN_F32.  Bathymetry arguments are always double.  Diagnostics are always
  *   accumulated in double.
@@ -283,7 +284,8 @@ SGN_API sgn_status sgn_step_relaxed(sgn_ctx* ctx, void* q_dev, double dt, int ns
  * after each attempt (synchronizes `stream` every attempt).
  * hist (host, 3*max_attempts doubles, or NULL) receives {dt, err, accepted}
  * per attempt; stats (host, 5 doubles) receives {accepted, rejected, t
- * reached, next dt, attempts}.  SGN_F64 contexts only (else
+ * reached, next dt, attempts}.  SGN_F64 or SGN_DF64 contexts (the RHS in
+ * double or in float pairs; the state, slopes and error norm in double; else
  * SGN_E_UNSUPPORTED).  The first call of a context allocates 35 planes of
  * scratch (SGN_E_NOMEM if that fails).  An initial state with h <= 0 or a
  * non-finite h returns SGN_E_NONPOSITIVE_H / SGN_E_NONFINITE without an

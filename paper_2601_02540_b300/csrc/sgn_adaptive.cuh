@@ -18,7 +18,8 @@
 //   BS_K4  stages q1, writes k4 and the per-block sum of
 //          (e / (atol + rtol max(|q_n|, |q1|)))^2 over its nodes and fields
 //          (fixed-order reduction; the host takes the root mean square).
-// FP64 only.
+// Compute type FP64 or df64 (float pairs); the state, the stage slopes and the
+// error arithmetic are double in both.
 #pragma once
 
 #include "sgn_kernels.cuh"
@@ -33,7 +34,7 @@ struct BsArgs {
     const double* k2;      // BS_K3, BS_K4
     const double* k3;      // BS_K4
     const double* X;       // stage input: Y3 (BS_K3) or q1 (BS_K4)
-    const double* b;
+    const void* b;         // bathymetry in the compute type
     double* kout;          // this stage's k
     double* Yout;          // BS_K2: Y3; BS_K3: q1
     double* partials;      // BS_K4: NDIAG doubles per block, the sum in slot 0
@@ -45,28 +46,34 @@ struct BsArgs {
     double rtol, atol;
 };
 
-template <int BC, int MODE>
-__global__ void __launch_bounds__(BLOCK_THREADS) k_bs3_stage(BsArgs a) {
+// TC: compute type of the RHS (double, or df64 with the float-pair stage
+// arithmetic); every array in global memory is double.
+template <typename TC, int BC, int MODE>
+__global__ void __launch_bounds__(BLOCK_THREADS, StageShape<TC>::min_blocks) k_bs3_stage(BsArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* sm = reinterpret_cast<double*>(smem_raw);
+    TC* sm = reinterpret_cast<TC*>(smem_raw);
+    constexpr int R = StageShape<TC>::rows;
+    constexpr int HX = TILE_X + 2, HN = HX * (THREADS_Y * R + 2);
     const Geom& G = a.G;
     const long long P = G.plane;
-    const int i0 = blockIdx.x * TILE_X, j0 = blockIdx.y * TILE_Y;
+    const int i0 = blockIdx.x * TILE_X, j0 = blockIdx.y * (THREADS_Y * R);
     const int tid = threadIdx.y * TILE_X + threadIdx.x;
 
     // ---- phase 1: halo tile of the stage input and of its products
     int bad = 0;
-    for (int t = tid; t < HALO_N; t += BLOCK_THREADS) {
-        const int li = t % HALO_X, lj = t / HALO_X;
+    const TC c_in = cvt<TC>(a.c_in);
+    for (int t = tid; t < HN; t += BLOCK_THREADS) {
+        const int li = t % HX, lj = t / HX;
         const int gx = halo_index<BC>(i0 - 1 + li, G.nx);
         const int gy = halo_index<BC>(j0 - 1 + lj, G.ny);
         const long long c = (long long)gy * G.nx + gx;
-        double y[5];
+        TC y[5];
 #pragma unroll
         for (int f = 0; f < 5; f++)
-            y[f] = (MODE == BS_K2) ? fma_(a.c_in, a.k1[f * P + c], a.q[f * P + c]) : a.X[f * P + c];
+            y[f] = (MODE == BS_K2) ? fma_(c_in, cvt<TC>(a.k1[f * P + c]), cvt<TC>(a.q[f * P + c]))
+                                   : cvt<TC>(a.X[f * P + c]);
         bad |= h_flags(y[0]);
-        store_operands<double, HALO_N>(sm, t, y[0], y[1], y[2], y[3], y[4], a.b[c]);
+        store_operands<TC, HN>(sm, t, y[0], y[1], y[2], y[3], y[4], static_cast<const TC*>(a.b)[c]);
     }
     if (bad) atomicOr(a.flag, bad);
     __syncthreads();
@@ -74,27 +81,31 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_bs3_stage(BsArgs a) {
     // ---- phase 2: k at this thread's nodes and the stage epilogue
     double esum = 0.0;
     const int gi = i0 + threadIdx.x;
+    const TC c_y = cvt<TC>(a.c_y), cb1 = cvt<TC>(a.cb1), cb2 = cvt<TC>(a.cb2), cb3 = cvt<TC>(a.cb3);
+    const TC ce1 = cvt<TC>(a.ce1), ce2 = cvt<TC>(a.ce2), ce3 = cvt<TC>(a.ce3), ce4 = cvt<TC>(a.ce4);
 #pragma unroll
-    for (int ry = 0; ry < ROWS_PER_THREAD; ry++) {
+    for (int ry = 0; ry < R; ry++) {
         const int ly = threadIdx.y + ry * THREADS_Y;
         const int gj = j0 + ly;
         if (gi >= G.nx || gj >= G.ny) continue;
-        const int t = (ly + 1) * HALO_X + (threadIdx.x + 1);
-        double k[5];
-        node_rhs<double, BC, HALO_X, HALO_N>(sm, t, gi, gj, G, k);
+        const int t = (ly + 1) * HX + (threadIdx.x + 1);
+        TC k[5];
+        node_rhs<TC, BC, HX, HN>(sm, t, gi, gj, G, k);
         const long long c = (long long)gj * G.nx + gi;
 #pragma unroll
         for (int f = 0; f < 5; f++) {
             const long long o = f * P + c;
-            a.kout[o] = k[f];
+            a.kout[o] = cvt<double>(k[f]);
             if (MODE == BS_K2) {
-                a.Yout[o] = fma_(a.c_y, k[f], a.q[o]);
+                a.Yout[o] = cvt<double>(fma_(c_y, k[f], cvt<TC>(a.q[o])));
             } else if (MODE == BS_K3) {
-                a.Yout[o] = fma_(a.cb3, k[f], fma_(a.cb2, a.k2[o], fma_(a.cb1, a.k1[o], a.q[o])));
+                a.Yout[o] = cvt<double>(fma_(cb3, k[f], fma_(cb2, cvt<TC>(a.k2[o]),
+                                                              fma_(cb1, cvt<TC>(a.k1[o]), cvt<TC>(a.q[o])))));
             } else {
-                const double e = fma_(a.ce4, k[f], fma_(a.ce3, a.k3[o], fma_(a.ce2, a.k2[o],
-                                                                            mul_(a.ce1, a.k1[o]))));
-                const double q1 = sm[f * HALO_N + t];     // this node's stage input (OP_H..OP_ETA)
+                const double e = cvt<double>(fma_(ce4, k[f], fma_(ce3, cvt<TC>(a.k3[o]),
+                                                                  fma_(ce2, cvt<TC>(a.k2[o]),
+                                                                       mul_(ce1, cvt<TC>(a.k1[o]))))));
+                const double q1 = a.X[o];                 // this node's stage input
                 const double sc = fma_(a.rtol, fmax(fabs(a.q[o]), fabs(q1)), a.atol);
                 const double r = mul_(e, recip<double>(sc));
                 esum = fma_(r, r, esum);

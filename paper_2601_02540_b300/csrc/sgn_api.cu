@@ -336,10 +336,10 @@ sgn_status need_f64(const sgn_ctx* c, const char* what) {
 }
 
 // ---- adaptive integrator (Sec. 6): third-order FSAL pair, host-side control
-template <int BC, int MODE>
+template <typename TC, int BC, int MODE>
 cudaError_t launch_bs3(const sgn_ctx* c, const sgn::BsArgs& a, cudaStream_t s) {
-    auto kern = sgn::k_bs3_stage<BC, MODE>;
-    const size_t smem = sgn::stage_smem_bytes<double, sgn::MODE_RHS>(sgn::ROWS_PER_THREAD);
+    auto kern = sgn::k_bs3_stage<TC, BC, MODE>;
+    const size_t smem = sgn::stage_smem_bytes<TC, sgn::MODE_RHS>(sgn::StageShape<TC>::rows);
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
@@ -359,7 +359,7 @@ constexpr double BS_E3 = 4.0 / 9.0 - 1.0 / 3.0, BS_E4 = -1.0 / 8.0;
 // step-size control: dt_next = dt min(QMAX, max(QMIN, SAFETY err^(-1/3)))
 constexpr double BS_SAFETY = 0.9, BS_QMIN = 0.2, BS_QMAX = 10.0;
 
-template <int BC>
+template <typename TC, int BC>
 sgn_status run_adaptive(sgn_ctx* c, double* q_user, double t0, double t_end, double dt0, double rtol,
                         double atol, int max_attempts, double* hist, double* stats, cudaStream_t s) {
     const long long P5 = 5 * c->G.plane;
@@ -372,13 +372,13 @@ sgn_status run_adaptive(sgn_ctx* c, double* q_user, double t0, double t_end, dou
     double* q1 = c->bs + 5 * P5;
     double* qc = c->bs + 6 * P5;
     CUDA_TRY(cudaMemcpyAsync(qc, q_user, bytes5, cudaMemcpyDeviceToDevice, s), "copy q");
-    CUDA_TRY((run_rhs<double, double, BC>(c, qc, k1, s)), "k1");
+    CUDA_TRY((run_rhs<TC, double, BC>(c, qc, k1, s)), "k1");
     sgn_status st = read_flag(c, s);
     if (st != SGN_OK) return st;
 
     sgn::BsArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.b = c->b64;
+    a.b = c->bT;                 // bathymetry in the compute type (the double one for FP64)
     a.flag = c->flag;
     a.G = c->G;
     a.rtol = rtol;
@@ -398,7 +398,7 @@ sgn_status run_adaptive(sgn_ctx* c, double* q_user, double t0, double t_end, dou
         a.c_y = 0.75 * h;
         a.kout = k2;
         a.Yout = Y3;
-        CUDA_TRY((launch_bs3<BC, sgn::BS_K2>(c, a, s)), "adaptive stage 2");
+        CUDA_TRY((launch_bs3<TC, BC, sgn::BS_K2>(c, a, s)), "adaptive stage 2");
         // k3 = f(Y3); q1 = q + h (b1 k1 + b2 k2 + b3 k3)
         a.X = Y3;
         a.kout = k3;
@@ -406,7 +406,7 @@ sgn_status run_adaptive(sgn_ctx* c, double* q_user, double t0, double t_end, dou
         a.cb1 = h * BS_B1;
         a.cb2 = h * BS_B2;
         a.cb3 = h * BS_B3;
-        CUDA_TRY((launch_bs3<BC, sgn::BS_K3>(c, a, s)), "adaptive stage 3");
+        CUDA_TRY((launch_bs3<TC, BC, sgn::BS_K3>(c, a, s)), "adaptive stage 3");
         // k4 = f(q1); error partial sums
         a.X = q1;
         a.kout = k4;
@@ -414,7 +414,7 @@ sgn_status run_adaptive(sgn_ctx* c, double* q_user, double t0, double t_end, dou
         a.ce2 = h * BS_E2;
         a.ce3 = h * BS_E3;
         a.ce4 = h * BS_E4;
-        CUDA_TRY((launch_bs3<BC, sgn::BS_K4>(c, a, s)), "adaptive stage 4");
+        CUDA_TRY((launch_bs3<TC, BC, sgn::BS_K4>(c, a, s)), "adaptive stage 4");
         sgn::k_reduce_partials<<<1, 256, 0, s>>>(c->partials, c->nblk, c->dout);
         count_launch();
         CUDA_TRY(cudaGetLastError(), "error reduction");
@@ -993,7 +993,8 @@ sgn_status sgn_step_relaxed(sgn_ctx* c, void* q_dev, double dt, int nsteps, doub
 sgn_status sgn_step_adaptive(sgn_ctx* c, void* q_dev, double t0, double t_end, double dt0, double rtol,
                              double atol, int max_attempts, double* hist, double* stats, void* stream) {
     if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
-    if (c->p.prec != SGN_F64) return fail(SGN_E_UNSUPPORTED, "sgn_step_adaptive needs an SGN_F64 context");
+    if (c->p.prec != SGN_F64 && c->p.prec != SGN_DF64)
+        return fail(SGN_E_UNSUPPORTED, "sgn_step_adaptive needs an SGN_F64 or SGN_DF64 context");
     sgn_status st = check_state_ptr(q_dev, "q_dev");
     if (st != SGN_OK) return st;
     if (!stats) return fail(SGN_E_INVAL, "stats is NULL");
@@ -1013,9 +1014,16 @@ sgn_status sgn_step_adaptive(sgn_ctx* c, void* q_dev, double t0, double t_end, d
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     double* q = static_cast<double*>(q_dev);
-    return c->p.bc == SGN_BC_REFLECTING
-               ? run_adaptive<sgn::BC_REFLECTING>(c, q, t0, t_end, dt0, rtol, atol, max_attempts, hist, stats, s)
-               : run_adaptive<sgn::BC_PERIODIC>(c, q, t0, t_end, dt0, rtol, atol, max_attempts, hist, stats, s);
+    const bool refl = c->p.bc == SGN_BC_REFLECTING;
+    if (c->p.prec == SGN_DF64)
+        return refl ? run_adaptive<sgn::df64, sgn::BC_REFLECTING>(c, q, t0, t_end, dt0, rtol, atol, max_attempts,
+                                                                 hist, stats, s)
+                    : run_adaptive<sgn::df64, sgn::BC_PERIODIC>(c, q, t0, t_end, dt0, rtol, atol, max_attempts,
+                                                               hist, stats, s);
+    return refl ? run_adaptive<double, sgn::BC_REFLECTING>(c, q, t0, t_end, dt0, rtol, atol, max_attempts, hist,
+                                                           stats, s)
+                : run_adaptive<double, sgn::BC_PERIODIC>(c, q, t0, t_end, dt0, rtol, atol, max_attempts, hist,
+                                                         stats, s);
 }
 
 }  // extern "C"

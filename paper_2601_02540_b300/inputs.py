@@ -326,6 +326,36 @@ def soliton(n: int, direction: str = "x", amp: float = 0.2, h_inf: float = 1.0, 
     return p
 
 
+def gaussian_obstacle(dx: float = 0.025, amp: float = 0.0365, h_inf: float = 0.2, x0: float = -3.0,
+                      lam: float = LAMBDA_DEFAULT, g: float = G_DEFAULT, t_end: float = 12.0) -> Problem:
+    """The shape of the paper's solitary wave over a Gaussian obstacle (Sec. 6,
+    "Solitary Wave over a Gaussian Obstacle"): periodic [-5, 35] x [-10, 10],
+    dx = dy = 0.025 (1600 x 800), still-water depth h_inf = 0.2, bathymetry
+    b = 0.1 exp(-(x^2 + y^2)/2), a solitary wave of amplitude 0.0365 starting
+    at x = -3 and moving toward +x, lambda = 500, to t = 12.  The paper starts
+    from the numerically computed traveling wave of the hyperbolic system (out
+    of scope here); this stand-in uses the SGN solitary-wave profile
+    (eq. (solitary_wave_analytical)), which the hyperbolic system carries with
+    a small adjustment.  Free surface at rest: h + b = h_inf."""
+    xmin, xmax, ymin, ymax = -5.0, 35.0, -10.0, 10.0
+    nx, ny = int(round((xmax - xmin) / dx)), int(round((ymax - ymin) / dx))
+    X, Y = _mesh(nx, ny, xmin, xmax, ymin, ymax, PERIODIC)
+    b = 0.1 * np.exp(-(X * X + Y * Y) / 2.0)
+    eps = amp / h_inf
+    kappa = np.sqrt(3.0 * eps / (4.0 * h_inf ** 2 * (1.0 + eps)))
+    C = np.sqrt(g * h_inf * (1.0 + eps))
+    L = xmax - xmin
+    xi = np.mod(X - x0 - xmin, L) + xmin          # x - x0 wrapped to [-5, 35)
+    wave = h_inf * eps / np.cosh(kappa * xi) ** 2  # surface elevation of the solitary wave
+    q0 = np.zeros((5, ny, nx))
+    q0[0] = h_inf + wave - b
+    q0[1] = C * wave / (h_inf + wave)              # C (1 - h_inf / (h_inf + wave))
+    p = Problem(nx, ny, xmin, xmax, ymin, ymax, PERIODIC, b, q0, g=g, lam=lam, name="gaussian_obstacle")
+    p.dt = cfl_dt(b, q0[0], q0[1], q0[2], dx, dx, g, lam)
+    p.extra.update(t_end=t_end, amp=amp, h_inf=h_inf, C=C)
+    return p
+
+
 # ----------------------------------------------------------------------------- test states
 def smooth_state(nx: int, ny: int, bc: int, seed: int = 0, xmin=0.0, xmax=1.0, ymin=0.0,
                  ymax=1.0, lam: float = LAMBDA_DEFAULT, amp: float = 0.2) -> Problem:
