@@ -29,14 +29,14 @@ namespace sgn {
 enum { BS_K2 = 0, BS_K3 = 1, BS_K4 = 2 };
 
 struct BsArgs {
-    const double* q;       // q_n (5 planes)
-    const double* k1;      // f(q_n)
-    const double* k2;      // BS_K3, BS_K4
-    const double* k3;      // BS_K4
-    const double* X;       // stage input: Y3 (BS_K3) or q1 (BS_K4)
+    const double* q;       // q_n (5 planes, double)
+    const void* k1;        // f(q_n)            (compute type)
+    const void* k2;        // BS_K3, BS_K4      (compute type)
+    const void* k3;        // BS_K4             (compute type)
+    void* Y3;              // written by BS_K2, staged by BS_K3 (compute type)
+    double* q1;            // written by BS_K3, staged by BS_K4 (double: the candidate state)
     const void* b;         // bathymetry in the compute type
-    double* kout;          // this stage's k
-    double* Yout;          // BS_K2: Y3; BS_K3: q1
+    void* kout;            // this stage's k    (compute type)
     double* partials;      // BS_K4: NDIAG doubles per block, the sum in slot 0
     int* flag;
     Geom G;
@@ -47,7 +47,8 @@ struct BsArgs {
 };
 
 // TC: compute type of the RHS (double, or df64 with the float-pair stage
-// arithmetic); every array in global memory is double.
+// arithmetic).  The slopes and Y3 are stored in the compute type (a float pair
+// takes 8 bytes, like a double); the state q_n and the candidate q1 in double.
 template <typename TC, int BC, int MODE>
 __global__ void __launch_bounds__(BLOCK_THREADS, StageShape<TC>::min_blocks) k_bs3_stage(BsArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -58,6 +59,11 @@ __global__ void __launch_bounds__(BLOCK_THREADS, StageShape<TC>::min_blocks) k_b
     const long long P = G.plane;
     const int i0 = blockIdx.x * TILE_X, j0 = blockIdx.y * (THREADS_Y * R);
     const int tid = threadIdx.y * TILE_X + threadIdx.x;
+    const TC* __restrict__ k1 = static_cast<const TC*>(a.k1);
+    const TC* __restrict__ k2 = static_cast<const TC*>(a.k2);
+    const TC* __restrict__ k3 = static_cast<const TC*>(a.k3);
+    TC* __restrict__ kout = static_cast<TC*>(a.kout);
+    TC* __restrict__ Y3 = static_cast<TC*>(a.Y3);
 
     // ---- phase 1: halo tile of the stage input and of its products
     int bad = 0;
@@ -70,8 +76,9 @@ __global__ void __launch_bounds__(BLOCK_THREADS, StageShape<TC>::min_blocks) k_b
         TC y[5];
 #pragma unroll
         for (int f = 0; f < 5; f++)
-            y[f] = (MODE == BS_K2) ? fma_(c_in, cvt<TC>(a.k1[f * P + c]), cvt<TC>(a.q[f * P + c]))
-                                   : cvt<TC>(a.X[f * P + c]);
+            y[f] = (MODE == BS_K2)   ? fma_(c_in, k1[f * P + c], cvt<TC>(a.q[f * P + c]))
+                   : (MODE == BS_K3) ? Y3[f * P + c]
+                                     : cvt<TC>(a.q1[f * P + c]);
         bad |= h_flags(y[0]);
         store_operands<TC, HN>(sm, t, y[0], y[1], y[2], y[3], y[4], static_cast<const TC*>(a.b)[c]);
     }
@@ -95,17 +102,14 @@ __global__ void __launch_bounds__(BLOCK_THREADS, StageShape<TC>::min_blocks) k_b
 #pragma unroll
         for (int f = 0; f < 5; f++) {
             const long long o = f * P + c;
-            a.kout[o] = cvt<double>(k[f]);
+            kout[o] = k[f];
             if (MODE == BS_K2) {
-                a.Yout[o] = cvt<double>(fma_(c_y, k[f], cvt<TC>(a.q[o])));
+                Y3[o] = fma_(c_y, k[f], cvt<TC>(a.q[o]));
             } else if (MODE == BS_K3) {
-                a.Yout[o] = cvt<double>(fma_(cb3, k[f], fma_(cb2, cvt<TC>(a.k2[o]),
-                                                              fma_(cb1, cvt<TC>(a.k1[o]), cvt<TC>(a.q[o])))));
+                a.q1[o] = cvt<double>(fma_(cb3, k[f], fma_(cb2, k2[o], fma_(cb1, k1[o], cvt<TC>(a.q[o])))));
             } else {
-                const double e = cvt<double>(fma_(ce4, k[f], fma_(ce3, cvt<TC>(a.k3[o]),
-                                                                  fma_(ce2, cvt<TC>(a.k2[o]),
-                                                                       mul_(ce1, cvt<TC>(a.k1[o]))))));
-                const double q1 = a.X[o];                 // this node's stage input
+                const double e = cvt<double>(fma_(ce4, k[f], fma_(ce3, k3[o], fma_(ce2, k2[o], mul_(ce1, k1[o])))));
+                const double q1 = a.q1[o];                // this node's stage input
                 const double sc = fma_(a.rtol, fmax(fabs(a.q[o]), fabs(q1)), a.atol);
                 const double r = mul_(e, recip<double>(sc));
                 esum = fma_(r, r, esum);

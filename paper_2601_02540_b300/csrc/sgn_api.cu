@@ -364,15 +364,22 @@ sgn_status run_adaptive(sgn_ctx* c, double* q_user, double t0, double t_end, dou
                         double atol, int max_attempts, double* hist, double* stats, cudaStream_t s) {
     const long long P5 = 5 * c->G.plane;
     const size_t bytes5 = (size_t)P5 * sizeof(double);
-    double* k1 = c->bs;
-    double* k2 = c->bs + P5;
-    double* k3 = c->bs + 2 * P5;
-    double* k4 = c->bs + 3 * P5;
-    double* Y3 = c->bs + 4 * P5;
+    static_assert(sizeof(TC) == sizeof(double), "the slots below hold 8-byte values");
+    TC* k1 = reinterpret_cast<TC*>(c->bs);
+    TC* k2 = reinterpret_cast<TC*>(c->bs + P5);
+    TC* k3 = reinterpret_cast<TC*>(c->bs + 2 * P5);
+    TC* k4 = reinterpret_cast<TC*>(c->bs + 3 * P5);
+    TC* Y3 = reinterpret_cast<TC*>(c->bs + 4 * P5);
     double* q1 = c->bs + 5 * P5;
     double* qc = c->bs + 6 * P5;
     CUDA_TRY(cudaMemcpyAsync(qc, q_user, bytes5, cudaMemcpyDeviceToDevice, s), "copy q");
-    CUDA_TRY((run_rhs<TC, double, BC>(c, qc, k1, s)), "k1");
+    {
+        // k1 = f(q), stored in the compute type
+        StageArgs<TC, double, TC> r = base_args<TC, double, TC>(c);
+        r.X = qc;
+        r.out = k1;
+        CUDA_TRY((launch_stage<TC, double, TC, BC, sgn::MODE_RHS>(c, r, s)), "k1");
+    }
     sgn_status st = read_flag(c, s);
     if (st != SGN_OK) return st;
 
@@ -397,18 +404,16 @@ sgn_status run_adaptive(sgn_ctx* c, double* q_user, double t0, double t_end, dou
         a.c_in = 0.5 * h;
         a.c_y = 0.75 * h;
         a.kout = k2;
-        a.Yout = Y3;
+        a.Y3 = Y3;
+        a.q1 = q1;
         CUDA_TRY((launch_bs3<TC, BC, sgn::BS_K2>(c, a, s)), "adaptive stage 2");
         // k3 = f(Y3); q1 = q + h (b1 k1 + b2 k2 + b3 k3)
-        a.X = Y3;
         a.kout = k3;
-        a.Yout = q1;
         a.cb1 = h * BS_B1;
         a.cb2 = h * BS_B2;
         a.cb3 = h * BS_B3;
         CUDA_TRY((launch_bs3<TC, BC, sgn::BS_K3>(c, a, s)), "adaptive stage 3");
         // k4 = f(q1); error partial sums
-        a.X = q1;
         a.kout = k4;
         a.ce1 = h * BS_E1;
         a.ce2 = h * BS_E2;
