@@ -31,12 +31,14 @@
 
 namespace sgn {
 
-// scratch layout (planes): products and 1/h at their OP_ slots (the state planes
-// themselves are read from the state), x weights (11), y weights (11)
+// scratch layout (planes): the differentiated products and 1/h (the state
+// planes themselves are read from the state), then the x weights (11) and the
+// y weights (11)
+enum { AP_HS, AP_HU, AP_HV, AP_HUV, AP_HUW, AP_HVW, AP_E2H, AP_E15, AP_R, ADJ_NP };
 constexpr int ADJ_NW = 11;
-constexpr int ADJ_WX = N_OPS;
-constexpr int ADJ_WY = N_OPS + ADJ_NW;
-constexpr int ADJ_SCRATCH_PLANES = N_OPS + 2 * ADJ_NW;
+constexpr int ADJ_WX = ADJ_NP;
+constexpr int ADJ_WY = ADJ_NP + ADJ_NW;
+constexpr int ADJ_SCRATCH_PLANES = ADJ_NP + 2 * ADJ_NW;
 constexpr int ADJ_BLOCK = 256;
 
 // weight slots: x uses {H,U,V,W,E15,HS,UU,HU,HUV,HUW,E2H},
@@ -110,15 +112,15 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adj_weights(AdjArgs a) {
     const double hu = h * u, hv = h * v, hw = h * w;
     const double hsum = h + bb, rho = eta * r;
     double* S = a.scratch;
-    S[OP_HS * P + c] = h * hsum;
-    S[OP_HU * P + c] = hu;
-    S[OP_HV * P + c] = hv;
-    S[OP_HUV * P + c] = hu * v;
-    S[OP_HUW * P + c] = hu * w;
-    S[OP_HVW * P + c] = hv * w;
-    S[OP_E2H * P + c] = rho * eta;
-    S[OP_E15 * P + c] = fma(1.5, bb, eta);
-    S[OP_R * P + c] = r;
+    S[AP_HS * P + c] = h * hsum;
+    S[AP_HU * P + c] = hu;
+    S[AP_HV * P + c] = hv;
+    S[AP_HUV * P + c] = hu * v;
+    S[AP_HUW * P + c] = hu * w;
+    S[AP_HVW * P + c] = hv * w;
+    S[AP_E2H * P + c] = rho * eta;
+    S[AP_E15 * P + c] = fma(1.5, bb, eta);
+    S[AP_R * P + c] = r;
 
     const double ah = a.A[c], au = a.A[P + c], av = a.A[2 * P + c];
     const double aw = a.A[3 * P + c], ae = a.A[4 * P + c];
@@ -240,15 +242,15 @@ __global__ void __launch_bounds__(ADJ_BLOCK, 2) k_adj_gather(AdjArgs a) {
 #define RY_(base) ((base)[ct] - (base)[cb])
     const double h = X[c], u = X[P + c], v = X[2 * P + c], w = X[3 * P + c], eta = X[4 * P + c];
     const double bb = a.b[c];
-    const double r = S[OP_R * P + c];
+    const double r = S[AP_R * P + c];
     const double ah = a.A[c], au = a.A[P + c], av = a.A[2 * P + c];
     const double aw = a.A[3 * P + c], ae = a.A[4 * P + c];
     // differences used more than once, scaled
     const double xh = kx.s * RX_(X), xu = kx.s * RX_(X + P), xv = kx.s * RX_(X + 2 * P);
-    const double xw = kx.s * RX_(X + 3 * P), xf = kx.s * RX_(S + OP_E15 * P);
+    const double xw = kx.s * RX_(X + 3 * P), xf = kx.s * RX_(S + AP_E15 * P);
     const double yh = ky.s * RY_(X), yu = ky.s * RY_(X + P), yv = ky.s * RY_(X + 2 * P);
-    const double yw = ky.s * RY_(X + 3 * P), yf = ky.s * RY_(S + OP_E15 * P);
-    const double hxhu = kx.hs * RX_(S + OP_HU * P), hyhv = ky.hs * RY_(S + OP_HV * P);  // D(hu)/2, D(hv)/2
+    const double yw = ky.s * RY_(X + 3 * P), yf = ky.s * RY_(S + AP_E15 * P);
+    const double hxhu = kx.hs * RX_(S + AP_HU * P), hyhv = ky.hs * RY_(S + AP_HV * P);  // D(hu)/2, D(hv)/2
 
     const double ar = r * au, br = r * av, cr_ = r * aw;
     const double rho = eta * r, rho2 = rho * rho;
@@ -258,21 +260,21 @@ __global__ void __launch_bounds__(ADJ_BLOCK, 2) k_adj_gather(AdjArgs a) {
     const double huv = 0.5 * uv;
     double Gu = xh * fma(-0.5 * u, u, q2);
     Gu = fma(l12, xf, Gu);
-    Gu = fma(kx.gs, RX_(S + OP_HS * P), Gu);
+    Gu = fma(kx.gs, RX_(S + AP_HS * P), Gu);
     Gu = fma(u, hxhu, Gu);
-    Gu = fma(-kx.l6s, RX_(S + OP_E2H * P), Gu);
-    Gu = fma(ky.hs, RY_(S + OP_HUV * P), Gu);
+    Gu = fma(-kx.l6s, RX_(S + AP_E2H * P), Gu);
+    Gu = fma(ky.hs, RY_(S + AP_HUV * P), Gu);
     Gu = fma(-huv, yh, Gu);
     double Gv = yh * fma(-0.5 * v, v, q2);
     Gv = fma(l12, yf, Gv);
-    Gv = fma(ky.gs, RY_(S + OP_HS * P), Gv);
+    Gv = fma(ky.gs, RY_(S + AP_HS * P), Gv);
     Gv = fma(v, hyhv, Gv);
-    Gv = fma(-ky.l6s, RY_(S + OP_E2H * P), Gv);
-    Gv = fma(kx.hs, RX_(S + OP_HUV * P), Gv);
+    Gv = fma(-ky.l6s, RY_(S + AP_E2H * P), Gv);
+    Gv = fma(kx.hs, RX_(S + AP_HUV * P), Gv);
     Gv = fma(-huv, xh, Gv);
     double Gw = fma(a.lam2x, rho, -G.lam);
-    Gw = fma(kx.hs, RX_(S + OP_HUW * P), Gw);
-    Gw = fma(ky.hs, RY_(S + OP_HVW * P), Gw);
+    Gw = fma(kx.hs, RX_(S + AP_HUW * P), Gw);
+    Gw = fma(ky.hs, RY_(S + AP_HVW * P), Gw);
     Gw = fma(-0.5, fma(uw, xh, vw_ * yh), Gw);
 #undef RX_
 #undef RY_
