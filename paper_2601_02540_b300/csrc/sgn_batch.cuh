@@ -64,10 +64,11 @@ k_batch_stage(BatchArgs<TC, TIN, TA> a) {
     s.c_acc = (TA)d.c_acc[a.stage];
     s.c_q = (TA)d.c_q[a.stage];
     double* slot = a.partials ? a.partials + (long long)blockIdx.x * NDIAG : nullptr;
+    // the full tile (the factored one is slower here, measured): same products, same rounding
     if (d.bc == BC_REFLECTING)
-        stage_tile<TC, TIN, TA, BC_REFLECTING, MODE, ROWS>(s, d.G, tile.y, tile.z, sm, slot);
+        stage_tile<TC, TIN, TA, BC_REFLECTING, MODE, ROWS, false>(s, d.G, tile.y, tile.z, sm, slot);
     else
-        stage_tile<TC, TIN, TA, BC_PERIODIC, MODE, ROWS>(s, d.G, tile.y, tile.z, sm, slot);
+        stage_tile<TC, TIN, TA, BC_PERIODIC, MODE, ROWS, false>(s, d.G, tile.y, tile.z, sm, slot);
 }
 
 // Per-instance sums of the per-tile partials, in tile order (one block each).

@@ -13,6 +13,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "sgn_df64.cuh"
@@ -267,6 +268,41 @@ __device__ __forceinline__ void store_operands(TC* __restrict__ sm, int t, TC h,
     for (int op = 0; op < N_OPS; op++) sm[op * HN + t] = o[op];
 }
 
+// The factored tile (float compute type): only the fields, eta + 3/2 b,
+// eta^2/h and 1/h are staged; the other differentiated products are formed
+// from the fields wherever node_rhs asks for them, with the same rounded
+// operations as make_ops (so the results are those of the full tile).  Float
+// arithmetic is plentiful and the float kernels are bound by memory traffic
+// and shared-memory instruction throughput, which this halves.
+enum { FP_H, FP_U, FP_V, FP_W, FP_ETA, FP_B, FP_E15, FP_E2H, FP_R, NF_OPS };
+
+template <typename TC>
+struct TileLayout {
+    static constexpr bool factored = false;
+    static constexpr int planes = N_OPS;
+};
+template <>
+struct TileLayout<float> {
+    static constexpr bool factored = true;
+    static constexpr int planes = NF_OPS;
+};
+
+template <typename TC, int HN>
+__device__ __forceinline__ void store_operands_factored(TC* __restrict__ sm, int t, TC h, TC u, TC v, TC w,
+                                                        TC eta, TC bb) {
+    const TC r = recip<TC>(h);
+    sm[FP_H * HN + t] = h;
+    sm[FP_U * HN + t] = u;
+    sm[FP_V * HN + t] = v;
+    sm[FP_W * HN + t] = w;
+    sm[FP_ETA * HN + t] = eta;
+    sm[FP_B * HN + t] = bb;
+    sm[FP_E15 * HN + t] = fma_(tc_const<TC>(1.5), bb, eta);
+    sm[FP_E2H * HN + t] = mul_(mul_(eta, eta), r);
+    sm[FP_R * HN + t] = r;
+}
+
+
 // Where node_rhs reads its operands: position 0 is the node itself, 1-4 its
 // left, right, lower and upper neighbours (already resolved to the node itself
 // on a reflecting wall, where the one-sided row uses it).
@@ -277,6 +313,43 @@ struct SmemOps {            // operands staged in a shared-memory halo tile
     const TC* sm;
     int idx[5];
     __device__ __forceinline__ TC get(int op, int pos) const { return sm[op * HN + idx[pos]]; }
+};
+
+template <typename TC, int HN>
+struct FactoredOps {        // the factored tile: products formed on request
+    const TC* sm;
+    int idx[5];
+    __device__ __forceinline__ TC at(int plane, int pos) const { return sm[plane * HN + idx[pos]]; }
+    __device__ __forceinline__ TC get(int op, int pos) const {
+        switch (op) {
+        case OP_H: return at(FP_H, pos);
+        case OP_U: return at(FP_U, pos);
+        case OP_V: return at(FP_V, pos);
+        case OP_W: return at(FP_W, pos);
+        case OP_ETA: return at(FP_ETA, pos);
+        case OP_B: return at(FP_B, pos);
+        case OP_E15: return at(FP_E15, pos);
+        case OP_E2H: return at(FP_E2H, pos);
+        case OP_R: return at(FP_R, pos);
+        case OP_HS: {
+            const TC h = at(FP_H, pos);
+            return mul_(h, add_(h, at(FP_B, pos)));
+        }
+        case OP_UU: {
+            const TC u = at(FP_U, pos);
+            return mul_(u, u);
+        }
+        case OP_VV: {
+            const TC v = at(FP_V, pos);
+            return mul_(v, v);
+        }
+        case OP_HU: return mul_(at(FP_H, pos), at(FP_U, pos));
+        case OP_HV: return mul_(at(FP_H, pos), at(FP_V, pos));
+        case OP_HUV: return mul_(mul_(at(FP_H, pos), at(FP_U, pos)), at(FP_V, pos));
+        case OP_HUW: return mul_(mul_(at(FP_H, pos), at(FP_U, pos)), at(FP_W, pos));
+        default: return mul_(mul_(at(FP_H, pos), at(FP_V, pos)), at(FP_W, pos));   // OP_HVW
+        }
+    }
 };
 
 // Right-hand side at node (gi, gj), its operands read from S (S.get(op, pos)).
@@ -361,10 +434,11 @@ __device__ __forceinline__ void node_rhs_src(const Src& S, int gi, int gj, const
 
 // Right-hand side at the node held in shared-memory slot t of a halo tile with
 // row stride HX and plane size HN, global (gi, gj).
-template <typename TC, int BC, int HX = HALO_X, int HN = HALO_N>
+template <typename TC, int BC, int HX = HALO_X, int HN = HALO_N, bool FACT = TileLayout<TC>::factored>
 __device__ __forceinline__ void node_rhs(const TC* __restrict__ sm, int t, int gi, int gj,
                                          const Geom& G, TC k[5]) {
-    SmemOps<TC, HN> S;
+    using Src = typename std::conditional<FACT, FactoredOps<TC, HN>, SmemOps<TC, HN>>::type;
+    Src S;
     S.sm = sm;
     S.idx[POS_C] = t;
     S.idx[POS_L] = t - 1;
@@ -460,16 +534,17 @@ __device__ __forceinline__ df64 stage_state<df64, double>(double c, df64 k, doub
 }
 
 // Dynamic shared memory of a stage launch: the halo tile of the operands.
-template <typename TC, int MODE>
+template <typename TC, int MODE, bool FACT = TileLayout<TC>::factored>
 constexpr size_t stage_smem_bytes(int rows) {
-    return (size_t)N_OPS * (TILE_X + 2) * (THREADS_Y * rows + 2) * sizeof(TC);
+    return (size_t)(FACT ? (int)NF_OPS : (int)N_OPS) * (TILE_X + 2) * (THREADS_Y * rows + 2) * sizeof(TC);
 }
 
 // One output tile (TILE_X x 8*ROWS nodes at (i0, j0)) of a stage launch: the
 // body shared by the single-grid and the batched kernels.  The pointers of `a`
 // address this grid's planes; `G` is its geometry; DIAG writes the tile's
 // partial sums to partial_slot[0..NDIAG).
-template <typename TC, typename TIN, typename TA, int BC, int MODE, int ROWS>
+template <typename TC, typename TIN, typename TA, int BC, int MODE, int ROWS,
+          bool FACT = TileLayout<TC>::factored>
 __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, const Geom& G, int i0, int j0,
                                            TC* __restrict__ sm, double* partial_slot) {
     constexpr int ROWS_PER_THREAD = ROWS;
@@ -543,7 +618,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
             bb = a.b[c];
         }
         bad |= h_flags(h);
-        store_operands<TC, HALO_N>(sm, t, h, u, v, w, eta, bb);
+        if constexpr (FACT)
+            store_operands_factored<TC, HALO_N>(sm, t, h, u, v, w, eta, bb);
+        else
+            store_operands<TC, HALO_N>(sm, t, h, u, v, w, eta, bb);
     }
     if (bad) atomicOr(a.flag, bad);
     __syncthreads();
@@ -557,7 +635,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
         if (gi >= G.nx || gj >= G.ny) continue;
         const int t = (ly + 1) * HALO_X + (threadIdx.x + 1);
         TC k[5];
-        node_rhs<TC, BC, HALO_X, HALO_N>(sm, t, gi, gj, G, k);
+        node_rhs<TC, BC, HALO_X, HALO_N, FACT>(sm, t, gi, gj, G, k);
         const long long c = (long long)gj * G.nx + gi;
         if (MODE == MODE_RHS) {
 #pragma unroll
