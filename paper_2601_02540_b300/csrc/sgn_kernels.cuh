@@ -553,13 +553,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
     const long long P = G.plane;
     const int tid = threadIdx.y * TILE_X + threadIdx.x;
 
-    // Memory-bound (float) variants issue every global load of the block early
-    // so that more bytes are in flight: the stage operands of this thread's
-    // output nodes first, then all halo-tile inputs of its share of the tile.
-    // (the stage operands only when they are float: 20 doubles of early loads
-    // cost the mixed-precision variant more occupancy than they gain)
+    // Memory-bound (float compute type, FP32 and mixed) variants issue every
+    // global load of the block early so that more bytes are in flight: the
+    // stage operands of this thread's output nodes first, then all halo-tile
+    // inputs of its share of the tile.
     constexpr bool kEarly = sizeof(TC) == 4;
-    constexpr bool kEarlyStage = kEarly && sizeof(TA) == 4;
+    constexpr bool kEarlyStage = kEarly;
     constexpr int NPER = (HALO_N + BLOCK_THREADS - 1) / BLOCK_THREADS;
     const int gi = i0 + threadIdx.x;
     TA pq[ROWS_PER_THREAD][5], pa[ROWS_PER_THREAD][5];
