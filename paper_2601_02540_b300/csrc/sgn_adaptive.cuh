@@ -68,10 +68,18 @@ __global__ void __launch_bounds__(BLOCK_THREADS, StageShape<TC>::min_blocks) k_b
     // ---- phase 1: halo tile of the stage input and of its products
     int bad = 0;
     const TC c_in = cvt<TC>(a.c_in);
+    if constexpr (kChecked) {                   // checked builds: poison the tile first
+        for (int k = tid; k < N_OPS * HN; k += BLOCK_THREADS) sm[k] = poison<TC>();
+        __syncthreads();
+    }
     for (int t = tid; t < HN; t += BLOCK_THREADS) {
         const int li = t % HX, lj = t / HX;
         const int gx = halo_index<BC>(i0 - 1 + li, G.nx);
         const int gy = halo_index<BC>(j0 - 1 + lj, G.ny);
+        if (kChecked && (gx < 0 || gx >= G.nx || gy < 0 || gy >= G.ny)) {
+            bad |= FLAG_BOUNDS;
+            continue;
+        }
         const long long c = (long long)gy * G.nx + gx;
         TC y[5];
 #pragma unroll

@@ -240,6 +240,7 @@ sgn_status read_flag(sgn_ctx* c, cudaStream_t s) {
     if (f) {
         CUDA_TRY(cudaMemsetAsync(c->flag, 0, sizeof(int), s), "clear flag");
         CUDA_TRY(cudaStreamSynchronize(s), "synchronize");
+        if (f & sgn::FLAG_BOUNDS) return fail(SGN_E_INVAL, "checked build: a tile index left its plane");
         if (f & sgn::FLAG_NONFINITE) return fail(SGN_E_NONFINITE, "a stage input had a non-finite water height");
         return fail(SGN_E_NONPOSITIVE_H, "a stage input had a non-positive water height");
     }

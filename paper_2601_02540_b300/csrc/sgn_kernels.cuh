@@ -53,6 +53,18 @@ enum {
 constexpr int NDIAG = 4;
 constexpr int FLAG_NONPOSITIVE = 1;
 constexpr int FLAG_NONFINITE = 2;
+constexpr int FLAG_BOUNDS = 4;
+
+// Checked builds (-DSGN_CHECKED, libsgn_checked.so): the stage kernels fill
+// their shared-memory tile with NaN before staging it, so that a tile entry
+// read but never written turns the results into NaN, and check every global
+// index of the tile loads against its plane; an index out of range sets
+// FLAG_BOUNDS and the load is skipped.  A substitute for a memory checker.
+#ifdef SGN_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
 
 struct Geom {
     int nx, ny;
@@ -132,6 +144,16 @@ template <typename TC>
 __device__ __forceinline__ TC tc_const(double d) { return (TC)d; }
 template <>
 __device__ __forceinline__ df64 tc_const<df64>(double d) { return df64_of_float((float)d); }
+
+// A quiet NaN in the compute type (the poison of checked builds).
+template <typename TC>
+__device__ __forceinline__ TC poison();
+template <>
+__device__ __forceinline__ double poison<double>() { return __longlong_as_double(0x7ff8000000000000LL); }
+template <>
+__device__ __forceinline__ float poison<float>() { return __int_as_float(0x7fc00000); }
+template <>
+__device__ __forceinline__ df64 poison<df64>() { return {__int_as_float(0x7fc00000), 0.0f}; }
 
 // Conversions between the storage and compute types (df64 by integer
 // operations on the bit patterns, see sgn_df64.cuh).
@@ -579,6 +601,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
 
     // ---- phase 1: halo tile of the inputs and of every differentiated product
     int bad = 0;
+    if constexpr (kChecked) {
+        constexpr int NP = FACT ? (int)NF_OPS : (int)N_OPS;
+        for (int k = tid; k < NP * HALO_N; k += BLOCK_THREADS) sm[k] = poison<TC>();
+        __syncthreads();
+    }
     TC lh[NPER], lu[NPER], lv[NPER], lw[NPER], le[NPER], lb[NPER];
     if (kEarly) {
 #pragma unroll
@@ -588,6 +615,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
             const int li = t % HALO_X, lj = t / HALO_X;
             const int gx = halo_index<BC>(i0 - 1 + li, G.nx);
             const int gy = halo_index<BC>(j0 - 1 + lj, G.ny);
+            if (kChecked && (gx < 0 || gx >= G.nx || gy < 0 || gy >= G.ny)) {
+                bad |= FLAG_BOUNDS;
+                continue;
+            }
             const long long c = (long long)gy * G.nx + gx;
             lh[k] = cvt<TC>(a.X[c]);
             lu[k] = cvt<TC>(a.X[P + c]);
@@ -603,11 +634,20 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
         if (t >= HALO_N) continue;
         TC h, u, v, w, eta, bb;
         if (kEarly) {
+            if constexpr (kChecked) {            // the early load skipped an out-of-range index
+                const int gx = halo_index<BC>(i0 - 1 + t % HALO_X, G.nx);
+                const int gy = halo_index<BC>(j0 - 1 + t / HALO_X, G.ny);
+                if (gx < 0 || gx >= G.nx || gy < 0 || gy >= G.ny) continue;
+            }
             h = lh[k]; u = lu[k]; v = lv[k]; w = lw[k]; eta = le[k]; bb = lb[k];
         } else {
             const int li = t % HALO_X, lj = t / HALO_X;
             const int gx = halo_index<BC>(i0 - 1 + li, G.nx);
             const int gy = halo_index<BC>(j0 - 1 + lj, G.ny);
+            if (kChecked && (gx < 0 || gx >= G.nx || gy < 0 || gy >= G.ny)) {
+                bad |= FLAG_BOUNDS;
+                continue;
+            }
             const long long c = (long long)gy * G.nx + gx;
             h = cvt<TC>(a.X[c]);
             u = cvt<TC>(a.X[P + c]);

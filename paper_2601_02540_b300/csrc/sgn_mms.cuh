@@ -163,10 +163,18 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_forced_stage(MmsArgs m) {
     const int i0 = blockIdx.x * TILE_X, j0 = blockIdx.y * TILE_Y;
     const int tid = threadIdx.y * TILE_X + threadIdx.x;
     int bad = 0;
+    if constexpr (kChecked) {                   // checked builds: poison the tile first
+        for (int k = tid; k < N_OPS * HALO_N; k += BLOCK_THREADS) sm[k] = poison<double>();
+        __syncthreads();
+    }
     for (int t = tid; t < HALO_N; t += BLOCK_THREADS) {
         const int li = t % HALO_X, lj = t / HALO_X;
         const int gx = halo_index<BC>(i0 - 1 + li, G.nx);
         const int gy = halo_index<BC>(j0 - 1 + lj, G.ny);
+        if (kChecked && (gx < 0 || gx >= G.nx || gy < 0 || gy >= G.ny)) {
+            bad |= FLAG_BOUNDS;
+            continue;
+        }
         const long long c = (long long)gy * G.nx + gx;
         const double h = a.X[c];
         bad |= h_flags(h);

@@ -14,7 +14,9 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsgn.so")
+# SGN_LIBRARY=checked selects the checked build (poisoned tiles, index checks)
+LIB_PATH = os.path.join(_HERE, "libsgn_checked.so" if os.environ.get("SGN_LIBRARY") == "checked"
+                        else "libsgn.so")
 
 SGN_OK = 0
 STATUS = {0: "SGN_OK", 1: "SGN_E_INVAL", 2: "SGN_E_NOMEM", 3: "SGN_E_CUDA",
