@@ -204,11 +204,21 @@ def _cpu_baseline(p_full: inputs.Problem) -> dict:
     g = orc.Grid(p.nx, p.ny, p.xmin, p.xmax, p.ymin, p.ymax, p.bc, p.g, p.lam)
     q0 = orc.init_aux(g, p.b, p.q0)
     t0 = time.perf_counter()
-    orc.rk4(g, p.b, q0, p_full.dt, nst)
+    ref = orc.rk4(g, p.b, q0, p_full.dt, nst)
     sec = time.perf_counter() - t0
+    # the same oracle source built with OpenMP, on all host cores (same results)
+    cores = len(os.sched_getaffinity(0))
+    os.environ["OMP_NUM_THREADS"] = str(cores)
+    om = orc.openmp()
+    t0 = time.perf_counter()
+    par = om.rk4(g, p.b, q0, p_full.dt, nst)
+    sec_par = time.perf_counter() - t0
     return {"value": 4 * n * n * nst / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"same recipe at {n}x{n} (dx = 0.1), {nst} RK4 steps, single-threaded C, "
-                      f"{sec:.1f} s"}
+                      f"{sec:.1f} s",
+            "all_cores": {"value": 4 * n * n * nst / sec_par, "cores": cores,
+                          "same_result": bool((ref == par).all()),
+                          "sample": f"the same sample, OpenMP build of the oracle, {sec_par:.1f} s"}}
 
 
 def run_ours(args) -> None:

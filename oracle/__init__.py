@@ -38,6 +38,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sgn_oracle.c")
 _LIB_REAL = os.path.join(_HERE, "liboracle.so")
 _LIB_CPLX = os.path.join(_HERE, "liboracle_cplx.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 
 PERIODIC = 0
 REFLECTING = 1
@@ -52,8 +53,9 @@ def _compile(out: str, defines: list[str]) -> None:
 
 
 def build(force: bool = False) -> None:
-    """Compile both oracle libraries with gcc (no FMA contraction)."""
-    for out, extra in ((_LIB_REAL, []), (_LIB_CPLX, ["-DORC_COMPLEX"])):
+    """Compile the oracle libraries with gcc (no FMA contraction): real, complex
+    (complex step) and real with OpenMP (the all-core CPU baseline)."""
+    for out, extra in ((_LIB_REAL, []), (_LIB_CPLX, ["-DORC_COMPLEX"]), (_LIB_OMP, ["-fopenmp"])):
         if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
             continue
         _compile(out, extra)
@@ -374,6 +376,13 @@ class Oracle:
 
 
 _default: Oracle | None = None
+
+
+def openmp() -> Oracle:
+    """The real oracle built with OpenMP (threads from OMP_NUM_THREADS): the
+    same results as default(), on all host cores."""
+    build()
+    return Oracle(_LIB_OMP, None)
 
 
 def default() -> Oracle:

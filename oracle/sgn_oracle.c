@@ -14,7 +14,11 @@
  *     below is a rational function of the state and the bathymetry, so
  *     Im f(x + i*eps*d) / eps = f'(x) d to rounding for tiny eps).
  * Build flags: -O2 -ffp-contract=off (no fused multiply-add), so every
- * expression is evaluated exactly as written, left to right.
+ * expression is evaluated exactly as written, left to right.  The loops over
+ * rows and nodes of the RHS and of RK4 carry OpenMP pragmas: a third build
+ * with -fopenmp (liboracle_omp.so) runs them on all host cores for the timed
+ * CPU baseline; every iteration is independent, so its results are those of
+ * the plain build bit for bit.
  *
  * Layout: a state q holds five planes h, u, v, w, eta (in that order), each
  * plane nx*ny values with x fastest: q[f*nx*ny + j*nx + i].  The bathymetry b
@@ -128,6 +132,7 @@ void ORC(dx_apply)(const orc_grid* G, const real* f, real* out)
 {
     double dx, dy;
     ORC(spacing)(G, &dx, &dy);
+#pragma omp parallel for
     for (int j = 0; j < G->ny; j++)
         sbp_line(G->bc, G->nx, dx, f + (long)j * G->nx, 1, out + (long)j * G->nx);
 }
@@ -137,6 +142,7 @@ void ORC(dy_apply)(const orc_grid* G, const real* f, real* out)
 {
     double dx, dy;
     ORC(spacing)(G, &dx, &dy);
+#pragma omp parallel for
     for (int i = 0; i < G->nx; i++)
         sbp_line(G->bc, G->ny, dy, f + i, G->nx, out + i);
 }
@@ -204,6 +210,7 @@ static int derivs_compute(const orc_grid* G, const real* b, const real* q, deriv
     for (int p = 0; p < NPROD; p++) {
         D->dx[p] = D->buf + (2 * p) * n;
         D->dy[p] = D->buf + (2 * p + 1) * n;
+#pragma omp parallel for
         for (long c = 0; c < n; c++) {
             real val;
             switch (p) {
@@ -367,6 +374,7 @@ int ORC(rhs)(const orc_grid* G, const real* b, const real* q, real* dq)
     derivs D;
     if (derivs_compute(G, b, q, &D, 0)) return -1;
     const long n = D.n;
+#pragma omp parallel for
     for (int j = 0; j < G->ny; j++)
         for (int i = 0; i < G->nx; i++) {
             long c = (long)j * G->nx + i;
@@ -458,12 +466,16 @@ int ORC(rk4)(const orc_grid* G, const real* b, real* q, double dt, int nsteps)
     int rc = 0;
     for (int s = 0; s < nsteps && rc == 0; s++) {
         rc |= ORC(rhs)(G, b, q, k1);
+#pragma omp parallel for
         for (long c = 0; c < m; c++) y[c] = q[c] + (dt / 2.0) * k1[c];
         rc |= ORC(rhs)(G, b, y, k2);
+#pragma omp parallel for
         for (long c = 0; c < m; c++) y[c] = q[c] + (dt / 2.0) * k2[c];
         rc |= ORC(rhs)(G, b, y, k3);
+#pragma omp parallel for
         for (long c = 0; c < m; c++) y[c] = q[c] + dt * k3[c];
         rc |= ORC(rhs)(G, b, y, k4);
+#pragma omp parallel for
         for (long c = 0; c < m; c++)
             q[c] = q[c] + (dt / 6.0) * (k1[c] + 2.0 * k2[c] + 2.0 * k3[c] + k4[c]);
     }
