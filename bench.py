@@ -169,11 +169,22 @@ def _time_steps(torch, solver, q, dt, steps, warmup, dist=None):
     launches = sgn.sgn_launch_count() - n0
     ms = e0.elapsed_time(e1)
     if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(torch, dist, ms, "cuda")
         dist.barrier()
     return ms, launches
+
+
+def max_over_ranks(torch, dist, ms: float, device: str) -> float:
+    """The slowest rank's time (replicas: the job ends when the last rank does)."""
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(cells: int, steps: int, ms_max: float, world: int) -> float:
+    """Whole-job cell-stage rate of `world` independent replicas, each advancing
+    `cells` nodes by `steps` RK4 steps (4 stages), over the slowest rank's time."""
+    return 4.0 * cells * steps * world / (ms_max * 1e-3)
 
 
 def _roofline(prec: str, cells: int, ms_total: float, launches_per_step: int, steps: int,
@@ -254,8 +265,7 @@ def run_ours(args) -> None:
             clocks = clk.summary()
         else:
             ms, launches = _time_steps(torch, s, q, p.dt, args.steps, args.warmup, dist)
-        rate = 4.0 * cells * args.steps / (ms * 1e-3)
-        results[prec] = {"value": rate * world, "ms_per_step": ms / args.steps,
+        results[prec] = {"value": replica_rate(cells, args.steps, ms, world), "ms_per_step": ms / args.steps,
                          "gpu_launches": launches,
                          "roofline": _roofline(prec, cells, ms, 4, args.steps, hbm_peak, hbm_kind)}
         if not args.no_drift:
