@@ -55,10 +55,11 @@ FP64_NOMINAL_TFLOPS = 1.25     # B300 dense FP64 (nominal; no measured entry)
 BYTES_PER_CELL_STAGE = {"f64": 84 * 8 / 4, "f32": 84 * 4 / 4, "f32_f64acc": 536 / 4,
                         "df64": 84 * 8 / 4}     # df64: stage states as float pairs, 8 bytes
 # Algorithmic floating-point operations per cell-stage of the implemented
-# formulation (an FMA counts 2; 1/h counts 1): products and eta + 3/2 b 14,
-# pointwise coefficients 16, 22 differences, h 9, u 25, v 25, w 18, eta 6,
-# stage algebra 17.5 (average of 20, 20, 20, 10).
-FLOPS_PER_CELL_STAGE = 152.5
+# formulation (an FMA counts 2; 1/h counts 1): pointwise operands (1/h, eta/h,
+# eta + 3/2 b, P2 = 2g h(h+b) - lam/3 eta^2/h) 10, products 7, coefficients 5,
+# 20 differences, the fluxes A_x, A_y 6, h 3, u 16, v 16, w 15, eta 6, stage
+# algebra 17.5 (average of 20, 20, 20, 10).
+FLOPS_PER_CELL_STAGE = 121.5
 DTYPE_NAME = {"f64": "f64", "f32": "f32", "f32_f64acc": "f32+f64acc", "df64": "df64 (float pairs)"}
 
 

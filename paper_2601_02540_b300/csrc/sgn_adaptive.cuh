@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS, StageShape<TC>::min_blocks) k_b
                    : (MODE == BS_K3) ? Y3[f * P + c]
                                      : cvt<TC>(a.q1[f * P + c]);
         bad |= h_flags(y[0]);
-        store_operands<TC, HN>(sm, t, y[0], y[1], y[2], y[3], y[4], static_cast<const TC*>(a.b)[c]);
+        store_operands<TC, HN>(sm, t, y[0], y[1], y[2], y[3], y[4], static_cast<const TC*>(a.b)[c], G);
     }
     if (bad) atomicOr(a.flag, bad);
     __syncthreads();

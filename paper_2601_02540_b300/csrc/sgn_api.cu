@@ -64,12 +64,13 @@ struct sgn_ctx {
     void* acc = nullptr;         // RK accumulator, state type
     void* Qa = nullptr;          // stage states, compute type
     void* Qb = nullptr;
-    double* partials = nullptr;  // NDIAG per block
+    double* partials = nullptr;  // NDIAG per 32 x 8 band (diagnostics) or per block (adaptive error)
     double* dout = nullptr;      // NDIAG device
     double* hout = nullptr;      // pinned host results (kHostOut doubles: diagnostics, relaxation sums)
     int* flag = nullptr;         // device error bits
     int* hflag = nullptr;        // pinned host copy
-    long long nblk = 0;
+    long long nblk = 0;          // blocks of the stage launch
+    long long nband = 0;         // 32 x 8 bands of the grid: partials of the diagnostics
     dim3 grid;
     double* adj = nullptr;       // adjoint scratch (FP64): accumulator + two cotangents
     double* bs = nullptr;        // adaptive integrator scratch (FP64): k1..k4, Y3, q1, q (35 planes)
@@ -155,7 +156,7 @@ cudaError_t run_steps(sgn_ctx* c, TA* q, double dt, int nsteps, cudaStream_t s, 
             StageArgs<TC, TC, TA> a4d = a4;
             a4d.partials = c->partials;
             if ((e = launch_stage<TC, TC, TA, BC, sgn::MODE_S4D>(c, a4d, s)) != cudaSuccess) return e;
-            sgn::k_reduce_partials<<<1, 256, 0, s>>>(c->partials, c->nblk, mon + (long long)n * sgn::NDIAG);
+            sgn::k_reduce_partials<<<1, 256, 0, s>>>(c->partials, c->nband, mon + (long long)n * sgn::NDIAG);
             count_launch();
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
@@ -176,7 +177,7 @@ cudaError_t run_diag(sgn_ctx* c, const TA* q, cudaStream_t s) {
     a.X = q; a.partials = c->partials;
     cudaError_t e = launch_stage<TC, TA, TA, BC, sgn::MODE_DIAG>(c, a, s);
     if (e != cudaSuccess) return e;
-    sgn::k_reduce_partials<<<1, 256, 0, s>>>(c->partials, c->nblk, c->dout);
+    sgn::k_reduce_partials<<<1, 256, 0, s>>>(c->partials, c->nband, c->dout);
     count_launch();
     return cudaGetLastError();
 }
@@ -473,7 +474,7 @@ sgn::MmsTime mms_time(double t) {
 template <int BC, int MODE, int FORCING>
 cudaError_t launch_forced(const sgn_ctx* c, const sgn::MmsArgs& m, cudaStream_t s) {
     auto kern = sgn::k_forced_stage<BC, MODE, FORCING>;
-    const size_t smem = sgn::stage_smem_bytes<double, sgn::MODE_RHS>(sgn::ROWS_PER_THREAD);
+    const size_t smem = sgn::stage_smem_bytes<double, sgn::MODE_RHS>(sgn::StageShape<double>::rows);
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
@@ -626,7 +627,9 @@ sgn_status sgn_create(const sgn_params* p, const void* b_dev, sgn_ctx** out) {
     if (!p) return fail(SGN_E_INVAL, "params is NULL");
     if (p->nx < 3 || p->ny < 3) return fail(SGN_E_INVAL, "grid %dx%d: need nx, ny >= 3", p->nx, p->ny);
     // tile height of the stage kernels for this compute type (StageShape)
-    const int tile_y = p->prec == SGN_DF64 ? sgn::THREADS_Y * sgn::StageShape<sgn::df64>::rows : sgn::TILE_Y;
+    const int tile_y = sgn::THREADS_Y * (p->prec == SGN_DF64  ? sgn::StageShape<sgn::df64>::rows
+                                         : p->prec == SGN_F64 ? sgn::StageShape<double>::rows
+                                                              : sgn::StageShape<float>::rows);
     if ((p->ny + tile_y - 1) / tile_y > 65535)
         return fail(SGN_E_INVAL, "ny = %d exceeds the launch-grid limit", p->ny);
     if (!(std::isfinite(p->xmin) && std::isfinite(p->xmax) && p->xmax > p->xmin &&
@@ -652,6 +655,7 @@ sgn_status sgn_create(const sgn_params* p, const void* b_dev, sgn_ctx** out) {
     c->ta_size = p->prec == SGN_F32 ? sizeof(float) : sizeof(double);
     c->grid = dim3((p->nx + sgn::TILE_X - 1) / sgn::TILE_X, (p->ny + tile_y - 1) / tile_y);
     c->nblk = (long long)c->grid.x * c->grid.y;
+    c->nband = (long long)c->grid.x * ((p->ny + sgn::THREADS_Y - 1) / sgn::THREADS_Y);   // >= nblk
 
     const size_t plane = (size_t)G.plane;
     bool ok = cudaMalloc(&c->b64, plane * sizeof(double)) == cudaSuccess;
@@ -660,7 +664,7 @@ sgn_status sgn_create(const sgn_params* p, const void* b_dev, sgn_ctx** out) {
     ok = ok && cudaMalloc(&c->acc, 5 * plane * c->ta_size) == cudaSuccess;
     ok = ok && cudaMalloc(&c->Qa, 5 * plane * c->tc_size) == cudaSuccess;
     ok = ok && cudaMalloc(&c->Qb, 5 * plane * c->tc_size) == cudaSuccess;
-    ok = ok && cudaMalloc(&c->partials, (size_t)c->nblk * sgn::NDIAG * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->partials, (size_t)c->nband * sgn::NDIAG * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc(&c->dout, sgn::NDIAG * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc(&c->flag, sizeof(int)) == cudaSuccess;
     ok = ok && cudaMallocHost(&c->hout, kHostOut * sizeof(double)) == cudaSuccess;

@@ -269,8 +269,7 @@ sgn_status sgn_batch_create(const sgn_instance* inst, int ninst, int prec, const
         off += d.G.plane;
     }
     B->cells = off;
-    // tile lists for the three tile heights; the descriptor keeps the rows = 2
-    // list's range, the others are stored per list below
+    // tile lists for the three tile heights (rows = 1: the 32 x 8 bands)
     for (int ri = 0; ri < 3; ri++) {
         const int th = sgn::THREADS_Y * (ri == 0 ? 1 : (ri == 1 ? 2 : 4));
         for (int k = 0; k < ninst; k++) {
@@ -302,8 +301,6 @@ sgn_status sgn_batch_create(const sgn_instance* inst, int ninst, int prec, const
         free_batch(B);
         return bfail(SGN_E_NOMEM, "batch scratch");
     }
-    // per-list tile ranges are recomputed on the device side only for diagnostics,
-    // which use the rows-specific list: store the ranges of list `rows` on use
     cudaError_t e = cudaSuccess;
     for (int ri = 0; ri < 3 && e == cudaSuccess; ri++)
         e = cudaMemcpy(B->tiles[ri], tl[ri].data(), sizeof(int4) * tl[ri].size(), cudaMemcpyHostToDevice);
@@ -322,16 +319,17 @@ sgn_status sgn_batch_create(const sgn_instance* inst, int ninst, int prec, const
         }
     }
     if (e == cudaSuccess) {
-        // descriptors with the tile ranges of the default list (rows = 2)
+        // descriptors with the band ranges: the rows = 1 tiles are the 32 x 8
+        // bands, enumerated instance by instance in band-major order
         std::vector<long long> first(ninst, -1), count(ninst, 0);
-        for (size_t k = 0; k < tl[1].size(); k++) {
-            const int i = tl[1][k].x;
+        for (size_t k = 0; k < tl[0].size(); k++) {
+            const int i = tl[0][k].x;
             if (first[i] < 0) first[i] = (long long)k;
             count[i]++;
         }
         for (int i = 0; i < ninst; i++) {
-            B->hdesc[i].tile0 = first[i];
-            B->hdesc[i].ntiles = (int)count[i];
+            B->hdesc[i].band0 = first[i];
+            B->hdesc[i].nbands = (int)count[i];
         }
         e = cudaMemcpy(B->desc, B->hdesc.data(), sizeof(sgn::InstDesc) * ninst, cudaMemcpyHostToDevice);
     }
@@ -389,16 +387,13 @@ sgn_status sgn_batch_mass_energy(sgn_batch* B, const void* q_dev, double* out, v
     if (!B || !out) return bfail(SGN_E_INVAL, "batch and out must not be NULL");
     if (!devptr(q_dev)) return bfail(SGN_E_INVAL, "q_dev is not device memory");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // the per-instance tile ranges in the descriptors refer to the rows = 2 list
-    const int saved = B->rows;
-    B->rows = 2;
+    // band partials: the same sums whatever the tile height
     cudaError_t e;
     switch (B->prec) {
     case SGN_F64: e = bdiag_rows<double, double>(B, q_dev, s); break;
     case SGN_F32: e = bdiag_rows<float, float>(B, q_dev, s); break;
     default: e = bdiag_rows<float, double>(B, q_dev, s); break;
     }
-    B->rows = saved;
     if (e != cudaSuccess) return bcuda(e, "sgn_batch_mass_energy");
     int flag = 0;
     e = cudaMemcpyAsync(out, B->dout, (size_t)B->ninst * sgn::NDIAG * sizeof(double), cudaMemcpyDeviceToHost, s);

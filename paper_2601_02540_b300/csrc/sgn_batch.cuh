@@ -21,8 +21,8 @@ struct InstDesc {
     long long off;         // element offset of the instance's first plane (b); state: 5 * off
     double c_acc[4];       // per-stage coefficients of the accumulator update
     double c_q[4];         // per-stage coefficients of the next stage state
-    long long tile0;       // first tile of the instance in the tile list
-    int ntiles;
+    long long band0;       // first diagnostics partial (32 x 8 band) of the instance
+    int nbands;            // its bands: ceil(nx/32) ceil(ny/8), band-major
 };
 
 template <typename TC, typename TIN, typename TA>
@@ -36,7 +36,7 @@ struct BatchArgs {
     TA* acc;
     TC* Qout;
     TA* out;
-    double* partials;      // DIAG: NDIAG per tile
+    double* partials;      // DIAG: NDIAG per 32 x 8 band of every instance
     int* flag;
     int stage;             // 0..3: index into c_acc / c_q
 };
@@ -63,24 +63,28 @@ k_batch_stage(BatchArgs<TC, TIN, TA> a) {
     s.G = d.G;
     s.c_acc = (TA)d.c_acc[a.stage];
     s.c_q = (TA)d.c_q[a.stage];
-    double* slot = a.partials ? a.partials + (long long)blockIdx.x * NDIAG : nullptr;
+    // the band partials of the instance, laid out as those of a single-grid launch
+    const long long nbx = (d.G.nx + TILE_X - 1) / TILE_X;
+    double* slot = a.partials ? a.partials + (d.band0 + (tile.z / THREADS_Y) * nbx + tile.y / TILE_X) * NDIAG
+                              : nullptr;
     // the full tile (the factored one is slower here, measured): same products, same rounding
     if (d.bc == BC_REFLECTING)
-        stage_tile<TC, TIN, TA, BC_REFLECTING, MODE, ROWS, false>(s, d.G, tile.y, tile.z, sm, slot);
+        stage_tile<TC, TIN, TA, BC_REFLECTING, MODE, ROWS, false>(s, d.G, tile.y, tile.z, sm, slot, nbx * NDIAG);
     else
-        stage_tile<TC, TIN, TA, BC_PERIODIC, MODE, ROWS, false>(s, d.G, tile.y, tile.z, sm, slot);
+        stage_tile<TC, TIN, TA, BC_PERIODIC, MODE, ROWS, false>(s, d.G, tile.y, tile.z, sm, slot, nbx * NDIAG);
 }
 
-// Per-instance sums of the per-tile partials, in tile order (one block each).
+// Per-instance sums of the band partials, in band order (one block each; the
+// same fixed-order sum as k_reduce_partials over a single grid's bands).
 static __global__ void __launch_bounds__(256) k_batch_reduce(const InstDesc* __restrict__ desc,
                                                               const double* __restrict__ partials,
                                                               double* __restrict__ out) {
     __shared__ double red[256][NDIAG];
     const InstDesc& d = desc[blockIdx.x];
     double s[NDIAG] = {0.0, 0.0, 0.0, 0.0};
-    for (int k = threadIdx.x; k < d.ntiles; k += 256)
+    for (int k = threadIdx.x; k < d.nbands; k += 256)
 #pragma unroll
-        for (int q = 0; q < NDIAG; q++) s[q] += partials[(d.tile0 + k) * NDIAG + q];
+        for (int q = 0; q < NDIAG; q++) s[q] += partials[(d.band0 + k) * NDIAG + q];
 #pragma unroll
     for (int q = 0; q < NDIAG; q++) red[threadIdx.x][q] = s[q];
     __syncthreads();

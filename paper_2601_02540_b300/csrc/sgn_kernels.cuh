@@ -2,10 +2,11 @@
 // the 2D hyperbolized Serre-Green-Naghdi equations (arXiv 2601.02540, Sec. 4),
 // fused with the stages of classical RK4.
 //
-// One thread block owns a TILE_X x TILE_Y tile of output nodes.  It stages the
-// six input planes (h, u, v, w, eta, b) of the tile plus a one-node halo in
-// shared memory, forms every product that is differentiated (h(h+b), u^2, v^2,
-// hu, hv, huv, huw, hvw, eta^2/h) and the reciprocal 1/h once per node, then
+// One thread block owns a TILE_X x TILE_Y tile of output nodes.  It reads the
+// six input planes (h, u, v, w, eta, b) of the tile plus a one-node halo,
+// forms every operand that is differentiated (h, u, v, w, u^2, v^2, hu, hv,
+// huv, huw, hvw, eta + 3/2 b and P2 = 2g h(h+b) - lam/3 eta^2/h) together with
+// eta/h and 1/h once per node and stages them in shared memory, then
 // each thread evaluates the right-hand side of eq. (sd_periodic_2D_SGN) /
 // eq. (semi_2D) at its nodes and applies the RK4 stage algebra.  The halo is
 // wrapped (periodic) or clamped (reflecting: the one-sided boundary rows of
@@ -42,12 +43,13 @@ constexpr int HALO_Y = TILE_Y + 2;
 constexpr int HALO_N = HALO_X * HALO_Y;
 constexpr int BLOCK_THREADS = TILE_X * THREADS_Y;
 
-// shared-memory planes: the differentiated operands, eta + 3/2 b (eta and b are
-// differentiated only in that combination, see node_rhs), then 1/h
+// shared-memory planes: the fields h, u, v, w, then rho = eta/h and r = 1/h
+// (read at the node only), eta + 3/2 b and P2 = 2g h(h+b) - lam/3 eta^2/h (eta
+// and b are differentiated only through these two, see node_rhs_src), and the
+// differentiated products
 enum {
-    OP_H, OP_U, OP_V, OP_W, OP_ETA, OP_B,
-    OP_HS, OP_UU, OP_VV, OP_HU, OP_HV, OP_HUV, OP_HUW, OP_HVW, OP_E2H,
-    OP_E15, OP_R, N_OPS
+    OP_H, OP_U, OP_V, OP_W, OP_RHO, OP_R, OP_E15, OP_P2,
+    OP_UU, OP_VV, OP_HU, OP_HV, OP_HUV, OP_HUW, OP_HVW, N_OPS
 };
 
 constexpr int NDIAG = 4;
@@ -71,14 +73,19 @@ struct Geom {
     long long plane;       // nx * ny
     double cx2, cy2;       // 1 / (2 dx), 1 / (2 dy): central rows
     double cx1, cy1;       // 1 / dx, 1 / dy: one-sided boundary rows
+    double hcx2, hcy2;     // halves of the above (the 1/2 of the split forms folded in)
+    double hcx1, hcy1;
     double satx, saty;     // 2 / dx, 2 / dy: SAT weights
     double dx, dy;         // mass-matrix spacing
     double g, lam;
     double lam2, lam3, lam6;  // lambda/2, lambda/3, lambda/6
+    double g2, lam23;         // 2 g, 2 lambda/3
     // the same constants rounded to float, so that float kernels never convert
     // (a double-to-float conversion occupies the FP64 pipe), and as df64 pairs
-    float f_cx2, f_cy2, f_cx1, f_cy1, f_satx, f_saty, f_g, f_lam, f_lam3, f_lam6;
-    df64 w_cx2, w_cy2, w_cx1, w_cy1, w_satx, w_saty, w_g, w_lam, w_lam3, w_lam6;
+    float f_cx2, f_cy2, f_cx1, f_cy1, f_hcx2, f_hcy2, f_hcx1, f_hcy1, f_satx, f_saty;
+    float f_lam, f_lam3, f_g2, f_lam23;
+    df64 w_cx2, w_cy2, w_cx1, w_cy1, w_hcx2, w_hcy2, w_hcx1, w_hcy1, w_satx, w_saty;
+    df64 w_lam, w_lam3, w_g2, w_lam23;
 };
 
 // Host: a double as a df64 pair (hi the nearest float, lo the nearest float
@@ -97,6 +104,10 @@ inline void fill_geom(Geom& G, int nx, int ny, double dx, double dy, double g, d
     G.cy2 = 1.0 / (2.0 * dy);
     G.cx1 = 1.0 / dx;
     G.cy1 = 1.0 / dy;
+    G.hcx2 = 0.5 * G.cx2;
+    G.hcy2 = 0.5 * G.cy2;
+    G.hcx1 = 0.5 * G.cx1;
+    G.hcy1 = 0.5 * G.cy1;
     G.satx = 2.0 / dx;
     G.saty = 2.0 / dy;
     G.dx = dx;
@@ -106,26 +117,24 @@ inline void fill_geom(Geom& G, int nx, int ny, double dx, double dy, double g, d
     G.lam2 = lam / 2.0;
     G.lam3 = lam / 3.0;
     G.lam6 = lam / 6.0;
-    G.f_cx2 = (float)G.cx2;
-    G.f_cy2 = (float)G.cy2;
-    G.f_cx1 = (float)G.cx1;
-    G.f_cy1 = (float)G.cy1;
-    G.f_satx = (float)G.satx;
-    G.f_saty = (float)G.saty;
-    G.f_g = (float)G.g;
-    G.f_lam = (float)G.lam;
-    G.f_lam3 = (float)G.lam3;
-    G.f_lam6 = (float)G.lam6;
-    G.w_cx2 = host_df64(G.cx2);
-    G.w_cy2 = host_df64(G.cy2);
-    G.w_cx1 = host_df64(G.cx1);
-    G.w_cy1 = host_df64(G.cy1);
-    G.w_satx = host_df64(G.satx);
-    G.w_saty = host_df64(G.saty);
-    G.w_g = host_df64(G.g);
-    G.w_lam = host_df64(G.lam);
-    G.w_lam3 = host_df64(G.lam3);
-    G.w_lam6 = host_df64(G.lam6);
+    G.g2 = 2.0 * g;
+    G.lam23 = 2.0 * lam / 3.0;
+#define SGN_FILL_COPIES_(name) G.f_##name = (float)G.name; G.w_##name = host_df64(G.name)
+    SGN_FILL_COPIES_(cx2);
+    SGN_FILL_COPIES_(cy2);
+    SGN_FILL_COPIES_(cx1);
+    SGN_FILL_COPIES_(cy1);
+    SGN_FILL_COPIES_(hcx2);
+    SGN_FILL_COPIES_(hcy2);
+    SGN_FILL_COPIES_(hcx1);
+    SGN_FILL_COPIES_(hcy1);
+    SGN_FILL_COPIES_(satx);
+    SGN_FILL_COPIES_(saty);
+    SGN_FILL_COPIES_(lam);
+    SGN_FILL_COPIES_(lam3);
+    SGN_FILL_COPIES_(g2);
+    SGN_FILL_COPIES_(lam23);
+#undef SGN_FILL_COPIES_
 }
 
 // A grid constant in the compute type TC (the double or the float copy).
@@ -181,7 +190,7 @@ struct StageArgs {
     TA* acc;             // RK accumulator
     TC* Qout;            // next stage state
     TA* out;             // dq (RHS) or q_{n+1} (stage 4)
-    double* partials;    // DIAG, S4D: NDIAG doubles per block
+    double* partials;    // DIAG, S4D: NDIAG doubles per 32 x 8 band (band-major)
     const double* b64;   // DIAG, S4D: bathymetry in double
     int* flag;           // latched error bits
     Geom G;
@@ -256,19 +265,36 @@ __device__ __forceinline__ int halo_index(int k, int n) {
     return k;
 }
 
-// The shared-memory operands of one node: the raw fields, every product that
-// is differentiated, eta + 3/2 b and 1/h (HN: plane size of the tile).
+// The pointwise operands that do not need the products of the fields: 1/h,
+// eta/h, eta + 3/2 b and P2 = 2g h(h+b) - lam/3 eta^2/h, the last formed as
+// h (2g (h+b)) - (lam/3 rho) eta.
 template <typename TC>
-__device__ __forceinline__ void make_ops(TC h, TC u, TC v, TC w, TC eta, TC bb, TC o[N_OPS]) {
-    const TC r = recip<TC>(h);
+struct PointOps {
+    TC r, rho, e15, p2;
+};
+template <typename TC>
+__device__ __forceinline__ PointOps<TC> point_ops(TC h, TC eta, TC bb, const Geom& G) {
+    PointOps<TC> o;
+    o.r = recip<TC>(h);
+    o.rho = mul_(eta, o.r);
+    o.e15 = fma_(tc_const<TC>(1.5), bb, eta);
+    o.p2 = fma_(h, mul_(GC(TC, g2), add_(h, bb)), -mul_(mul_(GC(TC, lam3), o.rho), eta));
+    return o;
+}
+
+// The shared-memory operands of one node (see the OP_ planes).
+template <typename TC>
+__device__ __forceinline__ void make_ops(TC h, TC u, TC v, TC w, TC eta, TC bb, const Geom& G, TC o[N_OPS]) {
+    const PointOps<TC> p = point_ops<TC>(h, eta, bb, G);
     const TC hu = mul_(h, u), hv = mul_(h, v);
     o[OP_H] = h;
     o[OP_U] = u;
     o[OP_V] = v;
     o[OP_W] = w;
-    o[OP_ETA] = eta;
-    o[OP_B] = bb;
-    o[OP_HS] = mul_(h, add_(h, bb));
+    o[OP_RHO] = p.rho;
+    o[OP_R] = p.r;
+    o[OP_E15] = p.e15;
+    o[OP_P2] = p.p2;
     o[OP_UU] = mul_(u, u);
     o[OP_VV] = mul_(v, v);
     o[OP_HU] = hu;
@@ -276,27 +302,24 @@ __device__ __forceinline__ void make_ops(TC h, TC u, TC v, TC w, TC eta, TC bb, 
     o[OP_HUV] = mul_(hu, v);
     o[OP_HUW] = mul_(hu, w);
     o[OP_HVW] = mul_(hv, w);
-    o[OP_E2H] = mul_(mul_(eta, eta), r);
-    o[OP_E15] = fma_(tc_const<TC>(1.5), bb, eta);
-    o[OP_R] = r;
 }
 
 template <typename TC, int HN>
 __device__ __forceinline__ void store_operands(TC* __restrict__ sm, int t, TC h, TC u, TC v, TC w,
-                                               TC eta, TC bb) {
+                                               TC eta, TC bb, const Geom& G) {
     TC o[N_OPS];
-    make_ops<TC>(h, u, v, w, eta, bb, o);
+    make_ops<TC>(h, u, v, w, eta, bb, G, o);
 #pragma unroll
     for (int op = 0; op < N_OPS; op++) sm[op * HN + t] = o[op];
 }
 
-// The factored tile (float compute type): only the fields, eta + 3/2 b,
-// eta^2/h and 1/h are staged; the other differentiated products are formed
+// The factored tile (float compute type): only the fields and the pointwise
+// operands (1/h, eta/h, eta + 3/2 b, P2) are staged; the products are formed
 // from the fields wherever node_rhs asks for them, with the same rounded
 // operations as make_ops (so the results are those of the full tile).  Float
 // arithmetic is plentiful and the float kernels are bound by memory traffic
 // and shared-memory instruction throughput, which this halves.
-enum { FP_H, FP_U, FP_V, FP_W, FP_ETA, FP_B, FP_E15, FP_E2H, FP_R, NF_OPS };
+enum { FP_H, FP_U, FP_V, FP_W, FP_RHO, FP_R, FP_E15, FP_P2, NF_OPS };
 
 template <typename TC>
 struct TileLayout {
@@ -311,17 +334,16 @@ struct TileLayout<float> {
 
 template <typename TC, int HN>
 __device__ __forceinline__ void store_operands_factored(TC* __restrict__ sm, int t, TC h, TC u, TC v, TC w,
-                                                        TC eta, TC bb) {
-    const TC r = recip<TC>(h);
+                                                        TC eta, TC bb, const Geom& G) {
+    const PointOps<TC> p = point_ops<TC>(h, eta, bb, G);
     sm[FP_H * HN + t] = h;
     sm[FP_U * HN + t] = u;
     sm[FP_V * HN + t] = v;
     sm[FP_W * HN + t] = w;
-    sm[FP_ETA * HN + t] = eta;
-    sm[FP_B * HN + t] = bb;
-    sm[FP_E15 * HN + t] = fma_(tc_const<TC>(1.5), bb, eta);
-    sm[FP_E2H * HN + t] = mul_(mul_(eta, eta), r);
-    sm[FP_R * HN + t] = r;
+    sm[FP_RHO * HN + t] = p.rho;
+    sm[FP_R * HN + t] = p.r;
+    sm[FP_E15 * HN + t] = p.e15;
+    sm[FP_P2 * HN + t] = p.p2;
 }
 
 
@@ -348,15 +370,10 @@ struct FactoredOps {        // the factored tile: products formed on request
         case OP_U: return at(FP_U, pos);
         case OP_V: return at(FP_V, pos);
         case OP_W: return at(FP_W, pos);
-        case OP_ETA: return at(FP_ETA, pos);
-        case OP_B: return at(FP_B, pos);
-        case OP_E15: return at(FP_E15, pos);
-        case OP_E2H: return at(FP_E2H, pos);
+        case OP_RHO: return at(FP_RHO, pos);
         case OP_R: return at(FP_R, pos);
-        case OP_HS: {
-            const TC h = at(FP_H, pos);
-            return mul_(h, add_(h, at(FP_B, pos)));
-        }
+        case OP_E15: return at(FP_E15, pos);
+        case OP_P2: return at(FP_P2, pos);
         case OP_UU: {
             const TC u = at(FP_U, pos);
             return mul_(u, u);
@@ -375,42 +392,53 @@ struct FactoredOps {        // the factored tile: products formed on request
 };
 
 // Right-hand side at node (gi, gj), its operands read from S (S.get(op, pos)).
-// Every term of eq. (sd_periodic_2D_SGN) / (semi_2D) appears once; terms are
-// grouped by the difference they multiply, and two exact regroupings save
-// arithmetic: lam/3 (1 - eta/h) D eta + lam/2 (1 - eta/h) D b =
-// lam/3 (1 - eta/h) D(eta + 3/2 b), and in the eta equation
-// u D eta + 3/2 u D b = u D(eta + 3/2 b) (D is linear), so eta and b are
-// differentiated only through eta + 3/2 b.
+// Every term of eq. (sd_periodic_2D_SGN) / (semi_2D) appears once, in a
+// regrouping that is exact in real arithmetic and saves operations:
+//  - eta and b are differentiated only through eta + 3/2 b and P2:
+//    lam/3 (1 - rho) D eta + lam/2 (1 - rho) D b = lam/3 (1 - rho) D(eta + 3/2 b),
+//    u D eta + 3/2 u D b = u D(eta + 3/2 b) (D is linear), and
+//    g D(h(h+b)) - lam/6 D(eta^2/h) = 1/2 D P2, P2 = 2g h(h+b) - lam/3 eta^2/h;
+//  - the coefficient of D h in the u and v brackets,
+//    lam/6 rho^2 - g (h+b) = -P2/(2h), comes from P2 at the node (rho = eta/h);
+//  - the continuity flux A = u D h + h D u recurs: -1/2 u^2 D h - 1/2 hu D u =
+//    -1/2 u A_x, -1/2 uv D_y h - 1/2 hu D_y v = -1/2 u A_y (and the same with v),
+//    -uw D_x h - hw D_x u = -w A_x;
+//  - the factor 1/2 of the split forms and 1/h go into one scale r/2 per
+//    direction, applied once per equation.
+// The differences are unscaled (f_+ - f_-); sx, sy hold the operator's row
+// factor (1/(2dx) central, 1/dx on a reflecting wall's one-sided row).
 template <typename TC, int BC, typename Src>
 __device__ __forceinline__ void node_rhs_src(const Src& S, int gi, int gj, const Geom& G, TC k[5]) {
-    TC sx = GC(TC, cx2), sy = GC(TC, cy2);
+    TC sx = GC(TC, cx2), sy = GC(TC, cy2), hsx = GC(TC, hcx2), hsy = GC(TC, hcy2);
     if (BC == BC_REFLECTING) {
         // one-sided first/last rows of the reflecting operator: (f1 - f0)/dx
-        if (gi == 0 || gi == G.nx - 1) sx = GC(TC, cx1);
-        if (gj == 0 || gj == G.ny - 1) sy = GC(TC, cy1);
+        if (gi == 0 || gi == G.nx - 1) {
+            sx = GC(TC, cx1);
+            hsx = GC(TC, hcx1);
+        }
+        if (gj == 0 || gj == G.ny - 1) {
+            sy = GC(TC, cy1);
+            hsy = GC(TC, hcy1);
+        }
     }
 #define SM_(op, pos) S.get(op, pos)
 #define DXU(op) sub_(SM_(op, POS_R), SM_(op, POS_L))
 #define DYU(op) sub_(SM_(op, POS_T), SM_(op, POS_B))
-    const TC h = SM_(OP_H, POS_C), u = SM_(OP_U, POS_C), v = SM_(OP_V, POS_C);
-    const TC w = SM_(OP_W, POS_C), eta = SM_(OP_ETA, POS_C), b = SM_(OP_B, POS_C);
-    const TC r = SM_(OP_R, POS_C);
-    const TC hu = SM_(OP_HU, POS_C), hv = SM_(OP_HV, POS_C), uu = SM_(OP_UU, POS_C), vv = SM_(OP_VV, POS_C);
-    const TC g = GC(TC, g), lam = GC(TC, lam), lam3 = GC(TC, lam3), lam6 = GC(TC, lam6);
-    const TC half = tc_const<TC>(0.5);
-    const TC rho = mul_(eta, r);                          // eta / h
-    const TC om = sub_(tc_const<TC>(1.0), rho);                       // 1 - eta / h
-    const TC base = fma_(lam6, mul_(rho, rho), -mul_(g, add_(h, b)));   // lam/6 (eta/h)^2 - g (h + b)
-    const TC lom = mul_(lam3, om);
-    const TC uv = mul_(u, v), hw = mul_(h, w), uw = mul_(u, w), vw = mul_(v, w);
-    const TC rsx = mul_(r, sx), rsy = mul_(r, sy);
-    const TC hrsx = mul_(half, rsx), hrsy = mul_(half, rsy);
+    const TC h = SM_(OP_H, POS_C), u = SM_(OP_U, POS_C), v = SM_(OP_V, POS_C), w = SM_(OP_W, POS_C);
+    const TC rho = SM_(OP_RHO, POS_C), r = SM_(OP_R, POS_C);
+    const TC hu = SM_(OP_HU, POS_C), hv = SM_(OP_HV, POS_C);
+    const TC lam = GC(TC, lam), lam23 = GC(TC, lam23);
+    const TC hrsx = mul_(r, hsx), hrsy = mul_(r, hsy);          // r/(4dx) central
+    const TC base2 = mul_(-SM_(OP_P2, POS_C), r);               // lam/3 rho^2 - 2g (h+b)
+    const TC lom2 = fma_(-lam23, rho, lam23);                   // 2 lam/3 (1 - rho)
 
     const TC dxh = DXU(OP_H), dxu = DXU(OP_U), dxv = DXU(OP_V), dxw = DXU(OP_W), dxf = DXU(OP_E15);
     const TC dyh = DYU(OP_H), dyu = DYU(OP_U), dyv = DYU(OP_V), dyw = DYU(OP_W), dyf = DYU(OP_E15);
+    const TC Ax = fma_(u, dxh, mul_(h, dxu));                   // u D_x h + h D_x u (unscaled)
+    const TC Ay = fma_(v, dyh, mul_(h, dyv));
 
     // h_t = -(u D_x h + h D_x u + v D_y h + h D_y v) + SAT
-    TC kh = -fma_(sx, fma_(u, dxh, mul_(h, dxu)), mul_(sy, fma_(v, dyh, mul_(h, dyv))));
+    TC kh = -fma_(sx, Ax, mul_(sy, Ay));
     if (BC == BC_REFLECTING) {
         // M^{-1} R^T B N_x R (hu) + M^{-1} R^T B N_y R (hv); corners get both
         if (gi == 0) kh = fma_(-GC(TC, satx), hu, kh);
@@ -419,34 +447,29 @@ __device__ __forceinline__ void node_rhs_src(const Src& S, int gi, int gj, const
         if (gj == G.ny - 1) kh = fma_(GC(TC, saty), hv, kh);
     }
 
-    // h u_t = -[ g D_x(h(h+b)) - g(h+b) D_x h + 1/2 h D_x(u^2) - 1/2 u^2 D_x h
-    //           + 1/2 u D_x(hu) - 1/2 hu D_x u + 1/2 D_y(huv) - 1/2 uv D_y h
-    //           + 1/2 hv D_y u - 1/2 hu D_y v + lam/6 (eta/h)^2 D_x h + lam/3 D_x eta
-    //           - lam/3 (eta/h) D_x eta - lam/6 D_x(eta^2/h) + lam/2 (1 - eta/h) D_x b ]
-    TC Xu = mul_(fma_(-half, uu, base), dxh);
-    Xu = fma_(lom, dxf, Xu);
-    Xu = fma_(g, DXU(OP_HS), Xu);
-    Xu = fma_(half, fma_(-hu, dxu, fma_(u, DXU(OP_HU), mul_(h, DXU(OP_UU)))), Xu);
-    Xu = fma_(-lam6, DXU(OP_E2H), Xu);
-    const TC Yu2 = fma_(-hu, dyv, fma_(hv, dyu, fma_(-uv, dyh, DYU(OP_HUV))));   // 2 x the y part
-    const TC ku = -fma_(rsx, Xu, mul_(hrsy, Yu2));
+    // 2h u_t = -[ D_x P2 + (lam/3 rho^2 - 2g(h+b)) D_x h + u (D_x(hu) - A_x) + h D_x(u^2)
+    //             + 2 lam/3 (1 - rho) D_x(eta + 3/2 b) ]_x - [ D_y(huv) + hv D_y u - u A_y ]_y
+    TC Xu = fma_(base2, dxh, DXU(OP_P2));
+    Xu = fma_(u, sub_(DXU(OP_HU), Ax), Xu);
+    Xu = fma_(h, DXU(OP_UU), Xu);
+    Xu = fma_(lom2, dxf, Xu);
+    const TC Yu = fma_(-u, Ay, fma_(hv, dyu, DYU(OP_HUV)));
+    const TC ku = -fma_(hrsx, Xu, mul_(hrsy, Yu));
 
-    // h v_t: the same with x and y (and u and v) exchanged
-    TC Yv = mul_(fma_(-half, vv, base), dyh);
-    Yv = fma_(lom, dyf, Yv);
-    Yv = fma_(g, DYU(OP_HS), Yv);
-    Yv = fma_(half, fma_(-hv, dyv, fma_(v, DYU(OP_HV), mul_(h, DYU(OP_VV)))), Yv);
-    Yv = fma_(-lam6, DYU(OP_E2H), Yv);
-    const TC Xv2 = fma_(-hv, dxu, fma_(hu, dxv, fma_(-uv, dxh, DXU(OP_HUV))));
-    const TC kv = -fma_(rsy, Yv, mul_(hrsx, Xv2));
+    // 2h v_t: the same with x and y (and u and v) exchanged
+    TC Yv = fma_(base2, dyh, DYU(OP_P2));
+    Yv = fma_(v, sub_(DYU(OP_HV), Ay), Yv);
+    Yv = fma_(h, DYU(OP_VV), Yv);
+    Yv = fma_(lom2, dyf, Yv);
+    const TC Xv = fma_(-v, Ax, fma_(hu, dxv, DXU(OP_HUV)));
+    const TC kv = -fma_(hrsy, Yv, mul_(hrsx, Xv));
 
-    // h w_t = lam (1 - eta/h) - 1/2 [ D_x(huw) + hu D_x w - uw D_x h - hw D_x u
-    //                                + D_y(hvw) + hv D_y w - vw D_y h - hw D_y v ]
-    const TC Xw = fma_(-hw, dxu, fma_(-uw, dxh, fma_(hu, dxw, DXU(OP_HUW))));
-    const TC Yw = fma_(-hw, dyv, fma_(-vw, dyh, fma_(hv, dyw, DYU(OP_HVW))));
-    const TC kw = fma_(r, mul_(lam, om), -fma_(hrsx, Xw, mul_(hrsy, Yw)));
+    // h w_t = lam (1 - rho) - 1/2 [ D_x(huw) + hu D_x w - w A_x + D_y(hvw) + hv D_y w - w A_y ]
+    const TC Xw = fma_(-w, Ax, fma_(hu, dxw, DXU(OP_HUW)));
+    const TC Yw = fma_(-w, Ay, fma_(hv, dyw, DYU(OP_HVW)));
+    const TC kw = fma_(r, fma_(-lam, rho, lam), -fma_(hrsx, Xw, mul_(hrsy, Yw)));
 
-    // eta_t = w - u D_x eta - v D_y eta - 3/2 u D_x b - 3/2 v D_y b
+    // eta_t = w - u D_x(eta + 3/2 b) - v D_y(eta + 3/2 b)
     const TC ke = fma_(-v, mul_(sy, dyf), fma_(-u, mul_(sx, dxf), w));
 #undef DXU
 #undef DYU
@@ -563,12 +586,16 @@ constexpr size_t stage_smem_bytes(int rows) {
 
 // One output tile (TILE_X x 8*ROWS nodes at (i0, j0)) of a stage launch: the
 // body shared by the single-grid and the batched kernels.  The pointers of `a`
-// address this grid's planes; `G` is its geometry; DIAG writes the tile's
-// partial sums to partial_slot[0..NDIAG).
+// address this grid's planes; `G` is its geometry.  DIAG and S4D reduce their
+// per-node sums over each 32 x 8 band of the tile (band ry = rows
+// j0 + 8 ry .. j0 + 8 ry + 7) in a fixed order and write the band's NDIAG
+// sums to partial_band0 + ry * band_stride.  The band sums do not depend on
+// the tile height, so every launch shape (and the batched kernel) produces the
+// same partials for the same state.
 template <typename TC, typename TIN, typename TA, int BC, int MODE, int ROWS,
           bool FACT = TileLayout<TC>::factored>
 __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, const Geom& G, int i0, int j0,
-                                           TC* __restrict__ sm, double* partial_slot) {
+                                           TC* __restrict__ sm, double* partial_band0, long long band_stride) {
     constexpr int ROWS_PER_THREAD = ROWS;
     constexpr int HALO_X = TILE_X + 2;
     constexpr int HALO_N = HALO_X * (THREADS_Y * ROWS + 2);
@@ -658,15 +685,19 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
         }
         bad |= h_flags(h);
         if constexpr (FACT)
-            store_operands_factored<TC, HALO_N>(sm, t, h, u, v, w, eta, bb);
+            store_operands_factored<TC, HALO_N>(sm, t, h, u, v, w, eta, bb, G);
         else
-            store_operands<TC, HALO_N>(sm, t, h, u, v, w, eta, bb);
+            store_operands<TC, HALO_N>(sm, t, h, u, v, w, eta, bb, G);
     }
     if (bad) atomicOr(a.flag, bad);
     __syncthreads();
 
     // ---- phase 2: right-hand side and stage algebra at this thread's nodes
-    double dsum[NDIAG] = {0.0, 0.0, 0.0, 0.0};
+    double dsum[ROWS_PER_THREAD][NDIAG];
+#pragma unroll
+    for (int ry = 0; ry < ROWS_PER_THREAD; ry++)
+#pragma unroll
+        for (int q = 0; q < NDIAG; q++) dsum[ry][q] = 0.0;
 #pragma unroll
     for (int ry = 0; ry < ROWS_PER_THREAD; ry++) {
         const int ly = threadIdx.y + ry * THREADS_Y;
@@ -696,58 +727,103 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
                 a.out[f * P + c] = o;
                 qn1[f] = cvt<double>(o);
             }
-            if (MODE == MODE_S4D) node_mass_energy<BC>(qn1, a.b64[c], gi, gj, G, dsum);
+            if (MODE == MODE_S4D) node_mass_energy<BC>(qn1, a.b64[c], gi, gj, G, dsum[ry]);
         } else if (MODE == MODE_DIAG) {
             double qd[5];
 #pragma unroll
             for (int f = 0; f < 5; f++) qd[f] = cvt<double>(a.X[f * P + c]);
-            node_diag<TC, BC>(qd, a.b64[c], gi, gj, G, k, dsum);
+            node_diag<TC, BC>(qd, a.b64[c], gi, gj, G, k, dsum[ry]);
         }
     }
 
     if (MODE == MODE_DIAG || MODE == MODE_S4D) {
-        // fixed-order block reduction: warp shuffle, then thread q over the warps
-        __shared__ double red[BLOCK_THREADS / 32][NDIAG];
-        const int lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-        for (int q = 0; q < NDIAG; q++) {
-            double x = dsum[q];
-            for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-            if (lane == 0) red[warp][q] = x;
-        }
+        // Fixed-order band sums through shared memory (the operand tile is no
+        // longer read): value (ry, q) of thread tid at red[(ry NDIAG + q) 256 + tid];
+        // warp w sums the pairs (ry, q) = w, w + 8, ...: lane l adds the
+        // column-l nodes of the band's eight rows in row order, then a shuffle
+        // tree over the lanes.  Nodes outside the grid contribute +0.
+        constexpr int NPAIR = ROWS_PER_THREAD * NDIAG;
+        static_assert((size_t)(FACT ? (int)NF_OPS : (int)N_OPS) * HALO_N * sizeof(TC) >=
+                          (size_t)NPAIR * BLOCK_THREADS * sizeof(double),
+                      "the operand tile must hold the band sums");
+        double* red = reinterpret_cast<double*>(sm);
         __syncthreads();
-        if (tid < NDIAG) {
-            double x = 0.0;
-            for (int wgi = 0; wgi < BLOCK_THREADS / 32; wgi++) x += red[wgi][tid];
-            partial_slot[tid] = x;
+#pragma unroll
+        for (int ry = 0; ry < ROWS_PER_THREAD; ry++)
+#pragma unroll
+            for (int q = 0; q < NDIAG; q++) red[(ry * NDIAG + q) * BLOCK_THREADS + tid] = dsum[ry][q];
+        __syncthreads();
+        const int lane = tid & 31, warp = tid >> 5;
+        for (int pr = warp; pr < NPAIR; pr += BLOCK_THREADS / 32) {
+            const double* v = red + pr * BLOCK_THREADS;
+            double x = v[lane];
+#pragma unroll
+            for (int r8 = 1; r8 < THREADS_Y; r8++) x += v[r8 * TILE_X + lane];
+            for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+            const int ry = pr / NDIAG, q = pr % NDIAG;
+            if (lane == 0 && j0 + ry * THREADS_Y < G.ny) partial_band0[ry * band_stride + q] = x;
         }
     }
 }
 
 // Tile shape of the single-grid stage kernel per compute type: rows per
-// thread (tile height 8 rows) and the blocks per SM the registers must allow.
-// df64 is bound by the latency of its dependent float operations, so it takes
-// 32x8 tiles (half the shared memory) and four resident blocks.
+// thread (tile height 8 rows) and the blocks per SM the registers must allow
+// (measured choices; the macros allow other builds).  FP64 is bound by the
+// FP64 pipe: 32x24 tiles (106 KB of operands, two blocks per SM) recompute
+// the fewest halo operands.  Float: 32x16.  df64 is bound by the latency of
+// its dependent float operations, so it takes 32x8 tiles and four resident
+// blocks.
+#ifndef SGN_F64_ROWS
+#define SGN_F64_ROWS 3
+#endif
+#ifndef SGN_DF64_ROWS
+#define SGN_DF64_ROWS 1
+#endif
+#ifndef SGN_DF64_MINB
+#define SGN_DF64_MINB 4
+#endif
 template <typename TC>
 struct StageShape {
     static constexpr int rows = ROWS_PER_THREAD;
     static constexpr int min_blocks = 1;
 };
 template <>
+struct StageShape<double> {
+    static constexpr int rows = SGN_F64_ROWS;
+    static constexpr int min_blocks = 1;
+};
+template <>
 struct StageShape<df64> {
-    static constexpr int rows = 1;
-    static constexpr int min_blocks = 4;
+    static constexpr int rows = SGN_DF64_ROWS;
+    static constexpr int min_blocks = SGN_DF64_MINB;
+};
+
+// Resident blocks per SM the registers of the stage kernel must allow: the
+// compute type's, except for the mixed mode (float RHS, double registers).
+#ifndef SGN_MIX_MINB
+#define SGN_MIX_MINB 3
+#endif
+template <typename TC, typename TA>
+struct StageMinBlocks {
+    static constexpr int value = StageShape<TC>::min_blocks;
+};
+template <>
+struct StageMinBlocks<float, double> {
+    static constexpr int value = SGN_MIX_MINB;
 };
 
 template <typename TC, typename TIN, typename TA, int BC, int MODE>
-__global__ void __launch_bounds__(BLOCK_THREADS, StageShape<TC>::min_blocks)
+__global__ void __launch_bounds__(BLOCK_THREADS, StageMinBlocks<TC, TA>::value)
 k_stage(StageArgs<TC, TIN, TA> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TC* sm = reinterpret_cast<TC*>(smem_raw);
-    const long long blk = (long long)blockIdx.y * gridDim.x + blockIdx.x;
     constexpr int R = StageShape<TC>::rows;
+    // band partials in band-major order: band (blockIdx.y R + ry), column block blockIdx.x
     stage_tile<TC, TIN, TA, BC, MODE, R>(a, a.G, blockIdx.x * TILE_X, blockIdx.y * (THREADS_Y * R), sm,
-                                         a.partials ? a.partials + blk * NDIAG : nullptr);
+                                         a.partials ? a.partials + (blockIdx.y * R * (long long)gridDim.x +
+                                                                    blockIdx.x) * NDIAG
+                                                    : nullptr,
+                                         (long long)gridDim.x * NDIAG);
 }
 
 // Second pass of the diagnostics: one block sums the per-block partials in a

@@ -160,14 +160,16 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_forced_stage(MmsArgs m) {
     const StageArgs<double, double, double>& a = m.st;
     const Geom& G = a.G;
     const long long P = G.plane;
-    const int i0 = blockIdx.x * TILE_X, j0 = blockIdx.y * TILE_Y;
+    constexpr int R = StageShape<double>::rows;
+    constexpr int HY = THREADS_Y * R + 2, HN = HALO_X * HY;
+    const int i0 = blockIdx.x * TILE_X, j0 = blockIdx.y * (THREADS_Y * R);
     const int tid = threadIdx.y * TILE_X + threadIdx.x;
     int bad = 0;
     if constexpr (kChecked) {                   // checked builds: poison the tile first
-        for (int k = tid; k < N_OPS * HALO_N; k += BLOCK_THREADS) sm[k] = poison<double>();
+        for (int k = tid; k < N_OPS * HN; k += BLOCK_THREADS) sm[k] = poison<double>();
         __syncthreads();
     }
-    for (int t = tid; t < HALO_N; t += BLOCK_THREADS) {
+    for (int t = tid; t < HN; t += BLOCK_THREADS) {
         const int li = t % HALO_X, lj = t / HALO_X;
         const int gx = halo_index<BC>(i0 - 1 + li, G.nx);
         const int gy = halo_index<BC>(j0 - 1 + lj, G.ny);
@@ -178,20 +180,20 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_forced_stage(MmsArgs m) {
         const long long c = (long long)gy * G.nx + gx;
         const double h = a.X[c];
         bad |= h_flags(h);
-        store_operands<double, HALO_N>(sm, t, h, a.X[P + c], a.X[2 * P + c], a.X[3 * P + c], a.X[4 * P + c],
-                                       a.b[c]);
+        store_operands<double, HN>(sm, t, h, a.X[P + c], a.X[2 * P + c], a.X[3 * P + c], a.X[4 * P + c],
+                                       a.b[c], G);
     }
     if (bad) atomicOr(a.flag, bad);
     __syncthreads();
     const int gi = i0 + threadIdx.x;
 #pragma unroll
-    for (int ry = 0; ry < ROWS_PER_THREAD; ry++) {
+    for (int ry = 0; ry < R; ry++) {
         const int ly = threadIdx.y + ry * THREADS_Y;
         const int gj = j0 + ly;
         if (gi >= G.nx || gj >= G.ny) continue;
         const int t = (ly + 1) * HALO_X + (threadIdx.x + 1);
         double k[5], S[5];
-        node_rhs<double, BC, HALO_X, HALO_N>(sm, t, gi, gj, G, k);
+        node_rhs<double, BC, HALO_X, HN>(sm, t, gi, gj, G, k);
         const long long c = (long long)gj * G.nx + gi;
         const double x = m.xmin + gi * G.dx, y = m.ymin + gj * G.dy;
         if (FORCING == FORCING_MMS) {
@@ -199,7 +201,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_forced_stage(MmsArgs m) {
         } else {
             const double sg = sponge_sigma(x, y, m);
 #pragma unroll
-            for (int f = 0; f < 5; f++) S[f] = -sg * (sm[f * HALO_N + t] - m.q0[f * P + c]);
+            for (int f = 0; f < 5; f++) S[f] = -sg * (a.X[f * P + c] - m.q0[f * P + c]);
         }
 #pragma unroll
         for (int f = 0; f < 5; f++) {

@@ -22,12 +22,17 @@ void sgn_record_error(const char* msg);
 
 namespace {
 
-// Largest launch grid (blocks of 32x16 nodes) the static scratch can serve:
-// 32768 blocks = 16,777,216 nodes, e.g. 4096 x 4096.
+// Largest grid the static scratch serves, counted in blocks of 32x16 nodes:
+// 32768 blocks = 16,777,216 nodes, e.g. 4096 x 4096.  The diagnostics kernel
+// (the FP64 stage kernel's tiles, 32 x kTileY nodes) writes one partial per
+// 32 x 8 band: at most kMaxBands = 2 kMaxBlocks of them.
 constexpr long long kMaxBlocks = 32768;
-// Layout of the scratch, in doubles: [partials: kMaxBlocks * NDIAG | out: NDIAG |
+constexpr long long kMaxBands = 2 * kMaxBlocks;
+constexpr int kTileY = sgn::THREADS_Y * sgn::StageShape<double>::rows;
+constexpr size_t kSmem = sgn::stage_smem_bytes<double, sgn::MODE_DIAG>(sgn::StageShape<double>::rows);
+// Layout of the scratch, in doubles: [partials: kMaxBands * NDIAG | out: NDIAG |
 // flag (one int in the next double slot)].
-constexpr long long kOutOffset = kMaxBlocks * sgn::NDIAG;
+constexpr long long kOutOffset = kMaxBands * sgn::NDIAG;
 constexpr long long kFlagOffset = kOutOffset + sgn::NDIAG;
 constexpr long long kScratchDoubles = kFlagOffset + 1;
 
@@ -66,7 +71,7 @@ cudaError_t scratch_on_device(double** out) {
         double* p = nullptr;
         e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        const size_t smem = (size_t)sgn::N_OPS * sgn::HALO_N * sizeof(double);
+        const size_t smem = kSmem;
         e = cudaFuncSetAttribute(sgn::k_stage<double, double, double, sgn::BC_PERIODIC, sgn::MODE_DIAG>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
@@ -93,8 +98,8 @@ extern "C" SGN_API sgn_status sgn_mass_energy_noalloc(const sgn_params* p, const
     if (!(std::isfinite(p->g) && p->g > 0.0) || !(std::isfinite(p->lambda) && p->lambda >= 0.0))
         return fail(SGN_E_INVAL, "need g > 0 and lambda >= 0, finite");
     const long long gx = (p->nx + sgn::TILE_X - 1) / sgn::TILE_X;
-    const long long gy = (p->ny + sgn::TILE_Y - 1) / sgn::TILE_Y;
-    if (gx * gy > kMaxBlocks || gy > 65535)
+    const long long gy = (p->ny + kTileY - 1) / kTileY;
+    if (gx * ((p->ny + 15) / 16) > kMaxBlocks)
         return fail(SGN_E_INVAL, "grid too large for the static scratch: at most 32768 blocks of "
                                  "32x16 nodes (16,777,216 nodes, e.g. 4096x4096)");
     if (!device_ptr(b_dev) || !device_ptr(q_dev)) return fail(SGN_E_INVAL, "b_dev and q_dev must be device memory");
@@ -120,7 +125,7 @@ extern "C" SGN_API sgn_status sgn_mass_energy_noalloc(const sgn_params* p, const
     e = cudaMemsetAsync(a.flag, 0, sizeof(int), s);
     if (e != cudaSuccess) return fail(SGN_E_CUDA, cudaGetErrorString(e));
     const dim3 grid((unsigned)gx, (unsigned)gy);
-    const size_t smem = (size_t)sgn::N_OPS * sgn::HALO_N * sizeof(double);
+    const size_t smem = kSmem;
     if (per)
         sgn::k_stage<double, double, double, sgn::BC_PERIODIC, sgn::MODE_DIAG>
             <<<grid, dim3(sgn::TILE_X, sgn::THREADS_Y), smem, s>>>(a);
@@ -129,7 +134,8 @@ extern "C" SGN_API sgn_status sgn_mass_energy_noalloc(const sgn_params* p, const
             <<<grid, dim3(sgn::TILE_X, sgn::THREADS_Y), smem, s>>>(a);
     e = cudaGetLastError();
     if (e == cudaSuccess) {
-        sgn::k_reduce_partials<<<1, 256, 0, s>>>(scratch, gx * gy, scratch + kOutOffset);
+        const long long nband = gx * ((p->ny + sgn::THREADS_Y - 1) / sgn::THREADS_Y);
+        sgn::k_reduce_partials<<<1, 256, 0, s>>>(scratch, nband, scratch + kOutOffset);
         e = cudaGetLastError();
     }
     int flag = 0;
