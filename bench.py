@@ -424,7 +424,9 @@ def _adjoint(torch, nsteps: int = 0) -> dict:
         fwd, bwd = t1 - t0, t2 - t1
         res[name] = {"forward_s": fwd, "backward_s": bwd, "backward_over_forward": bwd / fwd,
                      "total_over_forward": (fwd + bwd) / fwd,
-                     "stash_gb": (min(K, p.nsteps) if K > 0 else p.nsteps) * 20 * p.nx * p.ny * 8 / 1e9}
+                     # K > 0: two K-step stashes (the recomputation of the next segment
+                     # overlaps the walk of the current one)
+                     "stash_gb": ((2 * min(K, p.nsteps)) if K > 0 else p.nsteps) * 20 * p.nx * p.ny * 8 / 1e9}
         del out, loss
         torch.cuda.empty_cache()
     s.close()

@@ -14,8 +14,9 @@ steps, so the backward pass need not recompute it.  Backward: for each
 segment, last to first, recompute it from its checkpoint with
 ``sgn_step_record`` (except the last), then walk its steps backwards with
 ``sgn_step_vjp``, adding the gauge cotangents to qbar_h at the observation
-steps.  Memory: the K-step stash, 20 planes per step (4.2 GB at 512^2 for
-K = 100).  K <= 0 keeps the stage states of every step during the forward pass
+steps.  The recomputation of the next segment runs on a second CUDA stream
+while the current one is walked, so the two overlap on the GPU.  Memory: two
+K-step stashes, 20 planes per step (4.2 GB each at 512^2 for K = 100).  K <= 0 keeps the stage states of every step during the forward pass
 instead (no recomputation; 84 GB at 512^2 for 2000 steps, which fits in a
 B300's HBM).
 
@@ -92,24 +93,58 @@ class GaugeRollout(torch.autograd.Function):
                 segments.append((ctx.last, nsteps - ctx.last))
         else:
             segments = [(0, nsteps)]
-        stash = ctx.stash
-        for s0, L in reversed(segments):
-            if K > 0 and s0 == ctx.last:
-                base = 0                            # kept by the forward pass
-            elif K > 0:
-                # recompute the segment from its checkpoint, keeping its stage states
-                if stash is None or stash.shape[0] < L:
-                    stash = torch.empty((L, 20, ny, nx), dtype=torch.float64, device=dev)
-                q = ctx.checkpoints[s0].clone()
-                solver.step_record(q, dt, L, stash)
-                base = 0
-            else:
-                base = s0
-            for n in reversed(range(L)):
-                g = s0 + n + 1                      # this step produces q_g
+        order = list(reversed(segments))
+        main = torch.cuda.current_stream(dev)
+        if K > 0:
+            # Segment k (last to first) is walked backwards on the current stream
+            # while segment k + 1 is recomputed from its checkpoint on a second
+            # stream into the other of two stash buffers (the recomputation uses
+            # the context's RK registers, the adjoint its own scratch), so the
+            # two overlap on the GPU.  Buffer k % 2 serves segment k; the last
+            # segment's stages were kept by the forward pass in buffer 0.
+            side = torch.cuda.Stream(dev)
+            side.wait_stream(main)
+            Kmax = max(L for _, L in order)
+            bufs = [ctx.stash, None]
+            ready = [None] * len(order)             # recomputation of segment k done
+            done = [None] * len(order)              # walk of segment k done
+
+            def recompute(k):
+                s0, L = order[k]
+                slot = k % 2
+                if bufs[slot] is None or bufs[slot].shape[0] < L:
+                    bufs[slot] = torch.empty((Kmax, 20, ny, nx), dtype=torch.float64, device=dev)
+                with torch.cuda.stream(side):
+                    if k >= 2:
+                        side.wait_event(done[k - 2])    # the walk that used this buffer
+                    q = ctx.checkpoints[s0].clone()
+                    solver.step_record(q, dt, L, bufs[slot])
+                    ready[k] = torch.cuda.Event()
+                    ready[k].record(side)
+
+            if len(order) > 1:
+                recompute(1)
+            for k, (s0, L) in enumerate(order):
+                if k > 0:
+                    main.wait_event(ready[k])
+                stash = bufs[k % 2]
+                for n in reversed(range(L)):
+                    g = s0 + n + 1                  # this step produces q_g
+                    if g % every == 0:
+                        qbar[0].reshape(-1).index_add_(0, gauges, grad_obs[g // every - 1])
+                    solver.step_vjp(stash[n], qbar, bbar, dt)
+                done[k] = torch.cuda.Event()
+                done[k].record(main)
+                if k + 2 < len(order):
+                    recompute(k + 2)
+            main.wait_stream(side)
+        else:
+            stash = ctx.stash
+            for n in reversed(range(nsteps)):
+                g = n + 1
                 if g % every == 0:
                     qbar[0].reshape(-1).index_add_(0, gauges, grad_obs[g // every - 1])
-                solver.step_vjp(stash[base + n], qbar, bbar, dt)
+                solver.step_vjp(stash[n], qbar, bbar, dt)
         ctx.stash = None
         h0bar = qbar[0] + qbar[4]
         return bbar, h0bar, None, None, None, None, None, None
