@@ -143,8 +143,12 @@ SGN_API sgn_status sgn_step(sgn_ctx* ctx, void* q_dev, double dt, int nsteps, vo
  * step of device scratch. */
 SGN_API sgn_status sgn_step_diag(sgn_ctx* ctx, void* q_dev, double dt, int nsteps, double* out, void* stream);
 
-/* Diagnostics of q_dev (state type), accumulated in double in a fixed order
- * (bitwise reproducible for a given grid):
+/* Diagnostics of q_dev (state type), accumulated in double in a fixed order:
+ * per-node values summed over 32 x 8 node bands, then the band sums in band
+ * order.  The order depends on the grid only (not on the precision mode or
+ * the kernels' tile shape), so the results are bitwise reproducible, and the
+ * mass and energies of a given double state agree bit for bit across
+ * contexts, the batched path and sgn_mass_energy_noalloc:
  *   out[0] = 1^T M h       out[1] = 1^T M E      out[2] = 1^T M E'
  *   out[3] = <d_q E, RHS(q)>_M
  * with E = h((u^2+v^2)/2 + w^2/6 + g/2 (h + 2b) + lambda/6 (eta/h - 1)^2)
@@ -163,7 +167,7 @@ SGN_API sgn_status sgn_mass_energy(sgn_ctx* ctx, const void* q_dev, double* out,
  * SGN_E_UNSUPPORTED), b_dev is the bathymetry (double, nx*ny, device), q_dev
  * the state (double, five planes, device, 16-byte aligned), out 4 doubles of
  * host memory, filled as by sgn_mass_energy.  Calls no allocating routine:
- * the per-block partial sums live in a 1 MiB array of static device memory
+ * the per-band partial sums live in a 2 MiB array of static device memory
  * that every GPU which loads the library keeps until the process exits.  That
  * limits the grid to 32768 blocks of 32x16 nodes (16,777,216 nodes, e.g.
  * 4096x4096); larger grids return SGN_E_INVAL.  The first call on a device
