@@ -586,6 +586,12 @@ constexpr size_t stage_smem_bytes(int rows) {
     return (size_t)(FACT ? (int)NF_OPS : (int)N_OPS) * (TILE_X + 2) * (THREADS_Y * rows + 2) * sizeof(TC);
 }
 
+#ifndef SGN_DF64_EARLY
+#define SGN_DF64_EARLY 1
+#endif
+#ifndef SGN_F64_EARLY
+#define SGN_F64_EARLY 0
+#endif
 // The stage inputs of one halo tile held in registers: thread tid holds the
 // tile nodes t = tid + k * BLOCK_THREADS, k < NPER.
 template <typename TC, int NPER>
@@ -601,6 +607,7 @@ __device__ __forceinline__ void tile_load(const StageArgs<TC, TIN, TA>& a, const
     const long long P = G.plane;
     const int tid = threadIdx.y * TILE_X + threadIdx.x;
     in.bad = 0;
+    TIN rh[NPER] = {}, ru[NPER] = {}, rv[NPER] = {}, rw[NPER] = {}, re[NPER] = {};
 #pragma unroll
     for (int k = 0; k < NPER; k++) {
         const int t = tid + k * BLOCK_THREADS;
@@ -613,12 +620,22 @@ __device__ __forceinline__ void tile_load(const StageArgs<TC, TIN, TA>& a, const
             continue;
         }
         const long long c = (long long)gy * G.nx + gx;
-        in.h[k] = cvt<TC>(a.X[c]);
-        in.u[k] = cvt<TC>(a.X[P + c]);
-        in.v[k] = cvt<TC>(a.X[2 * P + c]);
-        in.w[k] = cvt<TC>(a.X[3 * P + c]);
-        in.e[k] = cvt<TC>(a.X[4 * P + c]);
+        rh[k] = a.X[c];
+        ru[k] = a.X[P + c];
+        rv[k] = a.X[2 * P + c];
+        rw[k] = a.X[3 * P + c];
+        re[k] = a.X[4 * P + c];
         in.b[k] = a.b[c];
+    }
+    // conversions to the compute type after every load is issued (a conversion
+    // right behind its load would wait for it before the next load issues)
+#pragma unroll
+    for (int k = 0; k < NPER; k++) {
+        in.h[k] = cvt<TC>(rh[k]);
+        in.u[k] = cvt<TC>(ru[k]);
+        in.v[k] = cvt<TC>(rv[k]);
+        in.w[k] = cvt<TC>(rw[k]);
+        in.e[k] = cvt<TC>(re[k]);
     }
 }
 
@@ -649,7 +666,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
     // global load of the block early so that more bytes are in flight: the
     // stage operands of this thread's output nodes first, then all halo-tile
     // inputs of its share of the tile.
-    constexpr bool kEarly = sizeof(TC) == 4;
+    constexpr bool kEarly = sizeof(TC) == 4 || (SGN_DF64_EARLY && std::is_same<TC, df64>::value) ||
+                            (SGN_F64_EARLY && std::is_same<TC, double>::value);
     constexpr bool kEarlyStage = kEarly;
     constexpr int NPER = tile_nper<ROWS>();
     const int gi = i0 + threadIdx.x;
