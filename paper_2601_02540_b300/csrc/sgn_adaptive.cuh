@@ -72,23 +72,73 @@ __global__ void __launch_bounds__(BLOCK_THREADS, StageShape<TC>::min_blocks) k_b
         for (int k = tid; k < N_OPS * HN; k += BLOCK_THREADS) sm[k] = poison<TC>();
         __syncthreads();
     }
-    for (int t = tid; t < HN; t += BLOCK_THREADS) {
-        const int li = t % HX, lj = t / HX;
-        const int gx = halo_index<BC>(i0 - 1 + li, G.nx);
-        const int gy = halo_index<BC>(j0 - 1 + lj, G.ny);
-        if (kChecked && (gx < 0 || gx >= G.nx || gy < 0 || gy >= G.ny)) {
-            bad |= FLAG_BOUNDS;
-            continue;
-        }
-        const long long c = (long long)gy * G.nx + gx;
-        TC y[5];
+    if constexpr (std::is_same<TC, df64>::value) {
+        // df64 (bound by instruction issue): every load of the thread's share of
+        // the tile is issued before the stage input is formed and staged
+        constexpr int NPER = (HN + BLOCK_THREADS - 1) / BLOCK_THREADS;
+        TC ka[NPER][5], bv[NPER];
+        double qa[NPER][5];
 #pragma unroll
-        for (int f = 0; f < 5; f++)
-            y[f] = (MODE == BS_K2)   ? fma_(c_in, k1[f * P + c], cvt<TC>(a.q[f * P + c]))
-                   : (MODE == BS_K3) ? Y3[f * P + c]
-                                     : cvt<TC>(a.q1[f * P + c]);
-        bad |= h_flags(y[0]);
-        store_operands<TC, HN>(sm, t, y[0], y[1], y[2], y[3], y[4], static_cast<const TC*>(a.b)[c], G);
+        for (int k = 0; k < NPER; k++) {
+            const int t = tid + k * BLOCK_THREADS;
+            if (t >= HN) continue;
+            const int gx = halo_index<BC>(i0 - 1 + t % HX, G.nx);
+            const int gy = halo_index<BC>(j0 - 1 + t / HX, G.ny);
+            if (kChecked && (gx < 0 || gx >= G.nx || gy < 0 || gy >= G.ny)) {
+                bad |= FLAG_BOUNDS;
+                continue;
+            }
+            const long long c = (long long)gy * G.nx + gx;
+#pragma unroll
+            for (int f = 0; f < 5; f++) {
+                if (MODE == BS_K2) {
+                    ka[k][f] = k1[f * P + c];
+                    qa[k][f] = a.q[f * P + c];
+                } else if (MODE == BS_K3) {
+                    ka[k][f] = Y3[f * P + c];
+                } else {
+                    qa[k][f] = a.q1[f * P + c];
+                }
+            }
+            bv[k] = static_cast<const TC*>(a.b)[c];
+        }
+#pragma unroll
+        for (int k = 0; k < NPER; k++) {
+            const int t = tid + k * BLOCK_THREADS;
+            if (t >= HN) continue;
+            if constexpr (kChecked) {
+                const int gx = halo_index<BC>(i0 - 1 + t % HX, G.nx);
+                const int gy = halo_index<BC>(j0 - 1 + t / HX, G.ny);
+                if (gx < 0 || gx >= G.nx || gy < 0 || gy >= G.ny) continue;
+            }
+            TC y[5];
+#pragma unroll
+            for (int f = 0; f < 5; f++)
+                y[f] = (MODE == BS_K2)   ? fma_(c_in, ka[k][f], cvt<TC>(qa[k][f]))
+                       : (MODE == BS_K3) ? ka[k][f]
+                                         : cvt<TC>(qa[k][f]);
+            bad |= h_flags(y[0]);
+            store_operands<TC, HN>(sm, t, y[0], y[1], y[2], y[3], y[4], bv[k], G);
+        }
+    } else {
+        for (int t = tid; t < HN; t += BLOCK_THREADS) {
+            const int li = t % HX, lj = t / HX;
+            const int gx = halo_index<BC>(i0 - 1 + li, G.nx);
+            const int gy = halo_index<BC>(j0 - 1 + lj, G.ny);
+            if (kChecked && (gx < 0 || gx >= G.nx || gy < 0 || gy >= G.ny)) {
+                bad |= FLAG_BOUNDS;
+                continue;
+            }
+            const long long c = (long long)gy * G.nx + gx;
+            TC y[5];
+#pragma unroll
+            for (int f = 0; f < 5; f++)
+                y[f] = (MODE == BS_K2)   ? fma_(c_in, k1[f * P + c], cvt<TC>(a.q[f * P + c]))
+                       : (MODE == BS_K3) ? Y3[f * P + c]
+                                         : cvt<TC>(a.q1[f * P + c]);
+            bad |= h_flags(y[0]);
+            store_operands<TC, HN>(sm, t, y[0], y[1], y[2], y[3], y[4], static_cast<const TC*>(a.b)[c], G);
+        }
     }
     if (bad) atomicOr(a.flag, bad);
     __syncthreads();
