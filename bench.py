@@ -60,6 +60,12 @@ BYTES_PER_CELL_STAGE = {"f64": 84 * 8 / 4, "f32": 84 * 4 / 4, "f32_f64acc": 536 
 # 20 differences, the fluxes A_x, A_y 6, h 3, u 16, v 16, w 15, eta 6, stage
 # algebra 17.5 (average of 20, 20, 20, 10).
 FLOPS_PER_CELL_STAGE = 121.5
+# The same arithmetic counted in FP64 pipe operations (an FMA is one; 1/h is
+# one): operands 15, the node's RHS 60, stage algebra 8.75.  The FP64 pipe of
+# a B300 SM issues two thread-operations per clock.
+FP64_OPS_PER_CELL_STAGE = 83.75
+FP64_OPS_PER_SM_CLOCK = 2
+B300_SMS = 148
 DTYPE_NAME = {"f64": "f64", "f32": "f32", "f32_f64acc": "f32+f64acc", "df64": "df64 (float pairs)"}
 
 
@@ -189,7 +195,7 @@ def replica_rate(cells: int, steps: int, ms_max: float, world: int) -> float:
 
 
 def _roofline(prec: str, cells: int, ms_total: float, launches_per_step: int, steps: int,
-              hbm_peak: float, hbm_kind: str) -> dict:
+              hbm_peak: float, hbm_kind: str, sm_mhz: float | None = None) -> dict:
     launch_ms = ms_total / (launches_per_step * steps)
     traffic = _ncu_traffic(prec)
     if prec == "f64":
@@ -201,11 +207,23 @@ def _roofline(prec: str, cells: int, ms_total: float, launches_per_step: int, st
                 "launch_ms": launch_ms,
                 "hbm": {"achieved": BYTES_PER_CELL_STAGE[prec] * cells / (launch_ms * 1e-3) / 1e9,
                         "peak": hbm_peak, "unit": "GB/s",
-                        "frac": BYTES_PER_CELL_STAGE[prec] * cells / (launch_ms * 1e-3) / 1e9 / hbm_peak}}
+                        "frac": BYTES_PER_CELL_STAGE[prec] * cells / (launch_ms * 1e-3) / 1e9 / hbm_peak},
+                # the FP64 pipe's issue rate at the SM clock sampled under load
+                # (148 SMs x 2 thread-operations per clock), against the
+                # algorithmic FP64 operations (FMA = 1) per launch
+                "fp64_pipe": _fp64_pipe(cells, launch_ms, sm_mhz)}
     achieved = BYTES_PER_CELL_STAGE[prec] * cells / (launch_ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": hbm_kind,
             "kernel": "k_stage (RK4 stage, 4 launches/step)", "launch_ms": launch_ms}
+
+
+def _fp64_pipe(cells: int, launch_ms: float, sm_mhz: float | None) -> dict:
+    mhz = sm_mhz if sm_mhz else 2032.0
+    achieved = FP64_OPS_PER_CELL_STAGE * cells / (launch_ms * 1e-3) / 1e9
+    peak = FP64_OPS_PER_SM_CLOCK * B300_SMS * mhz * 1e6 / 1e9
+    return {"achieved": achieved, "peak": peak, "unit": "G FP64 ops/s (FMA = 1)", "frac": achieved / peak,
+            "sm_mhz": mhz}
 
 
 def _cpu_baseline(p_full: inputs.Problem) -> dict:
@@ -268,7 +286,8 @@ def run_ours(args) -> None:
             ms, launches = _time_steps(torch, s, q, p.dt, args.steps, args.warmup, dist)
         results[prec] = {"value": replica_rate(cells, args.steps, ms, world), "ms_per_step": ms / args.steps,
                          "gpu_launches": launches,
-                         "roofline": _roofline(prec, cells, ms, 4, args.steps, hbm_peak, hbm_kind)}
+                         "roofline": _roofline(prec, cells, ms, 4, args.steps, hbm_peak, hbm_kind,
+                                               clocks.get("sm_mhz") if clocks else None)}
         if not args.no_drift:
             # the full job, outside the timed region: energy drift and final state
             q.copy_(q_init)

@@ -6,8 +6,8 @@ diagnostics of float-stage contexts.
   state, bit for bit (same per-node arithmetic on the stored state, same
   fixed-order reduction), in all three precisions and both boundary
   treatments.
-- The diagnostics of a mixed-precision context (float stage states, double
-  q_n) are those of its double state: equal to an FP64 context's, bit for bit.
+- The diagnostics of a mixed-precision or df64 context (double q_n) are those
+  of its double state: equal to an FP64 context's, bit for bit.
 """
 from __future__ import annotations
 
@@ -38,14 +38,19 @@ def test_step_diag_equals_step_then_mass_energy(prec, bc):
     s.close()
 
 
+@pytest.mark.parametrize("prec", ["f32_f64acc", "df64"])
 @pytest.mark.parametrize("bc", [PERIODIC, REFLECTING])
-def test_mixed_context_diagnostics_are_those_of_the_double_state(bc):
+def test_double_state_contexts_share_the_diagnostics(bc, prec):
+    """Contexts with a double state (mixed: float stages; df64: float-pair
+    stages and 32 x 8 tiles instead of the FP64 kernel's 32 x 24) report the
+    mass and energies of the FP64 context bit for bit: the same per-node
+    arithmetic on the stored state, summed per 32 x 8 band in band order."""
     p = inputs.smooth_state(70, 45, bc, seed=32, xmax=1.3, ymax=0.9)
     s64 = gu.solver(p, "f64")
-    smx = gu.solver(p, "f32_f64acc")
+    sx = gu.solver(p, prec)
     q = s64.state(p.q0)
     a = s64.mass_energy(q)
-    b = smx.mass_energy(q)
+    b = sx.mass_energy(q)
     assert (a["mass"], a["energy"], a["energy_shifted"]) == (b["mass"], b["energy"], b["energy_shifted"])
     s64.close()
-    smx.close()
+    sx.close()
