@@ -77,12 +77,19 @@ def _peaks() -> tuple[float, str]:
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def _kernel_hash() -> str:
-    """Hash of the source that defines the stage kernels and their tile shape."""
-    h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2601_02540_b300", "csrc", "sgn_kernels.cuh"), "rb") as fh:
-        h.update(fh.read())
-    return h.hexdigest()[:16]
+def _kernel_hash(text: str | None = None) -> str:
+    """Hash of the source that defines the stage kernels and their tile shape,
+    with // comments, trailing blanks and empty lines removed (so that edits of
+    comments do not invalidate a capture)."""
+    if text is None:
+        with open(os.path.join(ROOT, "paper_2601_02540_b300", "csrc", "sgn_kernels.cuh")) as fh:
+            text = fh.read()
+    lines = []
+    for line in text.splitlines():
+        code = line.split("//", 1)[0].rstrip()
+        if code:
+            lines.append(code)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
 
 
 def _ncu_traffic(prec: str) -> float | None:

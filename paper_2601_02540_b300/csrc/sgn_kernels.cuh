@@ -870,8 +870,9 @@ k_stage(StageArgs<TC, TIN, TA> a) {
                                          (long long)gridDim.x * NDIAG);
 }
 
-// Second pass of the diagnostics: one block sums the per-block partials in a
-// fixed order (each thread a strided slice, then a fixed tree).
+// Second pass of the reductions: one block sums the partials (per band for the
+// diagnostics, per block for the adaptive error) in a fixed order (each thread
+// a strided slice, then a fixed tree).
 static __global__ void __launch_bounds__(256) k_reduce_partials(const double* __restrict__ partials,
                                                           long long nblk, double* __restrict__ out) {
     __shared__ double red[256][NDIAG];

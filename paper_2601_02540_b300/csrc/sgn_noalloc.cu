@@ -8,7 +8,7 @@
 // create allocations of their own.  sgn_mass_energy needs a context (created
 // by sgn_create, which allocates the RK registers and the reduction partials).
 // This entry point needs no context: the caller passes the grid parameters,
-// the bathymetry and the state, and the per-block partial sums live in the
+// the bathymetry and the state, and the per-band partial sums live in the
 // file-scope array below, which every GPU that loads the library holds until
 // the process exits.
 #include "sgn.h"
