@@ -79,7 +79,7 @@ def test_batch_diagnostics_do_not_depend_on_the_tile_height():
         assert np.array_equal(d, ref), rows
     for k, (p, g) in enumerate(zip(probs, bs.unpack(q))):
         s = sgn.Solver.from_problem(p, prec="f64")
-        d = s.mass_energy(g.contiguous())
+        d = s.mass_energy(g.clone())       # an aligned copy of the packed instance
         assert (ref[k, 0], ref[k, 1], ref[k, 2]) == (d["mass"], d["energy"], d["energy_shifted"]), p.name
         s.close()
     bs.close()
