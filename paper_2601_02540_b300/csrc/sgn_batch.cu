@@ -64,7 +64,7 @@ int rows_index(int rows) { return rows == 1 ? 0 : (rows == 2 ? 1 : 2); }
 template <typename TC, typename TIN, typename TA, int MODE, int ROWS>
 cudaError_t blaunch(const sgn_batch* B, const sgn::BatchArgs<TC, TIN, TA>& a, cudaStream_t s) {
     const int ri = rows_index(ROWS);
-    const size_t smem = sgn::stage_smem_bytes<TC, MODE, false>(ROWS);
+    const size_t smem = sgn::stage_smem_bytes<TC, MODE, sgn::kBatchFact<TC>>(ROWS);
     sgn::BatchArgs<TC, TIN, TA> b = a;
     b.tiles = B->tiles[ri];
     sgn::k_batch_stage<TC, TIN, TA, MODE, ROWS>
@@ -75,7 +75,7 @@ cudaError_t blaunch(const sgn_batch* B, const sgn::BatchArgs<TC, TIN, TA>& a, cu
 
 template <typename TC, typename TIN, typename TA, int MODE, int ROWS>
 cudaError_t set_attr() {
-    const size_t smem = sgn::stage_smem_bytes<TC, MODE, false>(ROWS);
+    const size_t smem = sgn::stage_smem_bytes<TC, MODE, sgn::kBatchFact<TC>>(ROWS);
     return cudaFuncSetAttribute(sgn::k_batch_stage<TC, TIN, TA, MODE, ROWS>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
