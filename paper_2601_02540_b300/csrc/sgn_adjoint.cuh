@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adj_weights(AdjArgs a) {
     const double h = a.X[c], u = a.X[P + c], v = a.X[2 * P + c], w = a.X[3 * P + c];
     const double eta = a.X[4 * P + c], bb = a.b[c];
     const double r = recip<double>(h);
-    const double hu = h * u, hv = h * v, hw = h * w;
+    const double hu = h * u, hv = h * v;
     const double hsum = h + bb, rho = eta * r;
     double* S = a.scratch;
     S[AP_HS * P + c] = h * hsum;
@@ -127,16 +127,20 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adj_weights(AdjArgs a) {
     const double lom = G.lam3 * (1.0 - rho);                       // lam/3 (1 - rho)
     const double cc = fma(G.lam6 * rho, rho, -G.g * hsum);         // lam/6 rho^2 - g (h + b)
     const double ra = -r * au, rb = -r * av, rc = (-0.5 * r) * aw; // d k / d B for u, v, w
-    const double uv = u * v;
+    // The D h and D u weights share T = s a_h + (r/2) s (u a_u + v a_v + w a_w)
+    // (the coefficients of the continuity flux u D h + h D u in the h equation
+    // and in the split brackets): V_h = -r s a_u (lam/6 rho^2 - g (h+b)) - u T,
+    // V_u = -h T (and the same with v for y).
     // x weights (row factor s of column i)
     {
         const bool wall = BC == BC_REFLECTING && (i == 0 || i == G.nx - 1);
         const double sx = wall ? a.kx[1].s : a.kx[0].s, hsx = wall ? a.kx[1].hs : a.kx[0].hs;
         const double ru = sx * ra, rw = sx * rc, sah = sx * ah, sae = sx * ae;
         const double hru = 0.5 * ru, hrv = hsx * rb;
+        const double T = fma(hru, u, fma(hrv, v, fma(rw, w, sah)));
         double* W = S + ADJ_WX * P + c;
-        W[VW_H * P] = fma(-rw, u * w, fma(-hrv, uv, fma(-u, sah, ru * fma(-0.5 * u, u, cc))));
-        W[VW_U * P] = fma(-rw, hw, fma(-hrv, hv, fma(-hru, hu, -h * sah)));
+        W[VW_H * P] = fma(ru, cc, -u * T);
+        W[VW_U * P] = -h * T;
         W[VW_V * P] = hrv * hu;
         W[VW_W * P] = rw * hu;
         W[VW_E15 * P] = fma(ru, lom, -u * sae);
@@ -153,9 +157,10 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adj_weights(AdjArgs a) {
         const double sy = wall ? a.ky[1].s : a.ky[0].s, hsy = wall ? a.ky[1].hs : a.ky[0].hs;
         const double rv = sy * rb, rw = sy * rc, sah = sy * ah, sae = sy * ae;
         const double hrv = 0.5 * rv, hru = hsy * ra;
+        const double T = fma(hru, u, fma(hrv, v, fma(rw, w, sah)));
         double* W = S + ADJ_WY * P + c;
-        W[VW_H * P] = fma(-rw, v * w, fma(-hru, uv, fma(-v, sah, rv * fma(-0.5 * v, v, cc))));
-        W[VW_V * P] = fma(-rw, hw, fma(-hru, hu, fma(-hrv, hv, -h * sah)));
+        W[VW_H * P] = fma(rv, cc, -v * T);
+        W[VW_V * P] = -h * T;
         W[VW_U * P] = hru * hv;
         W[VW_W * P] = rw * hv;
         W[VW_E15 * P] = fma(rv, lom, -v * sae);
