@@ -814,9 +814,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
 // thread (tile height 8 rows) and the blocks per SM the registers must allow
 // (measured choices; the macros allow other builds).  FP64 is bound by the
 // FP64 pipe: 32x24 tiles (106 KB of operands, two blocks per SM) recompute
-// the fewest halo operands.  Float: 32x16.  df64 is bound by the latency of
-// its dependent float operations, so it takes 32x8 tiles and four resident
-// blocks.
+// the fewest halo operands.  Float: 32x16, registers for five blocks per SM
+// (the FP32 mode; the mixed mode's limit is StageMinBlocks).  df64 is bound by
+// the latency of its dependent float operations, so it takes 32x8 tiles and
+// four resident blocks.
 #ifndef SGN_F64_ROWS
 #define SGN_F64_ROWS 3
 #endif
@@ -826,10 +827,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
 #ifndef SGN_DF64_MINB
 #define SGN_DF64_MINB 4
 #endif
+#ifndef SGN_F32_MINB
+#define SGN_F32_MINB 5
+#endif
 template <typename TC>
 struct StageShape {
     static constexpr int rows = ROWS_PER_THREAD;
-    static constexpr int min_blocks = 1;
+    static constexpr int min_blocks = SGN_F32_MINB;
 };
 template <>
 struct StageShape<double> {
