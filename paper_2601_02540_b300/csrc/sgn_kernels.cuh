@@ -849,7 +849,7 @@ struct StageShape<df64> {
 // Resident blocks per SM the registers of the stage kernel must allow: the
 // compute type's, except for the mixed mode (float RHS, double registers).
 #ifndef SGN_MIX_MINB
-#define SGN_MIX_MINB 3
+#define SGN_MIX_MINB 4
 #endif
 template <typename TC, typename TA>
 struct StageMinBlocks {
