@@ -335,8 +335,9 @@ SGN_API sgn_status sgn_batch_step(sgn_batch* batch, void* q_dev, int nsteps, voi
 SGN_API sgn_status sgn_batch_mass_energy(sgn_batch* batch, const void* q_dev, double* out, void* stream);
 /* Tile height 8*rows, rows in {1, 2, 4} (default 2). */
 SGN_API sgn_status sgn_batch_set_rows(sgn_batch* batch, int rows);
-/* Time 5 steps of each tile height on a copy of q_dev (allocated and freed
- * here), keep the fastest and return it in *rows_out.  Synchronizes. */
+/* Time 8 steps of each tile height on a copy of q_dev (allocated and freed
+ * here), in three rounds, keep the height with the fastest round and return
+ * it in *rows_out.  Synchronizes. */
 SGN_API sgn_status sgn_batch_autotune(sgn_batch* batch, const void* q_dev, int* rows_out, void* stream);
 
 /* Synchronize `stream` and report (and clear) the latched device flag. */

@@ -421,24 +421,32 @@ sgn_status sgn_batch_autotune(sgn_batch* B, const void* q_dev, int* rows_out, vo
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    // three rounds over the candidates, each timing 8 steps after 2 warm-up
+    // steps; a candidate's time is its fastest round (robust to a slow round,
+    // e.g. while the clocks ramp up)
     const int cand[3] = {1, 2, 4};
-    float best = 1e30f;
-    int best_rows = B->rows;
+    float tmin[3] = {1e30f, 1e30f, 1e30f};
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < 3 && e == cudaSuccess; k++) {
-        e = cudaMemcpyAsync(work, q_dev, bytes, cudaMemcpyDeviceToDevice, s);
-        if (e == cudaSuccess) e = bsteps_any(B, work, 2, cand[k], s);   // warm-up
-        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-        if (e == cudaSuccess) e = bsteps_any(B, work, 5, cand[k], s);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.0f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e == cudaSuccess && ms < best) {
-            best = ms;
-            best_rows = cand[k];
+    for (int round = 0; round < 3 && e == cudaSuccess; round++) {
+        for (int k = 0; k < 3 && e == cudaSuccess; k++) {
+            e = cudaMemcpyAsync(work, q_dev, bytes, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) e = bsteps_any(B, work, 2, cand[k], s);   // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess) e = bsteps_any(B, work, 8, cand[k], s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && ms < tmin[k]) tmin[k] = ms;
         }
     }
+    float best = 1e30f;
+    int best_rows = B->rows;
+    for (int k = 0; k < 3; k++)
+        if (tmin[k] < best) {
+            best = tmin[k];
+            best_rows = cand[k];
+        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(work);
