@@ -1,8 +1,8 @@
 """Parity of the CUDA path (through the C ABI) with the oracle.
 
-Sizes span several 32x16 tiles with ragged tails, tiny odd grids, both
-boundary treatments, the workloads' own initial states and generic states
-with every variable active; the full-size workloads are checked on the whole
+Sizes span several stage tiles (32x24 FP64, 32x16 float, 32x8 df64) with
+ragged tails, tiny odd grids, both boundary treatments, the workloads' own
+initial states and generic states with every variable active; the full-size workloads are checked on the whole
 grid where the oracle is fast enough (1024x512) and on sampled patches where it
 is not (8192^2).  Tolerances are stated in gpu_util.
 """
