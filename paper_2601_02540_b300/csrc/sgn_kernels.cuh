@@ -228,9 +228,9 @@ __device__ __forceinline__ int h_flags(float h) {
 // third-order step of the reciprocal iteration: with e = 1 - h x,
 // 1/h = x / (1 - e) = x (1 + e + e^2 + ...), so x' = x + x (e + e^2) leaves
 // the residual 1 - h x' = e^3 (below 2^-57).  Three fused multiply-adds; the
-// result is within one ulp of the correctly rounded quotient (measured on B300
-// against the IEEE division over 6.7e7 values of [2^-7, 2^7): 0.03% one ulp
-// off, none further), at a fraction of the FP64-pipe cost of a division.
+// result is within one ulp of the correctly rounded quotient (0.03% of values
+// one ulp off, none further; tests/test_gpu_recip.py checks this against the
+// IEEE division), at a fraction of the FP64-pipe cost of a division.
 // Float: the plain quotient.
 template <typename T>
 __device__ __forceinline__ T recip(T h);
