@@ -64,6 +64,18 @@ __device__ __forceinline__ df64 add_(df64 a, df64 b) {
 }
 __device__ __forceinline__ df64 sub_(df64 a, df64 b) { return add_(a, -b); }
 
+// a - b without the final renormalization: hi = fl(a.hi - b.hi), and lo its
+// exact error plus the difference of the low parts, so hi + lo carries the
+// difference to the double-word rounding of its operands but |lo| may exceed
+// ulp(hi)/2.  The consumers (mul_, fma_, add_) treat hi and lo linearly, so
+// an unnormalized pair is as good an input as a normalized one.  For the
+// stencil differences f_+ - f_-, whose results only enter products.
+__device__ __forceinline__ df64 diff_(df64 a, df64 b) {
+    float e;
+    const float s = two_sum(a.hi, -b.hi, e);
+    return {s, __fadd_rn(e, __fsub_rn(a.lo, b.lo))};
+}
+
 __device__ __forceinline__ df64 mul_(df64 a, df64 b) {
     float e;
     const float p = two_prod(a.hi, b.hi, e);

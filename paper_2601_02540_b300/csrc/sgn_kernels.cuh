@@ -259,6 +259,13 @@ __device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b)
 __device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
+// The stencil differences f_+ - f_- (df64: without renormalization, see sgn_df64.cuh).
+#ifndef SGN_DF64_DIFF
+#define SGN_DF64_DIFF 1
+#endif
+__device__ __forceinline__ double diff_(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float diff_(float a, float b) { return __fsub_rn(a, b); }
+
 // Index of the halo node at global coordinate k (k may be -1 or >= n).
 template <int BC>
 __device__ __forceinline__ int halo_index(int k, int n) {
@@ -424,8 +431,13 @@ __device__ __forceinline__ void node_rhs_src(const Src& S, int gi, int gj, const
         }
     }
 #define SM_(op, pos) S.get(op, pos)
+#if SGN_DF64_DIFF
+#define DXU(op) diff_(SM_(op, POS_R), SM_(op, POS_L))
+#define DYU(op) diff_(SM_(op, POS_T), SM_(op, POS_B))
+#else
 #define DXU(op) sub_(SM_(op, POS_R), SM_(op, POS_L))
 #define DYU(op) sub_(SM_(op, POS_T), SM_(op, POS_B))
+#endif
     const TC h = SM_(OP_H, POS_C), u = SM_(OP_U, POS_C), v = SM_(OP_V, POS_C), w = SM_(OP_W, POS_C);
     const TC rho = SM_(OP_RHO, POS_C), r = SM_(OP_R, POS_C);
     const TC hu = SM_(OP_HU, POS_C), hv = SM_(OP_HV, POS_C);
