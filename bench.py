@@ -332,6 +332,7 @@ def run_ours(args) -> None:
     adapt = None if args.no_extra else _adaptive(torch, args.size, results["f64"]["ms_per_step"])
     relax = None if args.no_extra else _relaxed(torch, args.size, results["f64"]["ms_per_step"])
     mms = None if args.no_extra else _manufactured(torch)
+    refl = None if args.no_extra else _reflecting(torch)
     obst = None if args.no_extra else {"f64": _gaussian_obstacle(torch, "f64"),
                                        "df64": _gaussian_obstacle(torch, "df64")}
     head = results["f64"]
@@ -359,6 +360,7 @@ def run_ours(args) -> None:
         "relaxed": relax,
         "manufactured": mms,
         "gaussian_obstacle": obst,
+        "reflecting": refl,
         "energy_drift": drift,
         "errors_vs_f64_after_job": errors,
         "kernel_hash": _kernel_hash(),
@@ -521,6 +523,29 @@ def _relaxed(torch, size: int, rk4_ms_per_step: float, nsteps: int = 20) -> dict
             "overhead": wall / nsteps * 1e3 / rk4_ms_per_step - 1.0,
             "gamma_minus_1_max": float(np.max(np.abs(np.array(gam) - 1.0))),
             "energy_drift_relaxed": er, "energy_drift_rk4": e4}
+
+
+def _reflecting(torch, steps: int = 20, warmup: int = 3) -> dict:
+    """Reflecting walls (SATs and one-sided boundary rows): the workload-2
+    recipe (reflecting [0,200]x[0,100], bumpy bathymetry, one hump) at its own
+    size 1024x512 and scaled to 8192x4096 nodes, RK4 in each precision, timed
+    like the periodic line."""
+    from paper_2601_02540_b300 import sgn
+    out = {}
+    for nx, ny in ((1024, 512), (8192, 4096)):
+        p = inputs.workload2(nx, ny)
+        row = {"workload": f"reflecting {nx}x{ny} (workload-2 recipe), RK4"}
+        for prec in ("f64", "f32", "f32_f64acc", "df64"):
+            s = sgn.Solver.from_problem(p, prec=prec)
+            q = s.state(p.q0)
+            s.init_aux(q)
+            ms, _ = _time_steps(torch, s, q, p.dt, steps, warmup)
+            row[prec] = 4.0 * nx * ny * steps / (ms * 1e-3)
+            del q
+            s.close()
+        out[f"{nx}x{ny}"] = row
+    torch.cuda.empty_cache()
+    return {"unit": UNIT, **out}
 
 
 def _gaussian_obstacle(torch, prec: str = "f64") -> dict:
