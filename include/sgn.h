@@ -186,7 +186,7 @@ SGN_API sgn_status sgn_mass_energy_noalloc(const sgn_params* p, const void* b_de
  *   bbar_dev += (d RHS / d b)^T abar   (accumulated, one plane)
  * All double, device; qbar_dev must not overlap q_dev or abar_dev.  SGN_F64
  * contexts only (else SGN_E_UNSUPPORTED).  The first adjoint call of a context
- * allocates 46 planes of scratch (SGN_E_NOMEM if that fails).  Asynchronous. */
+ * allocates 43 planes of scratch (SGN_E_NOMEM if that fails).  Asynchronous. */
 SGN_API sgn_status sgn_rhs_vjp(sgn_ctx* ctx, const void* q_dev, const void* abar_dev, void* qbar_dev,
                                void* bbar_dev, void* stream);
 
@@ -208,7 +208,7 @@ SGN_API sgn_status sgn_step_record(sgn_ctx* ctx, void* q_dev, double dt, int nst
  * stage).  Internally the stage cotangents are carried with the scales
  * dt/6, dt^2/6, dt^3/12, dt^4/24 factored out; a dt for which dt^4/24 is not a
  * normal double returns SGN_E_INVAL.  The first adjoint call of a context
- * allocates 46 planes of scratch (SGN_E_NOMEM if that fails).  SGN_F64 only.
+ * allocates 43 planes of scratch (SGN_E_NOMEM if that fails).  SGN_F64 only.
  * Asynchronous. */
 SGN_API sgn_status sgn_step_vjp(sgn_ctx* ctx, const void* stash_dev, void* qbar_dev, void* bbar_dev,
                                 double dt, void* stream);

@@ -15,7 +15,7 @@
 //     n <= N-2, and the one-sided end rows add +V(N-1) at n = N-1 and -V(0) at
 //     n = 0), then the chain rule through P_t(q_n, b_n).
 // Two passes, both one node per thread and free of halos and atomics:
-//   k_adj_weights  products P_t, 1/h and the 22 direction weights of each node
+//   k_adj_weights  products P_t, 1/h and the 20 direction weights of each node
 //                  into scratch planes;
 //   k_adj_gather   differences, pointwise part, gathers of the weights of the
 //                  neighbours, chain rule, and (stage mode) the reverse RK4
@@ -32,27 +32,29 @@
 namespace sgn {
 
 // scratch layout (planes): the differentiated products and 1/h (the state
-// planes themselves are read from the state), then the x weights (11) and the
-// y weights (11)
-enum { AP_HS, AP_HU, AP_HV, AP_HUV, AP_HUW, AP_HVW, AP_E2H, AP_E15, AP_R, ADJ_NP };
-constexpr int ADJ_NW = 11;
+// planes themselves are read from the state), then the x weights (10) and the
+// y weights (10).  P = g h(h+b) - lam/6 eta^2/h: g D(h(h+b)) - lam/6 D(eta^2/h)
+// = D P (D is linear), so the two products of the brackets share one plane
+// and one weight slot.
+enum { AP_P, AP_HU, AP_HV, AP_HUV, AP_HUW, AP_HVW, AP_E15, AP_R, ADJ_NP };
+constexpr int ADJ_NW = 10;
 constexpr int ADJ_WX = ADJ_NP;
 constexpr int ADJ_WY = ADJ_NP + ADJ_NW;
 constexpr int ADJ_SCRATCH_PLANES = ADJ_NP + 2 * ADJ_NW;
 constexpr int ADJ_BLOCK = 256;
 
-// weight slots: x uses {H,U,V,W,E15,HS,UU,HU,HUV,HUW,E2H},
-// y uses {H,U,V,W,E15,HS,VV,HV,HUV,HVW,E2H}.  eta and b enter the forward RHS
-// only through eta + 3/2 b, so one E15 slot carries both (d/d eta = 1, d/d b = 3/2).
-enum { VW_H, VW_U, VW_V, VW_W, VW_E15, VW_HS, VW_SQ, VW_HM, VW_HUV, VW_HMW, VW_E2H };
+// weight slots: x uses {H,U,V,W,E15,P,UU,HU,HUV,HUW},
+// y uses {H,U,V,W,E15,P,VV,HV,HUV,HVW}.  eta and b enter the forward RHS
+// only through eta + 3/2 b and P, so one E15 slot carries both
+// (d/d eta = 1, d/d b = 3/2).
+enum { VW_H, VW_U, VW_V, VW_W, VW_E15, VW_P, VW_SQ, VW_HM, VW_HUV, VW_HMW };
 
 enum { ADJ_MODE_RHS = 0, ADJ_MODE_STAGE = 1 };
 
 // Per-direction constants of the pointwise part, for interior rows ([0]) and
-// the one-sided boundary rows ([1]): s = row factor of D, hs = s/2, gs = g s,
-// l6s = (lambda/6) s.
+// the one-sided boundary rows ([1]): s = row factor of D, hs = s/2.
 struct AdjDir {
-    double s, hs, gs, l6s;
+    double s, hs;
 };
 
 struct AdjArgs {
@@ -85,8 +87,8 @@ inline void fill_adj_constants(AdjArgs& a) {
     const Geom& G = a.G;
     const double sx[2] = {G.cx2, G.cx1}, sy[2] = {G.cy2, G.cy1};
     for (int k = 0; k < 2; k++) {
-        a.kx[k] = {sx[k], 0.5 * sx[k], G.g * sx[k], G.lam6 * sx[k]};
-        a.ky[k] = {sy[k], 0.5 * sy[k], G.g * sy[k], G.lam6 * sy[k]};
+        a.kx[k] = {sx[k], 0.5 * sx[k]};
+        a.ky[k] = {sy[k], 0.5 * sy[k]};
     }
     a.m2lam3 = -2.0 * G.lam3;
     a.lam2x = 2.0 * G.lam;
@@ -112,13 +114,12 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adj_weights(AdjArgs a) {
     const double hu = h * u, hv = h * v;
     const double hsum = h + bb, rho = eta * r;
     double* S = a.scratch;
-    S[AP_HS * P + c] = h * hsum;
+    S[AP_P * P + c] = fma(G.g * h, hsum, -(G.lam6 * rho) * eta);
     S[AP_HU * P + c] = hu;
     S[AP_HV * P + c] = hv;
     S[AP_HUV * P + c] = hu * v;
     S[AP_HUW * P + c] = hu * w;
     S[AP_HVW * P + c] = hv * w;
-    S[AP_E2H * P + c] = rho * eta;
     S[AP_E15 * P + c] = fma(1.5, bb, eta);
     S[AP_R * P + c] = r;
 
@@ -144,12 +145,11 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adj_weights(AdjArgs a) {
         W[VW_V * P] = hrv * hu;
         W[VW_W * P] = rw * hu;
         W[VW_E15 * P] = fma(ru, lom, -u * sae);
-        W[VW_HS * P] = ru * G.g;
+        W[VW_P * P] = ru;
         W[VW_SQ * P] = hru * h;          // u^2
         W[VW_HM * P] = hru * u;          // hu
         W[VW_HUV * P] = hrv;
         W[VW_HMW * P] = rw;              // huw
-        W[VW_E2H * P] = -G.lam6 * ru;
     }
     // y weights (row factor s of row j)
     {
@@ -164,12 +164,11 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adj_weights(AdjArgs a) {
         W[VW_U * P] = hru * hv;
         W[VW_W * P] = rw * hv;
         W[VW_E15 * P] = fma(rv, lom, -v * sae);
-        W[VW_HS * P] = rv * G.g;
+        W[VW_P * P] = rv;
         W[VW_SQ * P] = hrv * h;          // v^2
         W[VW_HM * P] = hrv * v;          // hv
         W[VW_HUV * P] = hru;
         W[VW_HMW * P] = rw;              // hvw
-        W[VW_E2H * P] = -G.lam6 * rv;
     }
 }
 
@@ -215,8 +214,8 @@ __global__ void __launch_bounds__(ADJ_BLOCK, 2) k_adj_gather(AdjArgs a) {
 #define GY_(k) (flip_sign(WY[(k) * P + cb], fb) - flip_sign(WY[(k) * P + ct], ft))
     const double pH = GX_(VW_H) + GY_(VW_H), pU = GX_(VW_U) + GY_(VW_U);
     const double pV = GX_(VW_V) + GY_(VW_V), pW = GX_(VW_W) + GY_(VW_W);
-    const double pF = GX_(VW_E15) + GY_(VW_E15), pHS = GX_(VW_HS) + GY_(VW_HS);
-    const double pHUV = GX_(VW_HUV) + GY_(VW_HUV), pE2H = GX_(VW_E2H) + GY_(VW_E2H);
+    const double pF = GX_(VW_E15) + GY_(VW_E15), pP = GX_(VW_P) + GY_(VW_P);
+    const double pHUV = GX_(VW_HUV) + GY_(VW_HUV);
     const double pUU = GX_(VW_SQ), pHU = GX_(VW_HM), pHUW = GX_(VW_HMW);
     const double pVV = GY_(VW_SQ), pHV = GY_(VW_HM), pHVW = GY_(VW_HMW);
 #undef GX_
@@ -227,7 +226,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK, 2) k_adj_gather(AdjArgs a) {
     // h-derivatives combine as d(k_u)/dh = r^2 G_u, d(k_v)/dh = r^2 G_v,
     // d(k_w)/dh = r^2 G_w, where (using r h = 1; the dropped terms are rounding)
     //   G_u = D_x h (lam/2 rho^2 - u^2/2 - g b) + lam/3 (1 - 2 rho) D_x(eta + 3/2 b)
-    //         + g D_x(h(h+b)) + u/2 D_x(hu) - lam/6 D_x(eta^2/h) + (D_y(huv) - uv D_y h)/2,
+    //         + D_x P + u/2 D_x(hu) + (D_y(huv) - uv D_y h)/2   (P = g h(h+b) - lam/6 eta^2/h),
     //   G_w = lam (2 rho - 1) + (D_x(huw) - uw D_x h + D_y(hvw) - vw D_y h)/2,
     // eta and b enter only through D(eta + 3/2 b), and r h = 1 also reduces the
     // u-, v- and w-derivatives to the forms below.
@@ -265,16 +264,14 @@ __global__ void __launch_bounds__(ADJ_BLOCK, 2) k_adj_gather(AdjArgs a) {
     const double huv = 0.5 * uv;
     double Gu = xh * fma(-0.5 * u, u, q2);
     Gu = fma(l12, xf, Gu);
-    Gu = fma(kx.gs, RX_(S + AP_HS * P), Gu);
+    Gu = fma(kx.s, RX_(S + AP_P * P), Gu);
     Gu = fma(u, hxhu, Gu);
-    Gu = fma(-kx.l6s, RX_(S + AP_E2H * P), Gu);
     Gu = fma(ky.hs, RY_(S + AP_HUV * P), Gu);
     Gu = fma(-huv, yh, Gu);
     double Gv = yh * fma(-0.5 * v, v, q2);
     Gv = fma(l12, yf, Gv);
-    Gv = fma(ky.gs, RY_(S + AP_HS * P), Gv);
+    Gv = fma(ky.s, RY_(S + AP_P * P), Gv);
     Gv = fma(v, hyhv, Gv);
-    Gv = fma(-ky.l6s, RY_(S + AP_E2H * P), Gv);
     Gv = fma(kx.hs, RX_(S + AP_HUV * P), Gv);
     Gv = fma(-huv, xh, Gv);
     double Gw = fma(a.lam2x, rho, -G.lam);
@@ -307,13 +304,14 @@ __global__ void __launch_bounds__(ADJ_BLOCK, 2) k_adj_gather(AdjArgs a) {
     }
 
     // ---- chain rule through the products
-    hb = fma(-rho2, pE2H, fma(vw_, pHVW, fma(uw, pHUW, fma(uv, pHUV, fma(v, pHV, fma(u, pHU,
-         fma(fma(2.0, h, bb), pHS, hb + pH)))))));
+    // dP/dh = g (2h + b) + lam/6 rho^2, dP/deta = -lam/3 rho, dP/db = g h
+    hb = fma(vw_, pHVW, fma(uw, pHUW, fma(uv, pHUV, fma(v, pHV, fma(u, pHU,
+         fma(fma(G.g, fma(2.0, h, bb), G.lam6 * rho2), pP, hb + pH))))));
     ub = fma(hw, pHUW, fma(hv, pHUV, fma(h, pHU, fma(2.0 * u, pUU, ub + pU))));
     vb = fma(hw, pHVW, fma(hu, pHUV, fma(h, pHV, fma(2.0 * v, pVV, vb + pV))));
     wb = fma(hv, pHVW, fma(hu, pHUW, wb + pW));
-    eb = fma(2.0 * rho, pE2H, eb + pF);
-    bbar = fma(h, pHS, fma(1.5, pF, bbar));
+    eb = fma(-G.lam3 * rho, pP, eb + pF);
+    bbar = fma(G.g * h, pP, fma(1.5, pF, bbar));
 
     const double qb[5] = {hb, ub, vb, wb, eb};
     const double sg = a.sigma;
