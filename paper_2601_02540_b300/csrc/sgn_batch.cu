@@ -418,9 +418,13 @@ sgn_status sgn_batch_autotune(sgn_batch* B, const void* q_dev, int* rows_out, vo
         cudaGetLastError();
         return bfail(SGN_E_NOMEM, "autotune work copy");
     }
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        cudaFree(work);
+        return bfail(SGN_E_NOMEM, "autotune events");
+    }
     // three rounds over the candidates, each timing 8 steps after 2 warm-up
     // steps; a candidate's time is its fastest round (robust to a slow round,
     // e.g. while the clocks ramp up)
