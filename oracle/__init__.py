@@ -17,7 +17,9 @@ Functions and the passages they follow:
   dx_apply / dy_apply   1D SBP operators, Remark "Concrete SBP operators and SATs"
   mass_weights          diagonal mass matrix M of the same remark
   rhs                   eq. (sd_periodic_2D_SGN) (periodic), eq. (semi_2D) (reflecting)
-  rhs_scale             sum of |terms| of each RHS value (tolerance scale)
+  rhs_scale             forward rounding-error scale of each RHS value: every term
+                        coef * D f counted as |coef| |D| |f|, the factor (1 - eta/h)
+                        as 1 + |eta/h|, pointwise terms by |value| (tolerance scale)
   init_aux              eq. (initialization), Sec. 6
   rk4                   classical RK4 with fixed dt
   diagnostics           mass and energy of Thm. 4.1/4.2 and the rate of eq. (splitcondition)

@@ -99,15 +99,29 @@ sgn_status check_state_ptr(const void* p, const char* name) {
     return SGN_OK;
 }
 
+// The opt-in to more than 48 KB of dynamic shared memory.  The runtime keeps
+// this attribute per device, so it is set once per (kernel, device), with the
+// device current; the result of that first call is kept for later launches.
+constexpr int kMaxDevices = 64;
+template <auto Kern>
+cudaError_t smem_optin(size_t smem) {
+    static std::once_flag once[kMaxDevices];
+    static cudaError_t err[kMaxDevices];
+    int dev = 0;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::call_once(once[dev], [&] {
+        err[dev] = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    return err[dev];
+}
+
 template <typename TC, typename TIN, typename TA, int BC, int MODE>
 cudaError_t launch_stage(const sgn_ctx* c, const StageArgs<TC, TIN, TA>& a, cudaStream_t s) {
     auto kern = sgn::k_stage<TC, TIN, TA, BC, MODE>;
     const size_t smem = sgn::stage_smem_bytes<TC, MODE>(sgn::StageShape<TC>::rows);
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [&] {
-        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    });
+    const cudaError_t attr_err = smem_optin<sgn::k_stage<TC, TIN, TA, BC, MODE>>(smem);
     if (attr_err != cudaSuccess) return attr_err;
     kern<<<c->grid, dim3(sgn::TILE_X, sgn::THREADS_Y), smem, s>>>(a);
     count_launch();
@@ -342,11 +356,7 @@ template <typename TC, int BC, int MODE>
 cudaError_t launch_bs3(const sgn_ctx* c, const sgn::BsArgs& a, cudaStream_t s) {
     auto kern = sgn::k_bs3_stage<TC, BC, MODE>;
     const size_t smem = sgn::stage_smem_bytes<TC, sgn::MODE_RHS>(sgn::StageShape<TC>::rows);
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [&] {
-        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    });
+    const cudaError_t attr_err = smem_optin<sgn::k_bs3_stage<TC, BC, MODE>>(smem);
     if (attr_err != cudaSuccess) return attr_err;
     kern<<<c->grid, dim3(sgn::TILE_X, sgn::THREADS_Y), smem, s>>>(a);
     count_launch();
@@ -475,11 +485,7 @@ template <int BC, int MODE, int FORCING>
 cudaError_t launch_forced(const sgn_ctx* c, const sgn::MmsArgs& m, cudaStream_t s) {
     auto kern = sgn::k_forced_stage<BC, MODE, FORCING>;
     const size_t smem = sgn::stage_smem_bytes<double, sgn::MODE_RHS>(sgn::StageShape<double>::rows);
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [&] {
-        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    });
+    const cudaError_t attr_err = smem_optin<sgn::k_forced_stage<BC, MODE, FORCING>>(smem);
     if (attr_err != cudaSuccess) return attr_err;
     kern<<<c->grid, dim3(sgn::TILE_X, sgn::THREADS_Y), smem, s>>>(m);
     count_launch();

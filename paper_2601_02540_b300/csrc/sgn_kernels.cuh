@@ -227,7 +227,12 @@ __device__ __forceinline__ int h_flags(float h) {
 // rcp.approx.ftz.f64, relative error below 2^-19 as measured on B300) one
 // third-order step of the reciprocal iteration: with e = 1 - h x,
 // 1/h = x / (1 - e) = x (1 + e + e^2 + ...), so x' = x + x (e + e^2) leaves
-// the residual 1 - h x' = e^3 (below 2^-57).  Three fused multiply-adds; the
+// the residual 1 - h x' = e^3 (below 2^-57).  This is the truncated series
+// 1/(1 - e) = 1 + e + e^2 + ... used for division by functional iteration
+// (M. J. Flynn, "On division by functional iteration", IEEE Trans. Computers
+// C-19 (1970); J.-M. Muller et al., Handbook of Floating-Point Arithmetic,
+// 2nd ed. (2018), the chapter on Newton-Raphson-based division), written out
+// as above.  Three fused multiply-adds; the
 // result is within one ulp of the correctly rounded quotient (0.03% of values
 // one ulp off, none further; tests/test_gpu_recip.py checks this against the
 // IEEE division), at a fraction of the FP64-pipe cost of a division.

@@ -144,6 +144,7 @@ extern "C" SGN_API sgn_status sgn_mass_energy_noalloc(const sgn_params* p, const
     if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, a.flag, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(SGN_E_CUDA, cudaGetErrorString(e));
+    if (flag & sgn::FLAG_BOUNDS) return fail(SGN_E_INVAL, "checked build: a tile index left its plane");
     if (flag & sgn::FLAG_NONFINITE) return fail(SGN_E_NONFINITE, "a state value had a non-finite water height");
     if (flag) return fail(SGN_E_NONPOSITIVE_H, "a state value had a non-positive water height");
     return SGN_OK;
