@@ -54,7 +54,11 @@ enum { BC_PERIODIC = 0, BC_REFLECTING = 1 };
  *       sign-flipped (1) or halved (2);
  *   orc_mut_op: 1 one-sided boundary row with 1/(2dx), 2 periodic wrap
  *       missing at the last node, 3 SAT weight 1/dx, 4 SAT sign flipped in y,
- *       5 trapezoid end weights missing in M. */
+ *       5 trapezoid end weights missing in M; in the rounding-error scale
+ *       (orc_rhs_scale): 6 interior rows of |D| with 1/d instead of 1/(2d),
+ *       7 one-sided rows of |D| with 1/(2d) instead of 1/d, 8 the factor
+ *       (1 - eta/h) counted as 2 (1 + |eta/h|), 9 |sum of terms| instead of
+ *       the sum of |terms|, 10 the u, v, w values not divided by |h|. */
 #ifdef ORC_MUTABLE
 int orc_mut_f = -1, orc_mut_k = -1, orc_mut_kind = 0, orc_mut_op = 0;
 #define MUT_OP(n) (orc_mut_op == (n))
@@ -155,16 +159,18 @@ static void sbp_line_abs(int bc, int n, double d, const real* f, long s, real* o
 {
     for (int k = 0; k < n; k++) {
         real val;
+        const double ci = MUT_OP(6) ? 1.0 / d : 1.0 / (2.0 * d);   /* central rows */
+        const double cb = MUT_OP(7) ? 1.0 / (2.0 * d) : 1.0 / d;   /* one-sided rows */
         if (bc == BC_PERIODIC) {
             int kp = (k + 1) % n;
             int km = (k - 1 + n) % n;
-            val = (fabs(f[kp * s]) + fabs(f[km * s])) / (2.0 * d);
+            val = (fabs(f[kp * s]) + fabs(f[km * s])) * ci;
         } else if (k == 0) {
-            val = (fabs(f[1 * s]) + fabs(f[0])) / d;
+            val = (fabs(f[1 * s]) + fabs(f[0])) * cb;
         } else if (k == n - 1) {
-            val = (fabs(f[(n - 1) * s]) + fabs(f[(n - 2) * s])) / d;
+            val = (fabs(f[(n - 1) * s]) + fabs(f[(n - 2) * s])) * cb;
         } else {
-            val = (fabs(f[(k + 1) * s]) + fabs(f[(k - 1) * s])) / (2.0 * d);
+            val = (fabs(f[(k + 1) * s]) + fabs(f[(k - 1) * s])) * ci;
         }
         out[k * s] = val;
     }
@@ -418,13 +424,15 @@ int orc_rhs_scale(const orc_grid* G, const real* b, const real* q, real* scale)
              * difference of two O(1) numbers: its rounding error scales with
              * 1 + |eta/h|, not with its (possibly tiny) value. */
             const real rho = fabs(q[F_ETA * n + c] / h);
-            T.t[F_U][14] = (G->lambda / 2.0) * (1.0 + rho) * D.dx[P_B][c];
-            T.t[F_V][14] = (G->lambda / 2.0) * (1.0 + rho) * D.dy[P_B][c];
-            T.t[F_W][8] = G->lambda * (1.0 + rho);
+            const real one_rho = MUT_OP(8) ? 2.0 * (1.0 + rho) : 1.0 + rho;
+            T.t[F_U][14] = (G->lambda / 2.0) * one_rho * D.dx[P_B][c];
+            T.t[F_V][14] = (G->lambda / 2.0) * one_rho * D.dy[P_B][c];
+            T.t[F_W][8] = G->lambda * one_rho;
             for (int f = 0; f < NFIELD; f++) {
                 real s = 0.0;
-                for (int k = 0; k < T.nt[f]; k++) s += fabs(T.t[f][k]);
-                if (f == F_U || f == F_V || f == F_W) s = s / fabs(h);
+                for (int k = 0; k < T.nt[f]; k++) s += MUT_OP(9) ? T.t[f][k] : fabs(T.t[f][k]);
+                if (MUT_OP(9)) s = fabs(s);
+                if ((f == F_U || f == F_V || f == F_W) && !MUT_OP(10)) s = s / fabs(h);
                 scale[f * n + c] = s;
             }
         }

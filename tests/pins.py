@@ -130,6 +130,54 @@ def transpose_symmetry(o, bc: int, nx=7, ny=5, seed=5) -> tuple[float, float]:
     return float(np.max(np.abs(back - dq) / np.max(sc, axis=(1, 2), keepdims=True))), 1e-13
 
 
+def rhs_scale_constant(o, bc: int, H=0.9, U=0.3, V=-0.2, W=0.15, E=1.1, B=-0.8) -> tuple[float, float]:
+    """Closed form of the rounding-error scale on a constant state (every field
+    and b constant, all active, eta != h).  Each split-form term coef * D f
+    contributes |coef| |D| |f| = |coef| |f| kappa, where kappa is the row sum
+    of |D|: 1/dx on central rows (|f|/(2dx) + |f|/(2dx)), 2/dx on the one-sided
+    rows (f1 - f0)/dx of a reflecting wall.  Summing the terms of eqs.
+    (sd_periodic_2D_SGN) / (semi_2D) by hand, with rho = E/H and the factor
+    (1 - rho) counted as 1 + |rho|:
+      S_h = 2H|U| kx + 2H|V| ky (+ (2/dx) H|U| at x-walls, (2/dy) H|V| at y-walls)
+      S_u = [kx (2gH|H+B| + 2HU^2 + lam/6 rho^2 H + lam/3 |E| (1 + |rho|)
+                + lam/6 E^2/H + lam/2 (1 + |rho|)|B|) + ky 2H|U||V|] / H
+      S_v = the same with (x, U) and (y, V) exchanged
+      S_w = [lam (1 + |rho|) + 2H|W| (|U| kx + |V| ky)] / H
+      S_eta = |W| + |U| (|E| + 3/2 |B|) kx + |V| (|E| + 3/2 |B|) ky
+    (the actual RHS of a constant state is lam (1 - rho)/H in w and W in eta,
+    zero elsewhere).  Returns the largest relative deviation of the oracle's
+    scale from this closed form over all nodes and fields."""
+    nx, ny = 7, 6
+    g = Grid(nx, ny, 0.0, 1.4, 0.0, 0.9, bc, 9.81, 500.0)
+    dx, dy = g.spacing()
+    b = np.full((ny, nx), B)
+    q = np.empty((5, ny, nx))
+    for f, val in enumerate((H, U, V, W, E)):
+        q[f] = val
+    S = o.rhs_scale(g, b, q)
+    kx = np.full(nx, 1.0 / dx)
+    ky = np.full(ny, 1.0 / dy)
+    if bc == REFLECTING:
+        kx[[0, -1]] = 2.0 / dx
+        ky[[0, -1]] = 2.0 / dy
+    KX, KY = np.meshgrid(kx, ky)
+    gr, lam = g.g, g.lam
+    rho = E / H
+    aU, aV, aW, aE, aB = abs(U), abs(V), abs(W), abs(E), abs(B)
+    lam_part = lam / 6 * rho ** 2 * H + lam / 3 * aE * (1 + abs(rho)) + lam / 6 * E ** 2 / H \
+        + lam / 2 * (1 + abs(rho)) * aB
+    ex = np.empty_like(S)
+    ex[0] = 2 * H * aU * KX + 2 * H * aV * KY
+    if bc == REFLECTING:
+        ex[0][:, [0, -1]] += 2.0 / dx * H * aU
+        ex[0][[0, -1], :] += 2.0 / dy * H * aV
+    ex[1] = (KX * (2 * gr * H * abs(H + B) + 2 * H * U ** 2 + lam_part) + KY * 2 * H * aU * aV) / H
+    ex[2] = (KY * (2 * gr * H * abs(H + B) + 2 * H * V ** 2 + lam_part) + KX * 2 * H * aU * aV) / H
+    ex[3] = (lam * (1 + abs(rho)) + 2 * H * aW * (aU * KX + aV * KY)) / H
+    ex[4] = aW + aU * (aE + 1.5 * aB) * KX + aV * (aE + 1.5 * aB) * KY
+    return float(np.max(np.abs(S - ex) / ex)), 1e-14
+
+
 # ------------------------------------------------------------------ consistency (sympy)
 def _analytic_fields(bc: int):
     """Smooth analytic fields on [0,1]^2 with every variable active.  For the

@@ -1,7 +1,8 @@
 """Mutation test: plant one mistake at a time in the oracle (a dropped term, a
 flipped sign, a wrong factor 1/2 in any term of any equation; a wrong boundary
-row, periodic wrap, SAT weight or sign, or mass-matrix end weight) and check
-that at least one of the pins detects it.  The planted mistakes live only in a
+row, periodic wrap, SAT weight or sign, or mass-matrix end weight; a wrong row
+factor, (1 - eta/h) count, summation or division by h in the rounding-error
+scale) and check that at least one of the pins detects it.  The planted mistakes live only in a
 test build of the oracle (-DORC_MUTABLE)."""
 from __future__ import annotations
 
@@ -70,5 +71,37 @@ def test_operator_mistake_is_caught(mutant, op):
     mutant.mutate(-1, -1, 0, op)
     try:
         assert _caught(mutant) != []
+    finally:
+        mutant.mutate()
+
+
+def _scale_caught(M) -> list[str]:
+    fails = []
+    for bc in (PERIODIC, REFLECTING):
+        dev, tol = pins.rhs_scale_constant(M, bc)
+        if not dev <= tol:
+            fails.append(f"scale_constant{bc}")
+        st = inputs.smooth_state(11, 9, bc, seed=4, xmax=1.3, ymax=0.9)
+        g = pins.grid_of(st)
+        k = M.rhs(g, st.b, st.q0)
+        S = M.rhs_scale(g, st.b, st.q0)
+        if not np.all(S >= np.abs(k) * (1 - 1e-14)):
+            fails.append(f"scale_bound{bc}")
+    return fails
+
+
+def test_unmutated_scale_passes(mutant):
+    mutant.mutate()
+    assert _scale_caught(mutant) == []
+
+
+@pytest.mark.parametrize("op", [6, 7, 8, 9, 10])
+def test_rhs_scale_mistake_is_caught(mutant, op):
+    """Mistakes that make the rounding-error scale too large (a row factor of
+    |D| doubled, (1 - eta/h) counted twice, no division by h) or too small
+    (a one-sided row factor halved, |sum| in place of the sum of |terms|)."""
+    mutant.mutate(-1, -1, 0, op)
+    try:
+        assert _scale_caught(mutant) != []
     finally:
         mutant.mutate()

@@ -365,6 +365,17 @@ def test_rhs_scale_bounds_the_rhs(bc, nx, ny):
     assert np.all(S > 0)
 
 
+@pytest.mark.parametrize("bc", [PERIODIC, REFLECTING])
+def test_rhs_scale_closed_form_on_constant_states(bc):
+    """Pins the scale from above: on a constant state its value has a closed
+    form (pins.rhs_scale_constant), which fixes the row sums of |D| (central
+    and one-sided rows), the SAT terms, the count of (1 - eta/h) as
+    1 + |eta/h| and the division of the u, v, w brackets by h; a scale that
+    is too large anywhere would widen every parity bar that uses it."""
+    dev, tol = pins.rhs_scale_constant(O, bc)
+    assert dev <= tol, dev
+
+
 # ------------------------------------------------------------------ solitary wave
 @pytest.mark.slow
 def test_soliton_second_order_against_sgn_solution():
