@@ -25,6 +25,9 @@ Functions and the passages they follow:
   diagnostics           mass and energy of Thm. 4.1/4.2 and the rate of eq. (splitcondition)
   energy_total          1^T M E
   gauge_record / gauge_loss   gauge misfit of the inversion problem
+  bs3_fixed, rk_adaptive     Bogacki-Shampine 3(2) FSAL pair, fixed / adaptive steps
+  p5_tableau, p5_fixed, p5_adaptive   the five-stage third-order FSAL pair of Sec. 6
+                        (coefficients constructed here; PI step-size control)
   *_jvp                 complex-step directional derivatives of the above
 """
 from __future__ import annotations
@@ -141,6 +144,11 @@ def _bind(lib: ctypes.CDLL, pre: str, real: bool) -> None:
                                               ctypes.c_double, ctypes.c_double, ctypes.c_double]),
                 ("rk_adaptive", ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_double,
                                                ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_int, _P, _P]),
+                ("p5_tableau", None, [_P, _P, _P]),
+                ("p5_fixed", ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, _P]),
+                ("p5_adaptive", ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                ctypes.c_int, _P, _P])]
     for name, res, args in sig:
         fn = getattr(lib, pre + name)
@@ -235,6 +243,39 @@ class Oracle:
         n = self._r.orc_rk_adaptive(ctypes.byref(g), _ptr(b), _ptr(q), t0, t_end, dt0, rtol, atol,
                                     max_attempts, _ptr(hist), _ptr(st))
         self._ok(0 if n >= 0 else n, "rk_adaptive")
+        return q, hist[:n].copy(), dict(accepted=int(st[0]), rejected=int(st[1]), t=float(st[2]),
+                                        dt_next=float(st[3]))
+
+    def p5_tableau(self):
+        """(A 5x5, b 5, bhat 6) of the five-stage third-order FSAL pair."""
+        A, b, bh = np.zeros(25), np.zeros(5), np.zeros(6)
+        self._r.orc_p5_tableau(_ptr(A), _ptr(b), _ptr(bh))
+        return A.reshape(5, 5), b, bh
+
+    def p5_fixed(self, grid: Grid, b, q, dt: float, nsteps: int):
+        """The five-stage third-order FSAL pair with a fixed step (every step
+        accepted): (q after nsteps, error vector e of the last step)."""
+        b = _arr(b)
+        q = _arr(q).copy()
+        _check(grid, b, q)
+        e = np.zeros_like(q)
+        g = grid.c()
+        self._ok(self._r.orc_p5_fixed(ctypes.byref(g), _ptr(b), _ptr(q), dt, nsteps, _ptr(e)), "p5_fixed")
+        return q, e
+
+    def p5_adaptive(self, grid: Grid, b, q, t0: float, t_end: float, dt0: float,
+                    rtol: float = 1e-6, atol: float = 1e-6, max_attempts: int = 100000):
+        """Adaptive integration with the five-stage pair and its PI controller
+        (Sec. 6): (q, history, stats) as rk_adaptive."""
+        b = _arr(b)
+        q = _arr(q).copy()
+        _check(grid, b, q)
+        hist = np.zeros((max_attempts, 3))
+        st = np.zeros(4)
+        g = grid.c()
+        n = self._r.orc_p5_adaptive(ctypes.byref(g), _ptr(b), _ptr(q), t0, t_end, dt0, rtol, atol,
+                                    max_attempts, _ptr(hist), _ptr(st))
+        self._ok(0 if n >= 0 else n, "p5_adaptive")
         return q, hist[:n].copy(), dict(accepted=int(st[0]), rejected=int(st[1]), t=float(st[2]),
                                         dt_next=float(st[3]))
 

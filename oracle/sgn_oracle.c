@@ -750,6 +750,160 @@ int orc_rk_adaptive(const orc_grid* G, const double* b, double* q, double t0, do
     free(buf);
     return n;
 }
+
+/* ---- The five-stage third-order FSAL pair (Sec. 6) ------------------------
+ * Sec. 6 integrates with an explicit third-order, five-stage Runge-Kutta
+ * method with the FSAL property and an embedded error estimator, optimized
+ * for stability-limited discretizations of hyperbolic problems; the paper
+ * does not print its coefficients.  The pair below has exactly these
+ * properties; its coefficients were constructed for this build:
+ *  - stability polynomial R(z) = 1 + z + z^2/2 + z^3/6 + 0.0324 z^4 + 0.006 z^5
+ *    (|R(iy)| <= 1 for |y| <= 3.8798: the central SBP operators give an
+ *    imaginary spectrum; classical RK4 reaches 2.83 with four stages);
+ *  - Butcher matrix of the two-register form a_ij = b_j for j < i - 1, with
+ *    a21 = 0.3464, a32 = 0.5544, a43 = 0.3078 and a54, b1..b5 the solution of
+ *    the four third-order conditions and the two stability coefficients;
+ *  - embedded weights bhat over k1..k5 and k6 = f(q_{n+1}) (FSAL), order 2,
+ *    with bhat3..bhat6 = 0.103, 0.1816, 0.1978, 0.2406 and bhat1, bhat2 from
+ *    the two order conditions.
+ * One attempt of size dt from q_n (k1 = f(q_n)):
+ *   k_i = f(q_n + dt sum_{j<i} a_ij k_j),  i = 2..5
+ *   q_{n+1} = q_n + dt sum_i b_i k_i,  k6 = f(q_{n+1})
+ *   e = dt sum_{i<=6} (b_i - bhat_i) k_i     (b6 = 0)
+ * err = sqrt(mean((e / (atol + rtol max(|q_n|, |q_{n+1}|)))^2)), accepted
+ * when err <= 1.  Step size (PI control in digital-filter form, Soederlind
+ * 2003, with the limiter of Soederlind and Wang 2006):
+ *   dt_next = dt rho(eps_n^(B1/K) eps_prev^(B2/K)),  rho(x) = 1 + atan(x - 1),
+ *   eps = 1 / max(err, 1e-10), K = 3, B1 = 0.6, B2 = -0.2,
+ * eps_prev the value of the last accepted attempt (1 before the first); a
+ * rejected attempt is retried from q_n with dt_next (k1 kept); a step that
+ * would pass t_end is cut to land on it. */
+static const double P5_A[5][5] = {
+    {0.0, 0.0, 0.0, 0.0, 0.0},
+    {0.3464, 0.0, 0.0, 0.0, 0.0},
+    {-0.077114705798502101362, 0.5544, 0.0, 0.0, 0.0},
+    {-0.077114705798502101362, 0.51296293729322573879, 0.3078, 0.0, 0.0},
+    {-0.077114705798502101362, 0.51296293729322573879, -0.53636230691175187515,
+     0.25084211224332113157, 0.0}};
+static const double P5_B[5] = {-0.077114705798502101362, 0.51296293729322573879,
+                               -0.53636230691175187515, 0.69586264419699749322,
+                               0.40465143122003074449};
+static const double P5_BHAT[6] = {0.14576960111557976478, 0.13123039888442023522, 0.103, 0.1816,
+                                  0.1978, 0.2406};
+#define P5_B1 0.6
+#define P5_B2 (-0.2)
+#define P5_K 3.0
+#define P5_ERR_FLOOR 1e-10
+
+/* The coefficients above, for the tests: A (25, row-major), b (5), bhat (6). */
+void orc_p5_tableau(double* A, double* b, double* bhat)
+{
+    for (int i = 0; i < 5; i++)
+        for (int j = 0; j < 5; j++) A[5 * i + j] = P5_A[i][j];
+    for (int i = 0; i < 5; i++) b[i] = P5_B[i];
+    for (int i = 0; i < 6; i++) bhat[i] = P5_BHAT[i];
+}
+
+/* One attempt: writes q1 = q_{n+1}, k6 = f(q1) and e; returns err, or -1.
+ * k holds 5 slopes (k[0] = k1 = f(q) on entry), y one stage state. */
+static double p5_attempt(const orc_grid* G, const double* b, const double* q, double* const k[5],
+                         double dt, double rtol, double atol, double* q1, double* k6, double* e,
+                         double* y)
+{
+    const long m = (long)NFIELD * G->nx * G->ny;
+    for (int i = 1; i < 5; i++) {
+        for (long c = 0; c < m; c++) {
+            double s = 0.0;
+            for (int j = 0; j < i; j++) s += P5_A[i][j] * k[j][c];
+            y[c] = q[c] + dt * s;
+        }
+        if (orc_rhs(G, b, y, k[i])) return -1.0;
+    }
+    for (long c = 0; c < m; c++) {
+        double s = 0.0;
+        for (int j = 0; j < 5; j++) s += P5_B[j] * k[j][c];
+        q1[c] = q[c] + dt * s;
+    }
+    if (orc_rhs(G, b, q1, k6)) return -1.0;
+    double sum = 0.0;
+    for (long c = 0; c < m; c++) {
+        double s = 0.0;
+        for (int j = 0; j < 5; j++) s += (P5_B[j] - P5_BHAT[j]) * k[j][c];
+        s += (0.0 - P5_BHAT[5]) * k6[c];
+        e[c] = dt * s;
+        double sc = atol + rtol * fmax(fabs(q[c]), fabs(q1[c]));
+        double r = e[c] / sc;
+        sum += r * r;
+    }
+    return sqrt(sum / (double)m);
+}
+
+/* nsteps fixed steps of the five-stage pair (every step accepted); e_last
+ * (may be NULL) receives the error vector of the last step. */
+int orc_p5_fixed(const orc_grid* G, const double* b, double* q, double dt, int nsteps, double* e_last)
+{
+    const long m = (long)NFIELD * G->nx * G->ny;
+    double* buf = (double*)malloc(sizeof(double) * m * 9);
+    if (!buf) return -1;
+    double* k[5] = {buf, buf + m, buf + 2 * m, buf + 3 * m, buf + 4 * m};
+    double *k6 = buf + 5 * m, *q1 = buf + 6 * m, *e = buf + 7 * m, *y = buf + 8 * m;
+    int rc = orc_rhs(G, b, q, k[0]) ? -1 : 0;
+    for (int s = 0; s < nsteps && rc == 0; s++) {
+        if (p5_attempt(G, b, q, k, dt, 1.0, 1.0, q1, k6, e, y) < 0.0) { rc = -1; break; }
+        memcpy(q, q1, sizeof(double) * m);
+        memcpy(k[0], k6, sizeof(double) * m);
+        if (e_last) memcpy(e_last, e, sizeof(double) * m);
+    }
+    free(buf);
+    return rc;
+}
+
+/* Adaptive integration with the five-stage pair and the PI controller above;
+ * arguments and results as orc_rk_adaptive. */
+int orc_p5_adaptive(const orc_grid* G, const double* b, double* q, double t0, double t_end,
+                    double dt0, double rtol, double atol, int max_attempts, double* hist, double* stats)
+{
+    const long m = (long)NFIELD * G->nx * G->ny;
+    double* buf = (double*)malloc(sizeof(double) * m * 9);
+    if (!buf) return -1;
+    double* k[5] = {buf, buf + m, buf + 2 * m, buf + 3 * m, buf + 4 * m};
+    double *k6 = buf + 5 * m, *q1 = buf + 6 * m, *e = buf + 7 * m, *y = buf + 8 * m;
+    if (orc_rhs(G, b, q, k[0])) { free(buf); return -1; }
+    double t = t0, dt = dt0, eps_prev = 1.0;
+    int acc = 0, rej = 0, n = 0;
+    while (t < t_end && n < max_attempts) {
+        const int last = dt >= t_end - t;
+        const double h = last ? t_end - t : dt;
+        const double err = p5_attempt(G, b, q, k, h, rtol, atol, q1, k6, e, y);
+        if (err < 0.0) { free(buf); return -1; }
+        const int ok = err <= 1.0;
+        const double eps = 1.0 / fmax(err, P5_ERR_FLOOR);
+        const double x = pow(eps, P5_B1 / P5_K) * pow(eps_prev, P5_B2 / P5_K);
+        const double fac = 1.0 + atan(x - 1.0);
+        if (hist) {
+            hist[3 * n] = h;
+            hist[3 * n + 1] = err;
+            hist[3 * n + 2] = ok;
+        }
+        if (ok) {
+            memcpy(q, q1, sizeof(double) * m);
+            memcpy(k[0], k6, sizeof(double) * m);
+            t = last ? t_end : t + h;
+            eps_prev = eps;
+            acc++;
+        } else {
+            rej++;
+        }
+        dt = h * fac;
+        n++;
+    }
+    stats[0] = acc;
+    stats[1] = rej;
+    stats[2] = t;
+    stats[3] = dt;
+    free(buf);
+    return n;
+}
 #endif
 
 /* ---- Relaxation Runge-Kutta (Sec. 7, named there as future work) ----------
