@@ -772,12 +772,17 @@ int orc_rk_adaptive(const orc_grid* G, const double* b, double* q, double t0, do
  *   e = dt sum_{i<=6} (b_i - bhat_i) k_i     (b6 = 0)
  * err = sqrt(mean((e / (atol + rtol max(|q_n|, |q_{n+1}|)))^2)), accepted
  * when err <= 1.  Step size (PI control in digital-filter form, Soederlind
- * 2003, with the limiter of Soederlind and Wang 2006):
- *   dt_next = dt rho(eps_n^(B1/K) eps_prev^(B2/K)),  rho(x) = 1 + atan(x - 1),
- *   eps = 1 / max(err, 1e-10), K = 3, B1 = 0.6, B2 = -0.2,
- * eps_prev the value of the last accepted attempt (1 before the first); a
- * rejected attempt is retried from q_n with dt_next (k1 kept); a step that
- * would pass t_end is cut to land on it. */
+ * 2003, with the limiter of Soederlind and Wang 2006), rho(x) = 1 + atan(x - 1),
+ * eps = 0.9 / max(err, 1e-10) (the controller aims at err = 0.9), K = 3:
+ *   accepted:  dt_next = dt rho(eps^(B1/K) eps_prev^(B2/K)), B1 = 0.7, B2 = -0.4
+ *              (the stabilized PI control of Gustafsson, with exponents
+ *              0.7/K and 0.4/K as in Hairer, Noersett and Wanner, Solving
+ *              Ordinary Differential Equations I, Sec. II.4),
+ *              eps_prev the value of the previous accepted attempt (1 before
+ *              the first);
+ *   rejected:  dt_next = dt rho(eps^(1/K)) (the elementary controller), and the
+ *              attempt is retried from q_n with dt_next (k1 kept).
+ * A step that would pass t_end is cut to land on it. */
 static const double P5_A[5][5] = {
     {0.0, 0.0, 0.0, 0.0, 0.0},
     {0.3464, 0.0, 0.0, 0.0, 0.0},
@@ -790,10 +795,11 @@ static const double P5_B[5] = {-0.077114705798502101362, 0.51296293729322573879,
                                0.40465143122003074449};
 static const double P5_BHAT[6] = {0.14576960111557976478, 0.13123039888442023522, 0.103, 0.1816,
                                   0.1978, 0.2406};
-#define P5_B1 0.6
-#define P5_B2 (-0.2)
+#define P5_B1 0.7
+#define P5_B2 (-0.4)
 #define P5_K 3.0
 #define P5_ERR_FLOOR 1e-10
+#define P5_SAFETY 0.9
 
 /* The coefficients above, for the tests: A (25, row-major), b (5), bhat (6). */
 void orc_p5_tableau(double* A, double* b, double* bhat)
@@ -877,8 +883,8 @@ int orc_p5_adaptive(const orc_grid* G, const double* b, double* q, double t0, do
         const double err = p5_attempt(G, b, q, k, h, rtol, atol, q1, k6, e, y);
         if (err < 0.0) { free(buf); return -1; }
         const int ok = err <= 1.0;
-        const double eps = 1.0 / fmax(err, P5_ERR_FLOOR);
-        const double x = pow(eps, P5_B1 / P5_K) * pow(eps_prev, P5_B2 / P5_K);
+        const double eps = P5_SAFETY / fmax(err, P5_ERR_FLOOR);
+        const double x = ok ? pow(eps, P5_B1 / P5_K) * pow(eps_prev, P5_B2 / P5_K) : pow(eps, 1.0 / P5_K);
         const double fac = 1.0 + atan(x - 1.0);
         if (hist) {
             hist[3 * n] = h;
