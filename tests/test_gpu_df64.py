@@ -4,8 +4,10 @@ The RHS is evaluated in float-pair arithmetic with about 48 significant bits,
 so its rounding unit is u_dw = 2^-48 instead of u = 2^-53, and the bar is the
 FP64 parity bar with that unit:
   RHS    ||gpu_f - orc_f||_inf <= 1e-12 ||orc_f||_inf + 16 u_dw ||S_f||_inf
-  steps  the FP64 step bar (1e-10 relative), the state and the RK
-         accumulator being double
+  steps  the FP64 step bar (1e-10 relative) on short runs, the state and the
+         RK accumulator being double; on the 2000-step workload the bar scaled
+         by the ratio of the rounding units, 2^5 (gpu_util.STEP_TOL_DF64), since
+         rounding errors accumulated over a run scale with the unit
 The diagnostics of a df64 context are those of its double state (equal to an
 FP64 context's bit for bit).
 """
@@ -94,3 +96,19 @@ def test_df64_diagnostics_are_those_of_the_double_state(bc):
     assert abs(a["dEdt"] - b["dEdt"]) <= 1e-10 * abs(a["energy"])
     s64.close()
     sdw.close()
+
+
+def test_df64_workload2_2000_steps_vs_oracle():
+    """The reflecting-wall workload at its stated length (1024x512, 2000 RK4
+    steps) in df64 against the oracle's stored FP64 run: the df64 step bar
+    on every sampled node and on the whole-state norms."""
+    p = inputs.workload2()
+    gd = gu.workload2_golden(p)
+    s = gu.solver(p, "df64")
+    q = s.state(gd["q0"])
+    s.step(q, p.dt, p.nsteps)
+    e = gu.golden_state_errors(gu.to_np(q), gd)
+    s.close()
+    gu.report("df64 steps workload2 1024x512 x2000 (sampled)", state_rel=e["samples"])
+    assert np.all(e["samples"] <= gu.STEP_TOL_DF64), e
+    assert np.all(e["norms"] <= gu.STEP_TOL_DF64), e

@@ -40,8 +40,7 @@ def test_rhs_parity_generic_states(bc, nx, ny):
         s = gu.solver(p)
         dq = gu.to_np(s.rhs(s.state(p.q0)))
         ref, sc = gu.oracle_rhs_and_scale(p, p.q0)
-        e = gu.rhs_errors(dq, ref, sc)
-        assert np.all(e <= 1.0), e
+        gu.check_rhs(f"rhs {nx}x{ny} bc{bc} seed{seed}", dq, ref, sc)
         s.close()
 
 
@@ -57,11 +56,10 @@ def test_rhs_parity_workloads(make):
     q0 = orc.init_aux(g, p.b, p.q0)
     q5 = orc.rk4(g, p.b, q0, p.dt, 5)
     s = gu.solver(p)
-    for q in (q0, q5):
+    for tag, q in (("q0", q0), ("q5", q5)):
         dq = gu.to_np(s.rhs(s.state(q)))
         ref, sc = gu.oracle_rhs_and_scale(p, q)
-        e = gu.rhs_errors(dq, ref, sc)
-        assert np.all(e <= 1.0), e
+        gu.check_rhs(f"rhs {p.name} {p.nx}x{p.ny} {tag}", dq, ref, sc)
     s.close()
 
 
@@ -94,6 +92,7 @@ def test_step_parity_workload1_full():
     """Periodic 64^2, 200 RK4 steps, FP64: within 1e-10 of the oracle."""
     p = inputs.workload1()
     e, out, ref = _step_compare(p, p.nsteps)
+    gu.report("steps workload1 64^2 x200", state_rel=e)
     assert np.all(e <= gu.STEP_TOL), e
 
 
@@ -116,7 +115,32 @@ def test_step_parity_workload2_full_size():
     10 steps on the whole grid."""
     p = inputs.workload2()
     e, _, _ = _step_compare(p, 10)
+    gu.report("steps workload2 1024x512 x10", state_rel=e)
     assert np.all(e <= gu.STEP_TOL), e
+
+
+def test_step_parity_workload2_2000_steps():
+    """The reflecting-wall workload at its stated length: 1024x512, 2000 FP64
+    RK4 steps, against the oracle's final state stored by
+    tests/golden/make_workload2_golden.py (sampled nodes on the walls and
+    inside, per-field norms and the diagnostics of the whole state).  Every
+    sampled value within 1e-10 max(||orc_f||, 1e-3 ||orc_h||) of the oracle."""
+    p = inputs.workload2()
+    gd = gu.workload2_golden(p)
+    s = gu.solver(p)
+    q = s.state(gd["q0"])
+    s.step(q, p.dt, p.nsteps)
+    out = gu.to_np(q)
+    d = s.mass_energy(q)
+    s.close()
+    e = gu.golden_state_errors(out, gd)
+    gu.report("steps workload2 1024x512 x2000 (sampled)", state_rel=e["samples"],
+              norm_rel=e["norms"])
+    assert np.all(e["samples"] <= gu.STEP_TOL), e
+    assert np.all(e["norms"] <= gu.STEP_TOL), e
+    for k, name in enumerate(("mass", "energy", "energy_shifted")):
+        ref = gd["diag_final"][k]
+        assert abs(d[name] - ref) <= 1e-12 * abs(ref), (name, d[name], ref)
 
 
 def _patch(a: np.ndarray, j0: int, i0: int, m: int) -> np.ndarray:
@@ -139,6 +163,9 @@ def test_workload3_full_size_sampled_patches():
     s.step(q, p.dt, 1)
     q1 = gu.to_np(q)
     s.close()
+    # the plain relative error is reported against the whole grid's RHS
+    # norm (a patch far from the humps has a near-zero RHS of its own)
+    kmax = np.max(np.abs(dq), axis=(1, 2))
     rng = np.random.default_rng(7)
     m = 24
     for _ in range(8):
@@ -153,12 +180,14 @@ def test_workload3_full_size_sampled_patches():
                 ref = orc.rhs(g, bp, qp)[sl]
                 sc = orc.rhs_scale(g, bp, qp)[sl]
                 got = _patch(dq, j0, i0, m)
-                e = gu.rhs_errors(got, ref, sc)
-                assert np.all(e <= 1.0), (what, e, gu.rhs_rel(got, ref))
+                gu.report(f"rhs workload3 8192^2 patch ({j0},{i0}) vs the grid's RHS norm",
+                          rel_err_global=np.max(np.abs(got - ref), axis=(1, 2)) / kmax)
+                gu.check_rhs(f"rhs workload3 8192^2 patch ({j0},{i0})", got, ref, sc)
             else:
                 ref = orc.rk4(g, bp, qp, p.dt, 1)[sl]
                 got = _patch(q1, j0, i0, m)
                 e = gu.state_errors(got, ref)
+                gu.report(f"step workload3 8192^2 patch ({j0},{i0})", state_rel=e)
                 assert np.all(e <= gu.STEP_TOL), (what, e)
 
 

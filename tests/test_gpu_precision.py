@@ -125,3 +125,41 @@ def test_mixed_mass_drift_below_float():
         s.close()
     assert drift["f64"] <= 1e-13, drift
     assert drift["f32_f64acc"] < 0.1 * drift["f32"] or drift["f32_f64acc"] <= 1e-10, drift
+
+
+def test_workload2_2000_steps_float_and_mixed_vs_oracle():
+    """The reflecting-wall workload as stated: 1024x512, 2000 RK4 steps in FP32
+    (float state and RHS, FP64 reductions) and in the mixed mode (float RHS,
+    q_n and the accumulator in double), against the FP64 oracle's stored run
+    (tests/golden/workload2_2000.txt).  The errors at the sampled nodes are
+    held to the a-priori bounds of the module docstring with n = 2000 and S,
+    K, Q the larger of the oracle's initial and final values (the FP32 bound's
+    n u32 ||q|| term also covers rounding the double initial state to float);
+    the errors reached and the energy drift (E' = E + g b^2/2, whose constant
+    offset is left out) of each run are reported beside the oracle's drift."""
+    p = inputs.workload2()
+    gd = gu.workload2_golden(p)
+    n = p.nsteps
+    S = np.maximum(gd["S_initial"], gd["S_final"])
+    K = np.maximum(gd["k_initial"], gd["k_final"])
+    Q = np.maximum(_fieldmax(gd["q0"]), gd["maxnorm"])
+    den = np.maximum(gd["maxnorm"], 1e-3 * gd["maxnorm"][0])
+    orc_drift = abs(gd["diag_final"][2] - gd["diag_initial"][2]) / abs(gd["diag_initial"][2])
+    allow = {"f32": 2 * n * (4 * U32 * Q + p.dt * MULT * U32 * (S + K)),
+             "f32_f64acc": 2 * n * p.dt * MULT * U32 * (S + K)}
+    errs = {}
+    for prec in ("f32", "f32_f64acc"):
+        s = gu.solver(p, prec)
+        q = s.state(gd["q0"])
+        e0 = s.mass_energy(q)["energy_shifted"]
+        s.step(q, p.dt, n)
+        e1 = s.mass_energy(q)["energy_shifted"]
+        out = gu.to_np(q)
+        s.close()
+        errs[prec] = np.max(np.abs(out[:, gd["j"], gd["i"]] - gd["values"]), axis=1)
+        gu.report(f"{prec} steps workload2 1024x512 x2000 vs oracle (sampled)",
+                  rel_err=errs[prec] / den, err_over_allow=errs[prec] / allow[prec],
+                  energy_drift=abs(e1 - e0) / abs(e0), oracle_energy_drift=orc_drift)
+    for prec in errs:
+        assert np.all(errs[prec] <= allow[prec]), (prec, errs[prec] / allow[prec])
+    assert errs["f32_f64acc"][0] < errs["f32"][0], errs
