@@ -78,6 +78,7 @@ struct AdjArgs {
     int first;
     Geom G;
     AdjDir kx[2], ky[2];
+    int* flag;             // latched error bits (FLAG_BOUNDS of checked builds)
     double m2lam3;         // -2 lambda / 3
     double lam2x;          // 2 lambda
 };
@@ -195,6 +196,17 @@ __global__ void __launch_bounds__(ADJ_BLOCK, 2) k_adj_gather(AdjArgs a) {
         cr = i < G.nx - 1 ? c + 1 : c;
         cb = j > 0 ? c - G.nx : c;
         ct = j < G.ny - 1 ? c + G.nx : c;
+    }
+    if constexpr (kChecked) {
+        // every neighbour must lie in this node's row (x) or column (y); an
+        // index that does not is flagged and replaced by the node itself
+        const bool bad_x = cl < row || cl >= row + G.nx || cr < row || cr >= row + G.nx;
+        const bool bad_y = cb < 0 || cb >= P || ct < 0 || ct >= P || cb % G.nx != i || ct % G.nx != i;
+        if (bad_x || bad_y) {
+            atomicOr(a.flag, FLAG_BOUNDS);
+            if (bad_x) cl = cr = c;
+            if (bad_y) cb = ct = c;
+        }
     }
 
     // ---- product part: gathers of the neighbours' weights.  At a reflecting

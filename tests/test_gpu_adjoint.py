@@ -18,6 +18,7 @@ import torch
 import oracle as orc
 from oracle import PERIODIC, REFLECTING
 from paper_2601_02540_b300 import adjoint, inputs, sgn
+import gpu_util as gu
 import pins
 
 pytestmark = pytest.mark.gpu
@@ -57,6 +58,7 @@ def test_rhs_vjp_full_transpose_tiny(bc, nx, ny):
         qbar, bbar = s.rhs_vjp(q, _t(a.reshape(p.q0.shape)))
         JqT[:, k] = qbar.cpu().numpy().ravel()
         JbT[:, k] = bbar.cpu().numpy().ravel()
+    s.check()           # latched flags (index bounds in the checked build)
     s.close()
     scale = np.max(np.abs(Jq))
     assert np.max(np.abs(JqT - Jq.T)) <= 1e-13 * scale, np.max(np.abs(JqT - Jq.T)) / scale
@@ -80,6 +82,7 @@ def test_rhs_vjp_dot_product(bc, nx, ny):
         rhs = float(np.sum(dq * qbar.cpu().numpy()) + np.sum(db * bbar.cpu().numpy()))
         mag = float(np.sum(np.abs(jd * a)))
         assert abs(lhs - rhs) <= 1e-13 * mag, (lhs, rhs, mag)
+    s.check()           # latched flags (index bounds in the checked build)
     s.close()
 
 
@@ -104,6 +107,7 @@ def test_step_vjp_dot_product(bc):
         rhs = float(np.sum(dq * qbar.cpu().numpy()) + np.sum(db * bbar.cpu().numpy()))
         mag = float(np.sum(np.abs(jd * a)))
         assert abs(lhs - rhs) <= 1e-13 * mag, (lhs, rhs, mag)
+    s.check()           # latched flags (index bounds in the checked build)
     s.close()
 
 
@@ -117,6 +121,7 @@ def test_step_record_matches_step():
     s.step_record(q2, p.dt, 3, stash)
     assert torch.equal(q1, q2)
     assert torch.equal(stash[0, :5], _t(p.q0))
+    s.check()           # latched flags (index bounds in the checked build)
     s.close()
 
 
@@ -137,6 +142,7 @@ def _gpu_loss_and_grad(p, obs, K, need_grad=True):
         gb, gh = b.grad.cpu().numpy(), h0.grad.cpu().numpy()
     else:
         gb = gh = None
+    s.check()           # latched flags (index bounds in the checked build)
     s.close()
     return float(loss.item()), gb, gh
 
@@ -165,6 +171,69 @@ def test_rollout_gradient_matches_oracle_tlm():
         tlm = orc.gauge_loss_jvp(g, p.b, q0, db, dq, p.dt, p.nsteps, p.extra["every"], gauges, obs)
         adj = float(np.sum(gb * db) + np.sum(gh * dh))
         assert abs(adj - tlm) <= 1e-10 * abs(tlm), (adj, tlm)
+
+
+def test_rollout_gradient_matches_oracle_tlm_checkpointed():
+    """The inversion recipe at 96^2, 200 steps, gauges every 10 steps,
+    checkpoints every 100 steps (two segments, the first recomputed): the
+    adjoint gradient along three of the workload's unit directions equals the
+    oracle's complex-step derivative of the whole rollout within 1e-10."""
+    p = _inversion_problem(96, 200, 10, ngauges=16)
+    g = pins.grid_of(p)
+    gauges = p.extra["gauges"]
+    qt = orc.init_aux(g, p.extra["b_true"], np.stack([p.extra["h_true0"]] + [np.zeros_like(p.b)] * 4))
+    obs = orc.gauge_record(g, p.extra["b_true"], qt, p.dt, p.nsteps, p.extra["every"], gauges)
+    loss, gb, gh = _gpu_loss_and_grad(p, obs, K=100)
+    q0 = orc.init_aux(g, p.b, p.q0)
+    for d in p.extra["dirs"][:3]:
+        dq = np.zeros_like(p.q0)
+        dq[0] = d[1]
+        dq[4] = d[1]          # eta0 = h0
+        tlm = orc.gauge_loss_jvp(g, p.b, q0, d[0], dq, p.dt, p.nsteps, p.extra["every"], gauges, obs)
+        adj = float(np.sum(gb * d[0]) + np.sum(gh * d[1]))
+        assert abs(adj - tlm) <= 1e-10 * abs(tlm), (adj, tlm)
+
+
+def _gpu_gauge_record(p, b, h0, K=100):
+    """Gauge readings of a GPU rollout from (b, h0) (no gradient)."""
+    s = sgn.Solver.from_problem(p)
+    gauges = torch.as_tensor(p.extra["gauges"], device="cuda")
+    with torch.no_grad():
+        out = adjoint.gauge_rollout(_t(b), _t(h0), s, p.dt, p.nsteps, p.extra["every"], gauges, K)
+    rec = out.cpu().numpy()
+    s.check()
+    s.close()
+    return rec
+
+
+def test_rollout_gradient_matches_finite_differences_full_size():
+    """The inversion workload as stated: reflecting 512^2, 2000 RK4 steps, 16
+    gauges read every 10 steps against the run with the perturbed (truth)
+    bathymetry, checkpoints every 100 steps; the adjoint gradient along each
+    of the 20 unit directions over (b, h0) against central differences of the
+    GPU loss with eps = 1e-6, within 1e-5 relative."""
+    p = inputs.workload4()
+    assert (p.nx, p.nsteps, p.extra["every"], len(p.extra["dirs"])) == (512, 2000, 10, 20)
+    obs = _gpu_gauge_record(p, p.extra["b_true"], p.extra["h_true0"])
+    loss, gb, gh = _gpu_loss_and_grad(p, obs, K=100)
+    eps = 1e-6
+    b0, h00 = p.b.copy(), p.q0[0].copy()
+    rel = []
+    try:
+        for d in p.extra["dirs"]:
+            p.b = b0 + eps * d[0]
+            p.q0[0] = h00 + eps * d[1]
+            lp, _, _ = _gpu_loss_and_grad(p, obs, K=100, need_grad=False)
+            p.b = b0 - eps * d[0]
+            p.q0[0] = h00 - eps * d[1]
+            lm, _, _ = _gpu_loss_and_grad(p, obs, K=100, need_grad=False)
+            fd = (lp - lm) / (2 * eps)
+            adj = float(np.sum(gb * d[0]) + np.sum(gh * d[1]))
+            rel.append(abs(adj - fd) / abs(adj))
+    finally:
+        p.b, p.q0[0] = b0, h00
+    gu.report("adjoint workload4 512^2 x2000 K=100 vs central FD (20 directions)", rel_err=rel)
+    assert max(rel) <= 1e-5, rel
 
 
 def test_rollout_gradient_matches_finite_differences():
@@ -204,4 +273,5 @@ def test_step_vjp_rejects_dt_outside_scaled_range():
         s.step_vjp(stash[0], qbar, bbar, 1e-90)
     assert ei.value.status == 1          # SGN_E_INVAL
     assert torch.equal(qbar, _t(np.ones_like(p.q0)))
+    s.check()           # latched flags (index bounds in the checked build)
     s.close()

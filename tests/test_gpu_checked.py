@@ -23,11 +23,12 @@ def test_parity_suites_pass_on_the_checked_build():
     assert os.path.exists(os.path.join(ROOT, "paper_2601_02540_b300", "libsgn_checked.so"))
     env = dict(os.environ, SGN_LIBRARY="checked")
     suites = ["test_gpu_parity.py", "test_gpu_precision.py", "test_gpu_df64.py", "test_gpu_monitor.py",
-              "test_gpu_adaptive.py", "test_gpu_mms.py", "test_gpu_sponge.py", "test_gpu_batch.py"]
+              "test_gpu_adaptive.py", "test_gpu_mms.py", "test_gpu_sponge.py", "test_gpu_batch.py",
+              "test_gpu_adjoint.py"]
     probe = ("import paper_2601_02540_b300.sgn as s; s.lib(); "
              "assert s.LIB_PATH.endswith('libsgn_checked.so'), s.LIB_PATH")
     subprocess.run([sys.executable, "-c", probe], cwd=ROOT, env=env, check=True)
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-m", "gpu", "-p", "no:cacheprovider",
                         *[os.path.join(HERE, f) for f in suites]],
-                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=1200)
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=1800)
     assert r.returncode == 0, r.stdout[-4000:] + r.stderr[-2000:]
