@@ -65,7 +65,6 @@ FLOPS_PER_CELL_STAGE = 121.5
 # a B300 SM issues two thread-operations per clock.
 FP64_OPS_PER_CELL_STAGE = 83.75
 FP64_OPS_PER_SM_CLOCK = 2
-B300_SMS = 148
 DTYPE_NAME = {"f64": "f64", "f32": "f32", "f32_f64acc": "f32+f64acc", "df64": "df64 (float pairs)"}
 
 
@@ -201,42 +200,63 @@ def replica_rate(cells: int, steps: int, ms_max: float, world: int) -> float:
     return 4.0 * cells * steps * world / (ms_max * 1e-3)
 
 
+def measure_fp64_peak(torch, local: int, iters: int = 16384, reps: int = 3) -> dict:
+    """The FP64 FMA rate of this GPU, measured by the library's FMA-chain
+    kernel (sgn_measure_fp64_fma: independent chains, 8 blocks of 256 threads
+    per SM), best of `reps` launches after one warm-up, with the SM clock
+    sampled while it runs.  The SM count is read from the device."""
+    from paper_2601_02540_b300 import sgn
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sgn.sgn_measure_fp64_fma(iters)
+    best = 0.0
+    with ClockSampler(local) as clk:
+        for _ in range(reps):
+            n, sec = sgn.sgn_measure_fp64_fma(iters)
+            best = max(best, n / sec)
+    clocks = clk.summary()
+    mhz = clocks.get("sm_mhz")
+    return {"fma_per_s": best, "tflops": 2.0 * best / 1e12, "sms": sms, "sm_mhz": mhz,
+            "fma_per_sm_clock": best / (sms * mhz * 1e6) if mhz else None,
+            "reasons": clocks.get("reasons"),
+            "how": f"sgn_measure_fp64_fma: {iters} iterations of 16 independent FMA chains per thread, "
+                   f"8 x 256 threads per SM, best of {reps} launches (CUDA events)"}
+
+
 def _roofline(prec: str, cells: int, ms_total: float, launches_per_step: int, steps: int,
-              hbm_peak: float, hbm_kind: str, sm_mhz: float | None = None) -> dict:
+              hbm_peak: float, hbm_kind: str, fp64: dict | None = None, sm_mhz: float | None = None) -> dict:
     launch_ms = ms_total / (launches_per_step * steps)
     traffic = _ncu_traffic(prec)
     if prec == "f64":
-        # peak from the unit counts and the clock: the FP64 pipe completes 2 FMA
-        # (4 flop) per SM and clock (ncu: sm__sass_thread_inst_executed_op_dfma
-        # peak_sustained = 2 per SM), 148 SMs, at the SM clock sampled under load
-        mhz = sm_mhz if sm_mhz else 2032.0
-        peak = 2.0 * FP64_OPS_PER_SM_CLOCK * B300_SMS * mhz * 1e6 / 1e12
+        # FP64 is ALU-bound on B300: the peak is the measured FMA rate of the
+        # FP64 pipe (2 flop per FMA), taken on this GPU by measure_fp64_peak
+        peak = fp64["tflops"]
         achieved = FLOPS_PER_CELL_STAGE * cells / (launch_ms * 1e-3) / 1e12
         return {"bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                "peak_kind": (f"FP64 pipe: 2 FMA per SM per clock x {B300_SMS} SMs x {mhz:.0f} MHz "
-                              f"(nominal {FP64_NOMINAL_TFLOPS} TFLOP/s; no measured FP64 entry)"),
+                "peak_kind": (f"measured: FP64 FMA-chain kernel, {fp64['fma_per_s'] / 1e12:.4f} T FMA/s on "
+                              f"{fp64['sms']} SMs at {fp64['sm_mhz']} MHz (nominal {FP64_NOMINAL_TFLOPS} "
+                              "TFLOP/s)"),
+                "fp64_peak": fp64,
                 "kernel": "k_stage (RK4 stage, 4 launches/step)",
                 "launch_ms": launch_ms,
                 "hbm": {"achieved": BYTES_PER_CELL_STAGE[prec] * cells / (launch_ms * 1e-3) / 1e9,
                         "peak": hbm_peak, "unit": "GB/s",
                         "frac": BYTES_PER_CELL_STAGE[prec] * cells / (launch_ms * 1e-3) / 1e9 / hbm_peak},
-                # the FP64 pipe's issue rate at the SM clock sampled under load
-                # (148 SMs x 2 thread-operations per clock), against the
-                # algorithmic FP64 operations (FMA = 1) per launch
-                "fp64_pipe": _fp64_pipe(cells, launch_ms, sm_mhz)}
+                # the algorithmic FP64 operations (FMA = 1, a subtraction = 1)
+                # per launch against the measured FMA rate: the FP64 pipe's
+                # issue rate, one operation per slot
+                "fp64_pipe": _fp64_pipe(cells, launch_ms, fp64, sm_mhz)}
     achieved = BYTES_PER_CELL_STAGE[prec] * cells / (launch_ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": hbm_kind,
             "kernel": "k_stage (RK4 stage, 4 launches/step)", "launch_ms": launch_ms}
 
 
-def _fp64_pipe(cells: int, launch_ms: float, sm_mhz: float | None) -> dict:
-    mhz = sm_mhz if sm_mhz else 2032.0
+def _fp64_pipe(cells: int, launch_ms: float, fp64: dict, sm_mhz: float | None) -> dict:
     achieved = FP64_OPS_PER_CELL_STAGE * cells / (launch_ms * 1e-3) / 1e9
-    peak = FP64_OPS_PER_SM_CLOCK * B300_SMS * mhz * 1e6 / 1e9
+    peak = fp64["fma_per_s"] / 1e9
     return {"achieved": achieved, "peak": peak, "unit": "G FP64 ops/s (FMA = 1)", "frac": achieved / peak,
-            "sm_mhz": mhz}
+            "peak_kind": "measured FMA rate", "sm_mhz_kernel": sm_mhz, "sm_mhz_peak": fp64["sm_mhz"]}
 
 
 def _cpu_baseline(p_full: inputs.Problem) -> dict:
@@ -283,6 +303,7 @@ def run_ours(args) -> None:
     p = inputs.workload3(args.size, args.size)
     cells = p.nx * p.ny
     hbm_peak, hbm_kind = _peaks()
+    fp64 = measure_fp64_peak(torch, local)
     results = {}
     finals = {}
     drift = {}
@@ -299,7 +320,7 @@ def run_ours(args) -> None:
             ms, launches = _time_steps(torch, s, q, p.dt, args.steps, args.warmup, dist)
         results[prec] = {"value": replica_rate(cells, args.steps, ms, world), "ms_per_step": ms / args.steps,
                          "gpu_launches": launches,
-                         "roofline": _roofline(prec, cells, ms, 4, args.steps, hbm_peak, hbm_kind,
+                         "roofline": _roofline(prec, cells, ms, 4, args.steps, hbm_peak, hbm_kind, fp64,
                                                clocks.get("sm_mhz") if clocks else None)}
         if not args.no_drift:
             # the full job, outside the timed region: energy drift and final state
@@ -333,14 +354,15 @@ def run_ours(args) -> None:
             dist.destroy_process_group()
         return
     cpu = _cpu_baseline(p) if world == 1 and not args.no_cpu else None
-    ens = None if args.no_extra else _ensemble(torch, 50, 5)
+    ens = None if args.no_extra else _ensemble(torch, 1000, 5)
     adj = None if args.no_extra else _adjoint(torch)
     adapt = None if args.no_extra else _adaptive(torch, args.size, results["f64"]["ms_per_step"])
     relax = None if args.no_extra else _relaxed(torch, args.size, results["f64"]["ms_per_step"])
     mms = None if args.no_extra else _manufactured(torch)
     refl = None if args.no_extra else _reflecting(torch)
     obst = None if args.no_extra else {"f64": _gaussian_obstacle(torch, "f64"),
-                                       "df64": _gaussian_obstacle(torch, "df64")}
+                                       "df64": _gaussian_obstacle(torch, "df64"),
+                                       "f64_bs3": _gaussian_obstacle(torch, "f64", "bs3")}
     head = results["f64"]
     line = {
         "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
@@ -376,11 +398,13 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
-def _ensemble(torch, steps: int, warmup: int) -> dict:
+def _ensemble(torch, steps: int, warmup: int, loop_steps: int = 50) -> dict:
     """Ragged ensemble (256 instances, N in {128,...,512}, half periodic, half
     reflecting, FP32 state, each with its own dt): the batched path (one
-    launch per stage over all instances, graph replays, autotuned tile height)
-    against a per-instance launch loop, both timed with CUDA events."""
+    launch per stage over all instances, graph replays, autotuned tiling: tile
+    height and per-tile or persistent kernel) over `steps` steps (the job's
+    1000 by default), against a per-instance launch loop over `loop_steps`,
+    both timed with CUDA events."""
     from paper_2601_02540_b300 import sgn
     probs = inputs.workload5()
     cells = sum(p.nx * p.ny for p in probs)
@@ -388,6 +412,7 @@ def _ensemble(torch, steps: int, warmup: int) -> dict:
     q = bs.pack([p.q0 for p in probs])
     bs.init_aux(q)
     rows = bs.autotune(q)
+    tiling = bs.tiling()
     bs.step(q, warmup)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -404,7 +429,7 @@ def _ensemble(torch, steps: int, warmup: int) -> dict:
         s.step(st, p.dt, warmup)
     torch.cuda.synchronize()
     e0.record()
-    for _ in range(steps):
+    for _ in range(loop_steps):
         for s, st, p in zip(solvers, states, probs):
             s.step(st, p.dt, 1)
     e1.record()
@@ -413,11 +438,14 @@ def _ensemble(torch, steps: int, warmup: int) -> dict:
     for s in solvers:
         s.close()
     rate_b = 4.0 * cells * steps / (ms_batch * 1e-3)
-    rate_l = 4.0 * cells * steps / (ms_loop * 1e-3)
+    rate_l = 4.0 * cells * loop_steps / (ms_loop * 1e-3)
+    hbm = BYTES_PER_CELL_STAGE["f32"] * rate_b / 1e9
+    peak, kind = _peaks()
     return {"workload": "256 instances N~U{128,192,256,384,512}, half periodic/half reflecting, FP32",
-            "cells": cells, "steps": steps, "value": rate_b, "unit": UNIT,
-            "per_instance_loop": rate_l, "speedup_vs_loop": rate_b / rate_l, "rows": rows,
-            "hbm_gbs": BYTES_PER_CELL_STAGE["f32"] * rate_b / 1e9,
+            "cells": cells, "steps": steps, "value": rate_b, "unit": UNIT, "wall_ms": ms_batch,
+            "per_instance_loop": rate_l, "loop_steps": loop_steps, "speedup_vs_loop": rate_b / rate_l,
+            "rows": rows, "tiling": tiling,
+            "hbm_gbs": hbm, "hbm_frac": hbm / peak, "hbm_peak_kind": kind,
             "mass_finite": bool(np.all(np.isfinite(d)))}
 
 
@@ -467,36 +495,43 @@ def _adjoint(torch, nsteps: int = 0) -> dict:
     return res
 
 
+RHS_PER_ATTEMPT = {"p5s3": 5, "bs3": 3}
+
+
 def _adaptive(torch, size: int, rk4_ms_per_step: float) -> dict:
-    """The paper's time path (Sec. 6): adaptive third-order FSAL pair, rtol =
-    atol = 1e-6, on the benchmark workload (FP64), over the job's time span
-    (500 fixed CFL steps), first step the CFL step.  Wall-clock time of the
-    whole call (the host reads the error norm after every attempt); one RHS
-    evaluation per node and stage counts as one cell-stage.  The fixed-step
-    RK4 job time over the same span is given for comparison."""
+    """The paper's time path (Sec. 6): adaptive third-order FSAL integration,
+    rtol = atol = 1e-6, on the benchmark workload (FP64), over the job's time
+    span (500 fixed CFL steps), first step the CFL step; with the five-stage
+    pair (the kind the paper uses) and, for comparison, Bogacki-Shampine 3(2).
+    Wall-clock time of the whole call (the host reads the error norm after
+    every attempt); one RHS evaluation per node and stage counts as one
+    cell-stage.  The fixed-step RK4 job time over the same span is given for
+    comparison."""
     from paper_2601_02540_b300 import sgn
     p = inputs.workload3(size, size)
     s = sgn.Solver.from_problem(p, prec="f64")
     q0 = s.state(p.q0)
     s.init_aux(q0)
     q = q0.clone()
-    s.step_adaptive(q, 0.0, 2 * p.dt, p.dt, want_history=False)       # warm-up (loads the kernels)
-    q.copy_(q0)
     T = p.nsteps * p.dt
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    st, hist = s.step_adaptive(q, 0.0, T, p.dt)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    s.close()
-    rhs_evals = 3 * st["attempts"] + 1
     cells = p.nx * p.ny
-    return {"workload": f"periodic {p.nx}x{p.ny}, t in [0, {p.nsteps} dt_cfl], rtol = atol = 1e-6, FP64",
-            "rk4_fixed_step_job_s": rk4_ms_per_step * p.nsteps / 1e3,
-            "accepted": st["accepted"], "rejected": st["rejected"], "rhs_evaluations": rhs_evals,
-            "mean_accepted_dt_over_cfl": float(np.mean([h[0] for h in hist if h[2] == 1.0]) / p.dt),
-            "wall_s": wall, "value": rhs_evals * cells / wall, "unit": "cell-stages/s",
-            "ms_per_rhs": wall / rhs_evals * 1e3}
+    out = {"workload": f"periodic {p.nx}x{p.ny}, t in [0, {p.nsteps} dt_cfl], rtol = atol = 1e-6, FP64",
+           "rk4_fixed_step_job_s": rk4_ms_per_step * p.nsteps / 1e3}
+    for pair in ("p5s3", "bs3"):
+        s.step_adaptive(q, 0.0, 2 * p.dt, p.dt, want_history=False, pair=pair)   # warm-up (loads the kernels)
+        q.copy_(q0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, hist = s.step_adaptive(q, 0.0, T, p.dt, pair=pair)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        rhs_evals = RHS_PER_ATTEMPT[pair] * st["attempts"] + 1
+        out[pair] = {"accepted": st["accepted"], "rejected": st["rejected"], "rhs_evaluations": rhs_evals,
+                     "mean_accepted_dt_over_cfl": float(np.mean([h[0] for h in hist if h[2] == 1.0]) / p.dt),
+                     "wall_s": wall, "value": rhs_evals * cells / wall, "unit": "cell-stages/s",
+                     "ms_per_rhs": wall / rhs_evals * 1e3}
+    s.close()
+    return out
 
 
 def _relaxed(torch, size: int, rk4_ms_per_step: float, nsteps: int = 20) -> dict:
@@ -554,33 +589,36 @@ def _reflecting(torch, steps: int = 20, warmup: int = 3) -> dict:
     return {"unit": UNIT, **out}
 
 
-def _gaussian_obstacle(torch, prec: str = "f64") -> dict:
+def _gaussian_obstacle(torch, prec: str = "f64", pair: str = "p5s3") -> dict:
     """The paper's headline GPU run shape (solitary wave over a Gaussian
-    obstacle, 1600 x 800 periodic, to t = 12) with its time path: the adaptive
-    third-order FSAL integrator at rtol = atol = 1e-6, FP64, from the CFL
-    step.  Wall-clock time to solution, inputs already on the device.  The
-    paper's H200 figure (12.7 s, FP64) is for its whole experiment including
-    analysis, with the hyperbolic traveling wave as initial data: context,
-    not the same measurement."""
+    obstacle, 1600 x 800 periodic, to t = 12) with its time path: an adaptive
+    third-order FSAL pair at rtol = atol = 1e-6 from the CFL step (the
+    five-stage pair, the kind of integrator the paper names; its coefficients
+    are this library's, so the step sequence is not the paper's).  Wall-clock
+    time to solution, inputs already on the device.  The paper's H200 figure
+    (12.7 s, FP64) is for its whole experiment including analysis, with the
+    hyperbolic traveling wave as initial data: context, not the same
+    measurement."""
     from paper_2601_02540_b300 import sgn
     p = inputs.gaussian_obstacle()
     s = sgn.Solver.from_problem(p, prec=prec)
     q0 = s.state(p.q0)
     s.init_aux(q0)
     q = q0.clone()
-    s.step_adaptive(q, 0.0, 20 * p.dt, p.dt, want_history=False)      # warm-up
+    s.step_adaptive(q, 0.0, 20 * p.dt, p.dt, want_history=False, pair=pair)      # warm-up
     q.copy_(q0)
     T = p.extra["t_end"]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    st, hist = s.step_adaptive(q, 0.0, T, p.dt, max_attempts=1000000)
+    st, hist = s.step_adaptive(q, 0.0, T, p.dt, max_attempts=1000000, pair=pair)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     d = s.mass_energy(q)
     d0 = s.mass_energy(q0)
     s.close()
-    rhs = 3 * st["attempts"] + 1
-    return {"workload": f"gaussian obstacle {p.nx}x{p.ny} periodic, t in [0, {T}], adaptive tol 1e-6, {prec}",
+    rhs = RHS_PER_ATTEMPT[pair] * st["attempts"] + 1
+    return {"workload": f"gaussian obstacle {p.nx}x{p.ny} periodic, t in [0, {T}], adaptive tol 1e-6, "
+                        f"{prec}, pair {pair}",
             "wall_s": wall, "t_reached": st["t"], "accepted": st["accepted"], "rejected": st["rejected"],
             "rhs_evaluations": rhs, "ms_per_rhs": wall / rhs * 1e3,
             "mean_dt": T / max(st["accepted"], 1), "dt_cfl": p.dt,
@@ -688,12 +726,19 @@ def main() -> None:
                     help="grid side (8192 = the workload; smaller sizes only for profiling)")
     ap.add_argument("--adjoint-only", type=int, default=0, metavar="NSTEPS",
                     help="run only the adjoint leg with NSTEPS RK4 steps and print its JSON (profiling)")
+    ap.add_argument("--ensemble-only", type=int, default=0, metavar="NSTEPS",
+                    help="run only the ensemble leg, timing NSTEPS steps, and print its JSON (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.adjoint_only > 0:
         import torch
         print(json.dumps({"adjoint": _adjoint(torch, args.adjoint_only)}))
+        return
+    if args.ensemble_only > 0:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"ensemble": _ensemble(torch, args.ensemble_only, 5, loop_steps=5)}))
         return
     if args.impl == "reference":
         run_reference(args)

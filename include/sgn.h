@@ -22,7 +22,8 @@
  *   sgn_step_relaxed energy-conserving relaxation RK4 (named as future work
  *                    in the paper's conclusions; energy of Thm. 4.1).
  *   sgn_step_adaptive  adaptive time integration with an embedded
- *                    third-order FSAL pair and step-size control (Sec. 6).
+ *                    five-stage third-order FSAL pair and step-size control
+ *                    (Sec. 6).
  *   sgn_rhs_vjp, sgn_step_record, sgn_step_vjp   the discrete adjoint of the
  *                    RHS and of one RK4 step (no counterpart in the paper).
  *
@@ -128,7 +129,11 @@ SGN_API sgn_status sgn_init_aux(sgn_ctx* ctx, void* q_dev, void* stream);
 SGN_API sgn_status sgn_rhs(sgn_ctx* ctx, const void* q_dev, void* dq_dev, void* stream);
 
 /* Advance q_dev (state type, in place) by nsteps >= 0 classical RK4 steps of
- * size dt (finite, > 0): 4 fused RHS+stage launches per step. */
+ * size dt (finite, > 0): 4 fused RHS+stage launches per step.  On grids of at
+ * most 2^21 nodes (launch-bound) runs of 50 steps are replayed from a CUDA
+ * graph, captured on the context's first such call for this (q_dev, dt) on a
+ * private stream; the launches and results are those of the direct path.
+ * When `stream` is itself capturing, the steps are launched directly. */
 SGN_API sgn_status sgn_step(sgn_ctx* ctx, void* q_dev, double dt, int nsteps, void* stream);
 
 /* sgn_step that also monitors every new state: the fourth stage launch of
@@ -270,32 +275,59 @@ SGN_API sgn_status sgn_step_sponge(sgn_ctx* ctx, void* q_dev, double dt, int nst
 SGN_API sgn_status sgn_step_relaxed(sgn_ctx* ctx, void* q_dev, double dt, int nsteps, double* gammas,
                                     double* t_out, void* stream);
 
+/* The Runge-Kutta pairs of sgn_step_adaptive. */
+typedef enum { SGN_PAIR_P5S3 = 0, SGN_PAIR_BS3 = 1 } sgn_pair;
+
 /* Adaptive time integration of q_dev (double, in place) from t0 to t_end
- * (Sec. 6: the paper uses an explicit third-order Runge-Kutta pair with the
- * first-same-as-last property, an embedded error estimate and automatic
- * step-size control, rtol = atol = 1e-6; it does not print the pair).  The
- * pair is Bogacki-Shampine 3(2): k1 = f(q_n) (reused from the previous
- * accepted step), k2 = f(q_n + dt/2 k1), k3 = f(q_n + 3dt/4 k2),
- * q_{n+1} = q_n + dt (2/9 k1 + 1/3 k2 + 4/9 k3), k4 = f(q_{n+1}), error
- * e = dt (-5/72 k1 + 1/12 k2 + 1/9 k3 - 1/8 k4).  An attempt is accepted when
+ * (Sec. 6: an explicit third-order, five-stage Runge-Kutta method with the
+ * first-same-as-last (FSAL) property and an embedded error estimator,
+ * optimized for stability-limited hyperbolic problems, rtol = atol = 1e-6;
+ * the paper does not print its coefficients).  `pair` selects
+ *   SGN_PAIR_P5S3  a five-stage third-order FSAL pair with those properties,
+ *                  constructed for this library: Butcher matrix of the
+ *                  two-register form a_ij = b_j (j < i-1) with
+ *                  a21 = 0.3464, a32 = 0.5544, a43 = 0.3078,
+ *                  a54 = 0.25084211224332113157,
+ *                  b = (-0.077114705798502101362, 0.51296293729322573879,
+ *                       -0.53636230691175187515, 0.69586264419699749322,
+ *                       0.40465143122003074449),
+ *                  embedded second-order weights over k1..k5 and
+ *                  k6 = f(q_{n+1}): bhat = (0.14576960111557976478,
+ *                  0.13123039888442023522, 0.103, 0.1816, 0.1978, 0.2406);
+ *                  stability polynomial 1 + z + z^2/2 + z^3/6 + 0.0324 z^4 +
+ *                  0.006 z^5, stable on the imaginary axis up to |z| = 3.8798.
+ *                  k_i = f(q_n + dt sum_{j<i} a_ij k_j), q_{n+1} = q_n +
+ *                  dt sum b_i k_i, e = dt sum_{i<=6} (b_i - bhat_i) k_i.
+ *                  Step size with the limiter rho(x) = 1 + atan(x - 1) and
+ *                  eps = 0.9 / max(err, 1e-10): after an accepted attempt
+ *                  dt_next = dt rho(eps^(0.7/3) eps_prev^(-0.4/3)) (Gustafsson's
+ *                  PI control; eps_prev that of the previous accepted attempt,
+ *                  1 before the first), after a rejected one
+ *                  dt_next = dt rho(eps^(1/3)).  Five fused RHS launches per attempt.
+ *   SGN_PAIR_BS3   the Bogacki-Shampine 3(2) FSAL pair: k2 = f(q_n + dt/2 k1),
+ *                  k3 = f(q_n + 3dt/4 k2), q_{n+1} = q_n + dt (2/9 k1 + 1/3 k2 +
+ *                  4/9 k3), k4 = f(q_{n+1}), e = dt (-5/72 k1 + 1/12 k2 + 1/9 k3
+ *                  - 1/8 k4); dt_next = dt min(10, max(0.2, 0.9 err^(-1/3)))
+ *                  (10 when err = 0).  Three fused RHS launches per attempt.
+ * In both, k1 = f(q_n) is the FSAL slope of the previous accepted step; an
+ * attempt is accepted when
  *   err = sqrt(mean over all 5 nx ny values of (e / (atol + rtol max(|q_n|, |q_{n+1}|)))^2) <= 1;
- * the next step size is dt min(10, max(0.2, 0.9 err^(-1/3))) (10 when err = 0);
  * a rejected attempt is retried from q_n; a step that would pass t_end is cut
  * to land on it.  An attempt whose stage inputs have h <= 0 or a non-finite h
  * counts as rejected with err = +inf.  The first attempt has size dt0 > 0;
- * rtol, atol >= 0, not both 0; at most max_attempts attempts.
- * Three fused RHS launches and one reduction per attempt; the host reads err
- * after each attempt (synchronizes `stream` every attempt).
+ * rtol, atol >= 0, not both 0; at most max_attempts attempts; an unknown pair
+ * returns SGN_E_INVAL.  One reduction per attempt; the host reads err after
+ * each attempt (synchronizes `stream` every attempt).
  * hist (host, 3*max_attempts doubles, or NULL) receives {dt, err, accepted}
  * per attempt; stats (host, 5 doubles) receives {accepted, rejected, t
  * reached, next dt, attempts}.  SGN_F64 or SGN_DF64 contexts (the RHS in
- * double or in float pairs; the state, slopes and error norm in double; else
- * SGN_E_UNSUPPORTED).  The first call of a context allocates 35 planes of
- * scratch (SGN_E_NOMEM if that fails).  An initial state with h <= 0 or a
- * non-finite h returns SGN_E_NONPOSITIVE_H / SGN_E_NONFINITE without an
+ * double or in float pairs; the state, the error norm in double; else
+ * SGN_E_UNSUPPORTED).  The first call of a context allocates 40 planes of
+ * 8-byte scratch (SGN_E_NOMEM if that fails).  An initial state with h <= 0 or
+ * a non-finite h returns SGN_E_NONPOSITIVE_H / SGN_E_NONFINITE without an
  * attempt. */
 SGN_API sgn_status sgn_step_adaptive(sgn_ctx* ctx, void* q_dev, double t0, double t_end, double dt0,
-                                     double rtol, double atol, int max_attempts, double* hist,
+                                     double rtol, double atol, int max_attempts, int pair, double* hist,
                                      double* stats, void* stream);
 
 /* ---- Ragged ensembles ----------------------------------------------------
@@ -335,9 +367,21 @@ SGN_API sgn_status sgn_batch_step(sgn_batch* batch, void* q_dev, int nsteps, voi
 SGN_API sgn_status sgn_batch_mass_energy(sgn_batch* batch, const void* q_dev, double* out, void* stream);
 /* Tile height 8*rows, rows in {1, 2, 4} (default 2). */
 SGN_API sgn_status sgn_batch_set_rows(sgn_batch* batch, int rows);
-/* Time 8 steps of each tile height on a copy of q_dev (allocated and freed
- * here), in three rounds, keep the height with the fastest round and return
- * it in *rows_out.  Synchronizes. */
+/* on = 1: run the four RK4 stages with the persistent kernel (a grid of
+ * resident blocks, resident blocks per SM x SMs, that walks the tile list and
+ * prefetches the next tile's inputs into shared memory with cp.async while it
+ * evaluates the current one); on = 0: one block per tile (default).  The same
+ * arithmetic either way (equal results bit for bit).  The persistent kernel
+ * serves the float compute types (SGN_F32, SGN_F32_F64ACC) and tile heights
+ * 8 and 16 (rows 1, 2); otherwise on = 1 returns SGN_E_UNSUPPORTED. */
+SGN_API sgn_status sgn_batch_set_persistent(sgn_batch* batch, int on);
+/* The current tiling: *rows (1, 2, 4) and *persistent (0, 1). */
+SGN_API sgn_status sgn_batch_tiling(const sgn_batch* batch, int* rows, int* persistent);
+/* Time 8 steps of each tiling -- rows 1, 2, 4 with one block per tile and,
+ * for the float compute types, rows 1, 2 with the persistent kernel -- on a
+ * copy of q_dev (allocated and freed here), in three rounds; keep the tiling
+ * with the fastest round and return its rows in *rows_out (or NULL; see
+ * sgn_batch_tiling for the kernel).  Synchronizes. */
 SGN_API sgn_status sgn_batch_autotune(sgn_batch* batch, const void* q_dev, int* rows_out, void* stream);
 
 /* Synchronize `stream` and report (and clear) the latched device flag. */
@@ -350,6 +394,16 @@ SGN_API const char* sgn_last_error(void);
 
 /* Kernel launches issued by this library since load (all contexts). */
 SGN_API unsigned long long sgn_launch_count(void);
+
+/* The FP64 fused multiply-add rate of the current device, for the roofline of
+ * the FP64 kernels (no counterpart in the paper).  One launch of 8 blocks of
+ * 256 threads per SM; every thread runs 16 independent chains x <- x a + c
+ * (0 < a < 1, so the values stay bounded) for `iters` iterations, a multiple
+ * of 4 in [4, 2^20] (else SGN_E_INVAL).  *fma_count receives the number of
+ * FMAs executed and *seconds the launch's duration, timed with CUDA events on
+ * `stream` (rate = *fma_count / *seconds; a B300 SM completes 2 per clock).
+ * Allocates and frees its small output buffer; synchronizes. */
+SGN_API sgn_status sgn_measure_fp64_fma(int iters, double* fma_count, double* seconds, void* stream);
 
 #ifdef __cplusplus
 }

@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libsgn.so")
 LIB_CHECKED = os.path.join(HERE, "libsgn_checked.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["sgn_api.cu", "sgn_noalloc.cu", "sgn_batch.cu"]
+SOURCES = ["sgn_api.cu", "sgn_noalloc.cu", "sgn_batch.cu", "sgn_rate.cu"]
 
 
 def _sources() -> list[str]:

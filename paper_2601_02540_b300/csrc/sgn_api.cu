@@ -4,6 +4,7 @@
 #include "sgn_kernels.cuh"
 #include "sgn_adjoint.cuh"
 #include "sgn_adaptive.cuh"
+#include "sgn_p5.cuh"
 #include "sgn_rrk.cuh"
 #include "sgn_mms.cuh"
 
@@ -44,7 +45,12 @@ sgn_status cuda_fail(cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, what); \
     } while (0)
 
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+// launches recorded into a CUDA graph are counted when the graph is replayed
+thread_local bool g_capturing = false;
+
+void count_launch() {
+    if (!g_capturing) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
 
 }  // namespace
 
@@ -73,11 +79,17 @@ struct sgn_ctx {
     long long nband = 0;         // 32 x 8 bands of the grid: partials of the diagnostics
     dim3 grid;
     double* adj = nullptr;       // adjoint scratch (FP64): accumulator + two cotangents
-    double* bs = nullptr;        // adaptive integrator scratch (FP64): k1..k4, Y3, q1, q (35 planes)
+    double* bs = nullptr;        // adaptive integrator scratch (8-byte slots, 40 planes)
     double* rrk = nullptr;       // relaxation scratch (FP64): plain RK4 update (5 planes), partials, sums
     double* mon = nullptr;       // per-step monitor sums of sgn_step_diag (NDIAG per step)
     int mon_cap = 0;
     long long rrk_nblk = 0;
+    // sgn_step on small grids: kGraphSteps RK4 steps captured once per (q, dt)
+    // on a private stream and replayed on the caller's stream
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t step_exec = nullptr;
+    const void* exec_q = nullptr;
+    double exec_dt = 0.0;
 };
 
 namespace {
@@ -118,12 +130,16 @@ cudaError_t smem_optin(size_t smem) {
 }
 
 template <typename TC, typename TIN, typename TA, int BC, int MODE>
+cudaError_t stage_attr() {
+    return smem_optin<sgn::k_stage<TC, TIN, TA, BC, MODE>>(sgn::stage_smem_bytes<TC, MODE>(sgn::StageShape<TC>::rows));
+}
+
+template <typename TC, typename TIN, typename TA, int BC, int MODE>
 cudaError_t launch_stage(const sgn_ctx* c, const StageArgs<TC, TIN, TA>& a, cudaStream_t s) {
-    auto kern = sgn::k_stage<TC, TIN, TA, BC, MODE>;
-    const size_t smem = sgn::stage_smem_bytes<TC, MODE>(sgn::StageShape<TC>::rows);
-    const cudaError_t attr_err = smem_optin<sgn::k_stage<TC, TIN, TA, BC, MODE>>(smem);
+    const cudaError_t attr_err = stage_attr<TC, TIN, TA, BC, MODE>();
     if (attr_err != cudaSuccess) return attr_err;
-    kern<<<c->grid, dim3(sgn::TILE_X, sgn::THREADS_Y), smem, s>>>(a);
+    const size_t smem = sgn::stage_smem_bytes<TC, MODE>(sgn::StageShape<TC>::rows);
+    sgn::k_stage<TC, TIN, TA, BC, MODE><<<c->grid, dim3(sgn::TILE_X, sgn::THREADS_Y), smem, s>>>(a);
     count_launch();
     return cudaGetLastError();
 }
@@ -242,11 +258,63 @@ struct StepDiagOp {
     cudaError_t operator()() { return run_steps<TC, TA, BC>(c, static_cast<TA*>(q), dt, n, s, mon); }
 };
 
+// the shared-memory opt-in of the four RK4 stage kernels of a context
+struct AttrOp {
+    sgn_ctx* c;
+    template <typename TC, typename TA, int BC>
+    cudaError_t operator()() {
+        cudaError_t e = stage_attr<TC, TA, TA, BC, sgn::MODE_S1>();
+        if (e == cudaSuccess) e = stage_attr<TC, TC, TA, BC, sgn::MODE_S2>();
+        if (e == cudaSuccess) e = stage_attr<TC, TC, TA, BC, sgn::MODE_S3>();
+        if (e == cudaSuccess) e = stage_attr<TC, TC, TA, BC, sgn::MODE_S4>();
+        return e;
+    }
+};
+
 struct DiagOp {
     sgn_ctx* c; const void* q; cudaStream_t s;
     template <typename TC, typename TA, int BC>
     cudaError_t operator()() { return run_diag<TC, TA, BC>(c, static_cast<const TA*>(q), s); }
 };
+
+// Small grids are launch-bound (four short launches per step): sgn_step
+// replays a CUDA graph of kGraphSteps steps there.  The graph is captured once
+// per (state pointer, dt) on the context's private stream (the same launches
+// as the direct path, so the same results bit for bit) and launched on the
+// caller's stream; a caller that is itself capturing gets the direct launches.
+constexpr int kGraphSteps = 50;
+constexpr long long kGraphMaxCells = 1LL << 21;
+
+sgn_status step_graph(sgn_ctx* c, void* q, double dt) {
+    if (c->step_exec && c->exec_q == q && c->exec_dt == dt) return SGN_OK;
+    if (c->step_exec) {
+        cudaGraphExecDestroy(c->step_exec);
+        c->step_exec = nullptr;
+    }
+    if (!c->cap) CUDA_TRY(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "capture stream");
+    AttrOp fa{c};                // kernel attributes are set outside the capture
+    CUDA_TRY(dispatch(c, fa), "stage kernel attributes");
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    StepOp f{c, q, dt, kGraphSteps, c->cap};
+    g_capturing = true;
+    const cudaError_t el = dispatch(c, f);
+    g_capturing = false;
+    const cudaError_t ec = cudaStreamEndCapture(c->cap, &graph);
+    if (el != cudaSuccess || ec != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(el != cudaSuccess ? el : ec, "capture");
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&c->step_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        c->step_exec = nullptr;
+        return cuda_fail(ei, "instantiate graph");
+    }
+    c->exec_q = q;
+    c->exec_dt = dt;
+    return SGN_OK;
+}
 
 sgn_status read_flag(sgn_ctx* c, cudaStream_t s) {
     CUDA_TRY(cudaMemcpyAsync(c->hflag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, s), "read flag");
@@ -264,6 +332,8 @@ sgn_status read_flag(sgn_ctx* c, cudaStream_t s) {
 
 void free_ctx(sgn_ctx* c) {
     if (!c) return;
+    if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+    if (c->cap) cudaStreamDestroy(c->cap);
     if (c->bT && c->bT != c->b64) cudaFree(c->bT);
     cudaFree(c->b64);
     cudaFree(c->acc);
@@ -458,6 +528,157 @@ sgn_status run_adaptive(sgn_ctx* c, double* q_user, double t0, double t_end, dou
             std::swap(qc, q1);
             std::swap(k1, k4);
             t = last ? t_end : t + h;
+            acc++;
+        } else {
+            rej++;
+        }
+        dt = h * fac;
+        n++;
+    }
+    CUDA_TRY(cudaMemcpyAsync(q_user, qc, bytes5, cudaMemcpyDeviceToDevice, s), "copy q back");
+    CUDA_TRY(cudaStreamSynchronize(s), "synchronize");
+    stats[0] = acc;
+    stats[1] = rej;
+    stats[2] = t;
+    stats[3] = dt;
+    stats[4] = n;
+    return SGN_OK;
+}
+
+// ---- the five-stage third-order FSAL pair (Sec. 6) -------------------------
+// Butcher matrix of the two-register form (a_ij = b_j for j < i-1): the
+// sub-diagonal a21, a32, a43, a54, the weights b and the embedded weights bhat
+// over k1..k5 and k6 = f(q_{n+1}).  Constructed for this library: stability
+// polynomial 1 + z + z^2/2 + z^3/6 + 0.0324 z^4 + 0.006 z^5 (imaginary-axis
+// stability up to |z| = 3.8798), third order, embedded second order.
+constexpr double P5_A21 = 0.3464, P5_A32 = 0.5544, P5_A43 = 0.3078, P5_A54 = 0.25084211224332113157;
+constexpr double P5_B[5] = {-0.077114705798502101362, 0.51296293729322573879, -0.53636230691175187515,
+                            0.69586264419699749322, 0.40465143122003074449};
+constexpr double P5_BHAT[6] = {0.14576960111557976478, 0.13123039888442023522, 0.103, 0.1816, 0.1978, 0.2406};
+// Step-size control with the limiter rho(x) = 1 + atan(x - 1) and
+// eps = 0.9 / max(err, 1e-10): an accepted attempt sets dt_next = dt rho(x)
+// with x = eps^(0.7/3) eps_prev^(-0.4/3) (Gustafsson's stabilized PI control;
+// eps_prev of the previous accepted attempt, 1 before the first), a rejected
+// one dt_next = dt rho(eps^(1/3)).
+constexpr double P5_PI_B1 = 0.7, P5_PI_B2 = -0.4, P5_PI_K = 3.0, P5_ERR_FLOOR = 1e-10, P5_SAFETY = 0.9;
+
+template <typename TC, int BC, int MODE>
+cudaError_t launch_p5(const sgn_ctx* c, const sgn::P5Args& a, cudaStream_t s) {
+    auto kern = sgn::k_p5_stage<TC, BC, MODE>;
+    const size_t smem = sgn::stage_smem_bytes<TC, sgn::MODE_RHS>(sgn::StageShape<TC>::rows);
+    const cudaError_t attr_err = smem_optin<sgn::k_p5_stage<TC, BC, MODE>>(smem);
+    if (attr_err != cudaSuccess) return attr_err;
+    kern<<<c->grid, dim3(sgn::TILE_X, sgn::THREADS_Y), smem, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename TC, int BC>
+sgn_status run_adaptive_p5(sgn_ctx* c, double* q_user, double t0, double t_end, double dt0, double rtol,
+                           double atol, int max_attempts, double* hist, double* stats, cudaStream_t s) {
+    const long long P5 = 5 * c->G.plane;
+    const size_t bytes5 = (size_t)P5 * sizeof(double);
+    static_assert(sizeof(TC) == sizeof(double), "the slots below hold 8-byte values");
+    TC* k1 = reinterpret_cast<TC*>(c->bs);
+    TC* k6 = reinterpret_cast<TC*>(c->bs + P5);
+    TC* Ya = reinterpret_cast<TC*>(c->bs + 2 * P5);
+    TC* Yb = reinterpret_cast<TC*>(c->bs + 3 * P5);
+    TC* U = reinterpret_cast<TC*>(c->bs + 4 * P5);
+    TC* E = reinterpret_cast<TC*>(c->bs + 5 * P5);
+    double* q1 = c->bs + 6 * P5;
+    double* qc = c->bs + 7 * P5;
+    CUDA_TRY(cudaMemcpyAsync(qc, q_user, bytes5, cudaMemcpyDeviceToDevice, s), "copy q");
+    {
+        // k1 = f(q), stored in the compute type
+        StageArgs<TC, double, TC> r = base_args<TC, double, TC>(c);
+        r.X = qc;
+        r.out = k1;
+        CUDA_TRY((launch_stage<TC, double, TC, BC, sgn::MODE_RHS>(c, r, s)), "k1");
+    }
+    sgn_status st = read_flag(c, s);
+    if (st != SGN_OK) return st;
+
+    sgn::P5Args a;
+    std::memset(&a, 0, sizeof(a));
+    a.b = c->bT;
+    a.flag = c->flag;
+    a.G = c->G;
+    a.rtol = rtol;
+    a.atol = atol;
+    a.partials = c->partials;
+    a.U = U;
+    a.E = E;
+    a.q1 = q1;
+    double t = t0, dt = dt0, eps_prev = 1.0;
+    int acc = 0, rej = 0, n = 0;
+    while (t < t_end && n < max_attempts) {
+        const bool last = dt >= t_end - t;
+        const double h = last ? t_end - t : dt;
+        a.q = qc;
+        a.k1 = k1;
+        // stage 2: Y2 = q + h a21 k1; writes Y3, U3, E3
+        a.c_in = h * P5_A21;
+        a.c_u1 = h * P5_B[0];
+        a.c_e1 = P5_B[0] - P5_BHAT[0];
+        a.c_y = h * P5_A32;
+        a.c_u = h * P5_B[1];
+        a.c_e = P5_B[1] - P5_BHAT[1];
+        a.Yout = Ya;
+        CUDA_TRY((launch_p5<TC, BC, sgn::P5_S2>(c, a, s)), "pair stage 2");
+        // stage 3: Y3 -> Y4, U4, E4
+        a.Yin = Ya;
+        a.Yout = Yb;
+        a.c_y = h * P5_A43;
+        a.c_u = h * P5_B[2];
+        a.c_e = P5_B[2] - P5_BHAT[2];
+        CUDA_TRY((launch_p5<TC, BC, sgn::P5_MID>(c, a, s)), "pair stage 3");
+        // stage 4: Y4 -> Y5, U5, E5
+        a.Yin = Yb;
+        a.Yout = Ya;
+        a.c_y = h * P5_A54;
+        a.c_u = h * P5_B[3];
+        a.c_e = P5_B[3] - P5_BHAT[3];
+        CUDA_TRY((launch_p5<TC, BC, sgn::P5_MID>(c, a, s)), "pair stage 4");
+        // stage 5: Y5 -> q1 = U5 + h b5 k5, E6
+        a.Yin = Ya;
+        a.c_u = h * P5_B[4];
+        a.c_e = P5_B[4] - P5_BHAT[4];
+        CUDA_TRY((launch_p5<TC, BC, sgn::P5_S5>(c, a, s)), "pair stage 5");
+        // k6 = f(q1) and the error partial sums
+        a.kout = k6;
+        a.c_e6 = 0.0 - P5_BHAT[5];
+        a.dt = h;
+        CUDA_TRY((launch_p5<TC, BC, sgn::P5_FSAL>(c, a, s)), "pair FSAL stage");
+        sgn::k_reduce_partials<<<1, 256, 0, s>>>(c->partials, c->nblk, c->dout);
+        count_launch();
+        CUDA_TRY(cudaGetLastError(), "error reduction");
+        CUDA_TRY(cudaMemcpyAsync(c->hout, c->dout, sizeof(double), cudaMemcpyDeviceToHost, s), "copy error");
+        CUDA_TRY(cudaMemcpyAsync(c->hflag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, s), "copy flag");
+        CUDA_TRY(cudaStreamSynchronize(s), "synchronize");
+        double err;
+        if (*c->hflag) {
+            // a trial stage left the admissible states: reject as an infinite error
+            CUDA_TRY(cudaMemsetAsync(c->flag, 0, sizeof(int), s), "clear flag");
+            err = INFINITY;
+        } else {
+            err = std::sqrt(c->hout[0] / (double)P5);
+        }
+        const bool ok = err <= 1.0;
+        const double eps = P5_SAFETY / std::fmax(err, P5_ERR_FLOOR);
+        const double x = ok ? std::pow(eps, P5_PI_B1 / P5_PI_K) * std::pow(eps_prev, P5_PI_B2 / P5_PI_K)
+                            : std::pow(eps, 1.0 / P5_PI_K);
+        const double fac = 1.0 + std::atan(x - 1.0);
+        if (hist) {
+            hist[3 * n] = h;
+            hist[3 * n + 1] = err;
+            hist[3 * n + 2] = ok ? 1.0 : 0.0;
+        }
+        if (ok) {
+            std::swap(qc, q1);
+            std::swap(k1, k6);
+            a.q1 = q1;
+            t = last ? t_end : t + h;
+            eps_prev = eps;
             acc++;
         } else {
             rej++;
@@ -747,7 +968,22 @@ sgn_status sgn_step(sgn_ctx* c, void* q_dev, double dt, int nsteps, void* stream
     if (st != SGN_OK) return st;
     if (!finite_pos(dt)) return fail(SGN_E_INVAL, "dt must be finite and > 0");
     if (nsteps < 0) return fail(SGN_E_INVAL, "nsteps must be >= 0");
-    StepOp f{c, q_dev, dt, nsteps, static_cast<cudaStream_t>(stream)};
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int left = nsteps;
+    if (left >= kGraphSteps && c->G.plane <= kGraphMaxCells) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        CUDA_TRY(cudaStreamIsCapturing(s, &cs), "capture status");
+        if (cs == cudaStreamCaptureStatusNone) {
+            st = step_graph(c, q_dev, dt);
+            if (st != SGN_OK) return st;
+            while (left >= kGraphSteps) {
+                CUDA_TRY(cudaGraphLaunch(c->step_exec, s), "graph launch");
+                g_launches.fetch_add(4ull * kGraphSteps, std::memory_order_relaxed);
+                left -= kGraphSteps;
+            }
+        }
+    }
+    StepOp f{c, q_dev, dt, left, s};
     cudaError_t e = dispatch(c, f);
     if (e != cudaSuccess) return cuda_fail(e, "sgn_step");
     return SGN_OK;
@@ -828,6 +1064,7 @@ sgn_status sgn_rhs_vjp(sgn_ctx* c, const void* q_dev, const void* abar_dev, void
     a.sigma = 1.0;
     a.qbar = static_cast<double*>(qbar_dev);
     a.bbar = static_cast<double*>(bbar_dev);
+    a.flag = c->flag;
     a.G = c->G;
     sgn::fill_adj_constants(a);
     cudaError_t e = adjoint<sgn::ADJ_MODE_RHS>(c, a, static_cast<cudaStream_t>(stream));
@@ -887,6 +1124,7 @@ sgn_status sgn_step_vjp(sgn_ctx* c, const void* stash_dev, void* qbar_dev, void*
     a.scratch = c->adj + 15 * c->G.plane;
     a.bbar = static_cast<double*>(bbar_dev);
     a.qprime = qbar;
+    a.flag = c->flag;
     a.G = c->G;
     sgn::fill_adj_constants(a);
     cudaError_t e;
@@ -1007,7 +1245,8 @@ sgn_status sgn_step_relaxed(sgn_ctx* c, void* q_dev, double dt, int nsteps, doub
 }
 
 sgn_status sgn_step_adaptive(sgn_ctx* c, void* q_dev, double t0, double t_end, double dt0, double rtol,
-                             double atol, int max_attempts, double* hist, double* stats, void* stream) {
+                             double atol, int max_attempts, int pair, double* hist, double* stats,
+                             void* stream) {
     if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
     if (c->p.prec != SGN_F64 && c->p.prec != SGN_DF64)
         return fail(SGN_E_UNSUPPORTED, "sgn_step_adaptive needs an SGN_F64 or SGN_DF64 context");
@@ -1020,8 +1259,9 @@ sgn_status sgn_step_adaptive(sgn_ctx* c, void* q_dev, double t0, double t_end, d
     if (!(finite_pos(rtol) || rtol == 0.0) || !(finite_pos(atol) || atol == 0.0) || rtol + atol <= 0.0)
         return fail(SGN_E_INVAL, "rtol, atol must be finite, >= 0 and not both 0");
     if (max_attempts < 0) return fail(SGN_E_INVAL, "max_attempts must be >= 0");
+    if (pair != SGN_PAIR_P5S3 && pair != SGN_PAIR_BS3) return fail(SGN_E_INVAL, "pair = %d", pair);
     if (!c->bs) {
-        const size_t bytes = (size_t)35 * (size_t)c->G.plane * sizeof(double);
+        const size_t bytes = (size_t)40 * (size_t)c->G.plane * sizeof(double);
         if (cudaMalloc(&c->bs, bytes) != cudaSuccess) {
             cudaGetLastError();
             c->bs = nullptr;
@@ -1031,6 +1271,17 @@ sgn_status sgn_step_adaptive(sgn_ctx* c, void* q_dev, double t0, double t_end, d
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     double* q = static_cast<double*>(q_dev);
     const bool refl = c->p.bc == SGN_BC_REFLECTING;
+    if (pair == SGN_PAIR_P5S3) {
+        if (c->p.prec == SGN_DF64)
+            return refl ? run_adaptive_p5<sgn::df64, sgn::BC_REFLECTING>(c, q, t0, t_end, dt0, rtol, atol,
+                                                                        max_attempts, hist, stats, s)
+                        : run_adaptive_p5<sgn::df64, sgn::BC_PERIODIC>(c, q, t0, t_end, dt0, rtol, atol,
+                                                                      max_attempts, hist, stats, s);
+        return refl ? run_adaptive_p5<double, sgn::BC_REFLECTING>(c, q, t0, t_end, dt0, rtol, atol, max_attempts,
+                                                                  hist, stats, s)
+                    : run_adaptive_p5<double, sgn::BC_PERIODIC>(c, q, t0, t_end, dt0, rtol, atol, max_attempts,
+                                                                hist, stats, s);
+    }
     if (c->p.prec == SGN_DF64)
         return refl ? run_adaptive<sgn::df64, sgn::BC_REFLECTING>(c, q, t0, t_end, dt0, rtol, atol, max_attempts,
                                                                  hist, stats, s)

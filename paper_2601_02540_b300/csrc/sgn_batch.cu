@@ -3,7 +3,9 @@
 // graphs, with the tile height chosen by timing (sgn_batch_autotune).
 #include "sgn.h"
 #include "sgn_batch.cuh"
+#include "sgn_persist.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -42,6 +44,11 @@ struct sgn_batch {
     sgn::InstDesc* desc = nullptr;     // device
     int4* tiles[3] = {nullptr, nullptr, nullptr};   // tile lists for rows = 1, 2, 4
     long long ntiles[3] = {0, 0, 0};
+    // the persistent kernel (float compute types): tile records for rows = 1, 2
+    // and its grid per (rows, stage), resident blocks per SM x SMs
+    sgn::PTile* ptiles[2] = {nullptr, nullptr};
+    int pgrid[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    int persist = 0;                   // 1: RK4 stages by the persistent kernel
     double* b64 = nullptr;
     void* bT = nullptr;
     void* acc = nullptr;
@@ -54,6 +61,7 @@ struct sgn_batch {
     cudaGraphExec_t exec = nullptr;
     const void* exec_q = nullptr;
     int exec_rows = 0;
+    int exec_persist = 0;
     bool capturing = false;            // launches recorded into a graph are counted on replay
 };
 
@@ -71,6 +79,48 @@ cudaError_t blaunch(const sgn_batch* B, const sgn::BatchArgs<TC, TIN, TA>& a, cu
         <<<(unsigned)B->ntiles[ri], dim3(sgn::TILE_X, sgn::THREADS_Y), smem, s>>>(b);
     if (!B->capturing) sgn_count_launches(1);
     return cudaGetLastError();
+}
+
+// the persistent kernel: one grid of resident blocks walks the tile list
+template <typename TC, typename TIN, typename TA, int MODE, int ROWS>
+cudaError_t plaunch(const sgn_batch* B, const sgn::PersistArgs<TC, TIN, TA>& a, cudaStream_t s) {
+    const int ri = ROWS == 1 ? 0 : 1;
+    sgn::PersistArgs<TC, TIN, TA> b = a;
+    b.tiles = B->ptiles[ri];
+    b.ntiles = B->ntiles[ri];
+    const int stage = MODE - sgn::MODE_S1;
+    sgn::k_batch_persist<TC, TIN, TA, MODE, ROWS>
+        <<<(unsigned)B->pgrid[ri][stage], dim3(sgn::TILE_X, sgn::THREADS_Y), sgn::PersistLayout<TC, TIN, ROWS>::bytes,
+           s>>>(b);
+    if (!B->capturing) sgn_count_launches(1);
+    return cudaGetLastError();
+}
+
+// shared-memory opt-in and grid (resident blocks per SM x SMs, at most one
+// block per tile) of one persistent kernel
+template <typename TC, typename TIN, typename TA, int MODE, int ROWS>
+cudaError_t set_persist(sgn_batch* B, int sms) {
+    auto kern = sgn::k_batch_persist<TC, TIN, TA, MODE, ROWS>;
+    const size_t smem = sgn::PersistLayout<TC, TIN, ROWS>::bytes;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, sgn::BLOCK_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int ri = ROWS == 1 ? 0 : 1;
+    const long long g = std::min<long long>((long long)per_sm * sms, B->ntiles[ri]);
+    B->pgrid[ri][MODE - sgn::MODE_S1] = (int)std::max<long long>(g, 1);
+    return cudaSuccess;
+}
+
+template <typename TC, typename TA, int ROWS>
+cudaError_t set_persist_rows(sgn_batch* B, int sms) {
+    cudaError_t e = set_persist<TC, TA, TA, sgn::MODE_S1, ROWS>(B, sms);
+    if (e == cudaSuccess) e = set_persist<TC, TC, TA, sgn::MODE_S2, ROWS>(B, sms);
+    if (e == cudaSuccess) e = set_persist<TC, TC, TA, sgn::MODE_S3, ROWS>(B, sms);
+    if (e == cudaSuccess) e = set_persist<TC, TC, TA, sgn::MODE_S4, ROWS>(B, sms);
+    return e;
 }
 
 template <typename TC, typename TIN, typename TA, int MODE, int ROWS>
@@ -117,6 +167,31 @@ cudaError_t bsteps(sgn_batch* B, TA* q, int nsteps, cudaStream_t s) {
     a3.X = static_cast<TC*>(B->Qb); a3.Qout = static_cast<TC*>(B->Qa); a3.stage = 2;
     sgn::BatchArgs<TC, TC, TA> a4 = a2;
     a4.X = static_cast<TC*>(B->Qa); a4.Qout = nullptr; a4.qn = nullptr; a4.out = q; a4.stage = 3;
+    if constexpr (sgn::TileLayout<TC>::factored && ROWS <= 2) {
+        if (B->persist) {
+            // the same four stages by the persistent kernel
+            sgn::PersistArgs<TC, TA, TA> p1;
+            std::memset(&p1, 0, sizeof(p1));
+            p1.desc = B->desc; p1.b = a1.b; p1.flag = B->flag;
+            p1.X = q; p1.qn = q; p1.acc = a1.acc; p1.Qout = a1.Qout; p1.stage = 0;
+            sgn::PersistArgs<TC, TC, TA> p2;
+            std::memset(&p2, 0, sizeof(p2));
+            p2.desc = B->desc; p2.b = a1.b; p2.flag = B->flag;
+            p2.X = a2.X; p2.qn = q; p2.acc = a1.acc; p2.Qout = a2.Qout; p2.stage = 1;
+            sgn::PersistArgs<TC, TC, TA> p3 = p2;
+            p3.X = a3.X; p3.Qout = a3.Qout; p3.stage = 2;
+            sgn::PersistArgs<TC, TC, TA> p4 = p2;
+            p4.X = a4.X; p4.Qout = nullptr; p4.qn = nullptr; p4.out = q; p4.stage = 3;
+            for (int n = 0; n < nsteps; n++) {
+                cudaError_t e;
+                if ((e = plaunch<TC, TA, TA, sgn::MODE_S1, ROWS>(B, p1, s)) != cudaSuccess) return e;
+                if ((e = plaunch<TC, TC, TA, sgn::MODE_S2, ROWS>(B, p2, s)) != cudaSuccess) return e;
+                if ((e = plaunch<TC, TC, TA, sgn::MODE_S3, ROWS>(B, p3, s)) != cudaSuccess) return e;
+                if ((e = plaunch<TC, TC, TA, sgn::MODE_S4, ROWS>(B, p4, s)) != cudaSuccess) return e;
+            }
+            return cudaSuccess;
+        }
+    }
     for (int n = 0; n < nsteps; n++) {
         cudaError_t e;
         if ((e = blaunch<TC, TA, TA, sgn::MODE_S1, ROWS>(B, a1, s)) != cudaSuccess) return e;
@@ -174,6 +249,7 @@ void free_batch(sgn_batch* B) {
     if (B->cap) cudaStreamDestroy(B->cap);
     cudaFree(B->desc);
     for (auto* t : B->tiles) cudaFree(t);
+    for (auto* t : B->ptiles) cudaFree(t);
     if (B->bT && B->bT != B->b64) cudaFree(B->bT);
     cudaFree(B->b64);
     cudaFree(B->acc);
@@ -197,7 +273,7 @@ bool devptr(const void* p) {
 
 // (re)build the graph of kGraphSteps RK4 steps for this state pointer and tiling
 sgn_status ensure_graph(sgn_batch* B, void* q) {
-    if (B->exec && B->exec_q == q && B->exec_rows == B->rows) return SGN_OK;
+    if (B->exec && B->exec_q == q && B->exec_rows == B->rows && B->exec_persist == B->persist) return SGN_OK;
     if (B->exec) {
         cudaGraphExecDestroy(B->exec);
         B->exec = nullptr;
@@ -221,6 +297,7 @@ sgn_status ensure_graph(sgn_batch* B, void* q) {
     }
     B->exec_q = q;
     B->exec_rows = B->rows;
+    B->exec_persist = B->persist;
     return SGN_OK;
 }
 
@@ -286,6 +363,8 @@ sgn_status sgn_batch_create(const sgn_instance* inst, int ninst, int prec, const
     const size_t n = (size_t)B->cells;
     bool ok = cudaMalloc(&B->desc, sizeof(sgn::InstDesc) * ninst) == cudaSuccess;
     for (int ri = 0; ri < 3 && ok; ri++) ok = cudaMalloc(&B->tiles[ri], sizeof(int4) * tl[ri].size()) == cudaSuccess;
+    for (int ri = 0; ri < 2 && ok; ri++)
+        ok = cudaMalloc(&B->ptiles[ri], sizeof(sgn::PTile) * tl[ri].size()) == cudaSuccess;
     ok = ok && cudaMalloc(&B->b64, n * sizeof(double)) == cudaSuccess;
     if (ok && prec != SGN_F64) ok = cudaMalloc(&B->bT, n * sizeof(float)) == cudaSuccess;
     if (ok && prec == SGN_F64) B->bT = B->b64;
@@ -304,6 +383,20 @@ sgn_status sgn_batch_create(const sgn_instance* inst, int ninst, int prec, const
     cudaError_t e = cudaSuccess;
     for (int ri = 0; ri < 3 && e == cudaSuccess; ri++)
         e = cudaMemcpy(B->tiles[ri], tl[ri].data(), sizeof(int4) * tl[ri].size(), cudaMemcpyHostToDevice);
+    for (int ri = 0; ri < 2 && e == cudaSuccess; ri++) {
+        std::vector<sgn::PTile> pt(tl[ri].size());
+        for (size_t k = 0; k < pt.size(); k++) {
+            const sgn::InstDesc& d = B->hdesc[tl[ri][k].x];
+            pt[k].off = d.off;
+            pt[k].inst = tl[ri][k].x;
+            pt[k].i0 = tl[ri][k].y;
+            pt[k].j0 = tl[ri][k].z;
+            pt[k].nx = d.G.nx;
+            pt[k].ny = d.G.ny;
+            pt[k].bc = d.bc;
+        }
+        e = cudaMemcpy(B->ptiles[ri], pt.data(), sizeof(sgn::PTile) * pt.size(), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaMemset(B->flag, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(B->b64, b_dev, n * sizeof(double), cudaMemcpyDeviceToDevice);
     if (e == cudaSuccess && prec != SGN_F64) {
@@ -317,6 +410,15 @@ sgn_status sgn_batch_create(const sgn_instance* inst, int ninst, int prec, const
         case SGN_F32: e = set_attrs<float, float>(); break;
         default: e = set_attrs<float, double>(); break;
         }
+    }
+    if (e == cudaSuccess && prec != SGN_F64) {
+        int dev = 0, sms = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = prec == SGN_F32 ? set_persist_rows<float, float, 1>(B, sms) : set_persist_rows<float, double, 1>(B, sms);
+        if (e == cudaSuccess)
+            e = prec == SGN_F32 ? set_persist_rows<float, float, 2>(B, sms) : set_persist_rows<float, double, 2>(B, sms);
     }
     if (e == cudaSuccess) {
         // descriptors with the band ranges: the rows = 1 tiles are the 32 x 8
@@ -355,7 +457,25 @@ long long sgn_batch_cells(const sgn_batch* B) { return B ? B->cells : -1; }
 sgn_status sgn_batch_set_rows(sgn_batch* B, int rows) {
     if (!B) return bfail(SGN_E_INVAL, "batch is NULL");
     if (rows != 1 && rows != 2 && rows != 4) return bfail(SGN_E_INVAL, "rows must be 1, 2 or 4");
+    if (rows == 4 && B->persist)
+        return bfail(SGN_E_UNSUPPORTED, "the persistent kernel serves rows 1 and 2");
     B->rows = rows;
+    return SGN_OK;
+}
+
+sgn_status sgn_batch_set_persistent(sgn_batch* B, int on) {
+    if (!B) return bfail(SGN_E_INVAL, "batch is NULL");
+    if (on != 0 && on != 1) return bfail(SGN_E_INVAL, "on must be 0 or 1");
+    if (on && (B->prec == SGN_F64 || B->rows == 4))
+        return bfail(SGN_E_UNSUPPORTED, "the persistent kernel serves float compute types with rows 1 or 2");
+    B->persist = on;
+    return SGN_OK;
+}
+
+sgn_status sgn_batch_tiling(const sgn_batch* B, int* rows, int* persistent) {
+    if (!B || !rows || !persistent) return bfail(SGN_E_INVAL, "batch, rows and persistent must not be NULL");
+    *rows = B->rows;
+    *persistent = B->persist;
     return SGN_OK;
 }
 
@@ -425,18 +545,22 @@ sgn_status sgn_batch_autotune(sgn_batch* B, const void* q_dev, int* rows_out, vo
         cudaFree(work);
         return bfail(SGN_E_NOMEM, "autotune events");
     }
-    // three rounds over the candidates, each timing 8 steps after 2 warm-up
-    // steps; a candidate's time is its fastest round (robust to a slow round,
-    // e.g. while the clocks ramp up)
-    const int cand[3] = {1, 2, 4};
-    float tmin[3] = {1e30f, 1e30f, 1e30f};
+    // three rounds over the candidate tilings, each timing 8 steps after 2
+    // warm-up steps; a candidate's time is its fastest round (robust to a slow
+    // round, e.g. while the clocks ramp up)
+    const int cand_rows[5] = {1, 2, 4, 1, 2};
+    const int cand_persist[5] = {0, 0, 0, 1, 1};
+    const int ncand = B->prec == SGN_F64 ? 3 : 5;
+    float tmin[5] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
+    const int keep_persist = B->persist;
     cudaError_t e = cudaSuccess;
     for (int round = 0; round < 3 && e == cudaSuccess; round++) {
-        for (int k = 0; k < 3 && e == cudaSuccess; k++) {
+        for (int k = 0; k < ncand && e == cudaSuccess; k++) {
+            B->persist = cand_persist[k];
             e = cudaMemcpyAsync(work, q_dev, bytes, cudaMemcpyDeviceToDevice, s);
-            if (e == cudaSuccess) e = bsteps_any(B, work, 2, cand[k], s);   // warm-up
+            if (e == cudaSuccess) e = bsteps_any(B, work, 2, cand_rows[k], s);   // warm-up
             if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-            if (e == cudaSuccess) e = bsteps_any(B, work, 8, cand[k], s);
+            if (e == cudaSuccess) e = bsteps_any(B, work, 8, cand_rows[k], s);
             if (e == cudaSuccess) e = cudaEventRecord(e1, s);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.0f;
@@ -444,19 +568,23 @@ sgn_status sgn_batch_autotune(sgn_batch* B, const void* q_dev, int* rows_out, vo
             if (e == cudaSuccess && ms < tmin[k]) tmin[k] = ms;
         }
     }
+    B->persist = keep_persist;
     float best = 1e30f;
-    int best_rows = B->rows;
-    for (int k = 0; k < 3; k++)
+    int best_k = -1;
+    for (int k = 0; k < ncand; k++)
         if (tmin[k] < best) {
             best = tmin[k];
-            best_rows = cand[k];
+            best_k = k;
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(work);
     if (e != cudaSuccess) return bcuda(e, "sgn_batch_autotune");
-    B->rows = best_rows;
-    if (rows_out) *rows_out = best_rows;
+    if (best_k >= 0) {
+        B->rows = cand_rows[best_k];
+        B->persist = cand_persist[best_k];
+    }
+    if (rows_out) *rows_out = B->rows;
     return SGN_OK;
 }
 

@@ -42,7 +42,8 @@ _SIGNATURES = {
                                        ctypes.c_double, ctypes.c_double, _V]),
     "sgn_step_relaxed": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_int, _V, _V, _V]),
     "sgn_step_adaptive": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, _V, _V, _V]),
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                         _V, _V, _V]),
     "sgn_mass_energy": (ctypes.c_int, [_V, _V, _V, _V]),
     "sgn_step_diag": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_int, _V, _V]),
     "sgn_check": (ctypes.c_int, [_V, _V]),
@@ -58,9 +59,12 @@ _SIGNATURES = {
     "sgn_batch_mass_energy": (ctypes.c_int, [_V, _V, _V, _V]),
     "sgn_batch_set_rows": (ctypes.c_int, [_V, ctypes.c_int]),
     "sgn_batch_autotune": (ctypes.c_int, [_V, _V, _V, _V]),
+    "sgn_batch_set_persistent": (ctypes.c_int, [_V, ctypes.c_int]),
+    "sgn_batch_tiling": (ctypes.c_int, [_V, _V, _V]),
     "sgn_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "sgn_last_error": (ctypes.c_char_p, []),
     "sgn_launch_count": (ctypes.c_ulonglong, []),
+    "sgn_measure_fp64_fma": (ctypes.c_int, [ctypes.c_int, _V, _V, _V]),
 }
 
 
@@ -185,15 +189,21 @@ def sgn_step_relaxed(ctx, q: torch.Tensor, dt: float, nsteps: int, stream=None):
     return list(gam[:int(nsteps)]), t.value
 
 
+PAIRS = {"p5s3": 0, "bs3": 1}
+
+
 def sgn_step_adaptive(ctx, q: torch.Tensor, t0: float, t_end: float, dt0: float, rtol: float,
-                      atol: float, max_attempts: int, want_history: bool = True, stream=None):
-    """Adaptive integration (FP64 contexts); returns (stats, history) with
-    stats = {accepted, rejected, t, dt_next, attempts} and history an
-    (attempts, 3) list of (dt, err, accepted) or None."""
+                      atol: float, max_attempts: int, want_history: bool = True, stream=None,
+                      pair: str = "p5s3"):
+    """Adaptive integration (FP64 / df64 contexts) with the pair `pair`
+    ("p5s3": the five-stage third-order FSAL pair, "bs3": Bogacki-Shampine);
+    returns (stats, history) with stats = {accepted, rejected, t, dt_next,
+    attempts} and history an (attempts, 3) list of (dt, err, accepted) or None."""
     st = (ctypes.c_double * 5)()
     hist = (ctypes.c_double * (3 * max(int(max_attempts), 1)))() if want_history else None
     _ok(lib().sgn_step_adaptive(ctx, _dptr(q, torch.float64, "q"), float(t0), float(t_end), float(dt0),
-                                float(rtol), float(atol), int(max_attempts), hist, st, _stream(stream)),
+                                float(rtol), float(atol), int(max_attempts), PAIRS[pair], hist, st,
+                                _stream(stream)),
         "sgn_step_adaptive")
     n = int(st[4])
     stats = dict(accepted=int(st[0]), rejected=int(st[1]), t=float(st[2]), dt_next=float(st[3]), attempts=n)
@@ -252,6 +262,14 @@ def sgn_check(ctx, stream=None) -> None:
 
 def sgn_launch_count() -> int:
     return int(lib().sgn_launch_count())
+
+
+def sgn_measure_fp64_fma(iters: int, stream=None) -> tuple[float, float]:
+    """(FMAs executed, seconds) of one launch of the FP64 FMA-chain kernel."""
+    n, sec = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _ok(lib().sgn_measure_fp64_fma(int(iters), ctypes.byref(n), ctypes.byref(sec), _stream(stream)),
+        "sgn_measure_fp64_fma")
+    return n.value, sec.value
 
 
 # ----------------------------------------------------------------------------- wrapper
@@ -321,10 +339,12 @@ class Solver:
         return sgn_step_relaxed(self.ctx, q, dt, nsteps)
 
     def step_adaptive(self, q: torch.Tensor, t0: float, t_end: float, dt0: float, rtol: float = 1e-6,
-                      atol: float = 1e-6, max_attempts: int = 100000, want_history: bool = True):
+                      atol: float = 1e-6, max_attempts: int = 100000, want_history: bool = True,
+                      pair: str = "p5s3"):
         """Adaptive third-order FSAL integration from t0 to t_end in place
-        (FP64 contexts); see sgn_step_adaptive."""
-        return sgn_step_adaptive(self.ctx, q, t0, t_end, dt0, rtol, atol, max_attempts, want_history)
+        (FP64 / df64 contexts); see sgn_step_adaptive."""
+        return sgn_step_adaptive(self.ctx, q, t0, t_end, dt0, rtol, atol, max_attempts, want_history,
+                                 pair=pair)
 
     def step_diag(self, q: torch.Tensor, dt: float, nsteps: int) -> list:
         """nsteps RK4 steps; (mass, energy, energy_shifted) after each."""
@@ -422,6 +442,14 @@ class BatchSolver:
 
     def set_rows(self, rows: int):
         _ok(lib().sgn_batch_set_rows(self.handle, int(rows)), "sgn_batch_set_rows")
+
+    def set_persistent(self, on: bool):
+        _ok(lib().sgn_batch_set_persistent(self.handle, int(bool(on))), "sgn_batch_set_persistent")
+
+    def tiling(self) -> dict:
+        rows, pers = ctypes.c_int(), ctypes.c_int()
+        _ok(lib().sgn_batch_tiling(self.handle, ctypes.byref(rows), ctypes.byref(pers)), "sgn_batch_tiling")
+        return {"rows": rows.value, "persistent": bool(pers.value)}
 
     def autotune(self, q) -> int:
         r = ctypes.c_int()

@@ -127,3 +127,66 @@ def test_batch_workload_recipe_small():
         assert diag[k, 0] == d["mass"] and diag[k, 1] == d["energy"]
         s.close()
     bs.close()
+
+
+# ------------------------------------------------------------------ the persistent kernel
+@pytest.mark.parametrize("prec", ["f32", "f32_f64acc"])
+@pytest.mark.parametrize("rows", [1, 2])
+def test_persistent_kernel_equals_per_tile_kernel_bitwise(prec, rows):
+    """The persistent kernel (resident blocks walking the tile list, next tile
+    prefetched with cp.async) runs the per-tile kernel's arithmetic: equal
+    states bit for bit, through a graph replay and direct steps, on ragged
+    grids of both boundary kinds."""
+    probs = _ensemble()
+    bs = sgn.BatchSolver(probs, prec=prec)
+    bs.set_rows(rows)
+    q1 = bs.pack([p.q0 for p in probs])
+    bs.step(q1, 30)
+    bs.set_persistent(True)
+    assert bs.tiling() == {"rows": rows, "persistent": True}
+    q2 = bs.pack([p.q0 for p in probs])
+    bs.step(q2, 30)
+    assert torch.equal(q1, q2)
+    bs.close()
+
+
+def test_persistent_kernel_workload_recipe_equals_single_grid():
+    probs = inputs.workload5(ninst=8, nsteps=10, sizes=(128, 192))
+    bs = sgn.BatchSolver(probs, prec="f32")
+    bs.set_persistent(True)
+    q = bs.pack([p.q0 for p in probs])
+    bs.init_aux(q)
+    bs.step(q, 10)
+    for k, p in enumerate(probs):
+        s = sgn.Solver.from_problem(p, prec="f32")
+        qs = s.state(p.q0)
+        s.init_aux(qs)
+        s.step(qs, p.dt, 10)
+        assert torch.equal(qs, bs.unpack(q)[k]), p.name
+        s.close()
+    bs.close()
+
+
+def test_persistent_kernel_unsupported_cases_and_autotune():
+    probs = _ensemble()
+    bs = sgn.BatchSolver(probs, prec="f64")
+    with pytest.raises(sgn.SgnError) as ei:
+        bs.set_persistent(True)
+    assert ei.value.status == 7
+    bs.close()
+    bs = sgn.BatchSolver(probs, prec="f32")
+    bs.set_rows(4)
+    with pytest.raises(sgn.SgnError) as ei:
+        bs.set_persistent(True)
+    assert ei.value.status == 7
+    bs.set_rows(2)
+    bs.set_persistent(True)
+    with pytest.raises(sgn.SgnError) as ei:
+        bs.set_rows(4)
+    assert ei.value.status == 7
+    q = bs.pack([p.q0 for p in probs])
+    rows = bs.autotune(q)
+    t = bs.tiling()
+    assert t["rows"] == rows and (rows in (1, 2) or not t["persistent"])
+    assert torch.equal(q, bs.pack([p.q0 for p in probs]))   # autotune works on a copy
+    bs.close()
