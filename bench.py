@@ -227,36 +227,33 @@ def _roofline(prec: str, cells: int, ms_total: float, launches_per_step: int, st
     launch_ms = ms_total / (launches_per_step * steps)
     traffic = _ncu_traffic(prec)
     if prec == "f64":
-        # FP64 is ALU-bound on B300: the peak is the measured FMA rate of the
-        # FP64 pipe (2 flop per FMA), taken on this GPU by measure_fp64_peak
-        peak = fp64["tflops"]
-        achieved = FLOPS_PER_CELL_STAGE * cells / (launch_ms * 1e-3) / 1e12
-        return {"bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                "peak_kind": (f"measured: FP64 FMA-chain kernel, {fp64['fma_per_s'] / 1e12:.4f} T FMA/s on "
-                              f"{fp64['sms']} SMs at {fp64['sm_mhz']} MHz (nominal {FP64_NOMINAL_TFLOPS} "
-                              "TFLOP/s)"),
+        # FP64 is ALU-bound on B300: the roofline is the FP64 pipe, whose
+        # issue slots each take one FMA, add or multiply.  achieved = the
+        # formulation's algorithmic FP64 operations per launch (FMA = 1) over
+        # the launch time; peak = the FMA rate measured on this GPU by
+        # measure_fp64_peak.  The flop form is given beside it.
+        ops = FP64_OPS_PER_CELL_STAGE * cells / (launch_ms * 1e-3) / 1e9
+        peak_ops = fp64["fma_per_s"] / 1e9
+        flops = FLOPS_PER_CELL_STAGE * cells / (launch_ms * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": ops, "peak": peak_ops,
+                "unit": "G FP64 ops/s (FMA, add, mul = 1 each)", "frac": ops / peak_ops, "traffic": traffic,
+                "peak_kind": (f"measured: FP64 FMA-chain kernel, {fp64['fma_per_s'] / 1e9:.1f} G FMA/s on "
+                              f"{fp64['sms']} SMs at {fp64['sm_mhz']} MHz = {fp64['fma_per_sm_clock']:.3f} per "
+                              f"SM-clock (unit count: 2; nominal {FP64_NOMINAL_TFLOPS} TFLOP/s)"),
+                "algorithmic_ops_per_cell_stage": FP64_OPS_PER_CELL_STAGE,
                 "fp64_peak": fp64,
                 "kernel": "k_stage (RK4 stage, 4 launches/step)",
                 "launch_ms": launch_ms,
+                "flops": {"achieved": flops, "peak": fp64["tflops"], "unit": "TFLOP/s",
+                          "frac": flops / fp64["tflops"], "flop_per_cell_stage": FLOPS_PER_CELL_STAGE},
                 "hbm": {"achieved": BYTES_PER_CELL_STAGE[prec] * cells / (launch_ms * 1e-3) / 1e9,
                         "peak": hbm_peak, "unit": "GB/s",
-                        "frac": BYTES_PER_CELL_STAGE[prec] * cells / (launch_ms * 1e-3) / 1e9 / hbm_peak},
-                # the algorithmic FP64 operations (FMA = 1, a subtraction = 1)
-                # per launch against the measured FMA rate: the FP64 pipe's
-                # issue rate, one operation per slot
-                "fp64_pipe": _fp64_pipe(cells, launch_ms, fp64, sm_mhz)}
+                        "frac": BYTES_PER_CELL_STAGE[prec] * cells / (launch_ms * 1e-3) / 1e9 / hbm_peak,
+                        "peak_kind": hbm_kind}}
     achieved = BYTES_PER_CELL_STAGE[prec] * cells / (launch_ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": hbm_kind,
             "kernel": "k_stage (RK4 stage, 4 launches/step)", "launch_ms": launch_ms}
-
-
-def _fp64_pipe(cells: int, launch_ms: float, fp64: dict, sm_mhz: float | None) -> dict:
-    achieved = FP64_OPS_PER_CELL_STAGE * cells / (launch_ms * 1e-3) / 1e9
-    peak = fp64["fma_per_s"] / 1e9
-    return {"achieved": achieved, "peak": peak, "unit": "G FP64 ops/s (FMA = 1)", "frac": achieved / peak,
-            "peak_kind": "measured FMA rate", "sm_mhz_kernel": sm_mhz, "sm_mhz_peak": fp64["sm_mhz"]}
 
 
 def _cpu_baseline(p_full: inputs.Problem) -> dict:
@@ -411,10 +408,27 @@ def _ensemble(torch, steps: int, warmup: int, loop_steps: int = 50) -> dict:
     bs = sgn.BatchSolver(probs, prec="f32")
     q = bs.pack([p.q0 for p in probs])
     bs.init_aux(q)
+    # every tiling the autotuner searches, timed over one 25-step graph replay
+    # on a copy of the state, then the autotuner's own choice
+    per_tiling = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for r, pers in ((1, False), (2, False), (4, False), (1, True), (2, True)):
+        bs.set_persistent(False)
+        bs.set_rows(r)
+        bs.set_persistent(pers)
+        w = q.clone()
+        bs.step(w, 25)
+        torch.cuda.synchronize()
+        e0.record()
+        bs.step(w, 25)
+        e1.record()
+        torch.cuda.synchronize()
+        per_tiling[f"rows{r}_{'persistent' if pers else 'per_tile'}"] = 4.0 * cells * 25 / (e0.elapsed_time(e1) * 1e-3)
+        del w
+    bs.set_persistent(False)
     rows = bs.autotune(q)
     tiling = bs.tiling()
     bs.step(q, warmup)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
     bs.step(q, steps)
@@ -444,7 +458,7 @@ def _ensemble(torch, steps: int, warmup: int, loop_steps: int = 50) -> dict:
     return {"workload": "256 instances N~U{128,192,256,384,512}, half periodic/half reflecting, FP32",
             "cells": cells, "steps": steps, "value": rate_b, "unit": UNIT, "wall_ms": ms_batch,
             "per_instance_loop": rate_l, "loop_steps": loop_steps, "speedup_vs_loop": rate_b / rate_l,
-            "rows": rows, "tiling": tiling,
+            "rows": rows, "tiling": tiling, "per_tiling_rate": per_tiling,
             "hbm_gbs": hbm, "hbm_frac": hbm / peak, "hbm_peak_kind": kind,
             "mass_finite": bool(np.all(np.isfinite(d)))}
 

@@ -42,11 +42,10 @@ struct sgn_batch {
     size_t tc = 8, ta = 8;
     std::vector<sgn::InstDesc> hdesc;
     sgn::InstDesc* desc = nullptr;     // device
-    int4* tiles[3] = {nullptr, nullptr, nullptr};   // tile lists for rows = 1, 2, 4
+    sgn::PTile* tiles[3] = {nullptr, nullptr, nullptr};   // tile records for rows = 1, 2, 4
     long long ntiles[3] = {0, 0, 0};
-    // the persistent kernel (float compute types): tile records for rows = 1, 2
-    // and its grid per (rows, stage), resident blocks per SM x SMs
-    sgn::PTile* ptiles[2] = {nullptr, nullptr};
+    // the persistent kernel (float compute types, rows = 1, 2): its grid per
+    // (rows, stage), resident blocks per SM x SMs
     int pgrid[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
     int persist = 0;                   // 1: RK4 stages by the persistent kernel
     double* b64 = nullptr;
@@ -86,7 +85,7 @@ template <typename TC, typename TIN, typename TA, int MODE, int ROWS>
 cudaError_t plaunch(const sgn_batch* B, const sgn::PersistArgs<TC, TIN, TA>& a, cudaStream_t s) {
     const int ri = ROWS == 1 ? 0 : 1;
     sgn::PersistArgs<TC, TIN, TA> b = a;
-    b.tiles = B->ptiles[ri];
+    b.tiles = B->tiles[ri];
     b.ntiles = B->ntiles[ri];
     const int stage = MODE - sgn::MODE_S1;
     sgn::k_batch_persist<TC, TIN, TA, MODE, ROWS>
@@ -249,7 +248,6 @@ void free_batch(sgn_batch* B) {
     if (B->cap) cudaStreamDestroy(B->cap);
     cudaFree(B->desc);
     for (auto* t : B->tiles) cudaFree(t);
-    for (auto* t : B->ptiles) cudaFree(t);
     if (B->bT && B->bT != B->b64) cudaFree(B->bT);
     cudaFree(B->b64);
     cudaFree(B->acc);
@@ -362,9 +360,8 @@ sgn_status sgn_batch_create(const sgn_instance* inst, int ninst, int prec, const
     }
     const size_t n = (size_t)B->cells;
     bool ok = cudaMalloc(&B->desc, sizeof(sgn::InstDesc) * ninst) == cudaSuccess;
-    for (int ri = 0; ri < 3 && ok; ri++) ok = cudaMalloc(&B->tiles[ri], sizeof(int4) * tl[ri].size()) == cudaSuccess;
-    for (int ri = 0; ri < 2 && ok; ri++)
-        ok = cudaMalloc(&B->ptiles[ri], sizeof(sgn::PTile) * tl[ri].size()) == cudaSuccess;
+    for (int ri = 0; ri < 3 && ok; ri++)
+        ok = cudaMalloc(&B->tiles[ri], sizeof(sgn::PTile) * tl[ri].size()) == cudaSuccess;
     ok = ok && cudaMalloc(&B->b64, n * sizeof(double)) == cudaSuccess;
     if (ok && prec != SGN_F64) ok = cudaMalloc(&B->bT, n * sizeof(float)) == cudaSuccess;
     if (ok && prec == SGN_F64) B->bT = B->b64;
@@ -381,9 +378,7 @@ sgn_status sgn_batch_create(const sgn_instance* inst, int ninst, int prec, const
         return bfail(SGN_E_NOMEM, "batch scratch");
     }
     cudaError_t e = cudaSuccess;
-    for (int ri = 0; ri < 3 && e == cudaSuccess; ri++)
-        e = cudaMemcpy(B->tiles[ri], tl[ri].data(), sizeof(int4) * tl[ri].size(), cudaMemcpyHostToDevice);
-    for (int ri = 0; ri < 2 && e == cudaSuccess; ri++) {
+    for (int ri = 0; ri < 3 && e == cudaSuccess; ri++) {
         std::vector<sgn::PTile> pt(tl[ri].size());
         for (size_t k = 0; k < pt.size(); k++) {
             const sgn::InstDesc& d = B->hdesc[tl[ri][k].x];
@@ -395,7 +390,7 @@ sgn_status sgn_batch_create(const sgn_instance* inst, int ninst, int prec, const
             pt[k].ny = d.G.ny;
             pt[k].bc = d.bc;
         }
-        e = cudaMemcpy(B->ptiles[ri], pt.data(), sizeof(sgn::PTile) * pt.size(), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(B->tiles[ri], pt.data(), sizeof(sgn::PTile) * pt.size(), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaMemset(B->flag, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(B->b64, b_dev, n * sizeof(double), cudaMemcpyDeviceToDevice);

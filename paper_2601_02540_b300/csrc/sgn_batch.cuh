@@ -3,8 +3,9 @@
 // The instances (each its own size, boundary treatment, parameters and time
 // step) are packed back to back in one state buffer; a tile list enumerates
 // every 32 x (8*ROWS) tile of every instance, instance by instance.  Block k
-// takes tile k, reads its instance descriptor and runs the same halo-tile
-// evaluation of the split-form RHS (eq. (sd_periodic_2D_SGN) / eq. (semi_2D))
+// takes tile k, reads its tile record and instance descriptor and runs the
+// same halo-tile evaluation of the split-form RHS (eq. (sd_periodic_2D_SGN) /
+// eq. (semi_2D))
 // and RK4 stage algebra as the single-grid kernel, with the same arithmetic in
 // the same order, so a batched run equals the per-instance runs bit for bit.
 // ROWS (rows per thread: 1, 2 or 4) sets the tile height; the autotuner picks
@@ -25,10 +26,22 @@ struct InstDesc {
     int nbands;            // its bands: ceil(nx/32) ceil(ny/8), band-major
 };
 
+// One tile of a tile list: the instance and where its planes start, the
+// instance's grid and boundary treatment (so that a block can address its
+// tile from this one record), and the tile's first node.
+struct PTile {
+    long long off;         // element offset of the instance's bathymetry plane (state: 5 off)
+    int inst;              // instance (descriptor index)
+    int i0, j0;            // first node of the tile
+    int nx, ny;            // the instance's grid
+    int bc;
+};
+static_assert(sizeof(PTile) == 32, "one 32-byte record per tile");
+
 template <typename TC, typename TIN, typename TA>
 struct BatchArgs {
     const InstDesc* desc;
-    const int4* tiles;     // {instance, i0, j0, 0}
+    const PTile* tiles;
     const TIN* X;          // packed stage input
     const TC* b;           // packed bathymetry (compute type)
     const double* b64;     // packed bathymetry (double; diagnostics)
@@ -50,37 +63,53 @@ struct BatchArgs {
 template <typename TC>
 constexpr bool kBatchFact = SGN_BATCH_FACT && TileLayout<TC>::factored;
 
+// Resident blocks per SM the registers of the batched kernel must allow in
+// the FP32 mode: five (48 registers) for the first and last stages, which
+// move 64 B per node and gain from more blocks in flight, four (64) for the
+// middle ones, which would spill at 48; no bound in the mixed mode, whose
+// double registers would spill under either.
+template <typename TC, typename TA, int MODE>
+constexpr int kBatchMinBlocks = !(TileLayout<TC>::factored && sizeof(TA) == 4) ? 1
+                                : (MODE == MODE_S2 || MODE == MODE_S3)       ? 4
+                                                                              : 5;
+
 template <typename TC, typename TIN, typename TA, int MODE, int ROWS>
-__global__ void __launch_bounds__(BLOCK_THREADS)
+__global__ void __launch_bounds__(BLOCK_THREADS, (kBatchMinBlocks<TC, TA, MODE>))
 k_batch_stage(BatchArgs<TC, TIN, TA> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TC* sm = reinterpret_cast<TC*>(smem_raw);
-    const int4 tile = a.tiles[blockIdx.x];
-    const InstDesc& d = a.desc[tile.x];
-    // the instance's planes and stage coefficients, then the shared tile body
+    const PTile T = a.tiles[blockIdx.x];
+    const InstDesc& d = a.desc[T.inst];
+    // The tile is addressed from its record alone (one dependent load before
+    // the tile's loads can issue); the grid constants come from the
+    // descriptor by loads that do not hold up the tile's.
+    Geom G = d.G;
+    G.nx = T.nx;
+    G.ny = T.ny;
+    G.plane = (long long)T.nx * T.ny;
     StageArgs<TC, TIN, TA> s;
-    const long long so = 5 * d.off;
+    const long long so = 5 * T.off;
     s.X = a.X + so;
-    s.b = a.b + d.off;
+    s.b = a.b + T.off;
     s.qn = a.qn ? a.qn + so : nullptr;
     s.acc = a.acc ? a.acc + so : nullptr;
     s.Qout = a.Qout ? a.Qout + so : nullptr;
     s.out = a.out ? a.out + so : nullptr;
     s.partials = nullptr;
-    s.b64 = a.b64 ? a.b64 + d.off : nullptr;
+    s.b64 = a.b64 ? a.b64 + T.off : nullptr;
     s.flag = a.flag;
-    s.G = d.G;
+    s.G = G;
     s.c_acc = (TA)d.c_acc[a.stage];
     s.c_q = (TA)d.c_q[a.stage];
     // the band partials of the instance, laid out as those of a single-grid launch
-    const long long nbx = (d.G.nx + TILE_X - 1) / TILE_X;
-    double* slot = a.partials ? a.partials + (d.band0 + (tile.z / THREADS_Y) * nbx + tile.y / TILE_X) * NDIAG
+    const long long nbx = (T.nx + TILE_X - 1) / TILE_X;
+    double* slot = a.partials ? a.partials + (d.band0 + (T.j0 / THREADS_Y) * nbx + T.i0 / TILE_X) * NDIAG
                               : nullptr;
     // the tile layout of kBatchFact: same products, same rounding either way
-    if (d.bc == BC_REFLECTING)
-        stage_tile<TC, TIN, TA, BC_REFLECTING, MODE, ROWS, kBatchFact<TC>>(s, d.G, tile.y, tile.z, sm, slot, nbx * NDIAG);
+    if (T.bc == BC_REFLECTING)
+        stage_tile<TC, TIN, TA, BC_REFLECTING, MODE, ROWS, kBatchFact<TC>>(s, G, T.i0, T.j0, sm, slot, nbx * NDIAG);
     else
-        stage_tile<TC, TIN, TA, BC_PERIODIC, MODE, ROWS, kBatchFact<TC>>(s, d.G, tile.y, tile.z, sm, slot, nbx * NDIAG);
+        stage_tile<TC, TIN, TA, BC_PERIODIC, MODE, ROWS, kBatchFact<TC>>(s, G, T.i0, T.j0, sm, slot, nbx * NDIAG);
 }
 
 // Per-instance sums of the band partials, in band order (one block each; the

@@ -18,17 +18,6 @@
 
 namespace sgn {
 
-// One tile of the persistent kernel's list: the instance and where its planes
-// start, and the tile's first node.
-struct PTile {
-    long long off;         // element offset of the instance's bathymetry plane (state: 5 off)
-    int inst;              // instance (descriptor index)
-    int i0, j0;            // first node of the tile
-    int nx, ny;            // the instance's grid
-    int bc;
-};
-static_assert(sizeof(PTile) == 32, "one 32-byte record per tile");
-
 template <typename TC, typename TIN, typename TA>
 struct PersistArgs {
     const InstDesc* desc;
@@ -70,7 +59,7 @@ template <typename TC, typename TIN, int ROWS>
 struct PersistLayout {
     static constexpr int HX = TILE_X + 2;
     static constexpr int HN = HX * (THREADS_Y * ROWS + 2);
-    static constexpr size_t geom = (sizeof(Geom) + 15) / 16 * 16;
+    static constexpr size_t geom = (sizeof(InstDesc) + 15) / 16 * 16;     // one instance descriptor
     static constexpr size_t raw = ((size_t)5 * HN * sizeof(TIN) + (size_t)HN * sizeof(TC) + 15) / 16 * 16;
     static constexpr size_t ops = (size_t)NF_OPS * HN * sizeof(TC);
     static constexpr size_t bytes = 2 * geom + 2 * raw + ops;
@@ -93,17 +82,20 @@ k_batch_persist(PersistArgs<TC, TIN, TA> a) {
     unsigned char* rawbase = smem_raw + 2 * L::geom;
     TC* ops = reinterpret_cast<TC*>(smem_raw + 2 * L::geom + 2 * L::raw);
     const int tid = threadIdx.y * TILE_X + threadIdx.x;
-    auto geom_slot = [&](int s) { return reinterpret_cast<Geom*>(smem_raw + s * L::geom); };
+    auto desc_slot = [&](int s) { return reinterpret_cast<InstDesc*>(smem_raw + s * L::geom); };
     auto raw_x = [&](int s) { return reinterpret_cast<TIN*>(rawbase + s * L::raw); };
     auto raw_b = [&](int s) { return reinterpret_cast<TC*>(rawbase + s * L::raw + (size_t)5 * HN * sizeof(TIN)); };
 
     int bad = 0;
-    // fetch tile T into buffer s: its geometry (threads 0.. of the copy) and
-    // the raw inputs of this thread's share of the halo tile (cp.async)
+    // fetch tile T into buffer s, all by cp.async (nothing waits here): its
+    // instance descriptor (geometry and RK coefficients) and the raw inputs of
+    // this thread's share of the halo tile
     auto fetch = [&](const PTile& T, int s) {
-        const int* src = reinterpret_cast<const int*>(&a.desc[T.inst].G);
-        int* dst = reinterpret_cast<int*>(geom_slot(s));
-        for (int k = tid; k < (int)(sizeof(Geom) / sizeof(int)); k += BLOCK_THREADS) dst[k] = src[k];
+        static_assert(sizeof(InstDesc) % sizeof(float) == 0, "copied in 4-byte words");
+        const float* src = reinterpret_cast<const float*>(&a.desc[T.inst]);
+        float* dst = reinterpret_cast<float*>(desc_slot(s));
+        for (int k = tid; k < (int)(sizeof(InstDesc) / sizeof(float)); k += BLOCK_THREADS)
+            cp_async_elem(dst + k, src + k);
         const bool per = T.bc == BC_PERIODIC;
         const long long P = (long long)T.nx * T.ny;
         const TIN* X = a.X + 5 * T.off;
@@ -132,10 +124,10 @@ k_batch_persist(PersistArgs<TC, TIN, TA> a) {
     // right-hand side and the stage algebra at its output nodes
     auto evaluate = [&](const PTile& T, int s, auto bc_tag) {
         constexpr int BC = decltype(bc_tag)::value;
-        const Geom& G = *geom_slot(s);
+        const InstDesc& d = *desc_slot(s);
+        const Geom& G = d.G;
         const long long P = G.plane;
         const long long so = 5 * T.off;
-        const InstDesc& d = a.desc[T.inst];
         if constexpr (kChecked) {       // poison the operand tile of every tile
             for (int k = tid; k < (int)(NF_OPS * HN); k += BLOCK_THREADS) ops[k] = poison<TC>();
             __syncthreads();
@@ -196,30 +188,34 @@ k_batch_persist(PersistArgs<TC, TIN, TA> a) {
                 }
             }
         }
-        __syncthreads();        // the operand tile and geometry slot s are free again
+        __syncthreads();        // the operand tile and descriptor slot s are free again
     };
 
     long long tile = blockIdx.x;
     if (tile >= a.ntiles) return;
+    const long long stride = gridDim.x;
     PTile cur = a.tiles[tile];
+    // the record of the tile after next is loaded one iteration ahead, so that
+    // no fetch waits for a record
+    PTile nxt = tile + stride < a.ntiles ? a.tiles[tile + stride] : cur;
     fetch(cur, 0);
     int s = 0;
-    for (; tile < a.ntiles; tile += gridDim.x) {
-        const long long next = tile + gridDim.x;
-        PTile nxt = cur;
-        if (next < a.ntiles) {
-            nxt = a.tiles[next];
+    for (; tile < a.ntiles; tile += stride) {
+        const bool more = tile + stride < a.ntiles;
+        const PTile after = tile + 2 * stride < a.ntiles ? a.tiles[tile + 2 * stride] : nxt;
+        if (more) {
             fetch(nxt, s ^ 1);          // in flight while this tile is evaluated
-            cp_async_wait<1>();         // this tile's inputs (this thread's copies) have landed
+            cp_async_wait<1>();         // this tile's copies (this thread's) have landed
         } else {
             cp_async_wait<0>();
         }
-        __syncthreads();                // this tile's geometry (copied by other threads) is visible
+        __syncthreads();                // everyone's copies of this tile are visible
         if (cur.bc == BC_REFLECTING)
             evaluate(cur, s, std::integral_constant<int, BC_REFLECTING>{});
         else
             evaluate(cur, s, std::integral_constant<int, BC_PERIODIC>{});
         cur = nxt;
+        nxt = after;
         s ^= 1;
     }
     if (bad) atomicOr(a.flag, bad);
