@@ -357,6 +357,7 @@ def run_ours(args) -> None:
     relax = None if args.no_extra else _relaxed(torch, args.size, results["f64"]["ms_per_step"])
     mms = None if args.no_extra else _manufactured(torch)
     refl = None if args.no_extra else _reflecting(torch)
+    small = None if args.no_extra else _small_grids(torch)
     obst = None if args.no_extra else {"f64": _gaussian_obstacle(torch, "f64"),
                                        "df64": _gaussian_obstacle(torch, "df64"),
                                        "f64_bs3": _gaussian_obstacle(torch, "f64", "bs3")}
@@ -386,6 +387,7 @@ def run_ours(args) -> None:
         "manufactured": mms,
         "gaussian_obstacle": obst,
         "reflecting": refl,
+        "small_grids": small,
         "energy_drift": drift,
         "errors_vs_f64_after_job": errors,
         "kernel_hash": _kernel_hash(),
@@ -578,6 +580,45 @@ def _relaxed(torch, size: int, rk4_ms_per_step: float, nsteps: int = 20) -> dict
             "overhead": wall / nsteps * 1e3 / rk4_ms_per_step - 1.0,
             "gamma_minus_1_max": float(np.max(np.abs(np.array(gam) - 1.0))),
             "energy_drift_relaxed": er, "energy_drift_rk4": e4}
+
+
+def _small_grids(torch) -> dict:
+    """The launch-bound workloads at their stated lengths, FP64 RK4: the
+    periodic 64^2 hump (200 steps) and the reflecting 1024x512 workload (2000
+    steps).  sgn_step replays 50-step CUDA graphs on grids of at most 2^21
+    nodes; the same steps issued one call per step take the direct launches.
+    Both timed with CUDA events over the whole run, after a warm-up run."""
+    from paper_2601_02540_b300 import sgn
+    out = {"unit": UNIT}
+    for name, p in (("workload1_64x64_200", inputs.workload1()), ("workload2_1024x512_2000", inputs.workload2())):
+        s = sgn.Solver.from_problem(p, prec="f64")
+        q0 = s.state(p.q0)
+        s.init_aux(q0)
+        row = {"steps": p.nsteps, "cells": p.nx * p.ny}
+        for mode in ("graph", "direct"):
+            q = q0.clone()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for rep in range(2):                 # the first run is the warm-up (and captures the graph)
+                q.copy_(q0)
+                torch.cuda.synchronize()
+                e0.record()
+                if mode == "graph":
+                    s.step(q, p.dt, p.nsteps)
+                else:
+                    for _ in range(p.nsteps):
+                        s.step(q, p.dt, 1)
+                e1.record()
+                torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            row[mode] = {"ms": ms, "value": 4.0 * p.nx * p.ny * p.nsteps / (ms * 1e-3)}
+            if mode == "graph":
+                qg = q.clone()
+            else:
+                row["equal_bitwise"] = bool(torch.equal(q, qg))
+        row["graph_speedup"] = row["direct"]["ms"] / row["graph"]["ms"]
+        out[name] = row
+        s.close()
+    return out
 
 
 def _reflecting(torch, steps: int = 20, warmup: int = 3) -> dict:
