@@ -48,11 +48,15 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6400.0
 FP64_NOMINAL_TFLOPS = 1.25     # B300 dense FP64 (nominal; no measured entry)
 # Algorithmic bytes per cell-stage of the three-register RK4 stage kernels
-# (each plane read or written once per stage, halos from cache):
+# (each plane read or written once per stage, halos from cache), FP64 and df64:
 #   stage 1: read q, b; write acc, Q             16 planes
 #   stages 2, 3: read Q, b, q, acc; write acc, Q  26 planes
-#   stage 4: read Q, b, acc; write q              16 planes
-BYTES_PER_CELL_STAGE = {"f64": 84 * 8 / 4, "f32": 84 * 4 / 4, "f32_f64acc": 536 / 4,
+#   stage 4: read Q, b, acc; write q              16 planes   -> 84 planes per step
+# The FP32 mode runs stages 1 and 2 as S1K / S2K:
+#   stage 1: read q, b; write k1                  11 planes
+#   stage 2: read q, k1, b; write acc, Q          21 planes   -> 74 planes per step
+# The mixed mode: q and acc double, Q and b float, the 84-plane scheme (536 B per step).
+BYTES_PER_CELL_STAGE = {"f64": 84 * 8 / 4, "f32": 74 * 4 / 4, "f32_f64acc": 536 / 4,
                         "df64": 84 * 8 / 4}     # df64: stage states as float pairs, 8 bytes
 # Algorithmic floating-point operations per cell-stage of the implemented
 # formulation (an FMA counts 2; 1/h counts 1): pointwise operands (1/h, eta/h,

@@ -171,12 +171,23 @@ cudaError_t run_steps(sgn_ctx* c, TA* q, double dt, int nsteps, cudaStream_t s, 
     a3.X = Qb; a3.Qout = Qa; a3.c_acc = dt3; a3.c_q = dt1;
     StageArgs<TC, TC, TA> a4 = base_args<TC, TC, TA>(c);
     a4.X = Qa; a4.acc = acc; a4.out = q; a4.c_acc = dt6;
+    // FP32: stage 1 stores only k1 (in Qa) and stage 2 forms q_n + dt/2 k1 and
+    // the accumulator itself (modes S1K, S2K; kStoreK1)
+    constexpr bool kK1 = sgn::kStoreK1<TC, TA>;
+    a2.c_acc1 = dt6;
+    a2.c_q1 = dt2;
     for (int n = 0; n < nsteps; n++) {
         cudaError_t e;
-        // k1 = f(q_n)
-        if ((e = launch_stage<TC, TA, TA, BC, sgn::MODE_S1>(c, a1, s)) != cudaSuccess) return e;
-        // k2 = f(q_n + dt/2 k1)
-        if ((e = launch_stage<TC, TC, TA, BC, sgn::MODE_S2>(c, a2, s)) != cudaSuccess) return e;
+        if constexpr (kK1) {
+            // k1 = f(q_n) -> Qa; k2 = f(q_n + dt/2 k1), acc = q_n + dt/6 k1 + dt/3 k2
+            if ((e = launch_stage<TC, TA, TA, BC, sgn::MODE_S1K>(c, a1, s)) != cudaSuccess) return e;
+            if ((e = launch_stage<TC, TC, TA, BC, sgn::MODE_S2K>(c, a2, s)) != cudaSuccess) return e;
+        } else {
+            // k1 = f(q_n)
+            if ((e = launch_stage<TC, TA, TA, BC, sgn::MODE_S1>(c, a1, s)) != cudaSuccess) return e;
+            // k2 = f(q_n + dt/2 k1)
+            if ((e = launch_stage<TC, TC, TA, BC, sgn::MODE_S2>(c, a2, s)) != cudaSuccess) return e;
+        }
         // k3 = f(q_n + dt/2 k2)
         if ((e = launch_stage<TC, TC, TA, BC, sgn::MODE_S3>(c, a3, s)) != cudaSuccess) return e;
         // k4 = f(q_n + dt k3); q_{n+1} = acc + dt/6 k4
@@ -263,8 +274,9 @@ struct AttrOp {
     sgn_ctx* c;
     template <typename TC, typename TA, int BC>
     cudaError_t operator()() {
-        cudaError_t e = stage_attr<TC, TA, TA, BC, sgn::MODE_S1>();
-        if (e == cudaSuccess) e = stage_attr<TC, TC, TA, BC, sgn::MODE_S2>();
+        constexpr bool kK1 = sgn::kStoreK1<TC, TA>;     // the stage modes run_steps launches
+        cudaError_t e = stage_attr<TC, TA, TA, BC, kK1 ? sgn::MODE_S1K : sgn::MODE_S1>();
+        if (e == cudaSuccess) e = stage_attr<TC, TC, TA, BC, kK1 ? sgn::MODE_S2K : sgn::MODE_S2>();
         if (e == cudaSuccess) e = stage_attr<TC, TC, TA, BC, sgn::MODE_S3>();
         if (e == cudaSuccess) e = stage_attr<TC, TC, TA, BC, sgn::MODE_S4>();
         return e;

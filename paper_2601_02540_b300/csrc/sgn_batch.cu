@@ -133,6 +133,10 @@ template <typename TC, typename TA, int ROWS>
 cudaError_t set_attrs_rows() {
     cudaError_t e = set_attr<TC, TA, TA, sgn::MODE_S1, ROWS>();
     if (e == cudaSuccess) e = set_attr<TC, TC, TA, sgn::MODE_S2, ROWS>();
+    if constexpr (sgn::kStoreK1<TC, TA>) {
+        if (e == cudaSuccess) e = set_attr<TC, TA, TA, sgn::MODE_S1K, ROWS>();
+        if (e == cudaSuccess) e = set_attr<TC, TC, TA, sgn::MODE_S2K, ROWS>();
+    }
     if (e == cudaSuccess) e = set_attr<TC, TC, TA, sgn::MODE_S3, ROWS>();
     if (e == cudaSuccess) e = set_attr<TC, TC, TA, sgn::MODE_S4, ROWS>();
     if (e == cudaSuccess) e = set_attr<TC, TA, TA, sgn::MODE_DIAG, ROWS>();
@@ -193,8 +197,14 @@ cudaError_t bsteps(sgn_batch* B, TA* q, int nsteps, cudaStream_t s) {
     }
     for (int n = 0; n < nsteps; n++) {
         cudaError_t e;
-        if ((e = blaunch<TC, TA, TA, sgn::MODE_S1, ROWS>(B, a1, s)) != cudaSuccess) return e;
-        if ((e = blaunch<TC, TC, TA, sgn::MODE_S2, ROWS>(B, a2, s)) != cudaSuccess) return e;
+        if constexpr (sgn::kStoreK1<TC, TA>) {
+            // FP32: stage 1 stores k1 only, stage 2 forms the rest
+            if ((e = blaunch<TC, TA, TA, sgn::MODE_S1K, ROWS>(B, a1, s)) != cudaSuccess) return e;
+            if ((e = blaunch<TC, TC, TA, sgn::MODE_S2K, ROWS>(B, a2, s)) != cudaSuccess) return e;
+        } else {
+            if ((e = blaunch<TC, TA, TA, sgn::MODE_S1, ROWS>(B, a1, s)) != cudaSuccess) return e;
+            if ((e = blaunch<TC, TC, TA, sgn::MODE_S2, ROWS>(B, a2, s)) != cudaSuccess) return e;
+        }
         if ((e = blaunch<TC, TC, TA, sgn::MODE_S3, ROWS>(B, a3, s)) != cudaSuccess) return e;
         if ((e = blaunch<TC, TC, TA, sgn::MODE_S4, ROWS>(B, a4, s)) != cudaSuccess) return e;
     }

@@ -65,11 +65,13 @@ constexpr bool kBatchFact = SGN_BATCH_FACT && TileLayout<TC>::factored;
 
 // Resident blocks per SM the registers of the batched kernel must allow in
 // the FP32 mode: five (48 registers) for the first and last stages, which
-// move 64 B per node and gain from more blocks in flight, four (64) for the
-// middle ones, which would spill at 48; no bound in the mixed mode, whose
-// double registers would spill under either.
+// move few bytes per node and gain from more blocks in flight, four (64) for
+// the middle ones, which would spill at 48, three for S2K (which holds q_n
+// and k1 of its halo nodes); no bound in the mixed mode, whose double
+// registers would spill under these.
 template <typename TC, typename TA, int MODE>
 constexpr int kBatchMinBlocks = !(TileLayout<TC>::factored && sizeof(TA) == 4) ? 1
+                                : MODE == MODE_S2K                           ? 3
                                 : (MODE == MODE_S2 || MODE == MODE_S3)       ? 4
                                                                               : 5;
 
@@ -101,6 +103,8 @@ k_batch_stage(BatchArgs<TC, TIN, TA> a) {
     s.G = G;
     s.c_acc = (TA)d.c_acc[a.stage];
     s.c_q = (TA)d.c_q[a.stage];
+    s.c_acc1 = (TA)d.c_acc[0];       // S2K: the first stage's dt/6 and dt/2
+    s.c_q1 = (TA)d.c_q[0];
     // the band partials of the instance, laid out as those of a single-grid launch
     const long long nbx = (T.nx + TILE_X - 1) / TILE_X;
     double* slot = a.partials ? a.partials + (d.band0 + (T.j0 / THREADS_Y) * nbx + T.i0 / TILE_X) * NDIAG

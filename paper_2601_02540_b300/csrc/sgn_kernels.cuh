@@ -32,7 +32,21 @@ enum { BC_PERIODIC = 0, BC_REFLECTING = 1 };
 // DIAG computes k = f(q) and reduces mass, energy and the energy rate.
 // S4D is S4 that also reduces the mass and energies of the new state q_{n+1}
 // (the per-step monitor, fused into the stage that produces the state).
-enum { MODE_RHS = 0, MODE_S1 = 1, MODE_S2 = 2, MODE_S3 = 3, MODE_S4 = 4, MODE_DIAG = 5, MODE_S4D = 6 };
+// S1K and S2K replace S1 and S2 in the FP32 mode, which is bound by memory
+// traffic: S1K stores only k1 (in Qout, 5 planes instead of the
+// 10 of acc and Q), and S2K forms Q = q_n + dt/2 k1 while staging its tile
+// from q_n and k1 (X) and the accumulator q_n + dt/6 k1 + dt/3 k2 at its
+// nodes, with the same roundings in the same order as S1 and S2:
+//   S1K: k1 = f(q_n) -> Qout
+//   S2K: k2 = f(q_n + dt/2 k1); acc = (q_n + dt/6 k1) + dt/3 k2; Q' = q_n + dt/2 k2
+// so that the first two stages move 11 + 21 planes instead of 16 + 26.
+enum { MODE_RHS = 0, MODE_S1 = 1, MODE_S2 = 2, MODE_S3 = 3, MODE_S4 = 4, MODE_DIAG = 5, MODE_S4D = 6,
+       MODE_S1K = 7, MODE_S2K = 8 };
+// Whether RK4 steps use S1K and S2K: the FP32 mode (float state and compute
+// type; the mixed mode's S2K, holding double q_n and float k1 of its halo
+// nodes, measured 15% slower than S1 and S2).
+template <typename TC, typename TA>
+constexpr bool kStoreK1 = sizeof(TC) == 4 && sizeof(TA) == 4;
 
 constexpr int TILE_X = 32;
 constexpr int THREADS_Y = 8;
@@ -195,6 +209,7 @@ struct StageArgs {
     int* flag;           // latched error bits
     Geom G;
     TA c_acc, c_q;       // stage coefficients (see the modes)
+    TA c_acc1, c_q1;     // S2K: the first stage's dt/6 and dt/2
 };
 
 template <typename T>
@@ -617,14 +632,16 @@ struct TileIn {
     int bad;                                    // FLAG_BOUNDS of checked builds
 };
 
-// Global -> registers: the six input planes of the halo tile at (i0, j0).
-template <typename TC, typename TIN, typename TA, int BC, int HALO_X, int HALO_N, int NPER>
+// Global -> registers: the six input planes of the halo tile at (i0, j0)
+// (S2K: the stage input formed from q_n and k1 = X, see the modes).
+template <typename TC, typename TIN, typename TA, int BC, int HALO_X, int HALO_N, int NPER, int MODE = MODE_RHS>
 __device__ __forceinline__ void tile_load(const StageArgs<TC, TIN, TA>& a, const Geom& G, int i0, int j0,
                                           TileIn<TC, NPER>& in) {
     const long long P = G.plane;
     const int tid = threadIdx.y * TILE_X + threadIdx.x;
     in.bad = 0;
     TIN rh[NPER] = {}, ru[NPER] = {}, rv[NPER] = {}, rw[NPER] = {}, re[NPER] = {};
+    TA qh[NPER] = {}, qu[NPER] = {}, qv[NPER] = {}, qw[NPER] = {}, qe[NPER] = {};
 #pragma unroll
     for (int k = 0; k < NPER; k++) {
         const int t = tid + k * BLOCK_THREADS;
@@ -642,17 +659,34 @@ __device__ __forceinline__ void tile_load(const StageArgs<TC, TIN, TA>& a, const
         rv[k] = a.X[2 * P + c];
         rw[k] = a.X[3 * P + c];
         re[k] = a.X[4 * P + c];
+        if (MODE == MODE_S2K) {
+            qh[k] = a.qn[c];
+            qu[k] = a.qn[P + c];
+            qv[k] = a.qn[2 * P + c];
+            qw[k] = a.qn[3 * P + c];
+            qe[k] = a.qn[4 * P + c];
+        }
         in.b[k] = a.b[c];
     }
     // conversions to the compute type after every load is issued (a conversion
     // right behind its load would wait for it before the next load issues)
 #pragma unroll
     for (int k = 0; k < NPER; k++) {
-        in.h[k] = cvt<TC>(rh[k]);
-        in.u[k] = cvt<TC>(ru[k]);
-        in.v[k] = cvt<TC>(rv[k]);
-        in.w[k] = cvt<TC>(rw[k]);
-        in.e[k] = cvt<TC>(re[k]);
+        if constexpr (MODE == MODE_S2K) {
+            // Q = q_n + dt/2 k1, as stage 1 forms it (stage_state)
+            static_assert(std::is_same<TIN, TC>::value, "S2K stages k1 stored in the compute type");
+            in.h[k] = stage_state<TC, TA>(a.c_q1, rh[k], cvt<TA>(rh[k]), qh[k]);
+            in.u[k] = stage_state<TC, TA>(a.c_q1, ru[k], cvt<TA>(ru[k]), qu[k]);
+            in.v[k] = stage_state<TC, TA>(a.c_q1, rv[k], cvt<TA>(rv[k]), qv[k]);
+            in.w[k] = stage_state<TC, TA>(a.c_q1, rw[k], cvt<TA>(rw[k]), qw[k]);
+            in.e[k] = stage_state<TC, TA>(a.c_q1, re[k], cvt<TA>(re[k]), qe[k]);
+        } else {
+            in.h[k] = cvt<TC>(rh[k]);
+            in.u[k] = cvt<TC>(ru[k]);
+            in.v[k] = cvt<TC>(rv[k]);
+            in.w[k] = cvt<TC>(rw[k]);
+            in.e[k] = cvt<TC>(re[k]);
+        }
     }
 }
 
@@ -686,11 +720,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
     constexpr bool kEarly = sizeof(TC) == 4 || (SGN_DF64_EARLY && std::is_same<TC, df64>::value) ||
                             (SGN_F64_EARLY && std::is_same<TC, double>::value);
     constexpr bool kEarlyStage = kEarly;
+    static_assert(kEarly || (MODE != MODE_S1K && MODE != MODE_S2K), "S1K and S2K serve the early-load kernels");
     constexpr int NPER = tile_nper<ROWS>();
     const int gi = i0 + threadIdx.x;
     TA pq[ROWS_PER_THREAD][5], pa[ROWS_PER_THREAD][5];
+    TC pk[ROWS_PER_THREAD][5];          // S2K: k1 at this thread's nodes
     if (kEarlyStage && (MODE == MODE_S1 || MODE == MODE_S2 || MODE == MODE_S3 || MODE == MODE_S4 ||
-                        MODE == MODE_S4D)) {
+                        MODE == MODE_S4D || MODE == MODE_S2K)) {
 #pragma unroll
         for (int ry = 0; ry < ROWS_PER_THREAD; ry++) {
             const int gj = j0 + threadIdx.y + ry * THREADS_Y;
@@ -699,7 +735,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
 #pragma unroll
             for (int f = 0; f < 5; f++) {
                 if (MODE != MODE_S4 && MODE != MODE_S4D) pq[ry][f] = a.qn[f * P + c];
-                if (MODE != MODE_S1) pa[ry][f] = a.acc[f * P + c];
+                if (MODE == MODE_S2K) pk[ry][f] = cvt<TC>(a.X[f * P + c]);
+                else if (MODE != MODE_S1) pa[ry][f] = a.acc[f * P + c];
             }
         }
     }
@@ -713,7 +750,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
     }
     TileIn<TC, NPER> in;
     if (kEarly) {
-        tile_load<TC, TIN, TA, BC, HALO_X, HALO_N, NPER>(a, G, i0, j0, in);
+        tile_load<TC, TIN, TA, BC, HALO_X, HALO_N, NPER, MODE>(a, G, i0, j0, in);
         bad |= in.bad;
     }
 #pragma unroll
@@ -778,6 +815,17 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
                 const TA kv = cvt<TA>(k[f]);
                 const TA av = (MODE == MODE_S1) ? qv : (kEarlyStage ? pa[ry][f] : a.acc[f * P + c]);
                 a.acc[f * P + c] = fma_(a.c_acc, kv, av);
+                a.Qout[f * P + c] = stage_state<TC, TA>(a.c_q, k[f], kv, qv);
+            }
+        } else if (MODE == MODE_S1K) {
+#pragma unroll
+            for (int f = 0; f < 5; f++) a.Qout[f * P + c] = k[f];
+        } else if (MODE == MODE_S2K) {
+#pragma unroll
+            for (int f = 0; f < 5; f++) {
+                const TA qv = pq[ry][f];
+                const TA kv = cvt<TA>(k[f]);
+                a.acc[f * P + c] = fma_(a.c_acc, kv, fma_(a.c_acc1, cvt<TA>(pk[ry][f]), qv));
                 a.Qout[f * P + c] = stage_state<TC, TA>(a.c_q, k[f], kv, qv);
             }
         } else if (MODE == MODE_S4 || MODE == MODE_S4D) {
@@ -877,8 +925,13 @@ struct StageMinBlocks<float, double> {
     static constexpr int value = SGN_MIX_MINB;
 };
 
+// S2K holds q_n and k1 of its halo nodes between their loads and the stage
+// input they form: one block per SM fewer than the other stages (no spills).
+template <typename TC, typename TA, int MODE>
+constexpr int kStageMinBlocks = MODE == MODE_S2K ? StageMinBlocks<TC, TA>::value - 1 : StageMinBlocks<TC, TA>::value;
+
 template <typename TC, typename TIN, typename TA, int BC, int MODE>
-__global__ void __launch_bounds__(BLOCK_THREADS, StageMinBlocks<TC, TA>::value)
+__global__ void __launch_bounds__(BLOCK_THREADS, (kStageMinBlocks<TC, TA, MODE>))
 k_stage(StageArgs<TC, TIN, TA> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TC* sm = reinterpret_cast<TC*>(smem_raw);
