@@ -66,3 +66,10 @@ def test_null_context_is_rejected(lib):
     assert lib.sgn_step(None, None, 0.1, 1, None) == 1
     assert lib.sgn_mass_energy(None, None, None, None) == 1
     assert lib.sgn_destroy(None) == 0
+
+
+def test_fma_rate_rejects_bad_arguments_without_device(lib):
+    n, sec = ctypes.c_double(), ctypes.c_double()
+    for iters in (0, 3, 1 << 21):
+        assert lib.sgn_measure_fp64_fma(iters, ctypes.byref(n), ctypes.byref(sec), None) == 1
+    assert lib.sgn_measure_fp64_fma(64, None, ctypes.byref(sec), None) == 1

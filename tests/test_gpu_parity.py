@@ -270,3 +270,32 @@ def test_zero_steps_is_identity():
     s.step(q, p.dt, 0)
     assert np.array_equal(gu.to_np(q), p.q0)
     s.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32_f64acc", "df64"])
+def test_graph_replay_equals_direct_steps(prec):
+    """Small grids replay 50-step CUDA graphs inside sgn_step: 120 steps in one
+    call (two replays + 20 direct steps) equal 120 single-step calls (direct
+    launches) bit for bit, and a second call with another dt recaptures."""
+    p = inputs.smooth_state(64, 40, REFLECTING, seed=9, xmax=1.3, ymax=0.9)
+    s = gu.solver(p, prec)
+    q1 = s.state(p.q0)
+    s.step(q1, p.dt, 120)
+    q2 = s.state(p.q0)
+    for _ in range(120):
+        s.step(q2, p.dt, 1)
+    assert torch.equal(q1, q2)
+    q3, q4 = s.state(p.q0), s.state(p.q0)
+    s.step(q3, 0.5 * p.dt, 60)
+    for _ in range(60):
+        s.step(q4, 0.5 * p.dt, 1)
+    assert torch.equal(q3, q4)
+    s.close()
+
+
+def test_fp64_fma_rate_measurement():
+    n, sec = sgn.sgn_measure_fp64_fma(256)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert n == sms * 8 * 256 * 16 * 256 and sec > 0
+    rate = n / sec
+    assert 1e10 < rate < 2e12, rate          # FMA per second: B300 ~5e11
