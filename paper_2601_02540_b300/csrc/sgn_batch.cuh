@@ -66,14 +66,12 @@ constexpr bool kBatchFact = SGN_BATCH_FACT && TileLayout<TC>::factored;
 // Resident blocks per SM the registers of the batched kernel must allow in
 // the FP32 mode: five (48 registers) for the first and last stages, which
 // move few bytes per node and gain from more blocks in flight, four (64) for
-// the middle ones, which would spill at 48, three for S2K (which holds q_n
-// and k1 of its halo nodes); no bound in the mixed mode, whose double
-// registers would spill under these.
+// the middle ones (S2K among them), which would spill at 48; no bound in the
+// mixed mode, whose double registers would spill under these.
 template <typename TC, typename TA, int MODE>
-constexpr int kBatchMinBlocks = !(TileLayout<TC>::factored && sizeof(TA) == 4) ? 1
-                                : MODE == MODE_S2K                           ? 3
-                                : (MODE == MODE_S2 || MODE == MODE_S3)       ? 4
-                                                                              : 5;
+constexpr int kBatchMinBlocks = !(TileLayout<TC>::factored && sizeof(TA) == 4)            ? 1
+                                : (MODE == MODE_S2 || MODE == MODE_S3 || MODE == MODE_S2K) ? 4
+                                                                                            : 5;
 
 template <typename TC, typename TIN, typename TA, int MODE, int ROWS>
 __global__ void __launch_bounds__(BLOCK_THREADS, (kBatchMinBlocks<TC, TA, MODE>))

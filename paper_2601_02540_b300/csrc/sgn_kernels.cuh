@@ -726,7 +726,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
     TA pq[ROWS_PER_THREAD][5], pa[ROWS_PER_THREAD][5];
     TC pk[ROWS_PER_THREAD][5];          // S2K: k1 at this thread's nodes
     if (kEarlyStage && (MODE == MODE_S1 || MODE == MODE_S2 || MODE == MODE_S3 || MODE == MODE_S4 ||
-                        MODE == MODE_S4D || MODE == MODE_S2K)) {
+                        MODE == MODE_S4D)) {
 #pragma unroll
         for (int ry = 0; ry < ROWS_PER_THREAD; ry++) {
             const int gj = j0 + threadIdx.y + ry * THREADS_Y;
@@ -735,8 +735,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
 #pragma unroll
             for (int f = 0; f < 5; f++) {
                 if (MODE != MODE_S4 && MODE != MODE_S4D) pq[ry][f] = a.qn[f * P + c];
-                if (MODE == MODE_S2K) pk[ry][f] = cvt<TC>(a.X[f * P + c]);
-                else if (MODE != MODE_S1) pa[ry][f] = a.acc[f * P + c];
+                if (MODE != MODE_S1) pa[ry][f] = a.acc[f * P + c];
             }
         }
     }
@@ -748,13 +747,77 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
         for (int k = tid; k < NP * HALO_N; k += BLOCK_THREADS) sm[k] = poison<TC>();
         __syncthreads();
     }
+    if constexpr (MODE == MODE_S2K) {
+        // Halo items of this thread: first its own output nodes (one per row
+        // of the tile), then, for the first RING threads, one node of the
+        // ring around the tile.  Its nodes' q_n and k1 stay in registers for
+        // the epilogue, so S2K loads every value once.
+        static_assert(std::is_same<TIN, TC>::value, "S2K stages k1 stored in the compute type");
+        constexpr int TY = THREADS_Y * ROWS_PER_THREAD;
+        constexpr int RING = 2 * HALO_X + 2 * TY;
+        constexpr int NIT = ROWS_PER_THREAD + 1;
+        static_assert(RING <= BLOCK_THREADS && HALO_N == TILE_X * TY + RING, "one ring node per thread");
+        TIN rk[NIT][5];
+        TA rq[NIT][5];
+        TC rb[NIT];
+        int tt[NIT];
+#pragma unroll
+        for (int k = 0; k < NIT; k++) {
+            int t = -1;
+            if (k < ROWS_PER_THREAD) {
+                t = (threadIdx.y + k * THREADS_Y + 1) * HALO_X + threadIdx.x + 1;
+            } else if (tid < RING) {
+                const int r = tid;
+                if (r < HALO_X) t = r;                                          // row above
+                else if (r < 2 * HALO_X) t = (TY + 1) * HALO_X + (r - HALO_X);  // row below
+                else if (r < 2 * HALO_X + TY) t = (r - 2 * HALO_X + 1) * HALO_X;               // left column
+                else t = (r - 2 * HALO_X - TY + 1) * HALO_X + HALO_X - 1;                     // right column
+            }
+            tt[k] = t;
+            if (t < 0) continue;
+            const int gx = halo_index<BC>(i0 - 1 + t % HALO_X, G.nx);
+            const int gy = halo_index<BC>(j0 - 1 + t / HALO_X, G.ny);
+            if (kChecked && (gx < 0 || gx >= G.nx || gy < 0 || gy >= G.ny)) {
+                bad |= FLAG_BOUNDS;
+                tt[k] = -1;
+                continue;
+            }
+            const long long c = (long long)gy * G.nx + gx;
+#pragma unroll
+            for (int f = 0; f < 5; f++) {
+                rk[k][f] = a.X[f * P + c];
+                rq[k][f] = a.qn[f * P + c];
+            }
+            rb[k] = a.b[c];
+        }
+#pragma unroll
+        for (int k = 0; k < NIT; k++) {
+            if (tt[k] < 0) continue;
+            TC y[5];
+#pragma unroll
+            for (int f = 0; f < 5; f++) y[f] = stage_state<TC, TA>(a.c_q1, rk[k][f], cvt<TA>(rk[k][f]), rq[k][f]);
+            bad |= h_flags(y[0]);
+            if constexpr (FACT)
+                store_operands_factored<TC, HALO_N>(sm, tt[k], y[0], y[1], y[2], y[3], y[4], rb[k], G);
+            else
+                store_operands<TC, HALO_N>(sm, tt[k], y[0], y[1], y[2], y[3], y[4], rb[k], G);
+        }
+#pragma unroll
+        for (int ry = 0; ry < ROWS_PER_THREAD; ry++)
+#pragma unroll
+            for (int f = 0; f < 5; f++) {
+                pq[ry][f] = rq[ry][f];
+                pk[ry][f] = rk[ry][f];
+            }
+    }
     TileIn<TC, NPER> in;
-    if (kEarly) {
+    if (kEarly && MODE != MODE_S2K) {
         tile_load<TC, TIN, TA, BC, HALO_X, HALO_N, NPER, MODE>(a, G, i0, j0, in);
         bad |= in.bad;
     }
 #pragma unroll
     for (int k = 0; k < NPER; k++) {
+        if (MODE == MODE_S2K) break;
         const int t = tid + k * BLOCK_THREADS;
         if (t >= HALO_N) continue;
         TC h, u, v, w, eta, bb;
@@ -926,12 +989,14 @@ struct StageMinBlocks<float, double> {
 };
 
 // S2K holds q_n and k1 of its halo nodes between their loads and the stage
-// input they form: one block per SM fewer than the other stages (no spills).
-template <typename TC, typename TA, int MODE>
-constexpr int kStageMinBlocks = MODE == MODE_S2K ? StageMinBlocks<TC, TA>::value - 1 : StageMinBlocks<TC, TA>::value;
+// input they form: with reflecting walls (the one-sided rows and SATs) one
+// block per SM fewer than the other stages, which it needs to avoid spills.
+template <typename TC, typename TA, int MODE, int BC>
+constexpr int kStageMinBlocks = (MODE == MODE_S2K && BC == BC_REFLECTING) ? StageMinBlocks<TC, TA>::value - 1
+                                                                           : StageMinBlocks<TC, TA>::value;
 
 template <typename TC, typename TIN, typename TA, int BC, int MODE>
-__global__ void __launch_bounds__(BLOCK_THREADS, (kStageMinBlocks<TC, TA, MODE>))
+__global__ void __launch_bounds__(BLOCK_THREADS, (kStageMinBlocks<TC, TA, MODE, BC>))
 k_stage(StageArgs<TC, TIN, TA> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TC* sm = reinterpret_cast<TC*>(smem_raw);
