@@ -787,12 +787,19 @@ def main() -> None:
                     help="run only the adjoint leg with NSTEPS RK4 steps and print its JSON (profiling)")
     ap.add_argument("--ensemble-only", type=int, default=0, metavar="NSTEPS",
                     help="run only the ensemble leg, timing NSTEPS steps, and print its JSON (profiling)")
+    ap.add_argument("--adaptive-only", type=int, default=0, metavar="SIZE",
+                    help="run only the adaptive leg on a SIZE x SIZE grid and print its JSON (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.adjoint_only > 0:
         import torch
         print(json.dumps({"adjoint": _adjoint(torch, args.adjoint_only)}))
+        return
+    if args.adaptive_only > 0:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"adaptive": _adaptive(torch, args.adaptive_only, float("nan"))}))
         return
     if args.ensemble_only > 0:
         import torch

@@ -44,7 +44,7 @@ enum { MODE_RHS = 0, MODE_S1 = 1, MODE_S2 = 2, MODE_S3 = 3, MODE_S4 = 4, MODE_DI
        MODE_S1K = 7, MODE_S2K = 8 };
 // Whether RK4 steps use S1K and S2K: the FP32 mode (float state and compute
 // type; the mixed mode's S2K, holding double q_n and float k1 of its halo
-// nodes, measured 15% slower than S1 and S2).
+// nodes, measured 3% slower than S1 and S2).
 template <typename TC, typename TA>
 constexpr bool kStoreK1 = sizeof(TC) == 4 && sizeof(TA) == 4;
 
