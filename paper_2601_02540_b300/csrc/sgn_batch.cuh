@@ -64,13 +64,15 @@ template <typename TC>
 constexpr bool kBatchFact = SGN_BATCH_FACT && TileLayout<TC>::factored;
 
 // Resident blocks per SM the registers of the batched kernel must allow in
-// the FP32 mode: five (48 registers) for the first and last stages, which
-// move few bytes per node and gain from more blocks in flight, four (64) for
-// the middle ones (S2K among them), which would spill at 48; no bound in the
-// mixed mode, whose double registers would spill under these.
+// the FP32 mode: six (40 registers) for S1K and five (48) for the last stage,
+// which move few bytes per node and gain from more blocks in flight (the last
+// stage's reflecting branch would spill at 40), four (64) for the middle ones
+// (S2K among them), which would spill at 48; no bound in the mixed mode, whose
+// double registers would spill under these.
 template <typename TC, typename TA, int MODE>
 constexpr int kBatchMinBlocks = !(TileLayout<TC>::factored && sizeof(TA) == 4)            ? 1
                                 : (MODE == MODE_S2 || MODE == MODE_S3 || MODE == MODE_S2K) ? 4
+                                : MODE == MODE_S1K                                         ? 6
                                                                                             : 5;
 
 template <typename TC, typename TIN, typename TA, int MODE, int ROWS>

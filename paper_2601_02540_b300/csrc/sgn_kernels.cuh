@@ -991,9 +991,16 @@ struct StageMinBlocks<float, double> {
 // S2K holds q_n and k1 of its halo nodes between their loads and the stage
 // input they form: with reflecting walls (the one-sided rows and SATs) one
 // block per SM fewer than the other stages, which it needs to avoid spills.
+// The FP32 S1K and (periodic) S4 move few bytes per node and are bound by
+// the latency of their loads: six blocks per SM (40 registers, no spills).
+#ifndef SGN_F32_LIGHT_MINB
+#define SGN_F32_LIGHT_MINB 6
+#endif
 template <typename TC, typename TA, int MODE, int BC>
-constexpr int kStageMinBlocks = (MODE == MODE_S2K && BC == BC_REFLECTING) ? StageMinBlocks<TC, TA>::value - 1
-                                                                           : StageMinBlocks<TC, TA>::value;
+constexpr int kStageMinBlocks =
+    (MODE == MODE_S2K && BC == BC_REFLECTING) ? StageMinBlocks<TC, TA>::value - 1
+    : (kStoreK1<TC, TA> && (MODE == MODE_S1K || (MODE == MODE_S4 && BC == BC_PERIODIC))) ? SGN_F32_LIGHT_MINB
+                                                                                          : StageMinBlocks<TC, TA>::value;
 
 template <typename TC, typename TIN, typename TA, int BC, int MODE>
 __global__ void __launch_bounds__(BLOCK_THREADS, (kStageMinBlocks<TC, TA, MODE, BC>))
