@@ -227,7 +227,7 @@ def measure_fp64_peak(torch, local: int, iters: int = 16384, reps: int = 3) -> d
 
 
 def _roofline(prec: str, cells: int, ms_total: float, launches_per_step: int, steps: int,
-              hbm_peak: float, hbm_kind: str, fp64: dict | None = None, sm_mhz: float | None = None) -> dict:
+              hbm_peak: float, hbm_kind: str, fp64: dict | None = None) -> dict:
     launch_ms = ms_total / (launches_per_step * steps)
     traffic = _ncu_traffic(prec)
     if prec == "f64":
@@ -321,8 +321,7 @@ def run_ours(args) -> None:
             ms, launches = _time_steps(torch, s, q, p.dt, args.steps, args.warmup, dist)
         results[prec] = {"value": replica_rate(cells, args.steps, ms, world), "ms_per_step": ms / args.steps,
                          "gpu_launches": launches,
-                         "roofline": _roofline(prec, cells, ms, 4, args.steps, hbm_peak, hbm_kind, fp64,
-                                               clocks.get("sm_mhz") if clocks else None)}
+                         "roofline": _roofline(prec, cells, ms, 4, args.steps, hbm_peak, hbm_kind, fp64)}
         if not args.no_drift:
             # the full job, outside the timed region: energy drift and final state
             q.copy_(q_init)

@@ -1,10 +1,11 @@
-// sgn_adaptive.cuh - stage kernels of the adaptive time integrator.
+// sgn_adaptive.cuh - stage kernels of the adaptive integrator's second pair.
 //
 // The paper advances the semi-discretization (eq. (sd_periodic_2D_SGN) /
-// eq. (semi_2D)) with an explicit third-order Runge-Kutta pair that has the
-// first-same-as-last (FSAL) property, an embedded error estimate and automatic
-// step-size control (Sec. 6); it does not print the pair.  The pair here is
-// the Bogacki-Shampine 3(2) pair:
+// eq. (semi_2D)) with an explicit third-order, five-stage Runge-Kutta pair
+// that has the first-same-as-last (FSAL) property, an embedded error estimate
+// and automatic step-size control (Sec. 6); it does not print the pair.  The
+// five-stage pair of that kind is in sgn_p5.cuh; this file holds the second
+// pair sgn_step_adaptive offers (SGN_PAIR_BS3), the Bogacki-Shampine 3(2) pair:
 //   k1 = f(q_n)                      (the k4 of the previous accepted step)
 //   k2 = f(Y2),  Y2 = q_n + dt/2 k1
 //   k3 = f(Y3),  Y3 = q_n + 3dt/4 k2

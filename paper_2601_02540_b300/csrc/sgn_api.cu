@@ -433,7 +433,7 @@ sgn_status need_f64(const sgn_ctx* c, const char* what) {
     return SGN_OK;
 }
 
-// ---- adaptive integrator (Sec. 6): third-order FSAL pair, host-side control
+// ---- adaptive integrator (Sec. 6), second pair: Bogacki-Shampine 3(2), host-side control
 template <typename TC, int BC, int MODE>
 cudaError_t launch_bs3(const sgn_ctx* c, const sgn::BsArgs& a, cudaStream_t s) {
     auto kern = sgn::k_bs3_stage<TC, BC, MODE>;
