@@ -110,7 +110,10 @@ typedef struct sgn_ctx sgn_ctx;
 
 /* Create a context for one grid.  Validates `p`, allocates the scratch and
  * copies the bathymetry b_dev (double, nx*ny, device) into the context.
- * Synchronizes.  On failure *out is NULL. */
+ * Synchronizes.  On failure *out is NULL.  SGN_F64 contexts pick the tile
+ * height of their stage kernels for the current device: 32 x 8 tiles where
+ * 32 x 24 tiles would load the SMs unevenly (small grids), else 32 x 24; the
+ * results are the same either way. */
 SGN_API sgn_status sgn_create(const sgn_params* p, const void* b_dev, sgn_ctx** out);
 
 /* Free the context and its scratch.  Synchronizes.  NULL is a no-op. */

@@ -77,7 +77,9 @@ struct sgn_ctx {
     int* hflag = nullptr;        // pinned host copy
     long long nblk = 0;          // blocks of the stage launch
     long long nband = 0;         // 32 x 8 bands of the grid: partials of the diagnostics
-    dim3 grid;
+    dim3 grid;                   // blocks of the compute type's stage tile (StageShape)
+    int rows = 0;                // tile height of the RK4 / RHS / diagnostics launches of k_stage
+    dim3 grid1;                  // blocks of 32 x 8 tiles (rows == 1)
     double* adj = nullptr;       // adjoint scratch (FP64): accumulator + two cotangents
     double* bs = nullptr;        // adaptive integrator scratch (8-byte slots, 40 planes)
     double* rrk = nullptr;       // relaxation scratch (FP64): plain RK4 update (5 planes), partials, sums
@@ -129,13 +131,26 @@ cudaError_t smem_optin(size_t smem) {
     return err[dev];
 }
 
-template <typename TC, typename TIN, typename TA, int BC, int MODE>
+template <typename TC, typename TIN, typename TA, int BC, int MODE, int R = sgn::StageShape<TC>::rows>
 cudaError_t stage_attr() {
-    return smem_optin<sgn::k_stage<TC, TIN, TA, BC, MODE>>(sgn::stage_smem_bytes<TC, MODE>(sgn::StageShape<TC>::rows));
+    return smem_optin<sgn::k_stage<TC, TIN, TA, BC, MODE, R>>(sgn::stage_smem_bytes<TC, MODE>(R));
 }
 
+// The stage kernel with the context's tile height: FP64 contexts on small
+// grids use 32 x 8 tiles (c->rows == 1, see sgn_create), all others the
+// compute type's StageShape.
 template <typename TC, typename TIN, typename TA, int BC, int MODE>
 cudaError_t launch_stage(const sgn_ctx* c, const StageArgs<TC, TIN, TA>& a, cudaStream_t s) {
+    if constexpr (std::is_same<TC, double>::value) {
+        if (c->rows == 1) {
+            const cudaError_t attr_err = stage_attr<TC, TIN, TA, BC, MODE, 1>();
+            if (attr_err != cudaSuccess) return attr_err;
+            sgn::k_stage<TC, TIN, TA, BC, MODE, 1>
+                <<<c->grid1, dim3(sgn::TILE_X, sgn::THREADS_Y), sgn::stage_smem_bytes<TC, MODE>(1), s>>>(a);
+            count_launch();
+            return cudaGetLastError();
+        }
+    }
     const cudaError_t attr_err = stage_attr<TC, TIN, TA, BC, MODE>();
     if (attr_err != cudaSuccess) return attr_err;
     const size_t smem = sgn::stage_smem_bytes<TC, MODE>(sgn::StageShape<TC>::rows);
@@ -274,11 +289,18 @@ struct AttrOp {
     sgn_ctx* c;
     template <typename TC, typename TA, int BC>
     cudaError_t operator()() {
+        if constexpr (std::is_same<TC, double>::value) {
+            if (c->rows == 1) return attrs<TC, TA, BC, 1>();
+        }
+        return attrs<TC, TA, BC, sgn::StageShape<TC>::rows>();
+    }
+    template <typename TC, typename TA, int BC, int R>
+    cudaError_t attrs() {
         constexpr bool kK1 = sgn::kStoreK1<TC, TA>;     // the stage modes run_steps launches
-        cudaError_t e = stage_attr<TC, TA, TA, BC, kK1 ? sgn::MODE_S1K : sgn::MODE_S1>();
-        if (e == cudaSuccess) e = stage_attr<TC, TC, TA, BC, kK1 ? sgn::MODE_S2K : sgn::MODE_S2>();
-        if (e == cudaSuccess) e = stage_attr<TC, TC, TA, BC, sgn::MODE_S3>();
-        if (e == cudaSuccess) e = stage_attr<TC, TC, TA, BC, sgn::MODE_S4>();
+        cudaError_t e = stage_attr<TC, TA, TA, BC, kK1 ? sgn::MODE_S1K : sgn::MODE_S1, R>();
+        if (e == cudaSuccess) e = stage_attr<TC, TC, TA, BC, kK1 ? sgn::MODE_S2K : sgn::MODE_S2, R>();
+        if (e == cudaSuccess) e = stage_attr<TC, TC, TA, BC, sgn::MODE_S3, R>();
+        if (e == cudaSuccess) e = stage_attr<TC, TC, TA, BC, sgn::MODE_S4, R>();
         return e;
     }
 };
@@ -895,6 +917,24 @@ sgn_status sgn_create(const sgn_params* p, const void* b_dev, sgn_ctx** out) {
     c->grid = dim3((p->nx + sgn::TILE_X - 1) / sgn::TILE_X, (p->ny + tile_y - 1) / tile_y);
     c->nblk = (long long)c->grid.x * c->grid.y;
     c->nband = (long long)c->grid.x * ((p->ny + sgn::THREADS_Y - 1) / sgn::THREADS_Y);   // >= nblk
+    c->grid1 = dim3(c->grid.x, (unsigned)((p->ny + sgn::THREADS_Y - 1) / sgn::THREADS_Y));
+    c->rows = tile_y / sgn::THREADS_Y;
+    if (p->prec == SGN_F64) {
+        // The FP64 stage kernels are bound by each SM's FP64 pipe, so a launch
+        // takes as long as its most loaded SM: with b blocks over S SMs that is
+        // ceil(b/S) blocks against b/S on average.  32 x 8 tiles (four times the
+        // blocks) recompute more halo operands (x 1.33 instead of x 1.15: about
+        // 3.4% more FP64 work); they are used where their balance wins by 5%.
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0) {
+            auto balance = [&](double blocks) { return blocks / sms / std::ceil(blocks / sms); };
+            const double b3 = (double)c->grid.x * c->grid.y, b1 = (double)c->grid1.x * c->grid1.y;
+            if (c->grid1.y <= 65535 && balance(b1) / 1.034 > 1.05 * balance(b3)) c->rows = 1;
+        } else {
+            cudaGetLastError();
+        }
+    }
 
     const size_t plane = (size_t)G.plane;
     bool ok = cudaMalloc(&c->b64, plane * sizeof(double)) == cudaSuccess;

@@ -1002,12 +1002,13 @@ constexpr int kStageMinBlocks =
     : (kStoreK1<TC, TA> && (MODE == MODE_S1K || (MODE == MODE_S4 && BC == BC_PERIODIC))) ? SGN_F32_LIGHT_MINB
                                                                                           : StageMinBlocks<TC, TA>::value;
 
-template <typename TC, typename TIN, typename TA, int BC, int MODE>
+// R: rows per thread (tile height 8 R); the compute type's StageShape, or 1
+// for FP64 grids too small to spread 32 x 24 tiles evenly over the SMs.
+template <typename TC, typename TIN, typename TA, int BC, int MODE, int R = StageShape<TC>::rows>
 __global__ void __launch_bounds__(BLOCK_THREADS, (kStageMinBlocks<TC, TA, MODE, BC>))
 k_stage(StageArgs<TC, TIN, TA> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TC* sm = reinterpret_cast<TC*>(smem_raw);
-    constexpr int R = StageShape<TC>::rows;
     // band partials in band-major order: band (blockIdx.y R + ry), column block blockIdx.x
     stage_tile<TC, TIN, TA, BC, MODE, R>(a, a.G, blockIdx.x * TILE_X, blockIdx.y * (THREADS_Y * R), sm,
                                          a.partials ? a.partials + (blockIdx.y * R * (long long)gridDim.x +
