@@ -473,8 +473,10 @@ def _adjoint(torch, nsteps: int = 0) -> dict:
     every 10 steps, checkpoints every 100 steps; time of the forward rollout
     (with checkpoints; the last segment keeps its stage states) and of the
     backward pass (recomputation of the other segments with stage stashes +
-    adjoint steps), and the same with every stage state kept (no
-    recomputation)."""
+    adjoint steps): with the tapes of the stage RHS evaluations recorded by
+    the recomputation (the default), without them (the adjoint evaluates
+    each stage's tape), and with every stage state kept (no recomputation,
+    no tape)."""
     from paper_2601_02540_b300 import adjoint, sgn
     p = inputs.workload4()
     if nsteps > 0:
@@ -485,17 +487,20 @@ def _adjoint(torch, nsteps: int = 0) -> dict:
     h0 = torch.as_tensor(p.q0[0], device="cuda").requires_grad_(True)
     obs = torch.zeros((p.nsteps // p.extra["every"], gauges.numel()), dtype=torch.float64, device="cuda")
     # warm-up with the same operations (loads every kernel module once)
-    out = adjoint.gauge_rollout(b, h0, s, p.dt, 20, p.extra["every"], gauges, 10)
-    torch.sum((out - obs[: out.shape[0]]) ** 2).backward()
-    b.grad = None
-    h0.grad = None
+    for tape in (True, False):
+        out = adjoint.gauge_rollout(b, h0, s, p.dt, 20, p.extra["every"], gauges, 10, tape)
+        torch.sum((out - obs[: out.shape[0]]) ** 2).backward()
+        b.grad = None
+        h0.grad = None
     res = {"workload": f"reflecting 512x512, {p.nsteps} RK4 steps, 16 gauges every 10 steps, FP64"}
-    for name, K in (("checkpoint_K100", 100), ("all_stages_kept", 0)):
+    TP = 4 * sgn.TAPE_PLANES
+    for name, K, tape in (("checkpoint_K100", 100, True), ("checkpoint_K100_no_tape", 100, False),
+                          ("all_stages_kept", 0, False)):
         b.grad = None
         h0.grad = None
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        out = adjoint.gauge_rollout(b, h0, s, p.dt, p.nsteps, p.extra["every"], gauges, K)
+        out = adjoint.gauge_rollout(b, h0, s, p.dt, p.nsteps, p.extra["every"], gauges, K, tape)
         loss = torch.sum((out - obs) ** 2)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
@@ -507,7 +512,8 @@ def _adjoint(torch, nsteps: int = 0) -> dict:
                      "total_over_forward": (fwd + bwd) / fwd,
                      # K > 0: two K-step stashes (the recomputation of the next segment
                      # overlaps the walk of the current one)
-                     "stash_gb": ((2 * min(K, p.nsteps)) if K > 0 else p.nsteps) * 20 * p.nx * p.ny * 8 / 1e9}
+                     "stash_gb": ((2 * min(K, p.nsteps)) if K > 0 else p.nsteps) * 20 * p.nx * p.ny * 8 / 1e9,
+                     "tape_gb": (2 * min(K, p.nsteps) * TP * p.nx * p.ny * 8 / 1e9) if tape else 0.0}
         del out, loss
         torch.cuda.empty_cache()
     s.close()

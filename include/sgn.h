@@ -24,8 +24,9 @@
  *   sgn_step_adaptive  adaptive time integration with an embedded
  *                    five-stage third-order FSAL pair and step-size control
  *                    (Sec. 6).
- *   sgn_rhs_vjp, sgn_step_record, sgn_step_vjp   the discrete adjoint of the
- *                    RHS and of one RK4 step (no counterpart in the paper).
+ *   sgn_rhs_vjp, sgn_step_record, sgn_step_vjp, sgn_step_record_tape,
+ *   sgn_step_vjp_tape   the discrete adjoint of the RHS and of one RK4 step
+ *                    (no counterpart in the paper).
  *
  * Data layout.  A state is five planes (h, u, v, w, eta), each plane nx*ny
  * values, x fastest: element (f, j, i) at index f*nx*ny + j*nx + i.  Node
@@ -193,8 +194,11 @@ SGN_API sgn_status sgn_mass_energy_noalloc(const sgn_params* p, const void* b_de
  *   qbar_dev  = J(q)^T abar            (overwritten, five planes)
  *   bbar_dev += (d RHS / d b)^T abar   (accumulated, one plane)
  * All double, device; qbar_dev must not overlap q_dev or abar_dev.  SGN_F64
- * contexts only (else SGN_E_UNSUPPORTED).  The first adjoint call of a context
- * allocates 43 planes of scratch (SGN_E_NOMEM if that fails).  Asynchronous. */
+ * contexts only (else SGN_E_UNSUPPORTED).  Three launches: the tape of the
+ * RHS at q (its intermediate values, SGN_TAPE_PLANES planes, written by the
+ * FP64 stage kernel), then the two adjoint passes, which read it.  The first
+ * adjoint call of a context allocates 62 planes of scratch (SGN_E_NOMEM if
+ * that fails).  Asynchronous. */
 SGN_API sgn_status sgn_rhs_vjp(sgn_ctx* ctx, const void* q_dev, const void* abar_dev, void* qbar_dev,
                                void* bbar_dev, void* stream);
 
@@ -212,14 +216,37 @@ SGN_API sgn_status sgn_step_record(sgn_ctx* ctx, void* q_dev, double dt, int nst
  * k3bar = dt/3 qbar' + dt Q4bar, Q3bar = J(Q3)^T k3bar, k2bar = dt/3 qbar' +
  * dt/2 Q3bar, Q2bar = J(Q2)^T k2bar, k1bar = dt/6 qbar' + dt/2 Q2bar,
  * Q1bar = J(q_n)^T k1bar, qbar = qbar' + Q1bar + Q2bar + Q3bar + Q4bar, and
- * bbar_dev += sum_s (d RHS / d b)(Q_s)^T ks_bar.  Eight launches (two per
- * stage).  Internally the stage cotangents are carried with the scales
+ * bbar_dev += sum_s (d RHS / d b)(Q_s)^T ks_bar.  Twelve launches (per
+ * stage: the tape of the RHS at Q_s, then the two adjoint passes).
+ * Internally the stage cotangents are carried with the scales
  * dt/6, dt^2/6, dt^3/12, dt^4/24 factored out; a dt for which dt^4/24 is not a
  * normal double returns SGN_E_INVAL.  The first adjoint call of a context
- * allocates 43 planes of scratch (SGN_E_NOMEM if that fails).  SGN_F64 only.
+ * allocates 62 planes of scratch (SGN_E_NOMEM if that fails).  SGN_F64 only.
  * Asynchronous. */
 SGN_API sgn_status sgn_step_vjp(sgn_ctx* ctx, const void* stash_dev, void* qbar_dev, void* bbar_dev,
                                 double dt, void* stream);
+
+/* Planes of the tape of one RHS evaluation: per node, intermediate values of
+ * the RHS (1/h, -P2/h, the unscaled differences of h, u, v, w, eta + 3/2 b,
+ * u^2, v^2, the continuity fluxes A_x, A_y, D_x(hu) - A_x, D_y(hv) - A_y and
+ * the RHS of u, v, w), which the adjoint passes read instead of recomputing. */
+#define SGN_TAPE_PLANES 21
+
+/* Like sgn_step_record, and the stage kernels also write the tapes of the
+ * step's four RHS evaluations: before step n the tape slot n
+ * (4 * SGN_TAPE_PLANES planes at tape_dev + 4 * SGN_TAPE_PLANES * n * nx*ny
+ * doubles) receives [T(q_n) | T(Q2) | T(Q3) | T(Q4)].  The stage states and
+ * q_{n+1} are those of sgn_step_record bit for bit.  tape_dev: caller-owned,
+ * device, double, nsteps slots, 16-byte aligned; NULL with nsteps > 0 is
+ * SGN_E_INVAL.  SGN_F64 only.  Asynchronous. */
+SGN_API sgn_status sgn_step_record_tape(sgn_ctx* ctx, void* q_dev, double dt, int nsteps, void* stash_dev,
+                                        void* tape_dev, void* stream);
+
+/* sgn_step_vjp with the step's tapes from sgn_step_record_tape (one tape slot,
+ * 4 * SGN_TAPE_PLANES planes): eight launches (two per stage) and the same
+ * results as sgn_step_vjp bit for bit.  NULL tape_dev is SGN_E_INVAL. */
+SGN_API sgn_status sgn_step_vjp_tape(sgn_ctx* ctx, const void* stash_dev, const void* tape_dev,
+                                     void* qbar_dev, void* bbar_dev, double dt, void* stream);
 
 /* ---- Manufactured solution (Sec. 6.1.2) ----------------------------------
  * The paper verifies the full 2D scheme, both boundary treatments, with the

@@ -15,10 +15,18 @@ segment, last to first, recompute it from its checkpoint with
 ``sgn_step_record`` (except the last), then walk its steps backwards with
 ``sgn_step_vjp``, adding the gauge cotangents to qbar_h at the observation
 steps.  The recomputation of the next segment runs on a second CUDA stream
-while the current one is walked, so the two overlap on the GPU.  Memory: two
-K-step stashes, 20 planes per step (4.2 GB each at 512^2 for K = 100).  K <= 0 keeps the stage states of every step during the forward pass
-instead (no recomputation; 84 GB at 512^2 for 2000 steps, which fits in a
-B300's HBM).
+while the current one is walked, so the two overlap on the GPU.
+
+With ``tape`` (K > 0), the recorded segments also keep the tapes of their
+stage RHS evaluations (``sgn_step_record_tape``: the intermediate values of
+the RHS, written by the stage kernels as they advance the state), and the
+walk reads them (``sgn_step_vjp_tape``) instead of evaluating them again:
+the adjoint then costs two launches per stage instead of three.  Memory: two
+K-step stashes of 20 planes per step, plus with the tape two of 84 planes
+per step (4.2 GB and 17.6 GB at 512^2 for K = 100).  ``tape=None`` takes the
+tape when it fits in half of the free device memory.  K <= 0 keeps the stage
+states of every step during the forward pass instead (no recomputation and
+no tape; 84 GB at 512^2 for 2000 steps, which fits in a B300's HBM).
 
 The gauge sampling, the seed injection and the checkpoint copies are small
 torch tensor operations; every RHS, stage and adjoint evaluation runs in the
@@ -34,7 +42,7 @@ from . import sgn
 class GaugeRollout(torch.autograd.Function):
     @staticmethod
     def forward(ctx, b, h0, solver: sgn.Solver, dt: float, nsteps: int, every: int,
-                gauges: torch.Tensor, K: int):
+                gauges: torch.Tensor, K: int, tape: bool | None = None):
         assert solver.prec == "f64", "the adjoint runs in FP64"
         ny, nx = h0.shape
         b = b.detach().to(torch.float64).contiguous()
@@ -45,15 +53,22 @@ class GaugeRollout(torch.autograd.Function):
         nobs = nsteps // every
         obs = torch.empty((nobs, gauges.numel()), dtype=torch.float64, device=h0.device)
         checkpoints = {}
-        stash = None
+        stash = tapes = None
         last = 0
+        TP = 4 * sgn.TAPE_PLANES
         if K <= 0:
             # keep every step's stage states (no recomputation in the backward pass)
+            tape = False
             stash = torch.empty((nsteps, 20, ny, nx), dtype=torch.float64, device=h0.device)
         elif nsteps > 0:
             # the last segment keeps its stage states (stash indexed from its start)
             last = ((nsteps - 1) // K) * K
+            if tape is None:
+                need = 2 * min(K, nsteps) * (20 + TP) * ny * nx * 8
+                tape = need <= 0.5 * torch.cuda.mem_get_info(h0.device)[0]
             stash = torch.empty((nsteps - last, 20, ny, nx), dtype=torch.float64, device=h0.device)
+            if tape:
+                tapes = torch.empty((nsteps - last, TP, ny, nx), dtype=torch.float64, device=h0.device)
         step = 0
         while step < nsteps:
             if K > 0 and step % K == 0 and step < last:
@@ -64,7 +79,8 @@ class GaugeRollout(torch.autograd.Function):
             if K > 0 and step < last:
                 solver.step(q, dt, nxt - step)
             else:
-                solver.step_record(q, dt, nxt - step, stash[step - last:nxt - last])
+                solver.step_record(q, dt, nxt - step, stash[step - last:nxt - last],
+                                   tapes[step - last:nxt - last] if tapes is not None else None)
             step = nxt
             if step % every == 0:
                 obs[step // every - 1] = q[0].reshape(-1)[gauges]
@@ -72,6 +88,7 @@ class GaugeRollout(torch.autograd.Function):
         ctx.gauges = gauges
         ctx.checkpoints = checkpoints
         ctx.stash = stash
+        ctx.tapes = tapes
         ctx.last = last
         ctx.shape = (ny, nx)
         ctx.b = b
@@ -105,7 +122,10 @@ class GaugeRollout(torch.autograd.Function):
             side = torch.cuda.Stream(dev)
             side.wait_stream(main)
             Kmax = max(L for _, L in order)
+            taped = ctx.tapes is not None
+            TP = 4 * sgn.TAPE_PLANES
             bufs = [ctx.stash, None]
+            tbufs = [ctx.tapes, None]
             ready = [None] * len(order)             # recomputation of segment k done
             done = [None] * len(order)              # walk of segment k done
 
@@ -114,11 +134,13 @@ class GaugeRollout(torch.autograd.Function):
                 slot = k % 2
                 if bufs[slot] is None or bufs[slot].shape[0] < L:
                     bufs[slot] = torch.empty((Kmax, 20, ny, nx), dtype=torch.float64, device=dev)
+                    if taped:
+                        tbufs[slot] = torch.empty((Kmax, TP, ny, nx), dtype=torch.float64, device=dev)
                 with torch.cuda.stream(side):
                     if k >= 2:
                         side.wait_event(done[k - 2])    # the walk that used this buffer
                     q = ctx.checkpoints[s0].clone()
-                    solver.step_record(q, dt, L, bufs[slot])
+                    solver.step_record(q, dt, L, bufs[slot], tbufs[slot] if taped else None)
                     ready[k] = torch.cuda.Event()
                     ready[k].record(side)
 
@@ -128,11 +150,12 @@ class GaugeRollout(torch.autograd.Function):
                 if k > 0:
                     main.wait_event(ready[k])
                 stash = bufs[k % 2]
+                tp = tbufs[k % 2]
                 for n in reversed(range(L)):
                     g = s0 + n + 1                  # this step produces q_g
                     if g % every == 0:
                         qbar[0].reshape(-1).index_add_(0, gauges, grad_obs[g // every - 1])
-                    solver.step_vjp(stash[n], qbar, bbar, dt)
+                    solver.step_vjp(stash[n], qbar, bbar, dt, tp[n] if taped else None)
                 done[k] = torch.cuda.Event()
                 done[k].record(main)
                 if k + 2 < len(order):
@@ -145,10 +168,10 @@ class GaugeRollout(torch.autograd.Function):
                 if g % every == 0:
                     qbar[0].reshape(-1).index_add_(0, gauges, grad_obs[g // every - 1])
                 solver.step_vjp(stash[n], qbar, bbar, dt)
-        ctx.stash = None
+        ctx.stash = ctx.tapes = None
         h0bar = qbar[0] + qbar[4]
-        return bbar, h0bar, None, None, None, None, None, None
+        return bbar, h0bar, None, None, None, None, None, None, None
 
 
-def gauge_rollout(b, h0, solver, dt, nsteps, every, gauges, K=100):
-    return GaugeRollout.apply(b, h0, solver, dt, nsteps, every, gauges, K)
+def gauge_rollout(b, h0, solver, dt, nsteps, every, gauges, K=100, tape=None):
+    return GaugeRollout.apply(b, h0, solver, dt, nsteps, every, gauges, K, tape)

@@ -1,64 +1,59 @@
 // sgn_adjoint.cuh - the exact discrete adjoint (vector-Jacobian product) of the
 // split-form SBP right-hand side and of one classical RK4 step.  The paper has
 // no adjoint; this is the transpose of the Jacobian of the RHS of
-// eq. (sd_periodic_2D_SGN) / eq. (semi_2D) as the forward kernels evaluate it.
+// eq. (sd_periodic_2D_SGN) / eq. (semi_2D) in the regrouped form the forward
+// kernels evaluate (node_rhs_src), differentiated step by step in reverse.
 //
-// Structure.  At node c the RHS is  k_f(c) = sum_t coef_{f,t}(q_c, b_c) (D P_t)(c)
-// + pointwise_f(q_c), where P_t are the differentiated products of the forward
-// kernel and every coefficient depends on node c only.  So for a cotangent a:
-//   - "pointwise" part: d k_f / d q_c with every D P_t held fixed (needs the
-//     differences at c);
-//   - "product" part: P̄_t(n) = sum_c D_{c,n} V_t(c) with
-//     V_t(c) = sum_f a_f(c) coef_{f,t}(c) (the row factor of D included), a
-//     gather over the rows c of the SBP operator that touch column n
-//     (periodic: V(n-1) - V(n+1); reflecting: V(n-1) for n >= 1, -V(n+1) for
-//     n <= N-2, and the one-sided end rows add +V(N-1) at n = N-1 and -V(0) at
-//     n = 0), then the chain rule through P_t(q_n, b_n).
-// Two passes, both one node per thread and free of halos and atomics:
-//   k_adj_weights  products P_t, 1/h and the 20 direction weights of each node
-//                  into scratch planes;
-//   k_adj_gather   differences, pointwise part, gathers of the weights of the
-//                  neighbours, chain rule, and (stage mode) the reverse RK4
-//                  stage algebra.
-// The kernels are FP64-pipe bound, so the formulas are arranged for the fewest
-// FP64 instructions: h r = 1 (r = 1/h) is used to cancel factors exactly up to
-// rounding, constant factors of the differences are folded on the host, and
-// the cotangent of a stage is carried as sigma * A with the scale sigma applied
-// only where a result is accumulated (see AdjArgs).
+// Structure.  At node c the forward RHS is a function of
+//   - the operands of node c itself: h, u, v, w, rho = eta/h, r = 1/h,
+//     hu, hv and P2 = 2g h(h+b) - lam/3 eta^2/h, and
+//   - twenty unscaled differences d(c) = f(R(c)) - f(L(c)) of operand planes
+//     f (x: h, u, v, w, F = eta + 3/2 b, P2, u^2, hu, huv, huw; y: h, u, v, w,
+//     F, P2, v^2, hv, huv, hvw), where R, L are the right and left neighbours
+//     (the node itself on a reflecting wall: the one-sided end rows).
+// For a cotangent a at c, reverse differentiation of node_rhs_src gives the
+// cotangents of the twenty differences ("weights" W) and of the node's own
+// operands; a difference weight W(c) reaches the operand f at node n through
+// the transposed operator, sum_c W(c) (delta(R(c), n) - delta(L(c), n)).
+// Two passes per RK stage, both one node per thread, without halos or atomics:
+//   k_adj_point   the weights and the node's own part (pointwise, no neighbours);
+//   k_adj_gather  gathers the neighbours' weights, adds the node's own part,
+//                 applies the chain rule from the operands to (h, u, v, w, eta, b),
+//                 and (stage mode) the reverse RK4 stage algebra.
+// The forward intermediates the reverse sweep needs (differences, A_x, A_y,
+// D(hu) - A_x, k_u, k_v, k_w, 1/h, -P2/h) are not recomputed: they come from
+// the tape of the forward evaluation at the same state (TP_ planes), written
+// by the FP64 stage kernel while it advances the state (sgn_step_record_tape)
+// or by a TAPE-mode launch.  The kernels are FP64-pipe bound, so the formulas
+// use the fewest FP64 operations: r h = 1 cancels factors exactly up to
+// rounding (the derivatives of k_u, k_v, k_w with respect to r are k/r), and
+// the cotangent of a stage is carried as sigma * A with the scale sigma
+// applied only where a result is accumulated (see AdjArgs).
 #pragma once
 
 #include "sgn_kernels.cuh"
 
 namespace sgn {
 
-// scratch layout (planes): the differentiated products and 1/h (the state
-// planes themselves are read from the state), then the x weights (10) and the
-// y weights (10).  P = g h(h+b) - lam/6 eta^2/h: g D(h(h+b)) - lam/6 D(eta^2/h)
-// = D P (D is linear), so the two products of the brackets share one plane
-// and one weight slot.
-enum { AP_P, AP_HU, AP_HV, AP_HUV, AP_HUW, AP_HVW, AP_E15, AP_R, ADJ_NP };
-constexpr int ADJ_NW = 10;
-constexpr int ADJ_WX = ADJ_NP;
-constexpr int ADJ_WY = ADJ_NP + ADJ_NW;
-constexpr int ADJ_SCRATCH_PLANES = ADJ_NP + 2 * ADJ_NW;
+// Weight planes (cotangents of the unscaled differences at each node): x
+// uses {H, U, V, W, F, P2, UU, HU, HUV, HUW}, y uses {H, U, V, W, F, P2, VV,
+// HV, HUV, HVW}; slot k of x and slot k of y differentiate the same operand
+// for k < VW_SQ and for VW_HUV.
+enum { VW_H, VW_U, VW_V, VW_W, VW_F, VW_P2, VW_SQ, VW_HM, VW_HUV, VW_HMW, ADJ_NW };
+// the node's own part of the cotangents of h, u, v, w, eta (the operands
+// rho, r, hu, hv already reduced to them) and of its P2
+enum { AC_H, AC_U, AC_V, AC_W, AC_E, AC_P2, ADJ_NC };
+constexpr int ADJ_WX = 0;
+constexpr int ADJ_WY = ADJ_NW;
+constexpr int ADJ_C = 2 * ADJ_NW;
+constexpr int ADJ_SCRATCH_PLANES = 2 * ADJ_NW + ADJ_NC;
 constexpr int ADJ_BLOCK = 256;
-
-// weight slots: x uses {H,U,V,W,E15,P,UU,HU,HUV,HUW},
-// y uses {H,U,V,W,E15,P,VV,HV,HUV,HVW}.  eta and b enter the forward RHS
-// only through eta + 3/2 b and P, so one E15 slot carries both
-// (d/d eta = 1, d/d b = 3/2).
-enum { VW_H, VW_U, VW_V, VW_W, VW_E15, VW_P, VW_SQ, VW_HM, VW_HUV, VW_HMW };
 
 enum { ADJ_MODE_RHS = 0, ADJ_MODE_STAGE = 1 };
 
-// Per-direction constants of the pointwise part, for interior rows ([0]) and
-// the one-sided boundary rows ([1]): s = row factor of D, hs = s/2.
-struct AdjDir {
-    double s, hs;
-};
-
 struct AdjArgs {
     const double* X;       // state at which the Jacobian is taken (5 planes)
+    const double* tape;    // the tape of f(X) (N_TAPE planes)
     const double* b;       // bathymetry
     const double* A;       // cotangent direction (5 planes); the cotangent is sigma * A
     double sigma;          // scale of the cotangent, applied to every result
@@ -77,105 +72,135 @@ struct AdjArgs {
     double kappa;
     int first;
     Geom G;
-    AdjDir kx[2], ky[2];
     int* flag;             // latched error bits (FLAG_BOUNDS of checked builds)
-    double m2lam3;         // -2 lambda / 3
-    double lam2x;          // 2 lambda
 };
-
-// Host: the derived constants of AdjArgs.
-inline void fill_adj_constants(AdjArgs& a) {
-    const Geom& G = a.G;
-    const double sx[2] = {G.cx2, G.cx1}, sy[2] = {G.cy2, G.cy1};
-    for (int k = 0; k < 2; k++) {
-        a.kx[k] = {sx[k], 0.5 * sx[k]};
-        a.ky[k] = {sy[k], 0.5 * sy[k]};
-    }
-    a.m2lam3 = -2.0 * G.lam3;
-    a.lam2x = 2.0 * G.lam;
-}
 
 // x with its sign bit flipped where m has it set (an exact negation).
 __device__ __forceinline__ double flip_sign(double x, unsigned long long m) {
     return __longlong_as_double((long long)((unsigned long long)__double_as_longlong(x) ^ m));
 }
 
-// Pass 1: products, 1/h and the direction weights V^x, V^y of one node
-// (for the cotangent direction A; sigma is applied by the gather pass).
+// Pass 1: the difference weights and the node's own cotangents at one node,
+// for the cotangent direction A (sigma is applied by the gather pass).  The
+// names follow node_rhs_src: Xu, Yu, ... are its bracket sums, A_x, A_y its
+// continuity fluxes, base2 = -P2/h, lom2 = 2 lam/3 (1 - rho), and a trailing
+// "b" marks a cotangent.
 template <int BC>
-__global__ void __launch_bounds__(ADJ_BLOCK) k_adj_weights(AdjArgs a) {
+__global__ void __launch_bounds__(ADJ_BLOCK) k_adj_point(AdjArgs a) {
     const Geom& G = a.G;
     const long long P = G.plane;
     const long long c = (long long)blockIdx.x * ADJ_BLOCK + threadIdx.x;
     if (c >= P) return;
     const int j = (int)(c / G.nx), i = (int)(c - (long long)j * G.nx);
-    const double h = a.X[c], u = a.X[P + c], v = a.X[2 * P + c], w = a.X[3 * P + c];
-    const double eta = a.X[4 * P + c], bb = a.b[c];
-    const double r = recip<double>(h);
-    const double hu = h * u, hv = h * v;
-    const double hsum = h + bb, rho = eta * r;
-    double* S = a.scratch;
-    S[AP_P * P + c] = fma(G.g * h, hsum, -(G.lam6 * rho) * eta);
-    S[AP_HU * P + c] = hu;
-    S[AP_HV * P + c] = hv;
-    S[AP_HUV * P + c] = hu * v;
-    S[AP_HUW * P + c] = hu * w;
-    S[AP_HVW * P + c] = hv * w;
-    S[AP_E15 * P + c] = fma(1.5, bb, eta);
-    S[AP_R * P + c] = r;
+    const double* __restrict__ T = a.tape + c;
+    const double r = T[TP_R * P], base2 = T[TP_BASE2 * P];
+    const double dxh = T[TP_DXH * P], dyh = T[TP_DYH * P], dxu = T[TP_DXU * P], dyu = T[TP_DYU * P];
+    const double dxv = T[TP_DXV * P], dyv = T[TP_DYV * P], dxw = T[TP_DXW * P], dyw = T[TP_DYW * P];
+    const double dxf = T[TP_DXF * P], dyf = T[TP_DYF * P], dxuu = T[TP_DXUU * P], dyvv = T[TP_DYVV * P];
+    const double xhu = T[TP_XHU * P], yhv = T[TP_YHV * P], Ax = T[TP_AX * P], Ay = T[TP_AY * P];
+    const double ku = T[TP_KU * P], kv = T[TP_KV * P], kw = T[TP_KW * P];
+    const double h = a.X[c], u = a.X[P + c], v = a.X[2 * P + c], w = a.X[3 * P + c], eta = a.X[4 * P + c];
+    const double ah = a.A[c], au = a.A[P + c], av = a.A[2 * P + c], aw = a.A[3 * P + c], ae = a.A[4 * P + c];
 
-    const double ah = a.A[c], au = a.A[P + c], av = a.A[2 * P + c];
-    const double aw = a.A[3 * P + c], ae = a.A[4 * P + c];
-    const double lom = G.lam3 * (1.0 - rho);                       // lam/3 (1 - rho)
-    const double cc = fma(G.lam6 * rho, rho, -G.g * hsum);         // lam/6 rho^2 - g (h + b)
-    const double ra = -r * au, rb = -r * av, rc = (-0.5 * r) * aw; // d k / d B for u, v, w
-    // The D h and D u weights share T = s a_h + (r/2) s (u a_u + v a_v + w a_w)
-    // (the coefficients of the continuity flux u D h + h D u in the h equation
-    // and in the split brackets): V_h = -r s a_u (lam/6 rho^2 - g (h+b)) - u T,
-    // V_u = -h T (and the same with v for y).
-    // x weights (row factor s of column i)
-    {
-        const bool wall = BC == BC_REFLECTING && (i == 0 || i == G.nx - 1);
-        const double sx = wall ? a.kx[1].s : a.kx[0].s, hsx = wall ? a.kx[1].hs : a.kx[0].hs;
-        const double ru = sx * ra, rw = sx * rc, sah = sx * ah, sae = sx * ae;
-        const double hru = 0.5 * ru, hrv = hsx * rb;
-        const double T = fma(hru, u, fma(hrv, v, fma(rw, w, sah)));
-        double* W = S + ADJ_WX * P + c;
-        W[VW_H * P] = fma(ru, cc, -u * T);
-        W[VW_U * P] = -h * T;
-        W[VW_V * P] = hrv * hu;
-        W[VW_W * P] = rw * hu;
-        W[VW_E15 * P] = fma(ru, lom, -u * sae);
-        W[VW_P * P] = ru;
-        W[VW_SQ * P] = hru * h;          // u^2
-        W[VW_HM * P] = hru * u;          // hu
-        W[VW_HUV * P] = hrv;
-        W[VW_HMW * P] = rw;              // huw
+    // the operator's row factors at this node (one-sided rows on a reflecting wall)
+    const bool wx = BC == BC_REFLECTING && (i == 0 || i == G.nx - 1);
+    const bool wy = BC == BC_REFLECTING && (j == 0 || j == G.ny - 1);
+    const double sx = wx ? G.cx1 : G.cx2, hsx = wx ? G.hcx1 : G.hcx2;
+    const double sy = wy ? G.cy1 : G.cy2, hsy = wy ? G.hcy1 : G.hcy2;
+
+    const double rho = eta * r;
+    const double lom2 = fma(-G.lam23, rho, G.lam23);
+    const double hu = h * u, hv = h * v;
+    const double al = r * hsx, be = r * hsy;           // hrsx, hrsy of the forward
+    // k_u = -(al Xu + be Yu), k_v = -(be Yv + al Xv), k_w = r lam (1 - rho) - (al Xw + be Yw)
+    const double Xub = -al * au, Yub = -be * au;
+    const double Yvb = -be * av, Xvb = -al * av;
+    const double Xwb = -al * aw, Ywb = -be * aw;
+    // k_h = -(sx A_x + sy A_y) + SAT, k_eta = w - u sx D_x F - v sy D_y F
+    const double ex = sx * ae, ey = sy * ae;
+
+    // Xu = base2 dxh + dxP2 + u (dxhu - A_x) + h dxuu + lom2 dxf and Xv, Xw into A_x
+    const double WxHU = Xub * u, WxUU = Xub * h;
+    double Axb = fma(-sx, ah, -WxHU);
+    Axb = fma(-Xvb, v, Axb);
+    Axb = fma(-Xwb, w, Axb);
+    const double WyHV = Yvb * v, WyVV = Yvb * h;
+    double Ayb = fma(-sy, ah, -WyHV);
+    Ayb = fma(-Yub, u, Ayb);
+    Ayb = fma(-Ywb, w, Ayb);
+
+    double* __restrict__ S = a.scratch + c;
+    double* WX = S + ADJ_WX * P;
+    double* WY = S + ADJ_WY * P;
+    WX[VW_H * P] = fma(Xub, base2, Axb * u);
+    WX[VW_U * P] = Axb * h;
+    WX[VW_V * P] = Xvb * hu;
+    WX[VW_W * P] = Xwb * hu;
+    WX[VW_F * P] = fma(Xub, lom2, -u * ex);
+    WX[VW_P2 * P] = Xub;
+    WX[VW_SQ * P] = WxUU;
+    WX[VW_HM * P] = WxHU;
+    WX[VW_HUV * P] = Xvb;
+    WX[VW_HMW * P] = Xwb;
+    WY[VW_H * P] = fma(Yvb, base2, Ayb * v);
+    WY[VW_U * P] = Yub * hv;
+    WY[VW_V * P] = Ayb * h;
+    WY[VW_W * P] = Ywb * hv;
+    WY[VW_F * P] = fma(Yvb, lom2, -v * ey);
+    WY[VW_P2 * P] = Yvb;
+    WY[VW_SQ * P] = WyVV;
+    WY[VW_HM * P] = WyHV;
+    WY[VW_HUV * P] = Yub;
+    WY[VW_HMW * P] = Ywb;
+
+    // the node's own operands
+    double ub = fma(Xub, xhu, -ex * dxf);
+    ub = fma(-Yub, Ay, ub);
+    ub = fma(Axb, dxh, ub);
+    double vb = fma(Yvb, yhv, -ey * dyf);
+    vb = fma(-Xvb, Ax, vb);
+    vb = fma(Ayb, dyh, vb);
+    double wb = fma(-Xwb, Ax, ae);
+    wb = fma(-Ywb, Ay, wb);
+    double hb = fma(Yvb, dyvv, Xub * dxuu);
+    hb = fma(Axb, dxu, hb);
+    hb = fma(Ayb, dyv, hb);
+    double hub = fma(Xvb, dxv, Xwb * dxw);
+    double hvb = fma(Yub, dyu, Ywb * dyw);
+    if (BC == BC_REFLECTING) {
+        // SAT of the h equation: -+ satx hu, -+ saty hv on the walls
+        if (i == 0) hub = fma(-G.satx, ah, hub);
+        if (i == G.nx - 1) hub = fma(G.satx, ah, hub);
+        if (j == 0) hvb = fma(-G.saty, ah, hvb);
+        if (j == G.ny - 1) hvb = fma(G.saty, ah, hvb);
     }
-    // y weights (row factor s of row j)
-    {
-        const bool wall = BC == BC_REFLECTING && (j == 0 || j == G.ny - 1);
-        const double sy = wall ? a.ky[1].s : a.ky[0].s, hsy = wall ? a.ky[1].hs : a.ky[0].hs;
-        const double rv = sy * rb, rw = sy * rc, sah = sy * ah, sae = sy * ae;
-        const double hrv = 0.5 * rv, hru = hsy * ra;
-        const double T = fma(hru, u, fma(hrv, v, fma(rw, w, sah)));
-        double* W = S + ADJ_WY * P + c;
-        W[VW_H * P] = fma(rv, cc, -v * T);
-        W[VW_V * P] = -h * T;
-        W[VW_U * P] = hru * hv;
-        W[VW_W * P] = rw * hv;
-        W[VW_E15 * P] = fma(rv, lom, -v * sae);
-        W[VW_P * P] = rv;
-        W[VW_SQ * P] = hrv * h;          // v^2
-        W[VW_HM * P] = hrv * v;          // hv
-        W[VW_HUV * P] = hru;
-        W[VW_HMW * P] = rw;              // hvw
-    }
+    const double Bb = fma(Xub, dxh, Yvb * dyh);        // base2
+    const double Lb = fma(Xub, dxf, Yvb * dyf);        // lom2
+    // r: d k_f / d r = k_f / r = h k_f (f = u, v, w), d base2 / d r = h base2
+    const double rb = h * fma(Bb, base2, fma(aw, kw, fma(av, kv, au * ku)));
+    // rho: lom2 and k_w
+    const double rhob = -fma(G.lam23, Lb, G.lam * (r * aw));
+    // rho = eta r, r = 1/h, hu, hv, base2 = -P2 r (P2 waits for the gathered part)
+    const double eb = r * rhob;
+    hb = fma(-(r * r), fma(eta, rhob, rb), hb);
+    hb = fma(u, hub, hb);
+    hb = fma(v, hvb, hb);
+    ub = fma(h, hub, ub);
+    vb = fma(h, hvb, vb);
+    double* C = S + ADJ_C * P;
+    C[AC_H * P] = hb;
+    C[AC_U * P] = ub;
+    C[AC_V * P] = vb;
+    C[AC_W * P] = wb;
+    C[AC_E * P] = eb;
+    C[AC_P2 * P] = -r * Bb;
 }
 
-// Pass 2: everything else at one node.
+// Pass 2: the transposed differences (gathers of the neighbours' weights),
+// the chain rule from the operands to the state and bathymetry, and the
+// stage algebra, at one node.
 template <int BC, int MODE>
-__global__ void __launch_bounds__(ADJ_BLOCK, 2) k_adj_gather(AdjArgs a) {
+__global__ void __launch_bounds__(ADJ_BLOCK) k_adj_gather(AdjArgs a) {
     const Geom& G = a.G;
     const long long P = G.plane;
     const long long c = (long long)blockIdx.x * ADJ_BLOCK + threadIdx.x;
@@ -209,9 +234,11 @@ __global__ void __launch_bounds__(ADJ_BLOCK, 2) k_adj_gather(AdjArgs a) {
         }
     }
 
-    // ---- product part: gathers of the neighbours' weights.  At a reflecting
-    // wall the clamped neighbour index is the node itself and its weight enters
-    // with a flipped sign (the one-sided end rows of the SBP operator).
+    // Transposed differences: the weight of node m reaches node n with +1 if
+    // n = R(m) and -1 if n = L(m).  Inside, that is W(n-1) - W(n+1); at a
+    // reflecting wall the clamped neighbour index is the node itself, whose
+    // one-sided row has the node as its L (first node) or R (last node), so
+    // its weight enters with a flipped sign.
     unsigned long long fl = 0ull, fr = 0ull, fb = 0ull, ft = 0ull;
     if (BC == BC_REFLECTING) {
         const unsigned long long sgn_bit = 0x8000000000000000ull;
@@ -222,108 +249,40 @@ __global__ void __launch_bounds__(ADJ_BLOCK, 2) k_adj_gather(AdjArgs a) {
     }
     const double* __restrict__ WX = S + ADJ_WX * P;
     const double* __restrict__ WY = S + ADJ_WY * P;
+    const double* __restrict__ C = S + ADJ_C * P + c;
 #define GX_(k) (flip_sign(WX[(k) * P + cl], fl) - flip_sign(WX[(k) * P + cr], fr))
 #define GY_(k) (flip_sign(WY[(k) * P + cb], fb) - flip_sign(WY[(k) * P + ct], ft))
-    const double pH = GX_(VW_H) + GY_(VW_H), pU = GX_(VW_U) + GY_(VW_U);
-    const double pV = GX_(VW_V) + GY_(VW_V), pW = GX_(VW_W) + GY_(VW_W);
-    const double pF = GX_(VW_E15) + GY_(VW_E15), pP = GX_(VW_P) + GY_(VW_P);
-    const double pHUV = GX_(VW_HUV) + GY_(VW_HUV);
-    const double pUU = GX_(VW_SQ), pHU = GX_(VW_HM), pHUW = GX_(VW_HMW);
-    const double pVV = GY_(VW_SQ), pHV = GY_(VW_HM), pHVW = GY_(VW_HMW);
+    double hb = GX_(VW_H) + GY_(VW_H) + C[AC_H * P];
+    double ub = GX_(VW_U) + GY_(VW_U) + C[AC_U * P];
+    double vb = GX_(VW_V) + GY_(VW_V) + C[AC_V * P];
+    double wb = GX_(VW_W) + GY_(VW_W) + C[AC_W * P];
+    const double Fb = GX_(VW_F) + GY_(VW_F);
+    const double P2b = GX_(VW_P2) + GY_(VW_P2) + C[AC_P2 * P];
+    const double HUVb = GX_(VW_HUV) + GY_(VW_HUV);
+    const double UUb = GX_(VW_SQ), HUb = GX_(VW_HM), HUWb = GX_(VW_HMW);
+    const double VVb = GY_(VW_SQ), HVb = GY_(VW_HM), HVWb = GY_(VW_HMW);
 #undef GX_
 #undef GY_
 
-    // ---- pointwise part: d k / d q at this node with every difference fixed.
-    // With k_u = -r B_u, k_w = r B_w (B the brackets of the forward kernel) the
-    // h-derivatives combine as d(k_u)/dh = r^2 G_u, d(k_v)/dh = r^2 G_v,
-    // d(k_w)/dh = r^2 G_w, where (using r h = 1; the dropped terms are rounding)
-    //   G_u = D_x h (lam/2 rho^2 - u^2/2 - g b) + lam/3 (1 - 2 rho) D_x(eta + 3/2 b)
-    //         + D_x P + u/2 D_x(hu) + (D_y(huv) - uv D_y h)/2   (P = g h(h+b) - lam/6 eta^2/h),
-    //   G_w = lam (2 rho - 1) + (D_x(huw) - uw D_x h + D_y(hvw) - vw D_y h)/2,
-    // eta and b enter only through D(eta + 3/2 b), and r h = 1 also reduces the
-    // u-, v- and w-derivatives to the forms below.
-    const bool wx = BC == BC_REFLECTING && (i == 0 || i == G.nx - 1);
-    const bool wy = BC == BC_REFLECTING && (j == 0 || j == G.ny - 1);
-    const AdjDir kx = wx ? a.kx[1] : a.kx[0];
-    const AdjDir ky = wy ? a.ky[1] : a.ky[0];
-    double sgx = 0.0, sgy = 0.0;
-    if (BC == BC_REFLECTING) {
-        if (i == 0) sgx = -G.satx;
-        if (i == G.nx - 1) sgx = G.satx;
-        if (j == 0) sgy = -G.saty;
-        if (j == G.ny - 1) sgy = G.saty;
-    }
-    const double* __restrict__ X = a.X;
-#define RX_(base) ((base)[cr] - (base)[cl])
-#define RY_(base) ((base)[ct] - (base)[cb])
-    const double h = X[c], u = X[P + c], v = X[2 * P + c], w = X[3 * P + c], eta = X[4 * P + c];
-    const double bb = a.b[c];
-    const double r = S[AP_R * P + c];
-    const double ah = a.A[c], au = a.A[P + c], av = a.A[2 * P + c];
-    const double aw = a.A[3 * P + c], ae = a.A[4 * P + c];
-    // differences used more than once, scaled
-    const double xh = kx.s * RX_(X), xu = kx.s * RX_(X + P), xv = kx.s * RX_(X + 2 * P);
-    const double xw = kx.s * RX_(X + 3 * P), xf = kx.s * RX_(S + AP_E15 * P);
-    const double yh = ky.s * RY_(X), yu = ky.s * RY_(X + P), yv = ky.s * RY_(X + 2 * P);
-    const double yw = ky.s * RY_(X + 3 * P), yf = ky.s * RY_(S + AP_E15 * P);
-    const double hxhu = kx.hs * RX_(S + AP_HU * P), hyhv = ky.hs * RY_(S + AP_HV * P);  // D(hu)/2, D(hv)/2
-
-    const double ar = r * au, br = r * av, cr_ = r * aw;
-    const double rho = eta * r, rho2 = rho * rho;
+    // chain rule from the operands to (h, u, v, w, eta, b) at this node:
+    // F = eta + 3/2 b; P2 = 2g h(h+b) - lam/3 eta^2/h with dP2/dh = 2g(2h+b) + lam/3 rho^2,
+    // dP2/deta = -2 lam/3 rho, dP2/db = 2g h; u^2, v^2, hu, hv, huv, huw, hvw
+    const double h = a.X[c], u = a.X[P + c], v = a.X[2 * P + c], w = a.X[3 * P + c];
+    const double eta = a.X[4 * P + c], bb = a.b[c];
+    const double r = a.tape[TP_R * P + c];
+    const double rho = eta * r;
     const double hu = h * u, hv = h * v, hw = h * w, uv = u * v, uw = u * w, vw_ = v * w;
-    const double q2 = fma(G.lam2, rho2, -G.g * bb);       // lam/2 rho^2 - g b
-    const double l12 = fma(a.m2lam3, rho, G.lam3);        // lam/3 (1 - 2 rho)
-    const double huv = 0.5 * uv;
-    double Gu = xh * fma(-0.5 * u, u, q2);
-    Gu = fma(l12, xf, Gu);
-    Gu = fma(kx.s, RX_(S + AP_P * P), Gu);
-    Gu = fma(u, hxhu, Gu);
-    Gu = fma(ky.hs, RY_(S + AP_HUV * P), Gu);
-    Gu = fma(-huv, yh, Gu);
-    double Gv = yh * fma(-0.5 * v, v, q2);
-    Gv = fma(l12, yf, Gv);
-    Gv = fma(ky.s, RY_(S + AP_P * P), Gv);
-    Gv = fma(v, hyhv, Gv);
-    Gv = fma(kx.hs, RX_(S + AP_HUV * P), Gv);
-    Gv = fma(-huv, xh, Gv);
-    double Gw = fma(a.lam2x, rho, -G.lam);
-    Gw = fma(kx.hs, RX_(S + AP_HUW * P), Gw);
-    Gw = fma(ky.hs, RY_(S + AP_HVW * P), Gw);
-    Gw = fma(-0.5, fma(uw, xh, vw_ * yh), Gw);
-#undef RX_
-#undef RY_
-
-    const double divu = xu + yv;
-    double hb = fma(-ah, divu, r * fma(ar, Gu, fma(br, Gv, cr_ * Gw)));
-    const double aru = ar * u, brv = br * v, crw = cr_ * w;
-    const double hau = 0.5 * au, hav = 0.5 * av, haw = 0.5 * aw;
-    double ub = xh * (fma(0.5, brv + crw, aru) - ah);
-    ub = fma(ar, fma(0.5 * v, yh, -hxhu), ub);
-    ub = fma(-ae, xf, fma(-haw, xw, fma(-hav, xv, fma(hau, divu, ub))));
-    double vb = yh * (fma(0.5, aru + crw, brv) - ah);
-    vb = fma(br, fma(0.5 * u, xh, -hyhv), vb);
-    vb = fma(-ae, yf, fma(-haw, yw, fma(-hau, yu, fma(hav, divu, vb))));
-    double wb = fma(0.5 * cr_, fma(u, xh, v * yh), fma(haw, divu, ae));
-    // d/d eta: only rho and 1 - rho depend on eta (d rho / d eta = r)
-    double eb = fma(ar, fma(rho, xh, -xf), br * fma(rho, yh, -yf));
-    eb = -r * fma(G.lam3, eb, G.lam * cr_);
-    double bbar = G.g * fma(ar, xh, br * yh);
-    if (BC == BC_REFLECTING) {
-        // SAT of the h equation: d/dh and d/du, d/dv of (sgx hu + sgy hv)
-        hb = fma(ah, fma(sgx, u, sgy * v), hb);
-        ub = fma(ah * sgx, h, ub);
-        vb = fma(ah * sgy, h, vb);
-    }
-
-    // ---- chain rule through the products
-    // dP/dh = g (2h + b) + lam/6 rho^2, dP/deta = -lam/3 rho, dP/db = g h
-    hb = fma(vw_, pHVW, fma(uw, pHUW, fma(uv, pHUV, fma(v, pHV, fma(u, pHU,
-         fma(fma(G.g, fma(2.0, h, bb), G.lam6 * rho2), pP, hb + pH))))));
-    ub = fma(hw, pHUW, fma(hv, pHUV, fma(h, pHU, fma(2.0 * u, pUU, ub + pU))));
-    vb = fma(hw, pHVW, fma(hu, pHUV, fma(h, pHV, fma(2.0 * v, pVV, vb + pV))));
-    wb = fma(hv, pHVW, fma(hu, pHUW, wb + pW));
-    eb = fma(-G.lam3 * rho, pP, eb + pF);
-    bbar = fma(G.g * h, pP, fma(1.5, pF, bbar));
+    double eb = C[AC_E * P] + Fb;
+    double bbar = 1.5 * Fb;
+    hb = fma(fma(G.g2, fma(2.0, h, bb), G.lam3 * (rho * rho)), P2b, hb);
+    eb = fma(-G.lam23 * rho, P2b, eb);
+    bbar = fma(G.g2 * h, P2b, bbar);
+    ub = fma(u + u, UUb, ub);
+    vb = fma(v + v, VVb, vb);
+    hb = fma(vw_, HVWb, fma(uw, HUWb, fma(uv, HUVb, fma(v, HVb, fma(u, HUb, hb)))));
+    ub = fma(hw, HUWb, fma(hv, HUVb, fma(h, HUb, ub)));
+    vb = fma(hw, HVWb, fma(hu, HUVb, fma(h, HVb, vb)));
+    wb = fma(hv, HVWb, fma(hu, HUWb, wb));
 
     const double qb[5] = {hb, ub, vb, wb, eb};
     const double sg = a.sigma;

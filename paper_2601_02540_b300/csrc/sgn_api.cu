@@ -131,30 +131,32 @@ cudaError_t smem_optin(size_t smem) {
     return err[dev];
 }
 
-template <typename TC, typename TIN, typename TA, int BC, int MODE, int R = sgn::StageShape<TC>::rows>
+template <typename TC, typename TIN, typename TA, int BC, int MODE, int R = sgn::StageShape<TC>::rows,
+          bool TAPE = false>
 cudaError_t stage_attr() {
-    return smem_optin<sgn::k_stage<TC, TIN, TA, BC, MODE, R>>(sgn::stage_smem_bytes<TC, MODE>(R));
+    return smem_optin<sgn::k_stage<TC, TIN, TA, BC, MODE, R, TAPE>>(sgn::stage_smem_bytes<TC, MODE>(R));
 }
 
 // The stage kernel with the context's tile height: FP64 contexts on small
 // grids use 32 x 8 tiles (c->rows == 1, see sgn_create), all others the
-// compute type's StageShape.
-template <typename TC, typename TIN, typename TA, int BC, int MODE>
+// compute type's StageShape.  TAPE: the FP64 kernel that also writes the tape.
+template <typename TC, typename TIN, typename TA, int BC, int MODE, bool TAPE = false>
 cudaError_t launch_stage(const sgn_ctx* c, const StageArgs<TC, TIN, TA>& a, cudaStream_t s) {
     if constexpr (std::is_same<TC, double>::value) {
         if (c->rows == 1) {
-            const cudaError_t attr_err = stage_attr<TC, TIN, TA, BC, MODE, 1>();
+            const cudaError_t attr_err = stage_attr<TC, TIN, TA, BC, MODE, 1, TAPE>();
             if (attr_err != cudaSuccess) return attr_err;
-            sgn::k_stage<TC, TIN, TA, BC, MODE, 1>
+            sgn::k_stage<TC, TIN, TA, BC, MODE, 1, TAPE>
                 <<<c->grid1, dim3(sgn::TILE_X, sgn::THREADS_Y), sgn::stage_smem_bytes<TC, MODE>(1), s>>>(a);
             count_launch();
             return cudaGetLastError();
         }
     }
-    const cudaError_t attr_err = stage_attr<TC, TIN, TA, BC, MODE>();
+    constexpr int R = sgn::StageShape<TC>::rows;
+    const cudaError_t attr_err = stage_attr<TC, TIN, TA, BC, MODE, R, TAPE>();
     if (attr_err != cudaSuccess) return attr_err;
-    const size_t smem = sgn::stage_smem_bytes<TC, MODE>(sgn::StageShape<TC>::rows);
-    sgn::k_stage<TC, TIN, TA, BC, MODE><<<c->grid, dim3(sgn::TILE_X, sgn::THREADS_Y), smem, s>>>(a);
+    const size_t smem = sgn::stage_smem_bytes<TC, MODE>(R);
+    sgn::k_stage<TC, TIN, TA, BC, MODE, R, TAPE><<<c->grid, dim3(sgn::TILE_X, sgn::THREADS_Y), smem, s>>>(a);
     count_launch();
     return cudaGetLastError();
 }
@@ -398,29 +400,49 @@ cudaError_t convert_bathymetry(sgn_ctx* c, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// The tape of f(X) (TAPE mode of the FP64 stage kernel), for a VJP whose
+// caller recorded none.
+template <int BC>
+cudaError_t launch_tape(const sgn_ctx* c, const double* X, double* tape, cudaStream_t s) {
+    StageArgs<double, double, double> t = base_args<double, double, double>(c);
+    t.X = X;
+    t.tape = tape;
+    return launch_stage<double, double, double, BC, sgn::MODE_TAPE, true>(c, t, s);
+}
+
+// J(X)^T (sigma A): the tape of f(X) from a.tape or, when that is NULL, from a
+// TAPE launch into `scratch_tape`; then the two adjoint passes.
 template <int BC, int MODE>
-cudaError_t launch_adjoint(const sgn_ctx* c, const sgn::AdjArgs& a, cudaStream_t s) {
+cudaError_t launch_adjoint(const sgn_ctx* c, sgn::AdjArgs a, double* scratch_tape, cudaStream_t s) {
+    cudaError_t e;
+    if (!a.tape) {
+        if ((e = launch_tape<BC>(c, a.X, scratch_tape, s)) != cudaSuccess) return e;
+        a.tape = scratch_tape;
+    }
     const unsigned blocks = (unsigned)((c->G.plane + sgn::ADJ_BLOCK - 1) / sgn::ADJ_BLOCK);
-    sgn::k_adj_weights<BC><<<blocks, sgn::ADJ_BLOCK, 0, s>>>(a);
+    sgn::k_adj_point<BC><<<blocks, sgn::ADJ_BLOCK, 0, s>>>(a);
     count_launch();
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     sgn::k_adj_gather<BC, MODE><<<blocks, sgn::ADJ_BLOCK, 0, s>>>(a);
     count_launch();
     return cudaGetLastError();
 }
 
+// Adjoint scratch, allocated on first use: RK accumulator and two cotangents
+// (15 planes), the weights and node parts (ADJ_SCRATCH_PLANES), a tape (N_TAPE).
+constexpr long long kAdjTapeOffset = 15 + sgn::ADJ_SCRATCH_PLANES;
+static_assert(SGN_TAPE_PLANES == sgn::N_TAPE, "the header's tape size");
+
 template <int MODE>
 cudaError_t adjoint(const sgn_ctx* c, const sgn::AdjArgs& a, cudaStream_t s) {
-    return c->p.bc == SGN_BC_REFLECTING ? launch_adjoint<sgn::BC_REFLECTING, MODE>(c, a, s)
-                                        : launch_adjoint<sgn::BC_PERIODIC, MODE>(c, a, s);
+    double* scratch_tape = c->adj + kAdjTapeOffset * c->G.plane;
+    return c->p.bc == SGN_BC_REFLECTING ? launch_adjoint<sgn::BC_REFLECTING, MODE>(c, a, scratch_tape, s)
+                                        : launch_adjoint<sgn::BC_PERIODIC, MODE>(c, a, scratch_tape, s);
 }
 
-// Adjoint scratch, allocated on first use: RK accumulator and two cotangents
-// (15 planes), then the products and direction weights (ADJ_SCRATCH_PLANES).
 sgn_status adjoint_scratch(sgn_ctx* c) {
     if (c->adj) return SGN_OK;
-    const size_t bytes = (size_t)(15 + sgn::ADJ_SCRATCH_PLANES) * (size_t)c->G.plane * sizeof(double);
+    const size_t bytes = (size_t)(kAdjTapeOffset + sgn::N_TAPE) * (size_t)c->G.plane * sizeof(double);
     if (cudaMalloc(&c->adj, bytes) != cudaSuccess) {
         cudaGetLastError();
         c->adj = nullptr;
@@ -429,25 +451,32 @@ sgn_status adjoint_scratch(sgn_ctx* c) {
     return SGN_OK;
 }
 
-// One RK4 step that also records its stage states: stash = [q_n | Q2 | Q3 | Q4].
-template <int BC>
-cudaError_t record_step(sgn_ctx* c, double* q, double dt, double* stash, cudaStream_t s) {
+// One RK4 step that also records its stage states: stash = [q_n | Q2 | Q3 | Q4],
+// and, with TAPE, the tapes of its four right-hand sides: tape = [T1 | T2 | T3 | T4]
+// (N_TAPE planes each), written by the stage kernels themselves.
+template <int BC, bool TAPE>
+cudaError_t record_step(sgn_ctx* c, double* q, double dt, double* stash, double* tape, cudaStream_t s) {
     const long long P5 = 5 * c->G.plane;
+    const long long PT = (long long)sgn::N_TAPE * c->G.plane;
     double* acc = static_cast<double*>(c->acc);
     cudaError_t e = cudaMemcpyAsync(stash, q, P5 * sizeof(double), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return e;
     StageArgs<double, double, double> a1 = base_args<double, double, double>(c);
     a1.X = q; a1.qn = q; a1.acc = acc; a1.Qout = stash + P5; a1.c_acc = dt / 6.0; a1.c_q = dt / 2.0;
-    if ((e = launch_stage<double, double, double, BC, sgn::MODE_S1>(c, a1, s)) != cudaSuccess) return e;
+    a1.tape = tape;
+    if ((e = launch_stage<double, double, double, BC, sgn::MODE_S1, TAPE>(c, a1, s)) != cudaSuccess) return e;
     StageArgs<double, double, double> a2 = a1;
     a2.X = stash + P5; a2.Qout = stash + 2 * P5; a2.c_acc = dt / 3.0; a2.c_q = dt / 2.0;
-    if ((e = launch_stage<double, double, double, BC, sgn::MODE_S2>(c, a2, s)) != cudaSuccess) return e;
+    a2.tape = TAPE ? tape + PT : nullptr;
+    if ((e = launch_stage<double, double, double, BC, sgn::MODE_S2, TAPE>(c, a2, s)) != cudaSuccess) return e;
     StageArgs<double, double, double> a3 = a1;
     a3.X = stash + 2 * P5; a3.Qout = stash + 3 * P5; a3.c_acc = dt / 3.0; a3.c_q = dt;
-    if ((e = launch_stage<double, double, double, BC, sgn::MODE_S3>(c, a3, s)) != cudaSuccess) return e;
+    a3.tape = TAPE ? tape + 2 * PT : nullptr;
+    if ((e = launch_stage<double, double, double, BC, sgn::MODE_S3, TAPE>(c, a3, s)) != cudaSuccess) return e;
     StageArgs<double, double, double> a4 = base_args<double, double, double>(c);
     a4.X = stash + 3 * P5; a4.acc = acc; a4.out = q; a4.c_acc = dt / 6.0;
-    return launch_stage<double, double, double, BC, sgn::MODE_S4>(c, a4, s);
+    a4.tape = TAPE ? tape + 3 * PT : nullptr;
+    return launch_stage<double, double, double, BC, sgn::MODE_S4, TAPE>(c, a4, s);
 }
 
 sgn_status need_f64(const sgn_ctx* c, const char* what) {
@@ -860,6 +889,96 @@ sgn_status run_relaxed(sgn_ctx* c, double* q, double dt, int nsteps, double* gam
     return SGN_OK;
 }
 
+// nsteps recorded RK4 steps (stash: 20 planes per step; tape: 4 N_TAPE planes
+// per step, or NULL for none).
+sgn_status record_steps(sgn_ctx* c, void* q_dev, double dt, int nsteps, void* stash_dev, void* tape_dev,
+                        void* stream, const char* what) {
+    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
+    sgn_status st = need_f64(c, what);
+    if (st == SGN_OK) st = check_state_ptr(q_dev, "q_dev");
+    if (st == SGN_OK && nsteps > 0) st = check_state_ptr(stash_dev, "stash_dev");
+    if (st == SGN_OK && nsteps > 0 && tape_dev) st = check_state_ptr(tape_dev, "tape_dev");
+    if (st != SGN_OK) return st;
+    if (!finite_pos(dt)) return fail(SGN_E_INVAL, "dt must be finite and > 0");
+    if (nsteps < 0) return fail(SGN_E_INVAL, "nsteps must be >= 0");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double* q = static_cast<double*>(q_dev);
+    double* stash = static_cast<double*>(stash_dev);
+    double* tape = static_cast<double*>(tape_dev);
+    const long long P20 = 20 * c->G.plane;
+    const long long PT = 4LL * sgn::N_TAPE * c->G.plane;
+    const bool refl = c->p.bc == SGN_BC_REFLECTING;
+    for (int n = 0; n < nsteps; n++) {
+        double* sn = stash + n * P20;
+        cudaError_t e;
+        if (tape)
+            e = refl ? record_step<sgn::BC_REFLECTING, true>(c, q, dt, sn, tape + n * PT, s)
+                     : record_step<sgn::BC_PERIODIC, true>(c, q, dt, sn, tape + n * PT, s);
+        else
+            e = refl ? record_step<sgn::BC_REFLECTING, false>(c, q, dt, sn, nullptr, s)
+                     : record_step<sgn::BC_PERIODIC, false>(c, q, dt, sn, nullptr, s);
+        if (e != cudaSuccess) return cuda_fail(e, what);
+    }
+    return SGN_OK;
+}
+
+// The VJP of one recorded RK4 step (tape: the step's four tapes, or NULL to
+// compute each stage's tape from its recorded state).
+sgn_status step_vjp(sgn_ctx* c, const void* stash_dev, const void* tape_dev, void* qbar_dev, void* bbar_dev,
+                    double dt, void* stream, const char* what) {
+    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
+    sgn_status st = need_f64(c, what);
+    if (st == SGN_OK) st = check_state_ptr(stash_dev, "stash_dev");
+    if (st == SGN_OK && tape_dev) st = check_state_ptr(tape_dev, "tape_dev");
+    if (st == SGN_OK) st = check_state_ptr(qbar_dev, "qbar_dev");
+    if (st == SGN_OK) st = check_state_ptr(bbar_dev, "bbar_dev");
+    if (st != SGN_OK) return st;
+    if (!finite_pos(dt)) return fail(SGN_E_INVAL, "dt must be finite and > 0");
+    const long long P5 = 5 * c->G.plane;
+    const long long PT = (long long)sgn::N_TAPE * c->G.plane;
+    st = adjoint_scratch(c);
+    if (st != SGN_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const double* stash = static_cast<const double*>(stash_dev);
+    const double* tape = static_cast<const double*>(tape_dev);
+    double* qbar = static_cast<double*>(qbar_dev);
+    double* qacc = c->adj;
+    double* A0 = c->adj + P5;
+    double* A1 = c->adj + 2 * P5;
+    // The cotangent of stage s is sigma_s * A_s: sigma_4 = dt/6, A_4 = qbar', and
+    // k_{s-1} = c' qbar' + cbar Qbar_s gives sigma_{s-1} = cbar sigma_s and
+    // A_{s-1} = (c' / sigma_{s-1}) qbar' + J^T A_s (one FMA per value).
+    const double sig4 = dt / 6.0, sig3 = dt * sig4, sig2 = 0.5 * dt * sig3, sig1 = 0.5 * dt * sig2;
+    const double kap3 = (dt / 3.0) / sig3, kap2 = (dt / 3.0) / sig2, kap1 = (dt / 6.0) / sig1;
+    if (!(std::isnormal(sig1) && std::isfinite(kap1)))
+        return fail(SGN_E_INVAL, "dt = %g is outside the range of the scaled adjoint recurrence", dt);
+    auto tape_of = [&](int stage) { return tape ? tape + (stage - 1) * PT : nullptr; };
+    sgn::AdjArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.b = c->b64;
+    a.scratch = c->adj + 15 * c->G.plane;
+    a.bbar = static_cast<double*>(bbar_dev);
+    a.qprime = qbar;
+    a.flag = c->flag;
+    a.G = c->G;
+    cudaError_t e;
+    // stage 4: k4bar = dt/6 qbar'; Q4bar = J(Q4)^T k4bar; k3bar = dt/3 qbar' + dt Q4bar
+    a.X = stash + 3 * P5; a.tape = tape_of(4); a.A = qbar; a.sigma = sig4;
+    a.first = 1; a.qacc_out = qacc; a.Anext = A0; a.kappa = kap3;
+    if ((e = adjoint<sgn::ADJ_MODE_STAGE>(c, a, s)) != cudaSuccess) return cuda_fail(e, what);
+    // stage 3: Q3bar = J(Q3)^T k3bar; k2bar = dt/3 qbar' + dt/2 Q3bar
+    a.X = stash + 2 * P5; a.tape = tape_of(3); a.A = A0; a.sigma = sig3;
+    a.first = 0; a.qacc_in = qacc; a.qacc_out = qacc; a.Anext = A1; a.kappa = kap2;
+    if ((e = adjoint<sgn::ADJ_MODE_STAGE>(c, a, s)) != cudaSuccess) return cuda_fail(e, what);
+    // stage 2: Q2bar = J(Q2)^T k2bar; k1bar = dt/6 qbar' + dt/2 Q2bar
+    a.X = stash + P5; a.tape = tape_of(2); a.A = A1; a.sigma = sig2; a.Anext = A0; a.kappa = kap1;
+    if ((e = adjoint<sgn::ADJ_MODE_STAGE>(c, a, s)) != cudaSuccess) return cuda_fail(e, what);
+    // stage 1: Q1bar = J(q_n)^T k1bar; qbar = qbar' + Q1bar + Q2bar + Q3bar + Q4bar
+    a.X = stash; a.tape = tape_of(1); a.A = A0; a.sigma = sig1; a.Anext = nullptr; a.qacc_out = qbar;
+    if ((e = adjoint<sgn::ADJ_MODE_STAGE>(c, a, s)) != cudaSuccess) return cuda_fail(e, what);
+    return SGN_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1118,83 +1237,30 @@ sgn_status sgn_rhs_vjp(sgn_ctx* c, const void* q_dev, const void* abar_dev, void
     a.bbar = static_cast<double*>(bbar_dev);
     a.flag = c->flag;
     a.G = c->G;
-    sgn::fill_adj_constants(a);
     cudaError_t e = adjoint<sgn::ADJ_MODE_RHS>(c, a, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "sgn_rhs_vjp");
     return SGN_OK;
 }
 
 sgn_status sgn_step_record(sgn_ctx* c, void* q_dev, double dt, int nsteps, void* stash_dev, void* stream) {
-    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
-    sgn_status st = need_f64(c, "sgn_step_record");
-    if (st == SGN_OK) st = check_state_ptr(q_dev, "q_dev");
-    if (st == SGN_OK && nsteps > 0) st = check_state_ptr(stash_dev, "stash_dev");
-    if (st != SGN_OK) return st;
-    if (!finite_pos(dt)) return fail(SGN_E_INVAL, "dt must be finite and > 0");
-    if (nsteps < 0) return fail(SGN_E_INVAL, "nsteps must be >= 0");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    double* q = static_cast<double*>(q_dev);
-    double* stash = static_cast<double*>(stash_dev);
-    const long long P20 = 20 * c->G.plane;
-    for (int n = 0; n < nsteps; n++) {
-        cudaError_t e = c->p.bc == SGN_BC_REFLECTING
-                            ? record_step<sgn::BC_REFLECTING>(c, q, dt, stash + n * P20, s)
-                            : record_step<sgn::BC_PERIODIC>(c, q, dt, stash + n * P20, s);
-        if (e != cudaSuccess) return cuda_fail(e, "sgn_step_record");
-    }
-    return SGN_OK;
+    return record_steps(c, q_dev, dt, nsteps, stash_dev, nullptr, stream, "sgn_step_record");
+}
+
+sgn_status sgn_step_record_tape(sgn_ctx* c, void* q_dev, double dt, int nsteps, void* stash_dev,
+                                void* tape_dev, void* stream) {
+    if (nsteps > 0 && !tape_dev) return fail(SGN_E_INVAL, "tape_dev is NULL");
+    return record_steps(c, q_dev, dt, nsteps, stash_dev, tape_dev, stream, "sgn_step_record_tape");
 }
 
 sgn_status sgn_step_vjp(sgn_ctx* c, const void* stash_dev, void* qbar_dev, void* bbar_dev, double dt,
                         void* stream) {
-    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
-    sgn_status st = need_f64(c, "sgn_step_vjp");
-    if (st == SGN_OK) st = check_state_ptr(stash_dev, "stash_dev");
-    if (st == SGN_OK) st = check_state_ptr(qbar_dev, "qbar_dev");
-    if (st == SGN_OK) st = check_state_ptr(bbar_dev, "bbar_dev");
-    if (st != SGN_OK) return st;
-    if (!finite_pos(dt)) return fail(SGN_E_INVAL, "dt must be finite and > 0");
-    const long long P5 = 5 * c->G.plane;
-    st = adjoint_scratch(c);
-    if (st != SGN_OK) return st;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const double* stash = static_cast<const double*>(stash_dev);
-    double* qbar = static_cast<double*>(qbar_dev);
-    double* qacc = c->adj;
-    double* A0 = c->adj + P5;
-    double* A1 = c->adj + 2 * P5;
-    // The cotangent of stage s is sigma_s * A_s: sigma_4 = dt/6, A_4 = qbar', and
-    // k_{s-1} = c' qbar' + cbar Qbar_s gives sigma_{s-1} = cbar sigma_s and
-    // A_{s-1} = (c' / sigma_{s-1}) qbar' + J^T A_s (one FMA per value).
-    const double sig4 = dt / 6.0, sig3 = dt * sig4, sig2 = 0.5 * dt * sig3, sig1 = 0.5 * dt * sig2;
-    const double kap3 = (dt / 3.0) / sig3, kap2 = (dt / 3.0) / sig2, kap1 = (dt / 6.0) / sig1;
-    if (!(std::isnormal(sig1) && std::isfinite(kap1)))
-        return fail(SGN_E_INVAL, "dt = %g is outside the range of the scaled adjoint recurrence", dt);
-    sgn::AdjArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.b = c->b64;
-    a.scratch = c->adj + 15 * c->G.plane;
-    a.bbar = static_cast<double*>(bbar_dev);
-    a.qprime = qbar;
-    a.flag = c->flag;
-    a.G = c->G;
-    sgn::fill_adj_constants(a);
-    cudaError_t e;
-    // stage 4: k4bar = dt/6 qbar'; Q4bar = J(Q4)^T k4bar; k3bar = dt/3 qbar' + dt Q4bar
-    a.X = stash + 3 * P5; a.A = qbar; a.sigma = sig4;
-    a.first = 1; a.qacc_out = qacc; a.Anext = A0; a.kappa = kap3;
-    if ((e = adjoint<sgn::ADJ_MODE_STAGE>(c, a, s)) != cudaSuccess) return cuda_fail(e, "sgn_step_vjp");
-    // stage 3: Q3bar = J(Q3)^T k3bar; k2bar = dt/3 qbar' + dt/2 Q3bar
-    a.X = stash + 2 * P5; a.A = A0; a.sigma = sig3;
-    a.first = 0; a.qacc_in = qacc; a.qacc_out = qacc; a.Anext = A1; a.kappa = kap2;
-    if ((e = adjoint<sgn::ADJ_MODE_STAGE>(c, a, s)) != cudaSuccess) return cuda_fail(e, "sgn_step_vjp");
-    // stage 2: Q2bar = J(Q2)^T k2bar; k1bar = dt/6 qbar' + dt/2 Q2bar
-    a.X = stash + P5; a.A = A1; a.sigma = sig2; a.Anext = A0; a.kappa = kap1;
-    if ((e = adjoint<sgn::ADJ_MODE_STAGE>(c, a, s)) != cudaSuccess) return cuda_fail(e, "sgn_step_vjp");
-    // stage 1: Q1bar = J(q_n)^T k1bar; qbar = qbar' + Q1bar + Q2bar + Q3bar + Q4bar
-    a.X = stash; a.A = A0; a.sigma = sig1; a.Anext = nullptr; a.qacc_out = qbar;
-    if ((e = adjoint<sgn::ADJ_MODE_STAGE>(c, a, s)) != cudaSuccess) return cuda_fail(e, "sgn_step_vjp");
-    return SGN_OK;
+    return step_vjp(c, stash_dev, nullptr, qbar_dev, bbar_dev, dt, stream, "sgn_step_vjp");
+}
+
+sgn_status sgn_step_vjp_tape(sgn_ctx* c, const void* stash_dev, const void* tape_dev, void* qbar_dev,
+                             void* bbar_dev, double dt, void* stream) {
+    if (!tape_dev) return fail(SGN_E_INVAL, "tape_dev is NULL");
+    return step_vjp(c, stash_dev, tape_dev, qbar_dev, bbar_dev, dt, stream, "sgn_step_vjp_tape");
 }
 
 sgn_status sgn_mms_exact(sgn_ctx* c, double t, void* q_dev, void* b_dev, void* stream) {

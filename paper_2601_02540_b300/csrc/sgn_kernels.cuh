@@ -40,8 +40,12 @@ enum { BC_PERIODIC = 0, BC_REFLECTING = 1 };
 //   S1K: k1 = f(q_n) -> Qout
 //   S2K: k2 = f(q_n + dt/2 k1); acc = (q_n + dt/6 k1) + dt/3 k2; Q' = q_n + dt/2 k2
 // so that the first two stages move 11 + 21 planes instead of 16 + 26.
+// TAPE evaluates f(X) and writes only its tape (the TP_ planes below), the
+// intermediate values of the right-hand side that the adjoint kernels read
+// instead of recomputing them; FP64 stage kernels instantiated with their
+// TAPE flag write the same tape beside the stage update.
 enum { MODE_RHS = 0, MODE_S1 = 1, MODE_S2 = 2, MODE_S3 = 3, MODE_S4 = 4, MODE_DIAG = 5, MODE_S4D = 6,
-       MODE_S1K = 7, MODE_S2K = 8 };
+       MODE_S1K = 7, MODE_S2K = 8, MODE_TAPE = 9 };
 // Whether RK4 steps use S1K and S2K: the FP32 mode (float state and compute
 // type; the mixed mode's S2K, holding double q_n and float k1 of its halo
 // nodes, measured 3% slower than S1 and S2).
@@ -64,6 +68,19 @@ constexpr int BLOCK_THREADS = TILE_X * THREADS_Y;
 enum {
     OP_H, OP_U, OP_V, OP_W, OP_RHO, OP_R, OP_E15, OP_P2,
     OP_UU, OP_VV, OP_HU, OP_HV, OP_HUV, OP_HUW, OP_HVW, N_OPS
+};
+
+// The tape of one right-hand-side evaluation: per node, FP64 values of
+// node_rhs_src in its own rounding (the differences are unscaled, f_+ - f_-):
+//   R      1/h                       BASE2  -P2/h
+//   DXH .. DYF   D_x, D_y of h, u, v, w and eta + 3/2 b
+//   DXUU, DYVV   D_x(u^2), D_y(v^2)
+//   XHU    D_x(hu) - A_x              YHV    D_y(hv) - A_y
+//   AX, AY the continuity fluxes u D_x h + h D_x u, v D_y h + h D_y v
+//   KU, KV, KW   the right-hand side of u, v, w
+enum {
+    TP_R, TP_BASE2, TP_DXH, TP_DYH, TP_DXU, TP_DYU, TP_DXV, TP_DYV, TP_DXW, TP_DYW, TP_DXF, TP_DYF,
+    TP_DXUU, TP_DYVV, TP_XHU, TP_YHV, TP_AX, TP_AY, TP_KU, TP_KV, TP_KW, N_TAPE
 };
 
 constexpr int NDIAG = 4;
@@ -210,6 +227,7 @@ struct StageArgs {
     Geom G;
     TA c_acc, c_q;       // stage coefficients (see the modes)
     TA c_acc1, c_q1;     // S2K: the first stage's dt/6 and dt/2
+    double* tape;        // TAPE mode and TAPE-flagged kernels: N_TAPE planes (FP64)
 };
 
 template <typename T>
@@ -436,8 +454,10 @@ struct FactoredOps {        // the factored tile: products formed on request
 //    direction, applied once per equation.
 // The differences are unscaled (f_+ - f_-); sx, sy hold the operator's row
 // factor (1/(2dx) central, 1/dx on a reflecting wall's one-sided row).
-template <typename TC, int BC, typename Src>
-__device__ __forceinline__ void node_rhs_src(const Src& S, int gi, int gj, const Geom& G, TC k[5]) {
+// With TAPE, tp receives the node's tape values (the TP_ enum).
+template <typename TC, int BC, typename Src, bool TAPE = false>
+__device__ __forceinline__ void node_rhs_src(const Src& S, int gi, int gj, const Geom& G, TC k[5],
+                                             TC* tp = nullptr) {
     TC sx = GC(TC, cx2), sy = GC(TC, cy2), hsx = GC(TC, hcx2), hsy = GC(TC, hcy2);
     if (BC == BC_REFLECTING) {
         // one-sided first/last rows of the reflecting operator: (f1 - f0)/dx
@@ -505,17 +525,30 @@ __device__ __forceinline__ void node_rhs_src(const Src& S, int gi, int gj, const
 
     // eta_t = w - u D_x(eta + 3/2 b) - v D_y(eta + 3/2 b)
     const TC ke = fma_(-v, mul_(sy, dyf), fma_(-u, mul_(sx, dxf), w));
+    k[0] = kh; k[1] = ku; k[2] = kv; k[3] = kw; k[4] = ke;
+    if constexpr (TAPE) {
+        // the values the expressions above formed (the same operations on the
+        // same operands, so the same roundings)
+        const TC xhu = sub_(DXU(OP_HU), Ax), dxuu = DXU(OP_UU);
+        const TC yhv = sub_(DYU(OP_HV), Ay), dyvv = DYU(OP_VV);
+        tp[TP_R] = r; tp[TP_BASE2] = base2;
+        tp[TP_DXH] = dxh; tp[TP_DYH] = dyh; tp[TP_DXU] = dxu; tp[TP_DYU] = dyu;
+        tp[TP_DXV] = dxv; tp[TP_DYV] = dyv; tp[TP_DXW] = dxw; tp[TP_DYW] = dyw;
+        tp[TP_DXF] = dxf; tp[TP_DYF] = dyf; tp[TP_DXUU] = dxuu; tp[TP_DYVV] = dyvv;
+        tp[TP_XHU] = xhu; tp[TP_YHV] = yhv; tp[TP_AX] = Ax; tp[TP_AY] = Ay;
+        tp[TP_KU] = ku; tp[TP_KV] = kv; tp[TP_KW] = kw;
+    }
 #undef DXU
 #undef DYU
 #undef SM_
-    k[0] = kh; k[1] = ku; k[2] = kv; k[3] = kw; k[4] = ke;
 }
 
 // Right-hand side at the node held in shared-memory slot t of a halo tile with
 // row stride HX and plane size HN, global (gi, gj).
-template <typename TC, int BC, int HX = HALO_X, int HN = HALO_N, bool FACT = TileLayout<TC>::factored>
+template <typename TC, int BC, int HX = HALO_X, int HN = HALO_N, bool FACT = TileLayout<TC>::factored,
+          bool TAPE = false>
 __device__ __forceinline__ void node_rhs(const TC* __restrict__ sm, int t, int gi, int gj,
-                                         const Geom& G, TC k[5]) {
+                                         const Geom& G, TC k[5], TC* tp = nullptr) {
     using Src = typename std::conditional<FACT, FactoredOps<TC, HN>, SmemOps<TC, HN>>::type;
     Src S;
     S.sm = sm;
@@ -530,7 +563,7 @@ __device__ __forceinline__ void node_rhs(const TC* __restrict__ sm, int t, int g
         if (gj == 0) S.idx[POS_B] = t;
         if (gj == G.ny - 1) S.idx[POS_T] = t;
     }
-    node_rhs_src<TC, BC>(S, gi, gj, G, k);
+    node_rhs_src<TC, BC, Src, TAPE>(S, gi, gj, G, k, tp);
 }
 
 // Mass weight of node (gi, gj): dx dy, halved on each reflecting wall.
@@ -703,8 +736,9 @@ __host__ __device__ constexpr int tile_nper() {
 // sums to partial_band0 + ry * band_stride.  The band sums do not depend on
 // the tile height, so every launch shape (and the batched kernel) produces the
 // same partials for the same state.
+// With TAPE (FP64), every node also writes its tape to a.tape (N_TAPE planes).
 template <typename TC, typename TIN, typename TA, int BC, int MODE, int ROWS,
-          bool FACT = TileLayout<TC>::factored>
+          bool FACT = TileLayout<TC>::factored, bool TAPE = false>
 __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, const Geom& G, int i0, int j0,
                                            TC* __restrict__ sm, double* partial_band0, long long band_stride) {
     constexpr int ROWS_PER_THREAD = ROWS;
@@ -866,8 +900,17 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
         if (gi >= G.nx || gj >= G.ny) continue;
         const int t = (ly + 1) * HALO_X + (threadIdx.x + 1);
         TC k[5];
-        node_rhs<TC, BC, HALO_X, HALO_N, FACT>(sm, t, gi, gj, G, k);
         const long long c = (long long)gj * G.nx + gi;
+        if constexpr (TAPE) {
+            static_assert(std::is_same<TC, double>::value, "the tape is written by the FP64 kernels");
+            TC tp[N_TAPE];
+            node_rhs<TC, BC, HALO_X, HALO_N, FACT, true>(sm, t, gi, gj, G, k, tp);
+#pragma unroll
+            for (int p = 0; p < N_TAPE; p++) a.tape[p * P + c] = tp[p];
+        } else {
+            static_assert(MODE != MODE_TAPE, "the TAPE mode needs the TAPE flag");
+            node_rhs<TC, BC, HALO_X, HALO_N, FACT>(sm, t, gi, gj, G, k);
+        }
         if (MODE == MODE_RHS) {
 #pragma unroll
             for (int f = 0; f < 5; f++) a.out[f * P + c] = cvt<TA>(k[f]);
@@ -1004,13 +1047,15 @@ constexpr int kStageMinBlocks =
 
 // R: rows per thread (tile height 8 R); the compute type's StageShape, or 1
 // for FP64 grids too small to spread 32 x 24 tiles evenly over the SMs.
-template <typename TC, typename TIN, typename TA, int BC, int MODE, int R = StageShape<TC>::rows>
+// TAPE: also write the tape of every right-hand-side evaluation (FP64).
+template <typename TC, typename TIN, typename TA, int BC, int MODE, int R = StageShape<TC>::rows,
+          bool TAPE = false>
 __global__ void __launch_bounds__(BLOCK_THREADS, (kStageMinBlocks<TC, TA, MODE, BC>))
 k_stage(StageArgs<TC, TIN, TA> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TC* sm = reinterpret_cast<TC*>(smem_raw);
     // band partials in band-major order: band (blockIdx.y R + ry), column block blockIdx.x
-    stage_tile<TC, TIN, TA, BC, MODE, R>(a, a.G, blockIdx.x * TILE_X, blockIdx.y * (THREADS_Y * R), sm,
+    stage_tile<TC, TIN, TA, BC, MODE, R, TileLayout<TC>::factored, TAPE>(a, a.G, blockIdx.x * TILE_X, blockIdx.y * (THREADS_Y * R), sm,
                                          a.partials ? a.partials + (blockIdx.y * R * (long long)gridDim.x +
                                                                     blockIdx.x) * NDIAG
                                                     : nullptr,

@@ -51,6 +51,8 @@ _SIGNATURES = {
     "sgn_rhs_vjp": (ctypes.c_int, [_V, _V, _V, _V, _V, _V]),
     "sgn_step_record": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_int, _V, _V]),
     "sgn_step_vjp": (ctypes.c_int, [_V, _V, _V, _V, ctypes.c_double, _V]),
+    "sgn_step_record_tape": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_int, _V, _V, _V]),
+    "sgn_step_vjp_tape": (ctypes.c_int, [_V, _V, _V, _V, _V, ctypes.c_double, _V]),
     "sgn_batch_create": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int, _V, _V]),
     "sgn_batch_destroy": (ctypes.c_int, [_V]),
     "sgn_batch_cells": (ctypes.c_longlong, [_V]),
@@ -256,6 +258,25 @@ def sgn_step_vjp(ctx, stash_slot: torch.Tensor, qbar: torch.Tensor, bbar: torch.
                            _dptr(bbar, f, "bbar"), float(dt), _stream(stream)), "sgn_step_vjp")
 
 
+# planes of one RHS evaluation's tape (SGN_TAPE_PLANES); a step records four
+TAPE_PLANES = 21
+
+
+def sgn_step_record_tape(ctx, q: torch.Tensor, dt: float, nsteps: int, stash: torch.Tensor,
+                         tape: torch.Tensor, stream=None) -> None:
+    f = torch.float64
+    _ok(lib().sgn_step_record_tape(ctx, _dptr(q, f, "q"), float(dt), int(nsteps), _dptr(stash, f, "stash"),
+                                   _dptr(tape, f, "tape"), _stream(stream)), "sgn_step_record_tape")
+
+
+def sgn_step_vjp_tape(ctx, stash_slot: torch.Tensor, tape_slot: torch.Tensor, qbar: torch.Tensor,
+                      bbar: torch.Tensor, dt: float, stream=None) -> None:
+    f = torch.float64
+    _ok(lib().sgn_step_vjp_tape(ctx, _dptr(stash_slot, f, "stash"), _dptr(tape_slot, f, "tape"),
+                                _dptr(qbar, f, "qbar"), _dptr(bbar, f, "bbar"), float(dt), _stream(stream)),
+        "sgn_step_vjp_tape")
+
+
 def sgn_check(ctx, stream=None) -> None:
     _ok(lib().sgn_check(ctx, _stream(stream)), "sgn_check")
 
@@ -362,12 +383,23 @@ class Solver:
         sgn_rhs_vjp(self.ctx, q, abar, qbar, bbar)
         return qbar, bbar
 
-    def step_record(self, q: torch.Tensor, dt: float, nsteps: int, stash: torch.Tensor) -> torch.Tensor:
-        sgn_step_record(self.ctx, q, dt, nsteps, stash)
+    def step_record(self, q: torch.Tensor, dt: float, nsteps: int, stash: torch.Tensor,
+                    tape: torch.Tensor | None = None) -> torch.Tensor:
+        """nsteps RK4 steps recording the stage states (stash: nsteps x 20
+        planes) and, with `tape`, the tapes of the stage RHS evaluations
+        (nsteps x 4 TAPE_PLANES planes)."""
+        if tape is None:
+            sgn_step_record(self.ctx, q, dt, nsteps, stash)
+        else:
+            sgn_step_record_tape(self.ctx, q, dt, nsteps, stash, tape)
         return q
 
-    def step_vjp(self, stash_slot: torch.Tensor, qbar: torch.Tensor, bbar: torch.Tensor, dt: float):
-        sgn_step_vjp(self.ctx, stash_slot, qbar, bbar, dt)
+    def step_vjp(self, stash_slot: torch.Tensor, qbar: torch.Tensor, bbar: torch.Tensor, dt: float,
+                 tape_slot: torch.Tensor | None = None):
+        if tape_slot is None:
+            sgn_step_vjp(self.ctx, stash_slot, qbar, bbar, dt)
+        else:
+            sgn_step_vjp_tape(self.ctx, stash_slot, tape_slot, qbar, bbar, dt)
         return qbar, bbar
 
     def check(self) -> None:

@@ -5,6 +5,11 @@ step) and against finite differences.
   (GPU VJP of unit cotangents vs oracle JVP of unit directions), and dot-product
   tests <J d, a> = <d, J^T a> on multi-tile ragged grids, both boundaries.
 - One RK4 step: dot-product test through sgn_step_record + sgn_step_vjp.
+- The tape: sgn_step_record_tape advances and records exactly as
+  sgn_step_record, its tape holds the RHS intermediates it names (checked
+  against sgn_rhs and plain differences of the recorded states), and the VJP
+  from the recorded tape equals the VJP that evaluates the tape itself, bit
+  for bit (step and rollout).
 - The gauge-misfit rollout gradient (checkpointing + recomputation) against the
   oracle's complex-step derivative of the whole rollout, and against central
   finite differences of the GPU loss (eps = 1e-6) on the inversion workload.
@@ -125,17 +130,95 @@ def test_step_record_matches_step():
     s.close()
 
 
+def _shift(f, axis, k, bc):
+    """f at the neighbour k (+1 or -1) along `axis`; reflecting: the node
+    itself past a wall (the one-sided end rows of the operator)."""
+    if bc == PERIODIC:
+        return torch.roll(f, -k, dims=axis)
+    n = f.shape[axis]
+    idx = torch.arange(n, device=f.device) + k
+    idx = idx.clamp(0, n - 1)
+    return f.index_select(axis, idx)
+
+
+@pytest.mark.parametrize("bc", [PERIODIC, REFLECTING])
+@pytest.mark.parametrize("nx,ny", [(40, 23), (1000, 515)])     # 32x8 and 32x24 stage tiles
+def test_step_record_tape(bc, nx, ny):
+    """The taped record advances and records bit for bit as sgn_step_record;
+    its tape holds, for each stage state Q_s, k_u, k_v, k_w of sgn_rhs(Q_s)
+    and the unscaled differences of h, u, v, w, eta + 3/2 b (bit for bit),
+    1/h (to rounding of the reciprocal), and the continuity fluxes."""
+    p = inputs.smooth_state(nx, ny, bc, seed=12, xmax=1.3, ymax=0.9)
+    s = sgn.Solver.from_problem(p)
+    n = 2
+    q1, q2 = _t(p.q0), _t(p.q0)
+    st1 = torch.empty((n, 20, ny, nx), dtype=torch.float64, device="cuda")
+    st2 = torch.empty_like(st1)
+    tape = torch.full((n, 4 * sgn.TAPE_PLANES, ny, nx), float("nan"), dtype=torch.float64, device="cuda")
+    s.step_record(q1, p.dt, n, st1)
+    s.step_record(q2, p.dt, n, st2, tape)
+    assert torch.equal(q1, q2) and torch.equal(st1, st2)
+    assert bool(torch.isfinite(tape).all())
+    b = _t(p.b)
+    T = sgn.TAPE_PLANES
+    for m in range(n):
+        for stage in range(4):
+            X = st2[m, 5 * stage:5 * stage + 5].contiguous()
+            tp = tape[m, T * stage:T * stage + T]
+            k = s.rhs(X)
+            for f, slot in ((1, 18), (2, 19), (3, 20)):              # TP_KU, TP_KV, TP_KW
+                assert torch.equal(tp[slot], k[f])
+            F = X[4] + 1.5 * b
+            fields = [X[0], X[1], X[2], X[3], F]
+            for f in range(5):                                       # TP_DXH .. TP_DYF
+                dx = _shift(fields[f], 1, 1, bc) - _shift(fields[f], 1, -1, bc)
+                dy = _shift(fields[f], 0, 1, bc) - _shift(fields[f], 0, -1, bc)
+                tol = 0.0 if f < 4 else 1e-15 * float(F.abs().max())  # F is formed with one FMA
+                assert float((tp[2 + 2 * f] - dx).abs().max()) <= tol
+                assert float((tp[3 + 2 * f] - dy).abs().max()) <= tol
+            assert float((tp[0] * X[0] - 1).abs().max()) <= 5e-16          # TP_R
+            # A_x = u D_x h + h D_x u, A_y = v D_y h + h D_y v (one FMA each)
+            for slot, t1, t2 in ((16, X[1] * tp[2], X[0] * tp[4]), (17, X[2] * tp[3], X[0] * tp[7])):
+                err = (tp[slot] - (t1 + t2)).abs()
+                assert bool((err <= 5e-16 * (t1.abs() + t2.abs()) + 1e-300).all())
+    s.check()
+    s.close()
+
+
+@pytest.mark.parametrize("bc", [PERIODIC, REFLECTING])
+@pytest.mark.parametrize("nx,ny", [(40, 23), (1000, 515)])
+def test_step_vjp_tape_matches_step_vjp(bc, nx, ny):
+    """The VJP of a recorded step from its recorded tapes equals the VJP that
+    evaluates each stage's tape itself, bit for bit."""
+    p = inputs.smooth_state(nx, ny, bc, seed=13, xmax=1.3, ymax=0.9)
+    rng = np.random.default_rng(6)
+    s = sgn.Solver.from_problem(p)
+    q = _t(p.q0)
+    stash = torch.empty((1, 20, ny, nx), dtype=torch.float64, device="cuda")
+    tape = torch.empty((1, 4 * sgn.TAPE_PLANES, ny, nx), dtype=torch.float64, device="cuda")
+    s.step_record(q, p.dt, 1, stash, tape)
+    a = rng.standard_normal(p.q0.shape)
+    b0 = rng.standard_normal(p.b.shape)
+    qb1, bb1 = _t(a), _t(b0)
+    qb2, bb2 = _t(a), _t(b0)
+    s.step_vjp(stash[0], qb1, bb1, p.dt)
+    s.step_vjp(stash[0], qb2, bb2, p.dt, tape[0])
+    assert torch.equal(qb1, qb2) and torch.equal(bb1, bb2)
+    s.check()
+    s.close()
+
+
 def _inversion_problem(n, nsteps, every, ngauges=16, seed=1004):
     p = inputs.workload4(n=n, nsteps=nsteps, every=every, ngauges=ngauges, ndirs=5, seed=seed)
     return p
 
 
-def _gpu_loss_and_grad(p, obs, K, need_grad=True):
+def _gpu_loss_and_grad(p, obs, K, need_grad=True, tape=None):
     s = sgn.Solver.from_problem(p)
     gauges = torch.as_tensor(p.extra["gauges"], device="cuda")
     b = _t(p.b).requires_grad_(need_grad)
     h0 = _t(p.q0[0]).requires_grad_(need_grad)
-    out = adjoint.gauge_rollout(b, h0, s, p.dt, p.nsteps, p.extra["every"], gauges, K)
+    out = adjoint.gauge_rollout(b, h0, s, p.dt, p.nsteps, p.extra["every"], gauges, K, tape)
     loss = torch.sum((out - _t(obs)) ** 2)
     if need_grad:
         loss.backward()
@@ -183,7 +266,9 @@ def test_rollout_gradient_matches_oracle_tlm_checkpointed():
     gauges = p.extra["gauges"]
     qt = orc.init_aux(g, p.extra["b_true"], np.stack([p.extra["h_true0"]] + [np.zeros_like(p.b)] * 4))
     obs = orc.gauge_record(g, p.extra["b_true"], qt, p.dt, p.nsteps, p.extra["every"], gauges)
-    loss, gb, gh = _gpu_loss_and_grad(p, obs, K=100)
+    loss, gb, gh = _gpu_loss_and_grad(p, obs, K=100, tape=True)
+    _, gb2, gh2 = _gpu_loss_and_grad(p, obs, K=100, tape=False)     # tapes evaluated by the VJP
+    assert np.array_equal(gb, gb2) and np.array_equal(gh, gh2)
     q0 = orc.init_aux(g, p.b, p.q0)
     for d in p.extra["dirs"][:3]:
         dq = np.zeros_like(p.q0)
