@@ -85,8 +85,11 @@ __device__ __forceinline__ double flip_sign(double x, unsigned long long m) {
 // names follow node_rhs_src: Xu, Yu, ... are its bracket sums, A_x, A_y its
 // continuity fluxes, base2 = -P2/h, lom2 = 2 lam/3 (1 - rho), and a trailing
 // "b" marks a cotangent.
+#ifndef SGN_ADJ_POINT_MINB
+#define SGN_ADJ_POINT_MINB 3
+#endif
 template <int BC>
-__global__ void __launch_bounds__(ADJ_BLOCK) k_adj_point(AdjArgs a) {
+__global__ void __launch_bounds__(ADJ_BLOCK, SGN_ADJ_POINT_MINB) k_adj_point(AdjArgs a) {
     const Geom& G = a.G;
     const long long P = G.plane;
     const long long c = (long long)blockIdx.x * ADJ_BLOCK + threadIdx.x;

@@ -454,10 +454,14 @@ struct FactoredOps {        // the factored tile: products formed on request
 //    direction, applied once per equation.
 // The differences are unscaled (f_+ - f_-); sx, sy hold the operator's row
 // factor (1/(2dx) central, 1/dx on a reflecting wall's one-sided row).
-// With TAPE, tp receives the node's tape values (the TP_ enum).
+// With TAPE, tp (registers) receives the node's tape values (the TP_ enum).
 template <typename TC, int BC, typename Src, bool TAPE = false>
 __device__ __forceinline__ void node_rhs_src(const Src& S, int gi, int gj, const Geom& G, TC k[5],
                                              TC* tp = nullptr) {
+#define TPUT(slot, val)                          \
+    do {                                         \
+        if constexpr (TAPE) tp[(slot)] = (val);  \
+    } while (0)
     TC sx = GC(TC, cx2), sy = GC(TC, cy2), hsx = GC(TC, hcx2), hsy = GC(TC, hcy2);
     if (BC == BC_REFLECTING) {
         // one-sided first/last rows of the reflecting operator: (f1 - f0)/dx
@@ -485,11 +489,24 @@ __device__ __forceinline__ void node_rhs_src(const Src& S, int gi, int gj, const
     const TC hrsx = mul_(r, hsx), hrsy = mul_(r, hsy);          // r/(4dx) central
     const TC base2 = mul_(-SM_(OP_P2, POS_C), r);               // lam/3 rho^2 - 2g (h+b)
     const TC lom2 = fma_(-lam23, rho, lam23);                   // 2 lam/3 (1 - rho)
+    TPUT(TP_R, r);
+    TPUT(TP_BASE2, base2);
 
     const TC dxh = DXU(OP_H), dxu = DXU(OP_U), dxv = DXU(OP_V), dxw = DXU(OP_W), dxf = DXU(OP_E15);
     const TC dyh = DYU(OP_H), dyu = DYU(OP_U), dyv = DYU(OP_V), dyw = DYU(OP_W), dyf = DYU(OP_E15);
     const TC Ax = fma_(u, dxh, mul_(h, dxu));                   // u D_x h + h D_x u (unscaled)
     const TC Ay = fma_(v, dyh, mul_(h, dyv));
+    TPUT(TP_DXH, dxh); TPUT(TP_DYH, dyh); TPUT(TP_DXU, dxu); TPUT(TP_DYU, dyu);
+    TPUT(TP_DXV, dxv); TPUT(TP_DYV, dyv); TPUT(TP_DXW, dxw); TPUT(TP_DYW, dyw);
+    TPUT(TP_DXF, dxf); TPUT(TP_DYF, dyf); TPUT(TP_AX, Ax); TPUT(TP_AY, Ay);
+    if constexpr (TAPE) {
+        // values the expressions below form (the same operations on the same
+        // operands, so the same roundings)
+        TPUT(TP_XHU, sub_(DXU(OP_HU), Ax));
+        TPUT(TP_DXUU, DXU(OP_UU));
+        TPUT(TP_YHV, sub_(DYU(OP_HV), Ay));
+        TPUT(TP_DYVV, DYU(OP_VV));
+    }
 
     // h_t = -(u D_x h + h D_x u + v D_y h + h D_y v) + SAT
     TC kh = -fma_(sx, Ax, mul_(sy, Ay));
@@ -509,6 +526,7 @@ __device__ __forceinline__ void node_rhs_src(const Src& S, int gi, int gj, const
     Xu = fma_(lom2, dxf, Xu);
     const TC Yu = fma_(-u, Ay, fma_(hv, dyu, DYU(OP_HUV)));
     const TC ku = -fma_(hrsx, Xu, mul_(hrsy, Yu));
+    TPUT(TP_KU, ku);
 
     // 2h v_t: the same with x and y (and u and v) exchanged
     TC Yv = fma_(base2, dyh, DYU(OP_P2));
@@ -517,27 +535,18 @@ __device__ __forceinline__ void node_rhs_src(const Src& S, int gi, int gj, const
     Yv = fma_(lom2, dyf, Yv);
     const TC Xv = fma_(-v, Ax, fma_(hu, dxv, DXU(OP_HUV)));
     const TC kv = -fma_(hrsy, Yv, mul_(hrsx, Xv));
+    TPUT(TP_KV, kv);
 
     // h w_t = lam (1 - rho) - 1/2 [ D_x(huw) + hu D_x w - w A_x + D_y(hvw) + hv D_y w - w A_y ]
     const TC Xw = fma_(-w, Ax, fma_(hu, dxw, DXU(OP_HUW)));
     const TC Yw = fma_(-w, Ay, fma_(hv, dyw, DYU(OP_HVW)));
     const TC kw = fma_(r, fma_(-lam, rho, lam), -fma_(hrsx, Xw, mul_(hrsy, Yw)));
+    TPUT(TP_KW, kw);
 
     // eta_t = w - u D_x(eta + 3/2 b) - v D_y(eta + 3/2 b)
     const TC ke = fma_(-v, mul_(sy, dyf), fma_(-u, mul_(sx, dxf), w));
     k[0] = kh; k[1] = ku; k[2] = kv; k[3] = kw; k[4] = ke;
-    if constexpr (TAPE) {
-        // the values the expressions above formed (the same operations on the
-        // same operands, so the same roundings)
-        const TC xhu = sub_(DXU(OP_HU), Ax), dxuu = DXU(OP_UU);
-        const TC yhv = sub_(DYU(OP_HV), Ay), dyvv = DYU(OP_VV);
-        tp[TP_R] = r; tp[TP_BASE2] = base2;
-        tp[TP_DXH] = dxh; tp[TP_DYH] = dyh; tp[TP_DXU] = dxu; tp[TP_DYU] = dyu;
-        tp[TP_DXV] = dxv; tp[TP_DYV] = dyv; tp[TP_DXW] = dxw; tp[TP_DYW] = dyw;
-        tp[TP_DXF] = dxf; tp[TP_DYF] = dyf; tp[TP_DXUU] = dxuu; tp[TP_DYVV] = dyvv;
-        tp[TP_XHU] = xhu; tp[TP_YHV] = yhv; tp[TP_AX] = Ax; tp[TP_AY] = Ay;
-        tp[TP_KU] = ku; tp[TP_KV] = kv; tp[TP_KW] = kw;
-    }
+#undef TPUT
 #undef DXU
 #undef DYU
 #undef SM_
@@ -1047,10 +1056,21 @@ constexpr int kStageMinBlocks =
 
 // R: rows per thread (tile height 8 R); the compute type's StageShape, or 1
 // for FP64 grids too small to spread 32 x 24 tiles evenly over the SMs.
-// TAPE: also write the tape of every right-hand-side evaluation (FP64).
+// TAPE: also write the tape of every right-hand-side evaluation (FP64).  The
+// tape's values stay in registers until the node's stores; with 32 x 8 tiles
+// (35 KB of shared memory) the registers are limited to what SGN_TAPE_MINB
+// resident blocks per SM allow (32 x 24 tiles: two blocks by shared memory).
+#ifndef SGN_TAPE_MINB
+#define SGN_TAPE_MINB 3
+#endif
+template <typename TC, int MODE, int BC, int R, bool TAPE>
+constexpr int kStageLaunchMinBlocks =
+    TAPE ? (R == 1 ? SGN_TAPE_MINB : 2) : kStageMinBlocks<TC, TC, MODE, BC>;
 template <typename TC, typename TIN, typename TA, int BC, int MODE, int R = StageShape<TC>::rows,
           bool TAPE = false>
-__global__ void __launch_bounds__(BLOCK_THREADS, (kStageMinBlocks<TC, TA, MODE, BC>))
+__global__ void __launch_bounds__(BLOCK_THREADS,
+                                  (TAPE ? kStageLaunchMinBlocks<TC, MODE, BC, R, true>
+                                        : kStageMinBlocks<TC, TA, MODE, BC>))
 k_stage(StageArgs<TC, TIN, TA> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TC* sm = reinterpret_cast<TC*>(smem_raw);
