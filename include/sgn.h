@@ -112,9 +112,9 @@ typedef struct sgn_ctx sgn_ctx;
 /* Create a context for one grid.  Validates `p`, allocates the scratch and
  * copies the bathymetry b_dev (double, nx*ny, device) into the context.
  * Synchronizes.  On failure *out is NULL.  SGN_F64 contexts pick the tile
- * height of their stage kernels for the current device: 32 x 8 tiles where
- * 32 x 24 tiles would load the SMs unevenly (small grids), else 32 x 24; the
- * results are the same either way. */
+ * height of their stage kernels (32 x 8, 32 x 16 or 32 x 24) for the SM count
+ * of the current device: the one with the least FP64 work on the most loaded
+ * SM; the results are the same at every height. */
 SGN_API sgn_status sgn_create(const sgn_params* p, const void* b_dev, sgn_ctx** out);
 
 /* Free the context and its scratch.  Synchronizes.  NULL is a no-op. */
@@ -416,6 +416,15 @@ SGN_API sgn_status sgn_batch_autotune(sgn_batch* batch, const void* q_dev, int* 
 
 /* Synchronize `stream` and report (and clear) the latched device flag. */
 SGN_API sgn_status sgn_check(sgn_ctx* ctx, void* stream);
+
+/* The tile height of an SGN_F64 context's stage kernels: 32 x (8 rows), rows
+ * in {1, 2, 3}; sgn_create picks it (see there), sgn_set_tile_rows overrides
+ * it (a height whose launch grid would exceed 65535 rows of tiles is
+ * SGN_E_INVAL; other precisions: SGN_E_UNSUPPORTED).  Every height gives the
+ * same results bit for bit.  Not thread-safe against launches on the
+ * context. */
+SGN_API sgn_status sgn_set_tile_rows(sgn_ctx* ctx, int rows);
+SGN_API sgn_status sgn_tile_rows(const sgn_ctx* ctx, int* rows);
 
 /* Human-readable name of a status, and the last error message of the calling
  * thread (never NULL). */

@@ -79,7 +79,7 @@ struct sgn_ctx {
     long long nband = 0;         // 32 x 8 bands of the grid: partials of the diagnostics
     dim3 grid;                   // blocks of the compute type's stage tile (StageShape)
     int rows = 0;                // tile height of the RK4 / RHS / diagnostics launches of k_stage
-    dim3 grid1;                  // blocks of 32 x 8 tiles (rows == 1)
+    dim3 gridr;                  // FP64: blocks of the 32 x (8 rows) tiles of the chosen height
     double* adj = nullptr;       // adjoint scratch (FP64): accumulator + two cotangents
     double* bs = nullptr;        // adaptive integrator scratch (8-byte slots, 40 planes)
     double* rrk = nullptr;       // relaxation scratch (FP64): plain RK4 update (5 planes), partials, sums
@@ -137,20 +137,26 @@ cudaError_t stage_attr() {
     return smem_optin<sgn::k_stage<TC, TIN, TA, BC, MODE, R, TAPE>>(sgn::stage_smem_bytes<TC, MODE>(R));
 }
 
-// The stage kernel with the context's tile height: FP64 contexts on small
-// grids use 32 x 8 tiles (c->rows == 1, see sgn_create), all others the
-// compute type's StageShape.  TAPE: the FP64 kernel that also writes the tape.
+template <typename TC, typename TIN, typename TA, int BC, int MODE, int R, bool TAPE>
+cudaError_t launch_rows(dim3 grid, const StageArgs<TC, TIN, TA>& a, cudaStream_t s) {
+    const cudaError_t attr_err = stage_attr<TC, TIN, TA, BC, MODE, R, TAPE>();
+    if (attr_err != cudaSuccess) return attr_err;
+    sgn::k_stage<TC, TIN, TA, BC, MODE, R, TAPE>
+        <<<grid, dim3(sgn::TILE_X, sgn::THREADS_Y), sgn::stage_smem_bytes<TC, MODE>(R), s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// The stage kernel with the context's tile height: FP64 contexts take the
+// height sgn_create chose (c->rows: 32 x 8, 32 x 16 or 32 x 24 tiles), all
+// others the compute type's StageShape.  TAPE: the FP64 kernel that also
+// writes the tape.
 template <typename TC, typename TIN, typename TA, int BC, int MODE, bool TAPE = false>
 cudaError_t launch_stage(const sgn_ctx* c, const StageArgs<TC, TIN, TA>& a, cudaStream_t s) {
     if constexpr (std::is_same<TC, double>::value) {
-        if (c->rows == 1) {
-            const cudaError_t attr_err = stage_attr<TC, TIN, TA, BC, MODE, 1, TAPE>();
-            if (attr_err != cudaSuccess) return attr_err;
-            sgn::k_stage<TC, TIN, TA, BC, MODE, 1, TAPE>
-                <<<c->grid1, dim3(sgn::TILE_X, sgn::THREADS_Y), sgn::stage_smem_bytes<TC, MODE>(1), s>>>(a);
-            count_launch();
-            return cudaGetLastError();
-        }
+        static_assert(sgn::StageShape<double>::rows == 3, "FP64 tile heights 8, 16, 24");
+        if (c->rows == 1) return launch_rows<TC, TIN, TA, BC, MODE, 1, TAPE>(c->gridr, a, s);
+        if (c->rows == 2) return launch_rows<TC, TIN, TA, BC, MODE, 2, TAPE>(c->gridr, a, s);
     }
     constexpr int R = sgn::StageShape<TC>::rows;
     const cudaError_t attr_err = stage_attr<TC, TIN, TA, BC, MODE, R, TAPE>();
@@ -293,6 +299,7 @@ struct AttrOp {
     cudaError_t operator()() {
         if constexpr (std::is_same<TC, double>::value) {
             if (c->rows == 1) return attrs<TC, TA, BC, 1>();
+            if (c->rows == 2) return attrs<TC, TA, BC, 2>();
         }
         return attrs<TC, TA, BC, sgn::StageShape<TC>::rows>();
     }
@@ -1036,20 +1043,32 @@ sgn_status sgn_create(const sgn_params* p, const void* b_dev, sgn_ctx** out) {
     c->grid = dim3((p->nx + sgn::TILE_X - 1) / sgn::TILE_X, (p->ny + tile_y - 1) / tile_y);
     c->nblk = (long long)c->grid.x * c->grid.y;
     c->nband = (long long)c->grid.x * ((p->ny + sgn::THREADS_Y - 1) / sgn::THREADS_Y);   // >= nblk
-    c->grid1 = dim3(c->grid.x, (unsigned)((p->ny + sgn::THREADS_Y - 1) / sgn::THREADS_Y));
     c->rows = tile_y / sgn::THREADS_Y;
+    c->gridr = c->grid;
     if (p->prec == SGN_F64) {
         // The FP64 stage kernels are bound by each SM's FP64 pipe, so a launch
-        // takes as long as its most loaded SM: with b blocks over S SMs that is
-        // ceil(b/S) blocks against b/S on average.  32 x 8 tiles (four times the
-        // blocks) recompute more halo operands (x 1.33 instead of x 1.15: about
-        // 3.4% more FP64 work); they are used where their balance wins by 5%.
+        // takes as long as its most loaded SM: ceil(b/S) blocks of b over S
+        // SMs.  A 32 x 8R tile costs 256 R nodes x 68.75 FP64 operations (RHS
+        // and stage algebra) plus 34 (8R + 2) halo nodes x 15 (operands).  The
+        // height with the least work on the most loaded SM is taken (a lower
+        // one only where it saves more than 2%).
         int dev = 0, sms = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0) {
-            auto balance = [&](double blocks) { return blocks / sms / std::ceil(blocks / sms); };
-            const double b3 = (double)c->grid.x * c->grid.y, b1 = (double)c->grid1.x * c->grid1.y;
-            if (c->grid1.y <= 65535 && balance(b1) / 1.034 > 1.05 * balance(b3)) c->rows = 1;
+            auto cost = [&](int R) {
+                const double blocks = (double)c->grid.x * (double)((p->ny + 8 * R - 1) / (8 * R));
+                return std::ceil(blocks / sms) * (256.0 * R * 68.75 + 34.0 * (8 * R + 2) * 15.0);
+            };
+            double best = cost(c->rows);
+            for (int R = c->rows - 1; R >= 1; R--) {
+                const long long gy = (p->ny + 8 * R - 1) / (8 * R);
+                const double cr = cost(R);
+                if (gy <= 65535 && cr < 0.98 * best) {
+                    best = cr;
+                    c->rows = R;
+                }
+            }
+            c->gridr = dim3(c->grid.x, (unsigned)((p->ny + 8 * c->rows - 1) / (8 * c->rows)));
         } else {
             cudaGetLastError();
         }
@@ -1212,6 +1231,28 @@ sgn_status sgn_mass_energy(sgn_ctx* c, const void* q_dev, double* out, void* str
 sgn_status sgn_check(sgn_ctx* c, void* stream) {
     if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
     return read_flag(c, static_cast<cudaStream_t>(stream));
+}
+
+sgn_status sgn_set_tile_rows(sgn_ctx* c, int rows) {
+    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
+    if (c->p.prec != SGN_F64) return fail(SGN_E_UNSUPPORTED, "the tile height is chosen for SGN_F64 contexts only");
+    if (rows < 1 || rows > 3) return fail(SGN_E_INVAL, "rows = %d: need 1, 2 or 3", rows);
+    const long long gy = (c->p.ny + 8LL * rows - 1) / (8LL * rows);
+    if (gy > 65535) return fail(SGN_E_INVAL, "ny = %d exceeds the launch-grid limit at rows = %d", c->p.ny, rows);
+    if (rows != c->rows && c->step_exec) {
+        // the replayed graph holds the launches of the old tile height
+        cudaGraphExecDestroy(c->step_exec);
+        c->step_exec = nullptr;
+    }
+    c->rows = rows;
+    c->gridr = dim3(c->grid.x, (unsigned)gy);
+    return SGN_OK;
+}
+
+sgn_status sgn_tile_rows(const sgn_ctx* c, int* rows) {
+    if (!c || !rows) return fail(SGN_E_INVAL, "ctx and rows must not be NULL");
+    *rows = c->rows;
+    return SGN_OK;
 }
 
 sgn_status sgn_rhs_vjp(sgn_ctx* c, const void* q_dev, const void* abar_dev, void* qbar_dev,

@@ -1054,18 +1054,19 @@ constexpr int kStageMinBlocks =
     : (kStoreK1<TC, TA> && (MODE == MODE_S1K || (MODE == MODE_S4 && BC == BC_PERIODIC))) ? SGN_F32_LIGHT_MINB
                                                                                           : StageMinBlocks<TC, TA>::value;
 
-// R: rows per thread (tile height 8 R); the compute type's StageShape, or 1
-// for FP64 grids too small to spread 32 x 24 tiles evenly over the SMs.
+// R: rows per thread (tile height 8 R); the compute type's StageShape, or,
+// for FP64 grids whose 32 x 24 tiles would load the SMs unevenly, 1 or 2.
 // TAPE: also write the tape of every right-hand-side evaluation (FP64).  The
-// tape's values stay in registers until the node's stores; with 32 x 8 tiles
-// (35 KB of shared memory) the registers are limited to what SGN_TAPE_MINB
-// resident blocks per SM allow (32 x 24 tiles: two blocks by shared memory).
+// tape's values stay in registers until the node's stores; with 32 x 8 and
+// 32 x 16 tiles (35 and 73 KB of shared memory) the registers are limited to
+// what SGN_TAPE_MINB resident blocks per SM allow (32 x 24 tiles: two blocks
+// by shared memory).
 #ifndef SGN_TAPE_MINB
 #define SGN_TAPE_MINB 3
 #endif
 template <typename TC, int MODE, int BC, int R, bool TAPE>
 constexpr int kStageLaunchMinBlocks =
-    TAPE ? (R == 1 ? SGN_TAPE_MINB : 2) : kStageMinBlocks<TC, TC, MODE, BC>;
+    TAPE ? (R <= 2 ? SGN_TAPE_MINB : 2) : kStageMinBlocks<TC, TC, MODE, BC>;
 template <typename TC, typename TIN, typename TA, int BC, int MODE, int R = StageShape<TC>::rows,
           bool TAPE = false>
 __global__ void __launch_bounds__(BLOCK_THREADS,

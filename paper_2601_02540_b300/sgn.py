@@ -51,6 +51,8 @@ _SIGNATURES = {
     "sgn_rhs_vjp": (ctypes.c_int, [_V, _V, _V, _V, _V, _V]),
     "sgn_step_record": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_int, _V, _V]),
     "sgn_step_vjp": (ctypes.c_int, [_V, _V, _V, _V, ctypes.c_double, _V]),
+    "sgn_set_tile_rows": (ctypes.c_int, [_V, ctypes.c_int]),
+    "sgn_tile_rows": (ctypes.c_int, [_V, _V]),
     "sgn_step_record_tape": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_int, _V, _V, _V]),
     "sgn_step_vjp_tape": (ctypes.c_int, [_V, _V, _V, _V, _V, ctypes.c_double, _V]),
     "sgn_batch_create": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int, _V, _V]),
@@ -404,6 +406,15 @@ class Solver:
 
     def check(self) -> None:
         sgn_check(self.ctx)
+
+    def set_tile_rows(self, rows: int) -> None:
+        """Override the FP64 stage tile height (32 x 8 rows, rows in 1..3)."""
+        _ok(lib().sgn_set_tile_rows(self.ctx, int(rows)), "sgn_set_tile_rows")
+
+    def tile_rows(self) -> int:
+        r = ctypes.c_int()
+        _ok(lib().sgn_tile_rows(self.ctx, ctypes.byref(r)), "sgn_tile_rows")
+        return r.value
 
     def close(self) -> None:
         if self.ctx is not None and self.ctx.value:

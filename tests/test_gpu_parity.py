@@ -299,3 +299,56 @@ def test_fp64_fma_rate_measurement():
     assert n == sms * 8 * 256 * 16 * 256 and sec > 0
     rate = n / sec
     assert 1e10 < rate < 2e12, rate          # FMA per second: B300 ~5e11
+
+
+@pytest.mark.parametrize("bc", [PERIODIC, REFLECTING])
+def test_fp64_tile_heights_agree_bitwise(bc):
+    """Every FP64 stage tile height (32x8, 32x16, 32x24) gives the same states,
+    RHS and diagnostics bit for bit: the per-node arithmetic and the 32x8 band
+    sums do not depend on the tile (direct steps and graph replays, a ragged
+    grid of several tiles of each height)."""
+    p = inputs.smooth_state(100, 77, bc, seed=31, xmax=1.3, ymax=0.9)
+    s = gu.solver(p, "f64")
+    ref = None
+    for rows in (1, 2, 3):
+        s.set_tile_rows(rows)
+        assert s.tile_rows() == rows
+        q = s.state(p.q0)
+        s.step(q, p.dt, 60)
+        out = (q, s.rhs(q), s.mass_energy(q))
+        if ref is None:
+            ref = out
+        else:
+            assert torch.equal(out[0], ref[0]) and torch.equal(out[1], ref[1]), rows
+            assert out[2] == ref[2], rows
+    s.check()
+    s.close()
+
+
+@pytest.mark.parametrize("nx,ny", [(64, 64), (512, 512), (1024, 512), (8192, 512)])
+def test_fp64_tile_height_choice(nx, ny):
+    """sgn_create takes the height with the least FP64 work on the most
+    loaded SM (blocks per SM rounded up x the operations of one tile:
+    256 R x 68.75 + 34 (8 R + 2) x 15), a lower one only where it saves more
+    than 2%; float precisions keep their own tile."""
+    p = inputs.smooth_state(nx, ny, REFLECTING, seed=3)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+
+    def cost(R):
+        blocks = -(-nx // 32) * -(-ny // (8 * R))
+        return -(-blocks // sms) * (256 * R * 68.75 + 34 * (8 * R + 2) * 15)
+
+    want, best = 3, cost(3)
+    for R in (2, 1):
+        if cost(R) < 0.98 * best:
+            want, best = R, cost(R)
+    s = gu.solver(p, "f64")
+    assert s.tile_rows() == want
+    with pytest.raises(sgn.SgnError):
+        s.set_tile_rows(4)
+    s.close()
+    s = gu.solver(p, "f32")
+    with pytest.raises(sgn.SgnError) as ei:
+        s.set_tile_rows(1)
+    assert ei.value.status == 7          # SGN_E_UNSUPPORTED
+    s.close()
