@@ -632,15 +632,32 @@ constexpr double P5_BHAT[6] = {0.14576960111557976478, 0.13123039888442023522, 0
 // one dt_next = dt rho(eps^(1/3)).
 constexpr double P5_PI_B1 = 0.7, P5_PI_B2 = -0.4, P5_PI_K = 3.0, P5_ERR_FLOOR = 1e-10, P5_SAFETY = 0.9;
 
-template <typename TC, int BC, int MODE>
-cudaError_t launch_p5(const sgn_ctx* c, const sgn::P5Args& a, cudaStream_t s) {
-    auto kern = sgn::k_p5_stage<TC, BC, MODE>;
-    const size_t smem = sgn::stage_smem_bytes<TC, sgn::MODE_RHS>(sgn::StageShape<TC>::rows);
-    const cudaError_t attr_err = smem_optin<sgn::k_p5_stage<TC, BC, MODE>>(smem);
+template <typename TC, int BC, int MODE, int R>
+cudaError_t launch_p5_rows(dim3 grid, const sgn::P5Args& a, cudaStream_t s) {
+    const size_t smem = sgn::stage_smem_bytes<TC, sgn::MODE_RHS>(R);
+    const cudaError_t attr_err = smem_optin<sgn::k_p5_stage<TC, BC, MODE, R>>(smem);
     if (attr_err != cudaSuccess) return attr_err;
-    kern<<<c->grid, dim3(sgn::TILE_X, sgn::THREADS_Y), smem, s>>>(a);
+    sgn::k_p5_stage<TC, BC, MODE, R><<<grid, dim3(sgn::TILE_X, sgn::THREADS_Y), smem, s>>>(a);
     count_launch();
     return cudaGetLastError();
+}
+
+// The pair's stage kernels take the context's FP64 tile height, as the RK4
+// stage kernels do (the FSAL stage writes one error partial per block).
+template <typename TC, int BC, int MODE>
+cudaError_t launch_p5(const sgn_ctx* c, const sgn::P5Args& a, cudaStream_t s) {
+    if constexpr (std::is_same<TC, double>::value) {
+        if (c->rows == 1) return launch_p5_rows<TC, BC, MODE, 1>(c->gridr, a, s);
+        if (c->rows == 2) return launch_p5_rows<TC, BC, MODE, 2>(c->gridr, a, s);
+    }
+    return launch_p5_rows<TC, BC, MODE, sgn::StageShape<TC>::rows>(c->grid, a, s);
+}
+
+// Blocks of the pair's launches (error partials to reduce).
+template <typename TC>
+long long p5_blocks(const sgn_ctx* c) {
+    if (std::is_same<TC, double>::value) return (long long)c->gridr.x * c->gridr.y;
+    return c->nblk;
 }
 
 template <typename TC, int BC>
@@ -719,7 +736,7 @@ sgn_status run_adaptive_p5(sgn_ctx* c, double* q_user, double t0, double t_end, 
         a.c_e6 = 0.0 - P5_BHAT[5];
         a.dt = h;
         CUDA_TRY((launch_p5<TC, BC, sgn::P5_FSAL>(c, a, s)), "pair FSAL stage");
-        sgn::k_reduce_partials<<<1, 256, 0, s>>>(c->partials, c->nblk, c->dout);
+        sgn::k_reduce_partials<<<1, 256, 0, s>>>(c->partials, p5_blocks<TC>(c), c->dout);
         count_launch();
         CUDA_TRY(cudaGetLastError(), "error reduction");
         CUDA_TRY(cudaMemcpyAsync(c->hout, c->dout, sizeof(double), cudaMemcpyDeviceToHost, s), "copy error");

@@ -65,11 +65,12 @@ __device__ __forceinline__ void p5_input(const P5Args& a, long long c, long long
     }
 }
 
-template <typename TC, int BC, int MODE>
+// R: rows per thread (tile height 8 R): the compute type's StageShape, or
+// for FP64 the context's height (32 x 8, 32 x 16 or 32 x 24, see sgn_create).
+template <typename TC, int BC, int MODE, int R = StageShape<TC>::rows>
 __global__ void __launch_bounds__(BLOCK_THREADS, StageShape<TC>::min_blocks) k_p5_stage(P5Args a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TC* sm = reinterpret_cast<TC*>(smem_raw);
-    constexpr int R = StageShape<TC>::rows;
     constexpr int HX = TILE_X + 2, HN = HX * (THREADS_Y * R + 2);
     const Geom& G = a.G;
     const long long P = G.plane;
