@@ -50,11 +50,12 @@ struct BsArgs {
 // TC: compute type of the RHS (double, or df64 with the float-pair stage
 // arithmetic).  The slopes and Y3 are stored in the compute type (a float pair
 // takes 8 bytes, like a double); the state q_n and the candidate q1 in double.
-template <typename TC, int BC, int MODE>
+// R: rows per thread (tile height 8 R): the compute type's StageShape, or for
+// FP64 the context's height.
+template <typename TC, int BC, int MODE, int R = StageShape<TC>::rows>
 __global__ void __launch_bounds__(BLOCK_THREADS, StageShape<TC>::min_blocks) k_bs3_stage(BsArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TC* sm = reinterpret_cast<TC*>(smem_raw);
-    constexpr int R = StageShape<TC>::rows;
     constexpr int HX = TILE_X + 2, HN = HX * (THREADS_Y * R + 2);
     const Geom& G = a.G;
     const long long P = G.plane;

@@ -492,15 +492,32 @@ sgn_status need_f64(const sgn_ctx* c, const char* what) {
 }
 
 // ---- adaptive integrator (Sec. 6), second pair: Bogacki-Shampine 3(2), host-side control
-template <typename TC, int BC, int MODE>
-cudaError_t launch_bs3(const sgn_ctx* c, const sgn::BsArgs& a, cudaStream_t s) {
-    auto kern = sgn::k_bs3_stage<TC, BC, MODE>;
-    const size_t smem = sgn::stage_smem_bytes<TC, sgn::MODE_RHS>(sgn::StageShape<TC>::rows);
-    const cudaError_t attr_err = smem_optin<sgn::k_bs3_stage<TC, BC, MODE>>(smem);
+template <typename TC, int BC, int MODE, int R>
+cudaError_t launch_bs3_rows(dim3 grid, const sgn::BsArgs& a, cudaStream_t s) {
+    const size_t smem = sgn::stage_smem_bytes<TC, sgn::MODE_RHS>(R);
+    const cudaError_t attr_err = smem_optin<sgn::k_bs3_stage<TC, BC, MODE, R>>(smem);
     if (attr_err != cudaSuccess) return attr_err;
-    kern<<<c->grid, dim3(sgn::TILE_X, sgn::THREADS_Y), smem, s>>>(a);
+    sgn::k_bs3_stage<TC, BC, MODE, R><<<grid, dim3(sgn::TILE_X, sgn::THREADS_Y), smem, s>>>(a);
     count_launch();
     return cudaGetLastError();
+}
+
+// The pair's stage kernels take the context's FP64 tile height, as the RK4
+// stage kernels do (the last stage writes one error partial per block).
+template <typename TC, int BC, int MODE>
+cudaError_t launch_bs3(const sgn_ctx* c, const sgn::BsArgs& a, cudaStream_t s) {
+    if constexpr (std::is_same<TC, double>::value) {
+        if (c->rows == 1) return launch_bs3_rows<TC, BC, MODE, 1>(c->gridr, a, s);
+        if (c->rows == 2) return launch_bs3_rows<TC, BC, MODE, 2>(c->gridr, a, s);
+    }
+    return launch_bs3_rows<TC, BC, MODE, sgn::StageShape<TC>::rows>(c->grid, a, s);
+}
+
+// Blocks of the adaptive pairs' launches (error partials to reduce).
+template <typename TC>
+long long pair_blocks(const sgn_ctx* c) {
+    if (std::is_same<TC, double>::value) return (long long)c->gridr.x * c->gridr.y;
+    return c->nblk;
 }
 
 // Bogacki-Shampine 3(2): weights of the third-order solution and of the
@@ -572,7 +589,7 @@ sgn_status run_adaptive(sgn_ctx* c, double* q_user, double t0, double t_end, dou
         a.ce3 = h * BS_E3;
         a.ce4 = h * BS_E4;
         CUDA_TRY((launch_bs3<TC, BC, sgn::BS_K4>(c, a, s)), "adaptive stage 4");
-        sgn::k_reduce_partials<<<1, 256, 0, s>>>(c->partials, c->nblk, c->dout);
+        sgn::k_reduce_partials<<<1, 256, 0, s>>>(c->partials, pair_blocks<TC>(c), c->dout);
         count_launch();
         CUDA_TRY(cudaGetLastError(), "error reduction");
         CUDA_TRY(cudaMemcpyAsync(c->hout, c->dout, sizeof(double), cudaMemcpyDeviceToHost, s), "copy error");
@@ -653,12 +670,6 @@ cudaError_t launch_p5(const sgn_ctx* c, const sgn::P5Args& a, cudaStream_t s) {
     return launch_p5_rows<TC, BC, MODE, sgn::StageShape<TC>::rows>(c->grid, a, s);
 }
 
-// Blocks of the pair's launches (error partials to reduce).
-template <typename TC>
-long long p5_blocks(const sgn_ctx* c) {
-    if (std::is_same<TC, double>::value) return (long long)c->gridr.x * c->gridr.y;
-    return c->nblk;
-}
 
 template <typename TC, int BC>
 sgn_status run_adaptive_p5(sgn_ctx* c, double* q_user, double t0, double t_end, double dt0, double rtol,
@@ -736,7 +747,7 @@ sgn_status run_adaptive_p5(sgn_ctx* c, double* q_user, double t0, double t_end, 
         a.c_e6 = 0.0 - P5_BHAT[5];
         a.dt = h;
         CUDA_TRY((launch_p5<TC, BC, sgn::P5_FSAL>(c, a, s)), "pair FSAL stage");
-        sgn::k_reduce_partials<<<1, 256, 0, s>>>(c->partials, p5_blocks<TC>(c), c->dout);
+        sgn::k_reduce_partials<<<1, 256, 0, s>>>(c->partials, pair_blocks<TC>(c), c->dout);
         count_launch();
         CUDA_TRY(cudaGetLastError(), "error reduction");
         CUDA_TRY(cudaMemcpyAsync(c->hout, c->dout, sizeof(double), cudaMemcpyDeviceToHost, s), "copy error");
