@@ -92,7 +92,7 @@ typedef enum {
     SGN_E_NONPOSITIVE_H = 4,  /* a stage input had h <= 0 (dry state; excluded by the paper) */
     SGN_E_NONFINITE = 5,      /* a stage input had a non-finite h */
     SGN_E_TIMEOUT = 6,        /* a bounded device wait gave up */
-    SGN_E_UNSUPPORTED = 7     /* valid request this build does not implement */
+    SGN_E_UNSUPPORTED = 7     /* valid request the library does not implement */
 } sgn_status;
 
 typedef enum { SGN_BC_PERIODIC = 0, SGN_BC_REFLECTING = 1 } sgn_bc;
