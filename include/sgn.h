@@ -426,6 +426,17 @@ SGN_API sgn_status sgn_check(sgn_ctx* ctx, void* stream);
 SGN_API sgn_status sgn_set_tile_rows(sgn_ctx* ctx, int rows);
 SGN_API sgn_status sgn_tile_rows(const sgn_ctx* ctx, int* rows);
 
+/* SGN_F32 contexts: on = 1 (default) advances sgn_step two RK4 stages per
+ * launch (stages 1-2 and 3-4: the first stage of each pair is evaluated on
+ * the tile grown by one node and its result stays in shared memory), 37
+ * plane accesses per node and step instead of 74; on = 0 runs one launch
+ * per stage.  The same states bit for bit either way.  The fused step
+ * writes q_{n+1} alternately to q and to context scratch, so an odd step
+ * count ends with one device copy into q.  sgn_step_diag always runs one
+ * launch per stage.  Other precisions: SGN_E_UNSUPPORTED.  Not thread-safe
+ * against launches on the context. */
+SGN_API sgn_status sgn_set_stage_fusion(sgn_ctx* ctx, int on);
+
 /* Human-readable name of a status, and the last error message of the calling
  * thread (never NULL). */
 SGN_API const char* sgn_status_str(sgn_status s);

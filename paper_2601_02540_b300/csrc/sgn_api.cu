@@ -7,6 +7,7 @@
 #include "sgn_p5.cuh"
 #include "sgn_rrk.cuh"
 #include "sgn_mms.cuh"
+#include "sgn_fused.cuh"
 
 #include <algorithm>
 #include <atomic>
@@ -79,6 +80,7 @@ struct sgn_ctx {
     long long nband = 0;         // 32 x 8 bands of the grid: partials of the diagnostics
     dim3 grid;                   // blocks of the compute type's stage tile (StageShape)
     int rows = 0;                // tile height of the RK4 / RHS / diagnostics launches of k_stage
+    int fuse = 0;                // FP32: two RK4 stages per launch (sgn_set_stage_fusion)
     dim3 gridr;                  // FP64: blocks of the 32 x (8 rows) tiles of the chosen height
     double* adj = nullptr;       // adjoint scratch (FP64): accumulator + two cotangents
     double* bs = nullptr;        // adaptive integrator scratch (8-byte slots, 40 planes)
@@ -180,8 +182,54 @@ StageArgs<TC, TIN, TA> base_args(const sgn_ctx* c) {
 
 // nsteps RK4 steps; with `mon` the fourth stage also reduces the mass and
 // energies of each new state into mon[NDIAG n ..] (mode S4D).
+// FP32 steps with two stages per launch (sgn_fused.cuh): S12 and S34 per
+// step; q_{n+1} goes to the other of q and the context's Qb (S34 reads q_n on
+// its halo), and an odd step count ends with a copy back into q.
+template <typename TC, typename TA, int BC>
+cudaError_t run_steps_fused(sgn_ctx* c, TA* q, double dt, int nsteps, cudaStream_t s) {
+    constexpr int R = sgn::StageShape<TC>::rows;
+    const size_t smem = sgn::FusedLayout<R>::template bytes<TC>();
+    cudaError_t e = smem_optin<sgn::k_fused<TC, TA, BC, sgn::FUSED_S12, R>>(smem);
+    if (e == cudaSuccess) e = smem_optin<sgn::k_fused<TC, TA, BC, sgn::FUSED_S34, R>>(smem);
+    if (e != cudaSuccess) return e;
+    sgn::FusedArgs<TC, TA> f;
+    std::memset(&f, 0, sizeof(f));
+    f.b = static_cast<const TC*>(c->bT);
+    f.flag = c->flag;
+    f.G = c->G;
+    f.acc = static_cast<TA*>(c->acc);
+    // the coefficients of run_steps, rounded the same way
+    f.c_a1 = (TA)(dt / 6.0); f.c_a2 = (TA)(dt / 3.0); f.c_a3 = (TA)(dt / 3.0); f.c_a4 = (TA)(dt / 6.0);
+    f.c_q1 = (TA)(dt / 2.0); f.c_q2 = (TA)(dt / 2.0); f.c_q3 = (TA)dt;
+    static_assert(std::is_same<TC, TA>::value, "Qb holds a state");
+    TA* cur = q;
+    TA* nxt = static_cast<TA*>(c->Qb);
+    const dim3 block(sgn::TILE_X, sgn::THREADS_Y);
+    for (int n = 0; n < nsteps; n++) {
+        sgn::FusedArgs<TC, TA> f12 = f;
+        f12.q = cur;
+        f12.Qout = static_cast<TC*>(c->Qa);
+        sgn::k_fused<TC, TA, BC, sgn::FUSED_S12, R><<<c->grid, block, smem, s>>>(f12);
+        count_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        sgn::FusedArgs<TC, TA> f34 = f;
+        f34.q = cur;
+        f34.X = static_cast<const TC*>(c->Qa);
+        f34.out = nxt;
+        sgn::k_fused<TC, TA, BC, sgn::FUSED_S34, R><<<c->grid, block, smem, s>>>(f34);
+        count_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        std::swap(cur, nxt);
+    }
+    if (cur != q) e = cudaMemcpyAsync(q, cur, (size_t)5 * c->G.plane * sizeof(TA), cudaMemcpyDeviceToDevice, s);
+    return e;
+}
+
 template <typename TC, typename TA, int BC>
 cudaError_t run_steps(sgn_ctx* c, TA* q, double dt, int nsteps, cudaStream_t s, double* mon = nullptr) {
+    if constexpr (sgn::kStoreK1<TC, TA>) {
+        if (c->fuse && !mon) return run_steps_fused<TC, TA, BC>(c, q, dt, nsteps, s);
+    }
     TA* acc = static_cast<TA*>(c->acc);
     TC* Qa = static_cast<TC*>(c->Qa);
     TC* Qb = static_cast<TC*>(c->Qb);
@@ -306,6 +354,13 @@ struct AttrOp {
     template <typename TC, typename TA, int BC, int R>
     cudaError_t attrs() {
         constexpr bool kK1 = sgn::kStoreK1<TC, TA>;     // the stage modes run_steps launches
+        if constexpr (kK1) {
+            // the fused kernels of run_steps_fused
+            const size_t smem = sgn::FusedLayout<R>::template bytes<TC>();
+            cudaError_t ef = smem_optin<sgn::k_fused<TC, TA, BC, sgn::FUSED_S12, R>>(smem);
+            if (ef == cudaSuccess) ef = smem_optin<sgn::k_fused<TC, TA, BC, sgn::FUSED_S34, R>>(smem);
+            if (ef != cudaSuccess) return ef;
+        }
         cudaError_t e = stage_attr<TC, TA, TA, BC, kK1 ? sgn::MODE_S1K : sgn::MODE_S1, R>();
         if (e == cudaSuccess) e = stage_attr<TC, TC, TA, BC, kK1 ? sgn::MODE_S2K : sgn::MODE_S2, R>();
         if (e == cudaSuccess) e = stage_attr<TC, TC, TA, BC, sgn::MODE_S3, R>();
@@ -1073,6 +1128,7 @@ sgn_status sgn_create(const sgn_params* p, const void* b_dev, sgn_ctx** out) {
     c->nband = (long long)c->grid.x * ((p->ny + sgn::THREADS_Y - 1) / sgn::THREADS_Y);   // >= nblk
     c->rows = tile_y / sgn::THREADS_Y;
     c->gridr = c->grid;
+    c->fuse = p->prec == SGN_F32;
     if (p->prec == SGN_F64) {
         // The FP64 stage kernels are bound by each SM's FP64 pipe, so a launch
         // takes as long as its most loaded SM: ceil(b/S) blocks of b over S
@@ -1274,6 +1330,19 @@ sgn_status sgn_set_tile_rows(sgn_ctx* c, int rows) {
     }
     c->rows = rows;
     c->gridr = dim3(c->grid.x, (unsigned)gy);
+    return SGN_OK;
+}
+
+sgn_status sgn_set_stage_fusion(sgn_ctx* c, int on) {
+    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
+    if (on != 0 && on != 1) return fail(SGN_E_INVAL, "on must be 0 or 1");
+    if (c->p.prec != SGN_F32) return fail(SGN_E_UNSUPPORTED, "stage fusion serves SGN_F32 contexts");
+    if (on != c->fuse && c->step_exec) {
+        // the replayed graph holds the other kernels
+        cudaGraphExecDestroy(c->step_exec);
+        c->step_exec = nullptr;
+    }
+    c->fuse = on;
     return SGN_OK;
 }
 

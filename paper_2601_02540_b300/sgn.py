@@ -53,6 +53,7 @@ _SIGNATURES = {
     "sgn_step_vjp": (ctypes.c_int, [_V, _V, _V, _V, ctypes.c_double, _V]),
     "sgn_set_tile_rows": (ctypes.c_int, [_V, ctypes.c_int]),
     "sgn_tile_rows": (ctypes.c_int, [_V, _V]),
+    "sgn_set_stage_fusion": (ctypes.c_int, [_V, ctypes.c_int]),
     "sgn_step_record_tape": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_int, _V, _V, _V]),
     "sgn_step_vjp_tape": (ctypes.c_int, [_V, _V, _V, _V, _V, ctypes.c_double, _V]),
     "sgn_batch_create": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int, _V, _V]),
@@ -410,6 +411,10 @@ class Solver:
     def set_tile_rows(self, rows: int) -> None:
         """Override the FP64 stage tile height (32 x 8 rows, rows in 1..3)."""
         _ok(lib().sgn_set_tile_rows(self.ctx, int(rows)), "sgn_set_tile_rows")
+
+    def set_stage_fusion(self, on: bool) -> None:
+        """FP32: two RK4 stages per launch (default) or one."""
+        _ok(lib().sgn_set_stage_fusion(self.ctx, int(bool(on))), "sgn_set_stage_fusion")
 
     def tile_rows(self) -> int:
         r = ctypes.c_int()

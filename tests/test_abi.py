@@ -69,6 +69,7 @@ def test_null_context_is_rejected(lib):
     assert lib.sgn_step_vjp_tape(None, None, None, None, None, 0.1, None) == 1
     assert lib.sgn_set_tile_rows(None, 1) == 1
     assert lib.sgn_tile_rows(None, None) == 1
+    assert lib.sgn_set_stage_fusion(None, 1) == 1
     assert lib.sgn_destroy(None) == 0
 
 

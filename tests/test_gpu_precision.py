@@ -27,7 +27,7 @@ import torch
 
 import oracle as orc
 from oracle import PERIODIC, REFLECTING
-from paper_2601_02540_b300 import inputs
+from paper_2601_02540_b300 import inputs, sgn
 import gpu_util as gu
 import pins
 
@@ -163,3 +163,39 @@ def test_workload2_2000_steps_float_and_mixed_vs_oracle():
     for prec in errs:
         assert np.all(errs[prec] <= allow[prec]), (prec, errs[prec] / allow[prec])
     assert errs["f32_f64acc"][0] < errs["f32"][0], errs
+
+
+@pytest.mark.parametrize("bc", [PERIODIC, REFLECTING])
+@pytest.mark.parametrize("nx,ny,nsteps", [(3, 3, 3), (5, 4, 2), (33, 17, 7), (100, 37, 4),
+                                          (130, 70, 60), (1000, 515, 3)])
+def test_fp32_stage_fusion_equals_one_stage_per_launch(bc, nx, ny, nsteps):
+    """Two RK4 stages per launch (the first of each pair evaluated on the tile
+    grown by one node, its result kept in shared memory) give the states of
+    one launch per stage bit for bit: grids smaller than a tile, ragged tiles,
+    odd step counts (the result copied back from the scratch state) and a
+    50-step graph replay (130 x 70, 60 steps)."""
+    p = inputs.smooth_state(nx, ny, bc, seed=41, xmax=1.3, ymax=0.9)
+    s = gu.solver(p, "f32")
+    s.set_stage_fusion(False)
+    q1 = s.state(p.q0)
+    s.step(q1, p.dt, nsteps)
+    s.set_stage_fusion(True)
+    q2 = s.state(p.q0)
+    s.step(q2, p.dt, nsteps)
+    assert torch.equal(q1, q2)
+    q3 = s.state(p.q0)
+    for _ in range(nsteps):
+        s.step(q3, p.dt, 1)
+    assert torch.equal(q1, q3)
+    s.check()
+    s.close()
+
+
+def test_stage_fusion_is_for_fp32():
+    p = inputs.smooth_state(16, 9, PERIODIC, seed=2)
+    for prec in ("f64", "f32_f64acc", "df64"):
+        s = gu.solver(p, prec)
+        with pytest.raises(sgn.SgnError) as ei:
+            s.set_stage_fusion(True)
+        assert ei.value.status == 7          # SGN_E_UNSUPPORTED
+        s.close()
