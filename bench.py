@@ -52,12 +52,22 @@ FP64_NOMINAL_TFLOPS = 1.25     # B300 dense FP64 (nominal; no measured entry)
 #   stage 1: read q, b; write acc, Q             16 planes
 #   stages 2, 3: read Q, b, q, acc; write acc, Q  26 planes
 #   stage 4: read Q, b, acc; write q              16 planes   -> 84 planes per step
-# The FP32 mode runs stages 1 and 2 as S1K / S2K:
+# The FP32 mode advances two stages per launch (sgn_set_stage_fusion):
+#   stages 1-2: read q, b; write acc, Q3          16 planes
+#   stages 3-4: read Q3, b, q, acc; write q'      21 planes   -> 37 planes per step
+# and, one launch per stage, runs stages 1 and 2 as S1K / S2K:
 #   stage 1: read q, b; write k1                  11 planes
 #   stage 2: read q, k1, b; write acc, Q          21 planes   -> 74 planes per step
 # The mixed mode: q and acc double, Q and b float, the 84-plane scheme (536 B per step).
-BYTES_PER_CELL_STAGE = {"f64": 84 * 8 / 4, "f32": 74 * 4 / 4, "f32_f64acc": 536 / 4,
+BYTES_PER_CELL_STAGE = {"f64": 84 * 8 / 4, "f32": 37 * 4 / 4, "f32_unfused": 74 * 4 / 4,
+                        "f32_f64acc": 536 / 4,
                         "df64": 84 * 8 / 4}     # df64: stage states as float pairs, 8 bytes
+# (launches per step, stages per launch, kernel) of each timed path
+LAUNCH_SHAPE = {"f64": (4, 1, "k_stage (RK4 stage, 4 launches/step)"),
+                "f32": (2, 2, "k_fused (two RK4 stages per launch, 2 launches/step)"),
+                "f32_unfused": (4, 1, "k_stage (RK4 stage, 4 launches/step)"),
+                "f32_f64acc": (4, 1, "k_stage (RK4 stage, 4 launches/step)"),
+                "df64": (4, 1, "k_stage (RK4 stage, 4 launches/step)")}
 # Algorithmic floating-point operations per cell-stage of the implemented
 # formulation (an FMA counts 2; 1/h counts 1): pointwise operands (1/h, eta/h,
 # eta + 3/2 b, P2 = 2g h(h+b) - lam/3 eta^2/h) 10, products 7, coefficients 5,
@@ -69,7 +79,8 @@ FLOPS_PER_CELL_STAGE = 121.5
 # a B300 SM issues two thread-operations per clock.
 FP64_OPS_PER_CELL_STAGE = 83.75
 FP64_OPS_PER_SM_CLOCK = 2
-DTYPE_NAME = {"f64": "f64", "f32": "f32", "f32_f64acc": "f32+f64acc", "df64": "df64 (float pairs)"}
+DTYPE_NAME = {"f64": "f64", "f32": "f32", "f32_unfused": "f32 (one launch per stage)", "f32_f64acc": "f32+f64acc",
+              "df64": "df64 (float pairs)"}
 
 
 def _peaks() -> tuple[float, str]:
@@ -226,8 +237,9 @@ def measure_fp64_peak(torch, local: int, iters: int = 16384, reps: int = 3) -> d
                    f"8 x 256 threads per SM, best of {reps} launches (CUDA events)"}
 
 
-def _roofline(prec: str, cells: int, ms_total: float, launches_per_step: int, steps: int,
+def _roofline(prec: str, cells: int, ms_total: float, steps: int,
               hbm_peak: float, hbm_kind: str, fp64: dict | None = None) -> dict:
+    launches_per_step, stages_per_launch, kernel = LAUNCH_SHAPE[prec]
     launch_ms = ms_total / (launches_per_step * steps)
     traffic = _ncu_traffic(prec)
     if prec == "f64":
@@ -246,7 +258,7 @@ def _roofline(prec: str, cells: int, ms_total: float, launches_per_step: int, st
                               f"SM-clock (unit count: 2; nominal {FP64_NOMINAL_TFLOPS} TFLOP/s)"),
                 "algorithmic_ops_per_cell_stage": FP64_OPS_PER_CELL_STAGE,
                 "fp64_peak": fp64,
-                "kernel": "k_stage (RK4 stage, 4 launches/step)",
+                "kernel": kernel,
                 "launch_ms": launch_ms,
                 "flops": {"achieved": flops, "peak": fp64["tflops"], "unit": "TFLOP/s",
                           "frac": flops / fp64["tflops"], "flop_per_cell_stage": FLOPS_PER_CELL_STAGE},
@@ -254,10 +266,11 @@ def _roofline(prec: str, cells: int, ms_total: float, launches_per_step: int, st
                         "peak": hbm_peak, "unit": "GB/s",
                         "frac": BYTES_PER_CELL_STAGE[prec] * cells / (launch_ms * 1e-3) / 1e9 / hbm_peak,
                         "peak_kind": hbm_kind}}
-    achieved = BYTES_PER_CELL_STAGE[prec] * cells / (launch_ms * 1e-3) / 1e9
+    achieved = BYTES_PER_CELL_STAGE[prec] * stages_per_launch * cells / (launch_ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": hbm_kind,
-            "kernel": "k_stage (RK4 stage, 4 launches/step)", "launch_ms": launch_ms}
+            "kernel": kernel, "launch_ms": launch_ms,
+            "algorithmic_bytes_per_cell_stage": BYTES_PER_CELL_STAGE[prec]}
 
 
 def _cpu_baseline(p_full: inputs.Problem) -> dict:
@@ -321,7 +334,18 @@ def run_ours(args) -> None:
             ms, launches = _time_steps(torch, s, q, p.dt, args.steps, args.warmup, dist)
         results[prec] = {"value": replica_rate(cells, args.steps, ms, world), "ms_per_step": ms / args.steps,
                          "gpu_launches": launches,
-                         "roofline": _roofline(prec, cells, ms, 4, args.steps, hbm_peak, hbm_kind, fp64)}
+                         "roofline": _roofline(prec, cells, ms, args.steps, hbm_peak, hbm_kind, fp64)}
+        if prec == "f32":
+            # the same FP32 steps with one launch per stage, for comparison
+            s.set_stage_fusion(False)
+            qu = q_init.clone()
+            msu, lu = _time_steps(torch, s, qu, p.dt, args.steps, args.warmup, dist)
+            s.set_stage_fusion(True)
+            results["f32_unfused"] = {"value": replica_rate(cells, args.steps, msu, world),
+                                      "ms_per_step": msu / args.steps, "gpu_launches": lu,
+                                      "roofline": _roofline("f32_unfused", cells, msu, args.steps, hbm_peak,
+                                                            hbm_kind, fp64)}
+            del qu
         if not args.no_drift:
             # the full job, outside the timed region: energy drift and final state
             q.copy_(q_init)
@@ -403,10 +427,10 @@ def run_ours(args) -> None:
 def _ensemble(torch, steps: int, warmup: int, loop_steps: int = 50) -> dict:
     """Ragged ensemble (256 instances, N in {128,...,512}, half periodic, half
     reflecting, FP32 state, each with its own dt): the batched path (one
-    launch per stage over all instances, graph replays, autotuned tiling: tile
-    height and per-tile or persistent kernel) over `steps` steps (the job's
-    1000 by default), against a per-instance launch loop over `loop_steps`,
-    both timed with CUDA events."""
+    launch per stage, or per two stages, over all instances, graph replays,
+    autotuned tiling: tile height, per-tile or persistent kernel, two stages
+    per launch) over `steps` steps (the job's 1000 by default), against a
+    per-instance launch loop over `loop_steps`, both timed with CUDA events."""
     from paper_2601_02540_b300 import sgn
     probs = inputs.workload5()
     cells = sum(p.nx * p.ny for p in probs)
@@ -417,10 +441,12 @@ def _ensemble(torch, steps: int, warmup: int, loop_steps: int = 50) -> dict:
     # on a copy of the state, then the autotuner's own choice
     per_tiling = {}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for r, pers in ((1, False), (2, False), (4, False), (1, True), (2, True)):
+    for r, pers, fuse in ((1, False, False), (2, False, False), (4, False, False), (1, True, False),
+                          (2, True, False), (2, False, True)):
         bs.set_persistent(False)
         bs.set_rows(r)
         bs.set_persistent(pers)
+        bs.set_stage_fusion(fuse)
         w = q.clone()
         bs.step(w, 25)
         torch.cuda.synchronize()
@@ -428,7 +454,8 @@ def _ensemble(torch, steps: int, warmup: int, loop_steps: int = 50) -> dict:
         bs.step(w, 25)
         e1.record()
         torch.cuda.synchronize()
-        per_tiling[f"rows{r}_{'persistent' if pers else 'per_tile'}"] = 4.0 * cells * 25 / (e0.elapsed_time(e1) * 1e-3)
+        name = "rows2_two_stages_per_launch" if fuse else f"rows{r}_{'persistent' if pers else 'per_tile'}"
+        per_tiling[name] = 4.0 * cells * 25 / (e0.elapsed_time(e1) * 1e-3)
         del w
     bs.set_persistent(False)
     rows = bs.autotune(q)
@@ -458,13 +485,16 @@ def _ensemble(torch, steps: int, warmup: int, loop_steps: int = 50) -> dict:
         s.close()
     rate_b = 4.0 * cells * steps / (ms_batch * 1e-3)
     rate_l = 4.0 * cells * loop_steps / (ms_loop * 1e-3)
-    hbm = BYTES_PER_CELL_STAGE["f32"] * rate_b / 1e9
+    fused = bool(tiling.get("fused")) and not tiling.get("persistent")
+    bpcs = BYTES_PER_CELL_STAGE["f32" if fused else "f32_unfused"]
+    hbm = bpcs * rate_b / 1e9
     peak, kind = _peaks()
     return {"workload": "256 instances N~U{128,192,256,384,512}, half periodic/half reflecting, FP32",
             "cells": cells, "steps": steps, "value": rate_b, "unit": UNIT, "wall_ms": ms_batch,
             "per_instance_loop": rate_l, "loop_steps": loop_steps, "speedup_vs_loop": rate_b / rate_l,
             "rows": rows, "tiling": tiling, "per_tiling_rate": per_tiling,
             "hbm_gbs": hbm, "hbm_frac": hbm / peak, "hbm_peak_kind": kind,
+            "algorithmic_bytes_per_cell_stage": bpcs,
             "mass_finite": bool(np.all(np.isfinite(d)))}
 
 

@@ -405,13 +405,23 @@ SGN_API sgn_status sgn_batch_set_rows(sgn_batch* batch, int rows);
  * serves the float compute types (SGN_F32, SGN_F32_F64ACC) and tile heights
  * 8 and 16 (rows 1, 2); otherwise on = 1 returns SGN_E_UNSUPPORTED. */
 SGN_API sgn_status sgn_batch_set_persistent(sgn_batch* batch, int on);
+/* SGN_F32 ensembles: on = 1 (default) advances sgn_batch_step two RK4 stages
+ * per launch over 32 x 16 tiles (as sgn_set_stage_fusion for one grid; the
+ * same states bit for bit, q_{n+1} alternately in q_dev and batch scratch,
+ * an odd step count ends with one copy), on = 0 one launch per stage with the
+ * tiling of sgn_batch_set_rows / sgn_batch_set_persistent; the persistent
+ * kernel, when selected, takes precedence.  Other precisions: on = 1 is
+ * SGN_E_UNSUPPORTED. */
+SGN_API sgn_status sgn_batch_set_stage_fusion(sgn_batch* batch, int on);
+SGN_API sgn_status sgn_batch_stage_fusion(const sgn_batch* batch, int* on);
 /* The current tiling: *rows (1, 2, 4) and *persistent (0, 1). */
 SGN_API sgn_status sgn_batch_tiling(const sgn_batch* batch, int* rows, int* persistent);
-/* Time 8 steps of each tiling -- rows 1, 2, 4 with one block per tile and,
- * for the float compute types, rows 1, 2 with the persistent kernel -- on a
- * copy of q_dev (allocated and freed here), in three rounds; keep the tiling
- * with the fastest round and return its rows in *rows_out (or NULL; see
- * sgn_batch_tiling for the kernel).  Synchronizes. */
+/* Time 8 steps of each tiling -- rows 1, 2, 4 with one block per tile, for
+ * the float compute types rows 1, 2 with the persistent kernel, and for
+ * SGN_F32 two stages per launch -- on a copy of q_dev (allocated and freed
+ * here), in three rounds; keep the tiling with the fastest round and return
+ * its rows in *rows_out (or NULL; see sgn_batch_tiling and
+ * sgn_batch_stage_fusion for the kernel).  Synchronizes. */
 SGN_API sgn_status sgn_batch_autotune(sgn_batch* batch, const void* q_dev, int* rows_out, void* stream);
 
 /* Synchronize `stream` and report (and clear) the latched device flag. */

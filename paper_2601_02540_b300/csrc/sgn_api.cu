@@ -1252,7 +1252,7 @@ sgn_status sgn_step(sgn_ctx* c, void* q_dev, double dt, int nsteps, void* stream
             if (st != SGN_OK) return st;
             while (left >= kGraphSteps) {
                 CUDA_TRY(cudaGraphLaunch(c->step_exec, s), "graph launch");
-                g_launches.fetch_add(4ull * kGraphSteps, std::memory_order_relaxed);
+                g_launches.fetch_add((c->fuse ? 2ull : 4ull) * kGraphSteps, std::memory_order_relaxed);
                 left -= kGraphSteps;
             }
         }

@@ -48,6 +48,7 @@ struct sgn_batch {
     // (rows, stage), resident blocks per SM x SMs
     int pgrid[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
     int persist = 0;                   // 1: RK4 stages by the persistent kernel
+    int fuse = 0;                      // 1 (FP32): two RK4 stages per launch (k_batch_fused)
     double* b64 = nullptr;
     void* bT = nullptr;
     void* acc = nullptr;
@@ -61,6 +62,7 @@ struct sgn_batch {
     const void* exec_q = nullptr;
     int exec_rows = 0;
     int exec_persist = 0;
+    int exec_fuse = 0;
     bool capturing = false;            // launches recorded into a graph are counted on replay
 };
 
@@ -145,6 +147,15 @@ cudaError_t set_attrs_rows() {
 
 template <typename TC, typename TA>
 cudaError_t set_attrs() {
+    if constexpr (sgn::kStoreK1<TC, TA>) {
+        const size_t smem = sgn::FusedLayout<2>::template bytes<TC>();
+        cudaError_t ef = cudaFuncSetAttribute(sgn::k_batch_fused<TC, TA, sgn::FUSED_S12>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (ef == cudaSuccess)
+            ef = cudaFuncSetAttribute(sgn::k_batch_fused<TC, TA, sgn::FUSED_S34>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (ef != cudaSuccess) return ef;
+    }
     cudaError_t e = set_attrs_rows<TC, TA, 1>();
     if (e == cudaSuccess) e = set_attrs_rows<TC, TA, 2>();
     if (e == cudaSuccess) e = set_attrs_rows<TC, TA, 4>();
@@ -152,8 +163,49 @@ cudaError_t set_attrs() {
 }
 
 // nsteps RK4 steps, four launches each (ping-pong stage states as sgn_step)
+// nsteps FP32 steps, two stages per launch over the 32 x 16 tiles: q_{n+1}
+// goes to the other of q and Qb (the second launch reads q_n on its halo),
+// and an odd step count ends with a copy back into q.
+template <typename TC, typename TA>
+cudaError_t bsteps_fused(sgn_batch* B, TA* q, int nsteps, cudaStream_t s) {
+    static_assert(std::is_same<TC, TA>::value, "Qb holds a state");
+    const size_t smem = sgn::FusedLayout<2>::template bytes<TC>();
+    sgn::BatchFusedArgs<TC, TA> f;
+    std::memset(&f, 0, sizeof(f));
+    f.desc = B->desc;
+    f.tiles = B->tiles[1];
+    f.b = static_cast<const TC*>(B->bT);
+    f.acc = static_cast<TA*>(B->acc);
+    f.flag = B->flag;
+    TA* cur = q;
+    TA* nxt = static_cast<TA*>(B->Qb);
+    const dim3 grid((unsigned)B->ntiles[1]), block(sgn::TILE_X, sgn::THREADS_Y);
+    cudaError_t e = cudaSuccess;
+    for (int n = 0; n < nsteps; n++) {
+        sgn::BatchFusedArgs<TC, TA> f12 = f;
+        f12.q = cur;
+        f12.Qout = static_cast<TC*>(B->Qa);
+        sgn::k_batch_fused<TC, TA, sgn::FUSED_S12><<<grid, block, smem, s>>>(f12);
+        if (!B->capturing) sgn_count_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        sgn::BatchFusedArgs<TC, TA> f34 = f;
+        f34.q = cur;
+        f34.X = static_cast<const TC*>(B->Qa);
+        f34.out = nxt;
+        sgn::k_batch_fused<TC, TA, sgn::FUSED_S34><<<grid, block, smem, s>>>(f34);
+        if (!B->capturing) sgn_count_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        std::swap(cur, nxt);
+    }
+    if (cur != q) e = cudaMemcpyAsync(q, cur, (size_t)5 * B->cells * sizeof(TA), cudaMemcpyDeviceToDevice, s);
+    return e;
+}
+
 template <typename TC, typename TA, int ROWS>
 cudaError_t bsteps(sgn_batch* B, TA* q, int nsteps, cudaStream_t s) {
+    if constexpr (sgn::kStoreK1<TC, TA>) {
+        if (B->fuse && !B->persist) return bsteps_fused<TC, TA>(B, q, nsteps, s);
+    }
     sgn::BatchArgs<TC, TA, TA> a1;
     std::memset(&a1, 0, sizeof(a1));
     a1.desc = B->desc;
@@ -281,7 +333,9 @@ bool devptr(const void* p) {
 
 // (re)build the graph of kGraphSteps RK4 steps for this state pointer and tiling
 sgn_status ensure_graph(sgn_batch* B, void* q) {
-    if (B->exec && B->exec_q == q && B->exec_rows == B->rows && B->exec_persist == B->persist) return SGN_OK;
+    if (B->exec && B->exec_q == q && B->exec_rows == B->rows && B->exec_persist == B->persist &&
+        B->exec_fuse == B->fuse)
+        return SGN_OK;
     if (B->exec) {
         cudaGraphExecDestroy(B->exec);
         B->exec = nullptr;
@@ -306,6 +360,7 @@ sgn_status ensure_graph(sgn_batch* B, void* q) {
     B->exec_q = q;
     B->exec_rows = B->rows;
     B->exec_persist = B->persist;
+    B->exec_fuse = B->fuse;
     return SGN_OK;
 }
 
@@ -323,6 +378,7 @@ sgn_status sgn_batch_create(const sgn_instance* inst, int ninst, int prec, const
     if (!B) return bfail(SGN_E_NOMEM, "host allocation");
     B->ninst = ninst;
     B->prec = prec;
+    B->fuse = prec == SGN_F32;
     B->tc = prec == SGN_F64 ? 8 : 4;
     B->ta = prec == SGN_F32 ? 4 : 8;
     B->hdesc.resize(ninst);
@@ -477,6 +533,20 @@ sgn_status sgn_batch_set_persistent(sgn_batch* B, int on) {
     return SGN_OK;
 }
 
+sgn_status sgn_batch_set_stage_fusion(sgn_batch* B, int on) {
+    if (!B) return bfail(SGN_E_INVAL, "batch is NULL");
+    if (on != 0 && on != 1) return bfail(SGN_E_INVAL, "on must be 0 or 1");
+    if (on && B->prec != SGN_F32) return bfail(SGN_E_UNSUPPORTED, "stage fusion serves SGN_F32 ensembles");
+    B->fuse = on;
+    return SGN_OK;
+}
+
+sgn_status sgn_batch_stage_fusion(const sgn_batch* B, int* on) {
+    if (!B || !on) return bfail(SGN_E_INVAL, "batch and on must not be NULL");
+    *on = B->fuse;
+    return SGN_OK;
+}
+
 sgn_status sgn_batch_tiling(const sgn_batch* B, int* rows, int* persistent) {
     if (!B || !rows || !persistent) return bfail(SGN_E_INVAL, "batch, rows and persistent must not be NULL");
     *rows = B->rows;
@@ -497,7 +567,7 @@ sgn_status sgn_batch_step(sgn_batch* B, void* q_dev, int nsteps, void* stream) {
         while (left >= kGraphSteps) {
             cudaError_t e = cudaGraphLaunch(B->exec, s);
             if (e != cudaSuccess) return bcuda(e, "graph launch");
-            sgn_count_launches(4ull * kGraphSteps);
+            sgn_count_launches((B->fuse && !B->persist && B->prec == SGN_F32 ? 2ull : 4ull) * kGraphSteps);
             left -= kGraphSteps;
         }
     }
@@ -553,15 +623,18 @@ sgn_status sgn_batch_autotune(sgn_batch* B, const void* q_dev, int* rows_out, vo
     // three rounds over the candidate tilings, each timing 8 steps after 2
     // warm-up steps; a candidate's time is its fastest round (robust to a slow
     // round, e.g. while the clocks ramp up)
-    const int cand_rows[5] = {1, 2, 4, 1, 2};
-    const int cand_persist[5] = {0, 0, 0, 1, 1};
-    const int ncand = B->prec == SGN_F64 ? 3 : 5;
-    float tmin[5] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
-    const int keep_persist = B->persist;
+    // (FP32 also two stages per launch over 32 x 16 tiles)
+    const int cand_rows[6] = {1, 2, 4, 1, 2, 2};
+    const int cand_persist[6] = {0, 0, 0, 1, 1, 0};
+    const int cand_fuse[6] = {0, 0, 0, 0, 0, 1};
+    const int ncand = B->prec == SGN_F64 ? 3 : (B->prec == SGN_F32 ? 6 : 5);
+    float tmin[6] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
+    const int keep_persist = B->persist, keep_fuse = B->fuse;
     cudaError_t e = cudaSuccess;
     for (int round = 0; round < 3 && e == cudaSuccess; round++) {
         for (int k = 0; k < ncand && e == cudaSuccess; k++) {
             B->persist = cand_persist[k];
+            B->fuse = cand_fuse[k];
             e = cudaMemcpyAsync(work, q_dev, bytes, cudaMemcpyDeviceToDevice, s);
             if (e == cudaSuccess) e = bsteps_any(B, work, 2, cand_rows[k], s);   // warm-up
             if (e == cudaSuccess) e = cudaEventRecord(e0, s);
@@ -574,6 +647,7 @@ sgn_status sgn_batch_autotune(sgn_batch* B, const void* q_dev, int* rows_out, vo
         }
     }
     B->persist = keep_persist;
+    B->fuse = keep_fuse;
     float best = 1e30f;
     int best_k = -1;
     for (int k = 0; k < ncand; k++)
@@ -588,6 +662,7 @@ sgn_status sgn_batch_autotune(sgn_batch* B, const void* q_dev, int* rows_out, vo
     if (best_k >= 0) {
         B->rows = cand_rows[best_k];
         B->persist = cand_persist[best_k];
+        B->fuse = cand_fuse[best_k];
     }
     if (rows_out) *rows_out = B->rows;
     return SGN_OK;

@@ -13,6 +13,7 @@
 #pragma once
 
 #include "sgn_kernels.cuh"
+#include "sgn_fused.cuh"
 
 namespace sgn {
 
@@ -114,6 +115,56 @@ k_batch_stage(BatchArgs<TC, TIN, TA> a) {
         stage_tile<TC, TIN, TA, BC_REFLECTING, MODE, ROWS, kBatchFact<TC>>(s, G, T.i0, T.j0, sm, slot, nbx * NDIAG);
     else
         stage_tile<TC, TIN, TA, BC_PERIODIC, MODE, ROWS, kBatchFact<TC>>(s, G, T.i0, T.j0, sm, slot, nbx * NDIAG);
+}
+
+// Two RK4 stages per launch over the ensemble (FP32; see sgn_fused.cuh):
+// block k takes the 32 x 16 tile of record k and runs fused_tile with the
+// instance's planes, grid and coefficients, so every instance advances as
+// its single-grid fused (and unfused) steps do, bit for bit.
+template <typename TC, typename TA>
+struct BatchFusedArgs {
+    const InstDesc* desc;
+    const PTile* tiles;    // the 32 x 16 tiles (rows 2)
+    const TA* q;           // packed q_n
+    const TC* X;           // S34: packed Q3
+    const TC* b;           // packed bathymetry (compute type)
+    TA* acc;
+    TC* Qout;              // S12: packed Q3
+    TA* out;               // S34: packed q_{n+1}
+    int* flag;
+};
+
+template <typename TC, typename TA, int PAIR>
+__global__ void __launch_bounds__(BLOCK_THREADS, 4) k_batch_fused(BatchFusedArgs<TC, TA> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const PTile T = a.tiles[blockIdx.x];
+    const InstDesc& d = a.desc[T.inst];
+    Geom G = d.G;
+    G.nx = T.nx;
+    G.ny = T.ny;
+    G.plane = (long long)T.nx * T.ny;
+    FusedArgs<TC, TA> f;
+    const long long so = 5 * T.off;
+    f.q = a.q + so;
+    f.X = a.X ? a.X + so : nullptr;
+    f.b = a.b + T.off;
+    f.acc = a.acc + so;
+    f.Qout = a.Qout ? a.Qout + so : nullptr;
+    f.out = a.out ? a.out + so : nullptr;
+    f.flag = a.flag;
+    // the coefficients as the single-grid path rounds them: (TA)(dt/6) etc.
+    f.c_a1 = (TA)d.c_acc[0];
+    f.c_a2 = (TA)d.c_acc[1];
+    f.c_a3 = (TA)d.c_acc[2];
+    f.c_a4 = (TA)d.c_acc[3];
+    f.c_q1 = (TA)d.c_q[0];
+    f.c_q2 = (TA)d.c_q[1];
+    f.c_q3 = (TA)d.c_q[2];
+    TC* sm = reinterpret_cast<TC*>(smem_raw);
+    if (T.bc == BC_REFLECTING)
+        fused_tile<TC, TA, BC_REFLECTING, PAIR, 2>(f, G, T.i0, T.j0, sm);
+    else
+        fused_tile<TC, TA, BC_PERIODIC, PAIR, 2>(f, G, T.i0, T.j0, sm);
 }
 
 // Per-instance sums of the band partials, in band order (one block each; the

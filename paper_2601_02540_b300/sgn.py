@@ -66,6 +66,8 @@ _SIGNATURES = {
     "sgn_batch_autotune": (ctypes.c_int, [_V, _V, _V, _V]),
     "sgn_batch_set_persistent": (ctypes.c_int, [_V, ctypes.c_int]),
     "sgn_batch_tiling": (ctypes.c_int, [_V, _V, _V]),
+    "sgn_batch_set_stage_fusion": (ctypes.c_int, [_V, ctypes.c_int]),
+    "sgn_batch_stage_fusion": (ctypes.c_int, [_V, _V]),
     "sgn_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "sgn_last_error": (ctypes.c_char_p, []),
     "sgn_launch_count": (ctypes.c_ulonglong, []),
@@ -494,10 +496,14 @@ class BatchSolver:
     def set_persistent(self, on: bool):
         _ok(lib().sgn_batch_set_persistent(self.handle, int(bool(on))), "sgn_batch_set_persistent")
 
+    def set_stage_fusion(self, on: bool):
+        _ok(lib().sgn_batch_set_stage_fusion(self.handle, int(bool(on))), "sgn_batch_set_stage_fusion")
+
     def tiling(self) -> dict:
-        rows, pers = ctypes.c_int(), ctypes.c_int()
+        rows, pers, fuse = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _ok(lib().sgn_batch_tiling(self.handle, ctypes.byref(rows), ctypes.byref(pers)), "sgn_batch_tiling")
-        return {"rows": rows.value, "persistent": bool(pers.value)}
+        _ok(lib().sgn_batch_stage_fusion(self.handle, ctypes.byref(fuse)), "sgn_batch_stage_fusion")
+        return {"rows": rows.value, "persistent": bool(pers.value), "fused": bool(fuse.value)}
 
     def autotune(self, q) -> int:
         r = ctypes.c_int()

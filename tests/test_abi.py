@@ -70,6 +70,8 @@ def test_null_context_is_rejected(lib):
     assert lib.sgn_set_tile_rows(None, 1) == 1
     assert lib.sgn_tile_rows(None, None) == 1
     assert lib.sgn_set_stage_fusion(None, 1) == 1
+    assert lib.sgn_batch_set_stage_fusion(None, 1) == 1
+    assert lib.sgn_batch_stage_fusion(None, None) == 1
     assert lib.sgn_destroy(None) == 0
 
 

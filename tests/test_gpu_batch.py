@@ -129,6 +129,54 @@ def test_batch_workload_recipe_small():
     bs.close()
 
 
+# ------------------------------------------------------------------ two stages per launch
+@pytest.mark.parametrize("nsteps", [1, 30])
+def test_fused_ensemble_equals_one_stage_per_launch_and_single_grids(nsteps):
+    """FP32 ensembles advance two RK4 stages per launch by default: the
+    states equal one launch per stage and each instance's single-grid fused
+    steps bit for bit (ragged grids down to 3x3, both boundary kinds; 30
+    steps: a 25-step graph replay and 5 direct steps, both odd, so the
+    result is copied back from the scratch state twice)."""
+    probs = _ensemble()
+    bs = sgn.BatchSolver(probs, prec="f32")
+    assert bs.tiling()["fused"]
+    q1 = bs.pack([p.q0 for p in probs])
+    bs.step(q1, nsteps)
+    bs.set_stage_fusion(False)
+    assert not bs.tiling()["fused"]
+    q2 = bs.pack([p.q0 for p in probs])
+    bs.step(q2, nsteps)
+    assert torch.equal(q1, q2)
+    for p, g in zip(probs, bs.unpack(q1)):
+        s = sgn.Solver.from_problem(p, prec="f32")
+        qs = s.state(p.q0)
+        s.step(qs, p.dt, nsteps)
+        assert torch.equal(qs, g), p.name
+        s.close()
+    bs.close()
+
+
+def test_fused_ensemble_unsupported_precisions_and_autotune():
+    probs = _ensemble()
+    for prec in ("f64", "f32_f64acc"):
+        bs = sgn.BatchSolver(probs, prec=prec)
+        assert not bs.tiling()["fused"]
+        with pytest.raises(sgn.SgnError) as ei:
+            bs.set_stage_fusion(True)
+        assert ei.value.status == 7          # SGN_E_UNSUPPORTED
+        bs.close()
+    bs = sgn.BatchSolver(probs, prec="f32")
+    q = bs.pack([p.q0 for p in probs])
+    bs.autotune(q)
+    q1 = q.clone()
+    bs.step(q1, 7)
+    bs.set_stage_fusion(not bs.tiling()["fused"])
+    q2 = q.clone()
+    bs.step(q2, 7)
+    assert torch.equal(q1, q2)
+    bs.close()
+
+
 # ------------------------------------------------------------------ the persistent kernel
 @pytest.mark.parametrize("prec", ["f32", "f32_f64acc"])
 @pytest.mark.parametrize("rows", [1, 2])
@@ -143,7 +191,8 @@ def test_persistent_kernel_equals_per_tile_kernel_bitwise(prec, rows):
     q1 = bs.pack([p.q0 for p in probs])
     bs.step(q1, 30)
     bs.set_persistent(True)
-    assert bs.tiling() == {"rows": rows, "persistent": True}
+    t = bs.tiling()
+    assert t["rows"] == rows and t["persistent"]
     q2 = bs.pack([p.q0 for p in probs])
     bs.step(q2, 30)
     assert torch.equal(q1, q2)
