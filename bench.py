@@ -91,13 +91,20 @@ def _peaks() -> tuple[float, str]:
         return FALLBACK_HBM_GBS, "fallback"
 
 
+KERNEL_SOURCES = ("sgn_kernels.cuh", "sgn_fused.cuh")
+
+
 def _kernel_hash(text: str | None = None) -> str:
-    """Hash of the source that defines the stage kernels and their tile shape,
-    with // comments, trailing blanks and empty lines removed (so that edits of
-    comments do not invalidate a capture)."""
+    """Hash of the sources that define the stage kernels (one and two stages
+    per launch) and their tile shapes, with // comments, trailing blanks and
+    empty lines removed (so that edits of comments do not invalidate a
+    capture)."""
     if text is None:
-        with open(os.path.join(ROOT, "paper_2601_02540_b300", "csrc", "sgn_kernels.cuh")) as fh:
-            text = fh.read()
+        parts = []
+        for name in KERNEL_SOURCES:
+            with open(os.path.join(ROOT, "paper_2601_02540_b300", "csrc", name)) as fh:
+                parts.append(fh.read())
+        text = "\n".join(parts)
     lines = []
     for line in text.splitlines():
         code = line.split("//", 1)[0].rstrip()
