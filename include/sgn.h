@@ -197,7 +197,7 @@ SGN_API sgn_status sgn_mass_energy_noalloc(const sgn_params* p, const void* b_de
  * contexts only (else SGN_E_UNSUPPORTED).  Three launches: the tape of the
  * RHS at q (its intermediate values, SGN_TAPE_PLANES planes, written by the
  * FP64 stage kernel), then the two adjoint passes, which read it.  The first
- * adjoint call of a context allocates 62 planes of scratch (SGN_E_NOMEM if
+ * adjoint call of a context allocates 88 planes of scratch (SGN_E_NOMEM if
  * that fails).  Asynchronous. */
 SGN_API sgn_status sgn_rhs_vjp(sgn_ctx* ctx, const void* q_dev, const void* abar_dev, void* qbar_dev,
                                void* bbar_dev, void* stream);
@@ -221,7 +221,7 @@ SGN_API sgn_status sgn_step_record(sgn_ctx* ctx, void* q_dev, double dt, int nst
  * Internally the stage cotangents are carried with the scales
  * dt/6, dt^2/6, dt^3/12, dt^4/24 factored out; a dt for which dt^4/24 is not a
  * normal double returns SGN_E_INVAL.  The first adjoint call of a context
- * allocates 62 planes of scratch (SGN_E_NOMEM if that fails).  SGN_F64 only.
+ * allocates 88 planes of scratch (SGN_E_NOMEM if that fails).  SGN_F64 only.
  * Asynchronous. */
 SGN_API sgn_status sgn_step_vjp(sgn_ctx* ctx, const void* stash_dev, void* qbar_dev, void* bbar_dev,
                                 double dt, void* stream);
@@ -243,7 +243,8 @@ SGN_API sgn_status sgn_step_record_tape(sgn_ctx* ctx, void* q_dev, double dt, in
                                         void* tape_dev, void* stream);
 
 /* sgn_step_vjp with the step's tapes from sgn_step_record_tape (one tape slot,
- * 4 * SGN_TAPE_PLANES planes): eight launches (two per stage) and the same
+ * 4 * SGN_TAPE_PLANES planes): five launches (the second pass of stages 4, 3
+ * and 2 each fused with the first pass of the stage before it) and the same
  * results as sgn_step_vjp bit for bit.  NULL tape_dev is SGN_E_INVAL. */
 SGN_API sgn_status sgn_step_vjp_tape(sgn_ctx* ctx, const void* stash_dev, const void* tape_dev,
                                      void* qbar_dev, void* bbar_dev, double dt, void* stream);

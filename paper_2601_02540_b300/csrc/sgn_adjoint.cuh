@@ -85,16 +85,11 @@ __device__ __forceinline__ double flip_sign(double x, unsigned long long m) {
 // names follow node_rhs_src: Xu, Yu, ... are its bracket sums, A_x, A_y its
 // continuity fluxes, base2 = -P2/h, lom2 = 2 lam/3 (1 - rho), and a trailing
 // "b" marks a cotangent.
-#ifndef SGN_ADJ_POINT_MINB
-#define SGN_ADJ_POINT_MINB 3
-#endif
 template <int BC>
-__global__ void __launch_bounds__(ADJ_BLOCK, SGN_ADJ_POINT_MINB) k_adj_point(AdjArgs a) {
+__device__ __forceinline__ void adj_point_node(const AdjArgs& a, long long c, int i, int j, double ah, double au,
+                                               double av, double aw, double ae) {
     const Geom& G = a.G;
     const long long P = G.plane;
-    const long long c = (long long)blockIdx.x * ADJ_BLOCK + threadIdx.x;
-    if (c >= P) return;
-    const int j = (int)(c / G.nx), i = (int)(c - (long long)j * G.nx);
     const double* __restrict__ T = a.tape + c;
     const double r = T[TP_R * P], base2 = T[TP_BASE2 * P];
     const double dxh = T[TP_DXH * P], dyh = T[TP_DYH * P], dxu = T[TP_DXU * P], dyu = T[TP_DYU * P];
@@ -103,7 +98,6 @@ __global__ void __launch_bounds__(ADJ_BLOCK, SGN_ADJ_POINT_MINB) k_adj_point(Adj
     const double xhu = T[TP_XHU * P], yhv = T[TP_YHV * P], Ax = T[TP_AX * P], Ay = T[TP_AY * P];
     const double ku = T[TP_KU * P], kv = T[TP_KV * P], kw = T[TP_KW * P];
     const double h = a.X[c], u = a.X[P + c], v = a.X[2 * P + c], w = a.X[3 * P + c], eta = a.X[4 * P + c];
-    const double ah = a.A[c], au = a.A[P + c], av = a.A[2 * P + c], aw = a.A[3 * P + c], ae = a.A[4 * P + c];
 
     // the operator's row factors at this node (one-sided rows on a reflecting wall)
     const bool wx = BC == BC_REFLECTING && (i == 0 || i == G.nx - 1);
@@ -199,16 +193,27 @@ __global__ void __launch_bounds__(ADJ_BLOCK, SGN_ADJ_POINT_MINB) k_adj_point(Adj
     C[AC_P2 * P] = -r * Bb;
 }
 
-// Pass 2: the transposed differences (gathers of the neighbours' weights),
-// the chain rule from the operands to the state and bathymetry, and the
-// stage algebra, at one node.
-template <int BC, int MODE>
-__global__ void __launch_bounds__(ADJ_BLOCK) k_adj_gather(AdjArgs a) {
-    const Geom& G = a.G;
-    const long long P = G.plane;
+#ifndef SGN_ADJ_POINT_MINB
+#define SGN_ADJ_POINT_MINB 3
+#endif
+template <int BC>
+__global__ void __launch_bounds__(ADJ_BLOCK, SGN_ADJ_POINT_MINB) k_adj_point(AdjArgs a) {
+    const long long P = a.G.plane;
     const long long c = (long long)blockIdx.x * ADJ_BLOCK + threadIdx.x;
     if (c >= P) return;
-    const int j = (int)(c / G.nx), i = (int)(c - (long long)j * G.nx);
+    const int j = (int)(c / a.G.nx), i = (int)(c - (long long)j * a.G.nx);
+    adj_point_node<BC>(a, c, i, j, a.A[c], a.A[P + c], a.A[2 * P + c], a.A[3 * P + c], a.A[4 * P + c]);
+}
+
+// Pass 2: the transposed differences (gathers of the neighbours' weights),
+// the chain rule from the operands to the state and bathymetry, and the
+// stage algebra, at one node.  CHAIN (stage mode): the next stage's
+// cotangent direction kappa qprime + J^T A is returned in an[] instead of
+// being stored.
+template <int BC, int MODE, bool CHAIN>
+__device__ __forceinline__ void adj_gather_node(const AdjArgs& a, long long c, int i, int j, double an[5]) {
+    const Geom& G = a.G;
+    const long long P = G.plane;
     const double* __restrict__ S = a.scratch;
 
     // neighbours: left/right/below/above (periodic wrap; clamped at walls)
@@ -299,9 +304,34 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adj_gather(AdjArgs a) {
             const double qp = a.qprime[f * P + c];
             const double base = a.first ? qp : a.qacc_in[f * P + c];
             a.qacc_out[f * P + c] = fma(sg, qb[f], base);
-            if (a.Anext) a.Anext[f * P + c] = fma(a.kappa, qp, qb[f]);
+            if constexpr (CHAIN) an[f] = fma(a.kappa, qp, qb[f]);
+            else if (a.Anext) a.Anext[f * P + c] = fma(a.kappa, qp, qb[f]);
         }
     }
+}
+
+template <int BC, int MODE>
+__global__ void __launch_bounds__(ADJ_BLOCK) k_adj_gather(AdjArgs a) {
+    const long long c = (long long)blockIdx.x * ADJ_BLOCK + threadIdx.x;
+    if (c >= a.G.plane) return;
+    const int j = (int)(c / a.G.nx), i = (int)(c - (long long)j * a.G.nx);
+    double an[5];
+    adj_gather_node<BC, MODE, false>(a, c, i, j, an);
+}
+
+// Pass 2 of a stage followed, at the same node, by pass 1 of the stage before
+// it (a step's walk, stages 4-2): the point pass takes the cotangent direction
+// the gather pass forms, without storing it.  `n` addresses the earlier
+// stage's state, tape and a second weight buffer (the gather pass still reads
+// the neighbours' weights of this stage from `a`).
+template <int BC>
+__global__ void __launch_bounds__(ADJ_BLOCK, SGN_ADJ_POINT_MINB) k_adj_gather_point(AdjArgs a, AdjArgs n) {
+    const long long c = (long long)blockIdx.x * ADJ_BLOCK + threadIdx.x;
+    if (c >= a.G.plane) return;
+    const int j = (int)(c / a.G.nx), i = (int)(c - (long long)j * a.G.nx);
+    double an[5];
+    adj_gather_node<BC, ADJ_MODE_STAGE, true>(a, c, i, j, an);
+    adj_point_node<BC>(n, c, i, j, an[0], an[1], an[2], an[3], an[4]);
 }
 
 }  // namespace sgn

@@ -491,8 +491,10 @@ cudaError_t launch_adjoint(const sgn_ctx* c, sgn::AdjArgs a, double* scratch_tap
 }
 
 // Adjoint scratch, allocated on first use: RK accumulator and two cotangents
-// (15 planes), the weights and node parts (ADJ_SCRATCH_PLANES), a tape (N_TAPE).
-constexpr long long kAdjTapeOffset = 15 + sgn::ADJ_SCRATCH_PLANES;
+// (15 planes), two buffers of weights and node parts (ADJ_SCRATCH_PLANES
+// each: a chained walk alternates them), a tape (N_TAPE).
+constexpr long long kAdjScratchB = 15 + sgn::ADJ_SCRATCH_PLANES;
+constexpr long long kAdjTapeOffset = 15 + 2 * sgn::ADJ_SCRATCH_PLANES;
 static_assert(SGN_TAPE_PLANES == sgn::N_TAPE, "the header's tape size");
 
 template <int MODE>
@@ -500,6 +502,28 @@ cudaError_t adjoint(const sgn_ctx* c, const sgn::AdjArgs& a, cudaStream_t s) {
     double* scratch_tape = c->adj + kAdjTapeOffset * c->G.plane;
     return c->p.bc == SGN_BC_REFLECTING ? launch_adjoint<sgn::BC_REFLECTING, MODE>(c, a, scratch_tape, s)
                                         : launch_adjoint<sgn::BC_PERIODIC, MODE>(c, a, scratch_tape, s);
+}
+
+// The walk of one step with recorded tapes: pass 1 of stage 4, then pass 2
+// of stages 4, 3, 2 each chained with pass 1 of the stage before it
+// (k_adj_gather_point, alternating the two weight buffers), then pass 2 of
+// stage 1: five launches.  `g[s]` are the stage-mode arguments of stage s+1
+// (weights in buffer A for stages 4 and 2, B for 3 and 1).
+template <int BC>
+cudaError_t chained_walk(const sgn_ctx* c, const sgn::AdjArgs g[4], cudaStream_t s) {
+    const unsigned blocks = (unsigned)((c->G.plane + sgn::ADJ_BLOCK - 1) / sgn::ADJ_BLOCK);
+    sgn::k_adj_point<BC><<<blocks, sgn::ADJ_BLOCK, 0, s>>>(g[3]);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    for (int st = 3; st >= 1 && e == cudaSuccess; st--) {
+        sgn::k_adj_gather_point<BC><<<blocks, sgn::ADJ_BLOCK, 0, s>>>(g[st], g[st - 1]);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return e;
+    sgn::k_adj_gather<BC, sgn::ADJ_MODE_STAGE><<<blocks, sgn::ADJ_BLOCK, 0, s>>>(g[0]);
+    count_launch();
+    return cudaGetLastError();
 }
 
 sgn_status adjoint_scratch(sgn_ctx* c) {
@@ -1052,6 +1076,26 @@ sgn_status step_vjp(sgn_ctx* c, const void* stash_dev, const void* tape_dev, voi
     a.flag = c->flag;
     a.G = c->G;
     cudaError_t e;
+    if (tape) {
+        // recorded tapes: the chained walk (the same values in the same
+        // operations as the eight launches below, bit for bit)
+        sgn::AdjArgs g[4];
+        for (int st = 0; st < 4; st++) {
+            g[st] = a;
+            g[st].X = stash + st * P5;
+            g[st].tape = tape_of(st + 1);
+            g[st].scratch = c->adj + ((st % 2 == 1) ? 15 * c->G.plane : kAdjScratchB * c->G.plane);
+            g[st].Anext = nullptr;
+        }
+        g[3].A = qbar; g[3].sigma = sig4; g[3].first = 1; g[3].qacc_out = qacc; g[3].kappa = kap3;
+        g[2].sigma = sig3; g[2].first = 0; g[2].qacc_in = qacc; g[2].qacc_out = qacc; g[2].kappa = kap2;
+        g[1].sigma = sig2; g[1].first = 0; g[1].qacc_in = qacc; g[1].qacc_out = qacc; g[1].kappa = kap1;
+        g[0].sigma = sig1; g[0].first = 0; g[0].qacc_in = qacc; g[0].qacc_out = qbar;
+        e = c->p.bc == SGN_BC_REFLECTING ? chained_walk<sgn::BC_REFLECTING>(c, g, s)
+                                         : chained_walk<sgn::BC_PERIODIC>(c, g, s);
+        if (e != cudaSuccess) return cuda_fail(e, what);
+        return SGN_OK;
+    }
     // stage 4: k4bar = dt/6 qbar'; Q4bar = J(Q4)^T k4bar; k3bar = dt/3 qbar' + dt Q4bar
     a.X = stash + 3 * P5; a.tape = tape_of(4); a.A = qbar; a.sigma = sig4;
     a.first = 1; a.qacc_out = qacc; a.Anext = A0; a.kappa = kap3;
