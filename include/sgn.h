@@ -197,7 +197,7 @@ SGN_API sgn_status sgn_mass_energy_noalloc(const sgn_params* p, const void* b_de
  * contexts only (else SGN_E_UNSUPPORTED).  Three launches: the tape of the
  * RHS at q (its intermediate values, SGN_TAPE_PLANES planes, written by the
  * FP64 stage kernel), then the two adjoint passes, which read it.  The first
- * adjoint call of a context allocates 88 planes of scratch (SGN_E_NOMEM if
+ * adjoint call of a context allocates 99 planes of scratch (SGN_E_NOMEM if
  * that fails).  Asynchronous. */
 SGN_API sgn_status sgn_rhs_vjp(sgn_ctx* ctx, const void* q_dev, const void* abar_dev, void* qbar_dev,
                                void* bbar_dev, void* stream);
@@ -216,12 +216,13 @@ SGN_API sgn_status sgn_step_record(sgn_ctx* ctx, void* q_dev, double dt, int nst
  * k3bar = dt/3 qbar' + dt Q4bar, Q3bar = J(Q3)^T k3bar, k2bar = dt/3 qbar' +
  * dt/2 Q3bar, Q2bar = J(Q2)^T k2bar, k1bar = dt/6 qbar' + dt/2 Q2bar,
  * Q1bar = J(q_n)^T k1bar, qbar = qbar' + Q1bar + Q2bar + Q3bar + Q4bar, and
- * bbar_dev += sum_s (d RHS / d b)(Q_s)^T ks_bar.  Twelve launches (per
- * stage: the tape of the RHS at Q_s, then the two adjoint passes).
+ * bbar_dev += sum_s (d RHS / d b)(Q_s)^T ks_bar.  Nine launches: the tape
+ * of the RHS at each Q_s, and the two adjoint passes per stage, the second
+ * pass of stages 4, 3, 2 fused with the first pass of the stage before it.
  * Internally the stage cotangents are carried with the scales
  * dt/6, dt^2/6, dt^3/12, dt^4/24 factored out; a dt for which dt^4/24 is not a
  * normal double returns SGN_E_INVAL.  The first adjoint call of a context
- * allocates 88 planes of scratch (SGN_E_NOMEM if that fails).  SGN_F64 only.
+ * allocates 99 planes of scratch (SGN_E_NOMEM if that fails).  SGN_F64 only.
  * Asynchronous. */
 SGN_API sgn_status sgn_step_vjp(sgn_ctx* ctx, const void* stash_dev, void* qbar_dev, void* bbar_dev,
                                 double dt, void* stream);

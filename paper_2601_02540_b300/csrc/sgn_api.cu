@@ -490,11 +490,13 @@ cudaError_t launch_adjoint(const sgn_ctx* c, sgn::AdjArgs a, double* scratch_tap
     return cudaGetLastError();
 }
 
-// Adjoint scratch, allocated on first use: RK accumulator and two cotangents
-// (15 planes), two buffers of weights and node parts (ADJ_SCRATCH_PLANES
-// each: a chained walk alternates them), a tape (N_TAPE).
-constexpr long long kAdjScratchB = 15 + sgn::ADJ_SCRATCH_PLANES;
-constexpr long long kAdjTapeOffset = 15 + 2 * sgn::ADJ_SCRATCH_PLANES;
+// Adjoint scratch, allocated on first use: the RK accumulator of the
+// cotangents (5 planes), two buffers of weights and node parts
+// (ADJ_SCRATCH_PLANES each: a chained walk alternates them), two tapes
+// (N_TAPE each).
+constexpr long long kAdjScratchA = 5;
+constexpr long long kAdjScratchB = kAdjScratchA + sgn::ADJ_SCRATCH_PLANES;
+constexpr long long kAdjTapeOffset = kAdjScratchA + 2 * sgn::ADJ_SCRATCH_PLANES;
 static_assert(SGN_TAPE_PLANES == sgn::N_TAPE, "the header's tape size");
 
 template <int MODE>
@@ -504,18 +506,24 @@ cudaError_t adjoint(const sgn_ctx* c, const sgn::AdjArgs& a, cudaStream_t s) {
                                         : launch_adjoint<sgn::BC_PERIODIC, MODE>(c, a, scratch_tape, s);
 }
 
-// The walk of one step with recorded tapes: pass 1 of stage 4, then pass 2
-// of stages 4, 3, 2 each chained with pass 1 of the stage before it
-// (k_adj_gather_point, alternating the two weight buffers), then pass 2 of
-// stage 1: five launches.  `g[s]` are the stage-mode arguments of stage s+1
-// (weights in buffer A for stages 4 and 2, B for 3 and 1).
+// The walk of one step: pass 1 of stage 4, then pass 2 of stages 4, 3, 2
+// each chained with pass 1 of the stage before it (k_adj_gather_point,
+// alternating the two weight buffers), then pass 2 of stage 1: five launches.
+// `g[s]` are the stage-mode arguments of stage s+1 (weights in buffer A for
+// stages 4 and 2, B for 3 and 1).  With `tapes`, the tape of each stage is
+// first computed from its state (a TAPE launch) into g[s].tape, just before
+// the launch that first reads it: nine launches.
 template <int BC>
-cudaError_t chained_walk(const sgn_ctx* c, const sgn::AdjArgs g[4], cudaStream_t s) {
+cudaError_t chained_walk(const sgn_ctx* c, const sgn::AdjArgs g[4], bool tapes, cudaStream_t s) {
     const unsigned blocks = (unsigned)((c->G.plane + sgn::ADJ_BLOCK - 1) / sgn::ADJ_BLOCK);
+    cudaError_t e = cudaSuccess;
+    if (tapes && (e = launch_tape<BC>(c, g[3].X, const_cast<double*>(g[3].tape), s)) != cudaSuccess) return e;
     sgn::k_adj_point<BC><<<blocks, sgn::ADJ_BLOCK, 0, s>>>(g[3]);
     count_launch();
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     for (int st = 3; st >= 1 && e == cudaSuccess; st--) {
+        if (tapes && (e = launch_tape<BC>(c, g[st - 1].X, const_cast<double*>(g[st - 1].tape), s)) != cudaSuccess)
+            return e;
         sgn::k_adj_gather_point<BC><<<blocks, sgn::ADJ_BLOCK, 0, s>>>(g[st], g[st - 1]);
         count_launch();
         e = cudaGetLastError();
@@ -528,7 +536,7 @@ cudaError_t chained_walk(const sgn_ctx* c, const sgn::AdjArgs g[4], cudaStream_t
 
 sgn_status adjoint_scratch(sgn_ctx* c) {
     if (c->adj) return SGN_OK;
-    const size_t bytes = (size_t)(kAdjTapeOffset + sgn::N_TAPE) * (size_t)c->G.plane * sizeof(double);
+    const size_t bytes = (size_t)(kAdjTapeOffset + 2 * sgn::N_TAPE) * (size_t)c->G.plane * sizeof(double);
     if (cudaMalloc(&c->adj, bytes) != cudaSuccess) {
         cudaGetLastError();
         c->adj = nullptr;
@@ -1057,8 +1065,6 @@ sgn_status step_vjp(sgn_ctx* c, const void* stash_dev, const void* tape_dev, voi
     const double* tape = static_cast<const double*>(tape_dev);
     double* qbar = static_cast<double*>(qbar_dev);
     double* qacc = c->adj;
-    double* A0 = c->adj + P5;
-    double* A1 = c->adj + 2 * P5;
     // The cotangent of stage s is sigma_s * A_s: sigma_4 = dt/6, A_4 = qbar', and
     // k_{s-1} = c' qbar' + cbar Qbar_s gives sigma_{s-1} = cbar sigma_s and
     // A_{s-1} = (c' / sigma_{s-1}) qbar' + J^T A_s (one FMA per value).
@@ -1070,46 +1076,36 @@ sgn_status step_vjp(sgn_ctx* c, const void* stash_dev, const void* tape_dev, voi
     sgn::AdjArgs a;
     std::memset(&a, 0, sizeof(a));
     a.b = c->b64;
-    a.scratch = c->adj + 15 * c->G.plane;
+    a.scratch = c->adj + kAdjScratchA * c->G.plane;
     a.bbar = static_cast<double*>(bbar_dev);
     a.qprime = qbar;
     a.flag = c->flag;
     a.G = c->G;
-    cudaError_t e;
-    if (tape) {
-        // recorded tapes: the chained walk (the same values in the same
-        // operations as the eight launches below, bit for bit)
-        sgn::AdjArgs g[4];
-        for (int st = 0; st < 4; st++) {
-            g[st] = a;
-            g[st].X = stash + st * P5;
-            g[st].tape = tape_of(st + 1);
-            g[st].scratch = c->adj + ((st % 2 == 1) ? 15 * c->G.plane : kAdjScratchB * c->G.plane);
-            g[st].Anext = nullptr;
-        }
-        g[3].A = qbar; g[3].sigma = sig4; g[3].first = 1; g[3].qacc_out = qacc; g[3].kappa = kap3;
-        g[2].sigma = sig3; g[2].first = 0; g[2].qacc_in = qacc; g[2].qacc_out = qacc; g[2].kappa = kap2;
-        g[1].sigma = sig2; g[1].first = 0; g[1].qacc_in = qacc; g[1].qacc_out = qacc; g[1].kappa = kap1;
-        g[0].sigma = sig1; g[0].first = 0; g[0].qacc_in = qacc; g[0].qacc_out = qbar;
-        e = c->p.bc == SGN_BC_REFLECTING ? chained_walk<sgn::BC_REFLECTING>(c, g, s)
-                                         : chained_walk<sgn::BC_PERIODIC>(c, g, s);
-        if (e != cudaSuccess) return cuda_fail(e, what);
-        return SGN_OK;
+    // The chained walk (see chained_walk).  Without recorded tapes each
+    // stage's tape is computed from its recorded state just before the launch
+    // that first reads it, into two scratch tapes used alternately (stages 4
+    // and 2 in one, 3 and 1 in the other).
+    double* tA = c->adj + kAdjTapeOffset * c->G.plane;
+    double* tB = c->adj + (kAdjTapeOffset + sgn::N_TAPE) * c->G.plane;
+    sgn::AdjArgs g[4];
+    for (int k = 0; k < 4; k++) {
+        g[k] = a;
+        g[k].X = stash + k * P5;
+        g[k].tape = tape ? tape_of(k + 1) : ((k % 2 == 1) ? tA : tB);
+        g[k].scratch = c->adj + ((k % 2 == 1) ? kAdjScratchA : kAdjScratchB) * c->G.plane;
+        g[k].Anext = nullptr;
     }
     // stage 4: k4bar = dt/6 qbar'; Q4bar = J(Q4)^T k4bar; k3bar = dt/3 qbar' + dt Q4bar
-    a.X = stash + 3 * P5; a.tape = tape_of(4); a.A = qbar; a.sigma = sig4;
-    a.first = 1; a.qacc_out = qacc; a.Anext = A0; a.kappa = kap3;
-    if ((e = adjoint<sgn::ADJ_MODE_STAGE>(c, a, s)) != cudaSuccess) return cuda_fail(e, what);
+    g[3].A = qbar; g[3].sigma = sig4; g[3].first = 1; g[3].qacc_out = qacc; g[3].kappa = kap3;
     // stage 3: Q3bar = J(Q3)^T k3bar; k2bar = dt/3 qbar' + dt/2 Q3bar
-    a.X = stash + 2 * P5; a.tape = tape_of(3); a.A = A0; a.sigma = sig3;
-    a.first = 0; a.qacc_in = qacc; a.qacc_out = qacc; a.Anext = A1; a.kappa = kap2;
-    if ((e = adjoint<sgn::ADJ_MODE_STAGE>(c, a, s)) != cudaSuccess) return cuda_fail(e, what);
+    g[2].sigma = sig3; g[2].first = 0; g[2].qacc_in = qacc; g[2].qacc_out = qacc; g[2].kappa = kap2;
     // stage 2: Q2bar = J(Q2)^T k2bar; k1bar = dt/6 qbar' + dt/2 Q2bar
-    a.X = stash + P5; a.tape = tape_of(2); a.A = A1; a.sigma = sig2; a.Anext = A0; a.kappa = kap1;
-    if ((e = adjoint<sgn::ADJ_MODE_STAGE>(c, a, s)) != cudaSuccess) return cuda_fail(e, what);
+    g[1].sigma = sig2; g[1].first = 0; g[1].qacc_in = qacc; g[1].qacc_out = qacc; g[1].kappa = kap1;
     // stage 1: Q1bar = J(q_n)^T k1bar; qbar = qbar' + Q1bar + Q2bar + Q3bar + Q4bar
-    a.X = stash; a.tape = tape_of(1); a.A = A0; a.sigma = sig1; a.Anext = nullptr; a.qacc_out = qbar;
-    if ((e = adjoint<sgn::ADJ_MODE_STAGE>(c, a, s)) != cudaSuccess) return cuda_fail(e, what);
+    g[0].sigma = sig1; g[0].first = 0; g[0].qacc_in = qacc; g[0].qacc_out = qbar;
+    const cudaError_t e = c->p.bc == SGN_BC_REFLECTING ? chained_walk<sgn::BC_REFLECTING>(c, g, !tape, s)
+                                                       : chained_walk<sgn::BC_PERIODIC>(c, g, !tape, s);
+    if (e != cudaSuccess) return cuda_fail(e, what);
     return SGN_OK;
 }
 
@@ -1410,7 +1406,7 @@ sgn_status sgn_rhs_vjp(sgn_ctx* c, const void* q_dev, const void* abar_dev, void
     if (st != SGN_OK) return st;
     sgn::AdjArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.scratch = c->adj + 15 * c->G.plane;
+    a.scratch = c->adj + kAdjScratchA * c->G.plane;
     a.X = static_cast<const double*>(q_dev);
     a.b = c->b64;
     a.A = static_cast<const double*>(abar_dev);
