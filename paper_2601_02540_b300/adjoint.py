@@ -21,7 +21,7 @@ With ``tape`` (K > 0), the recorded segments also keep the tapes of their
 stage RHS evaluations (``sgn_step_record_tape``: the intermediate values of
 the RHS, written by the stage kernels as they advance the state), and the
 walk reads them (``sgn_step_vjp_tape``) instead of evaluating them again:
-the adjoint then costs two launches per stage instead of three.  Memory: two
+a step's adjoint then takes five launches instead of nine.  Memory: two
 K-step stashes of 20 planes per step, plus with the tape two of 84 planes
 per step (4.2 GB and 17.6 GB at 512^2 for K = 100).  ``tape=None`` takes the
 tape when it fits in half of the free device memory.  K <= 0 keeps the stage
