@@ -1,5 +1,7 @@
 // sgn_fused.cuh - two classical RK4 stages per launch (temporal blocking) for
-// the FP32 mode, which is bound by memory traffic.
+// the FP32 mode, which is bound by memory traffic.  The stages evaluate the
+// split-form SBP right-hand side of eq. (sd_periodic_2D_SGN) / eq. (semi_2D)
+// as the single-stage kernels do (node_rhs_src).
 //
 // The unfused FP32 step moves 74 planes per node (S1K 11, S2K 21, S3 26, S4
 // 16, see the stage modes).  Here one kernel advances stages 1 and 2 and one
