@@ -134,8 +134,11 @@ struct BatchFusedArgs {
     int* flag;
 };
 
+// (registers as the single-grid kernels: the S34 kernel, which holds the
+// reflecting branch, for three blocks per SM)
 template <typename TC, typename TA, int PAIR>
-__global__ void __launch_bounds__(BLOCK_THREADS, 4) k_batch_fused(BatchFusedArgs<TC, TA> a) {
+__global__ void __launch_bounds__(BLOCK_THREADS, (kFusedMinBlocks<BC_REFLECTING, PAIR>))
+k_batch_fused(BatchFusedArgs<TC, TA> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const PTile T = a.tiles[blockIdx.x];
     const InstDesc& d = a.desc[T.inst];
