@@ -1,8 +1,10 @@
 """The reciprocals 1/h of the stage kernels against the IEEE division on the
 GPU: the FP64 kernels refine the hardware's approximate reciprocal by one
 third-order step (at most one ulp from the correctly rounded quotient); the
-df64 kernels refine the float reciprocal by one Newton step in double-word
-arithmetic (relative error near 2^-46).  Compiles tests/recip_check.cu, which
+FP32 kernels refine the float approximation by one Newton step (at most one
+ulp; measured: correctly rounded on every sample); the df64 kernels refine
+the float reciprocal by one Newton step in double-word arithmetic (relative
+error near 2^-46).  Compiles tests/recip_check.cu, which
 includes the library's kernel header, with nvcc for sm_103a and runs it over
 1.7e7 values of h in [2^-20, 2^21)."""
 from __future__ import annotations
@@ -29,4 +31,6 @@ def test_reciprocals_against_ieee_division(tmp_path):
     assert int(vals["samples"]) == 1 << 24
     assert int(vals["f64_max_ulp"]) <= 1, out
     assert int(vals["f64_not_rounded"]) <= (1 << 24) // 1000, out      # measured: 0.03%
+    assert int(vals["f32_max_ulp"]) <= 1, out
+    assert int(vals["f32_not_rounded"]) <= (1 << 24) // 1000, out      # measured: none
     assert float(vals["df64_max_rel"]) <= 2.0 ** -44, out
