@@ -444,7 +444,7 @@ def _ensemble(torch, steps: int, warmup: int, loop_steps: int = 50) -> dict:
     bs = sgn.BatchSolver(probs, prec="f32")
     q = bs.pack([p.q0 for p in probs])
     bs.init_aux(q)
-    # every tiling the autotuner searches, timed over one 25-step graph replay
+    # every tiling the autotuner searches, timed over one 26-step graph replay
     # on a copy of the state, then the autotuner's own choice
     per_tiling = {}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -455,14 +455,14 @@ def _ensemble(torch, steps: int, warmup: int, loop_steps: int = 50) -> dict:
         bs.set_persistent(pers)
         bs.set_stage_fusion(fuse)
         w = q.clone()
-        bs.step(w, 25)
+        bs.step(w, 26)
         torch.cuda.synchronize()
         e0.record()
-        bs.step(w, 25)
+        bs.step(w, 26)
         e1.record()
         torch.cuda.synchronize()
         name = "rows2_two_stages_per_launch" if fuse else f"rows{r}_{'persistent' if pers else 'per_tile'}"
-        per_tiling[name] = 4.0 * cells * 25 / (e0.elapsed_time(e1) * 1e-3)
+        per_tiling[name] = 4.0 * cells * 26 / (e0.elapsed_time(e1) * 1e-3)
         del w
     bs.set_persistent(False)
     rows = bs.autotune(q)

@@ -366,7 +366,7 @@ SGN_API sgn_status sgn_step_adaptive(sgn_ctx* ctx, void* q_dev, double t0, doubl
  * Many independent grids (each its own size, boundary treatment, parameters
  * and fixed time step) advanced together: one launch per RK4 stage covers a
  * tile list spanning every instance, and sgn_batch_step replays CUDA graphs of
- * 25 steps.  The arithmetic per node is the single-grid kernel's, in the same
+ * 26 steps.  The arithmetic per node is the single-grid kernel's, in the same
  * order, so each instance evolves exactly as with sgn_step.
  *
  * Packed layout: instance i owns nx_i*ny_i nodes starting at node offset
@@ -410,7 +410,10 @@ SGN_API sgn_status sgn_batch_set_persistent(sgn_batch* batch, int on);
 /* SGN_F32 ensembles: on = 1 (default) advances sgn_batch_step two RK4 stages
  * per launch over 32 x 16 tiles (as sgn_set_stage_fusion for one grid; the
  * same states bit for bit, q_{n+1} alternately in q_dev and batch scratch,
- * an odd step count ends with one copy), on = 0 one launch per stage with the
+ * an odd step count ends with one copy), one launch per boundary class
+ * present (the periodic instances' tiles, then the reflecting ones, each
+ * kernel with the registers of its own boundary treatment), so two or four
+ * launches per step; on = 0 one launch per stage with the
  * tiling of sgn_batch_set_rows / sgn_batch_set_persistent; the persistent
  * kernel, when selected, takes precedence.  Other precisions: on = 1 is
  * SGN_E_UNSUPPORTED. */

@@ -30,7 +30,8 @@ sgn_status bcuda(cudaError_t e, const char* what) {
     return SGN_E_CUDA;
 }
 
-constexpr int kGraphSteps = 25;   // RK4 steps captured per graph replay
+constexpr int kGraphSteps = 26;   // RK4 steps captured per graph replay (even: the two-stage
+                                  // FP32 launches end an odd step count with a copy of the state)
 
 }  // namespace
 
@@ -44,6 +45,7 @@ struct sgn_batch {
     sgn::InstDesc* desc = nullptr;     // device
     sgn::PTile* tiles[3] = {nullptr, nullptr, nullptr};   // tile records for rows = 1, 2, 4
     long long ntiles[3] = {0, 0, 0};
+    long long nper2 = 0;               // periodic tiles, at the front of the rows-2 list
     // the persistent kernel (float compute types, rows = 1, 2): its grid per
     // (rows, stage), resident blocks per SM x SMs
     int pgrid[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
@@ -67,6 +69,12 @@ struct sgn_batch {
 };
 
 namespace {
+
+// Kernel launches per RK4 step of the batched path as configured.
+unsigned long long fused_launches_per_step(const sgn_batch* B) {
+    if (!(B->fuse && !B->persist && B->prec == SGN_F32)) return 4ull;
+    return 2ull * ((B->nper2 > 0 ? 1ull : 0ull) + (B->ntiles[1] > B->nper2 ? 1ull : 0ull));
+}
 
 int rows_index(int rows) { return rows == 1 ? 0 : (rows == 2 ? 1 : 2); }
 
@@ -149,12 +157,14 @@ template <typename TC, typename TA>
 cudaError_t set_attrs() {
     if constexpr (sgn::kStoreK1<TC, TA>) {
         const size_t smem = sgn::FusedLayout<2>::template bytes<TC>();
-        cudaError_t ef = cudaFuncSetAttribute(sgn::k_batch_fused<TC, TA, sgn::FUSED_S12>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (ef == cudaSuccess)
-            ef = cudaFuncSetAttribute(sgn::k_batch_fused<TC, TA, sgn::FUSED_S34>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (ef != cudaSuccess) return ef;
+        const void* fk[4] = {(const void*)sgn::k_batch_fused<TC, TA, sgn::FUSED_S12, sgn::CLS_PERIODIC>,
+                             (const void*)sgn::k_batch_fused<TC, TA, sgn::FUSED_S12, sgn::CLS_REFLECTING>,
+                             (const void*)sgn::k_batch_fused<TC, TA, sgn::FUSED_S34, sgn::CLS_PERIODIC>,
+                             (const void*)sgn::k_batch_fused<TC, TA, sgn::FUSED_S34, sgn::CLS_REFLECTING>};
+        for (const void* k : fk) {
+            const cudaError_t ef = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (ef != cudaSuccess) return ef;
+        }
     }
     cudaError_t e = set_attrs_rows<TC, TA, 1>();
     if (e == cudaSuccess) e = set_attrs_rows<TC, TA, 2>();
@@ -179,22 +189,40 @@ cudaError_t bsteps_fused(sgn_batch* B, TA* q, int nsteps, cudaStream_t s) {
     f.flag = B->flag;
     TA* cur = q;
     TA* nxt = static_cast<TA*>(B->Qb);
-    const dim3 grid((unsigned)B->ntiles[1]), block(sgn::TILE_X, sgn::THREADS_Y);
+    // one launch per tile class (periodic tiles first), each with the
+    // registers of its own boundary treatment
+    const long long np = B->nper2, nr = B->ntiles[1] - B->nper2;
+    const dim3 block(sgn::TILE_X, sgn::THREADS_Y);
     cudaError_t e = cudaSuccess;
     for (int n = 0; n < nsteps; n++) {
         sgn::BatchFusedArgs<TC, TA> f12 = f;
         f12.q = cur;
         f12.Qout = static_cast<TC*>(B->Qa);
-        sgn::k_batch_fused<TC, TA, sgn::FUSED_S12><<<grid, block, smem, s>>>(f12);
-        if (!B->capturing) sgn_count_launches(1);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
         sgn::BatchFusedArgs<TC, TA> f34 = f;
         f34.q = cur;
         f34.X = static_cast<const TC*>(B->Qa);
         f34.out = nxt;
-        sgn::k_batch_fused<TC, TA, sgn::FUSED_S34><<<grid, block, smem, s>>>(f34);
-        if (!B->capturing) sgn_count_launches(1);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        for (int pair = 0; pair < 2; pair++) {
+            sgn::BatchFusedArgs<TC, TA> fa = pair == 0 ? f12 : f34;
+            if (np > 0) {
+                fa.first = 0;
+                if (pair == 0)
+                    sgn::k_batch_fused<TC, TA, sgn::FUSED_S12, sgn::CLS_PERIODIC><<<(unsigned)np, block, smem, s>>>(fa);
+                else
+                    sgn::k_batch_fused<TC, TA, sgn::FUSED_S34, sgn::CLS_PERIODIC><<<(unsigned)np, block, smem, s>>>(fa);
+                if (!B->capturing) sgn_count_launches(1);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            }
+            if (nr > 0) {
+                fa.first = np;
+                if (pair == 0)
+                    sgn::k_batch_fused<TC, TA, sgn::FUSED_S12, sgn::CLS_REFLECTING><<<(unsigned)nr, block, smem, s>>>(fa);
+                else
+                    sgn::k_batch_fused<TC, TA, sgn::FUSED_S34, sgn::CLS_REFLECTING><<<(unsigned)nr, block, smem, s>>>(fa);
+                if (!B->capturing) sgn_count_launches(1);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            }
+        }
         std::swap(cur, nxt);
     }
     if (cur != q) e = cudaMemcpyAsync(q, cur, (size_t)5 * B->cells * sizeof(TA), cudaMemcpyDeviceToDevice, s);
@@ -413,10 +441,15 @@ sgn_status sgn_batch_create(const sgn_instance* inst, int ninst, int prec, const
     // tile lists for the three tile heights (rows = 1: the 32 x 8 bands)
     for (int ri = 0; ri < 3; ri++) {
         const int th = sgn::THREADS_Y * (ri == 0 ? 1 : (ri == 1 ? 2 : 4));
-        for (int k = 0; k < ninst; k++) {
-            const sgn::Geom& G = B->hdesc[k].G;
-            for (int j0 = 0; j0 < G.ny; j0 += th)
-                for (int i0 = 0; i0 < G.nx; i0 += sgn::TILE_X) tl[ri].push_back(make_int4(k, i0, j0, 0));
+        // rows 2 (the fused launches): the periodic instances' tiles first
+        for (int pass = 0; pass < (ri == 1 ? 2 : 1); pass++) {
+            for (int k = 0; k < ninst; k++) {
+                if (ri == 1 && (B->hdesc[k].bc == SGN_BC_PERIODIC) != (pass == 0)) continue;
+                const sgn::Geom& G = B->hdesc[k].G;
+                for (int j0 = 0; j0 < G.ny; j0 += th)
+                    for (int i0 = 0; i0 < G.nx; i0 += sgn::TILE_X) tl[ri].push_back(make_int4(k, i0, j0, 0));
+            }
+            if (ri == 1 && pass == 0) B->nper2 = (long long)tl[ri].size();
         }
         B->ntiles[ri] = (long long)tl[ri].size();
     }
@@ -567,7 +600,7 @@ sgn_status sgn_batch_step(sgn_batch* B, void* q_dev, int nsteps, void* stream) {
         while (left >= kGraphSteps) {
             cudaError_t e = cudaGraphLaunch(B->exec, s);
             if (e != cudaSuccess) return bcuda(e, "graph launch");
-            sgn_count_launches((B->fuse && !B->persist && B->prec == SGN_F32 ? 2ull : 4ull) * kGraphSteps);
+            sgn_count_launches(fused_launches_per_step(B) * kGraphSteps);
             left -= kGraphSteps;
         }
     }

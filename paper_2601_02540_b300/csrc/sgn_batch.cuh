@@ -118,7 +118,7 @@ k_batch_stage(BatchArgs<TC, TIN, TA> a) {
 }
 
 // Two RK4 stages per launch over the ensemble (FP32; see sgn_fused.cuh):
-// block k takes the 32 x 16 tile of record k and runs fused_tile with the
+// block k takes the 32 x 16 tile of record first + k and runs fused_tile with the
 // instance's planes, grid and coefficients, so every instance advances as
 // its single-grid fused (and unfused) steps do, bit for bit.
 template <typename TC, typename TA>
@@ -132,15 +132,19 @@ struct BatchFusedArgs {
     TC* Qout;              // S12: packed Q3
     TA* out;               // S34: packed q_{n+1}
     int* flag;
+    long long first;       // the launch's first tile record
 };
 
-// (registers as the single-grid kernels: the S34 kernel, which holds the
-// reflecting branch, for three blocks per SM)
-template <typename TC, typename TA, int PAIR>
-__global__ void __launch_bounds__(BLOCK_THREADS, (kFusedMinBlocks<BC_REFLECTING, PAIR>))
+// Tile classes of a fused launch: every tile periodic, every tile reflecting,
+// or either (the boundary treatment read from the record).
+enum { CLS_MIXED = 0, CLS_PERIODIC = 1, CLS_REFLECTING = 2 };
+// (registers as the single-grid kernels of the class: the reflecting S34 for
+// three blocks per SM)
+template <typename TC, typename TA, int PAIR, int CLS>
+__global__ void __launch_bounds__(BLOCK_THREADS, (kFusedMinBlocks<CLS == CLS_PERIODIC ? BC_PERIODIC : BC_REFLECTING, PAIR>))
 k_batch_fused(BatchFusedArgs<TC, TA> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const PTile T = a.tiles[blockIdx.x];
+    const PTile T = a.tiles[a.first + blockIdx.x];
     const InstDesc& d = a.desc[T.inst];
     Geom G = d.G;
     G.nx = T.nx;
@@ -164,10 +168,10 @@ k_batch_fused(BatchFusedArgs<TC, TA> a) {
     f.c_q2 = (TA)d.c_q[1];
     f.c_q3 = (TA)d.c_q[2];
     TC* sm = reinterpret_cast<TC*>(smem_raw);
-    if (T.bc == BC_REFLECTING)
-        fused_tile<TC, TA, BC_REFLECTING, PAIR, 2>(f, G, T.i0, T.j0, sm);
-    else
+    if (CLS == CLS_PERIODIC || (CLS == CLS_MIXED && T.bc == BC_PERIODIC))
         fused_tile<TC, TA, BC_PERIODIC, PAIR, 2>(f, G, T.i0, T.j0, sm);
+    else
+        fused_tile<TC, TA, BC_REFLECTING, PAIR, 2>(f, G, T.i0, T.j0, sm);
 }
 
 // Per-instance sums of the band partials, in band order (one block each; the

@@ -33,7 +33,7 @@ def test_batch_equals_single_grid_bitwise(prec):
     probs = _ensemble()
     bs = sgn.BatchSolver(probs, prec=prec)
     q = bs.pack([p.q0 for p in probs])
-    bs.step(q, 30)          # one 25-step graph replay + 5 direct steps
+    bs.step(q, 30)          # one 26-step graph replay + 4 direct steps
     got = bs.unpack(q)
     for p, g in zip(probs, got):
         s = sgn.Solver.from_problem(p, prec=prec)
@@ -130,13 +130,14 @@ def test_batch_workload_recipe_small():
 
 
 # ------------------------------------------------------------------ two stages per launch
-@pytest.mark.parametrize("nsteps", [1, 30])
+@pytest.mark.parametrize("nsteps", [1, 31])
 def test_fused_ensemble_equals_one_stage_per_launch_and_single_grids(nsteps):
-    """FP32 ensembles advance two RK4 stages per launch by default: the
-    states equal one launch per stage and each instance's single-grid fused
-    steps bit for bit (ragged grids down to 3x3, both boundary kinds; 30
-    steps: a 25-step graph replay and 5 direct steps, both odd, so the
-    result is copied back from the scratch state twice)."""
+    """FP32 ensembles advance two RK4 stages per launch by default, one
+    launch per boundary class: the states equal one launch per stage and
+    each instance's single-grid fused steps bit for bit (ragged grids down
+    to 3x3, both boundary kinds; 31 steps: a 26-step graph replay and 5
+    direct steps, the odd count ending with a copy back from the scratch
+    state)."""
     probs = _ensemble()
     bs = sgn.BatchSolver(probs, prec="f32")
     assert bs.tiling()["fused"]
