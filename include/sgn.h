@@ -152,6 +152,20 @@ SGN_API sgn_status sgn_step(sgn_ctx* ctx, void* q_dev, double dt, int nsteps, vo
  * step of device scratch. */
 SGN_API sgn_status sgn_step_diag(sgn_ctx* ctx, void* q_dev, double dt, int nsteps, double* out, void* stream);
 
+/* The end-to-end path for a state in host memory: copies the five planes at
+ * q_host ([5][ny][nx], x fastest, state type of prec, as q_dev elsewhere)
+ * into device memory owned by the context, advances them nsteps >= 0 RK4
+ * steps of size dt as sgn_step, or as sgn_step_diag when out is non-NULL
+ * (host, 3*nsteps doubles: mass, energy and shifted energy after each step),
+ * and copies the result back over q_host.  One copy each way per call, on
+ * `stream`; page-locked q_host moves at the link rate, pageable memory goes
+ * through the driver's staging.  Synchronizes `stream` and reports a latched
+ * h <= 0 / non-finite flag (the state is not copied back when the steps
+ * report an error).  q_host in device memory is SGN_E_INVAL.  The first call
+ * allocates the device state (5 planes), kept until sgn_destroy; calls on one
+ * context do not overlap. */
+SGN_API sgn_status sgn_step_host(sgn_ctx* ctx, void* q_host, double dt, int nsteps, double* out, void* stream);
+
 /* Diagnostics of q_dev (state type), accumulated in double in a fixed order:
  * per-node values summed over 32 x 8 node bands, then the band sums in band
  * order.  The order depends on the grid only (not on the precision mode or

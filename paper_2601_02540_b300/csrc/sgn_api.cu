@@ -87,6 +87,7 @@ struct sgn_ctx {
     double* rrk = nullptr;       // relaxation scratch (FP64): plain RK4 update (5 planes), partials, sums
     double* mon = nullptr;       // per-step monitor sums of sgn_step_diag (NDIAG per step)
     int mon_cap = 0;
+    void* hq = nullptr;          // device state of sgn_step_host (5 planes, state type)
     long long rrk_nblk = 0;
     // sgn_step on small grids: kGraphSteps RK4 steps captured once per (q, dt)
     // on a private stream and replayed on the caller's stream
@@ -444,6 +445,7 @@ void free_ctx(sgn_ctx* c) {
     cudaFree(c->bs);
     cudaFree(c->rrk);
     cudaFree(c->mon);
+    cudaFree(c->hq);
     cudaFreeHost(c->hout);
     cudaFreeHost(c->hflag);
     delete c;
@@ -1334,6 +1336,28 @@ sgn_status sgn_step_diag(sgn_ctx* c, void* q_dev, double dt, int nsteps, double*
     for (int n = 0; n < nsteps; n++)
         for (int k = 0; k < 3; k++) out[3 * n + k] = tmp[(size_t)n * sgn::NDIAG + k];
     return st;
+}
+
+sgn_status sgn_step_host(sgn_ctx* c, void* q_host, double dt, int nsteps, double* out, void* stream) {
+    if (!c) return fail(SGN_E_INVAL, "ctx is NULL");
+    if (!q_host) return fail(SGN_E_INVAL, "q_host is NULL");
+    if (is_device_ptr(q_host)) return fail(SGN_E_INVAL, "q_host is device memory (sgn_step takes device states)");
+    if (!finite_pos(dt)) return fail(SGN_E_INVAL, "dt must be finite and > 0");
+    if (nsteps < 0) return fail(SGN_E_INVAL, "nsteps must be >= 0");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)5 * (size_t)c->G.plane * c->ta_size;
+    if (!c->hq) {
+        if (cudaMalloc(&c->hq, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            c->hq = nullptr;
+            return fail(SGN_E_NOMEM, "device state of %zu bytes", bytes);
+        }
+    }
+    CUDA_TRY(cudaMemcpyAsync(c->hq, q_host, bytes, cudaMemcpyHostToDevice, s), "copy the state in");
+    sgn_status st = out ? sgn_step_diag(c, c->hq, dt, nsteps, out, stream) : sgn_step(c, c->hq, dt, nsteps, stream);
+    if (st != SGN_OK) return st;
+    CUDA_TRY(cudaMemcpyAsync(q_host, c->hq, bytes, cudaMemcpyDeviceToHost, s), "copy the state out");
+    return read_flag(c, s);
 }
 
 sgn_status sgn_mass_energy(sgn_ctx* c, const void* q_dev, double* out, void* stream) {

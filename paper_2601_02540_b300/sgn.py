@@ -46,6 +46,7 @@ _SIGNATURES = {
                                          _V, _V, _V]),
     "sgn_mass_energy": (ctypes.c_int, [_V, _V, _V, _V]),
     "sgn_step_diag": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_int, _V, _V]),
+    "sgn_step_host": (ctypes.c_int, [_V, _V, ctypes.c_double, ctypes.c_int, _V, _V]),
     "sgn_check": (ctypes.c_int, [_V, _V]),
     "sgn_mass_energy_noalloc": (ctypes.c_int, [_V, _V, _V, _V, _V]),
     "sgn_rhs_vjp": (ctypes.c_int, [_V, _V, _V, _V, _V, _V]),
@@ -227,6 +228,23 @@ def sgn_step_diag(ctx, q: torch.Tensor, dt: float, nsteps: int, dtype: torch.dty
     return [tuple(out[3 * k:3 * k + 3]) for k in range(int(nsteps))]
 
 
+def sgn_step_host(ctx, q_host: torch.Tensor, dt: float, nsteps: int, dtype: torch.dtype, monitor: bool = True,
+                  stream=None):
+    """RK4 steps of a state in host memory (copied in, advanced, copied back
+    over q_host by the library); with monitor, the list of (mass, energy,
+    energy_shifted) after each step, else None."""
+    if q_host.is_cuda:
+        raise ValueError("q_host must be a CPU tensor")
+    if q_host.dtype != dtype:
+        raise ValueError(f"q_host must be {dtype}, got {q_host.dtype}")
+    if not q_host.is_contiguous():
+        raise ValueError("q_host must be contiguous")
+    out = (ctypes.c_double * (3 * max(int(nsteps), 1)))() if monitor else None
+    _ok(lib().sgn_step_host(ctx, ctypes.c_void_p(q_host.data_ptr()), float(dt), int(nsteps), out,
+                            _stream(stream)), "sgn_step_host")
+    return [tuple(out[3 * k:3 * k + 3]) for k in range(int(nsteps))] if monitor else None
+
+
 def sgn_mass_energy(ctx, q: torch.Tensor, dtype: torch.dtype, stream=None) -> list[float]:
     out = (ctypes.c_double * 4)()
     _ok(lib().sgn_mass_energy(ctx, _dptr(q, dtype, "q"), out, _stream(stream)), "sgn_mass_energy")
@@ -375,6 +393,11 @@ class Solver:
     def step_diag(self, q: torch.Tensor, dt: float, nsteps: int) -> list:
         """nsteps RK4 steps; (mass, energy, energy_shifted) after each."""
         return sgn_step_diag(self.ctx, q, dt, nsteps, self.state_dtype)
+
+    def step_host(self, q_host: torch.Tensor, dt: float, nsteps: int, monitor: bool = True):
+        """nsteps RK4 steps of a state in host memory (CPU tensor, updated in
+        place through the library's own copies); see sgn_step_host."""
+        return sgn_step_host(self.ctx, q_host, dt, nsteps, self.state_dtype, monitor)
 
     def mass_energy(self, q: torch.Tensor) -> dict:
         m, e, es, r = sgn_mass_energy(self.ctx, q, self.state_dtype)

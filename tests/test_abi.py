@@ -65,6 +65,7 @@ def test_null_context_is_rejected(lib):
     assert lib.sgn_rhs(None, None, None, None) == 1
     assert lib.sgn_step(None, None, 0.1, 1, None) == 1
     assert lib.sgn_mass_energy(None, None, None, None) == 1
+    assert lib.sgn_step_host(None, None, 0.1, 1, None, None) == 1
     assert lib.sgn_step_record_tape(None, None, 0.1, 1, None, None, None) == 1
     assert lib.sgn_step_vjp_tape(None, None, None, None, None, 0.1, None) == 1
     assert lib.sgn_set_tile_rows(None, 1) == 1
