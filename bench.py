@@ -113,9 +113,16 @@ def _kernel_hash(text: str | None = None) -> str:
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
 
 
-def _ncu_traffic(prec: str) -> float | None:
+# The grid the committed per-launch traffic is stated for (the 4096^2 capture x 4).
+TRAFFIC_CELLS = 8192 * 8192
+
+
+def _ncu_traffic(prec: str, cells: int) -> float | None:
     """DRAM bytes per launch of the stage kernel from the committed ncu summary,
-    or None when the kernels changed since it was captured."""
+    or None when the kernels changed since it was captured or the grid is not
+    the one the figure is stated for."""
+    if cells != TRAFFIC_CELLS:
+        return None
     path = os.path.join(ROOT, "profiles", "k_stage_traffic_4096.md")
     if not os.path.exists(path):
         return None
@@ -248,7 +255,7 @@ def _roofline(prec: str, cells: int, ms_total: float, steps: int,
               hbm_peak: float, hbm_kind: str, fp64: dict | None = None) -> dict:
     launches_per_step, stages_per_launch, kernel = LAUNCH_SHAPE[prec]
     launch_ms = ms_total / (launches_per_step * steps)
-    traffic = _ncu_traffic(prec)
+    traffic = _ncu_traffic(prec, cells)
     if prec == "f64":
         # FP64 is ALU-bound on B300: the roofline is the FP64 pipe, whose
         # issue slots each take one FMA, add or multiply.  achieved = the
