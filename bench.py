@@ -281,10 +281,15 @@ def _roofline(prec: str, cells: int, ms_total: float, steps: int,
                         "frac": BYTES_PER_CELL_STAGE[prec] * cells / (launch_ms * 1e-3) / 1e9 / hbm_peak,
                         "peak_kind": hbm_kind}}
     achieved = BYTES_PER_CELL_STAGE[prec] * stages_per_launch * cells / (launch_ms * 1e-3) / 1e9
-    return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": hbm_kind,
-            "kernel": kernel, "launch_ms": launch_ms,
-            "algorithmic_bytes_per_cell_stage": BYTES_PER_CELL_STAGE[prec]}
+    out = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+           "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": hbm_kind,
+           "kernel": kernel, "launch_ms": launch_ms,
+           "algorithmic_bytes_per_cell_stage": BYTES_PER_CELL_STAGE[prec]}
+    if stages_per_launch > 1:
+        # two stages per launch halve the bytes and are bound by instruction
+        # issue: their rate against the roof of one launch per stage
+        out["single_stage_hbm_roof"] = _single_stage_roof(4.0 * cells * steps / (ms_total * 1e-3), hbm_peak)
+    return out
 
 
 def _cpu_baseline(p_full: inputs.Problem) -> dict:
@@ -509,7 +514,17 @@ def _ensemble(torch, steps: int, warmup: int, loop_steps: int = 50) -> dict:
             "rows": rows, "tiling": tiling, "per_tiling_rate": per_tiling,
             "hbm_gbs": hbm, "hbm_frac": hbm / peak, "hbm_peak_kind": kind,
             "algorithmic_bytes_per_cell_stage": bpcs,
+            "single_stage_hbm_roof": _single_stage_roof(rate_b, peak),
             "mass_finite": bool(np.all(np.isfinite(d)))}
+
+
+def _single_stage_roof(rate: float, hbm_peak: float) -> dict:
+    """The FP32 rate against the HBM roof of one launch per stage (the 74 B
+    per cell-stage that scheme must move): the highest rate any single-stage
+    FP32 kernel could reach at the measured copy bandwidth."""
+    bpcs = BYTES_PER_CELL_STAGE["f32_unfused"]
+    roof = hbm_peak * 1e9 / bpcs
+    return {"bytes_per_cell_stage": bpcs, "roof_rate": roof, "value_over_roof": rate / roof}
 
 
 def _adjoint(torch, nsteps: int = 0) -> dict:
