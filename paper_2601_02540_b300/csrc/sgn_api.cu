@@ -1142,8 +1142,10 @@ sgn_status sgn_create(const sgn_params* p, const void* b_dev, sgn_ctx** out) {
     const int tile_y = sgn::THREADS_Y * (p->prec == SGN_DF64  ? sgn::StageShape<sgn::df64>::rows
                                          : p->prec == SGN_F64 ? sgn::StageShape<double>::rows
                                                               : sgn::StageShape<float>::rows);
-    if ((p->ny + tile_y - 1) / tile_y > 65535)
-        return fail(SGN_E_INVAL, "ny = %d exceeds the launch-grid limit", p->ny);
+    // every launch over the grid fits the launch grid's y limit of 65535 blocks
+    // (the 32 x 8 launches, init_aux among them, are the tallest grids)
+    if ((p->ny + sgn::THREADS_Y - 1) / sgn::THREADS_Y > 65535 || (p->ny + tile_y - 1) / tile_y > 65535)
+        return fail(SGN_E_INVAL, "ny = %d exceeds the launch-grid limit (ny <= %d)", p->ny, 65535 * sgn::THREADS_Y);
     if (!(std::isfinite(p->xmin) && std::isfinite(p->xmax) && p->xmax > p->xmin &&
           std::isfinite(p->ymin) && std::isfinite(p->ymax) && p->ymax > p->ymin))
         return fail(SGN_E_INVAL, "domain must be finite with xmax > xmin and ymax > ymin");

@@ -414,7 +414,9 @@ sgn_status sgn_batch_create(const sgn_instance* inst, int ninst, int prec, const
     long long off = 0;
     for (int k = 0; k < ninst; k++) {
         const sgn_instance& p = inst[k];
-        if (p.nx < 3 || p.ny < 3 || (p.bc != SGN_BC_PERIODIC && p.bc != SGN_BC_REFLECTING) ||
+        // ny bound: the per-instance 32 x 8 launches (init_aux) fit the launch grid's y limit
+        if (p.nx < 3 || p.ny < 3 || p.ny > 65535 * sgn::THREADS_Y ||
+            (p.bc != SGN_BC_PERIODIC && p.bc != SGN_BC_REFLECTING) ||
             !(std::isfinite(p.xmin) && std::isfinite(p.xmax) && p.xmax > p.xmin && std::isfinite(p.ymin) &&
               std::isfinite(p.ymax) && p.ymax > p.ymin) ||
             !(std::isfinite(p.g) && p.g > 0) || !(std::isfinite(p.lambda) && p.lambda >= 0) ||

@@ -61,6 +61,15 @@ def test_create_rejects_bad_params_without_device(lib, field, value):
     assert lib.sgn_last_error().decode() != ""
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_create_rejects_grids_beyond_the_launch_limit_without_device(lib, prec):
+    p = sgn.Params(8, 65535 * 8 + 1, 0.0, 1.0, 0.0, 1.0, 0, 9.81, 500.0, prec)
+    ctx = ctypes.c_void_p(1234)
+    assert lib.sgn_create(ctypes.byref(p), None, ctypes.byref(ctx)) == 1
+    assert ctx.value is None
+    assert "launch-grid limit" in lib.sgn_last_error().decode()
+
+
 def test_null_context_is_rejected(lib):
     assert lib.sgn_rhs(None, None, None, None) == 1
     assert lib.sgn_step(None, None, 0.1, 1, None) == 1

@@ -240,3 +240,22 @@ def test_persistent_kernel_unsupported_cases_and_autotune():
     assert t["rows"] == rows and (rows in (1, 2) or not t["persistent"])
     assert torch.equal(q, bs.pack([p.q0 for p in probs]))   # autotune works on a copy
     bs.close()
+
+
+def test_batch_create_rejects_instances_beyond_the_launch_limit():
+    """An instance taller than 65535 rows of 8-node blocks is rejected before
+    any of its data is read (a small bathymetry buffer suffices)."""
+    import ctypes
+    b = torch.zeros(16, dtype=torch.float64, device="cuda")
+    for ny, ok in ((65535 * 8 + 1, False), (3, True)):
+        inst = sgn.Instance(3, ny, 0.0, 1.0, 0.0, 1.0, 0, 9.81, 500.0, 1e-3)
+        arr = (sgn.Instance * 1)(inst)
+        h = ctypes.c_void_p()
+        bb = torch.zeros(3 * ny, dtype=torch.float64, device="cuda") if ok else b
+        st = sgn.lib().sgn_batch_create(arr, 1, 0, ctypes.c_void_p(bb.data_ptr()), ctypes.byref(h))
+        if ok:
+            assert st == 0
+            sgn.lib().sgn_batch_destroy(h)
+        else:
+            assert st == 1 and h.value is None
+            assert "invalid instance" in sgn.lib().sgn_last_error().decode()
