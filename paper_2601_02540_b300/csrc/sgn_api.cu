@@ -189,9 +189,13 @@ StageArgs<TC, TIN, TA> base_args(const sgn_ctx* c) {
 template <typename TC, typename TA, int BC>
 cudaError_t run_steps_fused(sgn_ctx* c, TA* q, double dt, int nsteps, cudaStream_t s) {
     constexpr int R = sgn::StageShape<TC>::rows;
+    constexpr bool kW = sgn::kFusedW32<BC, sgn::FUSED_S34>;
+    // 32-bit element offsets (where the kernel takes them) for planes below 2^32 nodes
+    const bool w32 = kW && (unsigned long long)c->G.plane <= 0xffffffffull;
     const size_t smem = sgn::FusedLayout<R>::template bytes<TC>();
     cudaError_t e = smem_optin<sgn::k_fused<TC, TA, BC, sgn::FUSED_S12, R>>(smem);
     if (e == cudaSuccess) e = smem_optin<sgn::k_fused<TC, TA, BC, sgn::FUSED_S34, R>>(smem);
+    if (e == cudaSuccess && kW) e = smem_optin<sgn::k_fused<TC, TA, BC, sgn::FUSED_S34, R, kW>>(smem);
     if (e != cudaSuccess) return e;
     sgn::FusedArgs<TC, TA> f;
     std::memset(&f, 0, sizeof(f));
@@ -217,7 +221,10 @@ cudaError_t run_steps_fused(sgn_ctx* c, TA* q, double dt, int nsteps, cudaStream
         f34.q = cur;
         f34.X = static_cast<const TC*>(c->Qa);
         f34.out = nxt;
-        sgn::k_fused<TC, TA, BC, sgn::FUSED_S34, R><<<c->grid, block, smem, s>>>(f34);
+        if (w32)
+            sgn::k_fused<TC, TA, BC, sgn::FUSED_S34, R, kW><<<c->grid, block, smem, s>>>(f34);
+        else
+            sgn::k_fused<TC, TA, BC, sgn::FUSED_S34, R><<<c->grid, block, smem, s>>>(f34);
         count_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         std::swap(cur, nxt);
@@ -358,8 +365,10 @@ struct AttrOp {
         if constexpr (kK1) {
             // the fused kernels of run_steps_fused
             const size_t smem = sgn::FusedLayout<R>::template bytes<TC>();
+            constexpr bool kW = sgn::kFusedW32<BC, sgn::FUSED_S34>;
             cudaError_t ef = smem_optin<sgn::k_fused<TC, TA, BC, sgn::FUSED_S12, R>>(smem);
             if (ef == cudaSuccess) ef = smem_optin<sgn::k_fused<TC, TA, BC, sgn::FUSED_S34, R>>(smem);
+            if (ef == cudaSuccess && kW) ef = smem_optin<sgn::k_fused<TC, TA, BC, sgn::FUSED_S34, R, kW>>(smem);
             if (ef != cudaSuccess) return ef;
         }
         cudaError_t e = stage_attr<TC, TA, TA, BC, kK1 ? sgn::MODE_S1K : sgn::MODE_S1, R>();

@@ -136,11 +136,13 @@ struct BatchFusedArgs {
 };
 
 // Tile classes of a fused launch: every tile periodic, every tile reflecting,
-// or either (the boundary treatment read from the record).
+// or either (the boundary treatment read from the record).  W32: 32-bit
+// element offsets (every instance's plane below 2^32 nodes); in the batched
+// kernels they measured faster for both pairs and both classes.
 enum { CLS_MIXED = 0, CLS_PERIODIC = 1, CLS_REFLECTING = 2 };
 // (registers as the single-grid kernels of the class: the reflecting S34 for
 // three blocks per SM)
-template <typename TC, typename TA, int PAIR, int CLS>
+template <typename TC, typename TA, int PAIR, int CLS, bool W32 = false>
 __global__ void __launch_bounds__(BLOCK_THREADS, (kFusedMinBlocks<CLS == CLS_PERIODIC ? BC_PERIODIC : BC_REFLECTING, PAIR>))
 k_batch_fused(BatchFusedArgs<TC, TA> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -169,9 +171,9 @@ k_batch_fused(BatchFusedArgs<TC, TA> a) {
     f.c_q3 = (TA)d.c_q[2];
     TC* sm = reinterpret_cast<TC*>(smem_raw);
     if (CLS == CLS_PERIODIC || (CLS == CLS_MIXED && T.bc == BC_PERIODIC))
-        fused_tile<TC, TA, BC_PERIODIC, PAIR, 2>(f, G, T.i0, T.j0, sm);
+        fused_tile<TC, TA, BC_PERIODIC, PAIR, 2, W32>(f, G, T.i0, T.j0, sm);
     else
-        fused_tile<TC, TA, BC_REFLECTING, PAIR, 2>(f, G, T.i0, T.j0, sm);
+        fused_tile<TC, TA, BC_REFLECTING, PAIR, 2, W32>(f, G, T.i0, T.j0, sm);
 }
 
 // Per-instance sums of the band partials, in band order (one block each; the

@@ -71,8 +71,26 @@ struct FusedLayout {
     static constexpr size_t bytes() { return ((size_t)NP2 * HN2 + (size_t)NF_OPS * HN1) * sizeof(TC); }
 };
 
+// Global element offsets within a plane: 64-bit, or with W32 32-bit (one
+// multiply-add forms each address from the plane's base; planes of fewer than
+// 2^32 nodes).  The single-grid launches use 32-bit offsets where they
+// measured faster: the periodic S34 (1.1% on the FP32 step at 8192^2; slower
+// in S12 and in the reflecting S34); the batched kernels in every pair (see
+// k_batch_fused).  The results are the same bit for bit.
+template <int BC, int PAIR>
+constexpr bool kFusedW32 = BC == BC_PERIODIC && PAIR == FUSED_S34;
+
+// Element c of plane f of a plane-major array (plane size P).
+template <bool W32, typename T, typename IX>
+__device__ __forceinline__ T& plane_at(T* base, int f, long long P, IX c) {
+    if constexpr (W32)
+        return (base + f * P)[c];
+    else
+        return base[f * P + c];
+}
+
 // One fused output tile (32 x 8R nodes at (i0, j0)) of the pair PAIR.
-template <typename TC, typename TA, int BC, int PAIR, int R>
+template <typename TC, typename TA, int BC, int PAIR, int R, bool W32 = false>
 __device__ __forceinline__ void fused_tile(const FusedArgs<TC, TA>& a, const Geom& G, int i0, int j0,
                                            TC* __restrict__ sm) {
     static_assert(TileLayout<TC>::factored && std::is_same<TC, TA>::value, "the FP32 mode");
@@ -82,6 +100,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<TC, TA>& a, const Geo
     TC* s2 = sm;
     TC* s1 = sm + L::NP2 * HN2;
     const long long P = G.plane;
+    using IX = typename std::conditional<W32, unsigned, long long>::type;
     const int tid = threadIdx.y * TILE_X + threadIdx.x;
     int bad = 0;
 
@@ -130,17 +149,17 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<TC, TA>& a, const Geo
 #pragma unroll
         for (int k = 0; k < NIT; k++) {
             if (it1[k] < 0) continue;
-            const long long c = (long long)igy[k] * G.nx + igx[k];
+            const IX c = (IX)igy[k] * (IX)G.nx + (IX)igx[k];
 #pragma unroll
-            for (int f = 0; f < 5; f++) qn[k][f] = a.q[f * P + c];
+            for (int f = 0; f < 5; f++) qn[k][f] = plane_at<W32>(a.q, f, P, c);
         }
 #pragma unroll
         for (int k = 0; k < R; k++) {
             const int gi = i0 + threadIdx.x, gj = j0 + threadIdx.y + k * THREADS_Y;
             if (gi >= G.nx || gj >= G.ny) continue;
-            const long long c = (long long)gj * G.nx + gi;
+            const IX c = (IX)gj * (IX)G.nx + (IX)gi;
 #pragma unroll
-            for (int f = 0; f < 5; f++) av[k][f] = a.acc[f * P + c];
+            for (int f = 0; f < 5; f++) av[k][f] = plane_at<W32>(a.acc, f, P, c);
         }
     }
 
@@ -164,9 +183,9 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<TC, TA>& a, const Geo
             continue;
         }
         ok[k] = true;
-        const long long c = (long long)gy * G.nx + gx;
+        const IX c = (IX)gy * (IX)G.nx + (IX)gx;
 #pragma unroll
-        for (int f = 0; f < 5; f++) rv[k][f] = (PAIR == FUSED_S12) ? cvt<TC>(a.q[f * P + c]) : a.X[f * P + c];
+        for (int f = 0; f < 5; f++) rv[k][f] = (PAIR == FUSED_S12) ? cvt<TC>(plane_at<W32>(a.q, f, P, c)) : plane_at<W32>(a.X, f, P, c);
         rb[k] = a.b[c];
     }
 #pragma unroll
@@ -231,17 +250,17 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<TC, TA>& a, const Geo
         const int t1 = (threadIdx.y + k * THREADS_Y + 1) * HX1 + threadIdx.x + 1;
         TC kk[5];
         node_rhs<TC, BC, HX1, HN1, true>(s1, t1, gi, gj, G, kk);
-        const long long c = (long long)gj * G.nx + gi;
+        const IX c = (IX)gj * (IX)G.nx + (IX)gi;
 #pragma unroll
         for (int f = 0; f < 5; f++) {
             const TA kv = cvt<TA>(kk[f]);
             if constexpr (PAIR == FUSED_S12) {
                 // as S2K: acc = (q_n + dt/6 k1) + dt/3 k2, Q3 = q_n + dt/2 k2
-                a.acc[f * P + c] = fma_(a.c_a2, kv, fma_(a.c_a1, cvt<TA>(k1[k][f]), qk[k][f]));
-                a.Qout[f * P + c] = stage_state<TC, TA>(a.c_q2, kk[f], kv, qk[k][f]);
+                plane_at<W32>(a.acc, f, P, c) = fma_(a.c_a2, kv, fma_(a.c_a1, cvt<TA>(k1[k][f]), qk[k][f]));
+                plane_at<W32>(a.Qout, f, P, c) = stage_state<TC, TA>(a.c_q2, kk[f], kv, qk[k][f]);
             } else {
                 // as S4: q_{n+1} = (acc + dt/3 k3) + dt/6 k4
-                a.out[f * P + c] = fma_(a.c_a4, kv, a3[k][f]);
+                plane_at<W32>(a.out, f, P, c) = fma_(a.c_a4, kv, a3[k][f]);
             }
         }
     }
@@ -253,10 +272,10 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<TC, TA>& a, const Geo
 // which would spill under that bound and runs 4% faster with three.
 template <int BC, int PAIR>
 constexpr int kFusedMinBlocks = (BC == BC_REFLECTING && PAIR == FUSED_S34) ? 3 : 4;
-template <typename TC, typename TA, int BC, int PAIR, int R>
+template <typename TC, typename TA, int BC, int PAIR, int R, bool W32 = false>
 __global__ void __launch_bounds__(BLOCK_THREADS, (kFusedMinBlocks<BC, PAIR>)) k_fused(FusedArgs<TC, TA> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fused_tile<TC, TA, BC, PAIR, R>(a, a.G, blockIdx.x * TILE_X, blockIdx.y * (THREADS_Y * R),
+    fused_tile<TC, TA, BC, PAIR, R, W32>(a, a.G, blockIdx.x * TILE_X, blockIdx.y * (THREADS_Y * R),
                                     reinterpret_cast<TC*>(smem_raw));
 }
 
