@@ -135,7 +135,8 @@ SGN_API sgn_status sgn_init_aux(sgn_ctx* ctx, void* q_dev, void* stream);
 SGN_API sgn_status sgn_rhs(sgn_ctx* ctx, const void* q_dev, void* dq_dev, void* stream);
 
 /* Advance q_dev (state type, in place) by nsteps >= 0 classical RK4 steps of
- * size dt (finite, > 0): 4 fused RHS+stage launches per step.  On grids of at
+ * size dt (finite, > 0): 4 fused RHS+stage launches per step (SGN_F32: 2, two
+ * stages per launch, unless sgn_set_stage_fusion turns that off).  On grids of at
  * most 2^21 nodes (launch-bound) runs of 50 steps are replayed from a CUDA
  * graph, captured on the context's first such call for this (q_dev, dt) on a
  * private stream; the launches and results are those of the direct path.
@@ -380,7 +381,8 @@ SGN_API sgn_status sgn_step_adaptive(sgn_ctx* ctx, void* q_dev, double t0, doubl
 
 /* ---- Ragged ensembles ----------------------------------------------------
  * Many independent grids (each its own size, boundary treatment, parameters
- * and fixed time step) advanced together: one launch per RK4 stage covers a
+ * and fixed time step) advanced together: one launch per RK4 stage (SGN_F32:
+ * per two stages and boundary class, see sgn_batch_set_stage_fusion) covers a
  * tile list spanning every instance, and sgn_batch_step replays CUDA graphs of
  * 26 steps.  The arithmetic per node is the single-grid kernel's, in the same
  * order, so each instance evolves exactly as with sgn_step.
