@@ -199,3 +199,25 @@ def test_stage_fusion_is_for_fp32():
             s.set_stage_fusion(True)
         assert ei.value.status == 7          # SGN_E_UNSUPPORTED
         s.close()
+
+
+@pytest.mark.parametrize("bc", [PERIODIC, REFLECTING])
+@pytest.mark.parametrize("j,i", [(0, 0), (7, 31), (16, 32), (15, 63), (40, 77), (69, 129)])
+def test_fp32_two_stage_step_reports_bad_water_height(bc, j, i):
+    """The two-stage FP32 launches check h where they stage it: a negative or
+    NaN water height at a grid corner, on a tile's edge or corner, or inside
+    a tile is reported after one step (non-positive: status 4, non-finite:
+    5), and the flag is cleared by the report."""
+    p = inputs.smooth_state(130, 70, bc, seed=3)
+    s = gu.solver(p, "f32")
+    for val, status in ((-0.5, 4), (float("nan"), 5)):
+        q = s.state(p.q0)
+        q[0, j, i] = val
+        s.step(q, p.dt, 1)
+        with pytest.raises(sgn.SgnError) as ei:
+            s.check()
+        assert ei.value.status == status, (val, ei.value.status)
+    q = s.state(p.q0)
+    s.step(q, p.dt, 1)
+    s.check()
+    s.close()
