@@ -162,7 +162,7 @@ SGN_API sgn_status sgn_step_diag(sgn_ctx* ctx, void* q_dev, double dt, int nstep
  * (host, 3*nsteps doubles: mass, energy and shifted energy after each step),
  * and copies the result back over q_host.  One copy each way per call, on
  * `stream`; page-locked q_host moves at the link rate, pageable memory goes
- * through the driver's staging.  Synchronizes `stream` and reports a latched
+ * through the CUDA runtime's staging buffers.  Synchronizes `stream` and reports a latched
  * h <= 0 / non-finite flag (the state is not copied back when the steps
  * report an error).  q_host in device memory is SGN_E_INVAL.  The first call
  * allocates the device state (5 planes), kept until sgn_destroy; calls on one

@@ -756,7 +756,7 @@ int orc_rk_adaptive(const orc_grid* G, const double* b, double* q, double t0, do
  * method with the FSAL property and an embedded error estimator, optimized
  * for stability-limited discretizations of hyperbolic problems; the paper
  * does not print its coefficients.  The pair below has exactly these
- * properties; its coefficients were constructed for this build:
+ * properties; its coefficients were constructed to them here:
  *  - stability polynomial R(z) = 1 + z + z^2/2 + z^3/6 + 0.0324 z^4 + 0.006 z^5
  *    (|R(iy)| <= 1 for |y| <= 3.8798: the central SBP operators give an
  *    imaginary spectrum; classical RK4 reaches 2.83 with four stages);
