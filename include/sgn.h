@@ -101,7 +101,7 @@ typedef enum { SGN_F64 = 0, SGN_F32 = 1, SGN_F32_F64ACC = 2, SGN_DF64 = 3 } sgn_
 typedef struct {
     int nx, ny;                    /* nodes per direction, each >= 3; ny <= 524280
                                       (65535 rows of 8-node blocks: the launch grid's
-                                      y limit) */
+                                      y limit); nx*ny < 2^32 except for SGN_F64 */
     double xmin, xmax, ymin, ymax; /* domain, xmax > xmin, ymax > ymin */
     int bc;                        /* sgn_bc, both directions */
     double g;                      /* gravitational acceleration, > 0 */
@@ -392,7 +392,8 @@ SGN_API sgn_status sgn_step_adaptive(sgn_ctx* ctx, void* q_dev, double t0, doubl
  * (double).  State: five planes per instance at 5*off_i (state type of prec),
  * each plane nx_i*ny_i values, x fastest. */
 typedef struct {
-    int nx, ny;                    /* >= 3; ny <= 524280 as in sgn_params */
+    int nx, ny;                    /* >= 3; ny <= 524280 and nx*ny < 2^32 (the batched
+                                      precisions other than SGN_F64) as in sgn_params */
     double xmin, xmax, ymin, ymax;
     int bc;                        /* sgn_bc */
     double g, lambda;

@@ -1155,6 +1155,9 @@ sgn_status sgn_create(const sgn_params* p, const void* b_dev, sgn_ctx** out) {
     // (the 32 x 8 launches, init_aux among them, are the tallest grids)
     if ((p->ny + sgn::THREADS_Y - 1) / sgn::THREADS_Y > 65535 || (p->ny + tile_y - 1) / tile_y > 65535)
         return fail(SGN_E_INVAL, "ny = %d exceeds the launch-grid limit (ny <= %d)", p->ny, 65535 * sgn::THREADS_Y);
+    // the float-based kernels address a plane with 32-bit offsets
+    if (p->prec != SGN_F64 && (long long)p->nx * p->ny > 0xffffffffLL)
+        return fail(SGN_E_INVAL, "grids of 2^32 or more nodes need SGN_F64 (%d x %d)", p->nx, p->ny);
     if (!(std::isfinite(p->xmin) && std::isfinite(p->xmax) && p->xmax > p->xmin &&
           std::isfinite(p->ymin) && std::isfinite(p->ymax) && p->ymax > p->ymin))
         return fail(SGN_E_INVAL, "domain must be finite with xmax > xmin and ymax > ymin");

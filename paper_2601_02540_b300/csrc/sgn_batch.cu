@@ -431,7 +431,9 @@ sgn_status sgn_batch_create(const sgn_instance* inst, int ninst, int prec, const
     for (int k = 0; k < ninst; k++) {
         const sgn_instance& p = inst[k];
         // ny bound: the per-instance 32 x 8 launches (init_aux) fit the launch grid's y limit
+        // and below 2^32 nodes for the float-based kernels (32-bit offsets within a plane)
         if (p.nx < 3 || p.ny < 3 || p.ny > 65535 * sgn::THREADS_Y ||
+            (prec != SGN_F64 && (long long)p.nx * p.ny > 0xffffffffLL) ||
             (p.bc != SGN_BC_PERIODIC && p.bc != SGN_BC_REFLECTING) ||
             !(std::isfinite(p.xmin) && std::isfinite(p.xmax) && p.xmax > p.xmin && std::isfinite(p.ymin) &&
               std::isfinite(p.ymax) && p.ymax > p.ymin) ||

@@ -80,14 +80,6 @@ struct FusedLayout {
 template <int BC, int PAIR>
 constexpr bool kFusedW32 = BC == BC_PERIODIC && PAIR == FUSED_S34;
 
-// Element c of plane f of a plane-major array (plane size P).
-template <bool W32, typename T, typename IX>
-__device__ __forceinline__ T& plane_at(T* base, int f, long long P, IX c) {
-    if constexpr (W32)
-        return (base + f * P)[c];
-    else
-        return base[f * P + c];
-}
 
 // One fused output tile (32 x 8R nodes at (i0, j0)) of the pair PAIR.
 template <typename TC, typename TA, int BC, int PAIR, int R, bool W32 = false>

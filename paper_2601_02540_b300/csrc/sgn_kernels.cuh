@@ -293,6 +293,25 @@ __device__ __forceinline__ float recip<float>(float h) {
 template <>
 __device__ __forceinline__ df64 recip<df64>(df64 h) { return recip_df64(h); }
 
+// Element offsets within a plane: 32-bit for the float-based compute types
+// (each address one multiply-add from the plane's base; sgn_create and
+// sgn_batch_create admit their grids only below 2^32 nodes, which every such
+// grid that fits in the device's memory is), 64-bit for FP64.  Measured: the
+// mixed-mode step 5% faster, the single-stage FP32 step 0.5%; the FP64 and
+// df64 kernels unchanged.
+template <typename TC>
+constexpr bool kW32 = !std::is_same<TC, double>::value;
+template <typename TC>
+using SIdx = typename std::conditional<kW32<TC>, unsigned, long long>::type;
+// Element c of plane f of a plane-major array (plane size P).
+template <bool W32, typename T, typename IX>
+__device__ __forceinline__ T& plane_at(T* base, int f, long long P, IX c) {
+    if constexpr (W32)
+        return (base + f * P)[c];
+    else
+        return base[f * P + c];
+}
+
 // Explicitly rounded arithmetic for the per-node RHS and stage algebra:
 // products and sums that the compiler may not fuse, and fused multiply-adds
 // where fusion is intended.  Every kernel that inlines the same code then
@@ -704,18 +723,18 @@ __device__ __forceinline__ void tile_load(const StageArgs<TC, TIN, TA>& a, const
             in.bad |= FLAG_BOUNDS;
             continue;
         }
-        const long long c = (long long)gy * G.nx + gx;
-        rh[k] = a.X[c];
-        ru[k] = a.X[P + c];
-        rv[k] = a.X[2 * P + c];
-        rw[k] = a.X[3 * P + c];
-        re[k] = a.X[4 * P + c];
+        const SIdx<TC> c = (SIdx<TC>)gy * (SIdx<TC>)G.nx + (SIdx<TC>)gx;
+        rh[k] = plane_at<kW32<TC>>(a.X, 0, P, c);
+        ru[k] = plane_at<kW32<TC>>(a.X, 1, P, c);
+        rv[k] = plane_at<kW32<TC>>(a.X, 2, P, c);
+        rw[k] = plane_at<kW32<TC>>(a.X, 3, P, c);
+        re[k] = plane_at<kW32<TC>>(a.X, 4, P, c);
         if (MODE == MODE_S2K) {
-            qh[k] = a.qn[c];
-            qu[k] = a.qn[P + c];
-            qv[k] = a.qn[2 * P + c];
-            qw[k] = a.qn[3 * P + c];
-            qe[k] = a.qn[4 * P + c];
+            qh[k] = plane_at<kW32<TC>>(a.qn, 0, P, c);
+            qu[k] = plane_at<kW32<TC>>(a.qn, 1, P, c);
+            qv[k] = plane_at<kW32<TC>>(a.qn, 2, P, c);
+            qw[k] = plane_at<kW32<TC>>(a.qn, 3, P, c);
+            qe[k] = plane_at<kW32<TC>>(a.qn, 4, P, c);
         }
         in.b[k] = a.b[c];
     }
@@ -783,11 +802,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
         for (int ry = 0; ry < ROWS_PER_THREAD; ry++) {
             const int gj = j0 + threadIdx.y + ry * THREADS_Y;
             if (gi >= G.nx || gj >= G.ny) continue;
-            const long long c = (long long)gj * G.nx + gi;
+            const SIdx<TC> c = (SIdx<TC>)gj * (SIdx<TC>)G.nx + (SIdx<TC>)gi;
 #pragma unroll
             for (int f = 0; f < 5; f++) {
-                if (MODE != MODE_S4 && MODE != MODE_S4D) pq[ry][f] = a.qn[f * P + c];
-                if (MODE != MODE_S1) pa[ry][f] = a.acc[f * P + c];
+                if (MODE != MODE_S4 && MODE != MODE_S4D) pq[ry][f] = plane_at<kW32<TC>>(a.qn, f, P, c);
+                if (MODE != MODE_S1) pa[ry][f] = plane_at<kW32<TC>>(a.acc, f, P, c);
             }
         }
     }
@@ -834,11 +853,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
                 tt[k] = -1;
                 continue;
             }
-            const long long c = (long long)gy * G.nx + gx;
+            const SIdx<TC> c = (SIdx<TC>)gy * (SIdx<TC>)G.nx + (SIdx<TC>)gx;
 #pragma unroll
             for (int f = 0; f < 5; f++) {
-                rk[k][f] = a.X[f * P + c];
-                rq[k][f] = a.qn[f * P + c];
+                rk[k][f] = plane_at<kW32<TC>>(a.X, f, P, c);
+                rq[k][f] = plane_at<kW32<TC>>(a.qn, f, P, c);
             }
             rb[k] = a.b[c];
         }
@@ -888,12 +907,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
                 bad |= FLAG_BOUNDS;
                 continue;
             }
-            const long long c = (long long)gy * G.nx + gx;
-            h = cvt<TC>(a.X[c]);
-            u = cvt<TC>(a.X[P + c]);
-            v = cvt<TC>(a.X[2 * P + c]);
-            w = cvt<TC>(a.X[3 * P + c]);
-            eta = cvt<TC>(a.X[4 * P + c]);
+            const SIdx<TC> c = (SIdx<TC>)gy * (SIdx<TC>)G.nx + (SIdx<TC>)gx;
+            h = cvt<TC>(plane_at<kW32<TC>>(a.X, 0, P, c));
+            u = cvt<TC>(plane_at<kW32<TC>>(a.X, 1, P, c));
+            v = cvt<TC>(plane_at<kW32<TC>>(a.X, 2, P, c));
+            w = cvt<TC>(plane_at<kW32<TC>>(a.X, 3, P, c));
+            eta = cvt<TC>(plane_at<kW32<TC>>(a.X, 4, P, c));
             bb = a.b[c];
         }
         bad |= h_flags(h);
@@ -918,7 +937,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
         if (gi >= G.nx || gj >= G.ny) continue;
         const int t = (ly + 1) * HALO_X + (threadIdx.x + 1);
         TC k[5];
-        const long long c = (long long)gj * G.nx + gi;
+        const SIdx<TC> c = (SIdx<TC>)gj * (SIdx<TC>)G.nx + (SIdx<TC>)gi;
         if constexpr (TAPE) {
             static_assert(std::is_same<TC, double>::value, "the tape is written by the FP64 kernels");
             TC tp[N_TAPE];
@@ -931,40 +950,40 @@ __device__ __forceinline__ void stage_tile(const StageArgs<TC, TIN, TA>& a, cons
         }
         if (MODE == MODE_RHS) {
 #pragma unroll
-            for (int f = 0; f < 5; f++) a.out[f * P + c] = cvt<TA>(k[f]);
+            for (int f = 0; f < 5; f++) plane_at<kW32<TC>>(a.out, f, P, c) = cvt<TA>(k[f]);
         } else if (MODE == MODE_S1 || MODE == MODE_S2 || MODE == MODE_S3) {
 #pragma unroll
             for (int f = 0; f < 5; f++) {
-                const TA qv = kEarlyStage ? pq[ry][f] : a.qn[f * P + c];
+                const TA qv = kEarlyStage ? pq[ry][f] : plane_at<kW32<TC>>(a.qn, f, P, c);
                 const TA kv = cvt<TA>(k[f]);
-                const TA av = (MODE == MODE_S1) ? qv : (kEarlyStage ? pa[ry][f] : a.acc[f * P + c]);
-                a.acc[f * P + c] = fma_(a.c_acc, kv, av);
-                a.Qout[f * P + c] = stage_state<TC, TA>(a.c_q, k[f], kv, qv);
+                const TA av = (MODE == MODE_S1) ? qv : (kEarlyStage ? pa[ry][f] : plane_at<kW32<TC>>(a.acc, f, P, c));
+                plane_at<kW32<TC>>(a.acc, f, P, c) = fma_(a.c_acc, kv, av);
+                plane_at<kW32<TC>>(a.Qout, f, P, c) = stage_state<TC, TA>(a.c_q, k[f], kv, qv);
             }
         } else if (MODE == MODE_S1K) {
 #pragma unroll
-            for (int f = 0; f < 5; f++) a.Qout[f * P + c] = k[f];
+            for (int f = 0; f < 5; f++) plane_at<kW32<TC>>(a.Qout, f, P, c) = k[f];
         } else if (MODE == MODE_S2K) {
 #pragma unroll
             for (int f = 0; f < 5; f++) {
                 const TA qv = pq[ry][f];
                 const TA kv = cvt<TA>(k[f]);
-                a.acc[f * P + c] = fma_(a.c_acc, kv, fma_(a.c_acc1, cvt<TA>(pk[ry][f]), qv));
-                a.Qout[f * P + c] = stage_state<TC, TA>(a.c_q, k[f], kv, qv);
+                plane_at<kW32<TC>>(a.acc, f, P, c) = fma_(a.c_acc, kv, fma_(a.c_acc1, cvt<TA>(pk[ry][f]), qv));
+                plane_at<kW32<TC>>(a.Qout, f, P, c) = stage_state<TC, TA>(a.c_q, k[f], kv, qv);
             }
         } else if (MODE == MODE_S4 || MODE == MODE_S4D) {
             double qn1[5];
 #pragma unroll
             for (int f = 0; f < 5; f++) {
-                const TA o = fma_(a.c_acc, cvt<TA>(k[f]), kEarlyStage ? pa[ry][f] : a.acc[f * P + c]);
-                a.out[f * P + c] = o;
+                const TA o = fma_(a.c_acc, cvt<TA>(k[f]), kEarlyStage ? pa[ry][f] : plane_at<kW32<TC>>(a.acc, f, P, c));
+                plane_at<kW32<TC>>(a.out, f, P, c) = o;
                 qn1[f] = cvt<double>(o);
             }
             if (MODE == MODE_S4D) node_mass_energy<BC>(qn1, a.b64[c], gi, gj, G, dsum[ry]);
         } else if (MODE == MODE_DIAG) {
             double qd[5];
 #pragma unroll
-            for (int f = 0; f < 5; f++) qd[f] = cvt<double>(a.X[f * P + c]);
+            for (int f = 0; f < 5; f++) qd[f] = cvt<double>(plane_at<kW32<TC>>(a.X, f, P, c));
             node_diag<TC, BC>(qd, a.b64[c], gi, gj, G, k, dsum[ry]);
         }
     }

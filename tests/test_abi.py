@@ -70,6 +70,15 @@ def test_create_rejects_grids_beyond_the_launch_limit_without_device(lib, prec):
     assert "launch-grid limit" in lib.sgn_last_error().decode()
 
 
+@pytest.mark.parametrize("prec,rejected", [(0, False), (1, True), (2, True), (3, True)])
+def test_create_rejects_float_grids_of_2_32_nodes_without_device(lib, prec, rejected):
+    p = sgn.Params(65536, 65537, 0.0, 1.0, 0.0, 1.0, 0, 9.81, 500.0, prec)
+    ctx = ctypes.c_void_p(1234)
+    assert lib.sgn_create(ctypes.byref(p), None, ctypes.byref(ctx)) == 1     # FP64: no b_dev
+    assert ctx.value is None
+    assert ("2^32" in lib.sgn_last_error().decode()) == rejected
+
+
 def test_null_context_is_rejected(lib):
     assert lib.sgn_rhs(None, None, None, None) == 1
     assert lib.sgn_step(None, None, 0.1, 1, None) == 1
